@@ -1,0 +1,130 @@
+"""Pins of the oracle's layout: the paper's worked slot examples (tests/golden), the
+operation counts of Tab. 2 and Tab. 3, and exactness of the cleartext model against X y."""
+import json
+import os
+
+import numpy as np
+import pytest
+import sympy
+
+from oracle import layout
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")))
+
+
+def _sym_matrix(m, n):
+    """X[i, j] = symbol '<letter i><j>' as a sympy symbol."""
+    return np.array([[sympy.Symbol(f"{chr(65 + i)}{j}") for j in range(n)] for i in range(m)], dtype=object)
+
+
+def _diag_symbols(plan, X):
+    """Same index formula as layout.diagonal_slots, evaluated on symbols (object dtype)."""
+    # diagonal_slots works on float arrays; evaluate it on integer codes and map back
+    m, n = X.shape
+    codes = np.arange(1, m * n + 1, dtype=np.float64).reshape(m, n)
+    E = layout.diagonal_slots(codes, plan)
+    flat = X.reshape(-1)
+    return np.vectorize(lambda c: flat[int(c) - 1] if c else 0, otypes=[object])(E)
+
+
+def test_worked_example_diagonal_m4_n2():
+    ex = GOLD["diagonal_m4_n2"]
+    plan = layout.make_plan(ex["m"], ex["n"], ex["slots"])
+    X = _sym_matrix(4, 2)
+    E = _diag_symbols(plan, X)
+    assert [str(v) for v in E[0, 0, 0]] == ex["e0"]
+    codes = layout.vector_slots(np.array([1.0, 2.0]), plan)[0]
+    assert [f"M{int(c) - 1}" for c in codes] == ex["y_replicated"]
+
+
+def test_worked_example_input_packing():
+    ex = GOLD["input_packing_m4_n4_slots8"]
+    plan = layout.make_plan(ex["m"], ex["n"], ex["slots"])
+    assert plan.m_prime == 2 and plan.regime == "pack"
+    E = _diag_symbols(plan, _sym_matrix(4, 4))
+    assert [str(v) for v in E[0, 0, 1]] == ex["e1"]
+    codes = layout.vector_slots(np.array([1.0, 2.0, 3.0, 4.0]), plan)[0]
+    assert [f"M{int(c) - 1}" for c in codes] == ex["y_replicated"]
+
+
+def test_worked_example_lazy_ras():
+    ex = GOLD["lazy_ras_m4_n4_slots8"]
+    plan = layout.make_plan(4, 4, 8)
+    X = _sym_matrix(4, 4)
+    M = [sympy.Symbol(f"M{j}") for j in range(4)]
+    E = _diag_symbols(plan, X)
+    yrep = [M[s % 4] for s in range(8)]
+    slots = [sum(E[0, 0, i, s] * yrep[(s + i) % 8] for i in range(plan.m_prime)) for s in range(8)]
+
+    def parse(terms):
+        return sum(sympy.Symbol(t[:2]) * sympy.Symbol(t[2:]) for t in terms)
+
+    for s, terms in enumerate(ex["slots_first4"]):
+        assert sympy.expand(slots[s] - parse(terms)) == 0
+    # lazy RaS on symbols: out[b*m' + t] = sum_s slot[b*n + t + s*m']
+    out = [sum(slots[b * 4 + t + s * 2] for s in range(2)) for b in range(2) for t in range(2)]
+    for row, terms in enumerate(ex["result"]):
+        assert sympy.expand(out[row] - parse(terms)) == 0
+    # and layout.lazy_ras applies exactly that map
+    probe = np.zeros((1, 8))
+    probe[0] = np.arange(8) * 10.0 ** np.arange(8)
+    got = layout.lazy_ras(probe, plan)
+    want = [probe[0, 0] + probe[0, 2], probe[0, 1] + probe[0, 3], probe[0, 4] + probe[0, 6], probe[0, 5] + probe[0, 7]]
+    assert np.allclose(got, want)
+
+
+def test_rotation_direction_examples():
+    ex = GOLD["rotl_naive"]
+    assert list(layout.rotl(np.array(ex["input"], dtype=object), ex["step"]))[0] == ex["output_slot0"]
+    ex = GOLD["rotr_gala"]
+    # RotR is the inverse of RotL
+    assert list(layout.rotl(np.array(ex["input"], dtype=object), -ex["right_step"])) == ex["output"]
+
+
+# (m, n, N') and the paper's counts: Tab. 2 PackVFL row (m, n <= N'), Tab. 3 columns
+@pytest.mark.parametrize("m,n,slots", [(4, 4, 8), (16, 64, 2048), (256, 1024, 4096), (1024, 256, 4096), (64, 64, 4096),
+                                       (8192, 512, 4096), (16384, 64, 4096), (512, 8192, 4096), (64, 16384, 4096),
+                                       (8192, 8192, 4096), (16384, 8192, 4096)])
+def test_op_counts_match_tables(m, n, slots):
+    plan = layout.make_plan(m, n, slots)
+    if m <= slots and n <= slots:
+        mp = -(-m * n // slots)
+        assert (plan.n_add, plan.n_mult, plan.n_rot, plan.n_hstrot) == (mp - 1, mp, 0, mp - 1)
+        assert (plan.col_blocks, plan.row_blocks) == (1, 1)
+    elif m > slots >= n:
+        assert plan.n_add == (m * n - m) // slots
+        assert plan.n_mult == m * n // slots
+        assert plan.n_hstrot == n - 1
+        assert (plan.col_blocks, plan.row_blocks) == (1, m // slots)
+    elif m <= slots < n:
+        assert plan.n_add == (n * m - slots) // slots
+        assert plan.n_mult == m * n // slots
+        assert plan.n_hstrot == (m * n - n) // slots
+        assert (plan.col_blocks, plan.row_blocks) == (n // slots, 1)
+    else:
+        assert plan.n_mult == m * n // slots
+        assert plan.n_hstrot == (n * slots - n) // slots
+        assert (plan.col_blocks, plan.row_blocks) == (n // slots, m // slots)
+        # Tab. 3 prints mn/N' - 1 additions; summing each of the m/N' outputs separately takes
+        # mn/N' - m/N' (equal when m = N')
+        assert plan.n_add == m * n // slots - m // slots
+    assert plan.n_rot == 0
+
+
+@pytest.mark.parametrize("m,n,slots", [(4, 4, 8), (4, 2, 4), (16, 64, 2048), (64, 16, 2048), (256, 1024, 4096), (1024, 256, 4096),
+                                       (3, 5, 8), (100, 37, 64), (1, 1, 8), (130, 20, 64), (20, 130, 64), (130, 130, 64),
+                                       (64, 64, 64), (8, 1, 16), (1, 8, 16)])
+def test_cleartext_model_is_exact(m, n, slots):
+    rng = np.random.default_rng(m * 1000 + n)
+    X = rng.integers(-9, 10, size=(m, n)).astype(np.float64)
+    y = rng.integers(-9, 10, size=n).astype(np.float64)
+    plan = layout.make_plan(m, n, slots)
+    _, out = layout.cleartext_model(X, y, plan)
+    assert np.array_equal(out, X @ y)
+
+
+def test_plan_rejects_bad_input():
+    with pytest.raises(ValueError):
+        layout.make_plan(0, 4, 8)
+    with pytest.raises(ValueError):
+        layout.make_plan(4, 4, 6)

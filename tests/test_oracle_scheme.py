@@ -1,0 +1,219 @@
+"""Pins of the oracle's scheme: exact big-integer checks of ModUp, ModDown, rescale and the
+Galois-key relation (Python integers, CRT), homomorphism invariants of O1-O4 (Sec. 2.2),
+and the MatMult against the FP64 product X y (Eq. 1) within the stated tolerance."""
+import numpy as np
+import pytest
+
+from oracle import ckks, layout
+
+TOL_2_40 = 1e-4
+
+
+def crt(limbs, primes):
+    """Residues -> the integer in [0, prod primes)."""
+    M = 1
+    for q in primes:
+        M *= q
+    x = 0
+    for r, q in zip(limbs, primes):
+        Mq = M // q
+        x += int(r) * Mq * pow(Mq, -1, q)
+    return x % M, M
+
+
+@pytest.fixture(scope="module")
+def small():
+    # three Q primes, digits of one prime each, plus a two-prime P to exercise alpha > 1 elsewhere
+    return ckks.Oracle(log_n=5, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=1)
+
+
+@pytest.fixture(scope="module")
+def small_alpha2():
+    return ckks.Oracle(log_n=5, q_bits=[50, 40, 40, 40], p_bits=[55, 55], dnum=2, seed=2)
+
+
+def _rand_limbs(rng, primes, n):
+    return np.array([[int(v) % q for v in rng.integers(0, 1 << 62, size=n, dtype=np.int64)] for q in primes], dtype=np.uint64)
+
+
+@pytest.mark.parametrize("which", ["small", "small_alpha2"])
+def test_modup_is_exact_fast_base_conversion(which, request):
+    o = request.getfixturevalue(which)
+    rng = np.random.default_rng(0)
+    level = o.L - 1
+    c1 = _rand_limbs(rng, o.q, o.n)
+    D = o.modup(c1, level)
+    al = -(-o.L // o.dnum)
+    ext = o.level_primes(level, True)
+    for d in range(D.shape[0]):
+        dig = list(range(d * al, min((d + 1) * al, level + 1)))
+        Qd = 1
+        for i in dig:
+            Qd *= o.q[i]
+        for k in range(o.n):
+            xs = [int(c1[i, k]) for i in dig]
+            # sum_i [x_i (Qd/q_i)^-1]_{q_i} (Qd/q_i): an integer congruent to the digit value mod Qd,
+            # equal to it plus a multiple u*Qd with 0 <= u < len(digit)
+            v = sum((x * pow(Qd // o.q[i], -1, o.q[i]) % o.q[i]) * (Qd // o.q[i]) for x, i in zip(xs, dig))
+            exact, _ = crt(xs, [o.q[i] for i in dig])
+            assert (v - exact) % Qd == 0 and 0 <= (v - exact) // Qd < len(dig)
+            for u, t in enumerate(ext):
+                assert int(D[d, u, k]) == v % t
+
+
+@pytest.mark.parametrize("which", ["small", "small_alpha2"])
+def test_moddown_divides_by_p(which, request):
+    o = request.getfixturevalue(which)
+    rng = np.random.default_rng(1)
+    level = o.L - 1
+    ext = o.level_primes(level, True)
+    x = _rand_limbs(rng, ext, o.n)
+    out = o.moddown(x, level)
+    P = o.P
+    for k in range(o.n):
+        X, M = crt(x[:, k], ext)
+        for j, q in enumerate(o.q[: level + 1]):
+            # (X - (X mod P) - u P) / P = floor(X / P) - u with 0 <= u < K
+            ok = any((X // P - u - int(out[j, k])) % q == 0 for u in range(o.K))
+            assert ok
+    # a multiple of P comes back exactly
+    y = _rand_limbs(rng, o.q[: level + 1], o.n)
+    Py = np.concatenate([np.array([[(int(v) * P) % q for v in y[j]] for j, q in enumerate(o.q[: level + 1])], dtype=np.uint64),
+                         np.zeros((o.K, o.n), dtype=np.uint64)])
+    assert np.array_equal(o.moddown(Py, level), y)
+
+
+def test_rescale_rounds_to_nearest(small):
+    o = small
+    rng = np.random.default_rng(2)
+    level = 2
+    ct = ckks.Ciphertext(np.stack([_rand_limbs(rng, o.q, o.n) for _ in range(2)]), level, 2.0**80)
+    out = o.rescale(ct)
+    ql = o.q[level]
+    for c in range(2):
+        for k in range(o.n):
+            X, M = crt(ct.data[c, :, k], o.q)
+            r = X % ql
+            if r > ql // 2:
+                r -= ql
+            want = (X - r) // ql
+            for j in range(level):
+                assert int(out.data[c, j, k]) == want % o.q[j]
+
+
+@pytest.mark.parametrize("which", ["small", "small_alpha2"])
+def test_galois_key_relation(which, request):
+    """b_d + a_d s = e_d + P T_d phi_g(s) (mod QP) with |e_d| <= 19 (key-switching key form)."""
+    o = request.getfixturevalue(which)
+    g = o.galois(3)
+    o.gen_rotation_keys([3])
+    evk = o.keys[g]
+    s = [int(v) for v in o.sk]
+    n, P = o.n, o.P
+    # phi_g(s) as integers
+    sg = [0] * n
+    for k in range(n):
+        t = (k * g) % (2 * n)
+        if t < n:
+            sg[t] += s[k]
+        else:
+            sg[t - n] -= s[k]
+    al = -(-o.L // o.dnum)
+    Q = 1
+    for q in o.q:
+        Q *= q
+    for d in range(o.dnum):
+        dig = o.q[d * al:(d + 1) * al]
+        Qd = 1
+        for q in dig:
+            Qd *= q
+        Td = (Q // Qd) * pow(Q // Qd, -1, Qd)
+        for k in range(0, n, 7):
+            # (a s)_k negacyclic, as an integer
+            vals = []
+            for l, q in enumerate(o.primes):
+                a = [int(v) for v in evk[d, 1, l]]
+                as_k = sum(a[i] * s[(k - i) % n] * (1 if i <= k else -1) for i in range(n))
+                vals.append((int(evk[d, 0, l, k]) + as_k - P * Td * sg[k]) % q)
+            e, M = crt(vals, o.primes)
+            if e > M // 2:
+                e -= M
+            assert abs(e) <= 19
+
+
+def test_encrypt_decrypt_round_trip():
+    o = ckks.Oracle(log_n=10, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=3)
+    z = np.random.default_rng(4).uniform(-1, 1, o.slots)
+    ct = o.encrypt(o.encode(z, 2.0**40, 2), 2, 2.0**40, nonce=5)
+    # |e| <= 19 per coefficient, decode gain <= N: a loose deterministic bound, and a tight typical one
+    err = np.abs(o.decrypt_slots(ct) - z).max()
+    assert err < 19 * o.n / 2**40
+    assert err < 1e-9
+
+
+def test_homomorphism_add_mult_rotate():
+    o = ckks.Oracle(log_n=8, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=4)
+    rng = np.random.default_rng(5)
+    a, b, w = (rng.uniform(-1, 1, o.slots) for _ in range(3))
+    D = 2.0**40
+    ca = o.encrypt(o.encode(a, D, 2), 2, D, 1)
+    cb = o.encrypt(o.encode(b, D, 2), 2, D, 2)
+    assert np.abs(o.decrypt_slots(o.add(ca, cb)) - (a + b)).max() < 1e-9
+    qs = float(o.q[2])
+    prod = o.rescale(o.mul_plain(cb, o.encode(w, qs, 2), qs))
+    assert abs(prod.scale - D) < 1e-6 * D
+    assert np.abs(o.decrypt_slots(prod) - w * b).max() < 1e-8
+    for k in (1, 2, 5, o.slots - 1):
+        assert np.abs(o.decrypt_slots(o.rotate(ca, k)) - np.roll(a, -k)).max() < 1e-8
+    # hoisted rotations are the same definition: bit-equal to one-at-a-time
+    hs = o.rotate_hoisted(ca, [1, 2, 5])
+    for k, h in zip([1, 2, 5], hs):
+        assert np.array_equal(h.data, o.rotate(ca, k).data)
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (16, 8), (8, 16), (100, 3), (3, 100), (256, 16), (16, 256), (256, 256), (1, 1)])
+def test_matmult_matches_fp64_product(m, n):
+    """Dec(MatMult(X, Enc(y))) with lazy RaS equals X y within the scale-2^40 tolerance, both hoistings."""
+    o = ckks.Oracle(log_n=7, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=5)
+    rng = np.random.default_rng(m * 7 + n)
+    X = rng.normal(size=(m, n))
+    y = rng.uniform(-1, 1, n)
+    plan = layout.make_plan(m, n, o.slots)
+    cts = o.encrypt_vector(y, plan, 2.0**40)
+    res = {}
+    for h in ("single", "double"):
+        o.counts = ckks.OpCounts()
+        pts = o.encode_matrix(X, plan, 2, ext=(h == "double"))
+        outs = o.matmult(pts, cts, plan, hoisting=h)
+        assert len(outs) == plan.row_blocks
+        assert outs[0].level == 1 and abs(outs[0].scale - 2.0**40) < 1e-3
+        res[h] = o.matmult_decode(outs, plan)
+        assert np.abs(res[h] - X @ y).max() < TOL_2_40
+        assert (o.counts.mult, o.counts.hstrot, o.counts.rot) == (plan.n_mult, plan.n_hstrot, 0)
+        assert o.counts.add == plan.n_add
+    assert np.abs(res["single"] - res["double"]).max() < TOL_2_40
+
+
+def test_matmult_worked_example_through_encryption():
+    """m = n = 4, N' = 8 (ring degree 16): the Sec. 4.3 example end to end."""
+    o = ckks.Oracle(log_n=4, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=6)
+    X = np.arange(16, dtype=float).reshape(4, 4) / 10
+    y = np.array([0.5, -0.25, 0.75, 1.0])
+    plan = layout.make_plan(4, 4, 8)
+    outs = o.matmult(o.encode_matrix(X, plan, 2, ext=True), o.encrypt_vector(y, plan, 2.0**40), plan)
+    slots = o.decrypt_slots(outs[0])
+    want_slots, want = layout.cleartext_model(X, y, plan)
+    assert np.abs(slots - want_slots[0]).max() < TOL_2_40
+    assert np.abs(layout.lazy_ras(slots[None], plan) - X @ y).max() < TOL_2_40
+
+
+def test_config1_gradient_within_tolerance():
+    """N = 4096, Q = [40, 20], P = [40], scale 2^20: X^T r with X 64x16 ~ N(0,1), r ~ U[-1,1]."""
+    o = ckks.Oracle(log_n=12, q_bits=[40, 20], p_bits=[40], dnum=2, seed=0)
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(64, 16))
+    r = rng.uniform(-1, 1, 64)
+    plan = layout.make_plan(16, 64, o.slots)
+    assert plan.m_prime == 1
+    outs = o.matmult(o.encode_matrix(X.T, plan, 1, ext=True), o.encrypt_vector(r, plan, 2.0**20), plan)
+    assert np.abs(o.matmult_decode(outs, plan) - X.T @ r).max() < 5e-2
