@@ -1,0 +1,355 @@
+"""Benchmark of the PackVFL encrypted MatMult on GB300 (one JSON line on stdout).
+
+Workload (ring N = 2^13, chain [60, 40, 40 | 60], scale 2^40): X 1024x256 ~ N(0,1),
+r 1024 ~ U[-1,1], w 256 ~ N(0, 0.1).  One step is the whole hot path for the two
+products of a VFL linear-model iteration, both as single plain MatMult calls:
+  gradient X^T [[r]] (m=256, n=1024, m'=64: 63 hoisted rotations) and
+  forward  X [[w]]   (m=1024, n=256, m'=64),
+each = encode the diagonal plaintexts of the matrix, encode + encrypt the replicated
+vector, MatMult (ModUp, 63 key-switch / multiply-accumulate steps, ModDown, rescale),
+decrypt + decode, lazy rotate-and-sum.  Galois keys are made once, before timing.
+value = MatMults per second over all ranks (2 per step per rank).
+
+--impl reference times the CPU oracle (the only reference implementation: the paper
+ships no code) on one MatMult per step.  Multi-GPU runs are independent replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "encrypted MatMults/sec at N=2^13 (plain: one MatMult per call)"
+WORKLOAD = "VFL-LinR gradient X^T[[r]] + forward X[[w]], X 1024x256 fp64, N=8192, Q=[60,40,40], P=[60], dnum=3, scale 2^40"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time (weak scaling)."""
+    return units_per_rank * world / max_seconds
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100",
+                                          "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self) -> dict:
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i] and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def flush_l2(buf):
+    buf.add_(1)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2405_00482_gb300 import he, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    P = inputs.PARAMS_N8192
+    ctx = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=rank)
+    X, r, w = inputs.gradient_and_forward_n8192(seed=rank)
+    XT = np.ascontiguousarray(X.T)
+    level = P.top
+    plan_g = he.Plan(256, 1024, P.slots)
+    plan_f = he.Plan(1024, 256, P.slots)
+    steps = sorted(set(range(1, plan_g.m_prime)) | set(range(1, plan_f.m_prime)))
+    ctx.keygen(steps)
+    dXT, dX = torch.from_numpy(XT).to(dev), torch.from_numpy(X).to(dev)
+    dr, dw = torch.from_numpy(r).to(dev), torch.from_numpy(w).to(dev)
+    out_g = [ctx.new_ct(level - 1)]
+    out_f = [ctx.new_ct(level - 1)]
+    slots_g = torch.empty((1, P.slots), dtype=torch.float64, device=dev)
+    slots_f = torch.empty((1, P.slots), dtype=torch.float64, device=dev)
+    res_g = torch.empty(256, dtype=torch.float64, device=dev)
+    res_f = torch.empty(1024, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    # device buffers reused by every step: encoded matrices, vector plaintexts, ciphertexts
+    pm_g = ctx.encode_matrix(plan_g, dXT, level)
+    pm_f = ctx.encode_matrix(plan_f, dX, level)
+    pt_r, pt_w = ctx.new_pt(level), ctx.new_pt(level)
+    ct_r, ct_w = ctx.new_ct(level), ctx.new_ct(level)
+
+    def step(i, XTd, Xd, rd, wd):
+        ctx.encode_matrix(plan_g, XTd, level, out=pm_g)
+        ctx.encode_matrix(plan_f, Xd, level, out=pm_f)
+        ctx.encode_vector(plan_g, rd, P.scale, level, outs=[pt_r])
+        ctx.encode_vector(plan_f, wd, P.scale, level, outs=[pt_w])
+        ctx.encrypt(pt_r, 2 * i, out=ct_r)
+        ctx.encrypt(pt_w, 2 * i + 1, out=ct_w)
+        ctx.matmult(plan_g, pm_g, [ct_r], out_g)
+        ctx.matmult(plan_f, pm_f, [ct_w], out_f)
+        ctx.decrypt(out_g[0], slots_g[0])
+        ctx.decrypt(out_f[0], slots_f[0])
+        ctx.matmult_decode(plan_g, slots_g, res_g)
+        ctx.matmult_decode(plan_f, slots_f, res_f)
+
+    # correctness of the timed configuration against the FP64 product
+    step(0, dXT, dX, dr, dw)
+    torch.cuda.synchronize()
+    err = max(float(np.abs(res_g.cpu().numpy() - XT @ r).max()), float(np.abs(res_f.cpu().numpy() - X @ w).max()))
+    if err > 1e-4:
+        raise RuntimeError(f"decrypted MatMult error {err} above tolerance")
+
+    for i in range(args.warmup):
+        step(i + 1, dXT, dX, dr, dw)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    per_step = []
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush_l2(flush)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(1000 + i, dXT, dX, dr, dw)
+            b.record(stream)
+            per_step.append((a, b))
+        torch.cuda.synchronize()
+    loop_ms, loop_launches = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launch_count() - launches0
+    times = [a.elapsed_time(b) for a, b in per_step]
+    total_s = max_over_ranks(sum(times) / 1e3, world, dev)
+    if world > 1:
+        torch.distributed.barrier()
+
+    # MatMult call alone (inputs encoded and encrypted), same device timing
+    mm = []
+    for i in range(args.steps):
+        flush_l2(flush)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.matmult(plan_g, pm_g, [ct_r], out_g)
+        b.record(stream)
+        mm.append((a, b))
+    torch.cuda.synchronize()
+    mm_ms = sorted(a.elapsed_time(b) for a, b in mm)
+
+    # end to end through the API from pinned host buffers, result read back every step
+    hXT, hX = torch.from_numpy(XT).pin_memory(), torch.from_numpy(X).pin_memory()
+    hr, hw = torch.from_numpy(r).pin_memory(), torch.from_numpy(w).pin_memory()
+    hres_g = torch.empty(256, dtype=torch.float64).pin_memory()
+    hres_f = torch.empty(1024, dtype=torch.float64).pin_memory()
+    e2e = []
+    for i in range(args.steps):
+        flush_l2(flush)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(5000 + i, hXT.to(dev, non_blocking=True), hX.to(dev, non_blocking=True), hr.to(dev, non_blocking=True),
+             hw.to(dev, non_blocking=True))
+        hres_g.copy_(res_g, non_blocking=True)
+        hres_f.copy_(res_f, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e), world, dev)
+    h2d = (XT.nbytes + X.nbytes + r.nbytes + w.nbytes)
+    d2h = 256 * 8 + 1024 * 8
+
+    # dominant kernel roofline: key-switch / multiply-accumulate loop
+    N, ext, nq, K, dnum = P.n, level + 1 + len(P.p_bits), level + 1, len(P.p_bits), P.dnum
+    m_prime = plan_g.m_prime
+    alg_bytes = 8 * N * ((m_prime - 1) * dnum * 2 * ext + m_prime * ext + dnum * ext + 2 * nq + 2 * ext + 2 * nq)
+    per_launch_ms = loop_ms / max(loop_launches, 1)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    clocks = clk.summary()
+    value = whole_job_rate(2 * args.steps, world, total_s)
+    rot_per_step = (plan_g.m_prime - 1) + (plan_f.m_prime - 1)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "MatMult/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total_s / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "matmults_per_step": 2, "hoisted_rotations_per_step": rot_per_step,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "rotations_per_sec": round(rot_per_step * args.steps * world / total_s, 1),
+        "matmult_call_ms": {"p50": round(mm_ms[len(mm_ms) // 2], 4), "p99": round(mm_ms[min(len(mm_ms) - 1, int(0.99 * len(mm_ms)))], 4)},
+        "step_ms": {"p50": round(sorted(times)[len(times) // 2], 4), "p99": round(sorted(times)[min(len(times) - 1, int(0.99 * len(times)))], 4)},
+        "max_abs_err": err,
+        "roofline": {"kernel": "matmult_loop_kernel", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "alg_bytes_per_launch": alg_bytes,
+                     "launch_ms": round(per_launch_ms, 5), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "e2e": {"value": round(whole_job_rate(2 * args.steps, world, e2e_s), 2), "unit": "MatMult/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def oracle_one_matmult(seed: int = 0):
+    """The oracle (single-threaded C + numpy) on one gradient MatMult of the workload:
+    encode X^T's 64 diagonals, encrypt r, 63 hoisted rotations with multiply-accumulate,
+    rescale, decrypt, lazy rotate-and-sum.  Galois keys are made before timing."""
+    import numpy as np
+
+    from oracle import ckks, layout
+    from paper_2405_00482_gb300 import inputs
+
+    P = inputs.PARAMS_N8192
+    o = ckks.Oracle(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed)
+    X, r, _ = inputs.gradient_and_forward_n8192(seed)
+    XT = np.ascontiguousarray(X.T)
+    plan = layout.make_plan(256, 1024, P.slots)
+    o.gen_rotation_keys(plan.rotation_steps)
+
+    def run():
+        cts = o.encrypt_vector(r, plan, P.scale)
+        pts = o.encode_matrix(XT, plan, P.top, ext=True)
+        outs = o.matmult(pts, cts, plan)
+        return o.matmult_decode(outs, plan)
+
+    return run, XT @ r
+
+
+def cpu_baseline() -> dict:
+    run, want = oracle_one_matmult()
+    t0 = time.perf_counter()
+    res = run()
+    dt = time.perf_counter() - t0
+    import numpy as np
+
+    assert float(np.abs(res - want).max()) < 1e-4
+    return {"value": round(1.0 / dt, 5), "unit": "MatMult/s", "cores": 1, "kind": "oracle",
+            "sample": f"one gradient MatMult (m=256, n=1024, 63 rotations) incl. encoding, single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    run, want = oracle_one_matmult()
+    for _ in range(args.warmup):
+        run()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        run()
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 5),
+        "unit": "MatMult/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 2),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "matmults_per_step": 1},
+        "cpu_baseline": {"value": round(value, 5), "unit": "MatMult/s", "cores": 1, "kind": "oracle",
+                         "sample": "one gradient MatMult per step (the oracle is the reference: the paper ships no code)"},
+        "e2e": {"value": round(value, 5), "unit": "MatMult/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

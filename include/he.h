@@ -1,0 +1,176 @@
+/*
+ * he.h -- C ABI of the GB300 (sm_103a) library for the PackVFL encrypted MatMult.
+ *
+ * The library computes X [[y]] = [[X y]] (Eq. 1, Sec. 3) between a cleartext matrix X and
+ * CKKS/RLWE ciphertexts [[y]] (Sec. 2.2) in PackVFL's hybrid layout: diagonal encoding
+ * (Eq. 2, Sec. 4.1), input packing (Eq. 3, Sec. 4.2.1) and partitioning (Sec. 4.2.2),
+ * hoisted rotations (O4, Sec. 2.2) and lazy rotate-and-sum (Sec. 4.3).
+ *
+ * Conventions for every call:
+ *  - Return value: HE_OK (0) or a negative HE_E* status; nothing is thrown across the ABI.
+ *  - Bulk data (slots, matrices, ciphertexts, plaintexts) live in DEVICE memory owned by
+ *    the caller, passed as plain pointers.  Every device call is asynchronous on the
+ *    context's CUDA stream (given at creation); the caller orders other work against it.
+ *  - Ciphertext and plaintext buffers are in the library's internal form: limbs of
+ *    uint64 residues, NTT (evaluation) domain, bit-reversed slot order.  he_ct_export /
+ *    he_ct_import convert from / to the canonical coefficient form.
+ *  - Keys, tables, plans and encoded matrices are owned by the library and released by
+ *    the matching *_free / he_ctx_destroy.
+ *  - Rotation direction: RotL(x, r)[j] = x[(j + r) mod N/2] (Sec. 3.1.1), realised by the
+ *    automorphism X -> X^(5^r mod 2N).
+ */
+#ifndef HE_H
+#define HE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HE_OK = 0,
+    HE_EINVAL = -1,   /* bad argument (null pointer, size out of range, mismatched plan) */
+    HE_ENOMEM = -2,   /* device or host allocation failed */
+    HE_ECUDA = -3,    /* a CUDA call failed (no device, launch error) */
+    HE_EKEY = -4,     /* a rotation needs a Galois key that he_keygen did not make */
+    HE_ELEVEL = -5,   /* level out of range or operands at different levels */
+    HE_ESCALE = -6,   /* operand scales do not match */
+    HE_ETIMEOUT = -7, /* a bounded device wait gave up */
+    HE_EBUDGET = -8   /* request exceeds the configured memory budget */
+};
+
+typedef struct he_ctx he_ctx;       /* parameters, NTT tables, secret key, Galois keys */
+typedef struct he_plan he_plan;     /* MatMult layout plan (host only) */
+typedef struct he_ptmat he_ptmat;   /* encoded diagonal plaintext matrix (device) */
+
+/* RNS-CKKS parameters.  The ring is Z_q[X]/(X^N+1) with N = 2^log_n (Sec. 2.2), N/2 slots.
+ * Primes: for each bit size in q_bits then p_bits, the largest prime q < 2^bits with
+ * q = 1 mod 2N not already chosen.  Key switching splits the q primes into dnum digits of
+ * ceil(n_q / dnum) consecutive primes.  Secret ternary, noise discrete Gaussian sigma 3.2. */
+typedef struct he_params {
+    int32_t log_n;        /* 4 <= log_n <= 14 */
+    int32_t n_q;          /* ciphertext primes, 1..16 (levels 0..n_q-1) */
+    int32_t n_p;          /* special primes, 1..8 */
+    int32_t dnum;         /* 1..n_q */
+    int32_t q_bits[16];   /* each 20..61 */
+    int32_t p_bits[8];
+} he_params;
+
+/* A ciphertext [[x]] = (c0, c1) at `level` (level+1 primes) and scale.  data: device,
+ * 2*(level+1)*N uint64, caller-owned. */
+typedef struct he_ct {
+    uint64_t *data;
+    int32_t level;
+    double scale;
+} he_ct;
+
+/* A plaintext polynomial at `level`, data: device, (level+1)*N uint64, caller-owned. */
+typedef struct he_pt {
+    uint64_t *data;
+    int32_t level;
+    double scale;
+} he_pt;
+
+/* Human-readable text of a status code (static string). */
+const char *he_strerror(int status);
+
+/* Host only (no GPU): the prime chain of `p` into out[n_q + n_p] (q primes then p primes). */
+int he_params_primes(const he_params *p, uint64_t *out);
+
+/* Host only: the 38 thresholds of the Gaussian sampler's cumulative table (40-bit). */
+int he_cdt_table(uint64_t *out38);
+
+/* Create a context on the current CUDA device: tables, secret key s from `seed`
+ * (Philox-4x64-10 stream), all on `cuda_stream` (a cudaStream_t; NULL = legacy stream). */
+int he_ctx_create(const he_params *p, uint64_t seed, void *cuda_stream, he_ctx **out);
+void he_ctx_destroy(he_ctx *ctx);
+/* Wait for every call issued on the context's stream. */
+int he_synchronize(he_ctx *ctx);
+/* N of the ring and the prime count; any out pointer may be NULL. */
+int he_ctx_info(const he_ctx *ctx, int64_t *n, int32_t *n_q, int32_t *n_p);
+
+/* Number of kernels this context has launched so far (all calls). */
+int he_launch_count(const he_ctx *ctx, int64_t *count);
+/* Per-launch CUDA-event timing, on the context's stream, of the MatMult's key-switch /
+ * multiply-accumulate loop kernel.  Enabling (on != 0) or disabling clears the record. */
+int he_profile_enable(he_ctx *ctx, int on);
+/* Synchronises the stream; total milliseconds and number of timed launches since enabling. */
+int he_profile_read(he_ctx *ctx, double *ms_total, int64_t *launches);
+
+/* Galois keys for left rotations by each of steps[0..n_steps) (O3/O4, Sec. 2.2). Keys
+ * already present are kept.  Device memory: dnum*2*(n_q+n_p)*N*8 bytes per key. */
+int he_keygen(he_ctx *ctx, const int32_t *steps, int n_steps);
+
+/* Encode n_slots <= N/2 real slot values (device doubles) at `scale` into a plaintext at
+ * `level` (Sec. 2.2 encoding: slot j at root zeta^(5^j), zeta = exp(i pi / N)). */
+int he_encode(he_ctx *ctx, const double *slots, int64_t n_slots, double scale, int level, he_pt *out);
+
+/* Symmetric RLWE encryption (Sec. 2.2): c0 = m - a s + e, c1 = a, at the plaintext's level;
+ * a and e are drawn from the Philox stream selected by `nonce`. */
+int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t nonce, he_ct *out);
+
+/* Decryption (Sec. 2.2) at the first prime and decoding: N/2 real slot values (device) of
+ * c0 + c1 s divided by the ciphertext's scale. */
+int he_decrypt(he_ctx *ctx, const he_ct *ct, double *slots_out);
+
+/* O1 (Sec. 2.2): out = a + b (same level and scale). out may alias a or b. */
+int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out);
+/* O2 (Sec. 2.2): out = pt (x) ct slot-wise, scale multiplies; pt at a level >= ct's. */
+int he_mul_plain(he_ctx *ctx, const he_ct *ct, const he_pt *pt, he_ct *out);
+/* Rescale by the last prime: level -> level-1, scale / q_level (rounding division). */
+int he_rescale(he_ctx *ctx, const he_ct *in, he_ct *out);
+
+/* O3 (Sec. 2.2): out = RotL(in, step).  Needs the key for `step` (HE_EKEY otherwise). */
+int he_rotate(he_ctx *ctx, const he_ct *in, int32_t step, he_ct *out);
+/* O4 (Sec. 2.2): outs[i] = RotL(in, steps[i]) for i < k, sharing one decomposition of c1. */
+int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, int k, he_ct *outs);
+
+/* Host only: plan the MatMult of an m x n matrix with n-vectors in `slots` (= N/2) slots:
+ * zero padding to powers of two (Sec. 3), input packing with m' = ceil(m n / N') (Eq. 3),
+ * row/column partitioning when m or n exceed N' (Sec. 4.2.2, Tab. 3). */
+int he_plan_create(int64_t m, int64_t n, int64_t slots, he_plan **out);
+/* info[0..10] = m, n, slots, m_pad, n_pad, m_block, n_block, row_blocks (output cts),
+ * col_blocks (input cts), m_prime (diagonals per block), packed groups per ct. */
+int he_plan_query(const he_plan *plan, int64_t *info);
+void he_plan_free(he_plan *plan);
+
+/* Encode X (device, row-major m x n doubles) into its diagonal plaintexts (Eq. 2 after Eq. 3):
+ * e_{r,c,i}[b nb + j] = X[r mb + b m' + (j mod m'), c nb + (i + j) mod nb], at scale
+ * q_level so that the MatMult's rescale returns the input ciphertext's scale. */
+int he_encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int level, he_ptmat **out);
+/* Re-encode a new matrix X (same shape, device) into an existing encoded matrix, in place:
+ * no allocation, asynchronous on the stream (a VFL iteration's next batch). */
+int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X);
+/* Same object from integer plaintexts already encoded elsewhere: coeffs (device) holds
+ * [R][C][m'][level+1+n_p][N] canonical residues in coefficient form over q_0..q_level, p_*. */
+int he_ptmat_import(he_ctx *ctx, const he_plan *plan, const uint64_t *coeffs, int level, double scale, he_ptmat **out);
+void he_ptmat_free(he_ptmat *pm);
+
+/* P_B's side: replicate piece c of y (device, n doubles) N'/nb times and encode it into
+ * outs[c] for c < col_blocks (Sec. 4.2.1, "[[d]] is expanded by replicating its pattern"). */
+int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double scale, int level, he_pt *outs);
+
+/* The hot path: outs[r] = Rescale( sum_c sum_{i<m'} e_{r,c,i} (x) HstRotL(ins[c], i) ) for
+ * r < row_blocks, with ins[c] for c < col_blocks at the ptmat's level (Tab. 2 PackVFL row,
+ * Tab. 3).  Rotations stay in the extended basis and are divided by P once per output.
+ * outs[r].data must hold 2*level*N words (one level is consumed). */
+int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in,
+                            he_ct *outs, int n_out);
+
+/* P_B's side after decryption: lazy rotate-and-sum (Sec. 4.3).  slots: device
+ * [row_blocks][N/2] doubles (he_decrypt of each output), y_out: device m doubles. */
+int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out);
+
+/* Canonical coefficient form (device, [2][level+1][N]) of a ciphertext, and back. */
+int he_ct_export(he_ctx *ctx, const he_ct *ct, uint64_t *coeffs_out);
+int he_ct_import(he_ctx *ctx, const uint64_t *coeffs, int level, double scale, he_ct *out);
+/* Same for plaintexts ([level+1][N]). */
+int he_pt_export(he_ctx *ctx, const he_pt *pt, uint64_t *coeffs_out);
+int he_pt_import(he_ctx *ctx, const uint64_t *coeffs, int level, double scale, he_pt *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HE_H */

@@ -1,0 +1,784 @@
+// he_api.cu -- context, host-side parameter math and the C ABI entry points of he.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "he_internal.cuh"
+
+void ntt_set_smem_limits(int max_bytes);
+void ops_set_smem_limits(int max_bytes);
+void encode_set_smem_limits(int max_bytes);
+
+namespace {
+
+// ---------------------------------------------------------------- host number theory
+uint64_t hmul(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((u128)a * b % m); }
+uint64_t hpow(uint64_t a, uint64_t e, uint64_t m) {
+    uint64_t r = 1 % m;
+    a %= m;
+    for (; e; e >>= 1, a = hmul(a, a, m))
+        if (e & 1) r = hmul(r, a, m);
+    return r;
+}
+uint64_t hinv(uint64_t a, uint64_t m) { return hpow(a % m, m - 2, m); }  // m prime
+
+// strong-probable-prime test to the seven bases known to decide all 64-bit integers
+bool probable_prime(uint64_t n) {
+    if (n < 4) return n >= 2;
+    if (!(n & 1)) return false;
+    uint64_t d = n - 1;
+    int r = 0;
+    while (!(d & 1)) d >>= 1, ++r;
+    const uint64_t bases[7] = {2, 325, 9375, 28178, 450775, 9780504, 1795265022};
+    for (uint64_t b : bases) {
+        uint64_t a = b % n;
+        if (a == 0) continue;
+        uint64_t x = hpow(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool ok = false;
+        for (int i = 1; i < r && !ok; ++i) {
+            x = hmul(x, x, n);
+            ok = (x == n - 1);
+        }
+        if (!ok) return false;
+    }
+    return true;
+}
+
+// largest unused prime below 2^bits that is 1 mod 2N
+int prime_chain(int log_n, const std::vector<int> &bits, std::vector<uint64_t> &out) {
+    const uint64_t step = 2ull << log_n;
+    out.clear();
+    for (int b : bits) {
+        if (b < 20 || b > 61) return HE_EINVAL;
+        const uint64_t hi = 1ull << b, lo = hi >> 1;
+        uint64_t c = (hi - 1) - ((hi - 1 - 1) % step);  // largest value < hi with c = 1 mod step
+        bool found = false;
+        for (; c > lo; c -= step) {
+            if (std::find(out.begin(), out.end(), c) != out.end()) continue;
+            if (probable_prime(c)) {
+                out.push_back(c);
+                found = true;
+                break;
+            }
+        }
+        if (!found) return HE_EINVAL;
+    }
+    return HE_OK;
+}
+
+int check_params(const he_params *p) {
+    if (!p) return HE_EINVAL;
+    if (p->log_n < 4 || p->log_n > 14) return HE_EINVAL;
+    if (p->n_q < 1 || p->n_q > HE_MAX_Q || p->n_p < 1 || p->n_p > HE_MAX_P) return HE_EINVAL;
+    if (p->dnum < 1 || p->dnum > p->n_q || p->dnum > HE_MAX_DNUM) return HE_EINVAL;
+    if ((p->n_q + p->dnum - 1) / p->dnum > 4) return HE_EINVAL;  // at most 4 primes per digit
+    return HE_OK;
+}
+
+std::vector<int> all_bits(const he_params *p) {
+    std::vector<int> b(p->q_bits, p->q_bits + p->n_q);
+    b.insert(b.end(), p->p_bits, p->p_bits + p->n_p);
+    return b;
+}
+
+uint64_t shoup(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
+
+uint64_t brv(uint64_t x, int bits) {
+    uint64_t r = 0;
+    for (int i = 0; i < bits; ++i, x >>= 1) r = (r << 1) | (x & 1);
+    return r;
+}
+
+// a primitive 2N-th root: psi = x^((q-1)/2N) for the first odd x >= 3 with psi^N = -1
+uint64_t find_psi(uint64_t q, int log_n) {
+    const uint64_t n = 1ull << log_n;
+    for (uint64_t x = 3;; x += 2) {
+        uint64_t psi = hpow(x, (q - 1) / (2 * n), q);
+        if (hpow(psi, n, q) == q - 1) return psi;
+    }
+}
+
+ModConst make_modconst(uint64_t q, int log_n) {
+    ModConst m{};
+    m.q = q;
+    uint64_t inv = q;  // q * q = 1 mod 8: three correct bits, doubled by each Newton step
+    for (int i = 0; i < 5; ++i) inv *= 2 - q * inv;
+    m.qinv = (uint64_t)0 - inv;
+    uint64_t r1 = (uint64_t)(((u128)1 << 64) % q);
+    m.r2 = hmul(r1, r1, q);
+    m.ninv = hinv((1ull << log_n) % q, q);
+    m.ninv_shoup = shoup(m.ninv, q);
+    return m;
+}
+
+bool cuda_ok(cudaError_t e) { return e == cudaSuccess; }
+
+}  // namespace
+
+int he_check(cudaError_t e) { return e == cudaSuccess ? HE_OK : HE_ECUDA; }
+
+uint64_t *ctx_scratch(he_ctx *ctx, size_t words) {
+    if (words <= ctx->scratch_words) return ctx->scratch;
+    // previous users of the buffer are ordered on the stream; wait before releasing it
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_words = 0;
+    if (cudaMalloc(&ctx->scratch, words * 8) != cudaSuccess) return nullptr;
+    ctx->scratch_words = words;
+    return ctx->scratch;
+}
+
+static int last_launch() { return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA; }
+
+static LimbMap qmap(int level) {
+    LimbMap m{};
+    m.n = level + 1;
+    for (int l = 0; l <= level; ++l) m.prime[l] = l;
+    return m;
+}
+
+static LimbMap qpmap(const he_ctx *ctx, int level) {
+    LimbMap m{};
+    m.n = level + 1 + ctx->K;
+    for (int l = 0; l <= level; ++l) m.prime[l] = l;
+    for (int i = 0; i < ctx->K; ++i) m.prime[level + 1 + i] = ctx->L + i;
+    return m;
+}
+
+static uint32_t galois_of(const he_ctx *ctx, int64_t step) {
+    const int64_t slots = ctx->n / 2;
+    int64_t r = ((step % slots) + slots) % slots;
+    return (uint32_t)hpow(5, (uint64_t)r, 2ull * ctx->n);
+}
+
+extern "C" {
+
+const char *he_strerror(int s) {
+    switch (s) {
+        case HE_OK: return "ok";
+        case HE_EINVAL: return "invalid argument";
+        case HE_ENOMEM: return "out of memory";
+        case HE_ECUDA: return "CUDA error";
+        case HE_EKEY: return "missing Galois key";
+        case HE_ELEVEL: return "level out of range or mismatched";
+        case HE_ESCALE: return "scale mismatch";
+        case HE_ETIMEOUT: return "device wait timed out";
+        case HE_EBUDGET: return "memory budget exceeded";
+        default: return "unknown status";
+    }
+}
+
+int he_params_primes(const he_params *p, uint64_t *out) {
+    int rc = check_params(p);
+    if (rc != HE_OK || !out) return HE_EINVAL;
+    std::vector<uint64_t> pr;
+    rc = prime_chain(p->log_n, all_bits(p), pr);
+    if (rc != HE_OK) return rc;
+    std::copy(pr.begin(), pr.end(), out);
+    return HE_OK;
+}
+
+int he_cdt_table(uint64_t *out) {
+    if (!out) return HE_EINVAL;
+    // rho(y) = exp(-y^2 / 20.48) for y = -19..19 (sigma = 3.2); cumulative sums left to right
+    double rho[39], total = 0.0;
+    for (int i = 0; i < 39; ++i) {
+        const double y = (double)(i - 19);
+        rho[i] = exp(-(y * y) / 20.48);
+    }
+    for (int i = 0; i < 39; ++i) total += rho[i];
+    double cum = 0.0;
+    for (int k = 0; k < 38; ++k) {
+        cum += rho[k];
+        out[k] = (uint64_t)floor(ldexp(cum / total, 40));
+    }
+    return HE_OK;
+}
+
+void he_ctx_destroy(he_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &kv : ctx->keys) cudaFree(kv.second);
+    cudaFree(ctx->d_mc);
+    cudaFree(ctx->d_tw);
+    cudaFree(ctx->d_fft);
+    cudaFree(ctx->d_sk);
+    cudaFree(ctx->d_sk_mont);
+    cudaFree(ctx->scratch);
+    for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+    delete ctx;
+}
+
+int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out) {
+    if (!out) return HE_EINVAL;
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc != HE_OK) return rc;
+    he_ctx *ctx = new (std::nothrow) he_ctx();
+    if (!ctx) return HE_ENOMEM;
+    ctx->log_n = p->log_n;
+    ctx->n = 1 << p->log_n;
+    ctx->L = p->n_q;
+    ctx->K = p->n_p;
+    ctx->dnum = p->dnum;
+    ctx->alpha = (p->n_q + p->dnum - 1) / p->dnum;
+    ctx->seed = seed;
+    ctx->stream = (cudaStream_t)stream;
+    rc = prime_chain(p->log_n, all_bits(p), ctx->primes);
+    if (rc != HE_OK) {
+        delete ctx;
+        return rc;
+    }
+    he_cdt_table(ctx->cdt);
+    const int LK = ctx->L + ctx->K, N = ctx->n;
+    const int smem = N * 8;
+    ntt_set_smem_limits(smem);
+    ops_set_smem_limits(smem);
+    encode_set_smem_limits(smem);
+
+    // per-prime constants and NTT twiddles
+    std::vector<uint64_t> tw((size_t)LK * 4 * N);
+    for (int i = 0; i < LK; ++i) {
+        const uint64_t q = ctx->primes[i];
+        ctx->mc.push_back(make_modconst(q, ctx->log_n));
+        const uint64_t psi = find_psi(q, ctx->log_n), ipsi = hinv(psi, q);
+        std::vector<uint64_t> pw(N), ipw(N);
+        pw[0] = ipw[0] = 1;
+        for (int k = 1; k < N; ++k) {
+            pw[k] = hmul(pw[k - 1], psi, q);
+            ipw[k] = hmul(ipw[k - 1], ipsi, q);
+        }
+        uint64_t *t = tw.data() + (size_t)i * 4 * N;
+        for (int k = 0; k < N; ++k) {
+            const uint64_t e = brv(k, ctx->log_n);
+            t[k] = pw[e];
+            t[N + k] = shoup(pw[e], q);
+            t[2 * N + k] = ipw[e];
+            t[3 * N + k] = shoup(ipw[e], q);
+        }
+    }
+    // FFT tables: [N/4] exp(-2 pi i k/(N/2)), [N/2] exp(-i pi k / N), [N/2] int32 slot positions
+    const int M = N / 2;
+    std::vector<double> fft((size_t)2 * (M / 2) + 2 * M + M / 2 + 1, 0.0);
+    const double PI = 3.14159265358979323846264338327950288;
+    for (int k = 0; k < M / 2; ++k) {
+        fft[2 * k] = cos(2.0 * PI * k / M);
+        fft[2 * k + 1] = -sin(2.0 * PI * k / M);
+    }
+    double *twist = fft.data() + 2 * (M / 2);
+    for (int k = 0; k < M; ++k) {
+        twist[2 * k] = cos(PI * k / N);
+        twist[2 * k + 1] = -sin(PI * k / N);
+    }
+    int32_t *pos = reinterpret_cast<int32_t *>(twist + 2 * M);
+    uint64_t e = 1;
+    for (int j = 0; j < M; ++j) {
+        pos[j] = (int32_t)((e - 1) / 4);
+        e = e * 5 % (2ull * N);
+    }
+    // base-conversion constants per level
+    for (int level = 0; level < ctx->L; ++level) {
+        ModUpConst mu{};
+        mu.alpha = ctx->alpha;
+        mu.nq = level + 1;
+        mu.ext = level + 1 + ctx->K;
+        mu.ndig = (level + 1 + ctx->alpha - 1) / ctx->alpha;
+        for (int u = 0; u < mu.ext; ++u) mu.ext_prime[u] = u <= level ? u : ctx->L + (u - level - 1);
+        for (int d = 0; d < mu.ndig; ++d) {
+            const int lo = d * ctx->alpha, hi = std::min(lo + ctx->alpha, level + 1);
+            for (int i = lo; i < hi; ++i) {
+                const uint64_t qi = ctx->primes[i];
+                uint64_t hat_qi = 1;
+                for (int j = lo; j < hi; ++j)
+                    if (j != i) hat_qi = hmul(hat_qi, ctx->primes[j] % qi, qi);
+                mu.inv[d][i - lo] = hinv(hat_qi, qi);
+                mu.inv_shoup[d][i - lo] = shoup(mu.inv[d][i - lo], qi);
+                for (int u = 0; u < mu.ext; ++u) {
+                    const uint64_t t = ctx->primes[mu.ext_prime[u]];
+                    uint64_t h = 1 % t;
+                    for (int j = lo; j < hi; ++j)
+                        if (j != i) h = hmul(h, ctx->primes[j] % t, t);
+                    mu.hat[d][i - lo][u] = h;
+                    mu.hat_shoup[d][i - lo][u] = shoup(h, t);
+                }
+            }
+        }
+        ctx->modup.push_back(mu);
+        ModDownConst md{};
+        md.nq = level + 1;
+        md.K = ctx->K;
+        for (int j = 0; j <= level; ++j) md.q_prime[j] = j;
+        for (int i = 0; i < ctx->K; ++i) {
+            md.p_prime[i] = ctx->L + i;
+            const uint64_t pi = ctx->primes[ctx->L + i];
+            uint64_t hat = 1;
+            for (int r = 0; r < ctx->K; ++r)
+                if (r != i) hat = hmul(hat, ctx->primes[ctx->L + r] % pi, pi);
+            md.inv[i] = hinv(hat, pi);
+            md.inv_shoup[i] = shoup(md.inv[i], pi);
+            for (int j = 0; j <= level; ++j) {
+                const uint64_t q = ctx->primes[j];
+                uint64_t h = 1 % q;
+                for (int r = 0; r < ctx->K; ++r)
+                    if (r != i) h = hmul(h, ctx->primes[ctx->L + r] % q, q);
+                md.hat[i][j] = h;
+                md.hat_shoup[i][j] = shoup(h, q);
+            }
+        }
+        for (int j = 0; j <= level; ++j) {
+            const uint64_t q = ctx->primes[j];
+            uint64_t P = 1 % q;
+            for (int r = 0; r < ctx->K; ++r) P = hmul(P, ctx->primes[ctx->L + r] % q, q);
+            md.pinv[j] = hinv(P, q);
+            md.pinv_shoup[j] = shoup(md.pinv[j], q);
+        }
+        ctx->moddown.push_back(md);
+    }
+    bool ok = cuda_ok(cudaMalloc(&ctx->d_mc, sizeof(ModConst) * LK)) && cuda_ok(cudaMalloc(&ctx->d_tw, tw.size() * 8)) &&
+              cuda_ok(cudaMalloc(&ctx->d_fft, fft.size() * 8)) && cuda_ok(cudaMalloc(&ctx->d_sk, (size_t)LK * N * 8)) &&
+              cuda_ok(cudaMalloc(&ctx->d_sk_mont, (size_t)LK * N * 8));
+    if (!ok) {
+        he_ctx_destroy(ctx);
+        return HE_ENOMEM;
+    }
+    ok = cuda_ok(cudaMemcpy(ctx->d_mc, ctx->mc.data(), sizeof(ModConst) * LK, cudaMemcpyHostToDevice)) &&
+         cuda_ok(cudaMemcpy(ctx->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice)) &&
+         cuda_ok(cudaMemcpy(ctx->d_fft, fft.data(), fft.size() * 8, cudaMemcpyHostToDevice));
+    // secret key: ternary coefficients -> every prime of Q U P, NTT form (and Montgomery form)
+    int64_t *s_int = reinterpret_cast<int64_t *>(ctx_scratch(ctx, N));
+    if (!ok || !s_int) {
+        he_ctx_destroy(ctx);
+        return HE_ECUDA;
+    }
+    launch_sample_ternary(ctx, s_int);
+    LimbMap all{};
+    all.n = LK;
+    for (int i = 0; i < LK; ++i) all.prime[i] = i;
+    launch_ntt_from_int64(ctx, s_int, ctx->d_sk, 1, all, 0);
+    cudaMemcpyAsync(ctx->d_sk_mont, ctx->d_sk, (size_t)LK * N * 8, cudaMemcpyDeviceToDevice, ctx->stream);
+    launch_to_mont(ctx, ctx->d_sk_mont, 1, all);
+    if (last_launch() != HE_OK || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        he_ctx_destroy(ctx);
+        return HE_ECUDA;
+    }
+    *out = ctx;
+    return HE_OK;
+}
+
+int he_synchronize(he_ctx *ctx) {
+    if (!ctx) return HE_EINVAL;
+    return he_check(cudaStreamSynchronize(ctx->stream));
+}
+
+int he_launch_count(const he_ctx *ctx, int64_t *count) {
+    if (!ctx || !count) return HE_EINVAL;
+    *count = ctx->launches;
+    return HE_OK;
+}
+
+int he_profile_enable(he_ctx *ctx, int on) {
+    if (!ctx) return HE_EINVAL;
+    cudaStreamSynchronize(ctx->stream);
+    ctx->prof_on = on != 0;
+    ctx->prof_used = 0;
+    return HE_OK;
+}
+
+int he_profile_read(he_ctx *ctx, double *ms_total, int64_t *launches) {
+    if (!ctx || !ms_total || !launches) return HE_EINVAL;
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return HE_ECUDA;
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < ctx->prof_used; i += 2) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->prof_events[i], ctx->prof_events[i + 1]) != cudaSuccess) return HE_ECUDA;
+        total += ms;
+    }
+    *ms_total = total;
+    *launches = (int64_t)(ctx->prof_used / 2);
+    return HE_OK;
+}
+
+int he_ctx_info(const he_ctx *ctx, int64_t *n, int32_t *n_q, int32_t *n_p) {
+    if (!ctx) return HE_EINVAL;
+    if (n) *n = ctx->n;
+    if (n_q) *n_q = ctx->L;
+    if (n_p) *n_p = ctx->K;
+    return HE_OK;
+}
+
+int he_keygen(he_ctx *ctx, const int32_t *steps, int n_steps) {
+    if (!ctx || n_steps < 0 || (n_steps > 0 && !steps)) return HE_EINVAL;
+    const int LK = ctx->L + ctx->K, N = ctx->n;
+    LimbMap all{};
+    all.n = LK;
+    for (int i = 0; i < LK; ++i) all.prime[i] = i;
+    for (int s = 0; s < n_steps; ++s) {
+        const uint32_t g = galois_of(ctx, steps[s]);
+        if (ctx->keys.count(g)) continue;
+        uint64_t *key = nullptr;
+        if (cudaMalloc(&key, (size_t)ctx->dnum * 2 * LK * N * 8) != cudaSuccess) return HE_ENOMEM;
+        uint64_t *tmp = ctx_scratch(ctx, (size_t)2 * LK * N + N);
+        if (!tmp) {
+            cudaFree(key);
+            return HE_ENOMEM;
+        }
+        uint64_t *a = tmp, *e = tmp + (size_t)LK * N;
+        int64_t *e_int = reinterpret_cast<int64_t *>(tmp + (size_t)2 * LK * N);
+        for (int d = 0; d < ctx->dnum; ++d) {
+            const uint64_t nonce = ((uint64_t)g << 8) | (uint64_t)d;
+            launch_sample_uniform(ctx, 4, nonce, all, 0, a);
+            launch_ntt_fwd(ctx, a, a, 1, all);
+            launch_sample_gauss(ctx, 5, nonce, e_int);
+            launch_ntt_from_int64(ctx, e_int, e, 1, all, 0);
+            launch_keygen_combine(ctx, a, e, g, d, key + (size_t)d * 2 * LK * N);
+        }
+        if (last_launch() != HE_OK) {
+            cudaFree(key);
+            return HE_ECUDA;
+        }
+        ctx->keys[g] = key;
+    }
+    return HE_OK;
+}
+
+int he_encode(he_ctx *ctx, const double *slots, int64_t n_slots, double scale, int level, he_pt *out) {
+    if (!ctx || !out || !out->data || (n_slots > 0 && !slots) || n_slots < 0 || n_slots > ctx->n / 2) return HE_EINVAL;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    int64_t *coef = reinterpret_cast<int64_t *>(ctx_scratch(ctx, ctx->n));
+    if (!coef) return HE_ENOMEM;
+    launch_encode(ctx, slots, n_slots, n_slots, 1, scale, coef);
+    launch_ntt_from_int64(ctx, coef, out->data, 1, qmap(level), 0);
+    out->level = level;
+    out->scale = scale;
+    return last_launch();
+}
+
+int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t nonce, he_ct *out) {
+    if (!ctx || !pt || !out || !pt->data || !out->data) return HE_EINVAL;
+    const int level = pt->level;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    const size_t N = ctx->n, nl = level + 1;
+    uint64_t *tmp = ctx_scratch(ctx, 2 * nl * N + N);
+    if (!tmp) return HE_ENOMEM;
+    uint64_t *a = tmp, *e = tmp + nl * N;
+    int64_t *e_int = reinterpret_cast<int64_t *>(tmp + 2 * nl * N);
+    const LimbMap m = qmap(level);
+    launch_sample_uniform(ctx, 2, nonce, m, 0, a);
+    launch_ntt_fwd(ctx, a, a, 1, m);
+    launch_sample_gauss(ctx, 3, nonce, e_int);
+    launch_ntt_from_int64(ctx, e_int, e, 1, m, 0);
+    launch_encrypt_combine(ctx, pt->data, a, e, level, out->data);
+    out->level = level;
+    out->scale = pt->scale;
+    return last_launch();
+}
+
+int he_decrypt(he_ctx *ctx, const he_ct *ct, double *slots_out) {
+    if (!ctx || !ct || !ct->data || !slots_out) return HE_EINVAL;
+    if (ct->level < 0 || ct->level >= ctx->L) return HE_ELEVEL;
+    double *coef = reinterpret_cast<double *>(ctx_scratch(ctx, ctx->n));
+    if (!coef) return HE_ENOMEM;
+    launch_decrypt_coeffs(ctx, ct->data, ct->level, 1, coef, nullptr);
+    launch_decode(ctx, coef, 1, ct->scale, slots_out);
+    return last_launch();
+}
+
+int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out) {
+    if (!ctx || !a || !b || !out || !a->data || !b->data || !out->data) return HE_EINVAL;
+    if (a->level != b->level || a->level < 0 || a->level >= ctx->L) return HE_ELEVEL;
+    if (fabs(a->scale - b->scale) > 1e-9 * fabs(a->scale)) return HE_ESCALE;
+    launch_add(ctx, a->data, b->data, out->data, 2, qmap(a->level));
+    out->level = a->level;
+    out->scale = a->scale;
+    return last_launch();
+}
+
+int he_mul_plain(he_ctx *ctx, const he_ct *ct, const he_pt *pt, he_ct *out) {
+    if (!ctx || !ct || !pt || !out || !ct->data || !pt->data || !out->data) return HE_EINVAL;
+    if (ct->level < 0 || ct->level >= ctx->L || pt->level < ct->level) return HE_ELEVEL;
+    launch_mul_plain(ctx, ct->data, pt->data, out->data, ct->level);
+    out->level = ct->level;
+    out->scale = ct->scale * pt->scale;
+    return last_launch();
+}
+
+int he_rescale(he_ctx *ctx, const he_ct *in, he_ct *out) {
+    if (!ctx || !in || !in->data) return HE_EINVAL;
+    if (in->level < 1 || in->level >= ctx->L) return HE_ELEVEL;
+    if (!out || !out->data) return HE_EINVAL;
+    uint64_t *tmp = ctx_scratch(ctx, 2 * (size_t)ctx->n);
+    if (!tmp) return HE_ENOMEM;
+    const int level = in->level;
+    const double scale = in->scale / (double)ctx->primes[level];
+    launch_rescale(ctx, in->data, level, out->data, tmp);
+    out->level = level - 1;
+    out->scale = scale;
+    return last_launch();
+}
+
+int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, int k, he_ct *outs) {
+    if (!ctx || !in || !in->data || k < 0 || (k > 0 && (!steps || !outs))) return HE_EINVAL;
+    const int level = in->level;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    std::vector<const uint64_t *> keys(k);
+    for (int i = 0; i < k; ++i) {
+        if (!outs[i].data || outs[i].data == in->data) return HE_EINVAL;
+        auto it = ctx->keys.find(galois_of(ctx, steps[i]));
+        if (it == ctx->keys.end()) return HE_EKEY;
+        keys[i] = it->second;
+    }
+    if (k == 0) return HE_OK;
+    const ModUpConst &mu = ctx->modup[level];
+    const size_t N = ctx->n, nl = level + 1, ext = mu.ext;
+    const size_t wD = mu.ndig * ext * N, wc = nl * N, wu = 2 * ext * N, wr = nl * N, wt = 2 * ctx->K * N;
+    uint64_t *s = ctx_scratch(ctx, wD + wc + wu + wr + wt);
+    if (!s) return HE_ENOMEM;
+    uint64_t *D = s, *coef = D + wD, *u = coef + wc, *rc0 = u + wu, *tmp = rc0 + wr;
+    launch_modup(ctx, in->data + nl * N, level, D, coef);
+    for (int i = 0; i < k; ++i) {
+        const uint32_t g = galois_of(ctx, steps[i]);
+        launch_ks_inner(ctx, D, level, g, keys[i], u);
+        launch_automorph(ctx, in->data, rc0, 1, qmap(level), g);
+        launch_moddown(ctx, u, level, 2, rc0, nullptr, outs[i].data, tmp);
+        outs[i].level = level;
+        outs[i].scale = in->scale;
+    }
+    return last_launch();
+}
+
+int he_rotate(he_ctx *ctx, const he_ct *in, int32_t step, he_ct *out) { return he_rotate_hoisted(ctx, in, &step, 1, out); }
+
+int he_plan_create(int64_t m, int64_t n, int64_t slots, he_plan **out) {
+    if (!out) return HE_EINVAL;
+    *out = nullptr;
+    if (m < 1 || n < 1 || slots < 1 || (slots & (slots - 1)) || m > (1ll << 40) || n > (1ll << 40)) return HE_EINVAL;
+    he_plan *p = new (std::nothrow) he_plan();
+    if (!p) return HE_ENOMEM;
+    auto up = [](int64_t v) {
+        int64_t r = 1;
+        while (r < v) r <<= 1;
+        return r;
+    };
+    p->m = m;
+    p->n = n;
+    p->slots = slots;
+    p->mp = up(m);
+    p->np = up(n);
+    p->mb = std::min(p->mp, slots);
+    p->nb = std::min(p->np, slots);
+    p->row_blocks = p->mp / p->mb;
+    p->col_blocks = p->np / p->nb;
+    p->m_prime = std::max<int64_t>(1, p->mb * p->nb / slots);
+    p->blocks = slots / p->nb;
+    *out = p;
+    return HE_OK;
+}
+
+int he_plan_query(const he_plan *p, int64_t *info) {
+    if (!p || !info) return HE_EINVAL;
+    const int64_t v[11] = {p->m, p->n, p->slots, p->mp, p->np, p->mb, p->nb, p->row_blocks, p->col_blocks, p->m_prime, p->blocks};
+    memcpy(info, v, sizeof(v));
+    return HE_OK;
+}
+
+void he_plan_free(he_plan *p) { delete p; }
+
+static int ptmat_alloc(he_ctx *ctx, const he_plan *plan, int level, double scale, he_ptmat **out) {
+    if (!ctx || !plan || !out) return HE_EINVAL;
+    *out = nullptr;
+    if (plan->slots != ctx->n / 2) return HE_EINVAL;
+    if (level < 1 || level >= ctx->L) return HE_ELEVEL;
+    he_ptmat *pm = new (std::nothrow) he_ptmat();
+    if (!pm) return HE_ENOMEM;
+    pm->ctx = ctx;
+    pm->plan = *plan;
+    pm->level = level;
+    pm->scale = scale;
+    pm->ext = level + 1 + ctx->K;
+    const size_t count = (size_t)plan->row_blocks * plan->col_blocks * plan->m_prime;
+    if (cudaMalloc(&pm->data, count * pm->ext * ctx->n * 8) != cudaSuccess) {
+        delete pm;
+        return HE_ENOMEM;
+    }
+    *out = pm;
+    return HE_OK;
+}
+
+int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X) {
+    if (!ctx || !pm || !X || pm->ctx != ctx) return HE_EINVAL;
+    const he_plan &p = pm->plan;
+    const size_t N = ctx->n, count = (size_t)p.row_blocks * p.col_blocks * p.m_prime;
+    uint64_t *s = ctx_scratch(ctx, count * (N / 2) + count * N);
+    if (!s) return HE_ENOMEM;
+    double *slots = reinterpret_cast<double *>(s);
+    int64_t *coef = reinterpret_cast<int64_t *>(s + count * (N / 2));
+    launch_layout_matrix(ctx, p, X, slots);
+    launch_encode(ctx, slots, N / 2, N / 2, (int)count, pm->scale, coef);
+    launch_ntt_from_int64(ctx, coef, pm->data, (int)count, qpmap(ctx, pm->level), 1);
+    return last_launch();
+}
+
+int he_encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int level, he_ptmat **out) {
+    if (!ctx || !X) return HE_EINVAL;
+    if (level < 1 || level >= ctx->L) return HE_ELEVEL;
+    int rc = ptmat_alloc(ctx, plan, level, (double)ctx->primes[level], out);
+    if (rc != HE_OK) return rc;
+    rc = he_ptmat_encode(ctx, *out, X);
+    if (rc != HE_OK) {
+        he_ptmat_free(*out);
+        *out = nullptr;
+    }
+    return rc;
+}
+
+int he_ptmat_import(he_ctx *ctx, const he_plan *plan, const uint64_t *coeffs, int level, double scale, he_ptmat **out) {
+    if (!coeffs) return HE_EINVAL;
+    int rc = ptmat_alloc(ctx, plan, level, scale, out);
+    if (rc != HE_OK) return rc;
+    he_ptmat *pm = *out;
+    const size_t count = (size_t)plan->row_blocks * plan->col_blocks * plan->m_prime;
+    const LimbMap m = qpmap(ctx, level);
+    const int64_t gs = (int64_t)m.n * ctx->n;
+    launch_ntt_fwd_strided(ctx, coeffs, gs, pm->data, gs, (int)count, m, 1);
+    rc = last_launch();
+    if (rc != HE_OK) {
+        he_ptmat_free(pm);
+        *out = nullptr;
+    }
+    return rc;
+}
+
+void he_ptmat_free(he_ptmat *pm) {
+    if (!pm) return;
+    cudaStreamSynchronize(pm->ctx->stream);
+    cudaFree(pm->data);
+    cudaFree(pm->d_keys);
+    cudaFree(pm->d_galois);
+    delete pm;
+}
+
+int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double scale, int level, he_pt *outs) {
+    if (!ctx || !plan || !y || !outs || plan->slots != ctx->n / 2) return HE_EINVAL;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    const size_t N = ctx->n, C = plan->col_blocks;
+    for (size_t c = 0; c < C; ++c)
+        if (!outs[c].data) return HE_EINVAL;
+    uint64_t *s = ctx_scratch(ctx, C * (N / 2) + C * N);
+    if (!s) return HE_ENOMEM;
+    double *slots = reinterpret_cast<double *>(s);
+    int64_t *coef = reinterpret_cast<int64_t *>(s + C * (N / 2));
+    launch_layout_vector(ctx, *plan, y, slots);
+    launch_encode(ctx, slots, N / 2, N / 2, (int)C, scale, coef);
+    for (size_t c = 0; c < C; ++c) {
+        launch_ntt_from_int64(ctx, coef + c * N, outs[c].data, 1, qmap(level), 0);
+        outs[c].level = level;
+        outs[c].scale = scale;
+    }
+    return last_launch();
+}
+
+// resolve the Galois keys of rotation steps 1..m'-1 into a device pointer table, once
+static int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm) {
+    const int64_t steps = pm->plan.m_prime - 1;
+    if (steps <= 0 || pm->d_keys) return HE_OK;
+    std::vector<const uint64_t *> ptrs(steps);
+    std::vector<uint32_t> gal(steps);
+    for (int64_t i = 0; i < steps; ++i) {
+        gal[i] = galois_of(ctx, i + 1);
+        auto it = ctx->keys.find(gal[i]);
+        if (it == ctx->keys.end()) return HE_EKEY;
+        ptrs[i] = it->second;
+    }
+    if (cudaMalloc(&pm->d_keys, steps * sizeof(uint64_t *)) != cudaSuccess) return HE_ENOMEM;
+    if (cudaMalloc(&pm->d_galois, steps * sizeof(uint32_t)) != cudaSuccess) return HE_ENOMEM;
+    if (cudaMemcpy(pm->d_keys, ptrs.data(), steps * sizeof(uint64_t *), cudaMemcpyHostToDevice) != cudaSuccess) return HE_ECUDA;
+    if (cudaMemcpy(pm->d_galois, gal.data(), steps * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) return HE_ECUDA;
+    pm->galois = gal;
+    return HE_OK;
+}
+
+int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm_c, const he_ct *ins, int n_in, he_ct *outs, int n_out) {
+    if (!ctx || !plan || !pm_c || !ins || !outs || pm_c->ctx != ctx) return HE_EINVAL;
+    he_ptmat *pm = const_cast<he_ptmat *>(pm_c);
+    const he_plan &p = pm->plan;
+    if (p.m != plan->m || p.n != plan->n || p.slots != plan->slots) return HE_EINVAL;
+    if (n_in != p.col_blocks || n_out != p.row_blocks) return HE_EINVAL;
+    const int level = pm->level;
+    for (int c = 0; c < n_in; ++c) {
+        if (!ins[c].data) return HE_EINVAL;
+        if (ins[c].level != level) return HE_ELEVEL;
+    }
+    for (int r = 0; r < n_out; ++r)
+        if (!outs[r].data) return HE_EINVAL;
+    int rc = ptmat_bind_keys(ctx, pm);
+    if (rc != HE_OK) return rc;
+    const ModUpConst &mu = ctx->modup[level];
+    const size_t N = ctx->n, nl = level + 1, ext = mu.ext, C = p.col_blocks;
+    const bool rot = p.m_prime > 1;
+    const size_t wD = rot ? C * mu.ndig * ext * N : 0, wc = nl * N, wa = 2 * ext * N, wcc = 2 * nl * N, wsum = 2 * nl * N,
+                 wt = 2 * (ctx->K > 1 ? ctx->K : 1) * N + 2 * N;
+    uint64_t *s = ctx_scratch(ctx, wD + wc + wa + wcc + wsum + wt);
+    if (!s) return HE_ENOMEM;
+    uint64_t *D = s, *coef = D + wD, *acc = coef + wc, *cacc = acc + wa, *sum = cacc + wcc, *tmp = sum + wsum;
+    if (rot)
+        for (size_t c = 0; c < C; ++c) launch_modup(ctx, ins[c].data + nl * N, level, D + c * mu.ndig * ext * N, coef);
+    for (int r = 0; r < n_out; ++r) {
+        for (size_t c = 0; c < C; ++c)
+            launch_matmult_loop(ctx, pm, r, (int)c, ins[c].data, rot ? D + c * mu.ndig * ext * N : nullptr, acc, cacc, c > 0);
+        const uint64_t *pre = cacc;
+        if (rot) {
+            launch_moddown(ctx, acc, level, 2, cacc, cacc + nl * N, sum, tmp);
+            pre = sum;
+        }
+        launch_rescale(ctx, pre, level, outs[r].data, tmp);
+        outs[r].level = level - 1;
+        outs[r].scale = ins[0].scale * pm->scale / (double)ctx->primes[level];
+    }
+    return last_launch();
+}
+
+int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out) {
+    if (!ctx || !plan || !slots || !y_out || plan->slots != ctx->n / 2) return HE_EINVAL;
+    launch_lazy_ras(ctx, *plan, slots, y_out);
+    return last_launch();
+}
+
+int he_ct_export(he_ctx *ctx, const he_ct *ct, uint64_t *coeffs_out) {
+    if (!ctx || !ct || !ct->data || !coeffs_out) return HE_EINVAL;
+    if (ct->level < 0 || ct->level >= ctx->L) return HE_ELEVEL;
+    launch_ntt_inv(ctx, ct->data, coeffs_out, 2, qmap(ct->level));
+    return last_launch();
+}
+
+int he_ct_import(he_ctx *ctx, const uint64_t *coeffs, int level, double scale, he_ct *out) {
+    if (!ctx || !coeffs || !out || !out->data) return HE_EINVAL;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    launch_ntt_fwd(ctx, coeffs, out->data, 2, qmap(level));
+    out->level = level;
+    out->scale = scale;
+    return last_launch();
+}
+
+int he_pt_export(he_ctx *ctx, const he_pt *pt, uint64_t *coeffs_out) {
+    if (!ctx || !pt || !pt->data || !coeffs_out) return HE_EINVAL;
+    if (pt->level < 0 || pt->level >= ctx->L) return HE_ELEVEL;
+    launch_ntt_inv(ctx, pt->data, coeffs_out, 1, qmap(pt->level));
+    return last_launch();
+}
+
+int he_pt_import(he_ctx *ctx, const uint64_t *coeffs, int level, double scale, he_pt *out) {
+    if (!ctx || !coeffs || !out || !out->data) return HE_EINVAL;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    launch_ntt_fwd(ctx, coeffs, out->data, 1, qmap(level));
+    out->level = level;
+    out->scale = scale;
+    return last_launch();
+}
+
+}  // extern "C"

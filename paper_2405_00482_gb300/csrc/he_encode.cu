@@ -1,0 +1,270 @@
+// he_encode.cu -- CKKS encoding/decoding (FP64 FFT), Philox-4x64-10 sampling, encryption.
+//
+// Encoding (Sec. 2.2): the real polynomial m with m(zeta^(5^j)) = z_j, zeta = exp(i pi/N).
+// Since 5^j = 1 mod 4, the N/2 slot roots are zeta^(4t+1), and with c_k = m_k + i m_{k+N/2}
+//   z at t  =  sum_{k<N/2} (c_k zeta^k) w^(t k),  w = exp(2 pi i / (N/2)),
+// so encoding is an inverse length-N/2 DFT followed by a twist by zeta^-k, and decoding the
+// forward one.  Slot j sits at t_j = (5^j mod 2N - 1) / 4.
+#include "he_internal.cuh"
+#include "he_ntt.cuh"
+
+namespace {
+
+// iterative radix-2 FFT of M = N/2 complex values in shared memory, input already in
+// bit-reversed order.  tw[k] = exp(-2 pi i k / M) for k < M/2; sign = +1 uses conj(tw).
+__device__ void fft_smem(double2 *a, const double2 *__restrict__ tw, int logm, int sign) {
+    const int M = 1 << logm;
+    for (int lg = 1; lg <= logm; ++lg) {
+        const int half = 1 << (lg - 1);
+        const int stride = M >> lg;  // twiddle index step
+        for (int j = threadIdx.x; j < M / 2; j += blockDim.x) {
+            const int grp = j >> (lg - 1), pos = j & (half - 1);
+            const int i1 = (grp << lg) + pos, i2 = i1 + half;
+            double2 w = tw[pos * stride];
+            if (sign > 0) w.y = -w.y;
+            const double2 u = a[i1], v0 = a[i2];
+            const double2 v = make_double2(__dsub_rn(__dmul_rn(v0.x, w.x), __dmul_rn(v0.y, w.y)),
+                                           __dadd_rn(__dmul_rn(v0.x, w.y), __dmul_rn(v0.y, w.x)));
+            a[i1] = make_double2(__dadd_rn(u.x, v.x), __dadd_rn(u.y, v.y));
+            a[i2] = make_double2(__dsub_rn(u.x, v.x), __dsub_rn(u.y, v.y));
+        }
+        __syncthreads();
+    }
+}
+
+// one CTA per plaintext: slots [count][stride] (first n_slots used) -> coeffs int64 [count][N]
+__global__ void encode_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
+                              const double2 *__restrict__ tw, const double2 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
+                              int64_t *out, int logn) {
+    extern __shared__ double2 a[];
+    const int logm = logn - 1, M = 1 << logm, N = 1 << logn;
+    const double *z = slots + (int64_t)blockIdx.x * stride;
+    for (int t = threadIdx.x; t < M; t += blockDim.x) a[t] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const int t = slot_pos[j];
+        const int bt = __brev(t) >> (32 - logm);
+        a[bt] = make_double2(j < n_slots ? z[j] : 0.0, 0.0);
+    }
+    __syncthreads();
+    fft_smem(a, tw, logm, -1);
+    const double f = 2.0 / (double)N;
+    int64_t *o = out + (int64_t)blockIdx.x * N;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        const double2 y = a[k], w = twist[k];  // w = zeta^-k
+        const double re = __dsub_rn(__dmul_rn(y.x, w.x), __dmul_rn(y.y, w.y));
+        const double im = __dadd_rn(__dmul_rn(y.x, w.y), __dmul_rn(y.y, w.x));
+        o[k] = __double2ll_rn(__dmul_rn(__dmul_rn(re, f), scale));
+        o[k + M] = __double2ll_rn(__dmul_rn(__dmul_rn(im, f), scale));
+    }
+}
+
+// one CTA per polynomial: real coefficients [count][N] -> slot values [count][N/2] / scale
+__global__ void decode_kernel(const double *__restrict__ coeffs, double scale, const double2 *__restrict__ tw,
+                              const double2 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
+    extern __shared__ double2 a[];
+    const int logm = logn - 1, M = 1 << logm, N = 1 << logn;
+    const double *m = coeffs + (int64_t)blockIdx.x * N;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        const double2 w = twist[k];  // zeta^-k; use its conjugate zeta^k
+        const double re = m[k], im = m[k + M];
+        const int bk = __brev(k) >> (32 - logm);
+        a[bk] = make_double2(__dadd_rn(__dmul_rn(re, w.x), __dmul_rn(im, w.y)), __dsub_rn(__dmul_rn(im, w.x), __dmul_rn(re, w.y)));
+    }
+    __syncthreads();
+    fft_smem(a, tw, logm, +1);
+    double *o = out + (int64_t)blockIdx.x * M;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) o[j] = a[slot_pos[j]].x / scale;
+}
+
+// decrypt limb 0: m = c0 + c1 s (NTT), inverse NTT, centred, as doubles.  One CTA per ciphertext.
+__global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words, int nl, const uint64_t *__restrict__ sk_mont,
+                               double *coeffs, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const uint64_t q = mc[0].q, qinv = mc[0].qinv;
+    const uint64_t *c0 = ct + blockIdx.x * ct_words, *c1 = c0 + (int64_t)nl * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = add_mod(c0[k], mont_mul(c1[k], sk_mont[k], q, qinv), q);
+    __syncthreads();
+    ntt_inv_smem(s, twiddles(d_tw, 0, 2, logn), twiddles(d_tw, 0, 3, logn), q, logn);
+    double *o = coeffs + (int64_t)blockIdx.x * N;
+    const uint64_t half = q >> 1;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const uint64_t v = mul_shoup(s[k], mc[0].ninv, mc[0].ninv_shoup, q);
+        o[k] = v > half ? -(double)(q - v) : (double)v;
+    }
+}
+
+// ---- Philox-4x64-10 (Salmon et al., SC'11) ----
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t lo0 = 0xD2E7470EE14C6C93ull * c[0], hi0 = __umul64hi(0xD2E7470EE14C6C93ull, c[0]);
+        const uint64_t lo1 = 0xCA5A826395121157ull * c[2], hi1 = __umul64hi(0xCA5A826395121157ull, c[2]);
+        const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B97F4A7C15ull;
+        k1 += 0xBB67AE8584CAA73Bull;
+    }
+}
+
+// uniform residues: coefficient j of limb l (prime index map.prime[l]) from the 128-bit
+// integer (word 2(j&1)+1 : word 2(j&1)) of block (j/2, prime index, nonce, 0), key (seed, tag)
+__global__ void sample_uniform_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, LimbMap map, uint64_t *out,
+                                      const ModConst *__restrict__ mc, int logn) {
+    const int N = 1 << logn;
+    const int l = blockIdx.y;
+    const int p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 2; b += gridDim.x * blockDim.x) {
+        uint64_t c[4] = {(uint64_t)b, (uint64_t)p, nonce, 0};
+        philox4x64(c, seed, tag);
+        out[(int64_t)l * N + 2 * b] = (uint64_t)((((u128)c[1]) << 64 | c[0]) % q);
+        out[(int64_t)l * N + 2 * b + 1] = (uint64_t)((((u128)c[3]) << 64 | c[2]) % q);
+    }
+}
+
+struct Cdt {
+    uint64_t t[38];
+};
+
+// discrete Gaussian by cumulative table: r = word >> 24, x = -19 + #{k : r >= T_k}
+__global__ void sample_gauss_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, Cdt cdt, int64_t *out, int logn) {
+    const int N = 1 << logn;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 4; b += gridDim.x * blockDim.x) {
+        uint64_t c[4] = {(uint64_t)b, 0, nonce, 0};
+        philox4x64(c, seed, tag);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint64_t r = c[w] >> 24;
+            int64_t x = -19;
+            for (int k = 0; k < 38; ++k) x += (r >= cdt.t[k]);
+            out[4 * b + w] = x;
+        }
+    }
+}
+
+// ternary secret: (word mod 3) - 1, block (j/4, 0, 0, 0), key (seed, 1)
+__global__ void sample_ternary_kernel(uint64_t seed, int64_t *out, int logn) {
+    const int N = 1 << logn;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 4; b += gridDim.x * blockDim.x) {
+        uint64_t c[4] = {(uint64_t)b, 0, 0, 0};
+        philox4x64(c, seed, 1);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) out[4 * b + w] = (int64_t)(c[w] % 3) - 1;
+    }
+}
+
+// c0 = m - a s + e, c1 = a (NTT domain, limbs 0..level)
+__global__ void encrypt_combine_kernel(const uint64_t *__restrict__ pt, const uint64_t *__restrict__ a, const uint64_t *__restrict__ e,
+                                       const uint64_t *__restrict__ sk_mont, int nl, uint64_t *ct, const ModConst *__restrict__ mc, int logn) {
+    const int N = 1 << logn;
+    const int l = blockIdx.y;
+    const uint64_t q = mc[l].q, qinv = mc[l].qinv;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const int64_t i = (int64_t)l * N + k;
+        const uint64_t as = mont_mul(a[i], sk_mont[i], q, qinv);
+        ct[i] = add_mod(sub_mod(pt[i], as, q), e[i], q);
+        ct[(int64_t)nl * N + i] = a[i];
+    }
+}
+
+struct PmodQ {
+    uint64_t v[HE_MAX_LIMBS];  // P mod q_l for Q limbs
+};
+
+// Galois key digit d over Q U P (NTT): b = -a s + e + [l in digit d] (P mod q_l) s(X^g); stored (b, a) in Montgomery form
+__global__ void keygen_combine_kernel(const uint64_t *__restrict__ a, const uint64_t *__restrict__ e, const uint64_t *__restrict__ sk,
+                                      const uint64_t *__restrict__ sk_mont, uint32_t g, int d_lo, int d_hi, PmodQ pm, int LK,
+                                      uint64_t *key_d, const ModConst *__restrict__ mc, int logn) {
+    const int N = 1 << logn;
+    const int l = blockIdx.y;
+    const ModConst m = mc[l];
+    const bool in_digit = l >= d_lo && l < d_hi;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const int64_t i = (int64_t)l * N + k;
+        uint64_t b = sub_mod(e[i], mont_mul(a[i], sk_mont[i], m.q, m.qinv), m.q);
+        if (in_digit) {
+            const uint64_t sg = sk[(int64_t)l * N + automorph_src(k, g, logn)];
+            b = add_mod(b, (uint64_t)((u128)sg * pm.v[l] % m.q), m.q);
+        }
+        key_d[i] = mont_mul(b, m.r2, m.q, m.qinv);
+        key_d[(int64_t)LK * N + i] = mont_mul(a[i], m.r2, m.q, m.qinv);
+    }
+}
+
+}  // namespace
+
+static size_t fft_smem_bytes(int logn) { return (size_t)8 << logn; }  // N/2 double2
+
+void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs) {
+    if (count == 0) return;
+    const double2 *tw = reinterpret_cast<const double2 *>(ctx->d_fft);
+    const double2 *twist = tw + ctx->n / 4;
+    const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
+    ctx->launches++;
+    encode_kernel<<<count, 512, fft_smem_bytes(ctx->log_n), ctx->stream>>>(slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
+}
+
+void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots) {
+    if (count == 0) return;
+    const double2 *tw = reinterpret_cast<const double2 *>(ctx->d_fft);
+    const double2 *twist = tw + ctx->n / 4;
+    const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
+    ctx->launches++;
+    decode_kernel<<<count, 512, fft_smem_bytes(ctx->log_n), ctx->stream>>>(coeffs, scale, tw, twist, pos, slots, ctx->log_n);
+}
+
+void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *) {
+    const int64_t words = 2 * (int64_t)(level + 1) * ctx->n;
+    ctx->launches++;
+    decrypt_kernel<<<count, 512, (size_t)ctx->n * 8, ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
+                                                                    ctx->log_n);
+}
+
+void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int, uint64_t *out) {
+    dim3 grid((ctx->n / 2 + 255) / 256, map.n);
+    ctx->launches++;
+    sample_uniform_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->seed, tag, nonce, map, out, ctx->d_mc, ctx->log_n);
+}
+
+void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out) {
+    Cdt c;
+    for (int k = 0; k < 38; ++k) c.t[k] = ctx->cdt[k];
+    ctx->launches++;
+    sample_gauss_kernel<<<(ctx->n / 4 + 255) / 256, 256, 0, ctx->stream>>>(ctx->seed, tag, nonce, c, out, ctx->log_n);
+}
+
+void launch_sample_ternary(he_ctx *ctx, int64_t *out) {
+    ctx->launches++;
+    sample_ternary_kernel<<<(ctx->n / 4 + 255) / 256, 256, 0, ctx->stream>>>(ctx->seed, out, ctx->log_n);
+}
+
+void launch_encrypt_combine(he_ctx *ctx, const uint64_t *pt, const uint64_t *a, const uint64_t *e, int level, uint64_t *ct) {
+    dim3 grid((ctx->n + 255) / 256, level + 1);
+    ctx->launches++;
+    encrypt_combine_kernel<<<grid, 256, 0, ctx->stream>>>(pt, a, e, ctx->d_sk_mont, level + 1, ct, ctx->d_mc, ctx->log_n);
+}
+
+void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, uint32_t g, int digit, uint64_t *key_d) {
+    PmodQ pm{};
+    for (int l = 0; l < ctx->L; ++l) {
+        uint64_t q = ctx->primes[l], v = 1 % q;
+        for (int j = 0; j < ctx->K; ++j) v = (uint64_t)((u128)v * (ctx->primes[ctx->L + j] % q) % q);
+        pm.v[l] = v;
+    }
+    const int lo = digit * ctx->alpha, hi = lo + ctx->alpha < ctx->L ? lo + ctx->alpha : ctx->L;
+    dim3 grid((ctx->n + 255) / 256, ctx->L + ctx->K);
+    ctx->launches++;
+    keygen_combine_kernel<<<grid, 256, 0, ctx->stream>>>(a, e, ctx->d_sk, ctx->d_sk_mont, g, lo, hi, pm, ctx->L + ctx->K, key_d, ctx->d_mc,
+                                                         ctx->log_n);
+}
+
+void encode_set_smem_limits(int max_bytes) {
+    cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(decrypt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+}

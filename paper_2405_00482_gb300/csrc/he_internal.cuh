@@ -1,0 +1,199 @@
+// he_internal.cuh -- internal definitions of the GB300 RNS-CKKS / PackVFL library.
+//
+// Data layout in HBM (all residues uint64, canonical in [0, q)):
+//   limb-poly     [N] in NTT form, bit-reversed order: slot k holds a(psi^(2 brv(k) + 1))
+//   ciphertext    [2][level+1][N]   (c0, c1)
+//   Galois key    [dnum][2][L+K][N] (b_d, a_d), Montgomery form (x * 2^64 mod q)
+//   MatMult plaintexts [R][C][m'][level+1+K][N], Montgomery form
+// Montgomery form is used for operands that are fixed while a hot loop reads them,
+// so that one REDC returns a canonical product.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <vector>
+
+#include "../../include/he.h"
+
+#define HE_MAX_LIMBS 24   // Q primes + P primes
+#define HE_MAX_Q 16
+#define HE_MAX_P 8
+#define HE_MAX_DNUM 8
+
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------------------------------
+// modular arithmetic (device)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+    uint64_t s = a + b;
+    return s >= q ? s - q : s;
+}
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) { return a >= b ? a - b : a + q - b; }
+
+// Shoup: x * w mod q with wp = floor(w 2^64 / q); valid for any x < 2^64, q < 2^63
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t x, uint64_t w, uint64_t wp, uint64_t q) {
+    uint64_t hi = __umul64hi(x, wp);
+    uint64_t r = x * w - hi * q;
+    return r >= q ? r - q : r;
+}
+// lazy variant, result in [0, 2q)
+__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t x, uint64_t w, uint64_t wp, uint64_t q) {
+    return x * w - __umul64hi(x, wp) * q;
+}
+
+// Montgomery reduction of T = hi 2^64 + lo < q 2^64: returns T 2^-64 mod q in [0, q).
+// qinv = -q^-1 mod 2^64.
+__device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qinv) {
+    uint64_t m = lo * qinv;
+    uint64_t r = hi + __umul64hi(m, q) + (lo != 0);
+    return r >= q ? r - q : r;
+}
+__device__ __forceinline__ uint64_t redc128(u128 t, uint64_t q, uint64_t qinv) {
+    return redc((uint64_t)(t >> 64), (uint64_t)t, q, qinv);
+}
+// a * bM 2^-64 mod q  (bM in Montgomery form -> canonical product)
+__device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t bM, uint64_t q, uint64_t qinv) {
+    return redc128((u128)a * bM, q, qinv);
+}
+
+__device__ __forceinline__ uint64_t reduce_signed(int64_t v, uint64_t q) {
+    // v in (-2^63, 2^63): canonical residue
+    if (v >= 0) return (uint64_t)v % q;
+    uint64_t r = ((uint64_t)(-(v + 1))) % q;  // -(v+1) >= 0 and avoids overflow at INT64_MIN
+    return q - 1 - r;
+}
+
+// position of the NTT-domain slot k after the automorphism X -> X^g (bit-reversed order):
+// out[k] = in[automorph_src(k, g)], exponent e_k = 2 brv(k) + 1.
+__device__ __forceinline__ uint32_t automorph_src(uint32_t k, uint32_t g, int logn) {
+    uint32_t e = 2u * (__brev(k) >> (32 - logn)) + 1u;
+    uint32_t e2 = (uint32_t)(((uint64_t)e * g) & ((2ull << logn) - 1));
+    return __brev((e2 - 1u) >> 1) >> (32 - logn);
+}
+
+// ------------------------------------------------------------------------------------------
+// per-prime constants
+// ------------------------------------------------------------------------------------------
+struct ModConst {
+    uint64_t q;
+    uint64_t qinv;    // -q^-1 mod 2^64
+    uint64_t r2;      // 2^128 mod q (to Montgomery form: redc(x * r2))
+    uint64_t ninv, ninv_shoup;  // N^-1 mod q
+};
+
+// index map from a batch's limb position to the context's prime index
+struct LimbMap {
+    int32_t n;                     // limbs per group
+    int32_t prime[HE_MAX_LIMBS];   // prime index of each limb
+};
+
+// basis-conversion constants for ModUp of one level (digits of c1 -> Q_level U P)
+struct ModUpConst {
+    int32_t ndig, alpha, ext, nq;       // digits present, primes per digit, limbs of Q_level U P, level+1
+    int32_t ext_prime[HE_MAX_LIMBS];    // prime index of each extended limb
+    // for digit d, source i (0 <= i < alpha): [(Qd/q_i)^-1]_{q_i} with Shoup companion
+    uint64_t inv[HE_MAX_DNUM][4], inv_shoup[HE_MAX_DNUM][4];
+    // (Qd/q_i) mod target prime of extended limb u, with Shoup companion
+    uint64_t hat[HE_MAX_DNUM][4][HE_MAX_LIMBS], hat_shoup[HE_MAX_DNUM][4][HE_MAX_LIMBS];
+};
+
+// constants for ModDown of one level (Q_level U P -> Q_level)
+struct ModDownConst {
+    int32_t nq, K;                       // level+1, number of P primes
+    int32_t q_prime[HE_MAX_Q];           // prime indices of Q_level
+    int32_t p_prime[HE_MAX_P];
+    uint64_t inv[HE_MAX_P], inv_shoup[HE_MAX_P];                      // [(P/p_i)^-1]_{p_i}
+    uint64_t hat[HE_MAX_P][HE_MAX_Q], hat_shoup[HE_MAX_P][HE_MAX_Q];  // (P/p_i) mod q_j
+    uint64_t pinv[HE_MAX_Q], pinv_shoup[HE_MAX_Q];                    // P^-1 mod q_j
+};
+
+struct he_ctx {
+    int log_n, n, L, K, dnum, alpha;
+    uint64_t seed;
+    cudaStream_t stream;
+    std::vector<uint64_t> primes;     // Q then P
+    std::vector<ModConst> mc;         // host copy
+    ModConst *d_mc;                   // device copy
+    uint64_t *d_tw;                   // [L+K][4][N]: psi_rev, psi_rev_shoup, ipsi_rev, ipsi_rev_shoup
+    double *d_fft;                    // encode/decode tables: [N/2] twiddles (re, im) and [N] twist
+    uint64_t *d_sk_mont;              // [L+K][N] secret in NTT + Montgomery form
+    uint64_t *d_sk;                   // [L+K][N] secret in NTT form
+    std::map<uint32_t, uint64_t *> keys;  // Galois element -> [dnum][2][L+K][N]
+    std::vector<ModUpConst> modup;    // per level
+    std::vector<ModDownConst> moddown;  // per level
+    uint64_t cdt[38];
+    // scratch (grown on demand, reused across calls on this context's stream)
+    uint64_t *scratch;
+    size_t scratch_words;
+    // kernels launched so far, and CUDA-event timing of the MatMult loop kernel when enabled
+    int64_t launches;
+    bool prof_on;
+    std::vector<cudaEvent_t> prof_events;  // start/end pairs, recorded on `stream`
+    size_t prof_used;
+};
+
+struct he_plan {
+    int64_t m, n, slots, mp, np, mb, nb, row_blocks, col_blocks, m_prime, blocks;
+};
+
+struct he_ptmat {
+    he_ctx *ctx;
+    he_plan plan;
+    int level;
+    double scale;
+    int ext;                 // limbs per plaintext (level + 1 + K)
+    uint64_t *data;          // [R][C][m'][ext][N], NTT + Montgomery
+    const uint64_t **d_keys; // device array [m'-1] of Galois key pointers (filled at first use)
+    std::vector<uint32_t> galois;
+    uint32_t *d_galois;      // [m'-1]
+};
+
+// ------------------------------------------------------------------------------------------
+// launchers (all asynchronous on ctx->stream)
+// ------------------------------------------------------------------------------------------
+int he_check(cudaError_t e);
+uint64_t *ctx_scratch(he_ctx *ctx, size_t words);  // nullptr on allocation failure
+
+// NTT of `groups` x map.n limb-polys; in and out may alias.
+void launch_ntt_fwd(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map);
+void launch_ntt_inv(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map);
+// strided forms: limb l of group g at base + g * gs + l * N; to_mont stores x 2^64 mod q
+void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
+                            const LimbMap &map, int to_mont);
+void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map);
+int ntt_threads(int logn);
+// NTT forward of signed int64 coefficient vectors reduced per limb: in [groups][N] -> out [groups][map.n][N]
+void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int groups, const LimbMap &map, int to_mont);
+// x -> x 2^64 mod q in place
+void launch_to_mont(he_ctx *ctx, uint64_t *data, int groups, const LimbMap &map);
+
+// elementwise
+void launch_add(he_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, int groups, const LimbMap &map);
+void launch_mul_plain(he_ctx *ctx, const uint64_t *ct, const uint64_t *pt, uint64_t *out, int level);
+
+// key switching
+void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, uint64_t *tmp_coeff);
+void launch_ks_inner(he_ctx *ctx, const uint64_t *D, int level, uint32_t g, const uint64_t *key, uint64_t *u /*[2][ext][N]*/);
+// out_c = add_c (optional, NTT) + ModDown(x_c) for c = 0..ncomp-1 ; x [ncomp][ext][N], tmp [ncomp][K][N]
+void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const uint64_t *add0, const uint64_t *add1, uint64_t *out,
+                    uint64_t *tmp);
+void launch_automorph(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map, uint32_t g);
+void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, uint64_t *tmp);
+void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D,
+                         uint64_t *acc /*[2][ext][N]*/, uint64_t *cacc /*[2][level+1][N]*/, int accumulate);
+
+// encoding, sampling, encryption
+void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs);
+void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots);
+void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *tmp);
+void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int limb_offset, uint64_t *out);
+void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out);
+void launch_sample_ternary(he_ctx *ctx, int64_t *out);
+void launch_encrypt_combine(he_ctx *ctx, const uint64_t *pt, const uint64_t *a, const uint64_t *e, int level, uint64_t *ct);
+void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, uint32_t g, int digit, uint64_t *key_d);
+void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots);
+void launch_layout_vector(he_ctx *ctx, const he_plan &p, const double *y, double *slots);
+void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, double *y);

@@ -1,0 +1,123 @@
+// he_ntt.cu -- batched negacyclic NTT / inverse NTT kernels over RNS limbs.
+//
+// One CTA transforms one limb-poly of N residues staged in shared memory (8N bytes).
+// Batch layout: limb l of group g sits at base + g * group_stride + l * N, with prime
+// index map.prime[l].  Grid = groups * map.n CTAs.
+#include "he_internal.cuh"
+#include "he_ntt.cuh"
+
+namespace {
+
+__global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
+                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int to_mont) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int g = blockIdx.x / map.n, l = blockIdx.x % map.n;
+    const int p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    const uint64_t *src = in + g * in_gs + (int64_t)l * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    __syncthreads();
+    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), twiddles(d_tw, p, 1, logn), q, logn);
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N;
+    if (to_mont) {
+        const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[k], r2, q, qinv);
+    } else {
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
+    }
+}
+
+__global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
+                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int g = blockIdx.x / map.n, l = blockIdx.x % map.n;
+    const int p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    const uint64_t *src = in + g * in_gs + (int64_t)l * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    __syncthreads();
+    ntt_inv_smem(s, twiddles(d_tw, p, 2, logn), twiddles(d_tw, p, 3, logn), q, logn);
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N;
+    const uint64_t ni = mc[p].ninv, nis = mc[p].ninv_shoup;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], ni, nis, q);
+}
+
+// signed int64 coefficients of group g, reduced mod each limb's prime, then forward NTT
+__global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *out, LimbMap map, const uint64_t *__restrict__ d_tw,
+                                      const ModConst *__restrict__ mc, int logn, int to_mont) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int g = blockIdx.x / map.n, l = blockIdx.x % map.n;
+    const int p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    const int64_t *src = in + (int64_t)g * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = reduce_signed(src[k], q);
+    __syncthreads();
+    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), twiddles(d_tw, p, 1, logn), q, logn);
+    uint64_t *dst = out + ((int64_t)g * map.n + l) * N;
+    if (to_mont) {
+        const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[k], r2, q, qinv);
+    } else {
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
+    }
+}
+
+__global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__restrict__ mc, int logn) {
+    const int N = 1 << logn;
+    const int g = blockIdx.y, l = blockIdx.z;
+    const int p = map.prime[l];
+    uint64_t *d = data + ((int64_t)g * map.n + l) * N;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) d[k] = mont_mul(d[k], mc[p].r2, mc[p].q, mc[p].qinv);
+}
+
+}  // namespace
+
+int ntt_threads(int logn) { return logn >= 10 ? 512 : (1 << (logn - 1)); }
+
+void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
+                            const LimbMap &map, int to_mont) {
+    if (groups * map.n == 0) return;
+    ctx->launches++;
+    ntt_fwd_kernel<<<groups * map.n, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+                                                                                               ctx->d_mc, ctx->log_n, to_mont);
+}
+
+void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map) {
+    if (groups * map.n == 0) return;
+    ctx->launches++;
+    ntt_inv_kernel<<<groups * map.n, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+                                                                                               ctx->d_mc, ctx->log_n);
+}
+
+void launch_ntt_fwd(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map) {
+    int64_t gs = (int64_t)map.n * ctx->n;
+    launch_ntt_fwd_strided(ctx, in, gs, out, gs, groups, map, 0);
+}
+
+void launch_ntt_inv(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map) {
+    int64_t gs = (int64_t)map.n * ctx->n;
+    launch_ntt_inv_strided(ctx, in, gs, out, gs, groups, map);
+}
+
+void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int groups, const LimbMap &map, int to_mont) {
+    if (groups * map.n == 0) return;
+    ctx->launches++;
+    ntt_from_int64_kernel<<<groups * map.n, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(in, out, map, ctx->d_tw, ctx->d_mc,
+                                                                                                      ctx->log_n, to_mont);
+}
+
+void launch_to_mont(he_ctx *ctx, uint64_t *data, int groups, const LimbMap &map) {
+    if (groups * map.n == 0) return;
+    dim3 grid((ctx->n + 255) / 256, groups, map.n);
+    ctx->launches++;
+    to_mont_kernel<<<grid, 256, 0, ctx->stream>>>(data, map, ctx->d_mc, ctx->log_n);
+}
+
+void ntt_set_smem_limits(int max_bytes) {
+    cudaFuncSetAttribute(ntt_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_from_int64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+}

@@ -1,0 +1,370 @@
+"""Python binding of the C ABI in include/he.h (argument marshalling only).
+
+Every computation runs in the CUDA kernels of libhe.so; this module only allocates
+device buffers with torch, passes their pointers and the stream, and checks status codes.
+Residue buffers are torch.int64 tensors used as raw 64-bit storage (the library treats
+them as uint64).  Loading fails loudly if libhe.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhe.so")
+
+HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_EKEY, HE_ELEVEL, HE_ESCALE, HE_ETIMEOUT, HE_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7, -8
+
+
+class HEError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {_lib().he_strerror(status).decode()} ({status})")
+        self.status = status
+
+
+class HeParams(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_int32), ("n_q", ctypes.c_int32), ("n_p", ctypes.c_int32), ("dnum", ctypes.c_int32),
+                ("q_bits", ctypes.c_int32 * 16), ("p_bits", ctypes.c_int32 * 8)]
+
+
+class HeCt(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("level", ctypes.c_int32), ("scale", ctypes.c_double)]
+
+
+HePt = HeCt  # same layout: data, level, scale
+
+_vp, _i32, _i64, _u64, _dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+_SIGS = {
+    "he_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "he_params_primes": (ctypes.c_int, [ctypes.POINTER(HeParams), ctypes.POINTER(_u64)]),
+    "he_cdt_table": (ctypes.c_int, [ctypes.POINTER(_u64)]),
+    "he_ctx_create": (ctypes.c_int, [ctypes.POINTER(HeParams), _u64, _vp, ctypes.POINTER(_vp)]),
+    "he_ctx_destroy": (None, [_vp]),
+    "he_synchronize": (ctypes.c_int, [_vp]),
+    "he_ctx_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "he_keygen": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.c_int]),
+    "he_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "he_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "he_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
+    "he_encode": (ctypes.c_int, [_vp, _vp, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
+    "he_encrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _u64, ctypes.POINTER(HeCt)]),
+    "he_decrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
+    "he_add": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
+    "he_mul_plain": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HePt), ctypes.POINTER(HeCt)]),
+    "he_rescale": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
+    "he_rotate": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _i32, ctypes.POINTER(HeCt)]),
+    "he_rotate_hoisted": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(_i32), ctypes.c_int, ctypes.POINTER(HeCt)]),
+    "he_plan_create": (ctypes.c_int, [_i64, _i64, _i64, ctypes.POINTER(_vp)]),
+    "he_plan_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "he_plan_free": (None, [_vp]),
+    "he_encode_matrix": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "he_ptmat_encode": (ctypes.c_int, [_vp, _vp, _vp]),
+    "he_ptmat_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(_vp)]),
+    "he_ptmat_free": (None, [_vp]),
+    "he_encode_vector": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
+    "he_matmult_plain_cipher": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(HeCt), ctypes.c_int, ctypes.POINTER(HeCt), ctypes.c_int]),
+    "he_matmult_decode": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "he_ct_export": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
+    "he_ct_import": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(HeCt)]),
+    "he_pt_export": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp]),
+    "he_pt_import": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(HePt)]),
+}
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it first (python -m paper_2405_00482_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def lib():
+    return _lib()
+
+
+def _check(status: int, what: str):
+    if status != HE_OK:
+        raise HEError(status, what)
+
+
+def make_params(log_n: int, q_bits, p_bits, dnum: int) -> HeParams:
+    p = HeParams()
+    p.log_n, p.n_q, p.n_p, p.dnum = log_n, len(q_bits), len(p_bits), dnum
+    for i, b in enumerate(q_bits):
+        p.q_bits[i] = b
+    for i, b in enumerate(p_bits):
+        p.p_bits[i] = b
+    return p
+
+
+def primes(log_n: int, q_bits, p_bits, dnum: int) -> list[int]:
+    """Host-side prime chain of the library (no GPU needed)."""
+    p = make_params(log_n, q_bits, p_bits, dnum)
+    out = (_u64 * (len(q_bits) + len(p_bits)))()
+    _check(_lib().he_params_primes(ctypes.byref(p), out), "he_params_primes")
+    return [int(v) for v in out]
+
+
+def cdt_table() -> list[int]:
+    out = (_u64 * 38)()
+    _check(_lib().he_cdt_table(out), "he_cdt_table")
+    return [int(v) for v in out]
+
+
+class Plan:
+    """MatMult layout plan (host only): he_plan_create / he_plan_query."""
+
+    FIELDS = ("m", "n", "slots", "mp", "np", "mb", "nb", "row_blocks", "col_blocks", "m_prime", "blocks")
+
+    def __init__(self, m: int, n: int, slots: int):
+        h = _vp()
+        _check(_lib().he_plan_create(m, n, slots, ctypes.byref(h)), "he_plan_create")
+        self.handle = h
+        info = (_i64 * 11)()
+        _check(_lib().he_plan_query(h, info), "he_plan_query")
+        for k, v in zip(self.FIELDS, info):
+            setattr(self, k, int(v))
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib().he_plan_free(self.handle)
+            self.handle = None
+
+
+@dataclass
+class Ciphertext:
+    data: torch.Tensor  # int64 [2][level+1][N], NTT form
+    level: int
+    scale: float
+
+    def c(self) -> HeCt:
+        return HeCt(self.data.data_ptr(), self.level, self.scale)
+
+
+@dataclass
+class Plaintext:
+    data: torch.Tensor  # int64 [level+1][N], NTT form
+    level: int
+    scale: float
+
+    def c(self) -> HePt:
+        return HePt(self.data.data_ptr(), self.level, self.scale)
+
+
+class PtMatrix:
+    def __init__(self, ctx: "Context", handle, plan: Plan, level: int):
+        self.ctx, self.handle, self.plan, self.level = ctx, handle, plan, level
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib().he_ptmat_free(self.handle)
+            self.handle = None
+
+
+def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    return t.to(dtype).contiguous()
+
+
+class Context:
+    """he_ctx: parameters, tables, secret key and Galois keys on one CUDA device and stream."""
+
+    def __init__(self, log_n: int, q_bits, p_bits, dnum: int, seed: int = 0, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.stream = stream or torch.cuda.current_stream()
+        self.params = make_params(log_n, q_bits, p_bits, dnum)
+        h = _vp()
+        _check(_lib().he_ctx_create(ctypes.byref(self.params), seed, _vp(self.stream.cuda_stream), ctypes.byref(h)), "he_ctx_create")
+        self.handle = h
+        self.n = 1 << log_n
+        self.slots = self.n // 2
+        self.L, self.K = len(q_bits), len(p_bits)
+        self.primes = primes(log_n, q_bits, p_bits, dnum)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib().he_ctx_destroy(self.handle)
+            self.handle = None
+
+    # ---- buffers ----
+    def new_ct(self, level: int) -> Ciphertext:
+        return Ciphertext(torch.empty((2, level + 1, self.n), dtype=torch.int64, device=self.device), level, 0.0)
+
+    def new_pt(self, level: int) -> Plaintext:
+        return Plaintext(torch.empty((level + 1, self.n), dtype=torch.int64, device=self.device), level, 0.0)
+
+    def synchronize(self):
+        _check(_lib().he_synchronize(self.handle), "he_synchronize")
+
+    def launch_count(self) -> int:
+        v = _i64()
+        _check(_lib().he_launch_count(self.handle, ctypes.byref(v)), "he_launch_count")
+        return int(v.value)
+
+    def profile(self, on: bool):
+        _check(_lib().he_profile_enable(self.handle, int(on)), "he_profile_enable")
+
+    def profile_read(self) -> tuple[float, int]:
+        ms, n = _dbl(), _i64()
+        _check(_lib().he_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n)), "he_profile_read")
+        return float(ms.value), int(n.value)
+
+    # ---- keys / encode / encrypt / decrypt ----
+    def keygen(self, steps):
+        arr = (_i32 * len(steps))(*steps)
+        _check(_lib().he_keygen(self.handle, arr, len(steps)), "he_keygen")
+
+    def encode(self, slots: torch.Tensor, scale: float, level: int, out: Plaintext | None = None) -> Plaintext:
+        slots = _dev(slots, torch.float64)
+        pt = out or self.new_pt(level)
+        c = pt.c()
+        _check(_lib().he_encode(self.handle, slots.data_ptr(), slots.numel(), scale, level, ctypes.byref(c)), "he_encode")
+        pt.level, pt.scale = c.level, c.scale
+        return pt
+
+    def encrypt(self, pt: Plaintext, nonce: int, out: Ciphertext | None = None) -> Ciphertext:
+        ct = out or self.new_ct(pt.level)
+        p, c = pt.c(), ct.c()
+        _check(_lib().he_encrypt(self.handle, ctypes.byref(p), nonce, ctypes.byref(c)), "he_encrypt")
+        ct.level, ct.scale = c.level, c.scale
+        return ct
+
+    def decrypt(self, ct: Ciphertext, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = out if out is not None else torch.empty(self.slots, dtype=torch.float64, device=self.device)
+        c = ct.c()
+        _check(_lib().he_decrypt(self.handle, ctypes.byref(c), out.data_ptr()), "he_decrypt")
+        return out
+
+    # ---- O1..O4, rescale ----
+    def add(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        out = self.new_ct(a.level)
+        ca, cb, co = a.c(), b.c(), out.c()
+        _check(_lib().he_add(self.handle, ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(co)), "he_add")
+        out.scale = co.scale
+        return out
+
+    def mul_plain(self, ct: Ciphertext, pt: Plaintext) -> Ciphertext:
+        out = self.new_ct(ct.level)
+        c, p, o = ct.c(), pt.c(), out.c()
+        _check(_lib().he_mul_plain(self.handle, ctypes.byref(c), ctypes.byref(p), ctypes.byref(o)), "he_mul_plain")
+        out.scale = o.scale
+        return out
+
+    def rescale(self, ct: Ciphertext) -> Ciphertext:
+        out = self.new_ct(max(ct.level - 1, 0))
+        c, o = ct.c(), out.c()
+        _check(_lib().he_rescale(self.handle, ctypes.byref(c), ctypes.byref(o)), "he_rescale")
+        out.level, out.scale = o.level, o.scale
+        return out
+
+    def rotate(self, ct: Ciphertext, step: int) -> Ciphertext:
+        out = self.new_ct(ct.level)
+        c, o = ct.c(), out.c()
+        _check(_lib().he_rotate(self.handle, ctypes.byref(c), step, ctypes.byref(o)), "he_rotate")
+        out.scale = o.scale
+        return out
+
+    def rotate_hoisted(self, ct: Ciphertext, steps) -> list[Ciphertext]:
+        outs = [self.new_ct(ct.level) for _ in steps]
+        arr = (HeCt * len(steps))(*[o.c() for o in outs])
+        st = (_i32 * len(steps))(*steps)
+        c = ct.c()
+        _check(_lib().he_rotate_hoisted(self.handle, ctypes.byref(c), st, len(steps), arr), "he_rotate_hoisted")
+        for o, a in zip(outs, arr):
+            o.scale = a.scale
+        return outs
+
+    # ---- MatMult ----
+    def encode_matrix(self, plan: Plan, X: torch.Tensor, level: int, out: PtMatrix | None = None) -> PtMatrix:
+        X = _dev(X, torch.float64)
+        if out is not None:
+            _check(_lib().he_ptmat_encode(self.handle, out.handle, X.data_ptr()), "he_ptmat_encode")
+            return out
+        h = _vp()
+        _check(_lib().he_encode_matrix(self.handle, plan.handle, X.data_ptr(), level, ctypes.byref(h)), "he_encode_matrix")
+        return PtMatrix(self, h, plan, level)
+
+    def ptmat_import(self, plan: Plan, coeffs: torch.Tensor, level: int, scale: float) -> PtMatrix:
+        coeffs = _dev(coeffs, torch.int64)
+        h = _vp()
+        _check(_lib().he_ptmat_import(self.handle, plan.handle, coeffs.data_ptr(), level, scale, ctypes.byref(h)), "he_ptmat_import")
+        return PtMatrix(self, h, plan, level)
+
+    def encode_vector(self, plan: Plan, y: torch.Tensor, scale: float, level: int, outs: list[Plaintext] | None = None) -> list[Plaintext]:
+        y = _dev(y, torch.float64)
+        pts = outs or [self.new_pt(level) for _ in range(plan.col_blocks)]
+        arr = (HePt * len(pts))(*[p.c() for p in pts])
+        _check(_lib().he_encode_vector(self.handle, plan.handle, y.data_ptr(), scale, level, arr), "he_encode_vector")
+        for p, a in zip(pts, arr):
+            p.level, p.scale = a.level, a.scale
+        return pts
+
+    def matmult(self, plan: Plan, pm: PtMatrix, cts: list[Ciphertext], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
+        outs = outs or [self.new_ct(pm.level - 1) for _ in range(plan.row_blocks)]
+        ins = (HeCt * len(cts))(*[c.c() for c in cts])
+        oa = (HeCt * len(outs))(*[o.c() for o in outs])
+        _check(_lib().he_matmult_plain_cipher(self.handle, plan.handle, pm.handle, ins, len(cts), oa, len(outs)), "he_matmult_plain_cipher")
+        for o, a in zip(outs, oa):
+            o.level, o.scale = a.level, a.scale
+        return outs
+
+    def matmult_decode(self, plan: Plan, slots: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        slots = _dev(slots, torch.float64)
+        out = out if out is not None else torch.empty(plan.m, dtype=torch.float64, device=self.device)
+        _check(_lib().he_matmult_decode(self.handle, plan.handle, slots.data_ptr(), out.data_ptr()), "he_matmult_decode")
+        return out
+
+    # ---- canonical coefficient form ----
+    def ct_export(self, ct: Ciphertext) -> torch.Tensor:
+        out = torch.empty_like(ct.data)
+        c = ct.c()
+        _check(_lib().he_ct_export(self.handle, ctypes.byref(c), out.data_ptr()), "he_ct_export")
+        return out
+
+    def ct_import(self, coeffs: torch.Tensor, level: int, scale: float) -> Ciphertext:
+        coeffs = _dev(coeffs, torch.int64)
+        ct = self.new_ct(level)
+        c = ct.c()
+        _check(_lib().he_ct_import(self.handle, coeffs.data_ptr(), level, scale, ctypes.byref(c)), "he_ct_import")
+        ct.scale = scale
+        return ct
+
+    def pt_export(self, pt: Plaintext) -> torch.Tensor:
+        out = torch.empty_like(pt.data)
+        p = pt.c()
+        _check(_lib().he_pt_export(self.handle, ctypes.byref(p), out.data_ptr()), "he_pt_export")
+        return out
+
+    def pt_import(self, coeffs: torch.Tensor, level: int, scale: float) -> Plaintext:
+        coeffs = _dev(coeffs, torch.int64)
+        pt = self.new_pt(level)
+        p = pt.c()
+        _check(_lib().he_pt_import(self.handle, coeffs.data_ptr(), level, scale, ctypes.byref(p)), "he_pt_import")
+        pt.scale = scale
+        return pt
+
+
+def as_u64(t: torch.Tensor):
+    """Device int64 residue tensor -> host numpy uint64 array."""
+    return t.detach().cpu().numpy().view("uint64")
+
+
+def from_u64(a, device) -> torch.Tensor:
+    import numpy as np
+
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)

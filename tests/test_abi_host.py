@@ -1,0 +1,72 @@
+"""C-ABI library on the CPU (no compute calls): it loads, exports every symbol declared in
+include/he.h, and its host-side logic (prime chain, sampler table, MatMult planner,
+argument checks) agrees with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import ckks, layout
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def he():
+    from paper_2405_00482_gb300 import build as b
+
+    b.build()
+    from paper_2405_00482_gb300 import he as h
+
+    return h
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "he.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(he_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(he):
+    lib = ctypes.CDLL(he.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 25
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("log_n,qb,pb,dnum", [(12, [40, 20], [40], 2), (13, [60, 40, 40], [60], 3),
+                                               (14, [60] + [40] * 6, [60, 60, 60], 3), (6, [60, 40, 40], [60], 3),
+                                               (10, [50, 40, 40, 40], [55, 55], 2)])
+def test_prime_chain_agrees_with_oracle(he, log_n, qb, pb, dnum):
+    assert he.primes(log_n, qb, pb, dnum) == ckks.gen_primes(log_n, qb + pb)
+
+
+def test_gaussian_table_agrees_with_oracle(he, oracle_lib):
+    t = np.zeros(38, np.uint64)
+    oracle_lib.or_cdt_table(t)
+    assert [int(v) for v in t] == he.cdt_table()
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 5), (16, 64), (64, 16), (256, 1024), (1024, 256), (4096, 4096), (5000, 37),
+                                 (37, 5000), (9000, 9000), (4097, 4095), (512, 8192), (16384, 64), (128, 2)])
+def test_planner_agrees_with_oracle(he, m, n):
+    p = he.Plan(m, n, 4096)
+    o = layout.make_plan(m, n, 4096)
+    assert (p.m, p.n, p.slots, p.mp, p.np, p.mb, p.nb, p.row_blocks, p.col_blocks, p.m_prime, p.blocks) == (
+        o.m, o.n, o.slots, o.mp, o.np_, o.mb, o.nb, o.row_blocks, o.col_blocks, o.m_prime, o.blocks)
+
+
+def test_invalid_arguments_are_rejected(he):
+    with pytest.raises(he.HEError) as e:
+        he.Plan(0, 4, 8)
+    assert e.value.status == he.HE_EINVAL
+    with pytest.raises(he.HEError):
+        he.Plan(4, 4, 6)
+    with pytest.raises(he.HEError):
+        he.primes(13, [70], [60], 1)  # no 70-bit primes
+    with pytest.raises(he.HEError):
+        he.primes(13, [60, 40], [60], 3)  # more digits than primes
+    assert he.lib().he_strerror(he.HE_EKEY) == b"missing Galois key"
