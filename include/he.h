@@ -159,6 +159,18 @@ int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double s
 int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in,
                             he_ct *outs, int n_out);
 
+/* Batched form of the hot path for many independent MatMults of uneven shapes (one input
+ * and one output ciphertext each, i.e. m, n <= N/2) at one level.  he_batch_create binds the
+ * plans, encoded matrices and Galois keys and allocates the batch's scratch; he_batch_run
+ * computes outs[j] = MatMult(pms[j], ins[j]) for every j with one persistent work-queue kernel
+ * for all rotation steps of all jobs (keys shared across jobs), the whole sequence captured
+ * once into a CUDA graph and replayed on later runs.  Results are bit-identical to
+ * he_matmult_plain_cipher on each job.  Asynchronous on the context's stream. */
+typedef struct he_batch he_batch;
+int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const he_ptmat *const *pms, he_batch **out);
+int he_batch_run(he_ctx *ctx, he_batch *batch, const he_ct *ins, he_ct *outs);
+void he_batch_free(he_batch *batch);
+
 /* P_B's side after decryption: lazy rotate-and-sum (Sec. 4.3).  slots: device
  * [row_blocks][N/2] doubles (he_decrypt of each output), y_out: device m doubles. */
 int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out);

@@ -254,13 +254,14 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
             pw[k] = hmul(pw[k - 1], psi, q);
             ipw[k] = hmul(ipw[k - 1], ipsi, q);
         }
+        // [forward pairs (psi^brv(k), Shoup quotient)][inverse pairs (psi^-brv(k), quotient)]
         uint64_t *t = tw.data() + (size_t)i * 4 * N;
         for (int k = 0; k < N; ++k) {
             const uint64_t e = brv(k, ctx->log_n);
-            t[k] = pw[e];
-            t[N + k] = shoup(pw[e], q);
-            t[2 * N + k] = ipw[e];
-            t[3 * N + k] = shoup(ipw[e], q);
+            t[2 * k] = pw[e];
+            t[2 * k + 1] = shoup(pw[e], q);
+            t[2 * N + 2 * k] = ipw[e];
+            t[2 * N + 2 * k + 1] = shoup(ipw[e], q);
         }
     }
     // FFT tables: [N/4] exp(-2 pi i k/(N/2)), [N/2] exp(-i pi k / N), [N/2] int32 slot positions
@@ -741,6 +742,147 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
         outs[r].scale = ins[0].scale * pm->scale / (double)ctx->primes[level];
     }
     return last_launch();
+}
+
+void he_batch_free(he_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->have_graph) cudaGraphExecDestroy(b->exec);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaFreeHost(b->h_jobs);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_order);
+    cudaFree(b->d_counter);
+    cudaFree(b->mem);
+    delete b;
+}
+
+int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const he_ptmat *const *pms, he_batch **out) {
+    if (!ctx || !out || count < 1 || !plans || !pms) return HE_EINVAL;
+    *out = nullptr;
+    const int level = pms[0] ? pms[0]->level : -1;
+    for (int j = 0; j < count; ++j) {
+        if (!plans[j] || !pms[j] || pms[j]->ctx != ctx) return HE_EINVAL;
+        const he_plan &p = pms[j]->plan;
+        if (p.m != plans[j]->m || p.n != plans[j]->n || p.row_blocks != 1 || p.col_blocks != 1) return HE_EINVAL;
+        if (pms[j]->level != level) return HE_ELEVEL;
+        int rc = ptmat_bind_keys(ctx, const_cast<he_ptmat *>(pms[j]));
+        if (rc != HE_OK) return rc;
+    }
+    he_batch *b = new (std::nothrow) he_batch();
+    if (!b) return HE_ENOMEM;
+    b->ctx = ctx;
+    b->count = count;
+    b->pms.assign(pms, pms + count);
+    const ModUpConst &mu = ctx->modup[level];
+    const int64_t N = ctx->n, nq = level + 1;
+    BatchGeom &g = b->bg;
+    g.ndig = mu.ndig;
+    g.ext = mu.ext;
+    g.nq = (int)nq;
+    g.L = ctx->L;
+    g.LK = ctx->L + ctx->K;
+    g.K = ctx->K;
+    g.level = level;
+    g.d_words = (int64_t)mu.ndig * mu.ext * N;
+    g.coef_words = nq * N;
+    g.acc_words = 2 * (int64_t)mu.ext * N;
+    g.cacc_words = 2 * nq * N;
+    g.sum_words = 2 * nq * N;
+    g.tmp_words = 2 * (int64_t)ctx->K * N + 2 * N;
+    const int64_t per = g.d_words + g.coef_words + g.acc_words + g.cacc_words + g.sum_words + g.tmp_words;
+    bool ok = cudaMalloc(&b->mem, (size_t)per * count * 8) == cudaSuccess && cudaMallocHost(&b->h_jobs, sizeof(MMJob) * count) == cudaSuccess &&
+              cudaMalloc(&b->d_jobs, sizeof(MMJob) * count) == cudaSuccess && cudaMalloc(&b->d_counter, sizeof(unsigned int)) == cudaSuccess;
+    if (!ok) {
+        he_batch_free(b);
+        return HE_ENOMEM;
+    }
+    uint64_t *m = b->mem;
+    g.D = m;
+    m += g.d_words * count;
+    g.coef = m;
+    m += g.coef_words * count;
+    g.acc = m;
+    m += g.acc_words * count;
+    g.cacc = m;
+    m += g.cacc_words * count;
+    g.sum = m;
+    m += g.sum_words * count;
+    g.tmp = m;
+    for (int j = 0; j < count; ++j) {
+        MMJob &jb = b->h_jobs[j];
+        jb.ct = nullptr;
+        jb.out = nullptr;
+        jb.pts = pms[j]->data;
+        jb.keys = pms[j]->d_keys;
+        jb.galois = pms[j]->d_galois;
+        jb.m_prime = (int32_t)pms[j]->plan.m_prime;
+    }
+    // issue order: tile-major, then limb, then jobs by decreasing m', so the CTAs in flight read
+    // the same key tiles (shared by every job) and long jobs start first
+    const int tiles = (int)((N / 2 + mm_tile_pairs() - 1) / mm_tile_pairs());
+    std::vector<int> by_len(count);
+    for (int j = 0; j < count; ++j) by_len[j] = j;
+    std::stable_sort(by_len.begin(), by_len.end(), [&](int a, int c) { return b->h_jobs[a].m_prime > b->h_jobs[c].m_prime; });
+    std::vector<int32_t> order;
+    order.reserve((size_t)tiles * mu.ext * count);
+    for (int t = 0; t < tiles; ++t)
+        for (int u = 0; u < mu.ext; ++u)
+            for (int j : by_len) order.push_back((int32_t)(((int64_t)j * mu.ext + u) * tiles + t));
+    b->n_items = (int)order.size();
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->persistent_ctas = 2 * (sms > 0 ? sms : 1);
+    ok = cudaMalloc(&b->d_order, sizeof(int32_t) * order.size()) == cudaSuccess &&
+         cudaMemcpy(b->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        he_batch_free(b);
+        return HE_ENOMEM;
+    }
+    *out = b;
+    return HE_OK;
+}
+
+int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
+    if (!ctx || !b || b->ctx != ctx || !ins || !outs) return HE_EINVAL;
+    const int level = b->bg.level;
+    for (int j = 0; j < b->count; ++j) {
+        if (!ins[j].data || !outs[j].data) return HE_EINVAL;
+        if (ins[j].level != level) return HE_ELEVEL;
+    }
+    // the previous run's table copy must be done before the host table is rewritten
+    if (b->have_graph && cudaEventSynchronize(b->ev_out) != cudaSuccess) return HE_ECUDA;
+    for (int j = 0; j < b->count; ++j) {
+        b->h_jobs[j].ct = ins[j].data;
+        b->h_jobs[j].out = outs[j].data;
+    }
+    if (cudaEventRecord(b->ev_in, ctx->stream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev_in, 0) != cudaSuccess) return HE_ECUDA;
+    if (!b->have_graph) {
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HE_ECUDA;
+        int rc = launch_matmult_batch(ctx, b, b->stream);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (rc != HE_OK || e != cudaSuccess) return HE_ECUDA;
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return HE_ECUDA;
+        b->have_graph = true;
+    } else {
+        ctx->launches += 7;
+    }
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return HE_ECUDA;
+    if (cudaEventRecord(b->ev_out, b->stream) != cudaSuccess || cudaStreamWaitEvent(ctx->stream, b->ev_out, 0) != cudaSuccess) return HE_ECUDA;
+    for (int j = 0; j < b->count; ++j) {
+        outs[j].level = level - 1;
+        outs[j].scale = ins[j].scale * b->pms[j]->scale / (double)ctx->primes[level];
+    }
+    return HE_OK;
 }
 
 int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out) {

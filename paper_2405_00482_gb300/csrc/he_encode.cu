@@ -86,7 +86,7 @@ __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words
     const uint64_t *c0 = ct + blockIdx.x * ct_words, *c1 = c0 + (int64_t)nl * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = add_mod(c0[k], mont_mul(c1[k], sk_mont[k], q, qinv), q);
     __syncthreads();
-    ntt_inv_smem(s, twiddles(d_tw, 0, 2, logn), twiddles(d_tw, 0, 3, logn), q, logn);
+    ntt_inv_smem(s, twiddles(d_tw, 0, 1, logn), q, logn);
     double *o = coeffs + (int64_t)blockIdx.x * N;
     const uint64_t half = q >> 1;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -221,7 +221,7 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *) {
     const int64_t words = 2 * (int64_t)(level + 1) * ctx->n;
     ctx->launches++;
-    decrypt_kernel<<<count, 512, (size_t)ctx->n * 8, ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
+    decrypt_kernel<<<count, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
                                                                     ctx->log_n);
 }
 

@@ -117,7 +117,7 @@ struct he_ctx {
     std::vector<uint64_t> primes;     // Q then P
     std::vector<ModConst> mc;         // host copy
     ModConst *d_mc;                   // device copy
-    uint64_t *d_tw;                   // [L+K][4][N]: psi_rev, psi_rev_shoup, ipsi_rev, ipsi_rev_shoup
+    uint64_t *d_tw;                   // [L+K][2][N] pairs (w, Shoup(w)): forward psi^brv(k), inverse psi^-brv(k)
     double *d_fft;                    // encode/decode tables: [N/2] twiddles (re, im) and [N] twist
     uint64_t *d_sk_mont;              // [L+K][N] secret in NTT + Montgomery form
     uint64_t *d_sk;                   // [L+K][N] secret in NTT form
@@ -135,6 +135,23 @@ struct he_ctx {
     size_t prof_used;
 };
 
+// one MatMult of a batch (device table entry)
+struct MMJob {
+    const uint64_t *ct;            // input ciphertext [2][level+1][N]
+    uint64_t *out;                 // output ciphertext [2][level][N]
+    const uint64_t *pts;           // [m'][level+1+K][N], Montgomery form
+    const uint64_t *const *keys;   // [m'-1] Galois keys
+    const uint32_t *galois;        // [m'-1]
+    int32_t m_prime;
+};
+
+// shared geometry and per-job scratch strides of a batch
+struct BatchGeom {
+    int32_t ndig, ext, nq, L, LK, K, level;
+    uint64_t *D, *coef, *acc, *cacc, *sum, *tmp;
+    int64_t d_words, coef_words, acc_words, cacc_words, sum_words, tmp_words;
+};
+
 struct he_plan {
     int64_t m, n, slots, mp, np, mb, nb, row_blocks, col_blocks, m_prime, blocks;
 };
@@ -150,6 +167,28 @@ struct he_ptmat {
     std::vector<uint32_t> galois;
     uint32_t *d_galois;      // [m'-1]
 };
+
+// a prepared batch of R = C = 1 MatMults at one level (he_batch_create)
+struct he_batch {
+    he_ctx *ctx;
+    int count;
+    std::vector<const he_ptmat *> pms;
+    MMJob *h_jobs;               // pinned host table, copied to d_jobs at the start of every run
+    MMJob *d_jobs;
+    int32_t *d_order;            // work items (job, limb, tile) in issue order
+    int n_items;
+    unsigned int *d_counter;     // work-queue head
+    int persistent_ctas;
+    BatchGeom bg;
+    uint64_t *mem;               // per-job scratch
+    cudaStream_t stream;         // capture stream
+    cudaEvent_t ev_in, ev_out;
+    cudaGraphExec_t exec;
+    bool have_graph;
+};
+
+int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
+int mm_tile_pairs();
 
 // ------------------------------------------------------------------------------------------
 // launchers (all asynchronous on ctx->stream)

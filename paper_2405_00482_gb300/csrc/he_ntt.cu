@@ -18,7 +18,7 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const uint64_t *src = in + g * in_gs + (int64_t)l * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), twiddles(d_tw, p, 1, logn), q, logn);
+    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
@@ -38,7 +38,7 @@ __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const uint64_t *src = in + g * in_gs + (int64_t)l * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
     __syncthreads();
-    ntt_inv_smem(s, twiddles(d_tw, p, 2, logn), twiddles(d_tw, p, 3, logn), q, logn);
+    ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N;
     const uint64_t ni = mc[p].ninv, nis = mc[p].ninv_shoup;
     for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], ni, nis, q);
@@ -55,7 +55,7 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     const int64_t *src = in + (int64_t)g * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = reduce_signed(src[k], q);
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), twiddles(d_tw, p, 1, logn), q, logn);
+    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + ((int64_t)g * map.n + l) * N;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
@@ -75,7 +75,7 @@ __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__re
 
 }  // namespace
 
-int ntt_threads(int logn) { return logn >= 10 ? 512 : (1 << (logn - 1)); }
+int ntt_threads(int logn) { return logn > HE_NTT_RADIX_LOG ? 1 << (logn - HE_NTT_RADIX_LOG) : 1; }
 
 void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
                             const LimbMap &map, int to_mont) {

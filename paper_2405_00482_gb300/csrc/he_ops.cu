@@ -39,13 +39,12 @@ __global__ void automorph_kernel(const uint64_t *__restrict__ in, uint64_t *__re
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) out[base + k] = in[base + automorph_src(k, g, logn)];
 }
 
-// ModUp: CTA (d, u).  Digit-own limbs are copied from the NTT-form input; the others are
-// converted from the coefficient-form digit limbs and transformed.
-__global__ void modup_kernel(const uint64_t *__restrict__ c1_ntt, const uint64_t *__restrict__ c1_coef, uint64_t *D, ModUpConst mu,
-                             const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
-    extern __shared__ uint64_t s[];
+// ModUp body for CTA (d, u).  Digit-own limbs are copied from the NTT-form input; the
+// others are converted from the coefficient-form digit limbs and transformed.
+__device__ __forceinline__ void modup_body(const uint64_t *__restrict__ c1_ntt, const uint64_t *__restrict__ c1_coef, uint64_t *D,
+                                           const ModUpConst &mu, int d, int u, uint64_t *s, const uint64_t *__restrict__ d_tw,
+                                           const ModConst *__restrict__ mc, int logn) {
     const int N = 1 << logn;
-    const int d = blockIdx.x / mu.ext, u = blockIdx.x % mu.ext;
     const int lo = d * mu.alpha;
     const int hi = lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq;
     const int p = mu.ext_prime[u];
@@ -66,8 +65,14 @@ __global__ void modup_kernel(const uint64_t *__restrict__ c1_ntt, const uint64_t
         s[k] = acc;
     }
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), twiddles(d_tw, p, 1, logn), t, logn);
+    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), t, logn);
     for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
+}
+
+__global__ void modup_kernel(const uint64_t *__restrict__ c1_ntt, const uint64_t *__restrict__ c1_coef, uint64_t *D, ModUpConst mu,
+                             const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    modup_body(c1_ntt, c1_coef, D, mu, blockIdx.x / mu.ext, blockIdx.x % mu.ext, s, d_tw, mc, logn);
 }
 
 // u_c[u][k] = sum_d D[d][u][src(k)] * keyM[d][c][kl(u)][k], REDC in groups of at most 8 terms
@@ -96,14 +101,12 @@ __global__ void ks_inner_kernel(const uint64_t *__restrict__ D, int ndig, int ex
     }
 }
 
-// ModDown epilogue: CTA (c, j).  conv = Conv_{P->q_j}(x_P coefficient form) -> NTT ->
-// out = addend + (x_j - conv) P^-1.
-__global__ void moddown_kernel(const uint64_t *__restrict__ x, int ext, const uint64_t *__restrict__ xp_coef, ModDownConst md,
-                               const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *out,
-                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
-    extern __shared__ uint64_t s[];
+// ModDown body for CTA (c, j): conv = Conv_{P->q_j}(x_P, coefficient form) -> NTT ->
+// out = add_c + (x_j - conv) P^-1.
+__device__ __forceinline__ void moddown_body(const uint64_t *__restrict__ x, int ext, const uint64_t *__restrict__ xp_coef,
+                                             const ModDownConst &md, const uint64_t *__restrict__ ad, uint64_t *out, int c, int j,
+                                             uint64_t *s, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
     const int N = 1 << logn;
-    const int c = blockIdx.x / md.nq, j = blockIdx.x % md.nq;
     const int pj = md.q_prime[j];
     const uint64_t q = mc[pj].q;
     const uint64_t *xp = xp_coef + (int64_t)c * md.K * N;
@@ -117,9 +120,8 @@ __global__ void moddown_kernel(const uint64_t *__restrict__ x, int ext, const ui
         s[k] = acc;
     }
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, pj, 0, logn), twiddles(d_tw, pj, 1, logn), q, logn);
+    ntt_fwd_smem(s, twiddles(d_tw, pj, 0, logn), q, logn);
     const uint64_t *xj = x + ((int64_t)c * ext + j) * N;
-    const uint64_t *ad = c == 0 ? add0 : add1;
     uint64_t *o = out + ((int64_t)c * md.nq + j) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
         uint64_t v = mul_shoup(sub_mod(xj[k], s[k], q), md.pinv[j], md.pinv_shoup[j], q);
@@ -128,17 +130,25 @@ __global__ void moddown_kernel(const uint64_t *__restrict__ x, int ext, const ui
     }
 }
 
+__global__ void moddown_kernel(const uint64_t *__restrict__ x, int ext, const uint64_t *__restrict__ xp_coef, ModDownConst md,
+                               const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *out,
+                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int c = blockIdx.x / md.nq, j = blockIdx.x % md.nq;
+    moddown_body(x, ext, xp_coef, md, c == 0 ? add0 : add1, out, c, j, s, d_tw, mc, logn);
+}
+
 struct RescaleConst {
     uint64_t ql, half;
     uint64_t inv[HE_MAX_Q], inv_shoup[HE_MAX_Q];  // q_l^-1 mod q_j
 };
 
-// CTA (c, j), j < level: v = centred(last limb) mod q_j -> NTT -> out = (c_j - v) q_l^-1
-__global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const uint64_t *__restrict__ last_coef, RescaleConst rc,
-                               uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
-    extern __shared__ uint64_t s[];
+// Rescale body for CTA (c, j), j < level: v = centred(last limb) mod q_j -> NTT ->
+// out = (c_j - v) q_l^-1
+__device__ __forceinline__ void rescale_body(const uint64_t *__restrict__ ct, int level, const uint64_t *__restrict__ last_coef,
+                                             const RescaleConst &rc, uint64_t *out, int c, int j, uint64_t *s,
+                                             const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
     const int N = 1 << logn;
-    const int c = blockIdx.x / level, j = blockIdx.x % level;
     const uint64_t q = mc[j].q;
     const uint64_t *lc = last_coef + (int64_t)c * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -148,73 +158,274 @@ __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const
         s[k] = reduce_signed(centred, q);
     }
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, j, 0, logn), twiddles(d_tw, j, 1, logn), q, logn);
+    ntt_fwd_smem(s, twiddles(d_tw, j, 0, logn), q, logn);
     const uint64_t *cj = ct + ((int64_t)c * (level + 1) + j) * N;
     uint64_t *o = out + ((int64_t)c * level + j) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[k], q), rc.inv[j], rc.inv_shoup[j], q);
 }
 
-// The double-hoisted MatMult loop.  Thread (u, k) of the extended basis:
+__global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const uint64_t *__restrict__ last_coef, RescaleConst rc,
+                               uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    rescale_body(ct, level, last_coef, rc, out, blockIdx.x / level, blockIdx.x % level, s, d_tw, mc, logn);
+}
+
+// ---- batch forms: the same bodies over a job table (one job = one MatMult, R = C = 1) ----
+// iNTT of limbs [first, first + count) of component `comp` of the job's buffer `which`
+// (0: input ciphertext, 1: accumulator acc, 2: pre-rescale sum) into scratch.
+__global__ void batch_intt_c1_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, const uint64_t *__restrict__ d_tw,
+                                     const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int j = blockIdx.x / bg.nq, l = blockIdx.x % bg.nq;
+    if (jobs[j].m_prime <= 1) return;
+    const uint64_t q = mc[l].q;
+    const uint64_t *src = jobs[j].ct + ((int64_t)bg.nq + l) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    __syncthreads();
+    ntt_inv_smem(s, twiddles(d_tw, l, 1, logn), q, logn);
+    uint64_t *dst = bg.coef + (int64_t)j * bg.coef_words + (int64_t)l * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[l].ninv, mc[l].ninv_shoup, q);
+}
+
+__global__ void batch_modup_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                   const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int per = mu.ndig * mu.ext;
+    const int j = blockIdx.x / per, rest = blockIdx.x % per;
+    if (jobs[j].m_prime <= 1) return;
+    modup_body(jobs[j].ct + (int64_t)bg.nq * (1 << logn), bg.coef + (int64_t)j * bg.coef_words, bg.D + (int64_t)j * bg.d_words, mu,
+               rest / mu.ext, rest % mu.ext, s, d_tw, mc, logn);
+}
+
+// iNTT of the P limbs of both accumulator components: block (j, c, i) -> tmp_j [c][K][N]
+__global__ void batch_intt_p_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, const uint64_t *__restrict__ d_tw,
+                                    const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int per = 2 * bg.K;
+    const int j = blockIdx.x / per, c = (blockIdx.x % per) / bg.K, i = blockIdx.x % bg.K;
+    const int p = bg.L + i;
+    const uint64_t q = mc[p].q;
+    const uint64_t *src = bg.acc + (int64_t)j * bg.acc_words + ((int64_t)c * bg.ext + bg.nq + i) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    __syncthreads();
+    ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
+    uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)c * bg.K + i) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[p].ninv, mc[p].ninv_shoup, q);
+    (void)jobs;
+}
+
+__global__ void batch_moddown_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                     const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int per = 2 * md.nq;
+    const int j = blockIdx.x / per, c = (blockIdx.x % per) / md.nq, l = blockIdx.x % md.nq;
+    const uint64_t *cacc = bg.cacc + (int64_t)j * bg.cacc_words;
+    moddown_body(bg.acc + (int64_t)j * bg.acc_words, bg.ext, bg.tmp + (int64_t)j * bg.tmp_words, md, cacc + (int64_t)c * md.nq * (1 << logn),
+                 bg.sum + (int64_t)j * bg.sum_words, c, l, s, d_tw, mc, logn);
+    (void)jobs;
+}
+
+// iNTT of the last limb of both sum components -> tmp_j + 2K N
+__global__ void batch_intt_last_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, const uint64_t *__restrict__ d_tw,
+                                       const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int j = blockIdx.x / 2, c = blockIdx.x % 2;
+    const int p = bg.level;
+    const uint64_t q = mc[p].q;
+    const uint64_t *src = bg.sum + (int64_t)j * bg.sum_words + ((int64_t)c * bg.nq + bg.level) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    __syncthreads();
+    ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
+    uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)2 * bg.K + c) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[p].ninv, mc[p].ninv_shoup, q);
+    (void)jobs;
+}
+
+__global__ void batch_rescale_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, RescaleConst rc, const uint64_t *__restrict__ d_tw,
+                                     const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int per = 2 * bg.level;
+    const int j = blockIdx.x / per, c = (blockIdx.x % per) / bg.level, l = blockIdx.x % bg.level;
+    rescale_body(bg.sum + (int64_t)j * bg.sum_words, bg.level, bg.tmp + (int64_t)j * bg.tmp_words + (int64_t)2 * bg.K * (1 << logn), rc,
+                 jobs[j].out, c, l, s, d_tw, mc, logn);
+}
+
+// The double-hoisted MatMult loop.  For every coefficient k of extended limb u:
 //   acc_c[u][k]  = sum_{i>=1} ptM_i[u][k] * redc(sum_d D[d][u][src_i(k)] keyM_i[d][c][kl(u)][k])
 //   cacc_0[u][k] = ptM_0 * c0[u][k] + sum_{i>=1} ptM_i[u][k] * c0[u][src_i(k)]   (u in Q_level)
 //   cacc_1[u][k] = ptM_0 * c1[u][k]
-__global__ void matmult_loop_kernel(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
-                                    const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime,
-                                    int ndig, int ext, int nq, int L, int LK, LimbMap emap, uint64_t *acc, uint64_t *cacc,
-                                    int accumulate, const ModConst *__restrict__ mc, int logn) {
+// Thread layout: a block covers MM_PAIRS coefficient pairs of one limb (blockIdx.y) and splits
+// the rotations i = 1..m'-1 into MM_GROUPS interleaved groups, one per warp group; the group
+// sums meet in shared memory.  A pair (k, k+1), k even, gathers the aligned pair
+// (src, src ^ 1) of each digit, so every load is 16 bytes.  Products are accumulated in 128
+// bits and reduced once per 8 terms (8 q^2 < q 2^64 for q < 2^61).
+#define MM_PAIRS 64
+#define MM_GROUPS 4
+
+struct Acc2 {
+    u128 v[2];
+};
+
+__device__ __forceinline__ uint64_t fold(u128 t, uint64_t q, uint64_t qinv) { return redc128(t, q, qinv); }
+
+// One tile: MM_PAIRS coefficient pairs starting at pair index `pair0` of extended limb u.
+// Every thread of the block calls it (it synchronises once).
+template <int NDIG>
+__device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
+                                        const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime,
+                                        int ndig_rt, int ext, int nq, int L, int LK, int u, int p, int pair0, uint64_t *acc, uint64_t *cacc,
+                                        int accumulate, const ModConst *__restrict__ mc, int logn,
+                                        uint64_t (*red)[3][2][MM_PAIRS]) {
     const int N = 1 << logn;
-    const int u = blockIdx.y;
-    const int p = emap.prime[u];
+    const int ndig = NDIG > 0 ? NDIG : ndig_rt;
     const int kl = u < nq ? u : L + (u - nq);
     const uint64_t q = mc[p].q, qinv = mc[p].qinv;
     const bool inq = u < nq;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
-        uint64_t a0 = 0, a1 = 0, cc0 = 0, cc1 = 0;
-        const uint64_t pt0 = pts[(int64_t)u * N + k];
-        if (inq) {
-            cc0 = mont_mul(ct[(int64_t)u * N + k], pt0, q, qinv);
-            cc1 = mont_mul(ct[((int64_t)nq + u) * N + k], pt0, q, qinv);
-        }
-        for (int i = 1; i < m_prime; ++i) {
-            const uint32_t src = automorph_src(k, galois[i - 1], logn);
+    const int lane = threadIdx.x % MM_PAIRS, grp = threadIdx.x / MM_PAIRS;
+    const int k = 2 * (pair0 + lane);
+
+    uint64_t r0[2] = {0, 0}, r1[2] = {0, 0}, rc[2] = {0, 0};
+    if (k < N) {
+        u128 t0[2] = {0, 0}, t1[2] = {0, 0}, tc[2] = {0, 0};
+        int pending = 0;
+        for (int i = 1 + grp; i < m_prime; i += MM_GROUPS) {
+            const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
+            const int sp = src & ~1u, sw = src & 1;
             const uint64_t *key = keys[i - 1];
-            u128 t0 = 0, t1 = 0;
-            uint64_t u0 = 0, u1 = 0;
-            for (int d = 0; d < ndig; ++d) {
-                const uint64_t dv = D[((int64_t)d * ext + u) * N + src];
-                t0 += (u128)dv * key[((int64_t)(d * 2 + 0) * LK + kl) * N + k];
-                t1 += (u128)dv * key[((int64_t)(d * 2 + 1) * LK + kl) * N + k];
-                if ((d & 7) == 7) {
-                    u0 = add_mod(u0, redc128(t0, q, qinv), q);
-                    u1 = add_mod(u1, redc128(t1, q, qinv), q);
-                    t0 = t1 = 0;
-                }
+            u128 s0[2] = {0, 0}, s1[2] = {0, 0};
+#pragma unroll
+            for (int d = 0; d < (NDIG > 0 ? NDIG : 8); ++d) {
+                if (NDIG == 0 && d >= ndig) break;
+                const ulonglong2 dv = *reinterpret_cast<const ulonglong2 *>(D + ((int64_t)d * ext + u) * N + sp);
+                const uint64_t dk0 = sw ? dv.y : dv.x, dk1 = sw ? dv.x : dv.y;
+                const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k));
+                const ulonglong2 k1 = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k));
+                s0[0] += (u128)dk0 * k0.x;
+                s0[1] += (u128)dk1 * k0.y;
+                s1[0] += (u128)dk0 * k1.x;
+                s1[1] += (u128)dk1 * k1.y;
             }
-            u0 = add_mod(u0, redc128(t0, q, qinv), q);
-            u1 = add_mod(u1, redc128(t1, q, qinv), q);
-            const uint64_t ptm = pts[((int64_t)i * ext + u) * N + k];
-            a0 = add_mod(a0, mont_mul(u0, ptm, q, qinv), q);
-            a1 = add_mod(a1, mont_mul(u1, ptm, q, qinv), q);
-            if (inq) cc0 = add_mod(cc0, mont_mul(ct[(int64_t)u * N + src], ptm, q, qinv), q);
+            const ulonglong2 pm = __ldg(reinterpret_cast<const ulonglong2 *>(pts + ((int64_t)i * ext + u) * N + k));
+            const uint64_t u00 = fold(s0[0], q, qinv), u01 = fold(s0[1], q, qinv);
+            const uint64_t u10 = fold(s1[0], q, qinv), u11 = fold(s1[1], q, qinv);
+            t0[0] += (u128)u00 * pm.x;
+            t0[1] += (u128)u01 * pm.y;
+            t1[0] += (u128)u10 * pm.x;
+            t1[1] += (u128)u11 * pm.y;
+            if (inq) {
+                const ulonglong2 cv = *reinterpret_cast<const ulonglong2 *>(ct + (int64_t)u * N + sp);
+                tc[0] += (u128)(sw ? cv.y : cv.x) * pm.x;
+                tc[1] += (u128)(sw ? cv.x : cv.y) * pm.y;
+            }
+            if (++pending == 8) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
+                    r1[j] = add_mod(r1[j], fold(t1[j], q, qinv), q);
+                    rc[j] = add_mod(rc[j], fold(tc[j], q, qinv), q);
+                    t0[j] = t1[j] = tc[j] = 0;
+                }
+                pending = 0;
+            }
         }
-        const int64_t ia0 = (int64_t)u * N + k, ia1 = ((int64_t)ext + u) * N + k;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
+            r1[j] = add_mod(r1[j], fold(t1[j], q, qinv), q);
+            rc[j] = add_mod(rc[j], fold(tc[j], q, qinv), q);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        red[grp][0][j][lane] = r0[j];
+        red[grp][1][j][lane] = r1[j];
+        red[grp][2][j][lane] = rc[j];
+    }
+    __syncthreads();
+    if (grp == 0 && k < N) {
+        uint64_t a0[2], a1[2], cc0[2], cc1[2] = {0, 0};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            a0[j] = red[0][0][j][lane];
+            a1[j] = red[0][1][j][lane];
+            cc0[j] = red[0][2][j][lane];
+            for (int g = 1; g < MM_GROUPS; ++g) {
+                a0[j] = add_mod(a0[j], red[g][0][j][lane], q);
+                a1[j] = add_mod(a1[j], red[g][1][j][lane], q);
+                cc0[j] = add_mod(cc0[j], red[g][2][j][lane], q);
+            }
+        }
+        if (inq) {  // i = 0: no rotation
+            const ulonglong2 p0 = __ldg(reinterpret_cast<const ulonglong2 *>(pts + (int64_t)u * N + k));
+            const ulonglong2 c0v = *reinterpret_cast<const ulonglong2 *>(ct + (int64_t)u * N + k);
+            const ulonglong2 c1v = *reinterpret_cast<const ulonglong2 *>(ct + ((int64_t)nq + u) * N + k);
+            cc0[0] = add_mod(cc0[0], mont_mul(c0v.x, p0.x, q, qinv), q);
+            cc0[1] = add_mod(cc0[1], mont_mul(c0v.y, p0.y, q, qinv), q);
+            cc1[0] = mont_mul(c1v.x, p0.x, q, qinv);
+            cc1[1] = mont_mul(c1v.y, p0.y, q, qinv);
+        }
+        ulonglong2 *A0 = reinterpret_cast<ulonglong2 *>(acc + (int64_t)u * N + k);
+        ulonglong2 *A1 = reinterpret_cast<ulonglong2 *>(acc + ((int64_t)ext + u) * N + k);
         if (accumulate) {
-            acc[ia0] = add_mod(acc[ia0], a0, q);
-            acc[ia1] = add_mod(acc[ia1], a1, q);
+            const ulonglong2 o0 = *A0, o1 = *A1;
+            *A0 = make_ulonglong2(add_mod(o0.x, a0[0], q), add_mod(o0.y, a0[1], q));
+            *A1 = make_ulonglong2(add_mod(o1.x, a1[0], q), add_mod(o1.y, a1[1], q));
         } else {
-            acc[ia0] = a0;
-            acc[ia1] = a1;
+            *A0 = make_ulonglong2(a0[0], a0[1]);
+            *A1 = make_ulonglong2(a1[0], a1[1]);
         }
         if (inq) {
-            const int64_t ic0 = (int64_t)u * N + k, ic1 = ((int64_t)nq + u) * N + k;
+            ulonglong2 *C0 = reinterpret_cast<ulonglong2 *>(cacc + (int64_t)u * N + k);
+            ulonglong2 *C1 = reinterpret_cast<ulonglong2 *>(cacc + ((int64_t)nq + u) * N + k);
             if (accumulate) {
-                cacc[ic0] = add_mod(cacc[ic0], cc0, q);
-                cacc[ic1] = add_mod(cacc[ic1], cc1, q);
+                const ulonglong2 o0 = *C0, o1 = *C1;
+                *C0 = make_ulonglong2(add_mod(o0.x, cc0[0], q), add_mod(o0.y, cc0[1], q));
+                *C1 = make_ulonglong2(add_mod(o1.x, cc1[0], q), add_mod(o1.y, cc1[1], q));
             } else {
-                cacc[ic0] = cc0;
-                cacc[ic1] = cc1;
+                *C0 = make_ulonglong2(cc0[0], cc0[1]);
+                *C1 = make_ulonglong2(cc1[0], cc1[1]);
             }
         }
+    }
+}
+
+// single MatMult: block (pair tile, extended limb)
+template <int NDIG>
+__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS) matmult_loop_kernel(
+    const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
+    const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime, int ndig_rt, int ext, int nq, int L,
+    int LK, LimbMap emap, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
+    __shared__ uint64_t red[MM_GROUPS][3][2][MM_PAIRS];
+    mm_tile<NDIG>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, blockIdx.y, emap.prime[blockIdx.y], blockIdx.x * MM_PAIRS, acc,
+                  cacc, accumulate, mc, logn, red);
+}
+
+// batch: persistent CTAs pull (tile, limb, job) items from an ordered queue
+template <int NDIG>
+__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS) matmult_batch_loop_kernel(const MMJob *__restrict__ jobs, const int32_t *__restrict__ order,
+                                                                                 int n_items, unsigned int *counter, BatchGeom bg, LimbMap emap,
+                                                                                 const ModConst *__restrict__ mc, int logn) {
+    __shared__ uint64_t red[MM_GROUPS][3][2][MM_PAIRS];
+    __shared__ int item_s;
+    const int N = 1 << logn;
+    const int tiles = (N / 2 + MM_PAIRS - 1) / MM_PAIRS;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= n_items) return;
+        const int code = order[item];
+        const int j = code / (tiles * bg.ext), rest = code % (tiles * bg.ext);
+        const int u = rest / tiles, tile = rest % tiles;
+        const MMJob &jb = jobs[j];
+        mm_tile<NDIG>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L, bg.LK,
+                      u, emap.prime[u], tile * MM_PAIRS, bg.acc + (int64_t)j * bg.acc_words, bg.cacc + (int64_t)j * bg.cacc_words, 0, mc,
+                      logn, red);
+        __syncthreads();
     }
 }
 
@@ -325,17 +536,12 @@ void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const 
                                                                                               ctx->d_mc, ctx->log_n);
 }
 
-void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, uint64_t *tmp) {
-    LimbMap lmap{};
-    lmap.n = 1;
-    lmap.prime[0] = level;
-    const int64_t N = ctx->n;
-    launch_ntt_inv_strided(ctx, ct + (int64_t)level * N, (int64_t)(level + 1) * N, tmp, N, 2, lmap);
+static RescaleConst make_rescale_const(const he_ctx *ctx, int level) {
     RescaleConst rc{};
     rc.ql = ctx->primes[level];
     rc.half = rc.ql / 2;
     for (int j = 0; j < level; ++j) {
-        uint64_t q = ctx->primes[j];
+        const uint64_t q = ctx->primes[j];
         // q_l^-1 mod q_j by Fermat, host side
         uint64_t base = rc.ql % q, e = q - 2, r = 1;
         while (e) {
@@ -346,6 +552,16 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
         rc.inv[j] = r;
         rc.inv_shoup[j] = (uint64_t)(((u128)r << 64) / q);
     }
+    return rc;
+}
+
+void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, uint64_t *tmp) {
+    LimbMap lmap{};
+    lmap.n = 1;
+    lmap.prime[0] = level;
+    const int64_t N = ctx->n;
+    launch_ntt_inv_strided(ctx, ct + (int64_t)level * N, (int64_t)(level + 1) * N, tmp, N, 2, lmap);
+    const RescaleConst rc = make_rescale_const(ctx, level);
     ctx->launches++;
     rescale_kernel<<<2 * level, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(ct, level, tmp, rc, out, ctx->d_tw, ctx->d_mc,
                                                                                           ctx->log_n);
@@ -362,10 +578,19 @@ void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const ui
     const uint64_t *pts = pm->data + (((int64_t)r * p.col_blocks + c) * p.m_prime) * pm->ext * ctx->n;
     cudaEvent_t *ev = prof_pair(ctx);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
+    const dim3 grid((ctx->n / 2 + MM_PAIRS - 1) / MM_PAIRS, mu.ext);
+    const int m_prime = (int)p.m_prime;
+#define MM_ARGS ct, D, pts, pm->d_keys, pm->d_galois, m_prime, mu.ndig, mu.ext, level + 1, ctx->L, ctx->L + ctx->K, emap, acc, cacc, \
+                accumulate, ctx->d_mc, ctx->log_n
     ctx->launches++;
-    matmult_loop_kernel<<<elem_grid(ctx->n, mu.ext), 256, 0, ctx->stream>>>(ct, D, pts, pm->d_keys, pm->d_galois, (int)p.m_prime, mu.ndig,
-                                                                            mu.ext, level + 1, ctx->L, ctx->L + ctx->K, emap, acc, cacc,
-                                                                            accumulate, ctx->d_mc, ctx->log_n);
+    switch (mu.ndig) {
+        case 1: matmult_loop_kernel<1><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        case 2: matmult_loop_kernel<2><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        case 3: matmult_loop_kernel<3><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        case 4: matmult_loop_kernel<4><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        default: matmult_loop_kernel<0><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+    }
+#undef MM_ARGS
     if (ev) cudaEventRecord(ev[1], ctx->stream);
 }
 
@@ -389,7 +614,48 @@ void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, double 
     lazy_ras_kernel<<<blocks, 256, 0, ctx->stream>>>(p, slots, y);
 }
 
+// Whole batched MatMult on `stream`: ModUp of every input, one persistent loop launch over the
+// (tile, limb, job) queue, ModDown and rescale of every output.  Seven launches and two copies
+// in total, whatever the job count; the caller may capture them in a CUDA graph.
+int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
+    const BatchGeom &bg = b->bg;
+    const int count = b->count, thr = ntt_threads(ctx->log_n), level = bg.level;
+    const size_t smem = (size_t)ctx->n * 8;
+    const ModUpConst &mu = ctx->modup[level];
+    const ModDownConst &md = ctx->moddown[level];
+    const RescaleConst rc = make_rescale_const(ctx, level);
+    LimbMap emap{};
+    emap.n = mu.ext;
+    for (int v = 0; v < mu.ext; ++v) emap.prime[v] = mu.ext_prime[v];
+    if (cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(MMJob) * count, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HE_ECUDA;
+    if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), stream) != cudaSuccess) return HE_ECUDA;
+    batch_intt_c1_kernel<<<count * bg.nq, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    batch_modup_kernel<<<count * mu.ndig * mu.ext, thr, smem, stream>>>(b->d_jobs, bg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    const dim3 pgrid(b->persistent_ctas);
+    switch (bg.ndig) {
+        case 1: matmult_batch_loop_kernel<1><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
+        case 2: matmult_batch_loop_kernel<2><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
+        case 3: matmult_batch_loop_kernel<3><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
+        case 4: matmult_batch_loop_kernel<4><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
+        default: matmult_batch_loop_kernel<0><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
+    }
+    batch_intt_p_kernel<<<count * 2 * bg.K, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    batch_moddown_kernel<<<count * 2 * md.nq, thr, smem, stream>>>(b->d_jobs, bg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    batch_intt_last_kernel<<<count * 2, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    batch_rescale_kernel<<<count * 2 * level, thr, smem, stream>>>(b->d_jobs, bg, rc, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    ctx->launches += 7;
+    return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
+}
+
+int mm_tile_pairs() { return MM_PAIRS; }
+
 void ops_set_smem_limits(int max_bytes) {
+    cudaFuncSetAttribute(batch_intt_c1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(batch_modup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(batch_intt_p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(batch_moddown_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(batch_intt_last_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(batch_rescale_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(modup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(moddown_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(rescale_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);

@@ -67,6 +67,9 @@ _SIGS = {
     "he_encode_vector": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
     "he_matmult_plain_cipher": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(HeCt), ctypes.c_int, ctypes.POINTER(HeCt), ctypes.c_int]),
     "he_matmult_decode": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "he_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+    "he_batch_run": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
+    "he_batch_free": (None, [_vp]),
     "he_ct_export": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_ct_import": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(HeCt)]),
     "he_pt_export": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp]),
@@ -170,6 +173,33 @@ class PtMatrix:
     def __del__(self):
         if getattr(self, "handle", None):
             _lib().he_ptmat_free(self.handle)
+            self.handle = None
+
+
+class Batch:
+    """he_batch: many R = C = 1 MatMults run by one persistent kernel under a CUDA graph."""
+
+    def __init__(self, ctx: "Context", plans: list[Plan], pms: list["PtMatrix"]):
+        self.ctx, self.plans, self.pms = ctx, plans, pms
+        pa = (_vp * len(plans))(*[p.handle.value for p in plans])
+        ma = (_vp * len(pms))(*[m.handle.value for m in pms])
+        h = _vp()
+        _check(_lib().he_batch_create(ctx.handle, len(plans), pa, ma, ctypes.byref(h)), "he_batch_create")
+        self.handle = h
+        self.level = pms[0].level
+
+    def run(self, cts: list[Ciphertext], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
+        outs = outs or [self.ctx.new_ct(self.level - 1) for _ in cts]
+        ia = (HeCt * len(cts))(*[c.c() for c in cts])
+        oa = (HeCt * len(outs))(*[o.c() for o in outs])
+        _check(_lib().he_batch_run(self.ctx.handle, self.handle, ia, oa), "he_batch_run")
+        for o, a in zip(outs, oa):
+            o.level, o.scale = a.level, a.scale
+        return outs
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib().he_batch_free(self.handle)
             self.handle = None
 
 
