@@ -205,6 +205,7 @@ __global__ void batch_intt_p_kernel(const MMJob *__restrict__ jobs, BatchGeom bg
     const int N = 1 << logn;
     const int per = 2 * bg.K;
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / bg.K, i = blockIdx.x % bg.K;
+    if (jobs[j].m_prime == 0) return;  // empty slot
     const int p = bg.L + i;
     const uint64_t q = mc[p].q;
     const uint64_t *src = bg.acc + (int64_t)j * bg.acc_words + ((int64_t)c * bg.ext + bg.nq + i) * N;
@@ -213,7 +214,6 @@ __global__ void batch_intt_p_kernel(const MMJob *__restrict__ jobs, BatchGeom bg
     ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)c * bg.K + i) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[p].ninv, mc[p].ninv_shoup, q);
-    (void)jobs;
 }
 
 __global__ void batch_moddown_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModDownConst md, const uint64_t *__restrict__ d_tw,
@@ -221,10 +221,10 @@ __global__ void batch_moddown_kernel(const MMJob *__restrict__ jobs, BatchGeom b
     extern __shared__ uint64_t s[];
     const int per = 2 * md.nq;
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / md.nq, l = blockIdx.x % md.nq;
+    if (jobs[j].m_prime == 0) return;  // empty slot
     const uint64_t *cacc = bg.cacc + (int64_t)j * bg.cacc_words;
     moddown_body(bg.acc + (int64_t)j * bg.acc_words, bg.ext, bg.tmp + (int64_t)j * bg.tmp_words, md, cacc + (int64_t)c * md.nq * (1 << logn),
                  bg.sum + (int64_t)j * bg.sum_words, c, l, s, d_tw, mc, logn);
-    (void)jobs;
 }
 
 // iNTT of the last limb of both sum components -> tmp_j + 2K N
@@ -233,6 +233,7 @@ __global__ void batch_intt_last_kernel(const MMJob *__restrict__ jobs, BatchGeom
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int j = blockIdx.x / 2, c = blockIdx.x % 2;
+    if (jobs[j].m_prime == 0) return;  // empty slot
     const int p = bg.level;
     const uint64_t q = mc[p].q;
     const uint64_t *src = bg.sum + (int64_t)j * bg.sum_words + ((int64_t)c * bg.nq + bg.level) * N;
@@ -241,7 +242,6 @@ __global__ void batch_intt_last_kernel(const MMJob *__restrict__ jobs, BatchGeom
     ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)2 * bg.K + c) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[p].ninv, mc[p].ninv_shoup, q);
-    (void)jobs;
 }
 
 __global__ void batch_rescale_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, RescaleConst rc, const uint64_t *__restrict__ d_tw,
@@ -249,6 +249,7 @@ __global__ void batch_rescale_kernel(const MMJob *__restrict__ jobs, BatchGeom b
     extern __shared__ uint64_t s[];
     const int per = 2 * bg.level;
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / bg.level, l = blockIdx.x % bg.level;
+    if (jobs[j].m_prime == 0) return;  // empty slot
     rescale_body(bg.sum + (int64_t)j * bg.sum_words, bg.level, bg.tmp + (int64_t)j * bg.tmp_words + (int64_t)2 * bg.K * (1 << logn), rc,
                  jobs[j].out, c, l, s, d_tw, mc, logn);
 }
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS) matmult_batch_loop_kernel
         const int j = code / (tiles * bg.ext), rest = code % (tiles * bg.ext);
         const int u = rest / tiles, tile = rest % tiles;
         const MMJob &jb = jobs[j];
+        if (jb.m_prime == 0) continue;  // empty slot
         mm_tile<NDIG>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L, bg.LK,
                       u, emap.prime[u], tile * MM_PAIRS, bg.acc + (int64_t)j * bg.acc_words, bg.cacc + (int64_t)j * bg.cacc_words, 0, mc,
                       logn, red);
