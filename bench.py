@@ -256,6 +256,8 @@ def run_gpu(args):
     }
     if not args.no_batched:
         line["batched"] = run_batched(ctx, he, inputs, P, args, flush, world, dev)
+    if not args.no_serving and rank == 0:
+        line["serving"] = run_serving(ctx, he, inputs, P, args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -317,6 +319,62 @@ def run_batched(ctx, he, inputs, P, args, flush, world, dev):
             "p99": round(tb[min(len(tb) - 1, int(0.99 * len(tb)))], 4)}, "hoisted_rotations_per_batch": rot,
             "bit_identical_to_plain": bool(same),
             "workload": "64 gradient MatMults X^T[[r]], X b x f ~ N(0,1), b ~ U{128..4096}, f ~ U{16..512} (seed 0), N=8192"}
+
+
+def run_serving(ctx, he, inputs, P, args, dev):
+    """Poisson arrivals (mean 500 requests/s, seed 0) of MatMult requests whose shapes are drawn
+    uniformly from the N = 8192 workloads (gradient 256x1024, forward 1024x256, the 16x64
+    gradient shape, and the 64 uneven batched shapes), matrices and keys resident, admission by
+    a 120 GB budget.  The continuous-batching server and the one-request-per-call server see
+    the same arrival times; a second pass offers requests as fast as they can be submitted."""
+    import numpy as np
+    import torch
+
+    level = P.top
+    rng = np.random.default_rng(0)
+    shapes = [(256, 1024), (1024, 256), (16, 64)] + [(X.shape[1], X.shape[0]) for X, _ in inputs.batched_instances(64, seed=0)]
+    pool = []
+    for i, (m, n) in enumerate(shapes):
+        plan = he.Plan(m, n, P.slots)
+        ctx.keygen(list(range(1, plan.m_prime)))
+        X = torch.from_numpy(rng.normal(size=(m, n))).to(dev)
+        y = torch.from_numpy(rng.uniform(-1, 1, n)).to(dev)
+        pm = ctx.encode_matrix(plan, X, level)
+        ct = ctx.encrypt(ctx.encode_vector(plan, y, P.scale, level)[0], 70000 + i)
+        pool.append((plan, pm, ct))
+    ring = [ctx.new_ct(level - 1) for _ in range(1024)]
+    ctx.synchronize()
+    n_req = args.serve_requests
+    kinds = rng.integers(0, len(pool), size=n_req)
+    gaps = rng.exponential(1.0 / 500.0, size=n_req)
+
+    def serve(plain: bool, paced: bool):
+        server = he.Server(ctx, slots=32, level=level, hbm_budget_bytes=120 << 30, plain=plain)
+        rids = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(n_req):
+            if paced:
+                t_next += gaps[i]
+                while time.perf_counter() < t_next:
+                    pass
+            plan, pm, ct = pool[kinds[i]]
+            rids.append(server.submit(plan, pm, ct, ring[i % len(ring)]))
+            if i >= len(ring) - 1:  # the output ring slot is reused: wait for its previous owner
+                server.wait(rids[i - len(ring) + 1])
+        lats = [server.wait(r) for r in rids]
+        wall = time.perf_counter() - t0
+        _, launches, _ = server.stats()
+        server.close()
+        lat = sorted(lats)
+        return {"throughput": round(n_req / wall, 1), "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
+                "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3), "launches": launches}
+
+    out = {"offered_req_s": 500, "requests": n_req, "budget_gb": 120, "slots": 32,
+           "batched": serve(False, True), "plain": serve(True, True),
+           "saturated_batched": serve(False, False), "saturated_plain": serve(True, False),
+           "workload": "Poisson 500 req/s, shapes uniform over {256x1024, 1024x256, 16x64, 64 uneven batched shapes}, N=8192"}
+    return out
 
 
 def oracle_one_matmult(seed: int = 0):
@@ -400,6 +458,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

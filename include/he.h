@@ -171,6 +171,46 @@ int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const h
 int he_batch_run(he_ctx *ctx, he_batch *batch, const he_ct *ins, he_ct *outs);
 void he_batch_free(he_batch *batch);
 
+/* Serving loop with continuous batching (requests of differing shapes, m, n <= N/2, at one
+ * level).  A scheduler thread admits requests in arrival order while the device bytes they pin
+ * (encoded matrix, input and output ciphertext) fit hbm_budget_bytes, packs admitted requests
+ * into up to `slots` slots of one of two batch lanes and launches that lane's captured batch
+ * graph; requests arriving while a lane runs join the other lane's next launch, so their work
+ * overlaps.  plain != 0 serves one request per he_matmult_plain_cipher call instead (the
+ * one-request-per-launch baseline).  While a server runs it owns the context's stream and
+ * scratch: make no other calls on the context until he_server_free.  Completion is observed
+ * with CUDA events; no kernel waits on another. */
+typedef struct he_server he_server;
+int he_server_create(he_ctx *ctx, int slots, int level, size_t hbm_budget_bytes, int plain, he_server **out);
+/* Queue outs = MatMult(pm, in); in must be ready on the context's stream when this is called.
+ * HE_EBUDGET if the request alone exceeds the budget.  *out's level and scale are set now, its
+ * data when the request completes. */
+int he_server_submit(he_server *s, const he_plan *plan, const he_ptmat *pm, const he_ct *in, he_ct *out, int64_t *request_id);
+/* Block until the request completes (its output is then ready for any stream) or timeout_us
+ * passes (HE_ETIMEOUT); latency_s (optional) = completion - submission, host clock. */
+int he_server_wait(he_server *s, int64_t request_id, int64_t timeout_us, double *latency_s);
+int he_server_stats(he_server *s, int64_t *completed, int64_t *launches, size_t *bytes_in_use);
+/* Finishes every queued request, stops the scheduler and releases the lanes. */
+void he_server_free(he_server *s);
+
+/* VFL-NN forward pass with the encrypted operand diagonally encoded (Alg. 3, Sec. 5.3).
+ * P_A encrypts its activation matrix A (m x n, powers of two, max(m, n) <= N/2) as its
+ * min(m, n) diagonals e_i[j] = A[j mod m, (i + j) mod n] (Eq. 2), each repeated over the N/2
+ * slots (he_cdiag_encode_matrix, then he_encrypt of each).  P_B holds W (n x K, row-major,
+ * device); he_cdiag_encode_weights encodes each column, repeated with period n, at scale
+ * q_level.  he_cdiag_matmult then gives, for every column k,
+ *   outs[k] = Rescale( sum_i RotL(w_k, i) (x) [[e_i]] ),
+ * with the plaintext rotation done as the automorphism X -> X^(5^i) of w_k's plaintext (no
+ * key switching: "eliminate all O4").  After decryption, he_cdiag_decode turns the K slot
+ * vectors (device [K][N/2]) into Z = A W (device, m x K row-major), summing the n/m slot
+ * groups when m < n (lazy rotate-and-sum, Sec. 4.3).  n_ct <= 1024 per call. */
+typedef struct he_cdmat he_cdmat;
+int he_cdiag_encode_weights(he_ctx *ctx, const double *W, int64_t n, int64_t K, int level, he_cdmat **out);
+void he_cdmat_free(he_cdmat *W);
+int he_cdiag_encode_matrix(he_ctx *ctx, const double *A, int64_t m, int64_t n, double scale, int level, he_pt *outs);
+int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct, he_ct *outs);
+int he_cdiag_decode(he_ctx *ctx, int64_t m, int64_t n, int64_t K, const double *slots, double *Z);
+
 /* P_B's side after decryption: lazy rotate-and-sum (Sec. 4.3).  slots: device
  * [row_blocks][N/2] doubles (he_decrypt of each output), y_out: device m doubles. */
 int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out);

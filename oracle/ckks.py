@@ -302,3 +302,25 @@ class Oracle:
         """P_B's side: decrypt every output and apply the lazy rotate-and-sum (Sec. 4.3)."""
         slots = np.stack([self.decrypt_slots(o) for o in outs])
         return layout.lazy_ras(slots, plan)
+
+
+def automorph_pt(o: "Oracle", pt: np.ndarray, g: int) -> np.ndarray:
+    """X -> X^g on every limb of a plaintext (exact: a signed permutation of coefficients)."""
+    out = np.zeros_like(pt)
+    for l in range(pt.shape[0]):
+        lib().or_automorph(o.n, o.primes[l], g, np.ascontiguousarray(pt[l]), out[l])
+    return out
+
+
+def cipher_diag_matmult(o: "Oracle", cts: list, pts_w: list, pt_scale: float) -> list:
+    """Alg. 3, line 3, for every column k: [[z_k]] = Rescale( sum_i phi_{5^i}(p_k) (x) [[e_i]] ),
+    the plaintext rotation RotL(w_k, i) realised as the automorphism X -> X^(5^i) of p_k, so no
+    key switching is needed (Sec. 5.3: "eliminate all O4")."""
+    outs = []
+    for p in pts_w:
+        acc = None
+        for i, ct in enumerate(cts):
+            t = o.mul_plain(ct, automorph_pt(o, p, o.galois(i)), pt_scale)
+            acc = t if acc is None else o.add(acc, t)
+        outs.append(o.rescale(acc))
+    return outs

@@ -164,3 +164,48 @@ def cleartext_model(X: np.ndarray, y: np.ndarray, plan: Plan) -> tuple[np.ndarra
             for i in range(plan.m_prime):
                 acc[r] += E[r, c, i] * rotl(Y[c], i)
     return acc, lazy_ras(acc, plan)
+
+
+# ---- VFL-NN forward: the encrypted operand is the matrix (Sec. 5.3, Alg. 3) ----------------
+
+def cipher_diagonals(A: np.ndarray, slots: int) -> np.ndarray:
+    """Eq. 2 applied to the encrypted activation matrix A (m x n, powers of two, max(m, n) | N'):
+    e_i[j] = A[j mod m, (i + j) mod n] for i < min(m, n), j < max(m, n), each diagonal repeated
+    to fill the N' slots.  Shape [min(m, n)][N']."""
+    m, n = A.shape
+    lo, hi = min(m, n), max(m, n)
+    assert slots % hi == 0
+    out = np.zeros((lo, slots))
+    j = np.arange(slots) % hi
+    for i in range(lo):
+        out[i] = A[j % m, (i + j) % n]
+    return out
+
+
+def weight_slots(w: np.ndarray, slots: int) -> np.ndarray:
+    """A weight column w (length n) repeated with period n over the N' slots."""
+    n = len(w)
+    return w[np.arange(slots) % n]
+
+
+def cipher_diag_model(A: np.ndarray, W: np.ndarray, slots: int) -> np.ndarray:
+    """Cleartext model of Alg. 3's MatMult: output column k has slots
+    sum_i e_i (x) RotL(w_k, i); with m >= n, slot j < m holds (A W)[j, k] and with m < n the
+    n/m groups of m slots are summed after decryption (lazy RaS).  Returns A W (m x K)."""
+    m, n = A.shape
+    E = cipher_diagonals(A, slots)
+    out = np.zeros((m, W.shape[1]))
+    for k in range(W.shape[1]):
+        acc = np.zeros(slots)
+        for i in range(E.shape[0]):
+            acc += E[i] * rotl(weight_slots(W[:, k], slots), i)
+        out[:, k] = cipher_diag_decode(acc, m, n)
+    return out
+
+
+def cipher_diag_decode(slots_k: np.ndarray, m: int, n: int) -> np.ndarray:
+    """Rows of one output column from its decrypted slots: slot j for m >= n; the sum over the
+    n/m groups of m slots for m < n (lazy RaS, Sec. 4.3)."""
+    if m >= n:
+        return slots_k[:m].copy()
+    return sum(slots_k[s * m:(s + 1) * m] for s in range(n // m))

@@ -12,6 +12,7 @@
 void ntt_set_smem_limits(int max_bytes);
 void ops_set_smem_limits(int max_bytes);
 void encode_set_smem_limits(int max_bytes);
+void cdiag_set_smem_limits(int max_bytes);
 
 namespace {
 
@@ -237,10 +238,11 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     }
     he_cdt_table(ctx->cdt);
     const int LK = ctx->L + ctx->K, N = ctx->n;
-    const int smem = N * 8;
+    const int smem = (int)ntt_smem_bytes(ctx->log_n);  // >= the 8N bytes of the FFT kernels
     ntt_set_smem_limits(smem);
     ops_set_smem_limits(smem);
     encode_set_smem_limits(smem);
+    cdiag_set_smem_limits(smem);
 
     // per-prime constants and NTT twiddles
     std::vector<uint64_t> tw((size_t)LK * 4 * N);
@@ -264,20 +266,22 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
             t[2 * N + 2 * k + 1] = shoup(ipw[e], q);
         }
     }
-    // FFT tables: [N/4] exp(-2 pi i k/(N/2)), [N/2] exp(-i pi k / N), [N/2] int32 slot positions
+    // FFT tables as double-float (hi, lo) pairs: [N/4] exp(-2 pi i k/(N/2)), [N/2] exp(-i pi k / N),
+    // then [N/2] int32 slot positions t_j = (5^j mod 2N - 1) / 4
     const int M = N / 2;
-    std::vector<double> fft((size_t)2 * (M / 2) + 2 * M + M / 2 + 1, 0.0);
+    std::vector<float> fft((size_t)4 * (M / 2) + 4 * M + M, 0.0f);
     const double PI = 3.14159265358979323846264338327950288;
-    for (int k = 0; k < M / 2; ++k) {
-        fft[2 * k] = cos(2.0 * PI * k / M);
-        fft[2 * k + 1] = -sin(2.0 * PI * k / M);
-    }
-    double *twist = fft.data() + 2 * (M / 2);
-    for (int k = 0; k < M; ++k) {
-        twist[2 * k] = cos(PI * k / N);
-        twist[2 * k + 1] = -sin(PI * k / N);
-    }
-    int32_t *pos = reinterpret_cast<int32_t *>(twist + 2 * M);
+    auto put = [](float *dst, double re, double im) {
+        const float rh = (float)re, ih = (float)im;
+        dst[0] = rh;
+        dst[1] = (float)(re - (double)rh);
+        dst[2] = ih;
+        dst[3] = (float)(im - (double)ih);
+    };
+    for (int k = 0; k < M / 2; ++k) put(fft.data() + 4 * k, cos(2.0 * PI * k / M), -sin(2.0 * PI * k / M));
+    float *twist = fft.data() + 4 * (M / 2);
+    for (int k = 0; k < M; ++k) put(twist + 4 * k, cos(PI * k / N), -sin(PI * k / N));
+    int32_t *pos = reinterpret_cast<int32_t *>(twist + 4 * M);
     uint64_t e = 1;
     for (int j = 0; j < M; ++j) {
         pos[j] = (int32_t)((e - 1) / 4);
@@ -342,7 +346,7 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
         ctx->moddown.push_back(md);
     }
     bool ok = cuda_ok(cudaMalloc(&ctx->d_mc, sizeof(ModConst) * LK)) && cuda_ok(cudaMalloc(&ctx->d_tw, tw.size() * 8)) &&
-              cuda_ok(cudaMalloc(&ctx->d_fft, fft.size() * 8)) && cuda_ok(cudaMalloc(&ctx->d_sk, (size_t)LK * N * 8)) &&
+              cuda_ok(cudaMalloc(&ctx->d_fft, fft.size() * 4)) && cuda_ok(cudaMalloc(&ctx->d_sk, (size_t)LK * N * 8)) &&
               cuda_ok(cudaMalloc(&ctx->d_sk_mont, (size_t)LK * N * 8));
     if (!ok) {
         he_ctx_destroy(ctx);
@@ -350,7 +354,7 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     }
     ok = cuda_ok(cudaMemcpy(ctx->d_mc, ctx->mc.data(), sizeof(ModConst) * LK, cudaMemcpyHostToDevice)) &&
          cuda_ok(cudaMemcpy(ctx->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice)) &&
-         cuda_ok(cudaMemcpy(ctx->d_fft, fft.data(), fft.size() * 8, cudaMemcpyHostToDevice));
+         cuda_ok(cudaMemcpy(ctx->d_fft, fft.data(), fft.size() * 4, cudaMemcpyHostToDevice));
     // secret key: ternary coefficients -> every prime of Q U P, NTT form (and Montgomery form)
     int64_t *s_int = reinterpret_cast<int64_t *>(ctx_scratch(ctx, N));
     if (!ok || !s_int) {
@@ -685,7 +689,7 @@ int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double s
 }
 
 // resolve the Galois keys of rotation steps 1..m'-1 into a device pointer table, once
-static int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm) {
+int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm) {
     const int64_t steps = pm->plan.m_prime - 1;
     if (steps <= 0 || pm->d_keys) return HE_OK;
     std::vector<const uint64_t *> ptrs(steps);
@@ -759,23 +763,15 @@ void he_batch_free(he_batch *b) {
     delete b;
 }
 
-int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const he_ptmat *const *pms, he_batch **out) {
-    if (!ctx || !out || count < 1 || !plans || !pms) return HE_EINVAL;
-    *out = nullptr;
-    const int level = pms[0] ? pms[0]->level : -1;
-    for (int j = 0; j < count; ++j) {
-        if (!plans[j] || !pms[j] || pms[j]->ctx != ctx) return HE_EINVAL;
-        const he_plan &p = pms[j]->plan;
-        if (p.m != plans[j]->m || p.n != plans[j]->n || p.row_blocks != 1 || p.col_blocks != 1) return HE_EINVAL;
-        if (pms[j]->level != level) return HE_ELEVEL;
-        int rc = ptmat_bind_keys(ctx, const_cast<he_ptmat *>(pms[j]));
-        if (rc != HE_OK) return rc;
-    }
+// Allocate a batch of `count` job slots at `level`.  With pms, the slots hold those MatMults
+// (work order sorted by decreasing m'); without, they start empty (m' = 0, skipped by every
+// kernel) and a scheduler fills them before each launch.
+int batch_create_impl(he_ctx *ctx, int count, int level, const he_ptmat *const *pms, he_batch **out) {
     he_batch *b = new (std::nothrow) he_batch();
     if (!b) return HE_ENOMEM;
     b->ctx = ctx;
     b->count = count;
-    b->pms.assign(pms, pms + count);
+    if (pms) b->pms.assign(pms, pms + count);
     const ModUpConst &mu = ctx->modup[level];
     const int64_t N = ctx->n, nq = level + 1;
     BatchGeom &g = b->bg;
@@ -813,12 +809,13 @@ int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const h
     g.tmp = m;
     for (int j = 0; j < count; ++j) {
         MMJob &jb = b->h_jobs[j];
-        jb.ct = nullptr;
-        jb.out = nullptr;
-        jb.pts = pms[j]->data;
-        jb.keys = pms[j]->d_keys;
-        jb.galois = pms[j]->d_galois;
-        jb.m_prime = (int32_t)pms[j]->plan.m_prime;
+        jb = MMJob{};
+        if (pms) {
+            jb.pts = pms[j]->data;
+            jb.keys = pms[j]->d_keys;
+            jb.galois = pms[j]->d_galois;
+            jb.m_prime = (int32_t)pms[j]->plan.m_prime;
+        }
     }
     // issue order: tile-major, then limb, then jobs by decreasing m', so the CTAs in flight read
     // the same key tiles (shared by every job) and long jobs start first
@@ -849,20 +846,8 @@ int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const h
     return HE_OK;
 }
 
-int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
-    if (!ctx || !b || b->ctx != ctx || !ins || !outs) return HE_EINVAL;
-    const int level = b->bg.level;
-    for (int j = 0; j < b->count; ++j) {
-        if (!ins[j].data || !outs[j].data) return HE_EINVAL;
-        if (ins[j].level != level) return HE_ELEVEL;
-    }
-    // the previous run's table copy must be done before the host table is rewritten
-    if (b->have_graph && cudaEventSynchronize(b->ev_out) != cudaSuccess) return HE_ECUDA;
-    for (int j = 0; j < b->count; ++j) {
-        b->h_jobs[j].ct = ins[j].data;
-        b->h_jobs[j].out = outs[j].data;
-    }
-    if (cudaEventRecord(b->ev_in, ctx->stream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev_in, 0) != cudaSuccess) return HE_ECUDA;
+// Launch the batch (capturing its graph on first use) on its own stream; the job table must be filled.
+int batch_launch(he_ctx *ctx, he_batch *b) {
     if (!b->have_graph) {
         cudaGraph_t graph;
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return HE_ECUDA;
@@ -877,7 +862,41 @@ int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
         ctx->launches += 7;
     }
     if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return HE_ECUDA;
-    if (cudaEventRecord(b->ev_out, b->stream) != cudaSuccess || cudaStreamWaitEvent(ctx->stream, b->ev_out, 0) != cudaSuccess) return HE_ECUDA;
+    return cudaEventRecord(b->ev_out, b->stream) == cudaSuccess ? HE_OK : HE_ECUDA;
+}
+
+int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const he_ptmat *const *pms, he_batch **out) {
+    if (!ctx || !out || count < 1 || !plans || !pms) return HE_EINVAL;
+    *out = nullptr;
+    const int level = pms[0] ? pms[0]->level : -1;
+    for (int j = 0; j < count; ++j) {
+        if (!plans[j] || !pms[j] || pms[j]->ctx != ctx) return HE_EINVAL;
+        const he_plan &p = pms[j]->plan;
+        if (p.m != plans[j]->m || p.n != plans[j]->n || p.row_blocks != 1 || p.col_blocks != 1) return HE_EINVAL;
+        if (pms[j]->level != level) return HE_ELEVEL;
+        int rc = ptmat_bind_keys(ctx, const_cast<he_ptmat *>(pms[j]));
+        if (rc != HE_OK) return rc;
+    }
+    return batch_create_impl(ctx, count, level, pms, out);
+}
+
+int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
+    if (!ctx || !b || b->ctx != ctx || !ins || !outs || b->pms.empty()) return HE_EINVAL;
+    const int level = b->bg.level;
+    for (int j = 0; j < b->count; ++j) {
+        if (!ins[j].data || !outs[j].data) return HE_EINVAL;
+        if (ins[j].level != level) return HE_ELEVEL;
+    }
+    // the previous run's table copy must be done before the host table is rewritten
+    if (b->have_graph && cudaEventSynchronize(b->ev_out) != cudaSuccess) return HE_ECUDA;
+    for (int j = 0; j < b->count; ++j) {
+        b->h_jobs[j].ct = ins[j].data;
+        b->h_jobs[j].out = outs[j].data;
+    }
+    if (cudaEventRecord(b->ev_in, ctx->stream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev_in, 0) != cudaSuccess) return HE_ECUDA;
+    int rc = batch_launch(ctx, b);
+    if (rc != HE_OK) return rc;
+    if (cudaStreamWaitEvent(ctx->stream, b->ev_out, 0) != cudaSuccess) return HE_ECUDA;
     for (int j = 0; j < b->count; ++j) {
         outs[j].level = level - 1;
         outs[j].scale = ins[j].scale * b->pms[j]->scale / (double)ctx->primes[level];

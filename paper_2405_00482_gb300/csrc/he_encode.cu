@@ -10,9 +10,54 @@
 
 namespace {
 
+// ---- double-float arithmetic ----
+// GB300's FP64 pipe issues a small fraction of its FP32 rate, so the FFTs run on pairs of
+// floats (value = hi + lo, ~48-bit significand) built from error-free transforms: Knuth's
+// two-sum for additions and an FMA-based two-product for multiplications.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    const df t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_from(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+// complex value in shared memory: (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ void cmul(float4 v, float4 w, float4 &out) {
+    const df vr{v.x, v.y}, vi{v.z, v.w}, wr{w.x, w.y}, wi{w.z, w.w};
+    const df re = df_add(df_mul(vr, wr), df_neg(df_mul(vi, wi)));
+    const df im = df_add(df_mul(vr, wi), df_mul(vi, wr));
+    out = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
 // iterative radix-2 FFT of M = N/2 complex values in shared memory, input already in
 // bit-reversed order.  tw[k] = exp(-2 pi i k / M) for k < M/2; sign = +1 uses conj(tw).
-__device__ void fft_smem(double2 *a, const double2 *__restrict__ tw, int logm, int sign) {
+__device__ void fft_smem(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
     const int M = 1 << logm;
     for (int lg = 1; lg <= logm; ++lg) {
         const int half = 1 << (lg - 1);
@@ -20,13 +65,15 @@ __device__ void fft_smem(double2 *a, const double2 *__restrict__ tw, int logm, i
         for (int j = threadIdx.x; j < M / 2; j += blockDim.x) {
             const int grp = j >> (lg - 1), pos = j & (half - 1);
             const int i1 = (grp << lg) + pos, i2 = i1 + half;
-            double2 w = tw[pos * stride];
-            if (sign > 0) w.y = -w.y;
-            const double2 u = a[i1], v0 = a[i2];
-            const double2 v = make_double2(__dsub_rn(__dmul_rn(v0.x, w.x), __dmul_rn(v0.y, w.y)),
-                                           __dadd_rn(__dmul_rn(v0.x, w.y), __dmul_rn(v0.y, w.x)));
-            a[i1] = make_double2(__dadd_rn(u.x, v.x), __dadd_rn(u.y, v.y));
-            a[i2] = make_double2(__dsub_rn(u.x, v.x), __dsub_rn(u.y, v.y));
+            float4 w = tw[pos * stride];
+            if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
+            float4 v;
+            cmul(a[i2], w, v);
+            const float4 u = a[i1];
+            const df ur{u.x, u.y}, ui{u.z, u.w}, vr{v.x, v.y}, vi{v.z, v.w};
+            const df s0 = df_add(ur, vr), s1 = df_add(ui, vi), d0 = df_add(ur, df_neg(vr)), d1 = df_add(ui, df_neg(vi));
+            a[i1] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+            a[i2] = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
         }
         __syncthreads();
     }
@@ -34,47 +81,50 @@ __device__ void fft_smem(double2 *a, const double2 *__restrict__ tw, int logm, i
 
 // one CTA per plaintext: slots [count][stride] (first n_slots used) -> coeffs int64 [count][N]
 __global__ void encode_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
-                              const double2 *__restrict__ tw, const double2 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
+                              const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
                               int64_t *out, int logn) {
-    extern __shared__ double2 a[];
+    extern __shared__ float4 a[];
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn;
     const double *z = slots + (int64_t)blockIdx.x * stride;
-    for (int t = threadIdx.x; t < M; t += blockDim.x) a[t] = make_double2(0.0, 0.0);
-    __syncthreads();
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const int t = slot_pos[j];
         const int bt = __brev(t) >> (32 - logm);
-        a[bt] = make_double2(j < n_slots ? z[j] : 0.0, 0.0);
+        const df v = df_from(j < n_slots ? z[j] : 0.0);
+        a[bt] = make_float4(v.hi, v.lo, 0.f, 0.f);
     }
     __syncthreads();
     fft_smem(a, tw, logm, -1);
-    const double f = 2.0 / (double)N;
+    const df f = df_from(2.0 / (double)N * scale);  // exact: a power of two times the scale
     int64_t *o = out + (int64_t)blockIdx.x * N;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        const double2 y = a[k], w = twist[k];  // w = zeta^-k
-        const double re = __dsub_rn(__dmul_rn(y.x, w.x), __dmul_rn(y.y, w.y));
-        const double im = __dadd_rn(__dmul_rn(y.x, w.y), __dmul_rn(y.y, w.x));
-        o[k] = __double2ll_rn(__dmul_rn(__dmul_rn(re, f), scale));
-        o[k + M] = __double2ll_rn(__dmul_rn(__dmul_rn(im, f), scale));
+        float4 c;
+        cmul(a[k], twist[k], c);  // times zeta^-k
+        o[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
+        o[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
     }
 }
 
 // one CTA per polynomial: real coefficients [count][N] -> slot values [count][N/2] / scale
-__global__ void decode_kernel(const double *__restrict__ coeffs, double scale, const double2 *__restrict__ tw,
-                              const double2 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
-    extern __shared__ double2 a[];
+__global__ void decode_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
+                              const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
+    extern __shared__ float4 a[];
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn;
     const double *m = coeffs + (int64_t)blockIdx.x * N;
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        const double2 w = twist[k];  // zeta^-k; use its conjugate zeta^k
-        const double re = m[k], im = m[k + M];
-        const int bk = __brev(k) >> (32 - logm);
-        a[bk] = make_double2(__dadd_rn(__dmul_rn(re, w.x), __dmul_rn(im, w.y)), __dsub_rn(__dmul_rn(im, w.x), __dmul_rn(re, w.y)));
+        const float4 w = twist[k];  // zeta^-k; use its conjugate zeta^k
+        const df re = df_from(m[k]), im = df_from(m[k + M]);
+        float4 c;
+        cmul(make_float4(re.hi, re.lo, im.hi, im.lo), make_float4(w.x, w.y, -w.z, -w.w), c);
+        a[__brev(k) >> (32 - logm)] = c;
     }
     __syncthreads();
     fft_smem(a, tw, logm, +1);
     double *o = out + (int64_t)blockIdx.x * M;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) o[j] = a[slot_pos[j]].x / scale;
+    const double inv = 1.0 / scale;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const float4 v = a[slot_pos[j]];
+        o[j] = df_to(df{v.x, v.y}) * inv;
+    }
 }
 
 // decrypt limb 0: m = c0 + c1 s (NTT), inverse NTT, centred, as doubles.  One CTA per ciphertext.
@@ -84,13 +134,13 @@ __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words
     const int N = 1 << logn;
     const uint64_t q = mc[0].q, qinv = mc[0].qinv;
     const uint64_t *c0 = ct + blockIdx.x * ct_words, *c1 = c0 + (int64_t)nl * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = add_mod(c0[k], mont_mul(c1[k], sk_mont[k], q, qinv), q);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = add_mod(c0[k], mont_mul(c1[k], sk_mont[k], q, qinv), q);
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, 0, 1, logn), q, logn);
     double *o = coeffs + (int64_t)blockIdx.x * N;
     const uint64_t half = q >> 1;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const uint64_t v = mul_shoup(s[k], mc[0].ninv, mc[0].ninv_shoup, q);
+        const uint64_t v = mul_shoup(s[SIDX(k)], mc[0].ninv, mc[0].ninv_shoup, q);
         o[k] = v > half ? -(double)(q - v) : (double)v;
     }
 }
@@ -198,12 +248,13 @@ __global__ void keygen_combine_kernel(const uint64_t *__restrict__ a, const uint
 
 }  // namespace
 
-static size_t fft_smem_bytes(int logn) { return (size_t)8 << logn; }  // N/2 double2
+static size_t fft_smem_bytes(int logn) { return (size_t)8 << logn; }  // N/2 float4
 
+// FFT tables in ctx->d_fft: [N/4] float4 twiddles, [N/2] float4 twist, [N/2] int32 slot positions
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs) {
     if (count == 0) return;
-    const double2 *tw = reinterpret_cast<const double2 *>(ctx->d_fft);
-    const double2 *twist = tw + ctx->n / 4;
+    const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
+    const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
     encode_kernel<<<count, 512, fft_smem_bytes(ctx->log_n), ctx->stream>>>(slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
@@ -211,8 +262,8 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
 
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots) {
     if (count == 0) return;
-    const double2 *tw = reinterpret_cast<const double2 *>(ctx->d_fft);
-    const double2 *twist = tw + ctx->n / 4;
+    const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
+    const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
     decode_kernel<<<count, 512, fft_smem_bytes(ctx->log_n), ctx->stream>>>(coeffs, scale, tw, twist, pos, slots, ctx->log_n);
@@ -221,7 +272,7 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *) {
     const int64_t words = 2 * (int64_t)(level + 1) * ctx->n;
     ctx->launches++;
-    decrypt_kernel<<<count, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
+    decrypt_kernel<<<count, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
                                                                     ctx->log_n);
 }
 

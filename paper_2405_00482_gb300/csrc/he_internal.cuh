@@ -118,7 +118,7 @@ struct he_ctx {
     std::vector<ModConst> mc;         // host copy
     ModConst *d_mc;                   // device copy
     uint64_t *d_tw;                   // [L+K][2][N] pairs (w, Shoup(w)): forward psi^brv(k), inverse psi^-brv(k)
-    double *d_fft;                    // encode/decode tables: [N/2] twiddles (re, im) and [N] twist
+    void *d_fft;                      // encode/decode tables (double-float twiddles, twist, slot positions)
     uint64_t *d_sk_mont;              // [L+K][N] secret in NTT + Montgomery form
     uint64_t *d_sk;                   // [L+K][N] secret in NTT form
     std::map<uint32_t, uint64_t *> keys;  // Galois element -> [dnum][2][L+K][N]
@@ -188,6 +188,12 @@ struct he_batch {
 };
 
 int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
+// defined in he_api.cu (inside its extern "C" block)
+extern "C" {
+int batch_create_impl(he_ctx *ctx, int count, int level, const he_ptmat *const *pms, he_batch **out);
+int batch_launch(he_ctx *ctx, he_batch *b);
+int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm);
+}
 int mm_tile_pairs();
 
 // ------------------------------------------------------------------------------------------
@@ -204,6 +210,8 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
                             const LimbMap &map, int to_mont);
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map);
 int ntt_threads(int logn);
+// dynamic shared memory of a CTA that holds one limb-poly for the NTT (padded layout)
+inline size_t ntt_smem_bytes(int logn) { return ((size_t)1 << logn) * 8 + ((size_t)1 << logn) / 32 * 8; }
 // NTT forward of signed int64 coefficient vectors reduced per limb: in [groups][N] -> out [groups][map.n][N]
 void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int groups, const LimbMap &map, int to_mont);
 // x -> x 2^64 mod q in place

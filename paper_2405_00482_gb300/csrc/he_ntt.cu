@@ -16,15 +16,15 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
     const uint64_t *src = in + g * in_gs + (int64_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
     ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[k], r2, q, qinv);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
     } else {
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[SIDX(k)];
     }
 }
 
@@ -36,12 +36,12 @@ __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
     const uint64_t *src = in + g * in_gs + (int64_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N;
     const uint64_t ni = mc[p].ninv, nis = mc[p].ninv_shoup;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], ni, nis, q);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], ni, nis, q);
 }
 
 // signed int64 coefficients of group g, reduced mod each limb's prime, then forward NTT
@@ -53,15 +53,15 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
     const int64_t *src = in + (int64_t)g * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = reduce_signed(src[k], q);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = reduce_signed(src[k], q);
     __syncthreads();
     ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + ((int64_t)g * map.n + l) * N;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[k], r2, q, qinv);
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
     } else {
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
+        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[SIDX(k)];
     }
 }
 
@@ -81,14 +81,14 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
                             const LimbMap &map, int to_mont) {
     if (groups * map.n == 0) return;
     ctx->launches++;
-    ntt_fwd_kernel<<<groups * map.n, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+    ntt_fwd_kernel<<<groups * map.n, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
                                                                                                ctx->d_mc, ctx->log_n, to_mont);
 }
 
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map) {
     if (groups * map.n == 0) return;
     ctx->launches++;
-    ntt_inv_kernel<<<groups * map.n, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+    ntt_inv_kernel<<<groups * map.n, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
                                                                                                ctx->d_mc, ctx->log_n);
 }
 
@@ -105,7 +105,7 @@ void launch_ntt_inv(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, 
 void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int groups, const LimbMap &map, int to_mont) {
     if (groups * map.n == 0) return;
     ctx->launches++;
-    ntt_from_int64_kernel<<<groups * map.n, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(in, out, map, ctx->d_tw, ctx->d_mc,
+    ntt_from_int64_kernel<<<groups * map.n, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, out, map, ctx->d_tw, ctx->d_mc,
                                                                                                       ctx->log_n, to_mont);
 }
 

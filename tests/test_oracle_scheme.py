@@ -217,3 +217,23 @@ def test_config1_gradient_within_tolerance():
     assert plan.m_prime == 1
     outs = o.matmult(o.encode_matrix(X.T, plan, 1, ext=True), o.encrypt_vector(r, plan, 2.0**20), plan)
     assert np.abs(o.matmult_decode(outs, plan) - X.T @ r).max() < 5e-2
+
+
+@pytest.mark.parametrize("m,n,K", [(32, 8, 2), (8, 32, 2)])
+def test_cipher_diag_matmult_matches_fp64(m, n, K):
+    """Alg. 3 through encryption: the plaintext rotations as automorphisms, no key switching."""
+    o = ckks.Oracle(log_n=6, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=8)
+    rng = np.random.default_rng(m * n)
+    A = rng.uniform(-1, 1, (m, n))
+    W = rng.normal(size=(n, K)) / np.sqrt(n)
+    E = layout.cipher_diagonals(A, o.slots)
+    cts = [o.encrypt(o.encode(E[i], 2.0**40, 2), 2, 2.0**40, nonce=i) for i in range(E.shape[0])]
+    qs = float(o.q[2])
+    pts = [o.encode(layout.weight_slots(W[:, k], o.slots), qs, 2) for k in range(K)]
+    outs = ckks.cipher_diag_matmult(o, cts, pts, qs)
+    res = np.stack([layout.cipher_diag_decode(o.decrypt_slots(c), m, n) for c in outs], 1)
+    assert np.abs(res - A @ W).max() < TOL_2_40
+    # the automorphism of an encoded plaintext is the encoding of the rotated slots (up to rounding)
+    p = pts[0]
+    rot = ckks.automorph_pt(o, p, o.galois(3))
+    assert np.abs(o.decrypt_slots(o.encrypt(rot, 2, qs, 99)) - np.roll(layout.weight_slots(W[:, 0], o.slots), -3)).max() < 1e-6
