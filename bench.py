@@ -254,6 +254,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    line["rotations"] = run_rotations(ctx, he, P, args, flush, world, dev)
     if not args.no_batched:
         line["batched"] = run_batched(ctx, he, inputs, P, args, flush, world, dev)
     if not args.no_serving and rank == 0:
@@ -264,6 +265,41 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_rotations(ctx, he, P, args, flush, world, dev):
+    """O3 (one he_rotate call per rotation) and O4 (he_rotate_hoisted over the 63 steps of the
+    gradient product, one decomposition shared) on a fresh N = 8192 ciphertext, device time."""
+    import torch
+
+    level = P.top
+    ct = ctx.encrypt(ctx.encode(torch.ones(P.slots, dtype=torch.float64, device=dev), P.scale, level), 4242)
+    steps = list(range(1, 64))
+    out = ctx.new_ct(level)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = []
+        for _ in range(reps):
+            flush.add_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    reps = max(args.steps, 3)
+    t_single = max_over_ranks(timed(lambda: [ctx.rotate(ct, s) for s in steps], reps), world, dev)
+    t_hoist = max_over_ranks(timed(lambda: ctx.rotate_hoisted(ct, steps), reps), world, dev)
+    n = len(steps) * reps * world
+    return {"single_per_sec": round(n / t_single, 1), "hoisted_per_sec": round(n / t_hoist, 1), "unit": "rotations/s",
+            "workload": "RotL by 1..63 of one ciphertext, N=8192, Q=[60,40,40], P=[60], dnum=3; O3 = one call per rotation, "
+                        "O4 = one hoisted call for all 63"}
 
 
 def run_batched(ctx, he, inputs, P, args, flush, world, dev):

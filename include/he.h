@@ -210,6 +210,12 @@ void he_cdmat_free(he_cdmat *W);
 int he_cdiag_encode_matrix(he_ctx *ctx, const double *A, int64_t m, int64_t n, double scale, int level, he_pt *outs);
 int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct, he_ct *outs);
 int he_cdiag_decode(he_ctx *ctx, int64_t m, int64_t n, int64_t K, const double *slots, double *Z);
+/* Transposed matrices' diagonal conversion (Sec. 5.3, Eq. 5): from the min(m, n) diagonal
+ * ciphertexts of A (m x n), the diagonal ciphertexts of A^T (n x m) for the backward pass
+ * (Alg. 4), each a rotation outs[i] = RotL(cts[k], r) with k = (-i) mod min(m, n) and r = i
+ * when m >= n, r = (-k) mod n when m < n (the printed RotR form does not give A^T's diagonals).
+ * Needs the Galois keys of those steps (HE_EKEY otherwise); outs must not alias cts. */
+int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_ct *outs);
 
 /* P_B's side after decryption: lazy rotate-and-sum (Sec. 4.3).  slots: device
  * [row_blocks][N/2] doubles (he_decrypt of each output), y_out: device m doubles. */

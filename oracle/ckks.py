@@ -324,3 +324,11 @@ def cipher_diag_matmult(o: "Oracle", cts: list, pts_w: list, pt_scale: float) ->
             acc = t if acc is None else o.add(acc, t)
         outs.append(o.rescale(acc))
     return outs
+
+
+def transpose_diagonals(o: "Oracle", cts: list, m: int, n: int) -> list:
+    """[[A^T]]'s diagonal ciphertexts from [[A]]'s (Eq. 5 as read in layout.transpose_rotations)."""
+    outs = []
+    for k, r in layout.transpose_rotations(m, n):
+        outs.append(o.rotate(cts[k], r) if r else Ciphertext(cts[k].data.copy(), cts[k].level, cts[k].scale))
+    return outs

@@ -209,3 +209,18 @@ def cipher_diag_decode(slots_k: np.ndarray, m: int, n: int) -> np.ndarray:
     if m >= n:
         return slots_k[:m].copy()
     return sum(slots_k[s * m:(s + 1) * m] for s in range(n // m))
+
+
+def transpose_rotations(m: int, n: int) -> list[tuple[int, int]]:
+    """Transposed matrices' diagonal conversion (Sec. 5.3, Eq. 5): the diagonals of A^T are
+    rotations of A's diagonals, e'_i = RotL(e_k, r).  Worked out from Eq. 2 for both operands:
+    k = (-i) mod min(m, n); r = i when m >= n, r = (-k) mod n when m < n (rotation over the
+    period max(m, n) of the repeated diagonals).  The printed form, RotR by max - min + i, does
+    not reproduce A^T's diagonals (checked by brute force in the tests).  Returns [(k, r)]."""
+    lo = min(m, n)
+    out = []
+    for i in range(lo):
+        k = (-i) % lo
+        r = i if m >= n else (-k) % n
+        out.append((k, r))
+    return out

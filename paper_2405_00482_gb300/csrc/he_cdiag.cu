@@ -10,6 +10,8 @@
 // K gathered values of one (coefficient, diagonal) are one contiguous row.
 #include <algorithm>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "he_internal.cuh"
 #include "he_ntt.cuh"
@@ -298,6 +300,34 @@ int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct,
         outs[k].scale = scale;
     }
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
+}
+
+int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_ct *outs) {
+    if (!ctx || !cts || !outs || !pow2(m) || !pow2(n) || std::max(m, n) > ctx->n / 2) return HE_EINVAL;
+    const int64_t lo = std::min(m, n);
+    // e'_i = RotL(e_k, r): k = (-i) mod lo; r = i (m >= n) or (-k) mod n (m < n)
+    std::vector<std::pair<int64_t, int32_t>> kr((size_t)lo);
+    for (int64_t i = 0; i < lo; ++i) {
+        const int64_t k = (lo - i) % lo;
+        const int64_t r = m >= n ? i : (n - k) % n;
+        kr[(size_t)i] = {k, (int32_t)r};
+        if (!cts[k].data || !outs[i].data || outs[i].data == cts[k].data) return HE_EINVAL;
+        if (cts[k].level != cts[0].level) return HE_ELEVEL;
+    }
+    for (int64_t i = 0; i < lo; ++i) {
+        const int64_t k = kr[(size_t)i].first;
+        const int32_t r = kr[(size_t)i].second;
+        if (r == 0) {
+            const size_t words = 2 * (size_t)(cts[k].level + 1) * ctx->n;
+            if (cudaMemcpyAsync(outs[i].data, cts[k].data, words * 8, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) return HE_ECUDA;
+            outs[i].level = cts[k].level;
+            outs[i].scale = cts[k].scale;
+        } else {
+            const int rc = he_rotate(ctx, &cts[k], r, &outs[i]);
+            if (rc != HE_OK) return rc;
+        }
+    }
+    return HE_OK;
 }
 
 int he_cdiag_decode(he_ctx *ctx, int64_t m, int64_t n, int64_t K, const double *slots, double *Z) {

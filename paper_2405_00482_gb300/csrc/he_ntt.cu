@@ -75,7 +75,9 @@ __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__re
 
 }  // namespace
 
-int ntt_threads(int logn) { return logn > HE_NTT_RADIX_LOG ? 1 << (logn - HE_NTT_RADIX_LOG) : 1; }
+// N/16 threads (one radix-16 set each) up to 512; larger rings loop over several sets per thread
+// (the passes use ~128 registers, so 512 threads fill the register file of one SM)
+int ntt_threads(int logn) { return logn > HE_NTT_RADIX_LOG ? (logn - HE_NTT_RADIX_LOG > 9 ? 512 : 1 << (logn - HE_NTT_RADIX_LOG)) : 1; }
 
 void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
                             const LimbMap &map, int to_mont) {

@@ -10,8 +10,8 @@
 // radix-2 butterflies there and writes them back, so a N = 8192 transform makes 4 trips
 // through shared memory instead of 13.  Butterflies are Harvey's lazy form: forward values
 // stay in [0, 4q), inverse values in [0, 2q); products use Shoup's precomputed quotients
-// (twiddle tables hold (w, floor(w 2^64 / q)) pairs).  The block must have N/16 threads
-// (at least 1).
+// (twiddle tables hold (w, floor(w 2^64 / q)) pairs).  Any block size works: each thread loops
+// over the radix-16 sets it owns.
 #pragma once
 #include "he_internal.cuh"
 
@@ -20,8 +20,6 @@
 // Shared-memory position of element k: one pad word per 32 removes the bank conflicts of the
 // strided passes (a CTA needs ntt_smem_words(N) = N + N/32 words).
 #define SIDX(k) ((k) + ((k) >> 5))
-
-__device__ __forceinline__ int ntt_block_threads(int logn) { return logn > HE_NTT_RADIX_LOG ? 1 << (logn - HE_NTT_RADIX_LOG) : 1; }
 
 template <int NB>
 __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn, int s0, bool last) {

@@ -292,34 +292,51 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
     if (k < N) {
         u128 t0[2] = {0, 0}, t1[2] = {0, 0}, tc[2] = {0, 0};
         int pending = 0;
-        for (int i = 1 + grp; i < m_prime; i += MM_GROUPS) {
+        constexpr int ND = NDIG > 0 ? NDIG : 8;
+        // operands of one rotation step; the next step's are loaded while this one is computed
+        ulonglong2 dv[ND], k0[ND], k1[ND], pm, cv;
+        int sw = 0;
+        auto fetch = [&](int i) {
             const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
-            const int sp = src & ~1u, sw = src & 1;
+            const int sp = src & ~1u;
+            sw = src & 1;
             const uint64_t *key = keys[i - 1];
+#pragma unroll
+            for (int d = 0; d < ND; ++d) {
+                if (NDIG == 0 && d >= ndig) break;
+                dv[d] = *reinterpret_cast<const ulonglong2 *>(D + ((int64_t)d * ext + u) * N + sp);
+                k0[d] = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k));
+                k1[d] = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k));
+            }
+            pm = __ldg(reinterpret_cast<const ulonglong2 *>(pts + ((int64_t)i * ext + u) * N + k));
+            if (inq) cv = *reinterpret_cast<const ulonglong2 *>(ct + (int64_t)u * N + sp);
+        };
+        int i = 1 + grp;
+        if (i < m_prime) fetch(i);
+        while (i < m_prime) {
             u128 s0[2] = {0, 0}, s1[2] = {0, 0};
 #pragma unroll
-            for (int d = 0; d < (NDIG > 0 ? NDIG : 8); ++d) {
+            for (int d = 0; d < ND; ++d) {
                 if (NDIG == 0 && d >= ndig) break;
-                const ulonglong2 dv = *reinterpret_cast<const ulonglong2 *>(D + ((int64_t)d * ext + u) * N + sp);
-                const uint64_t dk0 = sw ? dv.y : dv.x, dk1 = sw ? dv.x : dv.y;
-                const ulonglong2 k0 = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k));
-                const ulonglong2 k1 = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k));
-                s0[0] += (u128)dk0 * k0.x;
-                s0[1] += (u128)dk1 * k0.y;
-                s1[0] += (u128)dk0 * k1.x;
-                s1[1] += (u128)dk1 * k1.y;
+                const uint64_t dk0 = sw ? dv[d].y : dv[d].x, dk1 = sw ? dv[d].x : dv[d].y;
+                s0[0] += (u128)dk0 * k0[d].x;
+                s0[1] += (u128)dk1 * k0[d].y;
+                s1[0] += (u128)dk0 * k1[d].x;
+                s1[1] += (u128)dk1 * k1[d].y;
             }
-            const ulonglong2 pm = __ldg(reinterpret_cast<const ulonglong2 *>(pts + ((int64_t)i * ext + u) * N + k));
+            const ulonglong2 pmc = pm;
+            const uint64_t c0a = sw ? cv.y : cv.x, c0b = sw ? cv.x : cv.y;
+            const int next = i + MM_GROUPS;
+            if (next < m_prime) fetch(next);
             const uint64_t u00 = fold(s0[0], q, qinv), u01 = fold(s0[1], q, qinv);
             const uint64_t u10 = fold(s1[0], q, qinv), u11 = fold(s1[1], q, qinv);
-            t0[0] += (u128)u00 * pm.x;
-            t0[1] += (u128)u01 * pm.y;
-            t1[0] += (u128)u10 * pm.x;
-            t1[1] += (u128)u11 * pm.y;
+            t0[0] += (u128)u00 * pmc.x;
+            t0[1] += (u128)u01 * pmc.y;
+            t1[0] += (u128)u10 * pmc.x;
+            t1[1] += (u128)u11 * pmc.y;
             if (inq) {
-                const ulonglong2 cv = *reinterpret_cast<const ulonglong2 *>(ct + (int64_t)u * N + sp);
-                tc[0] += (u128)(sw ? cv.y : cv.x) * pm.x;
-                tc[1] += (u128)(sw ? cv.x : cv.y) * pm.y;
+                tc[0] += (u128)c0a * pmc.x;
+                tc[1] += (u128)c0b * pmc.y;
             }
             if (++pending == 8) {
 #pragma unroll
@@ -331,6 +348,7 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                 }
                 pending = 0;
             }
+            i = next;
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -395,18 +413,19 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
 
 // single MatMult: block (pair tile, extended limb)
 template <int NDIG>
-__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS) matmult_loop_kernel(
+__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS, 2) matmult_loop_kernel(
     const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
     const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime, int ndig_rt, int ext, int nq, int L,
     int LK, LimbMap emap, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
     __shared__ uint64_t red[MM_GROUPS][3][2][MM_PAIRS];
-    mm_tile<NDIG>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, blockIdx.y, emap.prime[blockIdx.y], blockIdx.x * MM_PAIRS, acc,
+    const int u = blockIdx.y;
+    mm_tile<NDIG>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq), blockIdx.x * MM_PAIRS, acc,
                   cacc, accumulate, mc, logn, red);
 }
 
 // batch: persistent CTAs pull (tile, limb, job) items from an ordered queue
 template <int NDIG>
-__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS) matmult_batch_loop_kernel(const MMJob *__restrict__ jobs, const int32_t *__restrict__ order,
+__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS, 2) matmult_batch_loop_kernel(const MMJob *__restrict__ jobs, const int32_t *__restrict__ order,
                                                                                  int n_items, unsigned int *counter, BatchGeom bg, LimbMap emap,
                                                                                  const ModConst *__restrict__ mc, int logn) {
     __shared__ uint64_t red[MM_GROUPS][3][2][MM_PAIRS];
@@ -425,7 +444,7 @@ __global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS) matmult_batch_loop_kernel
         const MMJob &jb = jobs[j];
         if (jb.m_prime == 0) continue;  // empty slot
         mm_tile<NDIG>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L, bg.LK,
-                      u, emap.prime[u], tile * MM_PAIRS, bg.acc + (int64_t)j * bg.acc_words, bg.cacc + (int64_t)j * bg.cacc_words, 0, mc,
+                      u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * MM_PAIRS, bg.acc + (int64_t)j * bg.acc_words, bg.cacc + (int64_t)j * bg.cacc_words, 0, mc,
                       logn, red);
         __syncthreads();
     }

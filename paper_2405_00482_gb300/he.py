@@ -75,6 +75,7 @@ _SIGS = {
     "he_cdiag_encode_matrix": (ctypes.c_int, [_vp, _vp, _i64, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
     "he_cdiag_matmult": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(HeCt), ctypes.c_int, ctypes.POINTER(HeCt)]),
     "he_cdiag_decode": (ctypes.c_int, [_vp, _i64, _i64, _i64, _vp, _vp]),
+    "he_cdiag_transpose": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _i64, _i64, ctypes.POINTER(HeCt)]),
     "he_server_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_server_submit": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(_i64)]),
     "he_server_wait": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(_dbl)]),
@@ -441,6 +442,22 @@ class Context:
         ia = (HeCt * len(cts))(*[c.c() for c in cts])
         oa = (HeCt * len(outs))(*[o.c() for o in outs])
         _check(_lib().he_cdiag_matmult(self.handle, W.handle, ia, len(cts), oa), "he_cdiag_matmult")
+        for o, a in zip(outs, oa):
+            o.level, o.scale = a.level, a.scale
+        return outs
+
+    @staticmethod
+    def cdiag_transpose_steps(m: int, n: int) -> list[int]:
+        """Rotation steps he_cdiag_transpose needs keys for."""
+        lo = min(m, n)
+        steps = [i if m >= n else (-((-i) % lo)) % n for i in range(lo)]
+        return sorted(set(s for s in steps if s))
+
+    def cdiag_transpose(self, cts: list[Ciphertext], m: int, n: int) -> list[Ciphertext]:
+        outs = [self.new_ct(cts[0].level) for _ in range(min(m, n))]
+        ia = (HeCt * len(cts))(*[c.c() for c in cts])
+        oa = (HeCt * len(outs))(*[o.c() for o in outs])
+        _check(_lib().he_cdiag_transpose(self.handle, ia, m, n, oa), "he_cdiag_transpose")
         for o, a in zip(outs, oa):
             o.level, o.scale = a.level, a.scale
         return outs

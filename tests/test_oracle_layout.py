@@ -141,3 +141,17 @@ def test_cipher_diagonal_model_is_exact(m, n, slots):
     # the diagonal e_0 of the Sec. 4.1 example layout (m = 4, n = 2): [A0, B1, C0, D1]
     codes = np.arange(1, 9, dtype=float).reshape(4, 2)
     assert list(layout.cipher_diagonals(codes, 4)[0]) == [1.0, 4.0, 5.0, 8.0]
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (8, 4), (16, 4), (4, 8), (4, 16), (32, 8), (8, 32), (64, 64)])
+def test_transposed_diagonal_conversion(m, n):
+    """The diagonals of A^T are rotations of A's diagonals (Eq. 5 as read: see transpose_rotations);
+    the printed RotR(e_{(min-i) mod min}, max - min + i) fails on these same shapes."""
+    slots = 2 * max(m, n)
+    A = np.arange(m * n, dtype=float).reshape(m, n) + 1
+    E = layout.cipher_diagonals(A, slots)
+    Et = layout.cipher_diagonals(A.T.copy(), slots)
+    lo, hi = min(m, n), max(m, n)
+    for i, (k, r) in enumerate(layout.transpose_rotations(m, n)):
+        assert np.array_equal(layout.rotl(E[k], r), Et[i])
+    assert not all(np.array_equal(np.roll(E[(lo - i) % lo], hi - lo + i), Et[i]) for i in range(lo))

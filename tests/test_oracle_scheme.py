@@ -237,3 +237,24 @@ def test_cipher_diag_matmult_matches_fp64(m, n, K):
     p = pts[0]
     rot = ckks.automorph_pt(o, p, o.galois(3))
     assert np.abs(o.decrypt_slots(o.encrypt(rot, 2, qs, 99)) - np.roll(layout.weight_slots(W[:, 0], o.slots), -3)).max() < 1e-6
+
+
+@pytest.mark.parametrize("m,n", [(32, 8), (8, 32)])
+def test_transpose_then_backward_product(m, n):
+    """VFL-NN backward (Alg. 4): diagonals of [[A^T]] by rotation (Eq. 5), then [[A^T]] D^T."""
+    o = ckks.Oracle(log_n=6, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=9)
+    rng = np.random.default_rng(m + n)
+    A = rng.uniform(-1, 1, (m, n))
+    Dt = rng.normal(size=(m, 2)) / np.sqrt(m)
+    E = layout.cipher_diagonals(A, o.slots)
+    cts = [o.encrypt(o.encode(E[i], 2.0**40, 2), 2, 2.0**40, nonce=i) for i in range(E.shape[0])]
+    o.gen_rotation_keys([r for _, r in layout.transpose_rotations(m, n) if r])
+    tcts = ckks.transpose_diagonals(o, cts, m, n)
+    Et = layout.cipher_diagonals(A.T.copy(), o.slots)
+    for i, c in enumerate(tcts):
+        assert np.abs(o.decrypt_slots(c) - Et[i]).max() < 1e-8
+    qs = float(o.q[2])
+    pts = [o.encode(layout.weight_slots(Dt[:, k], o.slots), qs, 2) for k in range(2)]
+    outs = ckks.cipher_diag_matmult(o, tcts, pts, qs)
+    res = np.stack([layout.cipher_diag_decode(o.decrypt_slots(c), n, m) for c in outs], 1)
+    assert np.abs(res - A.T @ Dt).max() < TOL_2_40
