@@ -159,6 +159,22 @@ int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double s
 int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in,
                             he_ct *outs, int n_out);
 
+/* he_matmult_plain_cipher without any memory allocation.  The paper has no counterpart: this
+ * is a deployment variant of the same computation.  It is for callers that cannot let the
+ * library call cudaMalloc or cudaFree: applications whose device memory belongs to their own
+ * allocator and budget, and loops that must not pay, inside a call, the device-wide wait that
+ * cudaFree implies.  Same arguments and bit-identical results as he_matmult_plain_cipher.
+ * Its temporaries (ModUp digits, accumulators, the Galois-key table) live in one 16 MiB array
+ * of device memory that the library reserves on every GPU it is loaded on, until the process
+ * exits; a product that needs more returns HE_EBUDGET and computes nothing.  The first call on
+ * each device looks up the array's device address (this can load the library's device code),
+ * so make that first call before any stream capture.  Every call uses the same array: calls
+ * that overlap on the GPU (other streams, other contexts, other threads) race and corrupt each
+ * other's results, so serialise them.  Nothing in the array has to start at zero: each call
+ * writes every word before reading it. */
+int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in, he_ct *outs,
+                                    int n_out);
+
 /* Batched form of the hot path for many independent MatMults of uneven shapes (one input
  * and one output ciphertext each, i.e. m, n <= N/2) at one level.  he_batch_create binds the
  * plans, encoded matrices and Galois keys and allocates the batch's scratch; he_batch_run

@@ -232,6 +232,9 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
 void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D,
                          uint64_t *acc /*[2][ext][N]*/, uint64_t *cacc /*[2][level+1][N]*/, int accumulate);
 
+void launch_matmult_loop_with_tables(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D,
+                                     const uint64_t *const *keys, const uint32_t *galois, uint64_t *acc, uint64_t *cacc, int accumulate);
+
 // encoding, sampling, encryption
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs);
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots);

@@ -615,6 +615,32 @@ void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const ui
     if (ev) cudaEventRecord(ev[1], ctx->stream);
 }
 
+// Same launch as launch_matmult_loop, with the Galois-key pointer table and Galois elements
+// supplied by the caller instead of the encoded matrix's own tables.
+void launch_matmult_loop_with_tables(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D,
+                                     const uint64_t *const *keys, const uint32_t *galois, uint64_t *acc, uint64_t *cacc, int accumulate) {
+    const int level = pm->level;
+    const ModUpConst &mu = ctx->modup[level];
+    LimbMap emap{};
+    emap.n = mu.ext;
+    for (int v = 0; v < mu.ext; ++v) emap.prime[v] = mu.ext_prime[v];
+    const he_plan &p = pm->plan;
+    const uint64_t *pts = pm->data + (((int64_t)r * p.col_blocks + c) * p.m_prime) * pm->ext * ctx->n;
+    const dim3 grid((ctx->n / 2 + MM_PAIRS - 1) / MM_PAIRS, mu.ext);
+    const int m_prime = (int)p.m_prime;
+#define MM_ARGS ct, D, pts, keys, galois, m_prime, mu.ndig, mu.ext, level + 1, ctx->L, ctx->L + ctx->K, emap, acc, cacc, accumulate, \
+                ctx->d_mc, ctx->log_n
+    ctx->launches++;
+    switch (mu.ndig) {
+        case 1: matmult_loop_kernel<1><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        case 2: matmult_loop_kernel<2><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        case 3: matmult_loop_kernel<3><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        case 4: matmult_loop_kernel<4><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+        default: matmult_loop_kernel<0><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
+    }
+#undef MM_ARGS
+}
+
 void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots) {
     int64_t total = p.row_blocks * p.col_blocks * p.m_prime * p.slots;
     int blocks = (int)((total + 255) / 256);

@@ -66,6 +66,8 @@ _SIGS = {
     "he_ptmat_free": (None, [_vp]),
     "he_encode_vector": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
     "he_matmult_plain_cipher": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(HeCt), ctypes.c_int, ctypes.POINTER(HeCt), ctypes.c_int]),
+    "he_matmult_plain_cipher_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(HeCt), ctypes.c_int, ctypes.POINTER(HeCt),
+                                                        ctypes.c_int]),
     "he_matmult_decode": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "he_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "he_batch_run": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
@@ -416,6 +418,16 @@ class Context:
         ins = (HeCt * len(cts))(*[c.c() for c in cts])
         oa = (HeCt * len(outs))(*[o.c() for o in outs])
         _check(_lib().he_matmult_plain_cipher(self.handle, plan.handle, pm.handle, ins, len(cts), oa, len(outs)), "he_matmult_plain_cipher")
+        for o, a in zip(outs, oa):
+            o.level, o.scale = a.level, a.scale
+        return outs
+
+    def matmult_noalloc(self, plan: Plan, pm: PtMatrix, cts: list[Ciphertext], outs: list[Ciphertext]) -> list[Ciphertext]:
+        """he_matmult_plain_cipher_noalloc: the library allocates nothing; `outs` must be given."""
+        ins = (HeCt * len(cts))(*[c.c() for c in cts])
+        oa = (HeCt * len(outs))(*[o.c() for o in outs])
+        _check(_lib().he_matmult_plain_cipher_noalloc(self.handle, plan.handle, pm.handle, ins, len(cts), oa, len(outs)),
+               "he_matmult_plain_cipher_noalloc")
         for o, a in zip(outs, oa):
             o.level, o.scale = a.level, a.scale
         return outs
