@@ -224,6 +224,7 @@ def run_gpu(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = loop_kernel_traffic()
     clocks = clk.summary()
     value = whole_job_rate(2 * args.steps, world, total_s)
     rot_per_step = (plan_g.m_prime - 1) + (plan_f.m_prime - 1)
@@ -247,7 +248,7 @@ def run_gpu(args):
         "step_ms": {"p50": round(sorted(times)[len(times) // 2], 4), "p99": round(sorted(times)[min(len(times) - 1, int(0.99 * len(times)))], 4)},
         "max_abs_err": err,
         "roofline": {"kernel": "matmult_loop_kernel", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "alg_bytes_per_launch": alg_bytes,
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                      "launch_ms": round(per_launch_ms, 5), "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
         "e2e": {"value": round(whole_job_rate(2 * args.steps, world, e2e_s), 2), "unit": "MatMult/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -411,6 +412,20 @@ def run_serving(ctx, he, inputs, P, args, dev):
            "saturated_batched": serve(False, False), "saturated_plain": serve(True, False),
            "workload": "Poisson 500 req/s, shapes uniform over {256x1024, 1024x256, 16x64, 64 uneven batched shapes}, N=8192"}
     return out
+
+
+def loop_kernel_traffic():
+    """DRAM bytes per launch of the loop kernel from the committed ncu capture, if the kernel's
+    source is unchanged since the capture (sha256 of he_ops.cu), else None."""
+    import hashlib
+
+    rec_path = os.path.join(ROOT, "profiles", "loop_kernel_traffic.json")
+    try:
+        rec = json.load(open(rec_path))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
+        return None
+    return rec["dram_bytes_per_launch"] if hashlib.sha256(src).hexdigest() == rec["source_sha256"] else None
 
 
 def oracle_one_matmult(seed: int = 0):
