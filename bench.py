@@ -253,6 +253,8 @@ def run_gpu(args):
         "e2e": {"value": round(whole_job_rate(2 * args.steps, world, e2e_s), 2), "unit": "MatMult/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "autotune": {"plain_gradient": pm_g.tuning(), "plain_forward": pm_f.tuning(),
+                     "variants": "loop kernel (coefficients per thread, rotation groups): 0 (2,4), 1 (1,4), 2 (1,8), 3 (2,8)"},
         "clocks": clocks,
     }
     line["rotations"] = run_rotations(ctx, he, P, args, flush, world, dev)
@@ -354,7 +356,7 @@ def run_batched(ctx, he, inputs, P, args, flush, world, dev):
             "plain_same_jobs": round(whole_job_rate(64 * args.steps, world, sp), 1), "speedup_vs_plain": round(sp / sb, 3),
             "rotations_per_sec": round(rot * args.steps * world / sb, 1), "batch_ms": {"p50": round(tb[len(tb) // 2], 4),
             "p99": round(tb[min(len(tb) - 1, int(0.99 * len(tb)))], 4)}, "hoisted_rotations_per_batch": rot,
-            "bit_identical_to_plain": bool(same),
+            "bit_identical_to_plain": bool(same), "autotune": batch.tuning(),
             "workload": "64 gradient MatMults X^T[[r]], X b x f ~ N(0,1), b ~ U{128..4096}, f ~ U{16..512} (seed 0), N=8192"}
 
 

@@ -187,6 +187,15 @@ int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const h
 int he_batch_run(he_ctx *ctx, he_batch *batch, const he_ct *ins, he_ct *outs);
 void he_batch_free(he_batch *batch);
 
+/* Autotuning of the key-switch / multiply-accumulate loop kernel.  Its variants differ in
+ * coefficients per thread (1 or 2) and rotation groups per block (4 or 8) and give identical
+ * results; the first he_matmult_plain_cipher call with an encoded matrix, and the first
+ * he_batch_run of a batch, time each variant once (synchronising the stream) and keep the
+ * fastest.  These report the choice (variant 0..3, or -1 before the first call) and the timed
+ * milliseconds of the four variants (ms4 may be NULL). */
+int he_ptmat_tuning(const he_ptmat *pm, int *variant, float *ms4);
+int he_batch_tuning(const he_batch *batch, int *variant, float *ms4);
+
 /* Serving loop with continuous batching (requests of differing shapes, m, n <= N/2, at one
  * level).  A scheduler thread admits requests in arrival order while the device bytes they pin
  * (encoded matrix, input and output ciphertext) fit hbm_budget_bytes, packs admitted requests

@@ -733,6 +733,14 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
     uint64_t *D = s, *coef = D + wD, *acc = coef + wc, *cacc = acc + wa, *sum = cacc + wcc, *tmp = sum + wsum;
     if (rot)
         for (size_t c = 0; c < C; ++c) launch_modup(ctx, ins[c].data + nl * N, level, D + c * mu.ndig * ext * N, coef);
+    if (pm->variant < 0) {
+        if (rot) {
+            rc = tune_matmult_loop(ctx, pm, ins[0].data, D, acc, cacc);
+            if (rc != HE_OK) return rc;
+        } else {
+            pm->variant = 0;
+        }
+    }
     for (int r = 0; r < n_out; ++r) {
         for (size_t c = 0; c < C; ++c)
             launch_matmult_loop(ctx, pm, r, (int)c, ins[c].data, rot ? D + c * mu.ndig * ext * N : nullptr, acc, cacc, c > 0);
@@ -757,7 +765,7 @@ void he_batch_free(he_batch *b) {
     if (b->stream) cudaStreamDestroy(b->stream);
     cudaFreeHost(b->h_jobs);
     cudaFree(b->d_jobs);
-    cudaFree(b->d_order);
+    for (int v = 0; v < 4; ++v) cudaFree(b->d_order_v[v]);
     cudaFree(b->d_counter);
     cudaFree(b->mem);
     delete b;
@@ -817,25 +825,32 @@ int batch_create_impl(he_ctx *ctx, int count, int level, const he_ptmat *const *
             jb.m_prime = (int32_t)pms[j]->plan.m_prime;
         }
     }
-    // issue order: tile-major, then limb, then jobs by decreasing m', so the CTAs in flight read
-    // the same key tiles (shared by every job) and long jobs start first
-    const int tiles = (int)((N / 2 + mm_tile_pairs() - 1) / mm_tile_pairs());
+    // issue order, per loop-kernel variant (tile widths differ): tile-major, then limb, then
+    // jobs by decreasing m', so the CTAs in flight read the same key tiles (shared by every job)
+    // and long jobs start first
     std::vector<int> by_len(count);
     for (int j = 0; j < count; ++j) by_len[j] = j;
     std::stable_sort(by_len.begin(), by_len.end(), [&](int a, int c) { return b->h_jobs[a].m_prime > b->h_jobs[c].m_prime; });
-    std::vector<int32_t> order;
-    order.reserve((size_t)tiles * mu.ext * count);
-    for (int t = 0; t < tiles; ++t)
-        for (int u = 0; u < mu.ext; ++u)
-            for (int j : by_len) order.push_back((int32_t)(((int64_t)j * mu.ext + u) * tiles + t));
-    b->n_items = (int)order.size();
+    for (int v = 0; v < mm_variant_count(); ++v) {
+        const int tiles = (int)((N + mm_variant_tile(v) - 1) / mm_variant_tile(v));
+        std::vector<int32_t> order;
+        order.reserve((size_t)tiles * mu.ext * count);
+        for (int t = 0; t < tiles; ++t)
+            for (int u = 0; u < mu.ext; ++u)
+                for (int j : by_len) order.push_back((int32_t)(((int64_t)j * mu.ext + u) * tiles + t));
+        b->n_items_v[v] = (int)order.size();
+        if (cudaMalloc(&b->d_order_v[v], sizeof(int32_t) * order.size()) != cudaSuccess ||
+            cudaMemcpy(b->d_order_v[v], order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            he_batch_free(b);
+            return HE_ENOMEM;
+        }
+    }
+    b->variant = pms ? -1 : ctx->batch_variant;
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     b->persistent_ctas = 2 * (sms > 0 ? sms : 1);
-    ok = cudaMalloc(&b->d_order, sizeof(int32_t) * order.size()) == cudaSuccess &&
-         cudaMemcpy(b->d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
+    ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -894,6 +909,33 @@ int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
         b->h_jobs[j].out = outs[j].data;
     }
     if (cudaEventRecord(b->ev_in, ctx->stream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev_in, 0) != cudaSuccess) return HE_ECUDA;
+    if (b->variant < 0) {
+        // first run: time the whole batch once per loop-kernel variant (same results), keep the fastest
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HE_ECUDA;
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int v = 0; v < mm_variant_count(); ++v) {
+            b->variant = v;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, b->stream);
+                if (launch_matmult_batch(ctx, b, b->stream) != HE_OK) break;
+                cudaEventRecord(e1, b->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            b->tune_ms[v] = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->variant = best;
+        ctx->batch_variant = best;
+    }
     int rc = batch_launch(ctx, b);
     if (rc != HE_OK) return rc;
     if (cudaStreamWaitEvent(ctx->stream, b->ev_out, 0) != cudaSuccess) return HE_ECUDA;
@@ -901,6 +943,22 @@ int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
         outs[j].level = level - 1;
         outs[j].scale = ins[j].scale * b->pms[j]->scale / (double)ctx->primes[level];
     }
+    return HE_OK;
+}
+
+int he_ptmat_tuning(const he_ptmat *pm, int *variant, float *ms4) {
+    if (!pm || !variant) return HE_EINVAL;
+    *variant = pm->variant;
+    if (ms4)
+        for (int v = 0; v < 4; ++v) ms4[v] = pm->tune_ms[v];
+    return HE_OK;
+}
+
+int he_batch_tuning(const he_batch *b, int *variant, float *ms4) {
+    if (!b || !variant) return HE_EINVAL;
+    *variant = b->variant;
+    if (ms4)
+        for (int v = 0; v < 4; ++v) ms4[v] = b->tune_ms[v];
     return HE_OK;
 }
 

@@ -128,6 +128,7 @@ struct he_ctx {
     // scratch (grown on demand, reused across calls on this context's stream)
     uint64_t *scratch;
     size_t scratch_words;
+    int batch_variant = 0;            // last variant a batch tuned to (used by serving lanes)
     // kernels launched so far, and CUDA-event timing of the MatMult loop kernel when enabled
     int64_t launches;
     bool prof_on;
@@ -166,6 +167,8 @@ struct he_ptmat {
     const uint64_t **d_keys; // device array [m'-1] of Galois key pointers (filled at first use)
     std::vector<uint32_t> galois;
     uint32_t *d_galois;      // [m'-1]
+    int variant = -1;        // loop-kernel variant chosen by timing (-1: not yet tuned)
+    float tune_ms[8] = {};
 };
 
 // a prepared batch of R = C = 1 MatMults at one level (he_batch_create)
@@ -175,8 +178,10 @@ struct he_batch {
     std::vector<const he_ptmat *> pms;
     MMJob *h_jobs;               // pinned host table, copied to d_jobs at the start of every run
     MMJob *d_jobs;
-    int32_t *d_order;            // work items (job, limb, tile) in issue order
-    int n_items;
+    int32_t *d_order_v[4];       // work items (job, limb, tile) in issue order, per loop-kernel variant
+    int n_items_v[4];
+    int variant = -1;            // chosen by timing on the first run (-1: not yet)
+    float tune_ms[4] = {};
     unsigned int *d_counter;     // work-queue head
     int persistent_ctas;
     BatchGeom bg;
@@ -188,13 +193,34 @@ struct he_batch {
 };
 
 int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
+int mm_variant_count();
+int mm_variant_tile(int v);  // coefficients per tile of loop-kernel variant v
+int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc);
 // defined in he_api.cu (inside its extern "C" block)
 extern "C" {
 int batch_create_impl(he_ctx *ctx, int count, int level, const he_ptmat *const *pms, he_batch **out);
 int batch_launch(he_ctx *ctx, he_batch *b);
 int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm);
 }
-int mm_tile_pairs();
+
+// Launch `kernel` with thread-block clusters of HE_NTT_CL_SIZE CTAs along x.
+#define HE_NTT_CL_SIZE 8
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_cluster(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = HE_NTT_CL_SIZE;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // ------------------------------------------------------------------------------------------
 // launchers (all asynchronous on ctx->stream)
@@ -210,6 +236,9 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
                             const LimbMap &map, int to_mont);
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map);
 int ntt_threads(int logn);
+bool use_cluster(int logn, int polys);  // launch in the cluster form (few limb-polys)
+int cl_threads(int logn);
+size_t cl_smem_bytes(int logn);
 // dynamic shared memory of a CTA that holds one limb-poly for the NTT (padded layout)
 inline size_t ntt_smem_bytes(int logn) { return ((size_t)1 << logn) * 8 + ((size_t)1 << logn) / 32 * 8; }
 // NTT forward of signed int64 coefficient vectors reduced per limb: in [groups][N] -> out [groups][map.n][N]

@@ -8,60 +8,69 @@
 
 namespace {
 
+template <bool CL>
 __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
                                const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int to_mont) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
-    const int g = blockIdx.x / map.n, l = blockIdx.x % map.n;
+    int poly, off, len;
+    slice_of<CL>(logn, poly, off, len);
+    const int g = poly / map.n, l = poly % map.n;
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
-    const uint64_t *src = in + g * in_gs + (int64_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), q, logn);
-    uint64_t *dst = out + g * out_gs + (int64_t)l * N;
+    fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
     } else {
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[SIDX(k)];
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
     }
 }
 
+template <bool CL>
 __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
                                const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
-    const int g = blockIdx.x / map.n, l = blockIdx.x % map.n;
+    int poly, off, len;
+    slice_of<CL>(logn, poly, off, len);
+    const int g = poly / map.n, l = poly % map.n;
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
-    const uint64_t *src = in + g * in_gs + (int64_t)l * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
-    ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
-    uint64_t *dst = out + g * out_gs + (int64_t)l * N;
+    inv_any<CL>(s, twiddles(d_tw, p, 1, logn), q, logn);
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
     const uint64_t ni = mc[p].ninv, nis = mc[p].ninv_shoup;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], ni, nis, q);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], ni, nis, q);
 }
 
 // signed int64 coefficients of group g, reduced mod each limb's prime, then forward NTT
+template <bool CL>
 __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *out, LimbMap map, const uint64_t *__restrict__ d_tw,
                                       const ModConst *__restrict__ mc, int logn, int to_mont) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
-    const int g = blockIdx.x / map.n, l = blockIdx.x % map.n;
+    int poly, off, len;
+    slice_of<CL>(logn, poly, off, len);
+    const int g = poly / map.n, l = poly % map.n;
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
-    const int64_t *src = in + (int64_t)g * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = reduce_signed(src[k], q);
+    const int64_t *src = in + (int64_t)g * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = reduce_signed(src[k], q);
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), q, logn);
-    uint64_t *dst = out + ((int64_t)g * map.n + l) * N;
+    fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
+    uint64_t *dst = out + ((int64_t)g * map.n + l) * N + off;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
     } else {
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[SIDX(k)];
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
     }
 }
 
@@ -77,21 +86,38 @@ __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__re
 
 // N/16 threads (one radix-16 set each) up to 512; larger rings loop over several sets per thread
 // (the passes use ~128 registers, so 512 threads fill the register file of one SM)
+// cluster form for launches of at most this many limb-polys (one CTA each would leave most SMs idle)
+#define HE_CL_MAX_POLYS 48
+
+bool use_cluster(int logn, int polys) { return logn >= HE_NTT_CL_MIN_LOGN && polys <= HE_CL_MAX_POLYS; }
+int cl_threads(int logn) { return 1 << (logn - 6); }
+size_t cl_smem_bytes(int logn) { return ntt_smem_bytes(logn - 3); }
+
 int ntt_threads(int logn) { return logn > HE_NTT_RADIX_LOG ? (logn - HE_NTT_RADIX_LOG > 9 ? 512 : 1 << (logn - HE_NTT_RADIX_LOG)) : 1; }
 
 void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
                             const LimbMap &map, int to_mont) {
     if (groups * map.n == 0) return;
     ctx->launches++;
-    ntt_fwd_kernel<<<groups * map.n, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
-                                                                                               ctx->d_mc, ctx->log_n, to_mont);
+    const int polys = groups * map.n;
+    if (use_cluster(ctx->log_n, polys))
+        launch_cluster(ntt_fwd_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out,
+                       out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
+    else
+        ntt_fwd_kernel<false><<<polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+                                                                                                        ctx->d_mc, ctx->log_n, to_mont);
 }
 
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map) {
     if (groups * map.n == 0) return;
     ctx->launches++;
-    ntt_inv_kernel<<<groups * map.n, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
-                                                                                               ctx->d_mc, ctx->log_n);
+    const int polys = groups * map.n;
+    if (use_cluster(ctx->log_n, polys))
+        launch_cluster(ntt_inv_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out,
+                       out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    else
+        ntt_inv_kernel<false><<<polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+                                                                                                        ctx->d_mc, ctx->log_n);
 }
 
 void launch_ntt_fwd(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map) {
@@ -107,8 +133,13 @@ void launch_ntt_inv(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, 
 void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int groups, const LimbMap &map, int to_mont) {
     if (groups * map.n == 0) return;
     ctx->launches++;
-    ntt_from_int64_kernel<<<groups * map.n, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, out, map, ctx->d_tw, ctx->d_mc,
-                                                                                                      ctx->log_n, to_mont);
+    const int polys = groups * map.n;
+    if (use_cluster(ctx->log_n, polys))
+        launch_cluster(ntt_from_int64_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, out, map,
+                       ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
+    else
+        ntt_from_int64_kernel<false><<<polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, out, map, ctx->d_tw,
+                                                                                                               ctx->d_mc, ctx->log_n, to_mont);
 }
 
 void launch_to_mont(he_ctx *ctx, uint64_t *data, int groups, const LimbMap &map) {
@@ -119,7 +150,7 @@ void launch_to_mont(he_ctx *ctx, uint64_t *data, int groups, const LimbMap &map)
 }
 
 void ntt_set_smem_limits(int max_bytes) {
-    cudaFuncSetAttribute(ntt_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_from_int64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_inv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_from_int64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }

@@ -13,7 +13,11 @@
 // (twiddle tables hold (w, floor(w 2^64 / q)) pairs).  Any block size works: each thread loops
 // over the radix-16 sets it owns.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "he_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 #define HE_NTT_RADIX_LOG 4
 
@@ -21,19 +25,24 @@
 // strided passes (a CTA needs ntt_smem_words(N) = N + N/32 words).
 #define SIDX(k) ((k) + ((k) >> 5))
 
+// A pass over sets [set0, set1) of stages s0..s0+NB-1; element x lives at s[SIDX(x - off)].
+// The whole transform in one CTA uses set0 = 0, set1 = N >> NB, off = 0; a cluster member
+// holding the slice [off, off + N/8) uses the sets whose elements fall in its slice.
 template <int NB>
-__device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn, int s0, bool last) {
+__device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn, int s0, bool last,
+                                             int set0 = 0, int set1 = -1, int off = 0) {
     constexpr int E = 1 << NB;
     const int N = 1 << logn;
+    if (set1 < 0) set1 = N >> NB;
     const int lg_t0 = logn - 1 - s0;          // t0 = N / 2^(s0+1)
     const int lg_tl = lg_t0 - (NB - 1);       // stride between a set's elements
     const uint64_t two_q = 2 * q;
-    for (int set = threadIdx.x; set < (N >> NB); set += blockDim.x) {
+    for (int set = set0 + threadIdx.x; set < set1; set += blockDim.x) {
         const int g = set >> lg_tl, low = set & ((1 << lg_tl) - 1);
         const int base = (g << (lg_t0 + 1)) + low;
         uint64_t r[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_tl))];
+        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_tl) - off)];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const int h = E >> (j + 1);
@@ -61,23 +70,25 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__re
             }
         }
 #pragma unroll
-        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_tl))] = r[k];
+        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_tl) - off)] = r[k];
     }
     __syncthreads();
 }
 
 template <int NB>
-__device__ __forceinline__ void ntt_inv_pass(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn, int s0) {
+__device__ __forceinline__ void ntt_inv_pass(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn, int s0, int set0 = 0,
+                                             int set1 = -1, int off = 0) {
     constexpr int E = 1 << NB;
     const int N = 1 << logn;
+    if (set1 < 0) set1 = N >> NB;
     const int lg_t0 = s0;  // t of the pass's first stage
     const uint64_t two_q = 2 * q;
-    for (int set = threadIdx.x; set < (N >> NB); set += blockDim.x) {
+    for (int set = set0 + threadIdx.x; set < set1; set += blockDim.x) {
         const int g = set >> lg_t0, low = set & ((1 << lg_t0) - 1);
         const int base = (g << (lg_t0 + NB)) + low;
         uint64_t r[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_t0))];
+        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_t0) - off)];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const int h = 1 << j;
@@ -96,7 +107,7 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, const ulonglong2 *__re
             }
         }
 #pragma unroll
-        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_t0))] = r[k];
+        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_t0) - off)] = r[k];
     }
     __syncthreads();
 }
@@ -130,6 +141,145 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t *s, const ulonglong2 *__re
         }
         s0 += nb;
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// Cluster form: HE_NTT_CL CTAs (one thread-block cluster) share one limb-poly, CTA `rank`
+// holding the slice [rank N/CL, (rank+1) N/CL) in its shared memory (padded layout, local
+// index x - rank N/CL).  The stages whose butterflies span slices (the first 3 forward, the
+// last 3 inverse) are one radix-8 step through distributed shared memory: element j + c N/CL
+// lives in CTA c at local index j, and each CTA takes 1/CL of the offsets j.  The other stages
+// run on each slice with the radix-8 register passes.  Used for launches of few limb-polys,
+// where one CTA per limb-poly would leave most SMs idle.
+#define HE_NTT_CL HE_NTT_CL_SIZE
+
+template <bool FWD>
+__device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int lg_ns = logn - 3, NS = 1 << lg_ns;
+    const uint64_t two_q = 2 * q;
+    uint64_t *rem[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) rem[c] = cl.map_shared_rank(s, c);
+    const int per = NS >> 3;
+    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
+        uint64_t r[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) r[c] = rem[c][SIDX(j)];
+        if (FWD) {  // stages 0..2: t0 = N/2, elements j + c NS
+#pragma unroll
+            for (int st = 0; st < 3; ++st) {
+                const int h = 8 >> (st + 1), m = 1 << st, lg_2t = logn - st;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if ((c & (2 * h - 1)) < h) {
+                        const int x = j + (c << lg_ns);
+                        const ulonglong2 w = tw[m + (x >> lg_2t)];
+                        uint64_t X = r[c];
+                        X = X >= two_q ? X - two_q : X;
+                        const uint64_t T = mul_shoup_lazy(r[c + h], w.x, w.y, q);
+                        r[c] = X + T;
+                        r[c + h] = X - T + two_q;
+                    }
+                }
+            }
+        } else {  // stages logn-3..logn-1: t = NS, 2NS, 4NS
+#pragma unroll
+            for (int st = 0; st < 3; ++st) {
+                const int h = 1 << st, m = 4 >> st, lg_2t = lg_ns + st + 1;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if ((c & (2 * h - 1)) < h) {
+                        const int x = j + (c << lg_ns);
+                        const ulonglong2 w = tw[m + (x >> lg_2t)];
+                        const uint64_t U = r[c], V = r[c + h];
+                        const uint64_t X = U + V;
+                        r[c] = X >= two_q ? X - two_q : X;
+                        r[c + h] = mul_shoup_lazy(U - V + two_q, w.x, w.y, q);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) rem[c][SIDX(j)] = r[c];
+    }
+}
+
+// forward transform of a slice held by each CTA of the cluster; output canonical, bit-reversed
+// positions [rank N/8, (rank+1) N/8) in this CTA
+__device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int NS = 1 << (logn - 3), off = rank * NS;
+    cl.sync();
+    ntt_cross_step<true>(s, tw, q, logn);
+    cl.sync();
+    int s0 = 3;
+    while (s0 < logn) {
+        const int nb = logn - s0 < 3 ? logn - s0 : 3;
+        const bool last = s0 + nb == logn;
+        const int E = 1 << nb;
+        switch (nb) {
+            case 3: ntt_fwd_pass<3>(s, tw, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            case 2: ntt_fwd_pass<2>(s, tw, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            default: ntt_fwd_pass<1>(s, tw, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+        }
+        s0 += nb;
+    }
+}
+
+// inverse transform (without N^-1) of the slices; output in [0, 2q), natural order
+__device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int NS = 1 << (logn - 3), off = rank * NS;
+    int s0 = 0;
+    while (s0 < logn - 3) {
+        const int nb = logn - 3 - s0 < 3 ? logn - 3 - s0 : 3;
+        const int E = 1 << nb;
+        switch (nb) {
+            case 3: ntt_inv_pass<3>(s, itw, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            case 2: ntt_inv_pass<2>(s, itw, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            default: ntt_inv_pass<1>(s, itw, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+        }
+        s0 += nb;
+    }
+    cl.sync();
+    ntt_cross_step<false>(s, itw, q, logn);
+    cl.sync();
+}
+
+// the cluster form is used for rings of at least 2^10 (slices of at least 128 elements)
+#define HE_NTT_CL_MIN_LOGN 10
+__device__ __forceinline__ int cl_slice_threads(int logn) { return 1 << (logn - 6); }
+
+// Kernels over a batch of limb-polys: in the plain form one CTA transforms a whole limb-poly
+// (grid = polys); in the cluster form (CL) a cluster of HE_NTT_CL CTAs shares one limb-poly,
+// each CTA handling the slice [rank N/8, (rank+1) N/8) (grid = polys * HE_NTT_CL).
+template <bool CL>
+__device__ __forceinline__ void slice_of(int logn, int &poly, int &off, int &len) {
+    const int N = 1 << logn;
+    if (CL) {
+        poly = blockIdx.x / HE_NTT_CL;
+        len = N / HE_NTT_CL;
+        off = (int)cg::this_cluster().block_rank() * len;
+    } else {
+        poly = blockIdx.x;
+        len = N;
+        off = 0;
+    }
+}
+
+template <bool CL>
+__device__ __forceinline__ void fwd_any(uint64_t *s, const ulonglong2 *tw, uint64_t q, int logn) {
+    if (CL) ntt_fwd_cluster(s, tw, q, logn);
+    else ntt_fwd_smem(s, tw, q, logn);
+}
+template <bool CL>
+__device__ __forceinline__ void inv_any(uint64_t *s, const ulonglong2 *tw, uint64_t q, int logn) {
+    if (CL) ntt_inv_cluster(s, tw, q, logn);
+    else ntt_inv_smem(s, tw, q, logn);
 }
 
 // twiddle table of prime index p: which = 0 forward (psi^brv(k), Shoup), 1 inverse (psi^-brv(k), Shoup)

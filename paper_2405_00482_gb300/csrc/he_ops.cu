@@ -39,40 +39,45 @@ __global__ void automorph_kernel(const uint64_t *__restrict__ in, uint64_t *__re
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) out[base + k] = in[base + automorph_src(k, g, logn)];
 }
 
-// ModUp body for CTA (d, u).  Digit-own limbs are copied from the NTT-form input; the
-// others are converted from the coefficient-form digit limbs and transformed.
+// ModUp body for (d, u): digit-own limbs are copied from the NTT-form input; the others are
+// converted from the coefficient-form digit limbs and transformed.  CL: this CTA handles the
+// slice [off, off + len) of a cluster-shared limb-poly.
+template <bool CL>
 __device__ __forceinline__ void modup_body(const uint64_t *__restrict__ c1_ntt, const uint64_t *__restrict__ c1_coef, uint64_t *D,
                                            const ModUpConst &mu, int d, int u, uint64_t *s, const uint64_t *__restrict__ d_tw,
-                                           const ModConst *__restrict__ mc, int logn) {
+                                           const ModConst *__restrict__ mc, int logn, int off, int len) {
     const int N = 1 << logn;
     const int lo = d * mu.alpha;
     const int hi = lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq;
     const int p = mu.ext_prime[u];
     const uint64_t t = mc[p].q;
-    uint64_t *dst = D + ((int64_t)d * mu.ext + u) * N;
-    if (u >= lo && u < hi) {
-        for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = c1_ntt[(int64_t)u * N + k];
+    uint64_t *dst = D + ((int64_t)d * mu.ext + u) * N + off;
+    if (u >= lo && u < hi) {  // uniform over the whole cluster
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = c1_ntt[(int64_t)u * N + off + k];
         return;
     }
     const int na = hi - lo;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
         uint64_t acc = 0;
         for (int i = 0; i < na; ++i) {
             const uint64_t qi = mc[lo + i].q;
-            uint64_t v = mul_shoup(c1_coef[(int64_t)(lo + i) * N + k], mu.inv[d][i], mu.inv_shoup[d][i], qi);
+            uint64_t v = mul_shoup(c1_coef[(int64_t)(lo + i) * N + off + k], mu.inv[d][i], mu.inv_shoup[d][i], qi);
             acc = add_mod(acc, mul_shoup(v, mu.hat[d][i][u], mu.hat_shoup[d][i][u], t), t);
         }
         s[SIDX(k)] = acc;
     }
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, p, 0, logn), t, logn);
-    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = s[SIDX(k)];
+    fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), t, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
 }
 
+template <bool CL>
 __global__ void modup_kernel(const uint64_t *__restrict__ c1_ntt, const uint64_t *__restrict__ c1_coef, uint64_t *D, ModUpConst mu,
                              const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
     extern __shared__ uint64_t s[];
-    modup_body(c1_ntt, c1_coef, D, mu, blockIdx.x / mu.ext, blockIdx.x % mu.ext, s, d_tw, mc, logn);
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
+    modup_body<CL>(c1_ntt, c1_coef, D, mu, item / mu.ext, item % mu.ext, s, d_tw, mc, logn, off, len);
 }
 
 // u_c[u][k] = sum_d D[d][u][src(k)] * keyM[d][c][kl(u)][k], REDC in groups of at most 8 terms
@@ -101,16 +106,18 @@ __global__ void ks_inner_kernel(const uint64_t *__restrict__ D, int ndig, int ex
     }
 }
 
-// ModDown body for CTA (c, j): conv = Conv_{P->q_j}(x_P, coefficient form) -> NTT ->
-// out = add_c + (x_j - conv) P^-1.
+// ModDown body for (c, j): conv = Conv_{P->q_j}(x_P, coefficient form) -> NTT ->
+// out = add_c + (x_j - conv) P^-1.  CL: slice [off, off + len) of a cluster-shared limb-poly.
+template <bool CL>
 __device__ __forceinline__ void moddown_body(const uint64_t *__restrict__ x, int ext, const uint64_t *__restrict__ xp_coef,
                                              const ModDownConst &md, const uint64_t *__restrict__ ad, uint64_t *out, int c, int j,
-                                             uint64_t *s, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+                                             uint64_t *s, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn,
+                                             int off, int len) {
     const int N = 1 << logn;
     const int pj = md.q_prime[j];
     const uint64_t q = mc[pj].q;
-    const uint64_t *xp = xp_coef + (int64_t)c * md.K * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const uint64_t *xp = xp_coef + (int64_t)c * md.K * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
         uint64_t acc = 0;
         for (int i = 0; i < md.K; ++i) {
             const uint64_t pi = mc[md.p_prime[i]].q;
@@ -120,22 +127,26 @@ __device__ __forceinline__ void moddown_body(const uint64_t *__restrict__ x, int
         s[SIDX(k)] = acc;
     }
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, pj, 0, logn), q, logn);
-    const uint64_t *xj = x + ((int64_t)c * ext + j) * N;
-    uint64_t *o = out + ((int64_t)c * md.nq + j) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    fwd_any<CL>(s, twiddles(d_tw, pj, 0, logn), q, logn);
+    const uint64_t *xj = x + ((int64_t)c * ext + j) * N + off;
+    uint64_t *o = out + ((int64_t)c * md.nq + j) * N + off;
+    const uint64_t *a = ad ? ad + (int64_t)j * N + off : nullptr;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
         uint64_t v = mul_shoup(sub_mod(xj[k], s[SIDX(k)], q), md.pinv[j], md.pinv_shoup[j], q);
-        if (ad) v = add_mod(v, ad[(int64_t)j * N + k], q);
+        if (a) v = add_mod(v, a[k], q);
         o[k] = v;
     }
 }
 
+template <bool CL>
 __global__ void moddown_kernel(const uint64_t *__restrict__ x, int ext, const uint64_t *__restrict__ xp_coef, ModDownConst md,
                                const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *out,
                                const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
     extern __shared__ uint64_t s[];
-    const int c = blockIdx.x / md.nq, j = blockIdx.x % md.nq;
-    moddown_body(x, ext, xp_coef, md, c == 0 ? add0 : add1, out, c, j, s, d_tw, mc, logn);
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
+    const int c = item / md.nq, j = item % md.nq;
+    moddown_body<CL>(x, ext, xp_coef, md, c == 0 ? add0 : add1, out, c, j, s, d_tw, mc, logn, off, len);
 }
 
 struct RescaleConst {
@@ -143,31 +154,35 @@ struct RescaleConst {
     uint64_t inv[HE_MAX_Q], inv_shoup[HE_MAX_Q];  // q_l^-1 mod q_j
 };
 
-// Rescale body for CTA (c, j), j < level: v = centred(last limb) mod q_j -> NTT ->
-// out = (c_j - v) q_l^-1
+// Rescale body for (c, j), j < level: v = centred(last limb) mod q_j -> NTT ->
+// out = (c_j - v) q_l^-1.  CL: slice [off, off + len) of a cluster-shared limb-poly.
+template <bool CL>
 __device__ __forceinline__ void rescale_body(const uint64_t *__restrict__ ct, int level, const uint64_t *__restrict__ last_coef,
                                              const RescaleConst &rc, uint64_t *out, int c, int j, uint64_t *s,
-                                             const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+                                             const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int off, int len) {
     const int N = 1 << logn;
     const uint64_t q = mc[j].q;
-    const uint64_t *lc = last_coef + (int64_t)c * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const uint64_t *lc = last_coef + (int64_t)c * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
         uint64_t r = lc[k] + rc.half;
         if (r >= rc.ql) r -= rc.ql;
         int64_t centred = (int64_t)r - (int64_t)rc.half;
         s[SIDX(k)] = reduce_signed(centred, q);
     }
     __syncthreads();
-    ntt_fwd_smem(s, twiddles(d_tw, j, 0, logn), q, logn);
-    const uint64_t *cj = ct + ((int64_t)c * (level + 1) + j) * N;
-    uint64_t *o = out + ((int64_t)c * level + j) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
+    fwd_any<CL>(s, twiddles(d_tw, j, 0, logn), q, logn);
+    const uint64_t *cj = ct + ((int64_t)c * (level + 1) + j) * N + off;
+    uint64_t *o = out + ((int64_t)c * level + j) * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
 }
 
+template <bool CL>
 __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const uint64_t *__restrict__ last_coef, RescaleConst rc,
                                uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
     extern __shared__ uint64_t s[];
-    rescale_body(ct, level, last_coef, rc, out, blockIdx.x / level, blockIdx.x % level, s, d_tw, mc, logn);
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
+    rescale_body<CL>(ct, level, last_coef, rc, out, item / level, item % level, s, d_tw, mc, logn, off, len);
 }
 
 // ---- batch forms: the same bodies over a job table (one job = one MatMult, R = C = 1) ----
@@ -194,8 +209,8 @@ __global__ void batch_modup_kernel(const MMJob *__restrict__ jobs, BatchGeom bg,
     const int per = mu.ndig * mu.ext;
     const int j = blockIdx.x / per, rest = blockIdx.x % per;
     if (jobs[j].m_prime <= 1) return;
-    modup_body(jobs[j].ct + (int64_t)bg.nq * (1 << logn), bg.coef + (int64_t)j * bg.coef_words, bg.D + (int64_t)j * bg.d_words, mu,
-               rest / mu.ext, rest % mu.ext, s, d_tw, mc, logn);
+    modup_body<false>(jobs[j].ct + (int64_t)bg.nq * (1 << logn), bg.coef + (int64_t)j * bg.coef_words, bg.D + (int64_t)j * bg.d_words, mu,
+                      rest / mu.ext, rest % mu.ext, s, d_tw, mc, logn, 0, 1 << logn);
 }
 
 // iNTT of the P limbs of both accumulator components: block (j, c, i) -> tmp_j [c][K][N]
@@ -223,8 +238,8 @@ __global__ void batch_moddown_kernel(const MMJob *__restrict__ jobs, BatchGeom b
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / md.nq, l = blockIdx.x % md.nq;
     if (jobs[j].m_prime == 0) return;  // empty slot
     const uint64_t *cacc = bg.cacc + (int64_t)j * bg.cacc_words;
-    moddown_body(bg.acc + (int64_t)j * bg.acc_words, bg.ext, bg.tmp + (int64_t)j * bg.tmp_words, md, cacc + (int64_t)c * md.nq * (1 << logn),
-                 bg.sum + (int64_t)j * bg.sum_words, c, l, s, d_tw, mc, logn);
+    moddown_body<false>(bg.acc + (int64_t)j * bg.acc_words, bg.ext, bg.tmp + (int64_t)j * bg.tmp_words, md,
+                        cacc + (int64_t)c * md.nq * (1 << logn), bg.sum + (int64_t)j * bg.sum_words, c, l, s, d_tw, mc, logn, 0, 1 << logn);
 }
 
 // iNTT of the last limb of both sum components -> tmp_j + 2K N
@@ -250,97 +265,128 @@ __global__ void batch_rescale_kernel(const MMJob *__restrict__ jobs, BatchGeom b
     const int per = 2 * bg.level;
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / bg.level, l = blockIdx.x % bg.level;
     if (jobs[j].m_prime == 0) return;  // empty slot
-    rescale_body(bg.sum + (int64_t)j * bg.sum_words, bg.level, bg.tmp + (int64_t)j * bg.tmp_words + (int64_t)2 * bg.K * (1 << logn), rc,
-                 jobs[j].out, c, l, s, d_tw, mc, logn);
+    rescale_body<false>(bg.sum + (int64_t)j * bg.sum_words, bg.level, bg.tmp + (int64_t)j * bg.tmp_words + (int64_t)2 * bg.K * (1 << logn),
+                        rc, jobs[j].out, c, l, s, d_tw, mc, logn, 0, 1 << logn);
 }
 
 // The double-hoisted MatMult loop.  For every coefficient k of extended limb u:
 //   acc_c[u][k]  = sum_{i>=1} ptM_i[u][k] * redc(sum_d D[d][u][src_i(k)] keyM_i[d][c][kl(u)][k])
 //   cacc_0[u][k] = ptM_0 * c0[u][k] + sum_{i>=1} ptM_i[u][k] * c0[u][src_i(k)]   (u in Q_level)
 //   cacc_1[u][k] = ptM_0 * c1[u][k]
-// Thread layout: a block covers MM_PAIRS coefficient pairs of one limb (blockIdx.y) and splits
-// the rotations i = 1..m'-1 into MM_GROUPS interleaved groups, one per warp group; the group
-// sums meet in shared memory.  A pair (k, k+1), k even, gathers the aligned pair
-// (src, src ^ 1) of each digit, so every load is 16 bytes.  Products are accumulated in 128
-// bits and reduced once per 8 terms (8 q^2 < q 2^64 for q < 2^61).
-#define MM_PAIRS 64
-#define MM_GROUPS 4
-
-struct Acc2 {
-    u128 v[2];
-};
+// Variants (chosen per encoded matrix or batch by timing them, see mm_variant): a block of
+// MM_THREADS threads covers LANES = MM_THREADS / G lanes of VEC consecutive coefficients of one
+// limb and splits the rotations i = 1..m'-1 into G interleaved groups; the group sums meet in
+// shared memory.  With VEC = 2 a lane's pair (k, k+1), k even, gathers the aligned pair
+// (src, src ^ 1) of each digit, so every load is 16 bytes; VEC = 1 halves the registers and
+// doubles the warps.  Each lane loads the next rotation step's operands while it computes the
+// current one.  Products are accumulated in 128 bits and reduced once per 8 terms
+// (8 q^2 < q 2^64 for q < 2^61).
+#define MM_THREADS 256
 
 __device__ __forceinline__ uint64_t fold(u128 t, uint64_t q, uint64_t qinv) { return redc128(t, q, qinv); }
 
-// One tile: MM_PAIRS coefficient pairs starting at pair index `pair0` of extended limb u.
-// Every thread of the block calls it (it synchronises once).
-template <int NDIG>
+template <int VEC>
+__device__ __forceinline__ void ldv(const uint64_t *p, uint64_t (&o)[VEC]) {
+    if constexpr (VEC == 2) {
+        const ulonglong2 t = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+        o[0] = t.x;
+        o[1] = t.y;
+    } else {
+        o[0] = __ldg(p);
+    }
+}
+// gather of VEC values at the automorphism image of k..k+VEC-1 (src of k given)
+template <int VEC>
+__device__ __forceinline__ void gatherv(const uint64_t *base, uint32_t src, uint64_t (&o)[VEC]) {
+    if constexpr (VEC == 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(base + (src & ~1u));
+        o[0] = (src & 1) ? t.y : t.x;
+        o[1] = (src & 1) ? t.x : t.y;
+    } else {
+        o[0] = base[src];
+    }
+}
+template <int VEC>
+__device__ __forceinline__ void stv(uint64_t *p, const uint64_t (&v)[VEC]) {
+    if constexpr (VEC == 2) {
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(v[0], v[1]);
+    } else {
+        p[0] = v[0];
+    }
+}
+
+// One tile: MM_THREADS / G lanes of VEC coefficients starting at coefficient k0 of extended
+// limb u.  Every thread of the block calls it (it synchronises once).  red: G*3*MM_THREADS words.
+template <int NDIG, int VEC, int G>
 __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
                                         const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime,
-                                        int ndig_rt, int ext, int nq, int L, int LK, int u, int p, int pair0, uint64_t *acc, uint64_t *cacc,
-                                        int accumulate, const ModConst *__restrict__ mc, int logn,
-                                        uint64_t (*red)[3][2][MM_PAIRS]) {
+                                        int ndig_rt, int ext, int nq, int L, int LK, int u, int p, int k0, uint64_t *acc, uint64_t *cacc,
+                                        int accumulate, const ModConst *__restrict__ mc, int logn, uint64_t *red) {
+    constexpr int LANES = MM_THREADS / G;
     const int N = 1 << logn;
     const int ndig = NDIG > 0 ? NDIG : ndig_rt;
     const int kl = u < nq ? u : L + (u - nq);
     const uint64_t q = mc[p].q, qinv = mc[p].qinv;
     const bool inq = u < nq;
-    const int lane = threadIdx.x % MM_PAIRS, grp = threadIdx.x / MM_PAIRS;
-    const int k = 2 * (pair0 + lane);
+    const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES;
+    const int k = k0 + VEC * lane;
+    auto R = [&](int g, int which, int j) -> uint64_t & { return red[((g * 3 + which) * VEC + j) * LANES + lane]; };
 
-    uint64_t r0[2] = {0, 0}, r1[2] = {0, 0}, rc[2] = {0, 0};
+    uint64_t r0[VEC], r1[VEC], rc[VEC];
+#pragma unroll
+    for (int j = 0; j < VEC; ++j) r0[j] = r1[j] = rc[j] = 0;
     if (k < N) {
-        u128 t0[2] = {0, 0}, t1[2] = {0, 0}, tc[2] = {0, 0};
+        u128 t0[VEC], t1[VEC], tc[VEC];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) t0[j] = t1[j] = tc[j] = 0;
         int pending = 0;
         constexpr int ND = NDIG > 0 ? NDIG : 8;
-        // operands of one rotation step; the next step's are loaded while this one is computed
-        ulonglong2 dv[ND], k0[ND], k1[ND], pm, cv;
-        int sw = 0;
+        uint64_t dv[ND][VEC], kv0[ND][VEC], kv1[ND][VEC], pm[VEC], cv[VEC];
         auto fetch = [&](int i) {
             const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
-            const int sp = src & ~1u;
-            sw = src & 1;
             const uint64_t *key = keys[i - 1];
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 if (NDIG == 0 && d >= ndig) break;
-                dv[d] = *reinterpret_cast<const ulonglong2 *>(D + ((int64_t)d * ext + u) * N + sp);
-                k0[d] = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k));
-                k1[d] = __ldg(reinterpret_cast<const ulonglong2 *>(key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k));
+                gatherv<VEC>(D + ((int64_t)d * ext + u) * N, src, dv[d]);
+                ldv<VEC>(key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k, kv0[d]);
+                ldv<VEC>(key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k, kv1[d]);
             }
-            pm = __ldg(reinterpret_cast<const ulonglong2 *>(pts + ((int64_t)i * ext + u) * N + k));
-            if (inq) cv = *reinterpret_cast<const ulonglong2 *>(ct + (int64_t)u * N + sp);
+            ldv<VEC>(pts + ((int64_t)i * ext + u) * N + k, pm);
+            if (inq) gatherv<VEC>(ct + (int64_t)u * N, src, cv);
         };
         int i = 1 + grp;
         if (i < m_prime) fetch(i);
         while (i < m_prime) {
-            u128 s0[2] = {0, 0}, s1[2] = {0, 0};
+            u128 s0[VEC], s1[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) s0[j] = s1[j] = 0;
 #pragma unroll
             for (int d = 0; d < ND; ++d) {
                 if (NDIG == 0 && d >= ndig) break;
-                const uint64_t dk0 = sw ? dv[d].y : dv[d].x, dk1 = sw ? dv[d].x : dv[d].y;
-                s0[0] += (u128)dk0 * k0[d].x;
-                s0[1] += (u128)dk1 * k0[d].y;
-                s1[0] += (u128)dk0 * k1[d].x;
-                s1[1] += (u128)dk1 * k1[d].y;
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                    s0[j] += (u128)dv[d][j] * kv0[d][j];
+                    s1[j] += (u128)dv[d][j] * kv1[d][j];
+                }
             }
-            const ulonglong2 pmc = pm;
-            const uint64_t c0a = sw ? cv.y : cv.x, c0b = sw ? cv.x : cv.y;
-            const int next = i + MM_GROUPS;
+            uint64_t pmc[VEC], c0v[VEC];
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                pmc[j] = pm[j];
+                c0v[j] = cv[j];
+            }
+            const int next = i + G;
             if (next < m_prime) fetch(next);
-            const uint64_t u00 = fold(s0[0], q, qinv), u01 = fold(s0[1], q, qinv);
-            const uint64_t u10 = fold(s1[0], q, qinv), u11 = fold(s1[1], q, qinv);
-            t0[0] += (u128)u00 * pmc.x;
-            t0[1] += (u128)u01 * pmc.y;
-            t1[0] += (u128)u10 * pmc.x;
-            t1[1] += (u128)u11 * pmc.y;
-            if (inq) {
-                tc[0] += (u128)c0a * pmc.x;
-                tc[1] += (u128)c0b * pmc.y;
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                t0[j] += (u128)fold(s0[j], q, qinv) * pmc[j];
+                t1[j] += (u128)fold(s1[j], q, qinv) * pmc[j];
+                if (inq) tc[j] += (u128)c0v[j] * pmc[j];
             }
             if (++pending == 8) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < VEC; ++j) {
                     r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
                     r1[j] = add_mod(r1[j], fold(t1[j], q, qinv), q);
                     rc[j] = add_mod(rc[j], fold(tc[j], q, qinv), q);
@@ -351,87 +397,91 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
             i = next;
         }
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < VEC; ++j) {
             r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
             r1[j] = add_mod(r1[j], fold(t1[j], q, qinv), q);
             rc[j] = add_mod(rc[j], fold(tc[j], q, qinv), q);
         }
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        red[grp][0][j][lane] = r0[j];
-        red[grp][1][j][lane] = r1[j];
-        red[grp][2][j][lane] = rc[j];
+    for (int j = 0; j < VEC; ++j) {
+        R(grp, 0, j) = r0[j];
+        R(grp, 1, j) = r1[j];
+        R(grp, 2, j) = rc[j];
     }
     __syncthreads();
     if (grp == 0 && k < N) {
-        uint64_t a0[2], a1[2], cc0[2], cc1[2] = {0, 0};
+        uint64_t a0[VEC], a1[VEC], cc0[VEC], cc1[VEC];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            a0[j] = red[0][0][j][lane];
-            a1[j] = red[0][1][j][lane];
-            cc0[j] = red[0][2][j][lane];
-            for (int g = 1; g < MM_GROUPS; ++g) {
-                a0[j] = add_mod(a0[j], red[g][0][j][lane], q);
-                a1[j] = add_mod(a1[j], red[g][1][j][lane], q);
-                cc0[j] = add_mod(cc0[j], red[g][2][j][lane], q);
+        for (int j = 0; j < VEC; ++j) {
+            a0[j] = R(0, 0, j);
+            a1[j] = R(0, 1, j);
+            cc0[j] = R(0, 2, j);
+            cc1[j] = 0;
+            for (int g = 1; g < G; ++g) {
+                a0[j] = add_mod(a0[j], R(g, 0, j), q);
+                a1[j] = add_mod(a1[j], R(g, 1, j), q);
+                cc0[j] = add_mod(cc0[j], R(g, 2, j), q);
             }
         }
         if (inq) {  // i = 0: no rotation
-            const ulonglong2 p0 = __ldg(reinterpret_cast<const ulonglong2 *>(pts + (int64_t)u * N + k));
-            const ulonglong2 c0v = *reinterpret_cast<const ulonglong2 *>(ct + (int64_t)u * N + k);
-            const ulonglong2 c1v = *reinterpret_cast<const ulonglong2 *>(ct + ((int64_t)nq + u) * N + k);
-            cc0[0] = add_mod(cc0[0], mont_mul(c0v.x, p0.x, q, qinv), q);
-            cc0[1] = add_mod(cc0[1], mont_mul(c0v.y, p0.y, q, qinv), q);
-            cc1[0] = mont_mul(c1v.x, p0.x, q, qinv);
-            cc1[1] = mont_mul(c1v.y, p0.y, q, qinv);
-        }
-        ulonglong2 *A0 = reinterpret_cast<ulonglong2 *>(acc + (int64_t)u * N + k);
-        ulonglong2 *A1 = reinterpret_cast<ulonglong2 *>(acc + ((int64_t)ext + u) * N + k);
-        if (accumulate) {
-            const ulonglong2 o0 = *A0, o1 = *A1;
-            *A0 = make_ulonglong2(add_mod(o0.x, a0[0], q), add_mod(o0.y, a0[1], q));
-            *A1 = make_ulonglong2(add_mod(o1.x, a1[0], q), add_mod(o1.y, a1[1], q));
-        } else {
-            *A0 = make_ulonglong2(a0[0], a0[1]);
-            *A1 = make_ulonglong2(a1[0], a1[1]);
-        }
-        if (inq) {
-            ulonglong2 *C0 = reinterpret_cast<ulonglong2 *>(cacc + (int64_t)u * N + k);
-            ulonglong2 *C1 = reinterpret_cast<ulonglong2 *>(cacc + ((int64_t)nq + u) * N + k);
-            if (accumulate) {
-                const ulonglong2 o0 = *C0, o1 = *C1;
-                *C0 = make_ulonglong2(add_mod(o0.x, cc0[0], q), add_mod(o0.y, cc0[1], q));
-                *C1 = make_ulonglong2(add_mod(o1.x, cc1[0], q), add_mod(o1.y, cc1[1], q));
-            } else {
-                *C0 = make_ulonglong2(cc0[0], cc0[1]);
-                *C1 = make_ulonglong2(cc1[0], cc1[1]);
+            uint64_t p0[VEC], c0[VEC], c1[VEC];
+            ldv<VEC>(pts + (int64_t)u * N + k, p0);
+            ldv<VEC>(ct + (int64_t)u * N + k, c0);
+            ldv<VEC>(ct + ((int64_t)nq + u) * N + k, c1);
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                cc0[j] = add_mod(cc0[j], mont_mul(c0[j], p0[j], q, qinv), q);
+                cc1[j] = mont_mul(c1[j], p0[j], q, qinv);
             }
+        }
+        uint64_t *A0 = acc + (int64_t)u * N + k, *A1 = acc + ((int64_t)ext + u) * N + k;
+        if (accumulate) {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) {
+                a0[j] = add_mod(A0[j], a0[j], q);
+                a1[j] = add_mod(A1[j], a1[j], q);
+            }
+        }
+        stv<VEC>(A0, a0);
+        stv<VEC>(A1, a1);
+        if (inq) {
+            uint64_t *C0 = cacc + (int64_t)u * N + k, *C1 = cacc + ((int64_t)nq + u) * N + k;
+            if (accumulate) {
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                    cc0[j] = add_mod(C0[j], cc0[j], q);
+                    cc1[j] = add_mod(C1[j], cc1[j], q);
+                }
+            }
+            stv<VEC>(C0, cc0);
+            stv<VEC>(C1, cc1);
         }
     }
 }
 
-// single MatMult: block (pair tile, extended limb)
-template <int NDIG>
-__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS, 2) matmult_loop_kernel(
+// single MatMult: block (coefficient tile, extended limb)
+template <int NDIG, int VEC, int G>
+__global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_loop_kernel(
     const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
     const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime, int ndig_rt, int ext, int nq, int L,
-    int LK, LimbMap emap, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
-    __shared__ uint64_t red[MM_GROUPS][3][2][MM_PAIRS];
+    int LK, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
+    __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
     const int u = blockIdx.y;
-    mm_tile<NDIG>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq), blockIdx.x * MM_PAIRS, acc,
-                  cacc, accumulate, mc, logn, red);
+    mm_tile<NDIG, VEC, G>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq),
+                          blockIdx.x * (MM_THREADS / G) * VEC, acc, cacc, accumulate, mc, logn, red);
 }
 
 // batch: persistent CTAs pull (tile, limb, job) items from an ordered queue
-template <int NDIG>
-__global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS, 2) matmult_batch_loop_kernel(const MMJob *__restrict__ jobs, const int32_t *__restrict__ order,
-                                                                                 int n_items, unsigned int *counter, BatchGeom bg, LimbMap emap,
-                                                                                 const ModConst *__restrict__ mc, int logn) {
-    __shared__ uint64_t red[MM_GROUPS][3][2][MM_PAIRS];
+template <int NDIG, int VEC, int G>
+__global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_loop_kernel(
+    const MMJob *__restrict__ jobs, const int32_t *__restrict__ order, int n_items, unsigned int *counter, BatchGeom bg,
+    const ModConst *__restrict__ mc, int logn) {
+    __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
     __shared__ int item_s;
     const int N = 1 << logn;
-    const int tiles = (N / 2 + MM_PAIRS - 1) / MM_PAIRS;
+    constexpr int TILE = (MM_THREADS / G) * VEC;
+    const int tiles = (N + TILE - 1) / TILE;
     for (;;) {
         if (threadIdx.x == 0) item_s = (int)atomicAdd(counter, 1u);
         __syncthreads();
@@ -443,10 +493,73 @@ __global__ void __launch_bounds__(MM_PAIRS *MM_GROUPS, 2) matmult_batch_loop_ker
         const int u = rest / tiles, tile = rest % tiles;
         const MMJob &jb = jobs[j];
         if (jb.m_prime == 0) continue;  // empty slot
-        mm_tile<NDIG>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L, bg.LK,
-                      u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * MM_PAIRS, bg.acc + (int64_t)j * bg.acc_words, bg.cacc + (int64_t)j * bg.cacc_words, 0, mc,
-                      logn, red);
+        mm_tile<NDIG, VEC, G>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L,
+                              bg.LK, u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * TILE, bg.acc + (int64_t)j * bg.acc_words,
+                              bg.cacc + (int64_t)j * bg.cacc_words, 0, mc, logn, red);
         __syncthreads();
+    }
+}
+
+}  // namespace
+
+// ---- variant dispatch ----
+// variant v: (VEC, G) = {0: (2, 4), 1: (1, 4), 2: (1, 8), 3: (2, 8)}
+int mm_variant_count() { return 4; }
+int mm_variant_tile(int v) {
+    static const int vec[4] = {2, 1, 1, 2}, grp[4] = {4, 4, 8, 8};
+    return (MM_THREADS / grp[v]) * vec[v];
+}
+
+namespace {
+
+template <int NDIG, int VEC, int G>
+static void mm_launch_single(he_ctx *ctx, dim3 grid, const uint64_t *ct, const uint64_t *D, const uint64_t *pts, const uint64_t *const *keys,
+                             const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
+    matmult_loop_kernel<NDIG, VEC, G><<<grid, MM_THREADS, 0, ctx->stream>>>(ct, D, pts, keys, galois, m_prime, ndig, ext, nq, ctx->L,
+                                                                          ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n);
+}
+
+template <int VEC, int G>
+static void mm_launch_single_nd(he_ctx *ctx, dim3 grid, const uint64_t *ct, const uint64_t *D, const uint64_t *pts, const uint64_t *const *keys,
+                                const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
+    switch (ndig) {
+        case 1: mm_launch_single<1, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+        case 2: mm_launch_single<2, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+        case 3: mm_launch_single<3, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+        default: mm_launch_single<0, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+    }
+}
+
+void mm_launch_variant(he_ctx *ctx, int v, const uint64_t *ct, const uint64_t *D, const uint64_t *pts, const uint64_t *const *keys,
+                       const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
+    const dim3 grid((unsigned)((ctx->n + mm_variant_tile(v) - 1) / mm_variant_tile(v)), (unsigned)ext);
+    ctx->launches++;
+    switch (v) {
+        case 1: mm_launch_single_nd<1, 4>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+        case 2: mm_launch_single_nd<1, 8>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+        case 3: mm_launch_single_nd<2, 8>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+        default: mm_launch_single_nd<2, 4>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+    }
+}
+
+template <int VEC, int G>
+static void mm_launch_batch_nd(int ndig, dim3 grid, cudaStream_t st, const MMJob *jobs, const int32_t *order, int n_items, unsigned int *counter,
+                               const BatchGeom &bg, const ModConst *mc, int logn) {
+    switch (ndig) {
+        case 1: matmult_batch_loop_kernel<1, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
+        case 2: matmult_batch_loop_kernel<2, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
+        case 3: matmult_batch_loop_kernel<3, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
+        default: matmult_batch_loop_kernel<0, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
+    }
+}
+
+void mm_launch_batch_variant(int v, dim3 grid, cudaStream_t st, const MMJob *jobs, const int32_t *order, int n_items, unsigned int *counter,
+                             const BatchGeom &bg, const ModConst *mc, int logn) {
+    switch (v) {
+        case 1: mm_launch_batch_nd<1, 4>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
+        case 2: mm_launch_batch_nd<1, 8>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
+        case 3: mm_launch_batch_nd<2, 8>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
+        default: mm_launch_batch_nd<2, 4>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
     }
 }
 
@@ -529,8 +642,13 @@ void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, u
     for (int l = 0; l <= level; ++l) qmap.prime[l] = l;
     launch_ntt_inv_strided(ctx, c1_ntt, 0, tmp_coeff, 0, 1, qmap);
     ctx->launches++;
-    modup_kernel<<<mu.ndig * mu.ext, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
-                                                                                              ctx->d_mc, ctx->log_n);
+    const int items = mu.ndig * mu.ext;
+    if (use_cluster(ctx->log_n, items))
+        launch_cluster(modup_kernel<true>, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, c1_ntt,
+                       (const uint64_t *)tmp_coeff, D, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+    else
+        modup_kernel<false><<<items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
+                                                                                                       ctx->d_mc, ctx->log_n);
 }
 
 void launch_ks_inner(he_ctx *ctx, const uint64_t *D, int level, uint32_t g, const uint64_t *key, uint64_t *u) {
@@ -553,8 +671,13 @@ void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const 
     // P limbs of every component into coefficient form: tmp [ncomp][K][N]
     launch_ntt_inv_strided(ctx, x + (int64_t)(level + 1) * ctx->n, (int64_t)ext * ctx->n, tmp, (int64_t)ctx->K * ctx->n, ncomp, pmap);
     ctx->launches++;
-    moddown_kernel<<<ncomp * md.nq, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(x, ext, tmp, md, add0, add1, out, ctx->d_tw,
-                                                                                              ctx->d_mc, ctx->log_n);
+    const int items = ncomp * md.nq;
+    if (use_cluster(ctx->log_n, items))
+        launch_cluster(moddown_kernel<true>, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, x, ext,
+                       (const uint64_t *)tmp, md, add0, add1, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+    else
+        moddown_kernel<false><<<items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(x, ext, tmp, md, add0, add1, out,
+                                                                                                         ctx->d_tw, ctx->d_mc, ctx->log_n);
 }
 
 static RescaleConst make_rescale_const(const he_ctx *ctx, int level) {
@@ -584,35 +707,59 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
     launch_ntt_inv_strided(ctx, ct + (int64_t)level * N, (int64_t)(level + 1) * N, tmp, N, 2, lmap);
     const RescaleConst rc = make_rescale_const(ctx, level);
     ctx->launches++;
-    rescale_kernel<<<2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, level, tmp, rc, out, ctx->d_tw, ctx->d_mc,
-                                                                                          ctx->log_n);
+    if (use_cluster(ctx->log_n, 2 * level))
+        launch_cluster(rescale_kernel<true>, 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, ct, level,
+                       (const uint64_t *)tmp, rc, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+    else
+        rescale_kernel<false><<<2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, level, tmp, rc, out, ctx->d_tw,
+                                                                                                             ctx->d_mc, ctx->log_n);
 }
 
 void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D, uint64_t *acc,
                          uint64_t *cacc, int accumulate) {
     const int level = pm->level;
     const ModUpConst &mu = ctx->modup[level];
-    LimbMap emap{};
-    emap.n = mu.ext;
-    for (int v = 0; v < mu.ext; ++v) emap.prime[v] = mu.ext_prime[v];
     const he_plan &p = pm->plan;
     const uint64_t *pts = pm->data + (((int64_t)r * p.col_blocks + c) * p.m_prime) * pm->ext * ctx->n;
     cudaEvent_t *ev = prof_pair(ctx);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
-    const dim3 grid((ctx->n / 2 + MM_PAIRS - 1) / MM_PAIRS, mu.ext);
-    const int m_prime = (int)p.m_prime;
-#define MM_ARGS ct, D, pts, pm->d_keys, pm->d_galois, m_prime, mu.ndig, mu.ext, level + 1, ctx->L, ctx->L + ctx->K, emap, acc, cacc, \
-                accumulate, ctx->d_mc, ctx->log_n
-    ctx->launches++;
-    switch (mu.ndig) {
-        case 1: matmult_loop_kernel<1><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        case 2: matmult_loop_kernel<2><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        case 3: matmult_loop_kernel<3><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        case 4: matmult_loop_kernel<4><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        default: matmult_loop_kernel<0><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-    }
-#undef MM_ARGS
+    mm_launch_variant(ctx, pm->variant < 0 ? 0 : pm->variant, ct, D, pts, pm->d_keys, pm->d_galois, (int)p.m_prime, mu.ndig, mu.ext,
+                      level + 1, acc, cacc, accumulate);
     if (ev) cudaEventRecord(ev[1], ctx->stream);
+}
+
+// Time every loop-kernel variant once on this matrix's first product (the results are identical:
+// modular sums do not depend on the order) and keep the fastest.  Synchronises the stream.
+int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc) {
+    const ModUpConst &mu = ctx->modup[pm->level];
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return HE_ECUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return HE_ECUDA;
+    }
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < mm_variant_count(); ++v) {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch of a variant also loads its code
+            cudaEventRecord(a, ctx->stream);
+            mm_launch_variant(ctx, v, ct, D, pm->data, pm->d_keys, pm->d_galois, (int)pm->plan.m_prime, mu.ndig, mu.ext, pm->level + 1, acc, cacc,
+                              0);
+            cudaEventRecord(b, ctx->stream);
+            if (cudaEventSynchronize(b) != cudaSuccess) break;
+            cudaEventElapsedTime(&ms, a, b);
+        }
+        pm->tune_ms[v] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    pm->variant = best;
+    return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
 }
 
 // Same launch as launch_matmult_loop, with the Galois-key pointer table and Galois elements
@@ -621,24 +768,10 @@ void launch_matmult_loop_with_tables(he_ctx *ctx, const he_ptmat *pm, int r, int
                                      const uint64_t *const *keys, const uint32_t *galois, uint64_t *acc, uint64_t *cacc, int accumulate) {
     const int level = pm->level;
     const ModUpConst &mu = ctx->modup[level];
-    LimbMap emap{};
-    emap.n = mu.ext;
-    for (int v = 0; v < mu.ext; ++v) emap.prime[v] = mu.ext_prime[v];
     const he_plan &p = pm->plan;
     const uint64_t *pts = pm->data + (((int64_t)r * p.col_blocks + c) * p.m_prime) * pm->ext * ctx->n;
-    const dim3 grid((ctx->n / 2 + MM_PAIRS - 1) / MM_PAIRS, mu.ext);
-    const int m_prime = (int)p.m_prime;
-#define MM_ARGS ct, D, pts, keys, galois, m_prime, mu.ndig, mu.ext, level + 1, ctx->L, ctx->L + ctx->K, emap, acc, cacc, accumulate, \
-                ctx->d_mc, ctx->log_n
-    ctx->launches++;
-    switch (mu.ndig) {
-        case 1: matmult_loop_kernel<1><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        case 2: matmult_loop_kernel<2><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        case 3: matmult_loop_kernel<3><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        case 4: matmult_loop_kernel<4><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-        default: matmult_loop_kernel<0><<<grid, MM_PAIRS * MM_GROUPS, 0, ctx->stream>>>(MM_ARGS); break;
-    }
-#undef MM_ARGS
+    mm_launch_variant(ctx, pm->variant < 0 ? 0 : pm->variant, ct, D, pts, keys, galois, (int)p.m_prime, mu.ndig, mu.ext, level + 1, acc, cacc,
+                      accumulate);
 }
 
 void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots) {
@@ -671,21 +804,13 @@ int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
     const ModUpConst &mu = ctx->modup[level];
     const ModDownConst &md = ctx->moddown[level];
     const RescaleConst rc = make_rescale_const(ctx, level);
-    LimbMap emap{};
-    emap.n = mu.ext;
-    for (int v = 0; v < mu.ext; ++v) emap.prime[v] = mu.ext_prime[v];
     if (cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(MMJob) * count, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HE_ECUDA;
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), stream) != cudaSuccess) return HE_ECUDA;
     batch_intt_c1_kernel<<<count * bg.nq, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
     batch_modup_kernel<<<count * mu.ndig * mu.ext, thr, smem, stream>>>(b->d_jobs, bg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
     const dim3 pgrid(b->persistent_ctas);
-    switch (bg.ndig) {
-        case 1: matmult_batch_loop_kernel<1><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
-        case 2: matmult_batch_loop_kernel<2><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
-        case 3: matmult_batch_loop_kernel<3><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
-        case 4: matmult_batch_loop_kernel<4><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
-        default: matmult_batch_loop_kernel<0><<<pgrid, MM_PAIRS * MM_GROUPS, 0, stream>>>(b->d_jobs, b->d_order, b->n_items, b->d_counter, bg, emap, ctx->d_mc, ctx->log_n); break;
-    }
+    const int v = b->variant < 0 ? 0 : b->variant;
+    mm_launch_batch_variant(v, pgrid, stream, b->d_jobs, b->d_order_v[v], b->n_items_v[v], b->d_counter, bg, ctx->d_mc, ctx->log_n);
     batch_intt_p_kernel<<<count * 2 * bg.K, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
     batch_moddown_kernel<<<count * 2 * md.nq, thr, smem, stream>>>(b->d_jobs, bg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
     batch_intt_last_kernel<<<count * 2, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
@@ -694,7 +819,6 @@ int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
 }
 
-int mm_tile_pairs() { return MM_PAIRS; }
 
 void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(batch_intt_c1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
@@ -703,7 +827,7 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(batch_moddown_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(batch_intt_last_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(batch_rescale_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(modup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(moddown_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(rescale_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(modup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(moddown_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }

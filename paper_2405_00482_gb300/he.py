@@ -72,6 +72,8 @@ _SIGS = {
     "he_batch_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "he_batch_run": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
     "he_batch_free": (None, [_vp]),
+    "he_ptmat_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "he_batch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "he_cdiag_encode_weights": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_cdmat_free": (None, [_vp]),
     "he_cdiag_encode_matrix": (ctypes.c_int, [_vp, _vp, _i64, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
@@ -179,9 +181,20 @@ class Plaintext:
         return HePt(self.data.data_ptr(), self.level, self.scale)
 
 
+def _tuning(fn, handle) -> dict:
+    v = ctypes.c_int()
+    ms = (ctypes.c_float * 4)()
+    _check(fn(handle, ctypes.byref(v), ms), "tuning")
+    return {"variant": int(v.value), "variant_ms": [round(float(x), 4) for x in ms]}
+
+
 class PtMatrix:
     def __init__(self, ctx: "Context", handle, plan: Plan, level: int):
         self.ctx, self.handle, self.plan, self.level = ctx, handle, plan, level
+
+    def tuning(self) -> dict:
+        """Loop-kernel variant chosen on the first MatMult and the timed ms of each variant."""
+        return _tuning(_lib().he_ptmat_tuning, self.handle)
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -200,6 +213,9 @@ class Batch:
         _check(_lib().he_batch_create(ctx.handle, len(plans), pa, ma, ctypes.byref(h)), "he_batch_create")
         self.handle = h
         self.level = pms[0].level
+
+    def tuning(self) -> dict:
+        return _tuning(_lib().he_batch_tuning, self.handle)
 
     def run(self, cts: list[Ciphertext], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
         outs = outs or [self.ctx.new_ct(self.level - 1) for _ in cts]
