@@ -127,19 +127,23 @@ __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, c
     }
 }
 
-// decrypt limb 0: m = c0 + c1 s (NTT), inverse NTT, centred, as doubles.  One CTA per ciphertext.
+// decrypt limb 0: m = c0 + c1 s (NTT), inverse NTT, centred, as doubles.  One CTA per
+// ciphertext, or (CL) one cluster per ciphertext with each CTA on a slice.
+template <bool CL>
 __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words, int nl, const uint64_t *__restrict__ sk_mont,
                                double *coeffs, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
     const uint64_t q = mc[0].q, qinv = mc[0].qinv;
-    const uint64_t *c0 = ct + blockIdx.x * ct_words, *c1 = c0 + (int64_t)nl * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = add_mod(c0[k], mont_mul(c1[k], sk_mont[k], q, qinv), q);
+    const uint64_t *c0 = ct + item * ct_words + off, *c1 = ct + item * ct_words + (int64_t)nl * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = add_mod(c0[k], mont_mul(c1[k], sk_mont[off + k], q, qinv), q);
     __syncthreads();
-    ntt_inv_smem(s, twiddles(d_tw, 0, 1, logn), q, logn);
-    double *o = coeffs + (int64_t)blockIdx.x * N;
+    inv_any<CL>(s, twiddles(d_tw, 0, 1, logn), q, logn);
+    double *o = coeffs + (int64_t)item * N + off;
     const uint64_t half = q >> 1;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
         const uint64_t v = mul_shoup(s[SIDX(k)], mc[0].ninv, mc[0].ninv_shoup, q);
         o[k] = v > half ? -(double)(q - v) : (double)v;
     }
@@ -272,7 +276,12 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *) {
     const int64_t words = 2 * (int64_t)(level + 1) * ctx->n;
     ctx->launches++;
-    decrypt_kernel<<<count, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
+    if (use_cluster(ctx->log_n, count)) {
+        launch_cluster(decrypt_kernel<true>, count * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, ct, words,
+                       level + 1, (const uint64_t *)ctx->d_sk_mont, coeffs, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+        return;
+    }
+    decrypt_kernel<false><<<count, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
                                                                     ctx->log_n);
 }
 
@@ -317,5 +326,5 @@ void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, ui
 void encode_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(decrypt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(decrypt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }
