@@ -187,14 +187,27 @@ int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const h
 int he_batch_run(he_ctx *ctx, he_batch *batch, const he_ct *ins, he_ct *outs);
 void he_batch_free(he_batch *batch);
 
-/* Autotuning of the key-switch / multiply-accumulate loop kernel.  Its variants differ in
- * coefficients per thread (1 or 2) and rotation groups per block (4 or 8) and give identical
- * results; the first he_matmult_plain_cipher call with an encoded matrix, and the first
- * he_batch_run of a batch, time each variant once (synchronising the stream) and keep the
- * fastest.  These report the choice (variant 0..3, or -1 before the first call) and the timed
- * milliseconds of the four variants (ms4 may be NULL). */
-int he_ptmat_tuning(const he_ptmat *pm, int *variant, float *ms4);
-int he_batch_tuning(const he_batch *batch, int *variant, float *ms4);
+/* Autotuning of the key-switch / multiply-accumulate loop kernel.  Its variants give identical
+ * results and differ in coefficients per thread (1 or 2), rotation groups per block (4 or 8)
+ * and how the streamed key and plaintext operands are prefetched (registers, one rotation step
+ * ahead; or S = 3..4 steps ahead through a per-thread cp.async pipeline in shared memory).  The
+ * first he_matmult_plain_cipher call with an encoded matrix, and the first he_batch_run of a
+ * batch, time each variant once (synchronising the stream) and keep the fastest.
+ * he_loop_variant_count gives the number of variants (at most HE_MM_MAX_VARIANTS);
+ * he_loop_variant_shape the (vec, groups, stages) of variant v (HE_EINVAL if v is out of range).
+ * The tuning queries report the choice (-1 before the first call) and write the timed
+ * milliseconds of every variant to ms[0 .. count-1] (ms may be NULL; else it holds
+ * HE_MM_MAX_VARIANTS floats). */
+#define HE_MM_MAX_VARIANTS 8
+int he_loop_variant_count(void);
+int he_loop_variant_shape(int v, int *vec, int *groups, int *stages);
+int he_ptmat_tuning(const he_ptmat *pm, int *variant, float *ms);
+int he_batch_tuning(const he_batch *batch, int *variant, float *ms);
+/* Pin the loop-kernel variant of an encoded matrix or a batch (0 .. count-1), or with -1 let
+ * the next call tune again.  HE_EINVAL for NULL or v out of range.  A batch re-captures its
+ * graph on its next run (this call waits for the batch's previous run to finish). */
+int he_ptmat_set_variant(he_ptmat *pm, int v);
+int he_batch_set_variant(he_batch *batch, int v);
 
 /* Serving loop with continuous batching (requests of differing shapes, m, n <= N/2, at one
  * level).  A scheduler thread admits requests in arrival order while the device bytes they pin

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhe.so")
 SOURCES = ["he_api.cu", "he_ntt.cu", "he_ops.cu", "he_encode.cu", "he_noalloc.cu", "he_server.cu", "he_cdiag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "--fmad=false"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "--fmad=false"]
 
 
 def nvcc() -> str:

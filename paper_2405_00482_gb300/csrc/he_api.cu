@@ -765,7 +765,7 @@ void he_batch_free(he_batch *b) {
     if (b->stream) cudaStreamDestroy(b->stream);
     cudaFreeHost(b->h_jobs);
     cudaFree(b->d_jobs);
-    for (int v = 0; v < 4; ++v) cudaFree(b->d_order_v[v]);
+    for (int v = 0; v < HE_MM_MAX_VARIANTS; ++v) cudaFree(b->d_order_v[v]);
     cudaFree(b->d_counter);
     cudaFree(b->mem);
     delete b;
@@ -849,7 +849,7 @@ int batch_create_impl(he_ctx *ctx, int count, int level, const he_ptmat *const *
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->persistent_ctas = 2 * (sms > 0 ? sms : 1);
+    for (int v = 0; v < mm_variant_count(); ++v) b->ctas_v[v] = mm_batch_ctas_per_sm(v, mu.ndig) * (sms > 0 ? sms : 1);
     ok = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
@@ -946,19 +946,44 @@ int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
     return HE_OK;
 }
 
-int he_ptmat_tuning(const he_ptmat *pm, int *variant, float *ms4) {
-    if (!pm || !variant) return HE_EINVAL;
-    *variant = pm->variant;
-    if (ms4)
-        for (int v = 0; v < 4; ++v) ms4[v] = pm->tune_ms[v];
+int he_loop_variant_count(void) { return mm_variant_count(); }
+
+int he_loop_variant_shape(int v, int *vec, int *groups, int *stages) {
+    if (v < 0 || v >= mm_variant_count() || !vec || !groups || !stages) return HE_EINVAL;
+    mm_variant_shape(v, vec, groups, stages);
     return HE_OK;
 }
 
-int he_batch_tuning(const he_batch *b, int *variant, float *ms4) {
+int he_ptmat_tuning(const he_ptmat *pm, int *variant, float *ms) {
+    if (!pm || !variant) return HE_EINVAL;
+    *variant = pm->variant;
+    if (ms)
+        for (int v = 0; v < mm_variant_count(); ++v) ms[v] = pm->tune_ms[v];
+    return HE_OK;
+}
+
+int he_ptmat_set_variant(he_ptmat *pm, int v) {
+    if (!pm || v < -1 || v >= mm_variant_count()) return HE_EINVAL;
+    pm->variant = v;
+    return HE_OK;
+}
+
+int he_batch_set_variant(he_batch *b, int v) {
+    if (!b || v < -1 || v >= mm_variant_count()) return HE_EINVAL;
+    if (b->have_graph) {
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HE_ECUDA;
+        cudaGraphExecDestroy(b->exec);
+        b->have_graph = false;
+    }
+    b->variant = v;
+    return HE_OK;
+}
+
+int he_batch_tuning(const he_batch *b, int *variant, float *ms) {
     if (!b || !variant) return HE_EINVAL;
     *variant = b->variant;
-    if (ms4)
-        for (int v = 0; v < 4; ++v) ms4[v] = b->tune_ms[v];
+    if (ms)
+        for (int v = 0; v < mm_variant_count(); ++v) ms[v] = b->tune_ms[v];
     return HE_OK;
 }
 

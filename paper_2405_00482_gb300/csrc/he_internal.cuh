@@ -168,7 +168,7 @@ struct he_ptmat {
     std::vector<uint32_t> galois;
     uint32_t *d_galois;      // [m'-1]
     int variant = -1;        // loop-kernel variant chosen by timing (-1: not yet tuned)
-    float tune_ms[8] = {};
+    float tune_ms[HE_MM_MAX_VARIANTS] = {};
 };
 
 // a prepared batch of R = C = 1 MatMults at one level (he_batch_create)
@@ -178,12 +178,12 @@ struct he_batch {
     std::vector<const he_ptmat *> pms;
     MMJob *h_jobs;               // pinned host table, copied to d_jobs at the start of every run
     MMJob *d_jobs;
-    int32_t *d_order_v[4];       // work items (job, limb, tile) in issue order, per loop-kernel variant
-    int n_items_v[4];
+    int32_t *d_order_v[HE_MM_MAX_VARIANTS] = {};  // work items (job, limb, tile) in issue order, per loop-kernel variant
+    int n_items_v[HE_MM_MAX_VARIANTS] = {};
+    int ctas_v[HE_MM_MAX_VARIANTS] = {};           // persistent grid per variant (resident CTAs per SM x SMs)
     int variant = -1;            // chosen by timing on the first run (-1: not yet)
-    float tune_ms[4] = {};
+    float tune_ms[HE_MM_MAX_VARIANTS] = {};
     unsigned int *d_counter;     // work-queue head
-    int persistent_ctas;
     BatchGeom bg;
     uint64_t *mem;               // per-job scratch
     cudaStream_t stream;         // capture stream
@@ -195,6 +195,8 @@ struct he_batch {
 int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
 int mm_variant_count();
 int mm_variant_tile(int v);  // coefficients per tile of loop-kernel variant v
+void mm_variant_shape(int v, int *vec, int *grp, int *stages);
+int mm_batch_ctas_per_sm(int v, int ndig);
 int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc);
 // defined in he_api.cu (inside its extern "C" block)
 extern "C" {

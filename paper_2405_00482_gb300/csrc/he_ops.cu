@@ -315,13 +315,34 @@ __device__ __forceinline__ void stv(uint64_t *p, const uint64_t (&v)[VEC]) {
     }
 }
 
+// Asynchronous global -> shared copies of a thread's own operands.  Only the issuing thread
+// reads the destination (after cp_async_wait), so no block barrier is involved; the "memory"
+// clobbers keep the compiler from moving shared-memory reads across the issue or the wait.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint64_t *smem, const uint64_t *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
 // One tile: MM_THREADS / G lanes of VEC coefficients starting at coefficient k0 of extended
-// limb u.  Every thread of the block calls it (it synchronises once).  red: G*3*MM_THREADS words.
-template <int NDIG, int VEC, int G>
+// limb u.  Every thread of the block calls it (it synchronises once).  red: 3*VEC*MM_THREADS
+// words.  With S > 0 stages (fixed digit count only) each thread streams its key and plaintext
+// operands through S private stages of pipe (S*(2*NDIG+1)*VEC*MM_THREADS words), so S rotation
+// steps of HBM loads are in flight without occupying registers; the digit and c0 gathers, which
+// hit L2, keep the one-step register prefetch.
+template <int NDIG, int VEC, int G, int S>
 __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
                                         const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime,
                                         int ndig_rt, int ext, int nq, int L, int LK, int u, int p, int k0, uint64_t *acc, uint64_t *cacc,
-                                        int accumulate, const ModConst *__restrict__ mc, int logn, uint64_t *red) {
+                                        int accumulate, const ModConst *__restrict__ mc, int logn, uint64_t *red, uint64_t *pipe) {
     constexpr int LANES = MM_THREADS / G;
     const int N = 1 << logn;
     const int ndig = NDIG > 0 ? NDIG : ndig_rt;
@@ -341,60 +362,135 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
         for (int j = 0; j < VEC; ++j) t0[j] = t1[j] = tc[j] = 0;
         int pending = 0;
         constexpr int ND = NDIG > 0 ? NDIG : 8;
-        uint64_t dv[ND][VEC], kv0[ND][VEC], kv1[ND][VEC], pm[VEC], cv[VEC];
-        auto fetch = [&](int i) {
-            const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
-            const uint64_t *key = keys[i - 1];
+        constexpr int SP = NDIG > 0 ? S : 0;
+        if constexpr (SP > 0) {
+            // slot (stage, field f, thread) at pipe[((stage F + f) MM_THREADS + tid) VEC], F = 2 ND + 1
+            constexpr int F = 2 * ND + 1;
+            auto slot = [&](int st, int f) { return pipe + ((st * F + f) * MM_THREADS + (int)threadIdx.x) * VEC; };
+            auto issue = [&](int t) {
+                const int i = 1 + grp + t * G;
+                if (i < m_prime) {
+                    const uint64_t *key = keys[i - 1];
+                    const int st = t % SP;
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                if (NDIG == 0 && d >= ndig) break;
-                gatherv<VEC>(D + ((int64_t)d * ext + u) * N, src, dv[d]);
-                ldv<VEC>(key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k, kv0[d]);
-                ldv<VEC>(key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k, kv1[d]);
-            }
-            ldv<VEC>(pts + ((int64_t)i * ext + u) * N + k, pm);
-            if (inq) gatherv<VEC>(ct + (int64_t)u * N, src, cv);
-        };
-        int i = 1 + grp;
-        if (i < m_prime) fetch(i);
-        while (i < m_prime) {
-            u128 s0[VEC], s1[VEC];
+                    for (int d = 0; d < ND; ++d) {
+                        cp_async<8 * VEC>(slot(st, 2 * d), key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k);
+                        cp_async<8 * VEC>(slot(st, 2 * d + 1), key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k);
+                    }
+                    cp_async<8 * VEC>(slot(st, 2 * ND), pts + ((int64_t)i * ext + u) * N + k);
+                }
+                cp_async_commit();
+            };
+            uint64_t dv[ND][VEC], cv[VEC];
+            auto gather = [&](int t) {
+                const int i = 1 + grp + t * G;
+                if (i >= m_prime) return;
+                const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) s0[j] = s1[j] = 0;
+                for (int d = 0; d < ND; ++d) gatherv<VEC>(D + ((int64_t)d * ext + u) * N, src, dv[d]);
+                if (inq) gatherv<VEC>(ct + (int64_t)u * N, src, cv);
+            };
 #pragma unroll
-            for (int d = 0; d < ND; ++d) {
-                if (NDIG == 0 && d >= ndig) break;
+            for (int t = 0; t < SP; ++t) issue(t);
+            gather(0);
+            for (int t = 0; 1 + grp + t * G < m_prime; ++t) {
+                cp_async_wait<SP - 1>();
+                const int st = t % SP;
+                u128 s0[VEC], s1[VEC];
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) s0[j] = s1[j] = 0;
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    const uint64_t *a = slot(st, 2 * d), *b = slot(st, 2 * d + 1);
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        s0[j] += (u128)dv[d][j] * a[j];
+                        s1[j] += (u128)dv[d][j] * b[j];
+                    }
+                }
+                uint64_t pmc[VEC], c0v[VEC];
+                const uint64_t *pp = slot(st, 2 * ND);
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) {
-                    s0[j] += (u128)dv[d][j] * kv0[d][j];
-                    s1[j] += (u128)dv[d][j] * kv1[d][j];
+                    pmc[j] = pp[j];
+                    c0v[j] = cv[j];
                 }
-            }
-            uint64_t pmc[VEC], c0v[VEC];
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                pmc[j] = pm[j];
-                c0v[j] = cv[j];
-            }
-            const int next = i + G;
-            if (next < m_prime) fetch(next);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                t0[j] += (u128)fold(s0[j], q, qinv) * pmc[j];
-                t1[j] += (u128)fold(s1[j], q, qinv) * pmc[j];
-                if (inq) tc[j] += (u128)c0v[j] * pmc[j];
-            }
-            if (++pending == 8) {
+                issue(t + SP);
+                gather(t + 1);
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) {
-                    r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
-                    r1[j] = add_mod(r1[j], fold(t1[j], q, qinv), q);
-                    rc[j] = add_mod(rc[j], fold(tc[j], q, qinv), q);
-                    t0[j] = t1[j] = tc[j] = 0;
+                    t0[j] += (u128)fold(s0[j], q, qinv) * pmc[j];
+                    t1[j] += (u128)fold(s1[j], q, qinv) * pmc[j];
+                    if (inq) tc[j] += (u128)c0v[j] * pmc[j];
                 }
-                pending = 0;
+                if (++pending == 8) {
+#pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
+                        r1[j] = add_mod(r1[j], fold(t1[j], q, qinv), q);
+                        rc[j] = add_mod(rc[j], fold(tc[j], q, qinv), q);
+                        t0[j] = t1[j] = tc[j] = 0;
+                    }
+                    pending = 0;
+                }
             }
-            i = next;
+            cp_async_wait<0>();
+        } else {
+            uint64_t dv[ND][VEC], kv0[ND][VEC], kv1[ND][VEC], pm[VEC], cv[VEC];
+            auto fetch = [&](int i) {
+                const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
+                const uint64_t *key = keys[i - 1];
+    #pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    if (NDIG == 0 && d >= ndig) break;
+                    gatherv<VEC>(D + ((int64_t)d * ext + u) * N, src, dv[d]);
+                    ldv<VEC>(key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k, kv0[d]);
+                    ldv<VEC>(key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k, kv1[d]);
+                }
+                ldv<VEC>(pts + ((int64_t)i * ext + u) * N + k, pm);
+                if (inq) gatherv<VEC>(ct + (int64_t)u * N, src, cv);
+            };
+            int i = 1 + grp;
+            if (i < m_prime) fetch(i);
+            while (i < m_prime) {
+                u128 s0[VEC], s1[VEC];
+    #pragma unroll
+                for (int j = 0; j < VEC; ++j) s0[j] = s1[j] = 0;
+    #pragma unroll
+                for (int d = 0; d < ND; ++d) {
+                    if (NDIG == 0 && d >= ndig) break;
+    #pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        s0[j] += (u128)dv[d][j] * kv0[d][j];
+                        s1[j] += (u128)dv[d][j] * kv1[d][j];
+                    }
+                }
+                uint64_t pmc[VEC], c0v[VEC];
+    #pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                    pmc[j] = pm[j];
+                    c0v[j] = cv[j];
+                }
+                const int next = i + G;
+                if (next < m_prime) fetch(next);
+    #pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                    t0[j] += (u128)fold(s0[j], q, qinv) * pmc[j];
+                    t1[j] += (u128)fold(s1[j], q, qinv) * pmc[j];
+                    if (inq) tc[j] += (u128)c0v[j] * pmc[j];
+                }
+                if (++pending == 8) {
+    #pragma unroll
+                    for (int j = 0; j < VEC; ++j) {
+                        r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
+                        r1[j] = add_mod(r1[j], fold(t1[j], q, qinv), q);
+                        rc[j] = add_mod(rc[j], fold(tc[j], q, qinv), q);
+                        t0[j] = t1[j] = tc[j] = 0;
+                    }
+                    pending = 0;
+                }
+                i = next;
+            }
         }
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
@@ -460,25 +556,33 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
     }
 }
 
+// dynamic shared memory of the pipelined form
+constexpr size_t mm_pipe_bytes(int ndig, int vec, int stages) {
+    return ndig > 0 && stages > 0 ? (size_t)stages * (2 * ndig + 1) * MM_THREADS * vec * sizeof(uint64_t) : 0;
+}
+
 // single MatMult: block (coefficient tile, extended limb)
-template <int NDIG, int VEC, int G>
+template <int NDIG, int VEC, int G, int S>
 __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_loop_kernel(
     const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
     const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime, int ndig_rt, int ext, int nq, int L,
     int LK, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
     __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
+    extern __shared__ uint4 mm_pipe[];
     const int u = blockIdx.y;
-    mm_tile<NDIG, VEC, G>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq),
-                          blockIdx.x * (MM_THREADS / G) * VEC, acc, cacc, accumulate, mc, logn, red);
+    mm_tile<NDIG, VEC, G, S>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq),
+                             blockIdx.x * (MM_THREADS / G) * VEC, acc, cacc, accumulate, mc, logn, red,
+                             reinterpret_cast<uint64_t *>(mm_pipe));
 }
 
 // batch: persistent CTAs pull (tile, limb, job) items from an ordered queue
-template <int NDIG, int VEC, int G>
+template <int NDIG, int VEC, int G, int S>
 __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_loop_kernel(
     const MMJob *__restrict__ jobs, const int32_t *__restrict__ order, int n_items, unsigned int *counter, BatchGeom bg,
     const ModConst *__restrict__ mc, int logn) {
     __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
     __shared__ int item_s;
+    extern __shared__ uint4 mm_pipe[];
     const int N = 1 << logn;
     constexpr int TILE = (MM_THREADS / G) * VEC;
     const int tiles = (N + TILE - 1) / TILE;
@@ -493,9 +597,9 @@ __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_lo
         const int u = rest / tiles, tile = rest % tiles;
         const MMJob &jb = jobs[j];
         if (jb.m_prime == 0) continue;  // empty slot
-        mm_tile<NDIG, VEC, G>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L,
-                              bg.LK, u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * TILE, bg.acc + (int64_t)j * bg.acc_words,
-                              bg.cacc + (int64_t)j * bg.cacc_words, 0, mc, logn, red);
+        mm_tile<NDIG, VEC, G, S>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L,
+                                 bg.LK, u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * TILE, bg.acc + (int64_t)j * bg.acc_words,
+                                 bg.cacc + (int64_t)j * bg.cacc_words, 0, mc, logn, red, reinterpret_cast<uint64_t *>(mm_pipe));
         __syncthreads();
     }
 }
@@ -503,65 +607,80 @@ __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_lo
 }  // namespace
 
 // ---- variant dispatch ----
-// variant v: (VEC, G) = {0: (2, 4), 1: (1, 4), 2: (1, 8), 3: (2, 8)}
-int mm_variant_count() { return 4; }
-int mm_variant_tile(int v) {
-    static const int vec[4] = {2, 1, 1, 2}, grp[4] = {4, 4, 8, 8};
-    return (MM_THREADS / grp[v]) * vec[v];
+// variant v: (coefficients per thread VEC, rotation groups G, cp.async stages S); S = 0 is the
+// register-prefetch form
+struct MMShape {
+    int vec, grp, stages;
+};
+constexpr MMShape kMMShapes[] = {{2, 4, 0}, {1, 4, 0}, {1, 8, 0}, {2, 8, 0}, {2, 4, 3}, {1, 4, 4}, {1, 8, 3}};
+constexpr int kMMVariants = (int)(sizeof(kMMShapes) / sizeof(kMMShapes[0]));
+static_assert(kMMVariants <= HE_MM_MAX_VARIANTS, "variant table");
+
+int mm_variant_count() { return kMMVariants; }
+int mm_variant_tile(int v) { return (MM_THREADS / kMMShapes[v].grp) * kMMShapes[v].vec; }
+void mm_variant_shape(int v, int *vec, int *grp, int *stages) {
+    *vec = kMMShapes[v].vec;
+    *grp = kMMShapes[v].grp;
+    *stages = kMMShapes[v].stages;
 }
 
 namespace {
 
-template <int NDIG, int VEC, int G>
-static void mm_launch_single(he_ctx *ctx, dim3 grid, const uint64_t *ct, const uint64_t *D, const uint64_t *pts, const uint64_t *const *keys,
-                             const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
-    matmult_loop_kernel<NDIG, VEC, G><<<grid, MM_THREADS, 0, ctx->stream>>>(ct, D, pts, keys, galois, m_prime, ndig, ext, nq, ctx->L,
-                                                                          ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n);
-}
-
-template <int VEC, int G>
-static void mm_launch_single_nd(he_ctx *ctx, dim3 grid, const uint64_t *ct, const uint64_t *D, const uint64_t *pts, const uint64_t *const *keys,
-                                const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
-    switch (ndig) {
-        case 1: mm_launch_single<1, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
-        case 2: mm_launch_single<2, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
-        case 3: mm_launch_single<3, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
-        default: mm_launch_single<0, VEC, G>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
+// calls f.template operator()<NDIG, VEC, G, S>() for variant v and digit count ndig (NDIG = 0:
+// any digit count, register form)
+template <typename F>
+void mm_dispatch(int v, int ndig, F &&f) {
+    auto nd = [&](auto vec, auto grp, auto st) {
+        constexpr int VEC = decltype(vec)::value, G = decltype(grp)::value, S = decltype(st)::value;
+        switch (ndig) {
+            case 1: f.template operator()<1, VEC, G, S>(); break;
+            case 2: f.template operator()<2, VEC, G, S>(); break;
+            case 3: f.template operator()<3, VEC, G, S>(); break;
+            default: f.template operator()<0, VEC, G, 0>(); break;
+        }
+    };
+    using std::integral_constant;
+    switch (v) {
+        case 1: nd(integral_constant<int, 1>{}, integral_constant<int, 4>{}, integral_constant<int, 0>{}); break;
+        case 2: nd(integral_constant<int, 1>{}, integral_constant<int, 8>{}, integral_constant<int, 0>{}); break;
+        case 3: nd(integral_constant<int, 2>{}, integral_constant<int, 8>{}, integral_constant<int, 0>{}); break;
+        case 4: nd(integral_constant<int, 2>{}, integral_constant<int, 4>{}, integral_constant<int, 3>{}); break;
+        case 5: nd(integral_constant<int, 1>{}, integral_constant<int, 4>{}, integral_constant<int, 4>{}); break;
+        case 6: nd(integral_constant<int, 1>{}, integral_constant<int, 8>{}, integral_constant<int, 3>{}); break;
+        default: nd(integral_constant<int, 2>{}, integral_constant<int, 4>{}, integral_constant<int, 0>{}); break;
     }
 }
+
+}  // namespace
 
 void mm_launch_variant(he_ctx *ctx, int v, const uint64_t *ct, const uint64_t *D, const uint64_t *pts, const uint64_t *const *keys,
                        const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
     const dim3 grid((unsigned)((ctx->n + mm_variant_tile(v) - 1) / mm_variant_tile(v)), (unsigned)ext);
     ctx->launches++;
-    switch (v) {
-        case 1: mm_launch_single_nd<1, 4>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
-        case 2: mm_launch_single_nd<1, 8>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
-        case 3: mm_launch_single_nd<2, 8>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
-        default: mm_launch_single_nd<2, 4>(ctx, grid, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, acc, cacc, accumulate); break;
-    }
-}
-
-template <int VEC, int G>
-static void mm_launch_batch_nd(int ndig, dim3 grid, cudaStream_t st, const MMJob *jobs, const int32_t *order, int n_items, unsigned int *counter,
-                               const BatchGeom &bg, const ModConst *mc, int logn) {
-    switch (ndig) {
-        case 1: matmult_batch_loop_kernel<1, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
-        case 2: matmult_batch_loop_kernel<2, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
-        case 3: matmult_batch_loop_kernel<3, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
-        default: matmult_batch_loop_kernel<0, VEC, G><<<grid, MM_THREADS, 0, st>>>(jobs, order, n_items, counter, bg, mc, logn); break;
-    }
+    mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S>() {
+        matmult_loop_kernel<NDIG, VEC, G, S><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S), ctx->stream>>>(
+            ct, D, pts, keys, galois, m_prime, ndig, ext, nq, ctx->L, ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n);
+    });
 }
 
 void mm_launch_batch_variant(int v, dim3 grid, cudaStream_t st, const MMJob *jobs, const int32_t *order, int n_items, unsigned int *counter,
                              const BatchGeom &bg, const ModConst *mc, int logn) {
-    switch (v) {
-        case 1: mm_launch_batch_nd<1, 4>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
-        case 2: mm_launch_batch_nd<1, 8>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
-        case 3: mm_launch_batch_nd<2, 8>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
-        default: mm_launch_batch_nd<2, 4>(bg.ndig, grid, st, jobs, order, n_items, counter, bg, mc, logn); break;
-    }
+    mm_dispatch(v, bg.ndig, [&]<int NDIG, int VEC, int G, int S>() {
+        matmult_batch_loop_kernel<NDIG, VEC, G, S><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S), st>>>(jobs, order, n_items, counter, bg,
+                                                                                                           mc, logn);
+    });
 }
+
+// resident CTAs per SM of the batch kernel of variant v (the persistent grid is this times the SMs)
+int mm_batch_ctas_per_sm(int v, int ndig) {
+    int n = 0;
+    mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S>() {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matmult_batch_loop_kernel<NDIG, VEC, G, S>, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S));
+    });
+    return n > 0 ? n : 1;
+}
+
+namespace {
 
 // ---- cleartext layout (Eq. 2 after Eq. 3) and lazy rotate-and-sum (Sec. 4.3) ----
 __global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, double *out, int64_t total) {
@@ -808,8 +927,8 @@ int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), stream) != cudaSuccess) return HE_ECUDA;
     batch_intt_c1_kernel<<<count * bg.nq, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
     batch_modup_kernel<<<count * mu.ndig * mu.ext, thr, smem, stream>>>(b->d_jobs, bg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    const dim3 pgrid(b->persistent_ctas);
     const int v = b->variant < 0 ? 0 : b->variant;
+    const dim3 pgrid((unsigned)b->ctas_v[v]);
     mm_launch_batch_variant(v, pgrid, stream, b->d_jobs, b->d_order_v[v], b->n_items_v[v], b->d_counter, bg, ctx->d_mc, ctx->log_n);
     batch_intt_p_kernel<<<count * 2 * bg.K, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
     batch_moddown_kernel<<<count * 2 * md.nq, thr, smem, stream>>>(b->d_jobs, bg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
@@ -830,4 +949,16 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(modup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(moddown_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    for (int v = 0; v < kMMVariants; ++v)
+        for (int nd = 0; nd <= 3; ++nd)
+            mm_dispatch(v, nd, []<int NDIG, int VEC, int G, int S>() {
+                const int bytes = (int)mm_pipe_bytes(NDIG, VEC, S);
+                if (bytes == 0) return;
+                cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                cudaFuncSetAttribute(matmult_batch_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+                cudaFuncSetAttribute(matmult_batch_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+            });
 }

@@ -74,6 +74,11 @@ _SIGS = {
     "he_batch_free": (None, [_vp]),
     "he_ptmat_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "he_batch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "he_loop_variant_count": (ctypes.c_int, []),
+    "he_ptmat_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "he_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "he_loop_variant_shape": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]),
     "he_cdiag_encode_weights": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_cdmat_free": (None, [_vp]),
     "he_cdiag_encode_matrix": (ctypes.c_int, [_vp, _vp, _i64, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
@@ -181,11 +186,25 @@ class Plaintext:
         return HePt(self.data.data_ptr(), self.level, self.scale)
 
 
+HE_MM_MAX_VARIANTS = 8
+
+
+def loop_variants() -> list:
+    """(coefficients per thread, rotation groups, cp.async stages) of every loop-kernel variant."""
+    out = []
+    for v in range(_lib().he_loop_variant_count()):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().he_loop_variant_shape(v, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "he_loop_variant_shape")
+        out.append((a.value, b.value, c.value))
+    return out
+
+
 def _tuning(fn, handle) -> dict:
     v = ctypes.c_int()
-    ms = (ctypes.c_float * 4)()
+    ms = (ctypes.c_float * HE_MM_MAX_VARIANTS)()
     _check(fn(handle, ctypes.byref(v), ms), "tuning")
-    return {"variant": int(v.value), "variant_ms": [round(float(x), 4) for x in ms]}
+    n = _lib().he_loop_variant_count()
+    return {"variant": int(v.value), "variant_ms": [round(float(x), 4) for x in ms[:n]]}
 
 
 class PtMatrix:
@@ -195,6 +214,10 @@ class PtMatrix:
     def tuning(self) -> dict:
         """Loop-kernel variant chosen on the first MatMult and the timed ms of each variant."""
         return _tuning(_lib().he_ptmat_tuning, self.handle)
+
+    def set_variant(self, v: int) -> None:
+        """Pin the loop-kernel variant (-1: tune again on the next MatMult)."""
+        _check(_lib().he_ptmat_set_variant(self.handle, v), "he_ptmat_set_variant")
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -216,6 +239,10 @@ class Batch:
 
     def tuning(self) -> dict:
         return _tuning(_lib().he_batch_tuning, self.handle)
+
+    def set_variant(self, v: int) -> None:
+        """Pin the loop-kernel variant (-1: tune again on the next run)."""
+        _check(_lib().he_batch_set_variant(self.handle, v), "he_batch_set_variant")
 
     def run(self, cts: list[Ciphertext], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
         outs = outs or [self.ctx.new_ct(self.level - 1) for _ in cts]

@@ -70,3 +70,20 @@ def test_invalid_arguments_are_rejected(he):
     with pytest.raises(he.HEError):
         he.primes(13, [60, 40], [60], 3)  # more digits than primes
     assert he.lib().he_strerror(he.HE_EKEY) == b"missing Galois key"
+
+
+def test_loop_variant_table_and_argument_checks(he):
+    """The variant table is host data: readable without a device.  Out-of-range variants and
+    NULL handles are rejected before anything touches the GPU."""
+    shapes = he.loop_variants()
+    assert 7 <= len(shapes) <= he.HE_MM_MAX_VARIANTS
+    assert all(vec in (1, 2) and grp in (4, 8) and st >= 0 for vec, grp, st in shapes)
+    assert shapes[0] == (2, 4, 0)
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    lib = he.lib()
+    for v in (-1, len(shapes)):
+        assert lib.he_loop_variant_shape(v, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == he.HE_EINVAL
+    assert lib.he_ptmat_set_variant(None, 0) == he.HE_EINVAL
+    assert lib.he_batch_set_variant(None, 0) == he.HE_EINVAL
+    ms = (ctypes.c_float * he.HE_MM_MAX_VARIANTS)()
+    assert lib.he_ptmat_tuning(None, ctypes.byref(a), ms) == he.HE_EINVAL
