@@ -133,6 +133,9 @@ def run_gpu(args):
     # device buffers reused by every step: encoded matrices, vector plaintexts, ciphertexts
     pm_g = ctx.encode_matrix(plan_g, dXT, level)
     pm_f = ctx.encode_matrix(plan_f, dX, level)
+    if args.loop_variant >= 0:
+        pm_g.set_variant(args.loop_variant)
+        pm_f.set_variant(args.loop_variant)
     pt_r, pt_w = ctx.new_pt(level), ctx.new_pt(level)
     ct_r, ct_w = ctx.new_ct(level), ctx.new_ct(level)
 
@@ -254,7 +257,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "autotune": {"plain_gradient": pm_g.tuning(), "plain_forward": pm_f.tuning(),
-                     "variants": "loop kernel (coefficients per thread, rotation groups): 0 (2,4), 1 (1,4), 2 (1,8), 3 (2,8)"},
+                     "variants": "loop kernel (coefficients per thread, rotation groups, cp.async stages, gathers staged): "
+                                 + ", ".join(f"{v} {s}" for v, s in enumerate(he.loop_variants()))},
         "clocks": clocks,
     }
     line["rotations"] = run_rotations(ctx, he, P, args, flush, world, dev)
@@ -262,6 +266,10 @@ def run_gpu(args):
         line["batched"] = run_batched(ctx, he, inputs, P, args, flush, world, dev)
     if not args.no_serving and rank == 0:
         line["serving"] = run_serving(ctx, he, inputs, P, args, dev)
+    if not args.no_small:
+        line["small"] = run_small(he, inputs, args, flush, world, dev, rank)
+    if not args.no_vfl_nn:
+        line["vfl_nn"] = run_vfl_nn(he, inputs, args, flush, world, dev, rank)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -303,6 +311,119 @@ def run_rotations(ctx, he, P, args, flush, world, dev):
     return {"single_per_sec": round(n / t_single, 1), "hoisted_per_sec": round(n / t_hoist, 1), "unit": "rotations/s",
             "workload": "RotL by 1..63 of one ciphertext, N=8192, Q=[60,40,40], P=[60], dnum=3; O3 = one call per rotation, "
                         "O4 = one hoisted call for all 63"}
+
+
+def _event_times(fn, reps, flush, warm=3):
+    """Device milliseconds of fn() per repetition (CUDA events on the current stream, L2 flushed
+    before each)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(reps):
+        flush.add_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _pct(times, q):
+    t = sorted(times)
+    return round(t[min(len(t) - 1, int(q * len(t)))], 4)
+
+
+def run_small(he, inputs, args, flush, world, dev, rank):
+    """The N = 4096 gradient X^T [[r]] (X 64x16, chain [40, 20 | 40], scale 2^20; m = 16, n = 64,
+    m' = 1: no rotation): one plain MatMult call, and the whole path from fp64 inputs to the
+    decoded result, device time."""
+    import numpy as np
+    import torch
+
+    P = inputs.PARAMS_SMALL
+    ctx = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=100 + rank)
+    X, r = inputs.gradient_small(seed=rank)
+    XT = np.ascontiguousarray(X.T)
+    plan = he.Plan(16, 64, P.slots)
+    ctx.keygen(list(range(1, plan.m_prime)))
+    level = P.top
+    dXT, dr = torch.from_numpy(XT).to(dev), torch.from_numpy(r).to(dev)
+    pm = ctx.encode_matrix(plan, dXT, level)
+    pt, ct = ctx.new_pt(level), ctx.new_ct(level)
+    out = [ctx.new_ct(level - 1)]
+    slots = torch.empty((1, P.slots), dtype=torch.float64, device=dev)
+    res = torch.empty(16, dtype=torch.float64, device=dev)
+
+    def path(i):
+        ctx.encode_matrix(plan, dXT, level, out=pm)
+        ctx.encode_vector(plan, dr, P.scale, level, outs=[pt])
+        ctx.encrypt(pt, i, out=ct)
+        ctx.matmult(plan, pm, [ct], out)
+        ctx.decrypt(out[0], slots[0])
+        ctx.matmult_decode(plan, slots, res)
+
+    path(1)
+    torch.cuda.synchronize()
+    err = float(np.abs(res.cpu().numpy() - XT @ r).max())
+    reps = max(args.steps, 10)
+    t_mm = _event_times(lambda: ctx.matmult(plan, pm, [ct], out), reps, flush)
+    cnt = iter(range(10**6))
+    t_path = _event_times(lambda: path(2 + next(cnt)), reps, flush)
+    s_mm = max_over_ranks(sum(t_mm) / 1e3, world, dev)
+    return {"workload": "gradient X^T[[r]], X 64x16 ~ N(0,1), r ~ U[-1,1], N=4096, Q=[40,20], P=[40], dnum=2, scale 2^20 (m'=1)",
+            "matmult_per_sec": round(whole_job_rate(reps, world, s_mm), 1), "matmult_ms": {"p50": _pct(t_mm, 0.5), "p99": _pct(t_mm, 0.99)},
+            "path_ms": {"p50": _pct(t_path, 0.5), "p99": _pct(t_path, 0.99)}, "max_abs_err": err, "tolerance": 5e-2}
+
+
+def run_vfl_nn(he, inputs, args, flush, world, dev, rank):
+    """VFL neural layer at N = 16384 (Alg. 3 and the transposed-diagonal conversion): forward
+    [[A]] W with A 4096x256 encrypted as its 256 diagonals and W 256x128 (128 output
+    ciphertexts); backward [[A^T]] D^T with [[A^T]]'s diagonals rotated out of [[A]]'s (255
+    key switches) and D^T 4096x128."""
+    import numpy as np
+    import torch
+
+    P = inputs.PARAMS_N16384
+    ctx = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=200 + rank)
+    A, W, Dt = inputs.vfl_nn_layer(seed=rank)
+    m, n, K = 4096, 256, 128
+    level = P.top
+    cts = [ctx.encrypt(p, 10 + i) for i, p in enumerate(ctx.cdiag_encode_matrix(torch.from_numpy(A).to(dev), P.scale, level))]
+    Wm = he.WeightMatrix(ctx, torch.from_numpy(W).to(dev), level)
+    Dm = he.WeightMatrix(ctx, torch.from_numpy(Dt).to(dev), level)
+    ctx.keygen(he.Context.cdiag_transpose_steps(m, n))
+    fwd_out = [ctx.new_ct(level - 1) for _ in range(K)]
+    bwd_out = [ctx.new_ct(level - 1) for _ in range(K)]
+    ctx.cdiag_matmult(Wm, cts, fwd_out)
+    tcts = ctx.cdiag_transpose(cts, m, n)
+    ctx.cdiag_matmult(Dm, tcts, bwd_out)
+    Z = ctx.cdiag_decode(m, n, torch.stack([ctx.decrypt(c) for c in fwd_out])).cpu().numpy()
+    G = ctx.cdiag_decode(n, m, torch.stack([ctx.decrypt(c) for c in bwd_out])).cpu().numpy()
+    err = max(float(np.abs(Z - A @ W).max()), float(np.abs(G - A.T @ Dt).max()))
+    reps = max(3, min(args.steps, 10))
+    t_fwd = _event_times(lambda: ctx.cdiag_matmult(Wm, cts, fwd_out), reps, flush, warm=1)
+    t_tr = _event_times(lambda: ctx.cdiag_transpose(cts, m, n), reps, flush, warm=1)
+    t_bwd = _event_times(lambda: ctx.cdiag_matmult(Dm, tcts, bwd_out), reps, flush, warm=1)
+    s_fwd = max_over_ranks(sum(t_fwd) / 1e3, world, dev)
+    macs = K * (level + 1) * P.n * 2 * n  # 64-bit modular multiply-adds of one forward product
+    fwd_ms = statistics.median(t_fwd)
+    # ALU peak: 64 32-bit IMAD per SM per clock x 152 SMs x 2.07 GHz, 4 IMAD per 64x64 -> 128-bit product
+    peak = 64 * 152 * 2.07e9 / 4 / 1e12
+    achieved = macs / (fwd_ms / 1e3) / 1e12
+    return {"workload": "A 4096x256 ~ U[-1,1] as 256 diagonal ciphertexts, W 256x128 ~ N(0,1/256), D^T 4096x128 ~ N(0,1/4096); "
+                        "N=16384, Q=[60,40x6], P=[60,60,60], dnum=3, scale 2^40",
+            "forward_per_sec": round(whole_job_rate(reps, world, s_fwd), 2), "forward_ms": {"p50": _pct(t_fwd, 0.5), "p99": _pct(t_fwd, 0.99)},
+            "transpose_ms": {"p50": _pct(t_tr, 0.5), "p99": _pct(t_tr, 0.99), "key_switches": len(he.Context.cdiag_transpose_steps(m, n))},
+            "backward_matmult_ms": {"p50": _pct(t_bwd, 0.5), "p99": _pct(t_bwd, 0.99)}, "max_abs_err": err,
+            "roofline": {"kernel": "cdiag_mac_kernel (+ rescale, whole call)", "bound": "alu", "achieved": round(achieved, 3),
+                         "peak": round(peak, 3), "unit": "T modmul-add/s", "frac": round(achieved / peak, 4),
+                         "peak_source": "derived: 64 IMAD/clk/SM x 152 SMs x 2070 MHz / 4 IMAD per 64-bit product"}}
 
 
 def run_batched(ctx, he, inputs, P, args, flush, world, dev):
@@ -512,6 +633,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-vfl-nn", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--loop-variant", type=int, default=-1,
+                    help="pin the MatMult loop-kernel variant of the plain products (default: autotune)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -117,6 +117,10 @@ int he_decrypt(he_ctx *ctx, const he_ct *ct, double *slots_out);
 
 /* O1 (Sec. 2.2): out = a + b (same level and scale). out may alias a or b. */
 int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out);
+/* O1 with a plaintext operand (Sec. 2.2; the replicated d = u_A + (u_B - y) and the random
+ * masks of Alg. 1): out = (c0 + pt, c1).  pt at a level >= ct's and at the ct's scale
+ * (HE_ESCALE otherwise).  out may alias ct. */
+int he_add_plain(he_ctx *ctx, const he_ct *ct, const he_pt *pt, he_ct *out);
 /* O2 (Sec. 2.2): out = pt (x) ct slot-wise, scale multiplies; pt at a level >= ct's. */
 int he_mul_plain(he_ctx *ctx, const he_ct *ct, const he_pt *pt, he_ct *out);
 /* Rescale by the last prime: level -> level-1, scale / q_level (rounding division). */
@@ -189,18 +193,19 @@ void he_batch_free(he_batch *batch);
 
 /* Autotuning of the key-switch / multiply-accumulate loop kernel.  Its variants give identical
  * results and differ in coefficients per thread (1 or 2), rotation groups per block (4 or 8)
- * and how the streamed key and plaintext operands are prefetched (registers, one rotation step
- * ahead; or S = 3..4 steps ahead through a per-thread cp.async pipeline in shared memory).  The
- * first he_matmult_plain_cipher call with an encoded matrix, and the first he_batch_run of a
- * batch, time each variant once (synchronising the stream) and keep the fastest.
- * he_loop_variant_count gives the number of variants (at most HE_MM_MAX_VARIANTS);
- * he_loop_variant_shape the (vec, groups, stages) of variant v (HE_EINVAL if v is out of range).
- * The tuning queries report the choice (-1 before the first call) and write the timed
- * milliseconds of every variant to ms[0 .. count-1] (ms may be NULL; else it holds
+ * and how each rotation step's operands are prefetched: in registers one step ahead, or S
+ * steps ahead through a per-thread cp.async pipeline in shared memory that carries the key and
+ * plaintext streams and, in the "gathers" variants, the automorphism gathers of the ModUp
+ * digits and c0 too.  The first he_matmult_plain_cipher call with an encoded matrix, and the
+ * first he_batch_run of a batch, time each variant once (synchronising the stream) and keep the
+ * fastest.  he_loop_variant_count gives the number of variants (at most HE_MM_MAX_VARIANTS);
+ * he_loop_variant_shape the (vec, groups, stages, gathers) of variant v (HE_EINVAL if v is out
+ * of range).  The tuning queries report the choice (-1 before the first call) and write the
+ * timed milliseconds of every variant to ms[0 .. count-1] (ms may be NULL; else it holds
  * HE_MM_MAX_VARIANTS floats). */
 #define HE_MM_MAX_VARIANTS 8
 int he_loop_variant_count(void);
-int he_loop_variant_shape(int v, int *vec, int *groups, int *stages);
+int he_loop_variant_shape(int v, int *vec, int *groups, int *stages, int *gathers);
 int he_ptmat_tuning(const he_ptmat *pm, int *variant, float *ms);
 int he_batch_tuning(const he_batch *batch, int *variant, float *ms);
 /* Pin the loop-kernel variant of an encoded matrix or a batch (0 .. count-1), or with -1 let
@@ -258,6 +263,20 @@ int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_c
 /* P_B's side after decryption: lazy rotate-and-sum (Sec. 4.3).  slots: device
  * [row_blocks][N/2] doubles (he_decrypt of each output), y_out: device m doubles. */
 int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out);
+/* Alg. 1's last step: remove a slot mask (device [row_blocks][N/2] doubles, the values that
+ * were encoded and added with he_add_plain before decryption; NULL = none) and apply the lazy
+ * rotate-and-sum: y = lazyRaS(slots - mask). */
+int he_matmult_decode_masked(he_ctx *ctx, const he_plan *plan, const double *slots, const double *mask, double *y_out);
+
+/* The ciphertext rotate-and-sum that the lazy RaS replaces (Sec. 3, Sec. 4.3), for consumers
+ * that need the sums inside the ciphertext: for each step m' 2^j, j < log2(nb / m'), in turn,
+ * x <- x + RotL(x, step).  Afterwards slot b nb + t of row block r's ciphertext holds output
+ * row r mb + b m' + t.  he_plan_ras_steps lists the steps (steps may be NULL to count them;
+ * at most 40); he_ras needs their Galois keys (HE_EKEY) and runs on one row block's output
+ * ciphertext (out may alias in).  he_ras_decode gathers y from the decrypted slots [R][N/2]. */
+int he_plan_ras_steps(const he_plan *plan, int32_t *steps, int *n_steps);
+int he_ras(he_ctx *ctx, const he_plan *plan, const he_ct *in, he_ct *out);
+int he_ras_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out);
 
 /* Canonical coefficient form (device, [2][level+1][N]) of a ciphertext, and back. */
 int he_ct_export(he_ctx *ctx, const he_ct *ct, uint64_t *coeffs_out);

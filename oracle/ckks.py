@@ -62,6 +62,7 @@ def lib():
             "or_encrypt": (None, [P, u64, _i64p, u64, i32, _u64p, _u64p]),
             "or_decrypt": (None, [P, _i64p, i32, _u64p, _u64p]),
             "or_add": (None, [P, i32, _u64p, _u64p, _u64p]),
+            "or_add_plain": (None, [P, i32, _u64p, _u64p, _u64p]),
             "or_mul_plain": (None, [P, i32, _u64p, _u64p, _u64p]),
             "or_modup": (None, [P, i32, _u64p, _u64p]),
             "or_moddown": (None, [P, i32, _u64p, _u64p]),
@@ -194,6 +195,22 @@ class Oracle:
         lib().or_add(ctypes.byref(self.params), x.level, x.data.reshape(-1), y.data.reshape(-1), out.reshape(-1))
         self.counts.add += 1
         return Ciphertext(out, x.level, x.scale)
+
+    def add_plain(self, ct: Ciphertext, pt: np.ndarray) -> Ciphertext:
+        """O1 with a plaintext encoded at the ciphertext's scale (Sec. 2.2): (c0 + m, c1)."""
+        out = np.zeros_like(ct.data)
+        lib().or_add_plain(ctypes.byref(self.params), ct.level, ct.data.reshape(-1),
+                           np.ascontiguousarray(pt[: ct.level + 1]).reshape(-1), out.reshape(-1))
+        self.counts.add += 1
+        return Ciphertext(out, ct.level, ct.scale)
+
+    def ras(self, ct: Ciphertext, plan: layout.Plan) -> Ciphertext:
+        """Ciphertext rotate-and-sum, the step the lazy RaS of Sec. 4.3 replaces: for each step
+        r of layout.ras_steps, ct <- ct + RotL(ct, r); slot r*... b*nb + t then holds output
+        row b*m' + t of its row block."""
+        for r in layout.ras_steps(plan):
+            ct = self.add(ct, self.rotate(ct, r))
+        return ct
 
     def mul_plain(self, ct: Ciphertext, pt: np.ndarray, pt_scale: float) -> Ciphertext:
         out = np.zeros_like(ct.data)

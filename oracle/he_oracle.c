@@ -368,6 +368,18 @@ void or_add(const or_params *p, int level, const uint64_t *x, const uint64_t *y,
         }
 }
 
+/* O1 with a plaintext operand: (c0 + m, c1) (the decryption c0 + c1 s gains m) */
+void or_add_plain(const or_params *p, int level, const uint64_t *ct, const uint64_t *pt, uint64_t *out) {
+    int n = p->n, nl = level + 1;
+    for (int l = 0; l < nl; ++l) {
+        uint64_t q = p->primes[l];
+        for (int k = 0; k < n; ++k) {
+            out[(size_t)l * n + k] = addmod(ct[(size_t)l * n + k], pt[(size_t)l * n + k], q);
+            out[((size_t)nl + l) * n + k] = ct[((size_t)nl + l) * n + k];
+        }
+    }
+}
+
 /* O2: plaintext x ciphertext (each component times the plaintext polynomial) */
 void or_mul_plain(const or_params *p, int level, const uint64_t *ct, const uint64_t *pt, uint64_t *out) {
     int n = p->n, nl = level + 1;

@@ -132,6 +132,31 @@ def rotl(v: np.ndarray, i: int) -> np.ndarray:
     return np.roll(v, -i)
 
 
+def ras_steps(plan: Plan) -> list[int]:
+    """Rotation steps of the ciphertext rotate-and-sum (Sec. 3 / Sec. 4.3): m' * 2^j for
+    j < log2(nb / m'), applied one after the other as x <- x + RotL(x, step).  Afterwards slot
+    b*nb + t holds sum_{s < nb/m'} x[b*nb + t + s*m'] for t < m' (the blocks never mix, since
+    t + (nb/m' - 1) m' < nb)."""
+    steps, step = [], plan.m_prime
+    while step < plan.nb:
+        steps.append(step)
+        step *= 2
+    return steps
+
+
+def ras_decode(slots: np.ndarray, plan: Plan) -> np.ndarray:
+    """After the ciphertext RaS: out[r*mb + b*m' + t] = slot_r[b*nb + t]."""
+    out = np.zeros(plan.mp, dtype=np.float64)
+    mpr, nb, mb = plan.m_prime, plan.nb, plan.mb
+    t = np.arange(mpr)
+    for r in range(plan.row_blocks):
+        for b in range(plan.blocks):
+            row = r * mb + b * mpr + t
+            ok = row < plan.mp
+            out[row[ok]] = slots[r][b * nb + t][ok]
+    return out[: plan.m]
+
+
 def lazy_ras(slots: np.ndarray, plan: Plan) -> np.ndarray:
     """Lazy rotate-and-sum after decryption (Sec. 4.3), slots shape [R][N'] -> X y (length m).
 

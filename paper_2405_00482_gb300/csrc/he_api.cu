@@ -504,6 +504,20 @@ int he_add(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out) {
     return last_launch();
 }
 
+int he_add_plain(he_ctx *ctx, const he_ct *ct, const he_pt *pt, he_ct *out) {
+    if (!ctx || !ct || !pt || !out || !ct->data || !pt->data || !out->data) return HE_EINVAL;
+    if (ct->level < 0 || ct->level >= ctx->L || pt->level < ct->level) return HE_ELEVEL;
+    if (fabs(ct->scale - pt->scale) > 1e-9 * fabs(ct->scale)) return HE_ESCALE;
+    const size_t nl = ct->level + 1, N = ctx->n;
+    if (out->data != ct->data &&
+        cudaMemcpyAsync(out->data + nl * N, ct->data + nl * N, nl * N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+        return HE_ECUDA;
+    launch_add(ctx, ct->data, pt->data, out->data, 1, qmap(ct->level));
+    out->level = ct->level;
+    out->scale = ct->scale;
+    return last_launch();
+}
+
 int he_mul_plain(he_ctx *ctx, const he_ct *ct, const he_pt *pt, he_ct *out) {
     if (!ctx || !ct || !pt || !out || !ct->data || !pt->data || !out->data) return HE_EINVAL;
     if (ct->level < 0 || ct->level >= ctx->L || pt->level < ct->level) return HE_ELEVEL;
@@ -948,9 +962,9 @@ int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
 
 int he_loop_variant_count(void) { return mm_variant_count(); }
 
-int he_loop_variant_shape(int v, int *vec, int *groups, int *stages) {
-    if (v < 0 || v >= mm_variant_count() || !vec || !groups || !stages) return HE_EINVAL;
-    mm_variant_shape(v, vec, groups, stages);
+int he_loop_variant_shape(int v, int *vec, int *groups, int *stages, int *gathers) {
+    if (v < 0 || v >= mm_variant_count() || !vec || !groups || !stages || !gathers) return HE_EINVAL;
+    mm_variant_shape(v, vec, groups, stages, gathers);
     return HE_OK;
 }
 
@@ -988,8 +1002,65 @@ int he_batch_tuning(const he_batch *b, int *variant, float *ms) {
 }
 
 int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out) {
+    return he_matmult_decode_masked(ctx, plan, slots, nullptr, y_out);
+}
+
+int he_matmult_decode_masked(he_ctx *ctx, const he_plan *plan, const double *slots, const double *mask, double *y_out) {
     if (!ctx || !plan || !slots || !y_out || plan->slots != ctx->n / 2) return HE_EINVAL;
-    launch_lazy_ras(ctx, *plan, slots, y_out);
+    launch_lazy_ras(ctx, *plan, slots, mask, y_out);
+    return last_launch();
+}
+
+int he_plan_ras_steps(const he_plan *p, int32_t *steps, int *n_steps) {
+    if (!p || !n_steps) return HE_EINVAL;
+    int n = 0;
+    for (int64_t step = p->m_prime; step < p->nb; step *= 2) {
+        if (steps) steps[n] = (int32_t)step;
+        ++n;
+    }
+    *n_steps = n;
+    return HE_OK;
+}
+
+int he_ras(he_ctx *ctx, const he_plan *plan, const he_ct *in, he_ct *out) {
+    if (!ctx || !plan || !in || !out || !in->data || !out->data || plan->slots != ctx->n / 2) return HE_EINVAL;
+    const int level = in->level;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    int32_t steps[64];
+    int ns = 0;
+    he_plan_ras_steps(plan, steps, &ns);
+    std::vector<const uint64_t *> keys(ns);
+    for (int j = 0; j < ns; ++j) {
+        auto it = ctx->keys.find(galois_of(ctx, steps[j]));
+        if (it == ctx->keys.end()) return HE_EKEY;
+        keys[j] = it->second;
+    }
+    const ModUpConst &mu = ctx->modup[level];
+    const size_t N = ctx->n, nl = level + 1, ext = mu.ext;
+    const size_t wD = mu.ndig * ext * N, wc = nl * N, wu = 2 * ext * N, wr = nl * N, wt = 2 * ctx->K * N, wrot = 2 * nl * N;
+    uint64_t *s = ctx_scratch(ctx, wD + wc + wu + wr + wt + wrot);
+    if (!s) return HE_ENOMEM;
+    uint64_t *D = s, *coef = D + wD, *u = coef + wc, *rc0 = u + wu, *tmp = rc0 + wr, *rot = tmp + wt;
+    if (out->data != in->data &&
+        cudaMemcpyAsync(out->data, in->data, 2 * nl * N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+        return HE_ECUDA;
+    // x <- x + RotL(x, step) for each step in turn (each rotation depends on the previous sum)
+    for (int j = 0; j < ns; ++j) {
+        const uint32_t g = galois_of(ctx, steps[j]);
+        launch_modup(ctx, out->data + nl * N, level, D, coef);
+        launch_ks_inner(ctx, D, level, g, keys[j], u);
+        launch_automorph(ctx, out->data, rc0, 1, qmap(level), g);
+        launch_moddown(ctx, u, level, 2, rc0, nullptr, rot, tmp);
+        launch_add(ctx, out->data, rot, out->data, 2, qmap(level));
+    }
+    out->level = level;
+    out->scale = in->scale;
+    return last_launch();
+}
+
+int he_ras_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out) {
+    if (!ctx || !plan || !slots || !y_out || plan->slots != ctx->n / 2) return HE_EINVAL;
+    launch_ras_gather(ctx, *plan, slots, y_out);
     return last_launch();
 }
 

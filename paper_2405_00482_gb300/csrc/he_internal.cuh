@@ -195,7 +195,7 @@ struct he_batch {
 int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
 int mm_variant_count();
 int mm_variant_tile(int v);  // coefficients per tile of loop-kernel variant v
-void mm_variant_shape(int v, int *vec, int *grp, int *stages);
+void mm_variant_shape(int v, int *vec, int *grp, int *stages, int *ga);
 int mm_batch_ctas_per_sm(int v, int ndig);
 int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc);
 // defined in he_api.cu (inside its extern "C" block)
@@ -277,4 +277,5 @@ void launch_encrypt_combine(he_ctx *ctx, const uint64_t *pt, const uint64_t *a, 
 void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, uint32_t g, int digit, uint64_t *key_d);
 void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots);
 void launch_layout_vector(he_ctx *ctx, const he_plan &p, const double *y, double *slots);
-void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, double *y);
+void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, const double *mask, double *y);
+void launch_ras_gather(he_ctx *ctx, const he_plan &p, const double *slots, double *y);

@@ -335,12 +335,13 @@ __device__ __forceinline__ void cp_async_wait() {
 // One tile: MM_THREADS / G lanes of VEC coefficients starting at coefficient k0 of extended
 // limb u.  Every thread of the block calls it (it synchronises once).  red: 3*VEC*MM_THREADS
 // words.  With S > 0 stages (fixed digit count only) each thread streams its key and plaintext
-// operands through S private stages of pipe (S*(2*NDIG+1)*VEC*MM_THREADS words), so S rotation
-// steps of HBM loads are in flight without occupying registers; the digit and c0 gathers, which
-// hit L2, keep the one-step register prefetch.
-template <int NDIG, int VEC, int G, int S>
+// operands through S private stages of pipe, so S rotation steps of HBM loads are in flight
+// without occupying registers.  With GA the digit and c0 gathers (L2 hits) go through the same
+// stages; without, they keep the one-step register prefetch.  keys / galois may point to shared
+// memory (the kernels stage the tables there), so no global round trip precedes a step's loads.
+template <int NDIG, int VEC, int G, int S, bool GA>
 __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
-                                        const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime,
+                                        const uint64_t *const *keys, const uint32_t *galois, int m_prime,
                                         int ndig_rt, int ext, int nq, int L, int LK, int u, int p, int k0, uint64_t *acc, uint64_t *cacc,
                                         int accumulate, const ModConst *__restrict__ mc, int logn, uint64_t *red, uint64_t *pipe) {
     constexpr int LANES = MM_THREADS / G;
@@ -364,8 +365,10 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
         constexpr int ND = NDIG > 0 ? NDIG : 8;
         constexpr int SP = NDIG > 0 ? S : 0;
         if constexpr (SP > 0) {
-            // slot (stage, field f, thread) at pipe[((stage F + f) MM_THREADS + tid) VEC], F = 2 ND + 1
-            constexpr int F = 2 * ND + 1;
+            // slot (stage, field f, thread) at pipe[((stage F + f) MM_THREADS + tid) VEC]: fields
+            // 2d, 2d+1 key digit d; 2 ND the plaintext; with GA, 2 ND + 1 + d digit d's gather
+            // and 3 ND + 1 the c0 gather (aligned pairs when VEC = 2)
+            constexpr int F = 2 * ND + 1 + (GA ? ND + 1 : 0);
             auto slot = [&](int st, int f) { return pipe + ((st * F + f) * MM_THREADS + (int)threadIdx.x) * VEC; };
             auto issue = [&](int t) {
                 const int i = 1 + grp + t * G;
@@ -378,24 +381,49 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                         cp_async<8 * VEC>(slot(st, 2 * d + 1), key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k);
                     }
                     cp_async<8 * VEC>(slot(st, 2 * ND), pts + ((int64_t)i * ext + u) * N + k);
+                    if constexpr (GA) {
+                        const uint32_t src = automorph_src(k, galois[i - 1], logn);
+                        const uint32_t sa = VEC == 2 ? (src & ~1u) : src;
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) cp_async<8 * VEC>(slot(st, 2 * ND + 1 + d), D + ((int64_t)d * ext + u) * N + sa);
+                        if (inq) cp_async<8 * VEC>(slot(st, 3 * ND + 1), ct + (int64_t)u * N + sa);
+                    }
                 }
                 cp_async_commit();
             };
             uint64_t dv[ND][VEC], cv[VEC];
+            // gathered operands of step t: from the stage (GA) or straight from global memory
             auto gather = [&](int t) {
                 const int i = 1 + grp + t * G;
                 if (i >= m_prime) return;
-                const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
+                const uint32_t src = automorph_src(k, galois[i - 1], logn);
+                if constexpr (GA) {
+                    const int st = t % SP;
+                    const bool odd = VEC == 2 && (src & 1);
 #pragma unroll
-                for (int d = 0; d < ND; ++d) gatherv<VEC>(D + ((int64_t)d * ext + u) * N, src, dv[d]);
-                if (inq) gatherv<VEC>(ct + (int64_t)u * N, src, cv);
+                    for (int d = 0; d < ND; ++d) {
+                        const uint64_t *g = slot(st, 2 * ND + 1 + d);
+#pragma unroll
+                        for (int j = 0; j < VEC; ++j) dv[d][j] = g[odd ? VEC - 1 - j : j];
+                    }
+                    if (inq) {
+                        const uint64_t *g = slot(st, 3 * ND + 1);
+#pragma unroll
+                        for (int j = 0; j < VEC; ++j) cv[j] = g[odd ? VEC - 1 - j : j];
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) gatherv<VEC>(D + ((int64_t)d * ext + u) * N, src, dv[d]);
+                    if (inq) gatherv<VEC>(ct + (int64_t)u * N, src, cv);
+                }
             };
 #pragma unroll
             for (int t = 0; t < SP; ++t) issue(t);
-            gather(0);
+            if constexpr (!GA) gather(0);
             for (int t = 0; 1 + grp + t * G < m_prime; ++t) {
                 cp_async_wait<SP - 1>();
                 const int st = t % SP;
+                if constexpr (GA) gather(t);
                 u128 s0[VEC], s1[VEC];
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) s0[j] = s1[j] = 0;
@@ -416,7 +444,7 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                     c0v[j] = cv[j];
                 }
                 issue(t + SP);
-                gather(t + 1);
+                if constexpr (!GA) gather(t + 1);
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) {
                     t0[j] += (u128)fold(s0[j], q, qinv) * pmc[j];
@@ -438,7 +466,7 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
         } else {
             uint64_t dv[ND][VEC], kv0[ND][VEC], kv1[ND][VEC], pm[VEC], cv[VEC];
             auto fetch = [&](int i) {
-                const uint32_t src = automorph_src(k, __ldg(galois + i - 1), logn);
+                const uint32_t src = automorph_src(k, galois[i - 1], logn);
                 const uint64_t *key = keys[i - 1];
     #pragma unroll
                 for (int d = 0; d < ND; ++d) {
@@ -557,30 +585,59 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
 }
 
 // dynamic shared memory of the pipelined form
-constexpr size_t mm_pipe_bytes(int ndig, int vec, int stages) {
-    return ndig > 0 && stages > 0 ? (size_t)stages * (2 * ndig + 1) * MM_THREADS * vec * sizeof(uint64_t) : 0;
+constexpr size_t mm_pipe_bytes(int ndig, int vec, int stages, bool ga) {
+    return ndig > 0 && stages > 0 ? (size_t)stages * (2 * ndig + 1 + (ga ? ndig + 1 : 0)) * MM_THREADS * vec * sizeof(uint64_t) : 0;
+}
+
+// Key-pointer and Galois-element tables of up to MM_TABLE rotations are copied to shared memory
+// (one round trip per CTA) so that a step's loads do not wait on a table load; longer tables
+// are read from global memory.
+#define MM_TABLE 512
+struct MMTables {
+    const uint64_t *keys[MM_TABLE];
+    uint32_t gal[MM_TABLE];
+};
+__device__ __forceinline__ void stage_tables(MMTables &tb, const uint64_t *const *keys, const uint32_t *galois, int m_prime,
+                                             const uint64_t *const *&k_use, const uint32_t *&g_use) {
+    if (m_prime - 1 <= MM_TABLE) {  // uniform over the block
+        for (int i = threadIdx.x; i < m_prime - 1; i += blockDim.x) {
+            tb.keys[i] = keys[i];
+            tb.gal[i] = galois[i];
+        }
+        __syncthreads();
+        k_use = tb.keys;
+        g_use = tb.gal;
+    } else {
+        k_use = keys;
+        g_use = galois;
+    }
 }
 
 // single MatMult: block (coefficient tile, extended limb)
-template <int NDIG, int VEC, int G, int S>
+template <int NDIG, int VEC, int G, int S, bool GA>
 __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_loop_kernel(
     const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
     const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime, int ndig_rt, int ext, int nq, int L,
     int LK, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
     __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
+    __shared__ MMTables tb;
     extern __shared__ uint4 mm_pipe[];
     const int u = blockIdx.y;
-    mm_tile<NDIG, VEC, G, S>(ct, D, pts, keys, galois, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq),
-                             blockIdx.x * (MM_THREADS / G) * VEC, acc, cacc, accumulate, mc, logn, red,
-                             reinterpret_cast<uint64_t *>(mm_pipe));
+    const uint64_t *const *k_use;
+    const uint32_t *g_use;
+    stage_tables(tb, keys, galois, m_prime, k_use, g_use);
+    mm_tile<NDIG, VEC, G, S, GA>(ct, D, pts, k_use, g_use, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq),
+                                 blockIdx.x * (MM_THREADS / G) * VEC, acc, cacc, accumulate, mc, logn, red,
+                                 reinterpret_cast<uint64_t *>(mm_pipe));
 }
 
 // batch: persistent CTAs pull (tile, limb, job) items from an ordered queue
-template <int NDIG, int VEC, int G, int S>
+template <int NDIG, int VEC, int G, int S, bool GA>
 __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_loop_kernel(
     const MMJob *__restrict__ jobs, const int32_t *__restrict__ order, int n_items, unsigned int *counter, BatchGeom bg,
     const ModConst *__restrict__ mc, int logn) {
     __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
+    __shared__ MMTables tb;
     __shared__ int item_s;
     extern __shared__ uint4 mm_pipe[];
     const int N = 1 << logn;
@@ -597,9 +654,12 @@ __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_lo
         const int u = rest / tiles, tile = rest % tiles;
         const MMJob &jb = jobs[j];
         if (jb.m_prime == 0) continue;  // empty slot
-        mm_tile<NDIG, VEC, G, S>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, jb.keys, jb.galois, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L,
-                                 bg.LK, u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * TILE, bg.acc + (int64_t)j * bg.acc_words,
-                                 bg.cacc + (int64_t)j * bg.cacc_words, 0, mc, logn, red, reinterpret_cast<uint64_t *>(mm_pipe));
+        const uint64_t *const *k_use;
+        const uint32_t *g_use;
+        stage_tables(tb, jb.keys, jb.galois, jb.m_prime, k_use, g_use);
+        mm_tile<NDIG, VEC, G, S, GA>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, k_use, g_use, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L,
+                                     bg.LK, u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * TILE, bg.acc + (int64_t)j * bg.acc_words,
+                                     bg.cacc + (int64_t)j * bg.cacc_words, 0, mc, logn, red, reinterpret_cast<uint64_t *>(mm_pipe));
         __syncthreads();
     }
 }
@@ -607,47 +667,50 @@ __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_lo
 }  // namespace
 
 // ---- variant dispatch ----
-// variant v: (coefficients per thread VEC, rotation groups G, cp.async stages S); S = 0 is the
-// register-prefetch form
+// variant v: (coefficients per thread VEC, rotation groups G, cp.async stages S, gathers through
+// the stages GA); S = 0 is the register-prefetch form
 struct MMShape {
     int vec, grp, stages;
+    bool ga;
 };
-constexpr MMShape kMMShapes[] = {{2, 4, 0}, {1, 4, 0}, {1, 8, 0}, {2, 8, 0}, {2, 4, 3}, {1, 4, 4}, {1, 8, 3}};
+constexpr MMShape kMMShapes[] = {{2, 4, 0, false}, {1, 4, 0, false}, {1, 8, 0, false}, {2, 8, 0, false},
+                                 {2, 4, 3, false}, {2, 4, 2, true},  {1, 4, 2, true},  {1, 8, 2, true}};
 constexpr int kMMVariants = (int)(sizeof(kMMShapes) / sizeof(kMMShapes[0]));
 static_assert(kMMVariants <= HE_MM_MAX_VARIANTS, "variant table");
 
 int mm_variant_count() { return kMMVariants; }
 int mm_variant_tile(int v) { return (MM_THREADS / kMMShapes[v].grp) * kMMShapes[v].vec; }
-void mm_variant_shape(int v, int *vec, int *grp, int *stages) {
+void mm_variant_shape(int v, int *vec, int *grp, int *stages, int *ga) {
     *vec = kMMShapes[v].vec;
     *grp = kMMShapes[v].grp;
     *stages = kMMShapes[v].stages;
+    *ga = kMMShapes[v].ga ? 1 : 0;
 }
 
 namespace {
 
-// calls f.template operator()<NDIG, VEC, G, S>() for variant v and digit count ndig (NDIG = 0:
-// any digit count, register form)
+// calls f.template operator()<NDIG, VEC, G, S, GA>() for variant v and digit count ndig
+// (NDIG = 0: any digit count, register form)
+template <int VEC, int G, int S, bool GA, typename F>
+void mm_dispatch_nd(int ndig, F &&f) {
+    switch (ndig) {
+        case 1: f.template operator()<1, VEC, G, S, GA>(); break;
+        case 2: f.template operator()<2, VEC, G, S, GA>(); break;
+        case 3: f.template operator()<3, VEC, G, S, GA>(); break;
+        default: f.template operator()<0, VEC, G, 0, false>(); break;
+    }
+}
 template <typename F>
 void mm_dispatch(int v, int ndig, F &&f) {
-    auto nd = [&](auto vec, auto grp, auto st) {
-        constexpr int VEC = decltype(vec)::value, G = decltype(grp)::value, S = decltype(st)::value;
-        switch (ndig) {
-            case 1: f.template operator()<1, VEC, G, S>(); break;
-            case 2: f.template operator()<2, VEC, G, S>(); break;
-            case 3: f.template operator()<3, VEC, G, S>(); break;
-            default: f.template operator()<0, VEC, G, 0>(); break;
-        }
-    };
-    using std::integral_constant;
     switch (v) {
-        case 1: nd(integral_constant<int, 1>{}, integral_constant<int, 4>{}, integral_constant<int, 0>{}); break;
-        case 2: nd(integral_constant<int, 1>{}, integral_constant<int, 8>{}, integral_constant<int, 0>{}); break;
-        case 3: nd(integral_constant<int, 2>{}, integral_constant<int, 8>{}, integral_constant<int, 0>{}); break;
-        case 4: nd(integral_constant<int, 2>{}, integral_constant<int, 4>{}, integral_constant<int, 3>{}); break;
-        case 5: nd(integral_constant<int, 1>{}, integral_constant<int, 4>{}, integral_constant<int, 4>{}); break;
-        case 6: nd(integral_constant<int, 1>{}, integral_constant<int, 8>{}, integral_constant<int, 3>{}); break;
-        default: nd(integral_constant<int, 2>{}, integral_constant<int, 4>{}, integral_constant<int, 0>{}); break;
+        case 1: mm_dispatch_nd<1, 4, 0, false>(ndig, f); break;
+        case 2: mm_dispatch_nd<1, 8, 0, false>(ndig, f); break;
+        case 3: mm_dispatch_nd<2, 8, 0, false>(ndig, f); break;
+        case 4: mm_dispatch_nd<2, 4, 3, false>(ndig, f); break;
+        case 5: mm_dispatch_nd<2, 4, 2, true>(ndig, f); break;
+        case 6: mm_dispatch_nd<1, 4, 2, true>(ndig, f); break;
+        case 7: mm_dispatch_nd<1, 8, 2, true>(ndig, f); break;
+        default: mm_dispatch_nd<2, 4, 0, false>(ndig, f); break;
     }
 }
 
@@ -657,25 +720,26 @@ void mm_launch_variant(he_ctx *ctx, int v, const uint64_t *ct, const uint64_t *D
                        const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
     const dim3 grid((unsigned)((ctx->n + mm_variant_tile(v) - 1) / mm_variant_tile(v)), (unsigned)ext);
     ctx->launches++;
-    mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S>() {
-        matmult_loop_kernel<NDIG, VEC, G, S><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S), ctx->stream>>>(
+    mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S, bool GA>() {
+        matmult_loop_kernel<NDIG, VEC, G, S, GA><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S, GA), ctx->stream>>>(
             ct, D, pts, keys, galois, m_prime, ndig, ext, nq, ctx->L, ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n);
     });
 }
 
 void mm_launch_batch_variant(int v, dim3 grid, cudaStream_t st, const MMJob *jobs, const int32_t *order, int n_items, unsigned int *counter,
                              const BatchGeom &bg, const ModConst *mc, int logn) {
-    mm_dispatch(v, bg.ndig, [&]<int NDIG, int VEC, int G, int S>() {
-        matmult_batch_loop_kernel<NDIG, VEC, G, S><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S), st>>>(jobs, order, n_items, counter, bg,
-                                                                                                           mc, logn);
+    mm_dispatch(v, bg.ndig, [&]<int NDIG, int VEC, int G, int S, bool GA>() {
+        matmult_batch_loop_kernel<NDIG, VEC, G, S, GA><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S, GA), st>>>(jobs, order, n_items, counter,
+                                                                                                                 bg, mc, logn);
     });
 }
 
 // resident CTAs per SM of the batch kernel of variant v (the persistent grid is this times the SMs)
 int mm_batch_ctas_per_sm(int v, int ndig) {
     int n = 0;
-    mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S>() {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matmult_batch_loop_kernel<NDIG, VEC, G, S>, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S));
+    mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S, bool GA>() {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, matmult_batch_loop_kernel<NDIG, VEC, G, S, GA>, MM_THREADS,
+                                                      mm_pipe_bytes(NDIG, VEC, S, GA));
     });
     return n > 0 ? n : 1;
 }
@@ -706,14 +770,24 @@ __global__ void layout_vector_kernel(he_plan p, const double *__restrict__ y, do
     }
 }
 
-__global__ void lazy_ras_kernel(he_plan p, const double *__restrict__ slots, double *y) {
+// y[r mb + b m' + t] = sum_{s < nb/m'} (slots - mask)[r][b nb + t + s m'] (mask may be null)
+__global__ void lazy_ras_kernel(he_plan p, const double *__restrict__ slots, const double *__restrict__ mask, double *y) {
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < p.m; row += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = row / p.mb, rem = row % p.mb;
         const int64_t b = rem / p.m_prime, t = rem % p.m_prime;
-        const double *sl = slots + r * p.slots + b * p.nb + t;
+        const int64_t off = r * p.slots + b * p.nb + t;
         double acc = 0.0;
-        for (int64_t s = 0; s < p.nb / p.m_prime; ++s) acc += sl[s * p.m_prime];
+        for (int64_t s = 0; s < p.nb / p.m_prime; ++s) acc += mask ? slots[off + s * p.m_prime] - mask[off + s * p.m_prime] : slots[off + s * p.m_prime];
         y[row] = acc;
+    }
+}
+
+// after the ciphertext rotate-and-sum: y[r mb + b m' + t] = slots[r][b nb + t]
+__global__ void ras_gather_kernel(he_plan p, const double *__restrict__ slots, double *y) {
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < p.m; row += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = row / p.mb, rem = row % p.mb;
+        const int64_t b = rem / p.m_prime, t = rem % p.m_prime;
+        y[row] = slots[r * p.slots + b * p.nb + t];
     }
 }
 
@@ -907,10 +981,16 @@ void launch_layout_vector(he_ctx *ctx, const he_plan &p, const double *y, double
     layout_vector_kernel<<<blocks, 256, 0, ctx->stream>>>(p, y, slots);
 }
 
-void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, double *y) {
+void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, const double *mask, double *y) {
     int blocks = (int)((p.m + 255) / 256);
     ctx->launches++;
-    lazy_ras_kernel<<<blocks, 256, 0, ctx->stream>>>(p, slots, y);
+    lazy_ras_kernel<<<blocks, 256, 0, ctx->stream>>>(p, slots, mask, y);
+}
+
+void launch_ras_gather(he_ctx *ctx, const he_plan &p, const double *slots, double *y) {
+    int blocks = (int)((p.m + 255) / 256);
+    ctx->launches++;
+    ras_gather_kernel<<<blocks, 256, 0, ctx->stream>>>(p, slots, y);
 }
 
 // Whole batched MatMult on `stream`: ModUp of every input, one persistent loop launch over the
@@ -949,16 +1029,19 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(modup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(moddown_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(modup_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(moddown_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(rescale_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     for (int v = 0; v < kMMVariants; ++v)
         for (int nd = 0; nd <= 3; ++nd)
-            mm_dispatch(v, nd, []<int NDIG, int VEC, int G, int S>() {
-                const int bytes = (int)mm_pipe_bytes(NDIG, VEC, S);
+            mm_dispatch(v, nd, []<int NDIG, int VEC, int G, int S, bool GA>() {
+                const int bytes = (int)mm_pipe_bytes(NDIG, VEC, S, GA);
                 if (bytes == 0) return;
-                cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-                cudaFuncSetAttribute(matmult_batch_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-                cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S, GA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                cudaFuncSetAttribute(matmult_batch_loop_kernel<NDIG, VEC, G, S, GA>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S, GA>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
-                cudaFuncSetAttribute(matmult_batch_loop_kernel<NDIG, VEC, G, S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                cudaFuncSetAttribute(matmult_batch_loop_kernel<NDIG, VEC, G, S, GA>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
             });
 }

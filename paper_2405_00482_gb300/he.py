@@ -53,6 +53,11 @@ _SIGS = {
     "he_encrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _u64, ctypes.POINTER(HeCt)]),
     "he_decrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_add": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
+    "he_add_plain": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HePt), ctypes.POINTER(HeCt)]),
+    "he_matmult_decode_masked": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "he_plan_ras_steps": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]),
+    "he_ras": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
+    "he_ras_decode": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "he_mul_plain": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HePt), ctypes.POINTER(HeCt)]),
     "he_rescale": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
     "he_rotate": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _i32, ctypes.POINTER(HeCt)]),
@@ -78,7 +83,7 @@ _SIGS = {
     "he_ptmat_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_loop_variant_shape": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                             ctypes.POINTER(ctypes.c_int)]),
+                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "he_cdiag_encode_weights": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_cdmat_free": (None, [_vp]),
     "he_cdiag_encode_matrix": (ctypes.c_int, [_vp, _vp, _i64, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
@@ -159,6 +164,11 @@ class Plan:
         _check(_lib().he_plan_query(h, info), "he_plan_query")
         for k, v in zip(self.FIELDS, info):
             setattr(self, k, int(v))
+        n = ctypes.c_int()
+        _check(_lib().he_plan_ras_steps(h, None, ctypes.byref(n)), "he_plan_ras_steps")
+        steps = (ctypes.c_int32 * max(n.value, 1))()
+        _check(_lib().he_plan_ras_steps(h, steps, ctypes.byref(n)), "he_plan_ras_steps")
+        self.ras_steps = [int(v) for v in steps[: n.value]]
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -190,12 +200,13 @@ HE_MM_MAX_VARIANTS = 8
 
 
 def loop_variants() -> list:
-    """(coefficients per thread, rotation groups, cp.async stages) of every loop-kernel variant."""
+    """(coefficients per thread, rotation groups, cp.async stages, gathers staged) of every
+    loop-kernel variant."""
     out = []
     for v in range(_lib().he_loop_variant_count()):
-        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(_lib().he_loop_variant_shape(v, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "he_loop_variant_shape")
-        out.append((a.value, b.value, c.value))
+        a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib().he_loop_variant_shape(v, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)), "he_loop_variant_shape")
+        out.append((a.value, b.value, c.value, d.value))
     return out
 
 
@@ -400,6 +411,28 @@ class Context:
         out.scale = co.scale
         return out
 
+    def add_plain(self, ct: Ciphertext, pt: Plaintext, out: Ciphertext | None = None) -> Ciphertext:
+        """O1 with a plaintext at the ciphertext's scale: (c0 + pt, c1)."""
+        out = out if out is not None else self.new_ct(ct.level)
+        c, p, o = ct.c(), pt.c(), out.c()
+        _check(_lib().he_add_plain(self.handle, ctypes.byref(c), ctypes.byref(p), ctypes.byref(o)), "he_add_plain")
+        out.level, out.scale = o.level, o.scale
+        return out
+
+    def ras(self, plan: Plan, ct: Ciphertext, out: Ciphertext | None = None) -> Ciphertext:
+        """Ciphertext rotate-and-sum over plan.ras_steps (the non-lazy form of Sec. 4.3)."""
+        out = out if out is not None else self.new_ct(ct.level)
+        c, o = ct.c(), out.c()
+        _check(_lib().he_ras(self.handle, plan.handle, ctypes.byref(c), ctypes.byref(o)), "he_ras")
+        out.level, out.scale = o.level, o.scale
+        return out
+
+    def ras_decode(self, plan: Plan, slots: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        slots = _dev(slots, torch.float64)
+        out = out if out is not None else torch.empty(plan.m, dtype=torch.float64, device=self.device)
+        _check(_lib().he_ras_decode(self.handle, plan.handle, slots.data_ptr(), out.data_ptr()), "he_ras_decode")
+        return out
+
     def mul_plain(self, ct: Ciphertext, pt: Plaintext) -> Ciphertext:
         out = self.new_ct(ct.level)
         c, p, o = ct.c(), pt.c(), out.c()
@@ -475,10 +508,17 @@ class Context:
             o.level, o.scale = a.level, a.scale
         return outs
 
-    def matmult_decode(self, plan: Plan, slots: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    def matmult_decode(self, plan: Plan, slots: torch.Tensor, out: torch.Tensor | None = None,
+                       mask: torch.Tensor | None = None) -> torch.Tensor:
+        """Lazy RaS of the decrypted slots [R][N/2]; with mask, of (slots - mask) (Alg. 1)."""
         slots = _dev(slots, torch.float64)
         out = out if out is not None else torch.empty(plan.m, dtype=torch.float64, device=self.device)
-        _check(_lib().he_matmult_decode(self.handle, plan.handle, slots.data_ptr(), out.data_ptr()), "he_matmult_decode")
+        if mask is None:
+            _check(_lib().he_matmult_decode(self.handle, plan.handle, slots.data_ptr(), out.data_ptr()), "he_matmult_decode")
+        else:
+            mask = _dev(mask, torch.float64)
+            _check(_lib().he_matmult_decode_masked(self.handle, plan.handle, slots.data_ptr(), mask.data_ptr(), out.data_ptr()),
+                   "he_matmult_decode_masked")
         return out
 
     # ---- VFL-NN forward pass with the encrypted matrix diagonally encoded (Alg. 3) ----

@@ -35,6 +35,8 @@ class SchemeParams:
 PARAMS_SMALL = SchemeParams(12, (40, 20), (40,), 2, 2.0**20)
 # ring N = 8192, chain [60, 40, 40 | 60], scale 2^40, digits of one prime
 PARAMS_N8192 = SchemeParams(13, (60, 40, 40), (60,), 3, 2.0**40)
+# ring N = 16384, chain [60, 40 x 6 | 60, 60, 60], scale 2^40, dnum 3 (digits of three primes)
+PARAMS_N16384 = SchemeParams(14, (60, 40, 40, 40, 40, 40, 40), (60, 60, 60), 3, 2.0**40)
 
 
 def gradient_small(seed: int = 0):
@@ -52,6 +54,17 @@ def gradient_and_forward_n8192(seed: int = 0):
     r = rng.uniform(-1.0, 1.0, 1024)
     w = rng.normal(scale=np.sqrt(0.1), size=256)
     return X, r, w
+
+
+def vfl_nn_layer(seed: int = 0):
+    """VFL neural layer: activations A 4096x256 ~ U[-1,1] (encrypted as diagonals), weights
+    W 256x128 ~ N(0, var 1/256) (forward A W); output gradient D^T 4096x128 ~ N(0, var 1/4096)
+    (backward A^T D^T)."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1.0, 1.0, (4096, 256))
+    W = rng.normal(scale=1.0 / 16.0, size=(256, 128))
+    Dt = rng.normal(scale=1.0 / 64.0, size=(4096, 128))
+    return A, W, Dt
 
 
 def batched_instances(count: int = 64, seed: int = 0):

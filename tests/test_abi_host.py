@@ -77,13 +77,18 @@ def test_loop_variant_table_and_argument_checks(he):
     NULL handles are rejected before anything touches the GPU."""
     shapes = he.loop_variants()
     assert 7 <= len(shapes) <= he.HE_MM_MAX_VARIANTS
-    assert all(vec in (1, 2) and grp in (4, 8) and st >= 0 for vec, grp, st in shapes)
-    assert shapes[0] == (2, 4, 0)
-    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert all(vec in (1, 2) and grp in (4, 8) and st >= 0 and ga in (0, 1) and (st > 0 or not ga) for vec, grp, st, ga in shapes)
+    assert shapes[0] == (2, 4, 0, 0)
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     lib = he.lib()
     for v in (-1, len(shapes)):
-        assert lib.he_loop_variant_shape(v, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == he.HE_EINVAL
+        assert lib.he_loop_variant_shape(v, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)) == he.HE_EINVAL
     assert lib.he_ptmat_set_variant(None, 0) == he.HE_EINVAL
     assert lib.he_batch_set_variant(None, 0) == he.HE_EINVAL
     ms = (ctypes.c_float * he.HE_MM_MAX_VARIANTS)()
     assert lib.he_ptmat_tuning(None, ctypes.byref(a), ms) == he.HE_EINVAL
+
+
+@pytest.mark.parametrize("m,n,slots", [(4, 4, 8), (16, 64, 2048), (256, 1024, 4096), (3, 5, 8), (1, 8, 16), (5000, 300, 4096)])
+def test_ras_steps_agree_with_oracle(he, m, n, slots):
+    assert he.Plan(m, n, slots).ras_steps == layout.ras_steps(layout.make_plan(m, n, slots))

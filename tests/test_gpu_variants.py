@@ -25,7 +25,8 @@ def test_variant_table(he):
     shapes = he.loop_variants()
     assert len(shapes) >= 7 and len(shapes) <= he.HE_MM_MAX_VARIANTS
     assert len(set(shapes)) == len(shapes)
-    assert {s[2] for s in shapes} >= {0, 3}  # register form and a cp.async pipeline
+    assert {s[2] > 0 for s in shapes} == {False, True}  # register form and cp.async pipelines
+    assert {s[3] for s in shapes} == {0, 1}  # with and without staged gathers
 
 
 # (log N, Q bits, P bits, dnum, level, m, n): digits at that level = ceil((level + 1) / alpha)

@@ -155,3 +155,20 @@ def test_transposed_diagonal_conversion(m, n):
     for i, (k, r) in enumerate(layout.transpose_rotations(m, n)):
         assert np.array_equal(layout.rotl(E[k], r), Et[i])
     assert not all(np.array_equal(np.roll(E[(lo - i) % lo], hi - lo + i), Et[i]) for i in range(lo))
+
+
+@pytest.mark.parametrize("m,n,slots", [(4, 4, 8), (16, 64, 2048), (256, 1024, 4096), (1024, 256, 4096), (3, 5, 8), (100, 37, 64),
+                                       (64, 64, 64), (8, 1, 16), (1, 8, 16), (130, 20, 64), (20, 130, 64), (130, 130, 64)])
+def test_ciphertext_ras_model_equals_lazy_ras(m, n, slots):
+    """The rotate-and-sum that Sec. 4.3 makes lazy: log2(nb/m') rounds of x <- x + RotL(x, m' 2^j)
+    leave in slot b*nb + t exactly the cleartext sum the lazy RaS takes (brute force on integer
+    slot vectors, every regime)."""
+    plan = layout.make_plan(m, n, slots)
+    steps = layout.ras_steps(plan)
+    assert len(steps) == int(np.log2(plan.nb // plan.m_prime))
+    rng = np.random.default_rng(m + 3 * n)
+    S = rng.integers(-50, 50, size=(plan.row_blocks, slots)).astype(np.float64)
+    T = S.copy()
+    for r in steps:
+        T = T + np.stack([layout.rotl(row, r) for row in T])
+    assert np.array_equal(layout.ras_decode(T, plan), layout.lazy_ras(S, plan))

@@ -258,3 +258,52 @@ def test_transpose_then_backward_product(m, n):
     outs = ckks.cipher_diag_matmult(o, tcts, pts, qs)
     res = np.stack([layout.cipher_diag_decode(o.decrypt_slots(c), n, m) for c in outs], 1)
     assert np.abs(res - A.T @ Dt).max() < TOL_2_40
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (16, 64), (8, 16), (64, 8)])
+def test_add_plain_and_ciphertext_ras(m, n):
+    """O1 with a plaintext operand, and the MatMult finished by the ciphertext rotate-and-sum
+    instead of the lazy one: both decrypt to the FP64 result; the RaS costs len(ras_steps)
+    rotations and additions."""
+    o = ckks.Oracle(log_n=7, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=11)
+    rng = np.random.default_rng(m * n)
+    D = 2.0**40
+    a, w = rng.uniform(-1, 1, o.slots), rng.uniform(-1, 1, o.slots)
+    ca = o.encrypt(o.encode(a, D, 2), 2, D, 1)
+    s = o.add_plain(ca, o.encode(w, D, 2))
+    assert np.array_equal(s.data[1], ca.data[1])
+    assert np.abs(o.decrypt_slots(s) - (a + w)).max() < 1e-9
+    X = rng.normal(size=(m, n))
+    y = rng.uniform(-1, 1, n)
+    plan = layout.make_plan(m, n, o.slots)
+    outs = o.matmult(o.encode_matrix(X, plan, 2, ext=True), o.encrypt_vector(y, plan, D), plan)
+    o.gen_rotation_keys(layout.ras_steps(plan))
+    o.counts = ckks.OpCounts()
+    rased = [o.ras(c, plan) for c in outs]
+    assert (o.counts.rot, o.counts.add) == (len(layout.ras_steps(plan)) * len(outs),) * 2
+    got = layout.ras_decode(np.stack([o.decrypt_slots(c) for c in rased]), plan)
+    assert np.abs(got - X @ y).max() < TOL_2_40
+
+
+def test_vfl_linr_gradient_step():
+    """Alg. 1 for one party's gradient: [[d]] = [[u_A]] + (u_B - y) in the replicated layout,
+    X_A^T [[d]], a random mask added before decryption and removed after, lazy RaS.  Equals
+    X_A^T (u_A + u_B - y); the masked result alone does not."""
+    o = ckks.Oracle(log_n=8, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=12)
+    rng = np.random.default_rng(13)
+    b, f = 64, 16
+    XA = rng.normal(size=(b, f))
+    uA, uB, y = rng.normal(size=b), rng.normal(size=b), rng.uniform(-1, 1, b)
+    D = 2.0**40
+    plan = layout.make_plan(f, b, o.slots)  # X_A^T: m = features, n = batch
+    o.gen_rotation_keys(plan.rotation_steps)
+    ct_uA = o.encrypt_vector(uA, plan, D, nonce0=3)
+    dv = layout.vector_slots(uB - y, plan)
+    ct_d = [o.add_plain(c, o.encode(dv[i], D, o.L - 1)) for i, c in enumerate(ct_uA)]
+    outs = o.matmult(o.encode_matrix(XA.T, plan, o.L - 1, ext=True), ct_d, plan)
+    mask = rng.uniform(-100, 100, (len(outs), o.slots))
+    masked = [o.add_plain(c, o.encode(mask[i], c.scale, c.level)) for i, c in enumerate(outs)]
+    slots = np.stack([o.decrypt_slots(c) for c in masked])
+    want = XA.T @ (uA + uB - y)
+    assert np.abs(layout.lazy_ras(slots, plan) - want).max() > 1.0
+    assert np.abs(layout.lazy_ras(slots - mask, plan) - want).max() < TOL_2_40
