@@ -55,27 +55,59 @@ __device__ __forceinline__ void cmul(float4 v, float4 w, float4 &out) {
     out = make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
-// iterative radix-2 FFT of M = N/2 complex values in shared memory, input already in
-// bit-reversed order.  tw[k] = exp(-2 pi i k / M) for k < M/2; sign = +1 uses conj(tw).
-__device__ void fft_smem(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
-    const int M = 1 << logm;
-    for (int lg = 1; lg <= logm; ++lg) {
-        const int half = 1 << (lg - 1);
-        const int stride = M >> lg;  // twiddle index step
-        for (int j = threadIdx.x; j < M / 2; j += blockDim.x) {
-            const int grp = j >> (lg - 1), pos = j & (half - 1);
-            const int i1 = (grp << lg) + pos, i2 = i1 + half;
-            float4 w = tw[pos * stride];
-            if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
-            float4 v;
-            cmul(a[i2], w, v);
-            const float4 u = a[i1];
-            const df ur{u.x, u.y}, ui{u.z, u.w}, vr{v.x, v.y}, vi{v.z, v.w};
-            const df s0 = df_add(ur, vr), s1 = df_add(ui, vi), d0 = df_add(ur, df_neg(vr)), d1 = df_add(ui, df_neg(vi));
-            a[i1] = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
-            a[i2] = make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+// Radix-2 decimation-in-time FFT of M = N/2 complex values in shared memory, input in
+// bit-reversed order: stage lg (1..log M) combines a[i1], a[i2 = i1 + 2^(lg-1)] with
+// w = tw[(i1 mod 2^(lg-1)) * M / 2^lg], tw[k] = exp(-2 pi i k / M) (its conjugate for
+// sign = +1), as (u + v w, u - v w).  The stages are grouped into passes of up to three: a
+// thread loads the 8 elements that interact over a pass into registers, runs those butterflies
+// there (the same operations on the same values as one stage at a time, so the result does not
+// depend on the grouping) and writes them back, so a 4096-point transform makes 4 trips through
+// shared memory and block barriers instead of 12, with 4 independent butterflies per stage.
+template <int NB>
+__device__ __forceinline__ void fft_pass(float4 *a, const float4 *__restrict__ tw, int logm, int s0, int sign) {
+    constexpr int E = 1 << NB;
+    const int sets = 1 << (logm - NB);
+    for (int set = threadIdx.x; set < sets; set += blockDim.x) {
+        const int g = set >> s0, low = set & ((1 << s0) - 1);
+        const int base = (g << (s0 + NB)) + low;
+        float4 r[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) r[k] = a[base + (k << s0)];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const int h = 1 << j, lg = s0 + j + 1;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                if ((k & (2 * h - 1)) < h) {
+                    const int pos = (base + (k << s0)) & ((1 << (lg - 1)) - 1);
+                    float4 w = tw[pos << (logm - lg)];
+                    if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
+                    float4 v;
+                    cmul(r[k + h], w, v);
+                    const float4 u = r[k];
+                    const df ur{u.x, u.y}, ui{u.z, u.w}, vr{v.x, v.y}, vi{v.z, v.w};
+                    const df s0r = df_add(ur, vr), s0i = df_add(ui, vi), d0r = df_add(ur, df_neg(vr)), d0i = df_add(ui, df_neg(vi));
+                    r[k] = make_float4(s0r.hi, s0r.lo, s0i.hi, s0i.lo);
+                    r[k + h] = make_float4(d0r.hi, d0r.lo, d0i.hi, d0i.lo);
+                }
+            }
         }
-        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < E; ++k) a[base + (k << s0)] = r[k];
+    }
+    __syncthreads();
+}
+
+__device__ void fft_smem(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
+    int s0 = 0;
+    while (s0 < logm) {
+        const int nb = logm - s0 < 3 ? logm - s0 : 3;
+        switch (nb) {
+            case 3: fft_pass<3>(a, tw, logm, s0, sign); break;
+            case 2: fft_pass<2>(a, tw, logm, s0, sign); break;
+            default: fft_pass<1>(a, tw, logm, s0, sign); break;
+        }
+        s0 += nb;
     }
 }
 
@@ -137,6 +169,7 @@ __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words
     int item, off, len;
     slice_of<CL>(logn, item, off, len);
     const uint64_t q = mc[0].q, qinv = mc[0].qinv;
+    tw_prefetch<CL, false>(s, twiddles(d_tw, 0, 1, logn), logn);
     const uint64_t *c0 = ct + item * ct_words + off, *c1 = ct + item * ct_words + (int64_t)nl * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = add_mod(c0[k], mont_mul(c1[k], sk_mont[off + k], q, qinv), q);
     __syncthreads();
@@ -253,6 +286,7 @@ __global__ void keygen_combine_kernel(const uint64_t *__restrict__ a, const uint
 }  // namespace
 
 static size_t fft_smem_bytes(int logn) { return (size_t)8 << logn; }  // N/2 float4
+#define FFT_THREADS 512
 
 // FFT tables in ctx->d_fft: [N/4] float4 twiddles, [N/2] float4 twist, [N/2] int32 slot positions
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs) {
@@ -261,7 +295,7 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
     const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
-    encode_kernel<<<count, 512, fft_smem_bytes(ctx->log_n), ctx->stream>>>(slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
+    encode_kernel<<<count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream>>>(slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
 }
 
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots) {
@@ -270,7 +304,7 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
     const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
-    decode_kernel<<<count, 512, fft_smem_bytes(ctx->log_n), ctx->stream>>>(coeffs, scale, tw, twist, pos, slots, ctx->log_n);
+    decode_kernel<<<count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream>>>(coeffs, scale, tw, twist, pos, slots, ctx->log_n);
 }
 
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *) {
@@ -327,4 +361,5 @@ void encode_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decrypt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(decrypt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }

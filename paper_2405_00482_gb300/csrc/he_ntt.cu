@@ -18,6 +18,7 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const int g = poly / map.n, l = poly % map.n;
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
+    tw_prefetch<CL, true>(s, twiddles(d_tw, p, 0, logn), logn);
     const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
@@ -41,6 +42,7 @@ __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const int g = poly / map.n, l = poly % map.n;
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
+    tw_prefetch<CL, false>(s, twiddles(d_tw, p, 1, logn), logn);
     const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
@@ -61,6 +63,7 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     const int g = poly / map.n, l = poly % map.n;
     const int p = map.prime[l];
     const uint64_t q = mc[p].q;
+    tw_prefetch<CL, true>(s, twiddles(d_tw, p, 0, logn), logn);
     const int64_t *src = in + (int64_t)g * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = reduce_signed(src[k], q);
     __syncthreads();
@@ -84,16 +87,24 @@ __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__re
 
 }  // namespace
 
-// N/16 threads (one radix-16 set each) up to 512; larger rings loop over several sets per thread
-// (the passes use ~128 registers, so 512 threads fill the register file of one SM)
+// One-CTA form: N/16 threads (one radix-16 set each) up to 256, so that two CTAs (two limb-polys)
+// share an SM and one's barriers overlap the other's work (the passes use ~110 registers); from
+// N = 2^14 a limb-poly's shared memory allows one CTA per SM, which then takes 512 threads.
+// Threads loop over several sets when there are more sets than threads.
 // cluster form for launches of at most this many limb-polys (one CTA each would leave most SMs idle)
 #define HE_CL_MAX_POLYS 48
 
 bool use_cluster(int logn, int polys) { return logn >= HE_NTT_CL_MIN_LOGN && polys <= HE_CL_MAX_POLYS; }
 int cl_threads(int logn) { return 1 << (logn - 6); }
-size_t cl_smem_bytes(int logn) { return ntt_smem_bytes(logn - 3); }
+// the slice's padded data, then its N/8 - 1 twiddle pairs (16-byte aligned: N/8 + N/256 is even)
+size_t cl_smem_bytes(int logn) { return ntt_smem_bytes(logn - 3) + ((size_t)16 << (logn - 3)); }
 
-int ntt_threads(int logn) { return logn > HE_NTT_RADIX_LOG ? (logn - HE_NTT_RADIX_LOG > 9 ? 512 : 1 << (logn - HE_NTT_RADIX_LOG)) : 1; }
+int ntt_threads(int logn) {
+    if (logn <= HE_NTT_RADIX_LOG) return 1;
+    const int sets = 1 << (logn - HE_NTT_RADIX_LOG);
+    const int cap = logn >= 14 ? 512 : 256;
+    return sets < cap ? sets : cap;
+}
 
 void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
                             const LimbMap &map, int to_mont) {
@@ -153,4 +164,8 @@ void ntt_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(ntt_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(ntt_inv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(ntt_from_int64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    // cluster forms: slice plus its twiddles (above 48 KB from N = 2^14)
+    cudaFuncSetAttribute(ntt_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_from_int64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }

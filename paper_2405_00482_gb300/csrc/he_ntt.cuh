@@ -25,12 +25,20 @@ namespace cg = cooperative_groups;
 // strided passes (a CTA needs ntt_smem_words(N) = N + N/32 words).
 #define SIDX(k) ((k) + ((k) >> 5))
 
+// Twiddle access: entry idx of the bit-reversed table (idx = m + j for a stage with m groups).
+// TwGlobal reads the table in global memory; the cluster forms read a per-slice copy in shared
+// memory (see tw_prefetch).
+struct TwGlobal {
+    const ulonglong2 *tw;
+    __device__ __forceinline__ ulonglong2 operator()(int, int idx) const { return tw[idx]; }
+};
+
 // A pass over sets [set0, set1) of stages s0..s0+NB-1; element x lives at s[SIDX(x - off)].
 // The whole transform in one CTA uses set0 = 0, set1 = N >> NB, off = 0; a cluster member
 // holding the slice [off, off + N/8) uses the sets whose elements fall in its slice.
-template <int NB>
-__device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn, int s0, bool last,
-                                             int set0 = 0, int set1 = -1, int off = 0) {
+template <int NB, class TWA>
+__device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, int logn, int s0, bool last, int set0 = 0, int set1 = -1,
+                                             int off = 0) {
     constexpr int E = 1 << NB;
     const int N = 1 << logn;
     if (set1 < 0) set1 = N >> NB;
@@ -52,7 +60,7 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__re
             for (int k = 0; k < E; ++k) {
                 if ((k & (2 * h - 1)) < h) {
                     const int x = base + (k << lg_tl);
-                    const ulonglong2 w = tw[m + (x >> lg_2t)];
+                    const ulonglong2 w = tw(m, m + (x >> lg_2t));
                     uint64_t X = r[k];
                     X = X >= two_q ? X - two_q : X;
                     const uint64_t T = mul_shoup_lazy(r[k + h], w.x, w.y, q);
@@ -75,9 +83,9 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, const ulonglong2 *__re
     __syncthreads();
 }
 
-template <int NB>
-__device__ __forceinline__ void ntt_inv_pass(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn, int s0, int set0 = 0,
-                                             int set1 = -1, int off = 0) {
+template <int NB, class TWA>
+__device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, int logn, int s0, int set0 = 0, int set1 = -1,
+                                             int off = 0) {
     constexpr int E = 1 << NB;
     const int N = 1 << logn;
     if (set1 < 0) set1 = N >> NB;
@@ -98,7 +106,7 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, const ulonglong2 *__re
             for (int k = 0; k < E; ++k) {
                 if ((k & (2 * h - 1)) < h) {
                     const int x = base + (k << lg_t0);
-                    const ulonglong2 w = itw[m + (x >> lg_2t)];
+                    const ulonglong2 w = itw(m, m + (x >> lg_2t));
                     const uint64_t U = r[k], V = r[k + h];
                     uint64_t X = U + V;
                     r[k] = X >= two_q ? X - two_q : X;
@@ -119,10 +127,10 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t *s, const ulonglong2 *__re
         const int nb = logn - s0 < HE_NTT_RADIX_LOG ? logn - s0 : HE_NTT_RADIX_LOG;
         const bool last = s0 + nb == logn;
         switch (nb) {
-            case 4: ntt_fwd_pass<4>(s, tw, q, logn, s0, last); break;
-            case 3: ntt_fwd_pass<3>(s, tw, q, logn, s0, last); break;
-            case 2: ntt_fwd_pass<2>(s, tw, q, logn, s0, last); break;
-            default: ntt_fwd_pass<1>(s, tw, q, logn, s0, last); break;
+            case 4: ntt_fwd_pass<4>(s, TwGlobal{tw}, q, logn, s0, last); break;
+            case 3: ntt_fwd_pass<3>(s, TwGlobal{tw}, q, logn, s0, last); break;
+            case 2: ntt_fwd_pass<2>(s, TwGlobal{tw}, q, logn, s0, last); break;
+            default: ntt_fwd_pass<1>(s, TwGlobal{tw}, q, logn, s0, last); break;
         }
         s0 += nb;
     }
@@ -134,10 +142,10 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t *s, const ulonglong2 *__re
     while (s0 < logn) {
         const int nb = logn - s0 < HE_NTT_RADIX_LOG ? logn - s0 : HE_NTT_RADIX_LOG;
         switch (nb) {
-            case 4: ntt_inv_pass<4>(s, itw, q, logn, s0); break;
-            case 3: ntt_inv_pass<3>(s, itw, q, logn, s0); break;
-            case 2: ntt_inv_pass<2>(s, itw, q, logn, s0); break;
-            default: ntt_inv_pass<1>(s, itw, q, logn, s0); break;
+            case 4: ntt_inv_pass<4>(s, TwGlobal{itw}, q, logn, s0); break;
+            case 3: ntt_inv_pass<3>(s, TwGlobal{itw}, q, logn, s0); break;
+            case 2: ntt_inv_pass<2>(s, TwGlobal{itw}, q, logn, s0); break;
+            default: ntt_inv_pass<1>(s, TwGlobal{itw}, q, logn, s0); break;
         }
         s0 += nb;
     }
@@ -152,6 +160,51 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t *s, const ulonglong2 *__re
 // run on each slice with the radix-8 register passes.  Used for launches of few limb-polys,
 // where one CTA per limb-poly would leave most SMs idle.
 #define HE_NTT_CL HE_NTT_CL_SIZE
+
+// The local stages of a cluster member touch NS - 1 twiddles of its slice (NS = N/8): forward
+// stage t (3 <= t < log N, m = 2^t) the m/8 entries m + rank m/8 + j; inverse stage t
+// (0 <= t < log N - 3, m = N / 2^(t+1)) likewise.  tw_slice_issue puts them in shared memory,
+// ordered by stage, behind the slice's data: forward stage m from (m/8 - 1), inverse stage m
+// from (N/2 - m)/4.  The copy is one round of asynchronous 16-byte copies, waited for before the
+// transform, so the passes do not wait on global memory.
+__device__ __forceinline__ int cl_tw_offset_words(int logn) {  // the slice's padded data, in words
+    const int NS = 1 << (logn - 3);
+    return NS + (NS >> 5);
+}
+template <bool FWD>
+__device__ __forceinline__ void tw_slice_issue(ulonglong2 *stw, const ulonglong2 *__restrict__ tw, int logn, int rank) {
+    const int NS = 1 << (logn - 3);
+    for (int i = threadIdx.x; i < NS - 1; i += blockDim.x) {
+        int b = 0, c = FWD ? 1 : NS >> 1, m = FWD ? 8 : 1 << (logn - 1);
+        while (i >= b + c) {
+            b += c;
+            c = FWD ? c << 1 : c >> 1;
+            m = FWD ? m << 1 : m >> 1;
+        }
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(stw + i);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(tw + m + rank * (m >> 3) + (i - b)) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void tw_slice_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Kernels call this as soon as they know their prime, before loading their data, so the twiddle
+// copy overlaps the loads; the cluster transform waits for it.  Nothing in the one-CTA form.
+template <bool CL, bool FWD>
+__device__ __forceinline__ void tw_prefetch(uint64_t *s, const ulonglong2 *__restrict__ tw, int logn) {
+    if constexpr (CL)
+        tw_slice_issue<FWD>(reinterpret_cast<ulonglong2 *>(s + cl_tw_offset_words(logn)), tw, logn, (int)cg::this_cluster().block_rank());
+}
+struct TwSliceFwd {
+    const ulonglong2 *stw;
+    int rank;
+    __device__ __forceinline__ ulonglong2 operator()(int m, int idx) const { return stw[idx - m + (1 - rank) * (m >> 3) - 1]; }
+};
+struct TwSliceInv {
+    const ulonglong2 *stw;
+    int rank, half_n;
+    __device__ __forceinline__ ulonglong2 operator()(int m, int idx) const { return stw[((half_n - m) >> 2) + idx - m - rank * (m >> 3)]; }
+};
 
 template <bool FWD>
 __device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
@@ -207,41 +260,50 @@ __device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 *__
 }
 
 // forward transform of a slice held by each CTA of the cluster; output canonical, bit-reversed
-// positions [rank N/8, (rank+1) N/8) in this CTA
+// positions [rank N/8, (rank+1) N/8) in this CTA.  s must have cl_tw_offset_words(logn) words of
+// data followed by room for N/8 twiddle pairs, whose copy tw_prefetch<true, true> started.
 __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int NS = 1 << (logn - 3), off = rank * NS;
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(s + cl_tw_offset_words(logn));
+    tw_slice_wait();
     cl.sync();
     ntt_cross_step<true>(s, tw, q, logn);
     cl.sync();
+    const TwSliceFwd tws{stw, rank};
     int s0 = 3;
     while (s0 < logn) {
         const int nb = logn - s0 < 3 ? logn - s0 : 3;
         const bool last = s0 + nb == logn;
         const int E = 1 << nb;
         switch (nb) {
-            case 3: ntt_fwd_pass<3>(s, tw, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-            case 2: ntt_fwd_pass<2>(s, tw, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-            default: ntt_fwd_pass<1>(s, tw, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            case 3: ntt_fwd_pass<3>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            case 2: ntt_fwd_pass<2>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            default: ntt_fwd_pass<1>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
         }
         s0 += nb;
     }
 }
 
-// inverse transform (without N^-1) of the slices; output in [0, 2q), natural order
+// inverse transform (without N^-1) of the slices; output in [0, 2q), natural order (twiddle copy
+// started by tw_prefetch<true, false>)
 __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int NS = 1 << (logn - 3), off = rank * NS;
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(s + cl_tw_offset_words(logn));
+    tw_slice_wait();
+    __syncthreads();
+    const TwSliceInv tws{stw, rank, 1 << (logn - 1)};
     int s0 = 0;
     while (s0 < logn - 3) {
         const int nb = logn - 3 - s0 < 3 ? logn - 3 - s0 : 3;
         const int E = 1 << nb;
         switch (nb) {
-            case 3: ntt_inv_pass<3>(s, itw, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-            case 2: ntt_inv_pass<2>(s, itw, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-            default: ntt_inv_pass<1>(s, itw, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            case 3: ntt_inv_pass<3>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            case 2: ntt_inv_pass<2>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
+            default: ntt_inv_pass<1>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
         }
         s0 += nb;
     }

@@ -56,6 +56,7 @@ __device__ __forceinline__ void modup_body(const uint64_t *__restrict__ c1_ntt, 
         for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = c1_ntt[(int64_t)u * N + off + k];
         return;
     }
+    tw_prefetch<CL, true>(s, twiddles(d_tw, p, 0, logn), logn);
     const int na = hi - lo;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
         uint64_t acc = 0;
@@ -116,6 +117,7 @@ __device__ __forceinline__ void moddown_body(const uint64_t *__restrict__ x, int
     const int N = 1 << logn;
     const int pj = md.q_prime[j];
     const uint64_t q = mc[pj].q;
+    tw_prefetch<CL, true>(s, twiddles(d_tw, pj, 0, logn), logn);
     const uint64_t *xp = xp_coef + (int64_t)c * md.K * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
         uint64_t acc = 0;
@@ -162,6 +164,7 @@ __device__ __forceinline__ void rescale_body(const uint64_t *__restrict__ ct, in
                                              const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int off, int len) {
     const int N = 1 << logn;
     const uint64_t q = mc[j].q;
+    tw_prefetch<CL, true>(s, twiddles(d_tw, j, 0, logn), logn);
     const uint64_t *lc = last_coef + (int64_t)c * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
         uint64_t r = lc[k] + rc.half;
