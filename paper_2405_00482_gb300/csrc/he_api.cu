@@ -114,6 +114,7 @@ ModConst make_modconst(uint64_t q, int log_n) {
     m.r2 = hmul(r1, r1, q);
     m.ninv = hinv((1ull << log_n) % q, q);
     m.ninv_shoup = shoup(m.ninv, q);
+    m.mu = (uint64_t)((((u128)1) << 64) / q);
     return m;
 }
 

@@ -124,7 +124,7 @@ __global__ void cdiag_rescale_kernel(const uint64_t *__restrict__ pre, const uin
     for (int x = threadIdx.x; x < N; x += blockDim.x) {
         uint64_t r = lc[x] + rc.half;
         if (r >= rc.ql) r -= rc.ql;
-        s[SIDX(x)] = reduce_signed((int64_t)r - (int64_t)rc.half, q);
+        s[SIDX(x)] = reduce_signed((int64_t)r - (int64_t)rc.half, q, mc[j].mu);
     }
     __syncthreads();
     ntt_fwd_smem(s, twiddles(d_tw, j, 0, logn), q, logn);

@@ -64,10 +64,12 @@ __device__ __forceinline__ void cmul(float4 v, float4 w, float4 &out) {
 // depend on the grouping) and writes them back, so a 4096-point transform makes 4 trips through
 // shared memory and block barriers instead of 12, with 4 independent butterflies per stage.
 template <int NB>
-__device__ __forceinline__ void fft_pass(float4 *a, const float4 *__restrict__ tw, int logm, int s0, int sign) {
+__device__ __forceinline__ void fft_pass(float4 *a, const float4 *__restrict__ tw, int logm, int s0, int sign, int set0 = 0, int set1 = -1,
+                                         int off = 0) {
     constexpr int E = 1 << NB;
-    const int sets = 1 << (logm - NB);
-    for (int set = threadIdx.x; set < sets; set += blockDim.x) {
+    if (set1 < 0) set1 = 1 << (logm - NB);
+    a -= off;  // element x at a[x] (a slice holds [off, off + its length))
+    for (int set = set0 + threadIdx.x; set < set1; set += blockDim.x) {
         const int g = set >> s0, low = set & ((1 << s0) - 1);
         const int base = (g << (s0 + NB)) + low;
         float4 r[E];
@@ -157,6 +159,127 @@ __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, c
         const float4 v = a[slot_pos[j]];
         o[j] = df_to(df{v.x, v.y}) * inv;
     }
+}
+
+// ---- cluster form: CL = 2^CLG CTAs (one thread-block cluster) share one transform ----
+// CTA `rank` holds positions [rank MS, (rank+1) MS) of the array (MS = M / CL).  The first
+// log M - CLG stages pair elements of one slice and run as register passes on it; the last CLG
+// stages pair the CL elements j + c MS (c < CL), which lie in different CTAs, and run as one
+// radix-CL step through distributed shared memory, each CTA taking MS / CL of the offsets j.
+// The butterflies and their order per element are those of fft_smem, so the output is
+// bit-identical to the one-CTA form.  Used when a launch has few transforms, which would leave
+// most SMs idle with one CTA each.
+template <int CLG>
+__device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
+    constexpr int CL = 1 << CLG;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
+    int s0 = 0;
+    while (s0 < lg_ms) {
+        const int nb = lg_ms - s0 < 3 ? lg_ms - s0 : 3;
+        const int E = 1 << nb;
+        switch (nb) {
+            case 3: fft_pass<3>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+            case 2: fft_pass<2>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+            default: fft_pass<1>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+        }
+        s0 += nb;
+    }
+    cl.sync();
+    float4 *rem[CL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) rem[c] = cl.map_shared_rank(a, c);
+    const int per = MS >> CLG;
+    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
+        float4 r[CL];
+#pragma unroll
+        for (int c = 0; c < CL; ++c) r[c] = rem[c][j];
+#pragma unroll
+        for (int st = 0; st < CLG; ++st) {
+            const int h = 1 << st, lg = lg_ms + st + 1;
+#pragma unroll
+            for (int c = 0; c < CL; ++c) {
+                if ((c & (2 * h - 1)) < h) {
+                    const int pos = (j + (c << lg_ms)) & ((1 << (lg - 1)) - 1);
+                    float4 w = tw[pos << (logm - lg)];
+                    if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
+                    float4 v;
+                    cmul(r[c + h], w, v);
+                    const float4 u = r[c];
+                    const df ur{u.x, u.y}, ui{u.z, u.w}, vr{v.x, v.y}, vi{v.z, v.w};
+                    const df s0r = df_add(ur, vr), s0i = df_add(ui, vi), d0r = df_add(ur, df_neg(vr)), d0i = df_add(ui, df_neg(vi));
+                    r[c] = make_float4(s0r.hi, s0r.lo, s0i.hi, s0i.lo);
+                    r[c + h] = make_float4(d0r.hi, d0r.lo, d0i.hi, d0i.lo);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CL; ++c) rem[c][j] = r[c];
+    }
+    cl.sync();
+}
+
+// cluster per plaintext: the slot values go straight to their bit-reversed positions in the
+// owning CTAs; each CTA then twists and rounds the coefficients of its slice
+template <int CLG>
+__global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
+                                 const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
+                                 int64_t *out, int logn) {
+    extern __shared__ float4 a[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
+    const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
+    const double *z = slots + (int64_t)item * stride;
+    const int per = M >> CLG;
+    cl.sync();  // every CTA of the cluster has started before its shared memory is written
+    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
+        const int bt = __brev(slot_pos[j]) >> (32 - logm);
+        const df v = df_from(j < n_slots ? z[j] : 0.0);
+        cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(v.hi, v.lo, 0.f, 0.f);
+    }
+    cl.sync();
+    fft_cluster<CLG>(a, tw, logm, -1);
+    const df f = df_from(2.0 / (double)N * scale);
+    int64_t *o = out + (int64_t)item * N;
+    for (int i = threadIdx.x; i < MS; i += blockDim.x) {
+        const int k = off + i;
+        float4 c;
+        cmul(a[i], twist[k], c);
+        o[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
+        o[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
+    }
+}
+
+// cluster per polynomial: each CTA loads the coefficients whose bit-reversed positions it holds;
+// the slot values are read from the owning CTAs
+template <int CLG>
+__global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
+                                 const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
+    extern __shared__ float4 a[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
+    const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
+    const double *m = coeffs + (int64_t)item * N;
+    for (int i = threadIdx.x; i < MS; i += blockDim.x) {
+        const int k = __brev(off + i) >> (32 - logm);
+        const float4 w = twist[k];
+        const df re = df_from(m[k]), im = df_from(m[k + M]);
+        float4 c;
+        cmul(make_float4(re.hi, re.lo, im.hi, im.lo), make_float4(w.x, w.y, -w.z, -w.w), c);
+        a[i] = c;
+    }
+    __syncthreads();
+    fft_cluster<CLG>(a, tw, logm, +1);
+    double *o = out + (int64_t)item * M;
+    const double inv = 1.0 / scale;
+    const int per = M >> CLG;
+    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
+        const int pos = slot_pos[j];
+        const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
+        o[j] = df_to(df{v.x, v.y}) * inv;
+    }
+    cl.sync();  // the other CTAs read this one's shared memory until here
 }
 
 // decrypt limb 0: m = c0 + c1 s (NTT), inverse NTT, centred, as doubles.  One CTA per
@@ -289,12 +412,35 @@ static size_t fft_smem_bytes(int logn) { return (size_t)8 << logn; }  // N/2 flo
 #define FFT_THREADS 512
 
 // FFT tables in ctx->d_fft: [N/4] float4 twiddles, [N/2] float4 twist, [N/2] int32 slot positions
+// Cluster size for a launch of `count` transforms: 8, 4 or 2 CTAs per transform while the
+// launch stays within two CTAs per SM, else one (rings below 2^10 always one).
+static int fft_cluster_log(int logn, int count) {
+    if (logn < 10) return 0;
+    for (int clg = 3; clg >= 1; --clg)
+        if (count << clg <= 2 * 152) return clg;
+    return 0;
+}
+
+template <int CLG, typename... KArgs, typename... Args>
+static void launch_fft_cl(void (*kernel)(KArgs...), he_ctx *ctx, int count, Args... args) {
+    const int MS = ctx->n / 2 >> CLG;
+    int threads = MS / 8;
+    threads = threads < 32 ? 32 : (threads > 512 ? 512 : threads);
+    launch_cluster_n(kernel, count << CLG, threads, (size_t)MS * sizeof(float4), ctx->stream, 1 << CLG, args...);
+}
+
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs) {
     if (count == 0) return;
     const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
     const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
+    switch (fft_cluster_log(ctx->log_n, count)) {
+        case 3: launch_fft_cl<3>(encode_cl_kernel<3>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 2: launch_fft_cl<2>(encode_cl_kernel<2>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 1: launch_fft_cl<1>(encode_cl_kernel<1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        default: break;
+    }
     encode_kernel<<<count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream>>>(slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
 }
 
@@ -304,6 +450,12 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
     const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
+    switch (fft_cluster_log(ctx->log_n, count)) {
+        case 3: launch_fft_cl<3>(decode_cl_kernel<3>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 2: launch_fft_cl<2>(decode_cl_kernel<2>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 1: launch_fft_cl<1>(decode_cl_kernel<1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        default: break;
+    }
     decode_kernel<<<count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream>>>(coeffs, scale, tw, twist, pos, slots, ctx->log_n);
 }
 
@@ -362,4 +514,6 @@ void encode_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decrypt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decrypt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(encode_cl_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(decode_cl_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }

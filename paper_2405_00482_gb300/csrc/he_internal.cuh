@@ -59,10 +59,16 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t bM, uint64_t q
     return redc128((u128)a * bM, q, qinv);
 }
 
-__device__ __forceinline__ uint64_t reduce_signed(int64_t v, uint64_t q) {
-    // v in (-2^63, 2^63): canonical residue
-    if (v >= 0) return (uint64_t)v % q;
-    uint64_t r = ((uint64_t)(-(v + 1))) % q;  // -(v+1) >= 0 and avoids overflow at INT64_MIN
+// Barrett reduction (Barrett, CRYPTO '86) of x < 2^64 with mu = floor(2^64 / q): the quotient
+// estimate hi(x mu) is floor(x / q) or one less, so one conditional subtraction remains.
+__device__ __forceinline__ uint64_t reduce_barrett(uint64_t x, uint64_t q, uint64_t mu) {
+    const uint64_t r = x - __umul64hi(x, mu) * q;
+    return r >= q ? r - q : r;
+}
+// canonical residue of a signed v in (-2^63, 2^63)
+__device__ __forceinline__ uint64_t reduce_signed(int64_t v, uint64_t q, uint64_t mu) {
+    if (v >= 0) return reduce_barrett((uint64_t)v, q, mu);
+    const uint64_t r = reduce_barrett((uint64_t)(-(v + 1)), q, mu);  // -(v+1) >= 0, no overflow at INT64_MIN
     return q - 1 - r;
 }
 
@@ -82,6 +88,7 @@ struct ModConst {
     uint64_t qinv;    // -q^-1 mod 2^64
     uint64_t r2;      // 2^128 mod q (to Montgomery form: redc(x * r2))
     uint64_t ninv, ninv_shoup;  // N^-1 mod q
+    uint64_t mu;      // floor(2^64 / q), for reduce_barrett
 };
 
 // index map from a batch's limb position to the context's prime index
@@ -208,7 +215,7 @@ int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm);
 // Launch `kernel` with thread-block clusters of HE_NTT_CL_SIZE CTAs along x.
 #define HE_NTT_CL_SIZE 8
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_cluster(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+inline cudaError_t launch_cluster_n(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, int cl_size, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
@@ -216,12 +223,16 @@ inline cudaError_t launch_cluster(void (*kernel)(KArgs...), int grid, int block,
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = HE_NTT_CL_SIZE;
+    attr[0].val.clusterDim.x = (unsigned)cl_size;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_cluster(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, Args... args) {
+    return launch_cluster_n(kernel, grid, block, smem, st, HE_NTT_CL_SIZE, args...);
 }
 
 // ------------------------------------------------------------------------------------------

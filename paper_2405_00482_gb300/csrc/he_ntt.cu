@@ -65,7 +65,7 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     const uint64_t q = mc[p].q;
     tw_prefetch<CL, true>(s, twiddles(d_tw, p, 0, logn), logn);
     const int64_t *src = in + (int64_t)g * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = reduce_signed(src[k], q);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = reduce_signed(src[k], q, mc[p].mu);
     __syncthreads();
     fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + ((int64_t)g * map.n + l) * N + off;
@@ -95,7 +95,7 @@ __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__re
 #define HE_CL_MAX_POLYS 48
 
 bool use_cluster(int logn, int polys) { return logn >= HE_NTT_CL_MIN_LOGN && polys <= HE_CL_MAX_POLYS; }
-int cl_threads(int logn) { return 1 << (logn - 6); }
+int cl_threads(int logn) { return 1 << (logn - 3 - HE_NTT_CL_RADIX_LOG); }
 // the slice's padded data, then its N/8 - 1 twiddle pairs (16-byte aligned: N/8 + N/256 is even)
 size_t cl_smem_bytes(int logn) { return ntt_smem_bytes(logn - 3) + ((size_t)16 << (logn - 3)); }
 

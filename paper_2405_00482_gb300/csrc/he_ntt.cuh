@@ -157,9 +157,12 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t *s, const ulonglong2 *__re
 // index x - rank N/CL).  The stages whose butterflies span slices (the first 3 forward, the
 // last 3 inverse) are one radix-8 step through distributed shared memory: element j + c N/CL
 // lives in CTA c at local index j, and each CTA takes 1/CL of the offsets j.  The other stages
-// run on each slice with the radix-8 register passes.  Used for launches of few limb-polys,
+// run on each slice with radix-4 register passes.  Used for launches of few limb-polys,
 // where one CTA per limb-poly would leave most SMs idle.
 #define HE_NTT_CL HE_NTT_CL_SIZE
+// local passes of the cluster form are radix 4 with one set per thread (N/32 threads per CTA):
+// a cluster transform is latency-bound, so twice the warps of radix 8 with half the chain each
+#define HE_NTT_CL_RADIX_LOG 2
 
 // The local stages of a cluster member touch NS - 1 twiddles of its slice (NS = N/8): forward
 // stage t (3 <= t < log N, m = 2^t) the m/8 entries m + rank m/8 + j; inverse stage t
@@ -274,11 +277,10 @@ __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *_
     const TwSliceFwd tws{stw, rank};
     int s0 = 3;
     while (s0 < logn) {
-        const int nb = logn - s0 < 3 ? logn - s0 : 3;
+        const int nb = logn - s0 < HE_NTT_CL_RADIX_LOG ? logn - s0 : HE_NTT_CL_RADIX_LOG;
         const bool last = s0 + nb == logn;
         const int E = 1 << nb;
         switch (nb) {
-            case 3: ntt_fwd_pass<3>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
             case 2: ntt_fwd_pass<2>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
             default: ntt_fwd_pass<1>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
         }
@@ -298,10 +300,9 @@ __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *_
     const TwSliceInv tws{stw, rank, 1 << (logn - 1)};
     int s0 = 0;
     while (s0 < logn - 3) {
-        const int nb = logn - 3 - s0 < 3 ? logn - 3 - s0 : 3;
+        const int nb = logn - 3 - s0 < HE_NTT_CL_RADIX_LOG ? logn - 3 - s0 : HE_NTT_CL_RADIX_LOG;
         const int E = 1 << nb;
         switch (nb) {
-            case 3: ntt_inv_pass<3>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
             case 2: ntt_inv_pass<2>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
             default: ntt_inv_pass<1>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
         }
@@ -314,7 +315,7 @@ __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *_
 
 // the cluster form is used for rings of at least 2^10 (slices of at least 128 elements)
 #define HE_NTT_CL_MIN_LOGN 10
-__device__ __forceinline__ int cl_slice_threads(int logn) { return 1 << (logn - 6); }
+__device__ __forceinline__ int cl_slice_threads(int logn) { return 1 << (logn - 3 - HE_NTT_CL_RADIX_LOG); }
 
 // Kernels over a batch of limb-polys: in the plain form one CTA transforms a whole limb-poly
 // (grid = polys); in the cluster form (CL) a cluster of HE_NTT_CL CTAs shares one limb-poly,

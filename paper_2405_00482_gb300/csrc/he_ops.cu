@@ -170,7 +170,7 @@ __device__ __forceinline__ void rescale_body(const uint64_t *__restrict__ ct, in
         uint64_t r = lc[k] + rc.half;
         if (r >= rc.ql) r -= rc.ql;
         int64_t centred = (int64_t)r - (int64_t)rc.half;
-        s[SIDX(k)] = reduce_signed(centred, q);
+        s[SIDX(k)] = reduce_signed(centred, q, mc[j].mu);
     }
     __syncthreads();
     fwd_any<CL>(s, twiddles(d_tw, j, 0, logn), q, logn);
