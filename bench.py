@@ -227,7 +227,7 @@ def run_gpu(args):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = loop_kernel_traffic()
+    traffic = loop_kernel_traffic(pm_g.tuning()["variant"])
     clocks = clk.summary()
     value = whole_job_rate(2 * args.steps, world, total_s)
     rot_per_step = (plan_g.m_prime - 1) + (plan_f.m_prime - 1)
@@ -537,18 +537,24 @@ def run_serving(ctx, he, inputs, P, args, dev):
     return out
 
 
-def loop_kernel_traffic():
-    """DRAM bytes per launch of the loop kernel from the committed ncu capture, if the kernel's
-    source is unchanged since the capture (sha256 of he_ops.cu), else None."""
+def loop_kernel_traffic(variant: int):
+    """DRAM bytes per launch of the loop kernel from the committed ncu capture, when the kernel's
+    source region in he_ops.cu is unchanged since the capture (sha256 of that region) and the
+    timed launches ran the captured variant; else None."""
     import hashlib
 
     rec_path = os.path.join(ROOT, "profiles", "loop_kernel_traffic.json")
     try:
         rec = json.load(open(rec_path))
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        src = open(os.path.join(ROOT, rec["source"])).read()
+        start, end = rec["region"]
+        a = src.index(start)
+        region = src[a:src.index(end, a)]
     except (OSError, ValueError, KeyError):
         return None
-    return rec["dram_bytes_per_launch"] if hashlib.sha256(src).hexdigest() == rec["source_sha256"] else None
+    if hashlib.sha256(region.encode()).hexdigest() != rec["region_sha256"] or variant != rec["variant"]:
+        return None
+    return rec["dram_bytes_per_launch"]
 
 
 def oracle_one_matmult(seed: int = 0):

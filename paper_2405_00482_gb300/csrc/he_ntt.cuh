@@ -121,10 +121,14 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
 }
 
 // in-place forward transform of canonical residues in s[SIDX(0..N)); output canonical
+// The stage count left over by the radix-16 passes (log N mod 4) runs first: the early stages use
+// few distinct twiddles (stage t has 2^t), so a short pass there costs little, while the last
+// stages touch N/2 distinct twiddles and belong in full passes that load them together.
 __device__ __forceinline__ void ntt_fwd_smem(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
     int s0 = 0;
     while (s0 < logn) {
-        const int nb = logn - s0 < HE_NTT_RADIX_LOG ? logn - s0 : HE_NTT_RADIX_LOG;
+        const int first = logn % HE_NTT_RADIX_LOG;
+        const int nb = (s0 == 0 && first) ? first : HE_NTT_RADIX_LOG;
         const bool last = s0 + nb == logn;
         switch (nb) {
             case 4: ntt_fwd_pass<4>(s, TwGlobal{tw}, q, logn, s0, last); break;
