@@ -16,8 +16,8 @@
 #include "he_internal.cuh"
 #include "he_ntt.cuh"
 
-#define CD_KB 8        // columns per thread
-#define CD_TILE 32     // coefficients per block (one warp width)
+#define CD_COLS 4      // columns per lane (a warp covers 128 columns of one coefficient)
+#define CD_WARPS 8     // coefficients per block (one warp each)
 #define CD_MAX_IN 1024 // ciphertexts per launch (kernel-parameter table)
 #define CD_MAX_OUT 512 // outputs per rescale launch
 
@@ -38,54 +38,70 @@ struct OutTable {
     uint64_t *p[CD_MAX_OUT];
 };
 
-// pre[k][c][u][t] = sum_i ct_i[c][u][t] * pt_k[u][src_i(t)]
-__global__ void __launch_bounds__(512) cdiag_mac_kernel(CtTable cts, int n_ct, int nl, const uint64_t *__restrict__ pt, int K, int k_base,
-                                                        uint64_t *pre, const ModConst *__restrict__ mc, int logn) {
+// pre[k][c][u][t] = sum_i ct_i[c][u][t] * pt_k[u][src_i(t)].  Warp w of a block takes coefficient
+// t = blockIdx.x * CD_WARPS + w; lane l takes the CD_COLS columns k_base + CD_COLS l + (0..3), so
+// the warp's gather of weight row (u, src_i(t)) is one contiguous run of K words.  Ciphertext
+// words are used once and loaded with an evict-first hint, so the weight table (read once per
+// diagonal) stays in L2.  The next diagonal's operands are loaded while the current one is
+// multiplied.  Products of residues below q < 2^61 are summed 8 at a time in 128 bits.
+__global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts, int n_ct, int nl, const uint64_t *__restrict__ pt, int K,
+                                                                    int k_base, uint64_t *pre, const ModConst *__restrict__ mc, int logn) {
     const int N = 1 << logn;
     const int u = blockIdx.y;
     const uint64_t q = mc[u].q, qinv = mc[u].qinv;
-    const int t = blockIdx.x * CD_TILE + (threadIdx.x % CD_TILE);
-    const int k0 = k_base + (threadIdx.x / CD_TILE) * CD_KB;
-    if (k0 >= K) return;
-    const int kn = K - k0 < CD_KB ? K - k0 : CD_KB;
-    u128 a0[CD_KB], a1[CD_KB];
-    uint64_t r0[CD_KB], r1[CD_KB];
-#pragma unroll
-    for (int kk = 0; kk < CD_KB; ++kk) a0[kk] = a1[kk] = 0, r0[kk] = r1[kk] = 0;
+    const int t = blockIdx.x * CD_WARPS + (threadIdx.x >> 5);
+    const int k0 = k_base + (threadIdx.x & 31) * CD_COLS;
+    if (k0 >= K) return;  // no block-wide synchronisation below
+    const int kn = K - k0 < CD_COLS ? K - k0 : CD_COLS;
+    const bool vec = kn == CD_COLS && (K & 1) == 0;  // rows start 16-byte aligned when K is even
     const uint32_t two_n_mask = (2u << logn) - 1;
-    uint32_t g = 1;
-    int pending = 0;
-    for (int i = 0; i < n_ct; ++i) {
-        const uint32_t src = automorph_src(t, g, logn);
-        const uint64_t c0 = __ldg(cts.p[i] + (int64_t)u * N + t);
-        const uint64_t c1 = __ldg(cts.p[i] + ((int64_t)nl + u) * N + t);
-        const uint64_t *row = pt + ((int64_t)u * N + src) * K + k0;
-        if (kn == CD_KB && (K % 2) == 0) {
+    u128 a0[CD_COLS], a1[CD_COLS];
+    uint64_t r0[CD_COLS], r1[CD_COLS];
 #pragma unroll
-            for (int kk = 0; kk < CD_KB; kk += 2) {
-                const ulonglong2 pv = __ldg(reinterpret_cast<const ulonglong2 *>(row + kk));
-                a0[kk] += (u128)c0 * pv.x;
-                a1[kk] += (u128)c1 * pv.x;
-                a0[kk + 1] += (u128)c0 * pv.y;
-                a1[kk + 1] += (u128)c1 * pv.y;
+    for (int kk = 0; kk < CD_COLS; ++kk) a0[kk] = a1[kk] = 0, r0[kk] = r1[kk] = 0;
+    // operands of diagonal i: c0, c1 at t; weights at row src_i(t)
+    uint64_t c0n, c1n, pvn[CD_COLS];
+    auto fetch = [&](int i, uint32_t g) {
+        const uint32_t src = automorph_src(t, g, logn);
+        c0n = __ldcs(cts.p[i] + (int64_t)u * N + t);
+        c1n = __ldcs(cts.p[i] + ((int64_t)nl + u) * N + t);
+        const uint64_t *row = pt + ((int64_t)u * N + src) * K + k0;
+        if (vec) {
+#pragma unroll
+            for (int kk = 0; kk < CD_COLS; kk += 2) {
+                const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(row + kk));
+                pvn[kk] = v.x;
+                pvn[kk + 1] = v.y;
             }
         } else {
-            for (int kk = 0; kk < kn; ++kk) {
-                const uint64_t pv = __ldg(row + kk);
-                a0[kk] += (u128)c0 * pv;
-                a1[kk] += (u128)c1 * pv;
-            }
-        }
-        if (++pending == 8) {  // 8 products of residues below q < 2^61 stay below q 2^64
 #pragma unroll
-            for (int kk = 0; kk < CD_KB; ++kk) {
+            for (int kk = 0; kk < CD_COLS; ++kk) pvn[kk] = kk < kn ? __ldg(row + kk) : 0;
+        }
+    };
+    uint32_t g = 1;
+    fetch(0, g);
+    int pending = 0;
+    for (int i = 0; i < n_ct; ++i) {
+        const uint64_t c0 = c0n, c1 = c1n;
+        uint64_t pv[CD_COLS];
+#pragma unroll
+        for (int kk = 0; kk < CD_COLS; ++kk) pv[kk] = pvn[kk];
+        g = (uint32_t)(((uint64_t)g * 5u) & two_n_mask);
+        if (i + 1 < n_ct) fetch(i + 1, g);
+#pragma unroll
+        for (int kk = 0; kk < CD_COLS; ++kk) {
+            a0[kk] += (u128)c0 * pv[kk];
+            a1[kk] += (u128)c1 * pv[kk];
+        }
+        if (++pending == 8) {
+#pragma unroll
+            for (int kk = 0; kk < CD_COLS; ++kk) {
                 r0[kk] = add_mod(r0[kk], redc128(a0[kk], q, qinv), q);
                 r1[kk] = add_mod(r1[kk], redc128(a1[kk], q, qinv), q);
                 a0[kk] = a1[kk] = 0;
             }
             pending = 0;
         }
-        g = (uint32_t)(((uint64_t)g * 5u) & two_n_mask);
     }
     for (int kk = 0; kk < kn; ++kk) {
         r0[kk] = add_mod(r0[kk], redc128(a0[kk], q, qinv), q);
@@ -259,13 +275,11 @@ int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct,
     uint64_t *last = pre + K * 2 * nl * N;
     CtTable tab;
     for (int i = 0; i < n_ct; ++i) tab.p[i] = cts[i].data;
-    const int kmax = (512 / CD_TILE) * CD_KB;  // 128 columns (16 warps) per launch
+    const int kmax = 32 * CD_COLS;  // columns per launch (one warp's lanes)
     for (int64_t kb = 0; kb < K; kb += kmax) {
-        const int kn = (int)std::min<int64_t>(kmax, K - kb);
-        const int threads = CD_TILE * ((kn + CD_KB - 1) / CD_KB);
-        const dim3 grid((unsigned)(N / CD_TILE), (unsigned)nl);
+        const dim3 grid((unsigned)(N / CD_WARPS), (unsigned)nl);
         ctx->launches++;
-        cdiag_mac_kernel<<<grid, threads, 0, ctx->stream>>>(tab, n_ct, nl, W->pt, (int)K, (int)kb, pre, ctx->d_mc, ctx->log_n);
+        cdiag_mac_kernel<<<grid, CD_WARPS * 32, 0, ctx->stream>>>(tab, n_ct, nl, W->pt, (int)K, (int)kb, pre, ctx->d_mc, ctx->log_n);
     }
     // rescale every output: inverse NTT of the last limb of both components, then per (k, c, j)
     LimbMap lm{};
