@@ -130,6 +130,12 @@ int he_rescale(he_ctx *ctx, const he_ct *in, he_ct *out);
 int he_rotate(he_ctx *ctx, const he_ct *in, int32_t step, he_ct *out);
 /* O4 (Sec. 2.2): outs[i] = RotL(in, steps[i]) for i < k, sharing one decomposition of c1. */
 int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, int k, he_ct *outs);
+/* O3 on many different ciphertexts, each by its own step (outs[i] = RotL(ins[i], steps[i]),
+ * bit-identical to he_rotate per pair), as one launch per stage over all of them (in chunks of
+ * 64): ModUp, key-switch inner product, ModDown.  All inputs at one level; outputs must not
+ * overlap any input (HE_EINVAL); a missing Galois key gives HE_EKEY; steps that are multiples
+ * of N/2 copy. */
+int he_rotate_many(he_ctx *ctx, const he_ct *ins, const int32_t *steps, int count, he_ct *outs);
 
 /* Host only: plan the MatMult of an m x n matrix with n-vectors in `slots` (= N/2) slots:
  * zero padding to powers of two (Sec. 3), input packing with m' = ceil(m n / N') (Eq. 3),

@@ -574,6 +574,50 @@ int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, int k,
 
 int he_rotate(he_ctx *ctx, const he_ct *in, int32_t step, he_ct *out) { return he_rotate_hoisted(ctx, in, &step, 1, out); }
 
+int he_rotate_many(he_ctx *ctx, const he_ct *ins, const int32_t *steps, int count, he_ct *outs) {
+    if (!ctx || count < 0 || (count > 0 && (!ins || !steps || !outs))) return HE_EINVAL;
+    if (count == 0) return HE_OK;
+    const int level = ins[0].level;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    const size_t N = ctx->n, ct_words = 2 * (size_t)(level + 1) * N;
+    for (int i = 0; i < count; ++i) {
+        if (!ins[i].data || !outs[i].data) return HE_EINVAL;
+        if (ins[i].level != level) return HE_ELEVEL;
+        for (int j = 0; j < count; ++j)  // outputs are written while later jobs still read inputs
+            if (outs[i].data < ins[j].data + ct_words && ins[j].data < outs[i].data + ct_words) return HE_EINVAL;
+    }
+    std::vector<RotJob> jobs;
+    jobs.reserve(count);
+    for (int i = 0; i < count; ++i) {
+        const int64_t half = ctx->n / 2;
+        if (((int64_t)steps[i] % half + half) % half == 0) {  // RotL by a multiple of N/2 is the identity
+            if (cudaMemcpyAsync(outs[i].data, ins[i].data, ct_words * sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+                return HE_ECUDA;
+            continue;
+        }
+        const uint32_t g = galois_of(ctx, steps[i]);
+        auto it = ctx->keys.find(g);
+        if (it == ctx->keys.end()) return HE_EKEY;
+        jobs.push_back(RotJob{ins[i].data, outs[i].data, it->second, g, 0});
+    }
+    const int n_jobs = (int)jobs.size();
+    if (n_jobs > 0) {
+        const int chunk = n_jobs < 64 ? n_jobs : 64;
+        const size_t job_words = (sizeof(RotJob) * (size_t)n_jobs + 7) / 8;
+        uint64_t *s = ctx_scratch(ctx, (size_t)chunk * rotate_many_words(ctx, level) + job_words);
+        if (!s) return HE_ENOMEM;
+        RotJob *d_jobs = reinterpret_cast<RotJob *>(s + (size_t)chunk * rotate_many_words(ctx, level));
+        // from pageable memory the copy stages the table before returning, so `jobs` may go
+        if (cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(RotJob) * n_jobs, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) return HE_ECUDA;
+        for (int c0 = 0; c0 < n_jobs; c0 += chunk) launch_rotate_many(ctx, d_jobs + c0, std::min(chunk, n_jobs - c0), level, s);
+    }
+    for (int i = 0; i < count; ++i) {
+        outs[i].level = level;
+        outs[i].scale = ins[i].scale;
+    }
+    return last_launch();
+}
+
 int he_plan_create(int64_t m, int64_t n, int64_t slots, he_plan **out) {
     if (!out) return HE_EINVAL;
     *out = nullptr;

@@ -328,20 +328,14 @@ int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_c
         if (!cts[k].data || !outs[i].data || outs[i].data == cts[k].data) return HE_EINVAL;
         if (cts[k].level != cts[0].level) return HE_ELEVEL;
     }
+    // all rotations in one batch (steps that are multiples of N/2, here r = 0, are copies)
+    std::vector<he_ct> ins((size_t)lo);
+    std::vector<int32_t> steps((size_t)lo);
     for (int64_t i = 0; i < lo; ++i) {
-        const int64_t k = kr[(size_t)i].first;
-        const int32_t r = kr[(size_t)i].second;
-        if (r == 0) {
-            const size_t words = 2 * (size_t)(cts[k].level + 1) * ctx->n;
-            if (cudaMemcpyAsync(outs[i].data, cts[k].data, words * 8, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) return HE_ECUDA;
-            outs[i].level = cts[k].level;
-            outs[i].scale = cts[k].scale;
-        } else {
-            const int rc = he_rotate(ctx, &cts[k], r, &outs[i]);
-            if (rc != HE_OK) return rc;
-        }
+        ins[(size_t)i] = cts[kr[(size_t)i].first];
+        steps[(size_t)i] = kr[(size_t)i].second;
     }
-    return HE_OK;
+    return he_rotate_many(ctx, ins.data(), steps.data(), (int)lo, outs);
 }
 
 int he_cdiag_decode(he_ctx *ctx, int64_t m, int64_t n, int64_t K, const double *slots, double *Z) {

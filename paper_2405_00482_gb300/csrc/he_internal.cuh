@@ -153,6 +153,15 @@ struct MMJob {
     int32_t m_prime;
 };
 
+// one rotation of a batch of rotations (each job its own ciphertext and step)
+struct RotJob {
+    const uint64_t *ct;   // input [2][level+1][N]
+    uint64_t *out;        // output [2][level+1][N], not aliasing any input of the batch
+    const uint64_t *key;  // Galois key of the step
+    uint32_t g;           // Galois element
+    int32_t pad;
+};
+
 // shared geometry and per-job scratch strides of a batch
 struct BatchGeom {
     int32_t ndig, ext, nq, L, LK, K, level;
@@ -200,6 +209,9 @@ struct he_batch {
 };
 
 int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
+// words of scratch per rotation job at `level`, and the launches of `count` jobs (device table)
+size_t rotate_many_words(const he_ctx *ctx, int level);
+void launch_rotate_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, uint64_t *scratch);
 int mm_variant_count();
 int mm_variant_tile(int v);  // coefficients per tile of loop-kernel variant v
 void mm_variant_shape(int v, int *vec, int *grp, int *stages, int *ga);

@@ -188,6 +188,92 @@ __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const
     rescale_body<CL>(ct, level, last_coef, rc, out, item / level, item % level, s, d_tw, mc, logn, off, len);
 }
 
+// ---- many rotations: O3 of different ciphertexts, each by its own step, one launch per stage ----
+// (the same definition as launch_rotate: ModUp of c1, key-switch inner product after the
+// automorphism, ModDown, plus the automorphism of c0; bit-identical to one he_rotate per job)
+struct RotGeom {
+    int32_t nl, ext, K, L, LK;
+    uint64_t *coef, *D, *u, *pcoef, *rc0;  // per-job scratch
+    int64_t coef_w, d_w, u_w, p_w, r_w;    // their strides
+};
+
+__global__ void rot_intt_c1_kernel(const RotJob *__restrict__ jobs, RotGeom rg, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+                                   int logn) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int j = blockIdx.x / rg.nl, l = blockIdx.x % rg.nl;
+    const uint64_t q = mc[l].q;
+    const uint64_t *src = jobs[j].ct + ((int64_t)rg.nl + l) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    __syncthreads();
+    ntt_inv_smem(s, twiddles(d_tw, l, 1, logn), q, logn);
+    uint64_t *dst = rg.coef + j * rg.coef_w + (int64_t)l * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], mc[l].ninv, mc[l].ninv_shoup, q);
+}
+
+__global__ void rot_modup_kernel(const RotJob *__restrict__ jobs, RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                 const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int per = mu.ndig * mu.ext;
+    const int j = blockIdx.x / per, rest = blockIdx.x % per;
+    modup_body<false>(jobs[j].ct + (int64_t)rg.nl * (1 << logn), rg.coef + j * rg.coef_w, rg.D + j * rg.d_w, mu, rest / mu.ext, rest % mu.ext, s,
+                      d_tw, mc, logn, 0, 1 << logn);
+}
+
+// u_c[u][k] = sum_d D[d][u][src(k)] key[d][c][kl(u)][k] (REDC per 8 digits); rc0[u][k] = c0[u][src(k)]
+__global__ void rot_ks_kernel(const RotJob *__restrict__ jobs, RotGeom rg, int ndig, const ModConst *__restrict__ mc, int logn) {
+    const int N = 1 << logn;
+    const int u = blockIdx.y, j = blockIdx.z;
+    const int p = u < rg.nl ? u : rg.L + (u - rg.nl);
+    const uint64_t q = mc[p].q, qinv = mc[p].qinv;
+    const RotJob jb = jobs[j];
+    const uint64_t *D = rg.D + j * rg.d_w;
+    uint64_t *out = rg.u + j * rg.u_w;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const uint32_t src = automorph_src(k, jb.g, logn);
+        uint64_t r0 = 0, r1 = 0;
+        for (int d0 = 0; d0 < ndig; d0 += 8) {
+            u128 t0 = 0, t1 = 0;
+            for (int d = d0; d < ndig && d < d0 + 8; ++d) {
+                const uint64_t dv = D[((int64_t)d * rg.ext + u) * N + src];
+                t0 += (u128)dv * jb.key[((int64_t)(d * 2 + 0) * rg.LK + p) * N + k];
+                t1 += (u128)dv * jb.key[((int64_t)(d * 2 + 1) * rg.LK + p) * N + k];
+            }
+            r0 = add_mod(r0, redc128(t0, q, qinv), q);
+            r1 = add_mod(r1, redc128(t1, q, qinv), q);
+        }
+        out[(int64_t)u * N + k] = r0;
+        out[((int64_t)rg.ext + u) * N + k] = r1;
+        if (u < rg.nl) rg.rc0[j * rg.r_w + (int64_t)u * N + k] = jb.ct[(int64_t)u * N + src];
+    }
+}
+
+// iNTT of the P limbs of both components of u: block (j, c, i) -> pcoef_j [c][K][N]
+__global__ void rot_intt_p_kernel(const RotJob *__restrict__ jobs, RotGeom rg, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+                                  int logn) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    const int per = 2 * rg.K;
+    const int j = blockIdx.x / per, c = (blockIdx.x % per) / rg.K, i = blockIdx.x % rg.K;
+    const int p = rg.L + i;
+    const uint64_t q = mc[p].q;
+    const uint64_t *src = rg.u + j * rg.u_w + ((int64_t)c * rg.ext + rg.nl + i) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    __syncthreads();
+    ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
+    uint64_t *dst = rg.pcoef + j * rg.p_w + ((int64_t)c * rg.K + i) * N;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], mc[p].ninv, mc[p].ninv_shoup, q);
+}
+
+__global__ void rot_moddown_kernel(const RotJob *__restrict__ jobs, RotGeom rg, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                   const ModConst *__restrict__ mc, int logn) {
+    extern __shared__ uint64_t s[];
+    const int per = 2 * md.nq;
+    const int j = blockIdx.x / per, c = (blockIdx.x % per) / md.nq, l = blockIdx.x % md.nq;
+    moddown_body<false>(rg.u + j * rg.u_w, rg.ext, rg.pcoef + j * rg.p_w, md, c == 0 ? rg.rc0 + j * rg.r_w : nullptr, jobs[j].out, c, l, s, d_tw,
+                        mc, logn, 0, 1 << logn);
+}
+
 // ---- batch forms: the same bodies over a job table (one job = one MatMult, R = C = 1) ----
 // iNTT of limbs [first, first + count) of component `comp` of the job's buffer `which`
 // (0: input ciphertext, 1: accumulator acc, 2: pre-rescale sum) into scratch.
@@ -1022,6 +1108,51 @@ int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
 }
 
 
+static RotGeom rot_geom(const he_ctx *ctx, int level, uint64_t *scratch, int count) {
+    const ModUpConst &mu = ctx->modup[level];
+    const int64_t N = ctx->n, nl = level + 1;
+    RotGeom rg{};
+    rg.nl = (int32_t)nl;
+    rg.ext = mu.ext;
+    rg.K = ctx->K;
+    rg.L = ctx->L;
+    rg.LK = ctx->L + ctx->K;
+    rg.coef_w = nl * N;
+    rg.d_w = (int64_t)mu.ndig * mu.ext * N;
+    rg.u_w = 2 * (int64_t)mu.ext * N;
+    rg.p_w = 2 * (int64_t)ctx->K * N;
+    rg.r_w = nl * N;
+    rg.coef = scratch;
+    rg.D = rg.coef + count * rg.coef_w;
+    rg.u = rg.D + count * rg.d_w;
+    rg.pcoef = rg.u + count * rg.u_w;
+    rg.rc0 = rg.pcoef + count * rg.p_w;
+    return rg;
+}
+
+size_t rotate_many_words(const he_ctx *ctx, int level) {
+    const ModUpConst &mu = ctx->modup[level];
+    const size_t N = ctx->n, nl = level + 1;
+    return nl * N + (size_t)mu.ndig * mu.ext * N + 2 * (size_t)mu.ext * N + 2 * (size_t)ctx->K * N + nl * N;
+}
+
+void launch_rotate_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, uint64_t *scratch) {
+    if (count == 0) return;
+    const ModUpConst &mu = ctx->modup[level];
+    const ModDownConst &md = ctx->moddown[level];
+    const RotGeom rg = rot_geom(ctx, level, scratch, count);
+    const int thr = ntt_threads(ctx->log_n);
+    const size_t smem = ntt_smem_bytes(ctx->log_n);
+    cudaStream_t st = ctx->stream;
+    rot_intt_c1_kernel<<<count * rg.nl, thr, smem, st>>>(d_jobs, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    rot_modup_kernel<<<count * mu.ndig * mu.ext, thr, smem, st>>>(d_jobs, rg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    rot_ks_kernel<<<dim3((unsigned)((ctx->n + 255) / 256), (unsigned)mu.ext, (unsigned)count), 256, 0, st>>>(d_jobs, rg, mu.ndig, ctx->d_mc,
+                                                                                                          ctx->log_n);
+    rot_intt_p_kernel<<<count * 2 * ctx->K, thr, smem, st>>>(d_jobs, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    rot_moddown_kernel<<<count * 2 * md.nq, thr, smem, st>>>(d_jobs, rg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    ctx->launches += 5;
+}
+
 void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(batch_intt_c1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(batch_modup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
@@ -1029,6 +1160,10 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(batch_moddown_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(batch_intt_last_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(batch_rescale_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(rot_intt_c1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(rot_modup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(rot_intt_p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(rot_moddown_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(modup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(moddown_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);

@@ -61,6 +61,7 @@ _SIGS = {
     "he_mul_plain": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HePt), ctypes.POINTER(HeCt)]),
     "he_rescale": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
     "he_rotate": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _i32, ctypes.POINTER(HeCt)]),
+    "he_rotate_many": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(ctypes.c_int32), ctypes.c_int, ctypes.POINTER(HeCt)]),
     "he_rotate_hoisted": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(_i32), ctypes.c_int, ctypes.POINTER(HeCt)]),
     "he_plan_create": (ctypes.c_int, [_i64, _i64, _i64, ctypes.POINTER(_vp)]),
     "he_plan_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
@@ -439,6 +440,17 @@ class Context:
         _check(_lib().he_mul_plain(self.handle, ctypes.byref(c), ctypes.byref(p), ctypes.byref(o)), "he_mul_plain")
         out.scale = o.scale
         return out
+
+    def rotate_many(self, cts: list[Ciphertext], steps: list[int], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
+        """outs[i] = RotL(cts[i], steps[i]) for many ciphertexts, one launch per stage."""
+        outs = outs or [self.new_ct(c.level) for c in cts]
+        ia = (HeCt * len(cts))(*[c.c() for c in cts])
+        oa = (HeCt * len(outs))(*[o.c() for o in outs])
+        st = (ctypes.c_int32 * len(steps))(*steps)
+        _check(_lib().he_rotate_many(self.handle, ia, st, len(cts), oa), "he_rotate_many")
+        for o, a in zip(outs, oa):
+            o.level, o.scale = a.level, a.scale
+        return outs
 
     def rescale(self, ct: Ciphertext) -> Ciphertext:
         out = self.new_ct(max(ct.level - 1, 0))
