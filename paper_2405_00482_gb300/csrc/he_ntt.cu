@@ -90,6 +90,8 @@ __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__re
 // One-CTA form: N/16 threads (one radix-16 set each) up to 256, so that two CTAs (two limb-polys)
 // share an SM and one's barriers overlap the other's work (the passes use ~110 registers); from
 // N = 2^14 a limb-poly's shared memory allows one CTA per SM, which then takes 512 threads.
+// (Radix-8 passes need ~72 registers and fit three CTAs per SM at N = 2^13, but the extra pass
+// made the N = 2^13 plain step 2% slower on GB300.)
 // Threads loop over several sets when there are more sets than threads.
 // cluster form for launches of at most this many limb-polys (one CTA each would leave most SMs idle)
 #define HE_CL_MAX_POLYS 48
