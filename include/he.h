@@ -156,6 +156,10 @@ int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X);
 /* Same object from integer plaintexts already encoded elsewhere: coeffs (device) holds
  * [R][C][m'][level+1+n_p][N] canonical residues in coefficient form over q_0..q_level, p_*. */
 int he_ptmat_import(he_ctx *ctx, const he_plan *plan, const uint64_t *coeffs, int level, double scale, he_ptmat **out);
+/* The inverse of he_ptmat_import: the encoded matrix's plaintexts in canonical coefficient form,
+ * [R][C][m'][level+1+K][N] words, into caller-owned device memory (for parity checks and
+ * transport). */
+int he_ptmat_export(he_ctx *ctx, const he_ptmat *pm, uint64_t *coeffs_out);
 void he_ptmat_free(he_ptmat *pm);
 
 /* P_B's side: replicate piece c of y (device, n doubles) N'/nb times and encode it into
@@ -203,8 +207,8 @@ void he_batch_free(he_batch *batch);
  * steps ahead through a per-thread cp.async pipeline in shared memory that carries the key and
  * plaintext streams and, in the "gathers" variants, the automorphism gathers of the ModUp
  * digits and c0 too.  The first he_matmult_plain_cipher call with an encoded matrix, and the
- * first he_batch_run of a batch, time each variant once (synchronising the stream) and keep the
- * fastest.  he_loop_variant_count gives the number of variants (at most HE_MM_MAX_VARIANTS);
+ * first he_batch_run of a batch, time each variant (best of a few runs, synchronising the
+ * stream) and keep the fastest.  he_loop_variant_count gives the number of variants (at most HE_MM_MAX_VARIANTS);
  * he_loop_variant_shape the (vec, groups, stages, gathers) of variant v (HE_EINVAL if v is out
  * of range).  The tuning queries report the choice (-1 before the first call) and write the
  * timed milliseconds of every variant to ms[0 .. count-1] (ms may be NULL; else it holds

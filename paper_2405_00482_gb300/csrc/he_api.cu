@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -153,6 +154,27 @@ static LimbMap qpmap(const he_ctx *ctx, int level) {
     return m;
 }
 
+// The kernels' dynamic shared-memory limits are per function and per process, so they are set
+// once per device to the device's opt-in maximum (a context with a smaller ring must not lower
+// the limit that another context's launches need); the limit only permits, it reserves nothing.
+static int set_smem_limits_once() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HE_ECUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return HE_OK;
+    int smem = 0;
+    if (cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || smem <= 0) return HE_ECUDA;
+    ntt_set_smem_limits(smem);
+    ops_set_smem_limits(smem);
+    encode_set_smem_limits(smem);
+    cdiag_set_smem_limits(smem);
+    if (cudaGetLastError() != cudaSuccess) return HE_ECUDA;
+    done[dev] = true;
+    return HE_OK;
+}
+
 static uint32_t galois_of(const he_ctx *ctx, int64_t step) {
     const int64_t slots = ctx->n / 2;
     int64_t r = ((step % slots) + slots) % slots;
@@ -239,11 +261,11 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     }
     he_cdt_table(ctx->cdt);
     const int LK = ctx->L + ctx->K, N = ctx->n;
-    const int smem = (int)ntt_smem_bytes(ctx->log_n);  // >= the 8N bytes of the FFT kernels
-    ntt_set_smem_limits(smem);
-    ops_set_smem_limits(smem);
-    encode_set_smem_limits(smem);
-    cdiag_set_smem_limits(smem);
+    rc = set_smem_limits_once();
+    if (rc != HE_OK) {
+        delete ctx;
+        return rc;
+    }
 
     // per-prime constants and NTT twiddles
     std::vector<uint64_t> tw((size_t)LK * 4 * N);
@@ -701,6 +723,17 @@ int he_encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int leve
     return rc;
 }
 
+int he_ptmat_export(he_ctx *ctx, const he_ptmat *pm, uint64_t *coeffs_out) {
+    if (!ctx || !pm || !coeffs_out || pm->ctx != ctx) return HE_EINVAL;
+    const he_plan &p = pm->plan;
+    const int count = (int)(p.row_blocks * p.col_blocks * p.m_prime);
+    const LimbMap m = qpmap(ctx, pm->level);
+    const int64_t gs = (int64_t)m.n * ctx->n;
+    launch_from_mont(ctx, pm->data, coeffs_out, count, m);
+    launch_ntt_inv_strided(ctx, coeffs_out, gs, coeffs_out, gs, count, m);
+    return last_launch();
+}
+
 int he_ptmat_import(he_ctx *ctx, const he_plan *plan, const uint64_t *coeffs, int level, double scale, he_ptmat **out) {
     if (!coeffs) return HE_EINVAL;
     int rc = ptmat_alloc(ctx, plan, level, scale, out);
@@ -976,13 +1009,15 @@ int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
         float best_ms = 1e30f;
         for (int v = 0; v < mm_variant_count(); ++v) {
             b->variant = v;
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {  // one untimed run, then the better of two
                 cudaEventRecord(e0, b->stream);
                 if (launch_matmult_batch(ctx, b, b->stream) != HE_OK) break;
                 cudaEventRecord(e1, b->stream);
                 if (cudaEventSynchronize(e1) != cudaSuccess) break;
-                cudaEventElapsedTime(&ms, e0, e1);
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0 && t < ms) ms = t;
             }
             b->tune_ms[v] = ms;
             if (ms < best_ms) {

@@ -254,6 +254,7 @@ int he_check(cudaError_t e);
 uint64_t *ctx_scratch(he_ctx *ctx, size_t words);  // nullptr on allocation failure
 
 // NTT of `groups` x map.n limb-polys; in and out may alias.
+void launch_from_mont(he_ctx *ctx, const uint64_t *data, uint64_t *out, int groups, const LimbMap &map);
 void launch_ntt_fwd(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map);
 void launch_ntt_inv(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map);
 // strided forms: limb l of group g at base + g * gs + l * N; to_mont stores x 2^64 mod q

@@ -77,6 +77,15 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     }
 }
 
+// out = data 2^-64 mod q (Montgomery form back to canonical); grid (blocks, groups, limbs)
+__global__ void from_mont_kernel(const uint64_t *__restrict__ data, uint64_t *out, LimbMap map, const ModConst *__restrict__ mc, int logn) {
+    const int N = 1 << logn;
+    const int g = blockIdx.y, l = blockIdx.z;
+    const int p = map.prime[l];
+    const int64_t base = ((int64_t)g * map.n + l) * N;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) out[base + k] = mont_mul(data[base + k], 1, mc[p].q, mc[p].qinv);
+}
+
 __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__restrict__ mc, int logn) {
     const int N = 1 << logn;
     const int g = blockIdx.y, l = blockIdx.z;
@@ -131,6 +140,13 @@ void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
     else
         ntt_inv_kernel<false><<<polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
                                                                                                         ctx->d_mc, ctx->log_n);
+}
+
+void launch_from_mont(he_ctx *ctx, const uint64_t *data, uint64_t *out, int groups, const LimbMap &map) {
+    if (groups * map.n == 0) return;
+    ctx->launches++;
+    from_mont_kernel<<<dim3((unsigned)((ctx->n + 255) / 256), (unsigned)groups, (unsigned)map.n), 256, 0, ctx->stream>>>(data, out, map, ctx->d_mc,
+                                                                                                                     ctx->log_n);
 }
 
 void launch_ntt_fwd(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map) {

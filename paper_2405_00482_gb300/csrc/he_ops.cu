@@ -1023,14 +1023,17 @@ int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint6
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < mm_variant_count(); ++v) {
-        float ms = 0.0f;
-        for (int rep = 0; rep < 2; ++rep) {  // the first launch of a variant also loads its code
+        // one untimed launch (it also loads the variant's code), then the best of three
+        float ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
             cudaEventRecord(a, ctx->stream);
             mm_launch_variant(ctx, v, ct, D, pm->data, pm->d_keys, pm->d_galois, (int)pm->plan.m_prime, mu.ndig, mu.ext, pm->level + 1, acc, cacc,
                               0);
             cudaEventRecord(b, ctx->stream);
             if (cudaEventSynchronize(b) != cudaSuccess) break;
-            cudaEventElapsedTime(&ms, a, b);
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, a, b);
+            if (rep > 0 && t < ms) ms = t;
         }
         pm->tune_ms[v] = ms;
         if (ms < best_ms) {

@@ -68,6 +68,7 @@ _SIGS = {
     "he_plan_free": (None, [_vp]),
     "he_encode_matrix": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_ptmat_encode": (ctypes.c_int, [_vp, _vp, _vp]),
+    "he_ptmat_export": (ctypes.c_int, [_vp, _vp, _vp]),
     "he_ptmat_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(_vp)]),
     "he_ptmat_free": (None, [_vp]),
     "he_encode_vector": (ctypes.c_int, [_vp, _vp, _vp, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
@@ -230,6 +231,14 @@ class PtMatrix:
     def set_variant(self, v: int) -> None:
         """Pin the loop-kernel variant (-1: tune again on the next MatMult)."""
         _check(_lib().he_ptmat_set_variant(self.handle, v), "he_ptmat_set_variant")
+
+    def export(self) -> torch.Tensor:
+        """Plaintexts [R][C][m'][level+1+K][N] in canonical coefficient form (int64 storage)."""
+        p = self.plan
+        limbs = self.level + 1 + self.ctx.K
+        out = torch.empty((p.row_blocks, p.col_blocks, p.m_prime, limbs, self.ctx.n), dtype=torch.int64, device=self.ctx.device)
+        _check(_lib().he_ptmat_export(self.ctx.handle, self.handle, out.data_ptr()), "he_ptmat_export")
+        return out
 
     def __del__(self):
         if getattr(self, "handle", None):

@@ -253,3 +253,59 @@ def test_missing_key_and_level_errors(he):
     with pytest.raises(he.HEError) as e:
         ctx.rescale(ctx.rescale(low))
     assert e.value.status == he.HE_ELEVEL
+
+
+@pytest.mark.parametrize("name,m,n", [("n8192", 256, 1024), ("n8192", 1024, 256), ("n8192", 300, 5000), ("n4096", 64, 16),
+                                      ("n1024_alpha2", 100, 300), ("n32", 17, 31)])
+def test_encode_matrix_against_oracle(he, name, m, n):
+    """Eq. 2 / Eq. 3 plaintexts from fp64 X (layout, cluster FFT, NTT of every limb): every limb of
+    Q_level U P equals the oracle's rounding of the exact encoding, except where the exact value
+    is within the double-float window of a half-integer, and there by one."""
+    import torch
+
+    ctx, o = pair(he, name)
+    rng = np.random.default_rng(m + 3 * n)
+    X = rng.normal(size=(m, n))
+    level = o.L - 1
+    plan_o, plan_g = layout.make_plan(m, n, o.slots), he.Plan(m, n, o.slots)
+    pm = ctx.encode_matrix(plan_g, torch.from_numpy(X).cuda(), level)
+    got = he.as_u64(pm.export())
+    E = layout.diagonal_slots(X, plan_o)
+    primes = o.level_primes(level, True)
+    scale = float(o.q[level])
+    total_diff = total = 0
+    idxs = list(np.ndindex(*E.shape[:3]))
+    if len(idxs) > 32:  # a fixed sample of the diagonals (first, last, random middle)
+        pick = sorted(set([0, len(idxs) - 1] + list(np.random.default_rng(1).choice(len(idxs), 30, replace=False))))
+        idxs = [idxs[i] for i in pick]
+    for idx in idxs:
+        exact = encoding.encode_real(E[idx], scale, o.n)
+        ints = np.rint(exact).astype(np.int64)  # |coefficients| < 2^50
+        frac = np.abs(exact - np.floor(exact) - 0.5)
+        for li, q in enumerate(primes):
+            want = np.mod(ints, np.int64(q)).astype(np.uint64)
+            g = got[idx + (li,)]
+            diff = g != want
+            assert np.all(frac[diff] < 1e-2)
+            off = (g[diff].astype(object) - want[diff].astype(object)) % q
+            assert all(v in (1, q - 1) for v in off)
+            total_diff += int(diff.sum())
+            total += g.size
+    assert total_diff <= 0.03 * total
+
+
+def test_small_context_does_not_limit_a_large_one(he):
+    """Kernel shared-memory limits are per process: creating an N = 32 context after an N = 8192
+    one must leave the large context's launches (one-CTA NTTs above 48 KB) working."""
+    import torch
+
+    big = he.Context(13, [60, 40, 40], [60], 3, seed=41)
+    he.Context(5, [60, 40, 40], [60], 3, seed=42)
+    plan = he.Plan(256, 1024, big.slots)
+    big.keygen(list(range(1, plan.m_prime)))
+    X = torch.randn(256, 1024, dtype=torch.float64, device="cuda")
+    y = torch.rand(1024, dtype=torch.float64, device="cuda") * 2 - 1
+    pm = big.encode_matrix(plan, X, 2)
+    out = big.matmult(plan, pm, [big.encrypt(big.encode_vector(plan, y, 2.0**40, 2)[0], 1)])
+    res = big.matmult_decode(plan, torch.stack([big.decrypt(c) for c in out]))
+    assert torch.abs(res - X @ y).max().item() < 1e-4
