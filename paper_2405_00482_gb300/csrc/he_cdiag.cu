@@ -46,6 +46,7 @@ struct OutTable {
 // multiplied.  Products of residues below q < 2^61 are summed 8 at a time in 128 bits.
 __global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts, int n_ct, int nl, const uint64_t *__restrict__ pt, int K,
                                                                     int k_base, uint64_t *pre, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int u = blockIdx.y;
     const uint64_t q = mc[u].q, qinv = mc[u].qinv;
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts
 
 // encoded columns [K][nl][N] -> transposed [nl][N][K]
 __global__ void transpose_cols_kernel(const uint64_t *__restrict__ in, uint64_t *out, int K, int nl, int logn) {
+    HE_GRID_DEP();
     const int64_t N = 1 << logn;
     const int64_t total = (int64_t)K * nl * N;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -130,6 +132,7 @@ struct CdRescale {
 // CTA (k, c, j): v = centred(last limb of output k) mod q_j -> NTT -> out_k = (pre_j - v) q_l^-1
 __global__ void cdiag_rescale_kernel(const uint64_t *__restrict__ pre, const uint64_t *__restrict__ last, int level, CdRescale rc, OutTable outs,
                                      int k_first, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn, nl = level + 1;
     const int per = 2 * level;
@@ -151,6 +154,7 @@ __global__ void cdiag_rescale_kernel(const uint64_t *__restrict__ pre, const uin
 
 // slots of the diagonals e_i[j] = A[j mod m, (i + j) mod n], repeated over the N/2 slots
 __global__ void cdiag_layout_kernel(const double *__restrict__ A, int64_t m, int64_t n, int64_t slots, double *out) {
+    HE_GRID_DEP();
     const int64_t lo = m < n ? m : n, hi = m < n ? n : m;
     const int64_t total = lo * slots;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -161,6 +165,7 @@ __global__ void cdiag_layout_kernel(const double *__restrict__ A, int64_t m, int
 
 // weight column k repeated with period n: slots[k][s] = W[s mod n][k]
 __global__ void cdiag_weights_kernel(const double *__restrict__ W, int64_t n, int64_t K, int64_t slots, double *out) {
+    HE_GRID_DEP();
     const int64_t total = K * slots;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = idx / slots, s = idx % slots;
@@ -170,6 +175,7 @@ __global__ void cdiag_weights_kernel(const double *__restrict__ W, int64_t n, in
 
 // Z[r][k] from the decrypted slots of output k: slot r (m >= n) or the sum of the n/m groups (m < n)
 __global__ void cdiag_decode_kernel(const double *__restrict__ slots, int64_t m, int64_t n, int64_t K, int64_t n_slots, double *Z) {
+    HE_GRID_DEP();
     const int64_t total = m * K;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = idx / K, k = idx % K;
@@ -217,10 +223,10 @@ int he_cdiag_encode_weights(he_ctx *ctx, const double *W, int64_t n, int64_t K, 
     m.n = (int)nl;
     for (int l = 0; l < nl; ++l) m.prime[l] = l;
     ctx->launches += 3;
-    cdiag_weights_kernel<<<blocks_for(K * (N / 2)), 256, 0, ctx->stream>>>(W, n, K, N / 2, slots);
+    launch_k(cdiag_weights_kernel, blocks_for(K * (N / 2)), 256, 0, ctx->stream, W, n, K, N / 2, slots);
     launch_encode(ctx, slots, N / 2, N / 2, (int)K, cm->scale, coef);
     launch_ntt_from_int64(ctx, coef, cols, (int)K, m, 1);
-    transpose_cols_kernel<<<blocks_for(K * nl * N), 256, 0, ctx->stream>>>(cols, cm->pt, (int)K, (int)nl, ctx->log_n);
+    launch_k(transpose_cols_kernel, blocks_for(K * nl * N), 256, 0, ctx->stream, cols, cm->pt, (int)K, (int)nl, ctx->log_n);
     if (cudaGetLastError() != cudaSuccess) {
         he_cdmat_free(cm);
         return HE_ECUDA;
@@ -250,7 +256,7 @@ int he_cdiag_encode_matrix(he_ctx *ctx, const double *A, int64_t m, int64_t n, d
     map.n = level + 1;
     for (int l = 0; l <= level; ++l) map.prime[l] = l;
     ctx->launches++;
-    cdiag_layout_kernel<<<blocks_for(lo * (N / 2)), 256, 0, ctx->stream>>>(A, m, n, N / 2, slots);
+    launch_k(cdiag_layout_kernel, blocks_for(lo * (N / 2)), 256, 0, ctx->stream, A, m, n, N / 2, slots);
     launch_encode(ctx, slots, N / 2, N / 2, (int)lo, scale, coef);
     for (int64_t i = 0; i < lo; ++i) {
         launch_ntt_from_int64(ctx, coef + i * N, outs[i].data, 1, map, 0);
@@ -279,7 +285,7 @@ int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct,
     for (int64_t kb = 0; kb < K; kb += kmax) {
         const dim3 grid((unsigned)(N / CD_WARPS), (unsigned)nl);
         ctx->launches++;
-        cdiag_mac_kernel<<<grid, CD_WARPS * 32, 0, ctx->stream>>>(tab, n_ct, nl, W->pt, (int)K, (int)kb, pre, ctx->d_mc, ctx->log_n);
+        launch_k(cdiag_mac_kernel, grid, CD_WARPS * 32, 0, ctx->stream, tab, n_ct, nl, W->pt, (int)K, (int)kb, pre, ctx->d_mc, ctx->log_n);
     }
     // rescale every output: inverse NTT of the last limb of both components, then per (k, c, j)
     LimbMap lm{};
@@ -305,8 +311,7 @@ int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct,
         OutTable ot;
         for (int k = 0; k < kn; ++k) ot.p[k] = outs[kf + k].data;
         ctx->launches++;
-        cdiag_rescale_kernel<<<kn * 2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(
-            pre, last, level, rc, ot, (int)kf, ctx->d_tw, ctx->d_mc, ctx->log_n);
+        launch_k(cdiag_rescale_kernel, kn * 2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, pre, last, level, rc, ot, (int)kf, ctx->d_tw, ctx->d_mc, ctx->log_n);
     }
     const double scale = cts[0].scale * W->scale / (double)ctx->primes[level];
     for (int64_t k = 0; k < K; ++k) {
@@ -341,7 +346,7 @@ int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_c
 int he_cdiag_decode(he_ctx *ctx, int64_t m, int64_t n, int64_t K, const double *slots, double *Z) {
     if (!ctx || !slots || !Z || !pow2(m) || !pow2(n) || K < 1) return HE_EINVAL;
     ctx->launches++;
-    cdiag_decode_kernel<<<blocks_for(m * K), 256, 0, ctx->stream>>>(slots, m, n, K, ctx->n / 2, Z);
+    launch_k(cdiag_decode_kernel, blocks_for(m * K), 256, 0, ctx->stream, slots, m, n, K, ctx->n / 2, Z);
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
 }
 

@@ -117,6 +117,7 @@ __device__ void fft_smem(float4 *a, const float4 *__restrict__ tw, int logm, int
 __global__ void encode_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
                               const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
                               int64_t *out, int logn) {
+    HE_GRID_DEP();
     extern __shared__ float4 a[];
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn;
     const double *z = slots + (int64_t)blockIdx.x * stride;
@@ -141,6 +142,7 @@ __global__ void encode_kernel(const double *__restrict__ slots, int64_t n_slots,
 // one CTA per polynomial: real coefficients [count][N] -> slot values [count][N/2] / scale
 __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
                               const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
+    HE_GRID_DEP();
     extern __shared__ float4 a[];
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn;
     const double *m = coeffs + (int64_t)blockIdx.x * N;
@@ -226,6 +228,7 @@ template <int CLG>
 __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
                                  const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
                                  int64_t *out, int logn) {
+    HE_GRID_DEP();
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
@@ -256,6 +259,7 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
 template <int CLG>
 __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
                                  const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
+    HE_GRID_DEP();
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
@@ -287,6 +291,7 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
 template <bool CL>
 __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words, int nl, const uint64_t *__restrict__ sk_mont,
                                double *coeffs, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int item, off, len;
@@ -325,6 +330,7 @@ __device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t 
 // integer (word 2(j&1)+1 : word 2(j&1)) of block (j/2, prime index, nonce, 0), key (seed, tag)
 __global__ void sample_uniform_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, LimbMap map, uint64_t *out,
                                       const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int l = blockIdx.y;
     const int p = map.prime[l];
@@ -343,6 +349,7 @@ struct Cdt {
 
 // discrete Gaussian by cumulative table: r = word >> 24, x = -19 + #{k : r >= T_k}
 __global__ void sample_gauss_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, Cdt cdt, int64_t *out, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 4; b += gridDim.x * blockDim.x) {
         uint64_t c[4] = {(uint64_t)b, 0, nonce, 0};
@@ -359,6 +366,7 @@ __global__ void sample_gauss_kernel(uint64_t seed, uint64_t tag, uint64_t nonce,
 
 // ternary secret: (word mod 3) - 1, block (j/4, 0, 0, 0), key (seed, 1)
 __global__ void sample_ternary_kernel(uint64_t seed, int64_t *out, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 4; b += gridDim.x * blockDim.x) {
         uint64_t c[4] = {(uint64_t)b, 0, 0, 0};
@@ -371,6 +379,7 @@ __global__ void sample_ternary_kernel(uint64_t seed, int64_t *out, int logn) {
 // c0 = m - a s + e, c1 = a (NTT domain, limbs 0..level)
 __global__ void encrypt_combine_kernel(const uint64_t *__restrict__ pt, const uint64_t *__restrict__ a, const uint64_t *__restrict__ e,
                                        const uint64_t *__restrict__ sk_mont, int nl, uint64_t *ct, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int l = blockIdx.y;
     const uint64_t q = mc[l].q, qinv = mc[l].qinv;
@@ -390,6 +399,7 @@ struct PmodQ {
 __global__ void keygen_combine_kernel(const uint64_t *__restrict__ a, const uint64_t *__restrict__ e, const uint64_t *__restrict__ sk,
                                       const uint64_t *__restrict__ sk_mont, uint32_t g, int d_lo, int d_hi, PmodQ pm, int LK,
                                       uint64_t *key_d, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int l = blockIdx.y;
     const ModConst m = mc[l];
@@ -441,7 +451,7 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
         case 1: launch_fft_cl<1>(encode_cl_kernel<1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
         default: break;
     }
-    encode_kernel<<<count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream>>>(slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
+    launch_k(encode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
 }
 
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots) {
@@ -456,7 +466,7 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
         case 1: launch_fft_cl<1>(decode_cl_kernel<1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
         default: break;
     }
-    decode_kernel<<<count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream>>>(coeffs, scale, tw, twist, pos, slots, ctx->log_n);
+    launch_k(decode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, coeffs, scale, tw, twist, pos, slots, ctx->log_n);
 }
 
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *) {
@@ -467,32 +477,32 @@ void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count
                        level + 1, (const uint64_t *)ctx->d_sk_mont, coeffs, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
         return;
     }
-    decrypt_kernel<false><<<count, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
+    launch_k(decrypt_kernel<false>, count, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
                                                                     ctx->log_n);
 }
 
 void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int, uint64_t *out) {
     dim3 grid((ctx->n / 2 + 255) / 256, map.n);
     ctx->launches++;
-    sample_uniform_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->seed, tag, nonce, map, out, ctx->d_mc, ctx->log_n);
+    launch_k(sample_uniform_kernel, grid, 256, 0, ctx->stream, ctx->seed, tag, nonce, map, out, ctx->d_mc, ctx->log_n);
 }
 
 void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out) {
     Cdt c;
     for (int k = 0; k < 38; ++k) c.t[k] = ctx->cdt[k];
     ctx->launches++;
-    sample_gauss_kernel<<<(ctx->n / 4 + 255) / 256, 256, 0, ctx->stream>>>(ctx->seed, tag, nonce, c, out, ctx->log_n);
+    launch_k(sample_gauss_kernel, (ctx->n / 4 + 255) / 256, 256, 0, ctx->stream, ctx->seed, tag, nonce, c, out, ctx->log_n);
 }
 
 void launch_sample_ternary(he_ctx *ctx, int64_t *out) {
     ctx->launches++;
-    sample_ternary_kernel<<<(ctx->n / 4 + 255) / 256, 256, 0, ctx->stream>>>(ctx->seed, out, ctx->log_n);
+    launch_k(sample_ternary_kernel, (ctx->n / 4 + 255) / 256, 256, 0, ctx->stream, ctx->seed, out, ctx->log_n);
 }
 
 void launch_encrypt_combine(he_ctx *ctx, const uint64_t *pt, const uint64_t *a, const uint64_t *e, int level, uint64_t *ct) {
     dim3 grid((ctx->n + 255) / 256, level + 1);
     ctx->launches++;
-    encrypt_combine_kernel<<<grid, 256, 0, ctx->stream>>>(pt, a, e, ctx->d_sk_mont, level + 1, ct, ctx->d_mc, ctx->log_n);
+    launch_k(encrypt_combine_kernel, grid, 256, 0, ctx->stream, pt, a, e, ctx->d_sk_mont, level + 1, ct, ctx->d_mc, ctx->log_n);
 }
 
 void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, uint32_t g, int digit, uint64_t *key_d) {
@@ -505,7 +515,7 @@ void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, ui
     const int lo = digit * ctx->alpha, hi = lo + ctx->alpha < ctx->L ? lo + ctx->alpha : ctx->L;
     dim3 grid((ctx->n + 255) / 256, ctx->L + ctx->K);
     ctx->launches++;
-    keygen_combine_kernel<<<grid, 256, 0, ctx->stream>>>(a, e, ctx->d_sk, ctx->d_sk_mont, g, lo, hi, pm, ctx->L + ctx->K, key_d, ctx->d_mc,
+    launch_k(keygen_combine_kernel, grid, 256, 0, ctx->stream, a, e, ctx->d_sk, ctx->d_sk_mont, g, lo, hi, pm, ctx->L + ctx->K, key_d, ctx->d_mc,
                                                          ctx->log_n);
 }
 

@@ -224,7 +224,34 @@ int batch_launch(he_ctx *ctx, he_batch *b);
 int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm);
 }
 
-// Launch `kernel` with thread-block clusters of HE_NTT_CL_SIZE CTAs along x.
+// Programmatic dependent launch.  Every kernel is launched with programmatic stream
+// serialization and begins with HE_GRID_DEP(): it lets the next kernel in the stream be
+// scheduled at once (its blocks start while this grid drains), then waits until the previous
+// grid has completed and its writes are visible.  The body therefore runs strictly after its
+// predecessor, as with ordinary stream order; only the launch latency between dependent kernels
+// overlaps.  (Both instructions are no-ops for a launch without the attribute.)
+#define HE_GRID_DEP()                                                      \
+    do {                                                                   \
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   \
+        asm volatile("griddepcontrol.wait;" ::: "memory");                \
+    } while (0)
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// thread-block cluster launch (cluster of cl_size CTAs along x), also programmatically serialized
 #define HE_NTT_CL_SIZE 8
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_cluster_n(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st, int cl_size, Args... args) {
@@ -233,13 +260,15 @@ inline cudaError_t launch_cluster_n(void (*kernel)(KArgs...), int grid, int bloc
     cfg.blockDim = dim3((unsigned)block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)cl_size;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 template <typename... KArgs, typename... Args>

@@ -33,6 +33,7 @@ struct KeyChunk {
 };
 
 __global__ void fill_key_table_kernel(KeyChunk kc, int64_t n_steps) {
+    HE_GRID_DEP();
     const uint64_t **keys = reinterpret_cast<const uint64_t **>(g_noalloc_scratch);
     uint32_t *gal = reinterpret_cast<uint32_t *>(g_noalloc_scratch + n_steps);
     for (int t = threadIdx.x; t < kc.count; t += blockDim.x) {
@@ -104,7 +105,7 @@ extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan,
             kc.key[t] = ctx->keys.find(g)->second;
         }
         ctx->launches++;
-        fill_key_table_kernel<<<1, 128, 0, ctx->stream>>>(kc, (int64_t)steps);
+        launch_k(fill_key_table_kernel, 1, 128, 0, ctx->stream, kc, (int64_t)steps);
     }
     const uint64_t *const *keys = reinterpret_cast<const uint64_t *const *>(base);
     const uint32_t *galois = reinterpret_cast<const uint32_t *>(base + steps);

@@ -11,6 +11,7 @@ namespace {
 template <bool CL>
 __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
                                const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int to_mont) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int poly, off, len;
@@ -35,6 +36,7 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
 template <bool CL>
 __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
                                const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int poly, off, len;
@@ -56,6 +58,7 @@ __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
 template <bool CL>
 __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *out, LimbMap map, const uint64_t *__restrict__ d_tw,
                                       const ModConst *__restrict__ mc, int logn, int to_mont) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int poly, off, len;
@@ -79,6 +82,7 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
 
 // out = data 2^-64 mod q (Montgomery form back to canonical); grid (blocks, groups, limbs)
 __global__ void from_mont_kernel(const uint64_t *__restrict__ data, uint64_t *out, LimbMap map, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int g = blockIdx.y, l = blockIdx.z;
     const int p = map.prime[l];
@@ -87,6 +91,7 @@ __global__ void from_mont_kernel(const uint64_t *__restrict__ data, uint64_t *ou
 }
 
 __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int g = blockIdx.y, l = blockIdx.z;
     const int p = map.prime[l];
@@ -126,7 +131,7 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
         launch_cluster(ntt_fwd_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out,
                        out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
     else
-        ntt_fwd_kernel<false><<<polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+        launch_k(ntt_fwd_kernel<false>, polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw,
                                                                                                         ctx->d_mc, ctx->log_n, to_mont);
 }
 
@@ -138,14 +143,14 @@ void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
         launch_cluster(ntt_inv_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out,
                        out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n);
     else
-        ntt_inv_kernel<false><<<polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, in_gs, out, out_gs, map, ctx->d_tw,
+        launch_k(ntt_inv_kernel<false>, polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw,
                                                                                                         ctx->d_mc, ctx->log_n);
 }
 
 void launch_from_mont(he_ctx *ctx, const uint64_t *data, uint64_t *out, int groups, const LimbMap &map) {
     if (groups * map.n == 0) return;
     ctx->launches++;
-    from_mont_kernel<<<dim3((unsigned)((ctx->n + 255) / 256), (unsigned)groups, (unsigned)map.n), 256, 0, ctx->stream>>>(data, out, map, ctx->d_mc,
+    launch_k(from_mont_kernel, dim3((unsigned)((ctx->n + 255) / 256), (unsigned)groups, (unsigned)map.n), 256, 0, ctx->stream, data, out, map, ctx->d_mc,
                                                                                                                      ctx->log_n);
 }
 
@@ -167,7 +172,7 @@ void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int gr
         launch_cluster(ntt_from_int64_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, out, map,
                        ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
     else
-        ntt_from_int64_kernel<false><<<polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(in, out, map, ctx->d_tw,
+        launch_k(ntt_from_int64_kernel<false>, polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, in, out, map, ctx->d_tw,
                                                                                                                ctx->d_mc, ctx->log_n, to_mont);
 }
 
@@ -175,7 +180,7 @@ void launch_to_mont(he_ctx *ctx, uint64_t *data, int groups, const LimbMap &map)
     if (groups * map.n == 0) return;
     dim3 grid((ctx->n + 255) / 256, groups, map.n);
     ctx->launches++;
-    to_mont_kernel<<<grid, 256, 0, ctx->stream>>>(data, map, ctx->d_mc, ctx->log_n);
+    launch_k(to_mont_kernel, grid, 256, 0, ctx->stream, data, map, ctx->d_mc, ctx->log_n);
 }
 
 void ntt_set_smem_limits(int max_bytes) {

@@ -13,6 +13,7 @@ namespace {
 
 __global__ void add_kernel(const uint64_t *__restrict__ a, const uint64_t *__restrict__ b, uint64_t *out, LimbMap map,
                            const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int l = blockIdx.y, g = blockIdx.z;
     const uint64_t q = mc[map.prime[l]].q;
@@ -23,6 +24,7 @@ __global__ void add_kernel(const uint64_t *__restrict__ a, const uint64_t *__res
 // ct [2][nl][N] times pt [>= nl][N] (canonical): two Montgomery steps give the canonical product
 __global__ void mul_plain_kernel(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ pt, uint64_t *out, int nl,
                                  const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int l = blockIdx.y, c = blockIdx.z;
     const ModConst m = mc[l];
@@ -34,6 +36,7 @@ __global__ void mul_plain_kernel(const uint64_t *__restrict__ ct, const uint64_t
 }
 
 __global__ void automorph_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uint32_t g, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int64_t base = (int64_t)blockIdx.y * N;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) out[base + k] = in[base + automorph_src(k, g, logn)];
@@ -75,6 +78,7 @@ __device__ __forceinline__ void modup_body(const uint64_t *__restrict__ c1_ntt, 
 template <bool CL>
 __global__ void modup_kernel(const uint64_t *__restrict__ c1_ntt, const uint64_t *__restrict__ c1_coef, uint64_t *D, ModUpConst mu,
                              const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     int item, off, len;
     slice_of<CL>(logn, item, off, len);
@@ -84,6 +88,7 @@ __global__ void modup_kernel(const uint64_t *__restrict__ c1_ntt, const uint64_t
 // u_c[u][k] = sum_d D[d][u][src(k)] * keyM[d][c][kl(u)][k], REDC in groups of at most 8 terms
 __global__ void ks_inner_kernel(const uint64_t *__restrict__ D, int ndig, int ext, LimbMap emap, int nq, int L, int LK, uint32_t g, const uint64_t *__restrict__ key, uint64_t *out,
                                 const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int u = blockIdx.y;
     const int p = emap.prime[u];
@@ -144,6 +149,7 @@ template <bool CL>
 __global__ void moddown_kernel(const uint64_t *__restrict__ x, int ext, const uint64_t *__restrict__ xp_coef, ModDownConst md,
                                const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *out,
                                const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     int item, off, len;
     slice_of<CL>(logn, item, off, len);
@@ -182,6 +188,7 @@ __device__ __forceinline__ void rescale_body(const uint64_t *__restrict__ ct, in
 template <bool CL>
 __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const uint64_t *__restrict__ last_coef, RescaleConst rc,
                                uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     int item, off, len;
     slice_of<CL>(logn, item, off, len);
@@ -199,6 +206,7 @@ struct RotGeom {
 
 __global__ void rot_intt_c1_kernel(const RotJob *__restrict__ jobs, RotGeom rg, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
                                    int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int j = blockIdx.x / rg.nl, l = blockIdx.x % rg.nl;
@@ -213,6 +221,7 @@ __global__ void rot_intt_c1_kernel(const RotJob *__restrict__ jobs, RotGeom rg, 
 
 __global__ void rot_modup_kernel(const RotJob *__restrict__ jobs, RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
                                  const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int per = mu.ndig * mu.ext;
     const int j = blockIdx.x / per, rest = blockIdx.x % per;
@@ -222,6 +231,7 @@ __global__ void rot_modup_kernel(const RotJob *__restrict__ jobs, RotGeom rg, Mo
 
 // u_c[u][k] = sum_d D[d][u][src(k)] key[d][c][kl(u)][k] (REDC per 8 digits); rc0[u][k] = c0[u][src(k)]
 __global__ void rot_ks_kernel(const RotJob *__restrict__ jobs, RotGeom rg, int ndig, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     const int N = 1 << logn;
     const int u = blockIdx.y, j = blockIdx.z;
     const int p = u < rg.nl ? u : rg.L + (u - rg.nl);
@@ -251,6 +261,7 @@ __global__ void rot_ks_kernel(const RotJob *__restrict__ jobs, RotGeom rg, int n
 // iNTT of the P limbs of both components of u: block (j, c, i) -> pcoef_j [c][K][N]
 __global__ void rot_intt_p_kernel(const RotJob *__restrict__ jobs, RotGeom rg, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
                                   int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int per = 2 * rg.K;
@@ -267,6 +278,7 @@ __global__ void rot_intt_p_kernel(const RotJob *__restrict__ jobs, RotGeom rg, c
 
 __global__ void rot_moddown_kernel(const RotJob *__restrict__ jobs, RotGeom rg, ModDownConst md, const uint64_t *__restrict__ d_tw,
                                    const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int per = 2 * md.nq;
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / md.nq, l = blockIdx.x % md.nq;
@@ -279,6 +291,7 @@ __global__ void rot_moddown_kernel(const RotJob *__restrict__ jobs, RotGeom rg, 
 // (0: input ciphertext, 1: accumulator acc, 2: pre-rescale sum) into scratch.
 __global__ void batch_intt_c1_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, const uint64_t *__restrict__ d_tw,
                                      const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int j = blockIdx.x / bg.nq, l = blockIdx.x % bg.nq;
@@ -294,6 +307,7 @@ __global__ void batch_intt_c1_kernel(const MMJob *__restrict__ jobs, BatchGeom b
 
 __global__ void batch_modup_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
                                    const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int per = mu.ndig * mu.ext;
     const int j = blockIdx.x / per, rest = blockIdx.x % per;
@@ -305,6 +319,7 @@ __global__ void batch_modup_kernel(const MMJob *__restrict__ jobs, BatchGeom bg,
 // iNTT of the P limbs of both accumulator components: block (j, c, i) -> tmp_j [c][K][N]
 __global__ void batch_intt_p_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, const uint64_t *__restrict__ d_tw,
                                     const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int per = 2 * bg.K;
@@ -322,6 +337,7 @@ __global__ void batch_intt_p_kernel(const MMJob *__restrict__ jobs, BatchGeom bg
 
 __global__ void batch_moddown_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModDownConst md, const uint64_t *__restrict__ d_tw,
                                      const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int per = 2 * md.nq;
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / md.nq, l = blockIdx.x % md.nq;
@@ -334,6 +350,7 @@ __global__ void batch_moddown_kernel(const MMJob *__restrict__ jobs, BatchGeom b
 // iNTT of the last limb of both sum components -> tmp_j + 2K N
 __global__ void batch_intt_last_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, const uint64_t *__restrict__ d_tw,
                                        const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int j = blockIdx.x / 2, c = blockIdx.x % 2;
@@ -350,6 +367,7 @@ __global__ void batch_intt_last_kernel(const MMJob *__restrict__ jobs, BatchGeom
 
 __global__ void batch_rescale_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, RescaleConst rc, const uint64_t *__restrict__ d_tw,
                                      const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int per = 2 * bg.level;
     const int j = blockIdx.x / per, c = (blockIdx.x % per) / bg.level, l = blockIdx.x % bg.level;
@@ -708,6 +726,7 @@ __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_loop_ker
     const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
     const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime, int ndig_rt, int ext, int nq, int L,
     int LK, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
     __shared__ MMTables tb;
     extern __shared__ uint4 mm_pipe[];
@@ -725,6 +744,7 @@ template <int NDIG, int VEC, int G, int S, bool GA>
 __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_loop_kernel(
     const MMJob *__restrict__ jobs, const int32_t *__restrict__ order, int n_items, unsigned int *counter, BatchGeom bg,
     const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
     __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
     __shared__ MMTables tb;
     __shared__ int item_s;
@@ -810,15 +830,14 @@ void mm_launch_variant(he_ctx *ctx, int v, const uint64_t *ct, const uint64_t *D
     const dim3 grid((unsigned)((ctx->n + mm_variant_tile(v) - 1) / mm_variant_tile(v)), (unsigned)ext);
     ctx->launches++;
     mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S, bool GA>() {
-        matmult_loop_kernel<NDIG, VEC, G, S, GA><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S, GA), ctx->stream>>>(
-            ct, D, pts, keys, galois, m_prime, ndig, ext, nq, ctx->L, ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n);
+        launch_k(matmult_loop_kernel<NDIG, VEC, G, S, GA>, grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S, GA), ctx->stream, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, ctx->L, ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n);
     });
 }
 
 void mm_launch_batch_variant(int v, dim3 grid, cudaStream_t st, const MMJob *jobs, const int32_t *order, int n_items, unsigned int *counter,
                              const BatchGeom &bg, const ModConst *mc, int logn) {
     mm_dispatch(v, bg.ndig, [&]<int NDIG, int VEC, int G, int S, bool GA>() {
-        matmult_batch_loop_kernel<NDIG, VEC, G, S, GA><<<grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S, GA), st>>>(jobs, order, n_items, counter,
+        launch_k(matmult_batch_loop_kernel<NDIG, VEC, G, S, GA>, grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S, GA), st, jobs, order, n_items, counter,
                                                                                                                  bg, mc, logn);
     });
 }
@@ -837,6 +856,7 @@ namespace {
 
 // ---- cleartext layout (Eq. 2 after Eq. 3) and lazy rotate-and-sum (Sec. 4.3) ----
 __global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, double *out, int64_t total) {
+    HE_GRID_DEP();
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = idx % p.slots;
         int64_t rest = idx / p.slots;
@@ -851,6 +871,7 @@ __global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, do
 }
 
 __global__ void layout_vector_kernel(he_plan p, const double *__restrict__ y, double *out) {
+    HE_GRID_DEP();
     const int64_t total = p.col_blocks * p.slots;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = idx / p.slots, s = idx % p.slots;
@@ -861,6 +882,7 @@ __global__ void layout_vector_kernel(he_plan p, const double *__restrict__ y, do
 
 // y[r mb + b m' + t] = sum_{s < nb/m'} (slots - mask)[r][b nb + t + s m'] (mask may be null)
 __global__ void lazy_ras_kernel(he_plan p, const double *__restrict__ slots, const double *__restrict__ mask, double *y) {
+    HE_GRID_DEP();
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < p.m; row += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = row / p.mb, rem = row % p.mb;
         const int64_t b = rem / p.m_prime, t = rem % p.m_prime;
@@ -873,6 +895,7 @@ __global__ void lazy_ras_kernel(he_plan p, const double *__restrict__ slots, con
 
 // after the ciphertext rotate-and-sum: y[r mb + b m' + t] = slots[r][b nb + t]
 __global__ void ras_gather_kernel(he_plan p, const double *__restrict__ slots, double *y) {
+    HE_GRID_DEP();
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < p.m; row += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = row / p.mb, rem = row % p.mb;
         const int64_t b = rem / p.m_prime, t = rem % p.m_prime;
@@ -904,17 +927,17 @@ cudaEvent_t *prof_pair(he_ctx *ctx) {
 
 void launch_add(he_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, int groups, const LimbMap &map) {
     ctx->launches++;
-    add_kernel<<<elem_grid(ctx->n, map.n, groups), 256, 0, ctx->stream>>>(a, b, out, map, ctx->d_mc, ctx->log_n);
+    launch_k(add_kernel, elem_grid(ctx->n, map.n, groups), 256, 0, ctx->stream, a, b, out, map, ctx->d_mc, ctx->log_n);
 }
 
 void launch_mul_plain(he_ctx *ctx, const uint64_t *ct, const uint64_t *pt, uint64_t *out, int level) {
     ctx->launches++;
-    mul_plain_kernel<<<elem_grid(ctx->n, level + 1, 2), 256, 0, ctx->stream>>>(ct, pt, out, level + 1, ctx->d_mc, ctx->log_n);
+    launch_k(mul_plain_kernel, elem_grid(ctx->n, level + 1, 2), 256, 0, ctx->stream, ct, pt, out, level + 1, ctx->d_mc, ctx->log_n);
 }
 
 void launch_automorph(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map, uint32_t g) {
     ctx->launches++;
-    automorph_kernel<<<elem_grid(ctx->n, groups * map.n), 256, 0, ctx->stream>>>(in, out, g, ctx->log_n);
+    launch_k(automorph_kernel, elem_grid(ctx->n, groups * map.n), 256, 0, ctx->stream, in, out, g, ctx->log_n);
 }
 
 void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, uint64_t *tmp_coeff) {
@@ -929,7 +952,7 @@ void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, u
         launch_cluster(modup_kernel<true>, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, c1_ntt,
                        (const uint64_t *)tmp_coeff, D, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
     else
-        modup_kernel<false><<<items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
+        launch_k(modup_kernel<false>, items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
                                                                                                        ctx->d_mc, ctx->log_n);
 }
 
@@ -939,7 +962,7 @@ void launch_ks_inner(he_ctx *ctx, const uint64_t *D, int level, uint32_t g, cons
     emap.n = mu.ext;
     for (int v = 0; v < mu.ext; ++v) emap.prime[v] = mu.ext_prime[v];
     ctx->launches++;
-    ks_inner_kernel<<<elem_grid(ctx->n, mu.ext), 256, 0, ctx->stream>>>(D, mu.ndig, mu.ext, emap, level + 1, ctx->L,
+    launch_k(ks_inner_kernel, elem_grid(ctx->n, mu.ext), 256, 0, ctx->stream, D, mu.ndig, mu.ext, emap, level + 1, ctx->L,
                                                                         ctx->L + ctx->K, g, key, u, ctx->d_mc, ctx->log_n);
 }
 
@@ -958,7 +981,7 @@ void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const 
         launch_cluster(moddown_kernel<true>, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, x, ext,
                        (const uint64_t *)tmp, md, add0, add1, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
     else
-        moddown_kernel<false><<<items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(x, ext, tmp, md, add0, add1, out,
+        launch_k(moddown_kernel<false>, items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, x, ext, tmp, md, add0, add1, out,
                                                                                                          ctx->d_tw, ctx->d_mc, ctx->log_n);
 }
 
@@ -993,7 +1016,7 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
         launch_cluster(rescale_kernel<true>, 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, ct, level,
                        (const uint64_t *)tmp, rc, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
     else
-        rescale_kernel<false><<<2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream>>>(ct, level, tmp, rc, out, ctx->d_tw,
+        launch_k(rescale_kernel<false>, 2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, ct, level, tmp, rc, out, ctx->d_tw,
                                                                                                              ctx->d_mc, ctx->log_n);
 }
 
@@ -1064,25 +1087,25 @@ void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double
     int blocks = (int)((total + 255) / 256);
     if (blocks > 65535 * 8) blocks = 65535 * 8;
     ctx->launches++;
-    layout_matrix_kernel<<<blocks, 256, 0, ctx->stream>>>(p, X, slots, total);
+    launch_k(layout_matrix_kernel, blocks, 256, 0, ctx->stream, p, X, slots, total);
 }
 
 void launch_layout_vector(he_ctx *ctx, const he_plan &p, const double *y, double *slots) {
     int blocks = (int)((p.col_blocks * p.slots + 255) / 256);
     ctx->launches++;
-    layout_vector_kernel<<<blocks, 256, 0, ctx->stream>>>(p, y, slots);
+    launch_k(layout_vector_kernel, blocks, 256, 0, ctx->stream, p, y, slots);
 }
 
 void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, const double *mask, double *y) {
     int blocks = (int)((p.m + 255) / 256);
     ctx->launches++;
-    lazy_ras_kernel<<<blocks, 256, 0, ctx->stream>>>(p, slots, mask, y);
+    launch_k(lazy_ras_kernel, blocks, 256, 0, ctx->stream, p, slots, mask, y);
 }
 
 void launch_ras_gather(he_ctx *ctx, const he_plan &p, const double *slots, double *y) {
     int blocks = (int)((p.m + 255) / 256);
     ctx->launches++;
-    ras_gather_kernel<<<blocks, 256, 0, ctx->stream>>>(p, slots, y);
+    launch_k(ras_gather_kernel, blocks, 256, 0, ctx->stream, p, slots, y);
 }
 
 // Whole batched MatMult on `stream`: ModUp of every input, one persistent loop launch over the
@@ -1097,15 +1120,15 @@ int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
     const RescaleConst rc = make_rescale_const(ctx, level);
     if (cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(MMJob) * count, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HE_ECUDA;
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), stream) != cudaSuccess) return HE_ECUDA;
-    batch_intt_c1_kernel<<<count * bg.nq, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    batch_modup_kernel<<<count * mu.ndig * mu.ext, thr, smem, stream>>>(b->d_jobs, bg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(batch_intt_c1_kernel, count * bg.nq, thr, smem, stream, b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(batch_modup_kernel, count * mu.ndig * mu.ext, thr, smem, stream, b->d_jobs, bg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
     const int v = b->variant < 0 ? 0 : b->variant;
     const dim3 pgrid((unsigned)b->ctas_v[v]);
     mm_launch_batch_variant(v, pgrid, stream, b->d_jobs, b->d_order_v[v], b->n_items_v[v], b->d_counter, bg, ctx->d_mc, ctx->log_n);
-    batch_intt_p_kernel<<<count * 2 * bg.K, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    batch_moddown_kernel<<<count * 2 * md.nq, thr, smem, stream>>>(b->d_jobs, bg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    batch_intt_last_kernel<<<count * 2, thr, smem, stream>>>(b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    batch_rescale_kernel<<<count * 2 * level, thr, smem, stream>>>(b->d_jobs, bg, rc, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(batch_intt_p_kernel, count * 2 * bg.K, thr, smem, stream, b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(batch_moddown_kernel, count * 2 * md.nq, thr, smem, stream, b->d_jobs, bg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(batch_intt_last_kernel, count * 2, thr, smem, stream, b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(batch_rescale_kernel, count * 2 * level, thr, smem, stream, b->d_jobs, bg, rc, ctx->d_tw, ctx->d_mc, ctx->log_n);
     ctx->launches += 7;
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
 }
@@ -1147,12 +1170,12 @@ void launch_rotate_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level,
     const int thr = ntt_threads(ctx->log_n);
     const size_t smem = ntt_smem_bytes(ctx->log_n);
     cudaStream_t st = ctx->stream;
-    rot_intt_c1_kernel<<<count * rg.nl, thr, smem, st>>>(d_jobs, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    rot_modup_kernel<<<count * mu.ndig * mu.ext, thr, smem, st>>>(d_jobs, rg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    rot_ks_kernel<<<dim3((unsigned)((ctx->n + 255) / 256), (unsigned)mu.ext, (unsigned)count), 256, 0, st>>>(d_jobs, rg, mu.ndig, ctx->d_mc,
+    launch_k(rot_intt_c1_kernel, count * rg.nl, thr, smem, st, d_jobs, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(rot_modup_kernel, count * mu.ndig * mu.ext, thr, smem, st, d_jobs, rg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(rot_ks_kernel, dim3((unsigned)((ctx->n + 255) / 256), (unsigned)mu.ext, (unsigned)count), 256, 0, st, d_jobs, rg, mu.ndig, ctx->d_mc,
                                                                                                           ctx->log_n);
-    rot_intt_p_kernel<<<count * 2 * ctx->K, thr, smem, st>>>(d_jobs, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    rot_moddown_kernel<<<count * 2 * md.nq, thr, smem, st>>>(d_jobs, rg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(rot_intt_p_kernel, count * 2 * ctx->K, thr, smem, st, d_jobs, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(rot_moddown_kernel, count * 2 * md.nq, thr, smem, st, d_jobs, rg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
     ctx->launches += 5;
 }
 
