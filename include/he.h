@@ -99,6 +99,11 @@ int he_profile_enable(he_ctx *ctx, int on);
 /* Synchronises the stream; total milliseconds and number of timed launches since enabling. */
 int he_profile_read(he_ctx *ctx, double *ms_total, int64_t *launches);
 
+/* Bytes of a caller-owned ciphertext ([2][level+1][N] uint64 residues) or plaintext
+ * ([level+1][N]) buffer at `level`; 0 for a NULL context or a level outside 0 .. L-1. */
+size_t he_ct_bytes(const he_ctx *ctx, int level);
+size_t he_pt_bytes(const he_ctx *ctx, int level);
+
 /* Galois keys for left rotations by each of steps[0..n_steps) (O3/O4, Sec. 2.2). Keys
  * already present are kept.  Device memory: dnum*2*(n_q+n_p)*N*8 bytes per key. */
 int he_keygen(he_ctx *ctx, const int32_t *steps, int n_steps);

@@ -399,6 +399,16 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     return HE_OK;
 }
 
+size_t he_ct_bytes(const he_ctx *ctx, int level) {
+    if (!ctx || level < 0 || level >= ctx->L) return 0;
+    return 2 * (size_t)(level + 1) * ctx->n * sizeof(uint64_t);
+}
+
+size_t he_pt_bytes(const he_ctx *ctx, int level) {
+    if (!ctx || level < 0 || level >= ctx->L) return 0;
+    return (size_t)(level + 1) * ctx->n * sizeof(uint64_t);
+}
+
 int he_synchronize(he_ctx *ctx) {
     if (!ctx) return HE_EINVAL;
     return he_check(cudaStreamSynchronize(ctx->stream));

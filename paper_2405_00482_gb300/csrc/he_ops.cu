@@ -195,6 +195,135 @@ __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const
     rescale_body<CL>(ct, level, last_coef, rc, out, item / level, item % level, s, d_tw, mc, logn, off, len);
 }
 
+// ---- cluster forms with the inverse NTT inside: one launch per stage instead of two ----
+// Each cluster item transforms the limb-polys it needs back to coefficient form itself (a
+// cluster inverse NTT of the input slice, then the N^-1 scaling of the separate inverse-NTT
+// kernel), so ModUp, ModDown and rescale no longer wait on a preceding inverse-NTT launch and its
+// round trip through global memory.  The per-element operations and their order are those of
+// modup_body / moddown_body / rescale_body fed by that kernel, so results are bit-identical.
+// Shared memory: the slice, its twiddles, and an accumulator slice.
+
+// cluster inverse NTT of the slice [off, off + len) of limb-poly src (NTT form, prime index pr);
+// canonical coefficients are then s[SIDX(k)] * N^-1 (applied by the caller with mul_shoup)
+__device__ __forceinline__ void cl_intt_slice(uint64_t *s, const uint64_t *__restrict__ src, int pr, const uint64_t *__restrict__ d_tw,
+                                              const ModConst *__restrict__ mc, int logn, int len) {
+    const ulonglong2 *itw = twiddles(d_tw, pr, 1, logn);
+    tw_prefetch<true, false>(s, itw, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
+    __syncthreads();
+    ntt_inv_cluster(s, itw, mc[pr].q, logn);
+}
+__device__ __forceinline__ uint64_t *cl_acc_slice(uint64_t *s, int logn) { return s + cl_tw_offset_words(logn) + 2 * (1 << (logn - 3)); }
+
+__global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint64_t *D, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                      const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int d = item / mu.ext, u = item % mu.ext;
+    const int lo = d * mu.alpha;
+    const int hi = lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq;
+    const int p = mu.ext_prime[u];
+    const uint64_t t = mc[p].q;
+    uint64_t *dst = D + ((int64_t)d * mu.ext + u) * N + off;
+    if (u >= lo && u < hi) {  // uniform over the whole cluster
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = c1_ntt[(int64_t)u * N + off + k];
+        return;
+    }
+    uint64_t *acc = cl_acc_slice(s, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) acc[k] = 0;
+    for (int i = lo; i < hi; ++i) {
+        cl_intt_slice(s, c1_ntt + (int64_t)i * N + off, i, d_tw, mc, logn, len);
+        const uint64_t qi = mc[i].q;
+        for (int k = threadIdx.x; k < len; k += blockDim.x) {
+            uint64_t v = mul_shoup(s[SIDX(k)], mc[i].ninv, mc[i].ninv_shoup, qi);
+            v = mul_shoup(v, mu.inv[d][i - lo], mu.inv_shoup[d][i - lo], qi);
+            acc[k] = add_mod(acc[k], mul_shoup(v, mu.hat[d][i - lo][u], mu.hat_shoup[d][i - lo][u], t), t);
+        }
+        __syncthreads();
+    }
+    const ulonglong2 *tw = twiddles(d_tw, p, 0, logn);
+    tw_prefetch<true, true>(s, tw, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = acc[k];
+    __syncthreads();
+    ntt_fwd_cluster(s, tw, t, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
+}
+
+// ModDown of component c, output limb j: conversion of the K special-prime limbs (each brought
+// to coefficient form here), NTT, out = add_c + (x_j - conv) P^-1
+__global__ void moddown_cl_fused_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, const uint64_t *__restrict__ add0,
+                                        const uint64_t *__restrict__ add1, uint64_t *out, const uint64_t *__restrict__ d_tw,
+                                        const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int c = item / md.nq, j = item % md.nq;
+    const int pj = md.q_prime[j];
+    const uint64_t q = mc[pj].q;
+    uint64_t *acc = cl_acc_slice(s, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) acc[k] = 0;
+    for (int i = 0; i < md.K; ++i) {
+        const int pr = md.p_prime[i];
+        cl_intt_slice(s, x + ((int64_t)c * ext + md.nq + i) * N + off, pr, d_tw, mc, logn, len);
+        const uint64_t pi = mc[pr].q;
+        for (int k = threadIdx.x; k < len; k += blockDim.x) {
+            uint64_t v = mul_shoup(s[SIDX(k)], mc[pr].ninv, mc[pr].ninv_shoup, pi);
+            v = mul_shoup(v, md.inv[i], md.inv_shoup[i], pi);
+            acc[k] = add_mod(acc[k], mul_shoup(v, md.hat[i][j], md.hat_shoup[i][j], q), q);
+        }
+        __syncthreads();
+    }
+    const ulonglong2 *tw = twiddles(d_tw, pj, 0, logn);
+    tw_prefetch<true, true>(s, tw, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = acc[k];
+    __syncthreads();
+    ntt_fwd_cluster(s, tw, q, logn);
+    const uint64_t *xj = x + ((int64_t)c * ext + j) * N + off;
+    uint64_t *o = out + ((int64_t)c * md.nq + j) * N + off;
+    const uint64_t *ad = c == 0 ? add0 : add1;
+    const uint64_t *a = ad ? ad + (int64_t)j * N + off : nullptr;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        uint64_t v = mul_shoup(sub_mod(xj[k], s[SIDX(k)], q), md.pinv[j], md.pinv_shoup[j], q);
+        if (a) v = add_mod(v, a[k], q);
+        o[k] = v;
+    }
+}
+
+// rescale of component c, output limb j < level: the last limb in coefficient form (here),
+// centred, reduced mod q_j, NTT, out = (c_j - v) q_l^-1
+__global__ void rescale_cl_fused_kernel(const uint64_t *__restrict__ ct, int level, RescaleConst rc, uint64_t *out,
+                                        const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int c = item / level, j = item % level;
+    const uint64_t q = mc[j].q, ql = mc[level].q;
+    uint64_t *lc = cl_acc_slice(s, logn);
+    cl_intt_slice(s, ct + ((int64_t)c * (level + 1) + level) * N + off, level, d_tw, mc, logn, len);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) lc[k] = mul_shoup(s[SIDX(k)], mc[level].ninv, mc[level].ninv_shoup, ql);
+    __syncthreads();
+    const ulonglong2 *tw = twiddles(d_tw, j, 0, logn);
+    tw_prefetch<true, true>(s, tw, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        uint64_t r = lc[k] + rc.half;
+        if (r >= rc.ql) r -= rc.ql;
+        const int64_t centred = (int64_t)r - (int64_t)rc.half;
+        s[SIDX(k)] = reduce_signed(centred, q, mc[j].mu);
+    }
+    __syncthreads();
+    ntt_fwd_cluster(s, tw, q, logn);
+    const uint64_t *cj = ct + ((int64_t)c * (level + 1) + j) * N + off;
+    uint64_t *o = out + ((int64_t)c * level + j) * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
+}
+
 // ---- many rotations: O3 of different ciphertexts, each by its own step, one launch per stage ----
 // (the same definition as launch_rotate: ModUp of c1, key-switch inner product after the
 // automorphism, ModDown, plus the automorphism of c0; bit-identical to one he_rotate per job)
@@ -940,20 +1069,23 @@ void launch_automorph(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups
     launch_k(automorph_kernel, elem_grid(ctx->n, groups * map.n), 256, 0, ctx->stream, in, out, g, ctx->log_n);
 }
 
+static size_t cl_fused_smem_bytes(int logn) { return cl_smem_bytes(logn) + ((size_t)8 << (logn - 3)); }
+
 void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, uint64_t *tmp_coeff) {
     const ModUpConst &mu = ctx->modup[level];
+    const int items = mu.ndig * mu.ext;
+    ctx->launches++;
+    if (use_cluster(ctx->log_n, items)) {  // the inverse NTT of c1 happens inside
+        launch_cluster(modup_cl_fused_kernel, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream, c1_ntt,
+                       D, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+        return;
+    }
     LimbMap qmap{};
     qmap.n = level + 1;
     for (int l = 0; l <= level; ++l) qmap.prime[l] = l;
     launch_ntt_inv_strided(ctx, c1_ntt, 0, tmp_coeff, 0, 1, qmap);
-    ctx->launches++;
-    const int items = mu.ndig * mu.ext;
-    if (use_cluster(ctx->log_n, items))
-        launch_cluster(modup_kernel<true>, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, c1_ntt,
-                       (const uint64_t *)tmp_coeff, D, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
-    else
-        launch_k(modup_kernel<false>, items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
-                                                                                                       ctx->d_mc, ctx->log_n);
+    launch_k(modup_kernel<false>, items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, c1_ntt, tmp_coeff, D, mu, ctx->d_tw,
+             ctx->d_mc, ctx->log_n);
 }
 
 void launch_ks_inner(he_ctx *ctx, const uint64_t *D, int level, uint32_t g, const uint64_t *key, uint64_t *u) {
@@ -970,19 +1102,20 @@ void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const 
                     uint64_t *tmp) {
     const ModDownConst &md = ctx->moddown[level];
     const int ext = level + 1 + ctx->K;
+    const int items = ncomp * md.nq;
+    ctx->launches++;
+    if (use_cluster(ctx->log_n, items)) {  // the inverse NTT of the P limbs happens inside
+        launch_cluster(moddown_cl_fused_kernel, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream, x,
+                       ext, md, add0, add1, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+        return;
+    }
     LimbMap pmap{};
     pmap.n = ctx->K;
     for (int i = 0; i < ctx->K; ++i) pmap.prime[i] = ctx->L + i;
     // P limbs of every component into coefficient form: tmp [ncomp][K][N]
     launch_ntt_inv_strided(ctx, x + (int64_t)(level + 1) * ctx->n, (int64_t)ext * ctx->n, tmp, (int64_t)ctx->K * ctx->n, ncomp, pmap);
-    ctx->launches++;
-    const int items = ncomp * md.nq;
-    if (use_cluster(ctx->log_n, items))
-        launch_cluster(moddown_kernel<true>, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, x, ext,
-                       (const uint64_t *)tmp, md, add0, add1, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
-    else
-        launch_k(moddown_kernel<false>, items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, x, ext, tmp, md, add0, add1, out,
-                                                                                                         ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(moddown_kernel<false>, items, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, x, ext, tmp, md, add0, add1, out,
+             ctx->d_tw, ctx->d_mc, ctx->log_n);
 }
 
 static RescaleConst make_rescale_const(const he_ctx *ctx, int level) {
@@ -1005,19 +1138,20 @@ static RescaleConst make_rescale_const(const he_ctx *ctx, int level) {
 }
 
 void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, uint64_t *tmp) {
+    const RescaleConst rc = make_rescale_const(ctx, level);
+    ctx->launches++;
+    if (use_cluster(ctx->log_n, 2 * level)) {  // the inverse NTT of the last limb happens inside
+        launch_cluster(rescale_cl_fused_kernel, 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream,
+                       ct, level, rc, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+        return;
+    }
     LimbMap lmap{};
     lmap.n = 1;
     lmap.prime[0] = level;
     const int64_t N = ctx->n;
     launch_ntt_inv_strided(ctx, ct + (int64_t)level * N, (int64_t)(level + 1) * N, tmp, N, 2, lmap);
-    const RescaleConst rc = make_rescale_const(ctx, level);
-    ctx->launches++;
-    if (use_cluster(ctx->log_n, 2 * level))
-        launch_cluster(rescale_kernel<true>, 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, ct, level,
-                       (const uint64_t *)tmp, rc, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
-    else
-        launch_k(rescale_kernel<false>, 2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, ct, level, tmp, rc, out, ctx->d_tw,
-                                                                                                             ctx->d_mc, ctx->log_n);
+    launch_k(rescale_kernel<false>, 2 * level, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, ct, level, tmp, rc, out, ctx->d_tw,
+             ctx->d_mc, ctx->log_n);
 }
 
 void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D, uint64_t *acc,
@@ -1193,9 +1327,9 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(modup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(moddown_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(modup_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(moddown_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(rescale_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(modup_cl_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(moddown_cl_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(rescale_cl_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     for (int v = 0; v < kMMVariants; ++v)
         for (int nd = 0; nd <= 3; ++nd)
             mm_dispatch(v, nd, []<int NDIG, int VEC, int G, int S, bool GA>() {

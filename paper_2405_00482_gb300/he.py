@@ -68,6 +68,8 @@ _SIGS = {
     "he_plan_free": (None, [_vp]),
     "he_encode_matrix": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_ptmat_encode": (ctypes.c_int, [_vp, _vp, _vp]),
+    "he_ct_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int]),
+    "he_pt_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int]),
     "he_ptmat_export": (ctypes.c_int, [_vp, _vp, _vp]),
     "he_ptmat_import": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(_vp)]),
     "he_ptmat_free": (None, [_vp]),
@@ -367,6 +369,12 @@ class Context:
     # ---- buffers ----
     def new_ct(self, level: int) -> Ciphertext:
         return Ciphertext(torch.empty((2, level + 1, self.n), dtype=torch.int64, device=self.device), level, 0.0)
+
+    def ct_bytes(self, level: int) -> int:
+        return int(_lib().he_ct_bytes(self.handle, level))
+
+    def pt_bytes(self, level: int) -> int:
+        return int(_lib().he_pt_bytes(self.handle, level))
 
     def new_pt(self, level: int) -> Plaintext:
         return Plaintext(torch.empty((level + 1, self.n), dtype=torch.int64, device=self.device), level, 0.0)

@@ -87,6 +87,7 @@ def test_loop_variant_table_and_argument_checks(he):
     assert lib.he_batch_set_variant(None, 0) == he.HE_EINVAL
     ms = (ctypes.c_float * he.HE_MM_MAX_VARIANTS)()
     assert lib.he_ptmat_tuning(None, ctypes.byref(a), ms) == he.HE_EINVAL
+    assert lib.he_ct_bytes(None, 0) == 0 and lib.he_pt_bytes(None, 0) == 0
 
 
 @pytest.mark.parametrize("m,n,slots", [(4, 4, 8), (16, 64, 2048), (256, 1024, 4096), (3, 5, 8), (1, 8, 16), (5000, 300, 4096)])

@@ -309,3 +309,11 @@ def test_small_context_does_not_limit_a_large_one(he):
     out = big.matmult(plan, pm, [big.encrypt(big.encode_vector(plan, y, 2.0**40, 2)[0], 1)])
     res = big.matmult_decode(plan, torch.stack([big.decrypt(c) for c in out]))
     assert torch.abs(res - X @ y).max().item() < 1e-4
+
+
+def test_buffer_sizes(he):
+    ctx, o = pair(he, "n8192")
+    for level in range(o.L):
+        assert ctx.ct_bytes(level) == ctx.new_ct(level).data.numel() * 8 == 2 * (level + 1) * o.n * 8
+        assert ctx.pt_bytes(level) == ctx.new_pt(level).data.numel() * 8
+    assert ctx.ct_bytes(o.L) == 0 and ctx.pt_bytes(-1) == 0
