@@ -201,7 +201,7 @@ def test_matmult_bit_exact_alpha2(he, m, n):
     _matmult_case(he, "n1024_alpha2", m, n, seed=7)
 
 
-@pytest.mark.parametrize("name,m,n", [("n4096", 16, 64), ("n8192", 256, 1024)])
+@pytest.mark.parametrize("name,m,n", [("n4096", 16, 64), ("n8192", 256, 1024), ("n16384", 64, 512), ("n16384", 9000, 2)])
 def test_matmult_bit_exact_full_size(he, name, m, n):
     """The gradient X^T [[r]] at the benchmark sizes, bit-exact against the oracle."""
     ctx, o, X, y, plan, gouts, scale = _matmult_case(he, name, m, n, seed=11)
