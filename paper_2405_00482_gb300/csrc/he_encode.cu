@@ -171,6 +171,9 @@ __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, c
 // The butterflies and their order per element are those of fft_smem, so the output is
 // bit-identical to the one-CTA form.  Used when a launch has few transforms, which would leave
 // most SMs idle with one CTA each.
+// local passes of the cluster form: radix 4, one set per thread (MS/4 threads), since a cluster
+// transform is latency-bound and more warps with shorter chains finish it sooner
+#define FFT_CL_RADIX_LOG 2
 template <int CLG>
 __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
     constexpr int CL = 1 << CLG;
@@ -179,10 +182,9 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
     const int lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
     int s0 = 0;
     while (s0 < lg_ms) {
-        const int nb = lg_ms - s0 < 3 ? lg_ms - s0 : 3;
+        const int nb = lg_ms - s0 < FFT_CL_RADIX_LOG ? lg_ms - s0 : FFT_CL_RADIX_LOG;
         const int E = 1 << nb;
         switch (nb) {
-            case 3: fft_pass<3>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
             case 2: fft_pass<2>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
             default: fft_pass<1>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
         }
@@ -434,7 +436,7 @@ static int fft_cluster_log(int logn, int count) {
 template <int CLG, typename... KArgs, typename... Args>
 static void launch_fft_cl(void (*kernel)(KArgs...), he_ctx *ctx, int count, Args... args) {
     const int MS = ctx->n / 2 >> CLG;
-    int threads = MS / 8;
+    int threads = MS >> FFT_CL_RADIX_LOG;
     threads = threads < 32 ? 32 : (threads > 512 ? 512 : threads);
     launch_cluster_n(kernel, count << CLG, threads, (size_t)MS * sizeof(float4), ctx->stream, 1 << CLG, args...);
 }
