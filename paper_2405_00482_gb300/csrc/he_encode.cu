@@ -171,9 +171,10 @@ __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, c
 // The butterflies and their order per element are those of fft_smem, so the output is
 // bit-identical to the one-CTA form.  Used when a launch has few transforms, which would leave
 // most SMs idle with one CTA each.
-// local passes of the cluster form: radix 4, one set per thread (MS/4 threads), since a cluster
-// transform is latency-bound and more warps with shorter chains finish it sooner
-#define FFT_CL_RADIX_LOG 2
+// local passes of the cluster form: radix 2, one butterfly per thread per stage (MS/2 threads, at
+// most 512), since a cluster transform is latency-bound and on GB300 the most warps with the
+// shortest chains finished it soonest (radix 8 > radix 4 > radix 2 in time)
+#define FFT_CL_RADIX_LOG 1
 template <int CLG>
 __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
     constexpr int CL = 1 << CLG;

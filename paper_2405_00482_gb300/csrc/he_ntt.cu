@@ -3,6 +3,8 @@
 // One CTA transforms one limb-poly of N residues staged in shared memory (8N bytes).
 // Batch layout: limb l of group g sits at base + g * group_stride + l * N, with prime
 // index map.prime[l].  Grid = groups * map.n CTAs.
+#include <algorithm>
+
 #include "he_internal.cuh"
 #include "he_ntt.cuh"
 
@@ -111,7 +113,7 @@ __global__ void to_mont_kernel(uint64_t *data, LimbMap map, const ModConst *__re
 #define HE_CL_MAX_POLYS 48
 
 bool use_cluster(int logn, int polys) { return logn >= HE_NTT_CL_MIN_LOGN && polys <= HE_CL_MAX_POLYS; }
-int cl_threads(int logn) { return 1 << (logn - 3 - HE_NTT_CL_RADIX_LOG); }
+int cl_threads(int logn) { return std::min(512, 1 << (logn - 3 - HE_NTT_CL_RADIX_LOG)); }
 // the slice's padded data, then its N/8 - 1 twiddle pairs (16-byte aligned: N/8 + N/256 is even)
 size_t cl_smem_bytes(int logn) { return ntt_smem_bytes(logn - 3) + ((size_t)16 << (logn - 3)); }
 

@@ -161,12 +161,13 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t *s, const ulonglong2 *__re
 // index x - rank N/CL).  The stages whose butterflies span slices (the first 3 forward, the
 // last 3 inverse) are one radix-8 step through distributed shared memory: element j + c N/CL
 // lives in CTA c at local index j, and each CTA takes 1/CL of the offsets j.  The other stages
-// run on each slice with radix-4 register passes.  Used for launches of few limb-polys,
+// run on each slice one stage at a time (radix-2 passes).  Used for launches of few limb-polys,
 // where one CTA per limb-poly would leave most SMs idle.
 #define HE_NTT_CL HE_NTT_CL_SIZE
-// local passes of the cluster form are radix 4 with one set per thread (N/32 threads per CTA):
-// a cluster transform is latency-bound, so twice the warps of radix 8 with half the chain each
-#define HE_NTT_CL_RADIX_LOG 2
+// local passes of the cluster form are radix 2, one butterfly per thread per stage (N/16 threads
+// per CTA, at most 512): a cluster transform is latency-bound, and on GB300 the most warps with
+// the shortest chains finished it soonest (radix 8 > radix 4 > radix 2 in time)
+#define HE_NTT_CL_RADIX_LOG 1
 
 // The local stages of a cluster member touch NS - 1 twiddles of its slice (NS = N/8): forward
 // stage t (3 <= t < log N, m = 2^t) the m/8 entries m + rank m/8 + j; inverse stage t
@@ -319,7 +320,7 @@ __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *_
 
 // the cluster form is used for rings of at least 2^10 (slices of at least 128 elements)
 #define HE_NTT_CL_MIN_LOGN 10
-__device__ __forceinline__ int cl_slice_threads(int logn) { return 1 << (logn - 3 - HE_NTT_CL_RADIX_LOG); }
+__device__ __forceinline__ int cl_slice_threads(int logn) { return min(512, 1 << (logn - 3 - HE_NTT_CL_RADIX_LOG)); }
 
 // Kernels over a batch of limb-polys: in the plain form one CTA transforms a whole limb-poly
 // (grid = polys); in the cluster form (CL) a cluster of HE_NTT_CL CTAs shares one limb-poly,
