@@ -16,8 +16,8 @@
 #include "he_internal.cuh"
 #include "he_ntt.cuh"
 
-#define CD_COLS 4      // columns per lane (a warp covers 128 columns of one coefficient)
-#define CD_WARPS 8     // coefficients per block (one warp each)
+#define CD_COLS 8      // columns per lane (16 lanes cover 128 columns of one coefficient)
+#define CD_WARPS 8     // warps per block (two coefficients each)
 #define CD_MAX_IN 1024 // ciphertexts per launch (kernel-parameter table)
 #define CD_MAX_OUT 512 // outputs per rescale launch
 
@@ -38,20 +38,21 @@ struct OutTable {
     uint64_t *p[CD_MAX_OUT];
 };
 
-// pre[k][c][u][t] = sum_i ct_i[c][u][t] * pt_k[u][src_i(t)].  Warp w of a block takes coefficient
-// t = blockIdx.x * CD_WARPS + w; lane l takes the CD_COLS columns k_base + CD_COLS l + (0..3), so
-// the warp's gather of weight row (u, src_i(t)) is one contiguous run of K words.  Ciphertext
-// words are used once and loaded with an evict-first hint, so the weight table (read once per
-// diagonal) stays in L2.  The next diagonal's operands are loaded while the current one is
-// multiplied.  Products of residues below q < 2^61 are summed 8 at a time in 128 bits.
+// pre[k][c][u][t] = sum_i ct_i[c][u][t] * pt_k[u][src_i(t)].  Each half-warp takes one
+// coefficient t (two per warp, 2 CD_WARPS per block) and its 16 lanes the CD_COLS columns
+// k_base + CD_COLS l + (0..7) each, so a half-warp's gather of weight row (u, src_i(t)) is one
+// contiguous run of 128 words, and each diagonal's fixed work (automorphism index, ciphertext
+// loads, gather address) is shared by 16 multiply-adds per lane.  Ciphertext words are used once
+// and loaded with an evict-first hint, so the weight table (read once per diagonal) stays in L2.
+// Products of residues below q < 2^61 are summed 8 at a time in 128 bits.
 __global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts, int n_ct, int nl, const uint64_t *__restrict__ pt, int K,
                                                                     int k_base, uint64_t *pre, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
     const int N = 1 << logn;
     const int u = blockIdx.y;
     const uint64_t q = mc[u].q, qinv = mc[u].qinv;
-    const int t = blockIdx.x * CD_WARPS + (threadIdx.x >> 5);
-    const int k0 = k_base + (threadIdx.x & 31) * CD_COLS;
+    const int t = blockIdx.x * (2 * CD_WARPS) + (threadIdx.x >> 4);
+    const int k0 = k_base + (threadIdx.x & 15) * CD_COLS;
     if (k0 >= K) return;  // no block-wide synchronisation below
     const int kn = K - k0 < CD_COLS ? K - k0 : CD_COLS;
     const bool vec = kn == CD_COLS && (K & 1) == 0;  // rows start 16-byte aligned when K is even
@@ -80,19 +81,14 @@ __global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts
         }
     };
     uint32_t g = 1;
-    fetch(0, g);
     int pending = 0;
     for (int i = 0; i < n_ct; ++i) {
-        const uint64_t c0 = c0n, c1 = c1n;
-        uint64_t pv[CD_COLS];
-#pragma unroll
-        for (int kk = 0; kk < CD_COLS; ++kk) pv[kk] = pvn[kk];
+        fetch(i, g);
         g = (uint32_t)(((uint64_t)g * 5u) & two_n_mask);
-        if (i + 1 < n_ct) fetch(i + 1, g);
 #pragma unroll
         for (int kk = 0; kk < CD_COLS; ++kk) {
-            a0[kk] += (u128)c0 * pv[kk];
-            a1[kk] += (u128)c1 * pv[kk];
+            a0[kk] += (u128)c0n * pvn[kk];
+            a1[kk] += (u128)c1n * pvn[kk];
         }
         if (++pending == 8) {
 #pragma unroll
@@ -281,9 +277,9 @@ int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct,
     uint64_t *last = pre + K * 2 * nl * N;
     CtTable tab;
     for (int i = 0; i < n_ct; ++i) tab.p[i] = cts[i].data;
-    const int kmax = 32 * CD_COLS;  // columns per launch (one warp's lanes)
+    const int kmax = 16 * CD_COLS;  // columns per launch (16 lanes)
     for (int64_t kb = 0; kb < K; kb += kmax) {
-        const dim3 grid((unsigned)(N / CD_WARPS), (unsigned)nl);
+        const dim3 grid((unsigned)(N / (2 * CD_WARPS)), (unsigned)nl);
         ctx->launches++;
         launch_k(cdiag_mac_kernel, grid, CD_WARPS * 32, 0, ctx->stream, tab, n_ct, nl, W->pt, (int)K, (int)kb, pre, ctx->d_mc, ctx->log_n);
     }
