@@ -86,6 +86,12 @@ int he_cdt_table(uint64_t *out38);
  * (Philox-4x64-10 stream), all on `cuda_stream` (a cudaStream_t; NULL = legacy stream). */
 int he_ctx_create(const he_params *p, uint64_t seed, void *cuda_stream, he_ctx **out);
 void he_ctx_destroy(he_ctx *ctx);
+/* A context on another stream that shares parent's tables, secret and Galois keys (keys made on
+ * any context of the family are seen by all), with its own scratch, so calls on the two streams
+ * can run concurrently.  The family's tables and keys are freed with its last context; forks and
+ * parent may be destroyed in any order.  he_keygen on one context may run while the others work
+ * (the key table is guarded).  Waits for the parent's stream once. */
+int he_ctx_fork(he_ctx *parent, void *cuda_stream, he_ctx **out);
 /* Wait for every call issued on the context's stream. */
 int he_synchronize(he_ctx *ctx);
 /* N of the ring and the prime count; any out pointer may be NULL. */

@@ -228,13 +228,7 @@ int he_cdt_table(uint64_t *out) {
 void he_ctx_destroy(he_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
-    for (auto &kv : ctx->keys) cudaFree(kv.second);
-    cudaFree(ctx->d_mc);
-    cudaFree(ctx->d_tw);
-    cudaFree(ctx->d_fft);
-    cudaFree(ctx->d_sk);
-    cudaFree(ctx->d_sk_mont);
-    cudaFree(ctx->scratch);
+    cudaFree(ctx->scratch);  // the tables and keys go with the family's last context (he_shared)
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
     delete ctx;
 }
@@ -246,6 +240,7 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     if (rc != HE_OK) return rc;
     he_ctx *ctx = new (std::nothrow) he_ctx();
     if (!ctx) return HE_ENOMEM;
+    ctx->sh = std::make_shared<he_shared>();
     ctx->log_n = p->log_n;
     ctx->n = 1 << p->log_n;
     ctx->L = p->n_q;
@@ -371,6 +366,11 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     bool ok = cuda_ok(cudaMalloc(&ctx->d_mc, sizeof(ModConst) * LK)) && cuda_ok(cudaMalloc(&ctx->d_tw, tw.size() * 8)) &&
               cuda_ok(cudaMalloc(&ctx->d_fft, fft.size() * 4)) && cuda_ok(cudaMalloc(&ctx->d_sk, (size_t)LK * N * 8)) &&
               cuda_ok(cudaMalloc(&ctx->d_sk_mont, (size_t)LK * N * 8));
+    ctx->sh->owned[0] = ctx->d_mc;
+    ctx->sh->owned[1] = ctx->d_tw;
+    ctx->sh->owned[2] = ctx->d_fft;
+    ctx->sh->owned[3] = ctx->d_sk;
+    ctx->sh->owned[4] = ctx->d_sk_mont;
     if (!ok) {
         he_ctx_destroy(ctx);
         return HE_ENOMEM;
@@ -407,6 +407,41 @@ size_t he_ct_bytes(const he_ctx *ctx, int level) {
 size_t he_pt_bytes(const he_ctx *ctx, int level) {
     if (!ctx || level < 0 || level >= ctx->L) return 0;
     return (size_t)(level + 1) * ctx->n * sizeof(uint64_t);
+}
+
+int he_ctx_fork(he_ctx *parent, void *stream, he_ctx **out) {
+    if (!parent || !out) return HE_EINVAL;
+    *out = nullptr;
+    he_ctx *ctx = new (std::nothrow) he_ctx();
+    if (!ctx) return HE_ENOMEM;
+    // everything read-only is copied or shared; the stream, scratch, counters and profiling are own
+    ctx->log_n = parent->log_n;
+    ctx->n = parent->n;
+    ctx->L = parent->L;
+    ctx->K = parent->K;
+    ctx->dnum = parent->dnum;
+    ctx->alpha = parent->alpha;
+    ctx->seed = parent->seed;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->primes = parent->primes;
+    ctx->mc = parent->mc;
+    ctx->d_mc = parent->d_mc;
+    ctx->d_tw = parent->d_tw;
+    ctx->d_fft = parent->d_fft;
+    ctx->d_sk_mont = parent->d_sk_mont;
+    ctx->d_sk = parent->d_sk;
+    ctx->sh = parent->sh;
+    ctx->modup = parent->modup;
+    ctx->moddown = parent->moddown;
+    memcpy(ctx->cdt, parent->cdt, sizeof(ctx->cdt));
+    ctx->batch_variant = parent->batch_variant;
+    // the parent's pending work (keys, tables) must be complete before the fork's stream uses it
+    if (cudaStreamSynchronize(parent->stream) != cudaSuccess) {
+        delete ctx;
+        return HE_ECUDA;
+    }
+    *out = ctx;
+    return HE_OK;
 }
 
 int he_synchronize(he_ctx *ctx) {
@@ -458,7 +493,7 @@ int he_keygen(he_ctx *ctx, const int32_t *steps, int n_steps) {
     for (int i = 0; i < LK; ++i) all.prime[i] = i;
     for (int s = 0; s < n_steps; ++s) {
         const uint32_t g = galois_of(ctx, steps[s]);
-        if (ctx->keys.count(g)) continue;
+        if (ctx->sh->key(g)) continue;
         uint64_t *key = nullptr;
         if (cudaMalloc(&key, (size_t)ctx->dnum * 2 * LK * N * 8) != cudaSuccess) return HE_ENOMEM;
         uint64_t *tmp = ctx_scratch(ctx, (size_t)2 * LK * N + N);
@@ -480,7 +515,11 @@ int he_keygen(he_ctx *ctx, const int32_t *steps, int n_steps) {
             cudaFree(key);
             return HE_ECUDA;
         }
-        ctx->keys[g] = key;
+        {
+            std::lock_guard<std::mutex> lock(ctx->sh->mu);
+            auto ins = ctx->sh->keys.emplace(g, key);
+            if (!ins.second) cudaFree(key);  // another context of the family made it meanwhile
+        }
     }
     return HE_OK;
 }
@@ -581,9 +620,8 @@ int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, int k,
     std::vector<const uint64_t *> keys(k);
     for (int i = 0; i < k; ++i) {
         if (!outs[i].data || outs[i].data == in->data) return HE_EINVAL;
-        auto it = ctx->keys.find(galois_of(ctx, steps[i]));
-        if (it == ctx->keys.end()) return HE_EKEY;
-        keys[i] = it->second;
+        keys[i] = ctx->sh->key(galois_of(ctx, steps[i]));
+        if (!keys[i]) return HE_EKEY;
     }
     if (k == 0) return HE_OK;
     const ModUpConst &mu = ctx->modup[level];
@@ -628,9 +666,9 @@ int he_rotate_many(he_ctx *ctx, const he_ct *ins, const int32_t *steps, int coun
             continue;
         }
         const uint32_t g = galois_of(ctx, steps[i]);
-        auto it = ctx->keys.find(g);
-        if (it == ctx->keys.end()) return HE_EKEY;
-        jobs.push_back(RotJob{ins[i].data, outs[i].data, it->second, g, 0});
+        const uint64_t *key = ctx->sh->key(g);
+        if (!key) return HE_EKEY;
+        jobs.push_back(RotJob{ins[i].data, outs[i].data, key, g, 0});
     }
     const int n_jobs = (int)jobs.size();
     if (n_jobs > 0) {
@@ -798,9 +836,8 @@ int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm) {
     std::vector<uint32_t> gal(steps);
     for (int64_t i = 0; i < steps; ++i) {
         gal[i] = galois_of(ctx, i + 1);
-        auto it = ctx->keys.find(gal[i]);
-        if (it == ctx->keys.end()) return HE_EKEY;
-        ptrs[i] = it->second;
+        ptrs[i] = ctx->sh->key(gal[i]);
+        if (!ptrs[i]) return HE_EKEY;
     }
     if (cudaMalloc(&pm->d_keys, steps * sizeof(uint64_t *)) != cudaSuccess) return HE_ENOMEM;
     if (cudaMalloc(&pm->d_galois, steps * sizeof(uint32_t)) != cudaSuccess) return HE_ENOMEM;
@@ -1121,9 +1158,8 @@ int he_ras(he_ctx *ctx, const he_plan *plan, const he_ct *in, he_ct *out) {
     he_plan_ras_steps(plan, steps, &ns);
     std::vector<const uint64_t *> keys(ns);
     for (int j = 0; j < ns; ++j) {
-        auto it = ctx->keys.find(galois_of(ctx, steps[j]));
-        if (it == ctx->keys.end()) return HE_EKEY;
-        keys[j] = it->second;
+        keys[j] = ctx->sh->key(galois_of(ctx, steps[j]));
+        if (!keys[j]) return HE_EKEY;
     }
     const ModUpConst &mu = ctx->modup[level];
     const size_t N = ctx->n, nl = level + 1, ext = mu.ext;

@@ -13,6 +13,8 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "../../include/he.h"
@@ -117,6 +119,23 @@ struct ModDownConst {
     uint64_t pinv[HE_MAX_Q], pinv_shoup[HE_MAX_Q];                    // P^-1 mod q_j
 };
 
+// What the contexts of one family (a context and its forks) share: the device tables, the
+// secret, and the Galois keys.  Freed with the last context of the family.
+struct he_shared {
+    std::mutex mu;                            // guards keys (keygen on one context, lookups on others)
+    std::map<uint32_t, uint64_t *> keys;      // Galois element -> [dnum][2][L+K][N]
+    void *owned[5] = {};                      // device tables: d_mc, d_tw, d_fft, d_sk, d_sk_mont
+    ~he_shared() {
+        for (auto &kv : keys) cudaFree(kv.second);
+        for (void *p : owned) cudaFree(p);
+    }
+    uint64_t *key(uint32_t g) {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = keys.find(g);
+        return it == keys.end() ? nullptr : it->second;
+    }
+};
+
 struct he_ctx {
     int log_n, n, L, K, dnum, alpha;
     uint64_t seed;
@@ -128,7 +147,7 @@ struct he_ctx {
     void *d_fft;                      // encode/decode tables (double-float twiddles, twist, slot positions)
     uint64_t *d_sk_mont;              // [L+K][N] secret in NTT + Montgomery form
     uint64_t *d_sk;                   // [L+K][N] secret in NTT form
-    std::map<uint32_t, uint64_t *> keys;  // Galois element -> [dnum][2][L+K][N]
+    std::shared_ptr<he_shared> sh;   // tables and keys, shared with forks
     std::vector<ModUpConst> modup;    // per level
     std::vector<ModDownConst> moddown;  // per level
     uint64_t cdt[38];

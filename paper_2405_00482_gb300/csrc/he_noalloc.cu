@@ -90,7 +90,7 @@ extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan,
     const size_t need = w_tab_al + wD + wc + wa + wcc + wsum + wt;
     if (need > HE_NOALLOC_WORDS) return HE_EBUDGET;  // larger than the fixed 16 MiB array
     for (size_t i = 0; i < steps; ++i)
-        if (!ctx->keys.count(galois_elem(ctx, (int64_t)i + 1))) return HE_EKEY;
+        if (!ctx->sh->key(galois_elem(ctx, (int64_t)i + 1))) return HE_EKEY;
     uint64_t *base = nullptr;
     int rc = scratch_address(&base);
     if (rc != HE_OK) return rc;
@@ -102,7 +102,7 @@ extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan,
         for (int t = 0; t < kc.count; ++t) {
             const uint32_t g = galois_elem(ctx, (int64_t)(first + t) + 1);
             kc.galois[t] = g;
-            kc.key[t] = ctx->keys.find(g)->second;
+            kc.key[t] = ctx->sh->key(g);
         }
         ctx->launches++;
         launch_k(fill_key_table_kernel, 1, 128, 0, ctx->stream, kc, (int64_t)steps);

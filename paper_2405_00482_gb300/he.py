@@ -43,6 +43,7 @@ _SIGS = {
     "he_cdt_table": (ctypes.c_int, [ctypes.POINTER(_u64)]),
     "he_ctx_create": (ctypes.c_int, [ctypes.POINTER(HeParams), _u64, _vp, ctypes.POINTER(_vp)]),
     "he_ctx_destroy": (None, [_vp]),
+    "he_ctx_fork": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
     "he_synchronize": (ctypes.c_int, [_vp]),
     "he_ctx_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "he_keygen": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.c_int]),
@@ -365,6 +366,20 @@ class Context:
         if getattr(self, "handle", None):
             _lib().he_ctx_destroy(self.handle)
             self.handle = None
+
+    def fork(self, stream: torch.cuda.Stream | None = None) -> "Context":
+        """A context on `stream` (a new one by default) sharing this one's tables, secret and
+        Galois keys, with its own scratch: calls on the two run concurrently.  Tensors the
+        fork's calls allocate come from torch's current stream, so call it inside
+        `torch.cuda.stream(fork.stream)`."""
+        f = object.__new__(Context)
+        f.stream = stream or torch.cuda.Stream(device=self.device)
+        h = _vp()
+        _check(_lib().he_ctx_fork(self.handle, _vp(f.stream.cuda_stream), ctypes.byref(h)), "he_ctx_fork")
+        f.handle = h
+        for k in ("params", "n", "slots", "L", "K", "primes", "device"):
+            setattr(f, k, getattr(self, k))
+        return f
 
     # ---- buffers ----
     def new_ct(self, level: int) -> Ciphertext:
