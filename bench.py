@@ -111,6 +111,8 @@ def run_gpu(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
+    # a graph is captured on the context's stream, which therefore is not the legacy default one
+    torch.cuda.set_stream(torch.cuda.Stream(device=dev))
     P = inputs.PARAMS_N8192
     ctx = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=rank)
     X, r, w = inputs.gradient_and_forward_n8192(seed=rank)
@@ -159,52 +161,84 @@ def run_gpu(args):
         c.decrypt(out[0], slots[0])
         c.matmult_decode(plan, slots, res)
 
-    def step(i, XTd, Xd, rd, wd):
+    # encryption nonces live in device memory and advance by 2 on every step, so a replayed
+    # graph never encrypts twice under one nonce
+    nonce = torch.tensor([0, 1], dtype=torch.int64, device=dev)
+
+    def step(XTd, Xd, rd, wd):
         if two:
             fctx.stream.wait_stream(main)  # inputs copied / produced on the main stream
-        product(ctx, plan_g, pm_g, XTd, rd, pt_r, ct_r, 2 * i, out_g, slots_g, res_g)
+        product(ctx, plan_g, pm_g, XTd, rd, pt_r, ct_r, nonce[0:1], out_g, slots_g, res_g)
         with torch.cuda.stream(fctx.stream):
-            product(fctx, plan_f, pm_f, Xd, wd, pt_w, ct_w, 2 * i + 1, out_f, slots_f, res_f)
+            product(fctx, plan_f, pm_f, Xd, wd, pt_w, ct_w, nonce[1:2], out_f, slots_f, res_f)
         if two:
             main.wait_stream(fctx.stream)
+        nonce.add_(2)
+
+    def check(what):
+        torch.cuda.synchronize()
+        e = max(float(np.abs(res_g.cpu().numpy() - XT @ r).max()), float(np.abs(res_f.cpu().numpy() - X @ w).max()))
+        if e > 1e-4:
+            raise RuntimeError(f"decrypted MatMult error {e} above tolerance ({what})")
+        return e
 
     # correctness of the timed configuration against the FP64 product
-    step(0, dXT, dX, dr, dw)
-    torch.cuda.synchronize()
-    err = max(float(np.abs(res_g.cpu().numpy() - XT @ r).max()), float(np.abs(res_f.cpu().numpy() - X @ w).max()))
-    if err > 1e-4:
-        raise RuntimeError(f"decrypted MatMult error {err} above tolerance")
-
+    step(dXT, dX, dr, dw)
+    err = check("eager step")
     for i in range(args.warmup):
-        step(i + 1, dXT, dX, dr, dw)
+        step(dXT, dX, dr, dw)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    stream = torch.cuda.current_stream()
-    per_step = []
-    launches0 = ctx.launch_count() + (fctx.launch_count() if two else 0)
-    ctx.profile(True)
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
+    stream = main
+
+    def timed_steps(run):
+        per = []
         for i in range(args.steps):
             flush_l2(flush)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step(1000 + i, dXT, dX, dr, dw)
+            run()
             b.record(stream)
-            per_step.append((a, b))
+            per.append((a, b))
         torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in per]
+
+    # eager: one API call per operation
+    launches0 = ctx.launch_count() + (fctx.launch_count() if two else 0)
+    ctx.profile(True)
+    with ClockSampler(local) as clk_eager:
+        torch.cuda.synchronize()
+        times_eager = timed_steps(lambda: step(dXT, dX, dr, dw))
     loop_ms, loop_launches = ctx.profile_read()
     ctx.profile(False)
-    launches = ctx.launch_count() + (fctx.launch_count() if two else 0) - launches0
-    times = [a.elapsed_time(b) for a, b in per_step]
+    launches_eager = ctx.launch_count() + (fctx.launch_count() if two else 0) - launches0
+    step_loop_ms = loop_ms / max(loop_launches, 1)
+
+    # graph: the same calls captured once (he.Graph) and replayed with one launch per step
+    graph = he.Graph(ctx, lambda: step(dXT, dX, dr, dw), forks=[fctx] if two else [])
+    for i in range(args.warmup):
+        graph.replay()
+    res_g.zero_()
+    res_f.zero_()
+    graph.replay()
+    err = max(err, check("graph replay"))
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local) as clk_graph:
+        torch.cuda.synchronize()
+        times_graph = timed_steps(graph.replay)
+    use_graph = not args.no_graph
+    times = times_graph if use_graph else times_eager
+    clk = clk_graph if use_graph else clk_eager
+    launches = graph.launches * args.steps if use_graph else launches_eager
     total_s = max_over_ranks(sum(times) / 1e3, world, dev)
+    eager_s = max_over_ranks(sum(times_eager) / 1e3, world, dev)
     if world > 1:
         torch.distributed.barrier()
 
     # MatMult call alone (inputs encoded and encrypted), same device timing; the loop kernel's
     # roofline comes from these launches, where no kernel of the other stream shares the GPU
-    step_loop_ms = loop_ms / max(loop_launches, 1)
     ctx.profile(True)
     mm = []
     for i in range(args.steps):
@@ -219,22 +253,34 @@ def run_gpu(args):
     ctx.profile(False)
     mm_ms = sorted(a.elapsed_time(b) for a, b in mm)
 
-    # end to end through the API from pinned host buffers, result read back every step
+    # end to end through the API from pinned host buffers, result read back every step: the
+    # inputs are copied into the buffers the graph reads, the graph replayed, the results read
     hXT, hX = torch.from_numpy(XT).pin_memory(), torch.from_numpy(X).pin_memory()
     hr, hw = torch.from_numpy(r).pin_memory(), torch.from_numpy(w).pin_memory()
     hres_g = torch.empty(256, dtype=torch.float64).pin_memory()
     hres_f = torch.empty(1024, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        if use_graph:
+            for d, h in ((dXT, hXT), (dX, hX), (dr, hr), (dw, hw)):
+                d.copy_(h, non_blocking=True)
+            graph.replay()
+        else:
+            step(hXT.to(dev, non_blocking=True), hX.to(dev, non_blocking=True), hr.to(dev, non_blocking=True),
+                 hw.to(dev, non_blocking=True))
+        hres_g.copy_(res_g, non_blocking=True)
+        hres_f.copy_(res_f, non_blocking=True)
+
     e2e = []
     for i in range(args.steps):
         flush_l2(flush)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step(5000 + i, hXT.to(dev, non_blocking=True), hX.to(dev, non_blocking=True), hr.to(dev, non_blocking=True),
-             hw.to(dev, non_blocking=True))
-        hres_g.copy_(res_g, non_blocking=True)
-        hres_f.copy_(res_f, non_blocking=True)
+        e2e_step()
         torch.cuda.synchronize()
         e2e.append(time.perf_counter() - t0)
+    if np.abs(hres_g.numpy() - XT @ r).max() > 1e-4 or np.abs(hres_f.numpy() - X @ w).max() > 1e-4:
+        raise RuntimeError("end-to-end result above tolerance")
     e2e_s = max_over_ranks(sum(e2e), world, dev)
     h2d = (XT.nbytes + X.nbytes + r.nbytes + w.nbytes)
     d2h = 256 * 8 + 1024 * 8
@@ -266,19 +312,22 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "matmults_per_step": 2, "hoisted_rotations_per_step": rot_per_step,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}",
-                   "streams": args.streams},
+                   "streams": args.streams, "graph": use_graph},
         "rotations_per_sec": round(rot_per_step * args.steps * world / total_s, 1),
         "matmult_call_ms": {"p50": round(mm_ms[len(mm_ms) // 2], 4), "p99": round(mm_ms[min(len(mm_ms) - 1, int(0.99 * len(mm_ms)))], 4)},
         "step_ms": {"p50": round(sorted(times)[len(times) // 2], 4), "p99": round(sorted(times)[min(len(times) - 1, int(0.99 * len(times)))], 4)},
         "max_abs_err": err,
         "roofline": {"kernel": "matmult_loop_kernel", "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                     "launch_ms": round(per_launch_ms, 5), "launch_ms_in_step": round(step_loop_ms, 5),
+                     "launch_ms": round(per_launch_ms, 5),
                      "timed": "MatMult calls alone (inside the two-stream step the launch shares the GPU)",
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
         "e2e": {"value": round(whole_job_rate(2 * args.steps, world, e2e_s), 2), "unit": "MatMult/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "eager": {"value": round(whole_job_rate(2 * args.steps, world, eager_s), 2), "unit": "MatMult/s",
+                  "ms_per_step": round(1e3 * eager_s / args.steps, 4), "gpu_launches": launches_eager,
+                  "loop_launch_ms_in_step": round(step_loop_ms, 5), "clocks": clk_eager.summary()},
         "autotune": {"plain_gradient": pm_g.tuning(), "plain_forward": pm_f.tuning(),
                      "variants": "loop kernel (coefficients per thread, rotation groups, cp.async stages, gathers staged): "
                                  + ", ".join(f"{v} {s}" for v, s in enumerate(he.loop_variants()))},
@@ -669,6 +718,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-vfl-nn", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time the eager step (one API call per operation) as the headline")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
                     help="2: the forward product on a forked context and its own stream, overlapping the gradient product")
     ap.add_argument("--loop-variant", type=int, default=-1,

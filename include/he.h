@@ -122,6 +122,13 @@ int he_encode(he_ctx *ctx, const double *slots, int64_t n_slots, double scale, i
  * a and e are drawn from the Philox stream selected by `nonce`. */
 int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t nonce, he_ct *out);
 
+/* he_encrypt with the nonce read from device memory (one uint64_t at nonce_dev, 8-byte
+ * aligned) when the sampling kernels run, not when the call is made: a CUDA graph captured
+ * around this call encrypts under whatever nonce the buffer holds at each replay, so the
+ * caller writes a fresh nonce before each replay (never reuse one under the same key).
+ * Same ciphertext as he_encrypt with that nonce. */
+int he_encrypt_dnonce(he_ctx *ctx, const he_pt *pt, const uint64_t *nonce_dev, he_ct *out);
+
 /* Decryption (Sec. 2.2) at the first prime and decoding: N/2 real slot values (device) of
  * c0 + c1 s divided by the ciphertext's scale. */
 int he_decrypt(he_ctx *ctx, const he_ct *ct, double *slots_out);

@@ -536,7 +536,7 @@ int he_encode(he_ctx *ctx, const double *slots, int64_t n_slots, double scale, i
     return last_launch();
 }
 
-int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t nonce, he_ct *out) {
+static int encrypt_impl(he_ctx *ctx, const he_pt *pt, uint64_t nonce, const uint64_t *nonce_dev, he_ct *out) {
     if (!ctx || !pt || !out || !pt->data || !out->data) return HE_EINVAL;
     const int level = pt->level;
     if (level < 0 || level >= ctx->L) return HE_ELEVEL;
@@ -546,14 +546,21 @@ int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t nonce, he_ct *out) {
     uint64_t *a = tmp, *e = tmp + nl * N;
     int64_t *e_int = reinterpret_cast<int64_t *>(tmp + 2 * nl * N);
     const LimbMap m = qmap(level);
-    launch_sample_uniform(ctx, 2, nonce, m, 0, a);
+    launch_sample_uniform(ctx, 2, nonce, m, 0, a, nonce_dev);
     launch_ntt_fwd(ctx, a, a, 1, m);
-    launch_sample_gauss(ctx, 3, nonce, e_int);
+    launch_sample_gauss(ctx, 3, nonce, e_int, nonce_dev);
     launch_ntt_from_int64(ctx, e_int, e, 1, m, 0);
     launch_encrypt_combine(ctx, pt->data, a, e, level, out->data);
     out->level = level;
     out->scale = pt->scale;
     return last_launch();
+}
+
+int he_encrypt(he_ctx *ctx, const he_pt *pt, uint64_t nonce, he_ct *out) { return encrypt_impl(ctx, pt, nonce, nullptr, out); }
+
+int he_encrypt_dnonce(he_ctx *ctx, const he_pt *pt, const uint64_t *nonce_dev, he_ct *out) {
+    if (!nonce_dev) return HE_EINVAL;
+    return encrypt_impl(ctx, pt, 0, nonce_dev, out);
 }
 
 int he_decrypt(he_ctx *ctx, const he_ct *ct, double *slots_out) {

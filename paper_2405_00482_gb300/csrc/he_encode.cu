@@ -331,9 +331,12 @@ __device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t 
 
 // uniform residues: coefficient j of limb l (prime index map.prime[l]) from the 128-bit
 // integer (word 2(j&1)+1 : word 2(j&1)) of block (j/2, prime index, nonce, 0), key (seed, tag)
-__global__ void sample_uniform_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, LimbMap map, uint64_t *out,
-                                      const ModConst *__restrict__ mc, int logn) {
+// (nonce_dev, when given, holds the nonce in device memory: read when the kernel runs, so a
+// captured graph draws fresh randomness on every replay)
+__global__ void sample_uniform_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, const uint64_t *nonce_dev, LimbMap map,
+                                      uint64_t *out, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
+    if (nonce_dev) nonce = *nonce_dev;
     const int N = 1 << logn;
     const int l = blockIdx.y;
     const int p = map.prime[l];
@@ -351,8 +354,10 @@ struct Cdt {
 };
 
 // discrete Gaussian by cumulative table: r = word >> 24, x = -19 + #{k : r >= T_k}
-__global__ void sample_gauss_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, Cdt cdt, int64_t *out, int logn) {
+__global__ void sample_gauss_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, const uint64_t *nonce_dev, Cdt cdt, int64_t *out,
+                                    int logn) {
     HE_GRID_DEP();
+    if (nonce_dev) nonce = *nonce_dev;
     const int N = 1 << logn;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 4; b += gridDim.x * blockDim.x) {
         uint64_t c[4] = {(uint64_t)b, 0, nonce, 0};
@@ -484,17 +489,17 @@ void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count
                                                                     ctx->log_n);
 }
 
-void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int, uint64_t *out) {
+void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int, uint64_t *out, const uint64_t *nonce_dev) {
     dim3 grid((ctx->n / 2 + 255) / 256, map.n);
     ctx->launches++;
-    launch_k(sample_uniform_kernel, grid, 256, 0, ctx->stream, ctx->seed, tag, nonce, map, out, ctx->d_mc, ctx->log_n);
+    launch_k(sample_uniform_kernel, grid, 256, 0, ctx->stream, ctx->seed, tag, nonce, nonce_dev, map, out, ctx->d_mc, ctx->log_n);
 }
 
-void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out) {
+void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out, const uint64_t *nonce_dev) {
     Cdt c;
     for (int k = 0; k < 38; ++k) c.t[k] = ctx->cdt[k];
     ctx->launches++;
-    launch_k(sample_gauss_kernel, (ctx->n / 4 + 255) / 256, 256, 0, ctx->stream, ctx->seed, tag, nonce, c, out, ctx->log_n);
+    launch_k(sample_gauss_kernel, (ctx->n / 4 + 255) / 256, 256, 0, ctx->stream, ctx->seed, tag, nonce, nonce_dev, c, out, ctx->log_n);
 }
 
 void launch_sample_ternary(he_ctx *ctx, int64_t *out) {

@@ -52,6 +52,7 @@ _SIGS = {
     "he_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
     "he_encode": (ctypes.c_int, [_vp, _vp, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
     "he_encrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _u64, ctypes.POINTER(HeCt)]),
+    "he_encrypt_dnonce": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp, ctypes.POINTER(HeCt)]),
     "he_decrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_add": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
     "he_add_plain": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HePt), ctypes.POINTER(HeCt)]),
@@ -345,6 +346,36 @@ def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
     return t.to(dtype).contiguous()
 
 
+class Graph:
+    """The library calls `fn` issues, captured once into a CUDA graph and replayed with one launch.
+
+    `fn` issues its calls on `ctx` (whose stream is the capture stream and must not be the
+    legacy default stream) and on any forks, whose streams it joins back to ctx's stream before
+    it returns.  It runs once eagerly first (scratch growth and autotuning happen there), then
+    under capture.  Inputs and outputs are the device buffers `fn` names: write new inputs into
+    them before a replay; encrypt with a device nonce whose buffer changes between replays.
+    `launches` is the number of library kernels one replay runs."""
+
+    def __init__(self, ctx: "Context", fn, forks=()):
+        if ctx.stream.cuda_stream == 0:
+            raise ValueError("capture needs a context on a non-default stream")
+        self.ctxs = [ctx, *forks]
+        fn()
+        for c in self.ctxs:
+            c.synchronize()
+        l0 = sum(c.launch_count() for c in self.ctxs)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=ctx.stream):
+            fn()
+        self.launches = sum(c.launch_count() for c in self.ctxs) - l0
+        self.stream = ctx.stream
+
+    def replay(self):
+        """One replay on the capture context's stream."""
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+
+
 class Context:
     """he_ctx: parameters, tables, secret key and Galois keys on one CUDA device and stream."""
 
@@ -423,10 +454,17 @@ class Context:
         pt.level, pt.scale = c.level, c.scale
         return pt
 
-    def encrypt(self, pt: Plaintext, nonce: int, out: Ciphertext | None = None) -> Ciphertext:
+    def encrypt(self, pt: Plaintext, nonce, out: Ciphertext | None = None) -> Ciphertext:
+        """`nonce` an int, or a one-element int64 device tensor read when the kernels run (for
+        a captured Graph: write a fresh nonce there before each replay)."""
         ct = out or self.new_ct(pt.level)
         p, c = pt.c(), ct.c()
-        _check(_lib().he_encrypt(self.handle, ctypes.byref(p), nonce, ctypes.byref(c)), "he_encrypt")
+        if isinstance(nonce, torch.Tensor):
+            if nonce.numel() != 1 or nonce.dtype != torch.int64 or not nonce.is_cuda:
+                raise ValueError("device nonce: one int64 element on the GPU")
+            _check(_lib().he_encrypt_dnonce(self.handle, ctypes.byref(p), _vp(nonce.data_ptr()), ctypes.byref(c)), "he_encrypt_dnonce")
+        else:
+            _check(_lib().he_encrypt(self.handle, ctypes.byref(p), nonce, ctypes.byref(c)), "he_encrypt")
         ct.level, ct.scale = c.level, c.scale
         return ct
 
