@@ -143,8 +143,12 @@ def run_gpu(args):
 
     # the forward product runs on a forked context (own stream and scratch, shared keys) so the
     # two independent products of a step overlap on the GPU
-    two = args.streams == 2
+    two = args.streams >= 2
     fctx = ctx.fork() if two else ctx
+    # with four streams each product's matrix encoding runs on a fork of its own, beside the
+    # vector encoding and encryption
+    menc = [ctx.fork(), ctx.fork()] if args.streams == 4 else [ctx, fctx]
+    forks = ([fctx] if two else []) + (menc if args.streams == 4 else [])
     if two:
         with torch.cuda.stream(fctx.stream):
             pm_f = fctx.encode_matrix(plan_f, dX, level)
@@ -153,10 +157,17 @@ def run_gpu(args):
             pm_f.set_variant(args.loop_variant)
     main = torch.cuda.current_stream()
 
-    def product(c, plan, pm, Md, vd, pt, ct, nonce, out, slots, res):
-        c.encode_matrix(plan, Md, level, out=pm)
+    def product(c, cm, plan, pm, Md, vd, pt, ct, nonce, out, slots, res):
+        if cm is not c:
+            cm.stream.wait_stream(c.stream)
+            with torch.cuda.stream(cm.stream):
+                cm.encode_matrix(plan, Md, level, out=pm)
+        else:
+            c.encode_matrix(plan, Md, level, out=pm)
         c.encode_vector(plan, vd, P.scale, level, outs=[pt])
         c.encrypt(pt, nonce, out=ct)
+        if cm is not c:
+            c.stream.wait_stream(cm.stream)
         c.matmult(plan, pm, [ct], out)
         c.decrypt(out[0], slots[0])
         c.matmult_decode(plan, slots, res)
@@ -168,9 +179,9 @@ def run_gpu(args):
     def step(XTd, Xd, rd, wd):
         if two:
             fctx.stream.wait_stream(main)  # inputs copied / produced on the main stream
-        product(ctx, plan_g, pm_g, XTd, rd, pt_r, ct_r, nonce[0:1], out_g, slots_g, res_g)
+        product(ctx, menc[0], plan_g, pm_g, XTd, rd, pt_r, ct_r, nonce[0:1], out_g, slots_g, res_g)
         with torch.cuda.stream(fctx.stream):
-            product(fctx, plan_f, pm_f, Xd, wd, pt_w, ct_w, nonce[1:2], out_f, slots_f, res_f)
+            product(fctx, menc[1], plan_f, pm_f, Xd, wd, pt_w, ct_w, nonce[1:2], out_f, slots_f, res_f)
         if two:
             main.wait_stream(fctx.stream)
         nonce.add_(2)
@@ -205,18 +216,18 @@ def run_gpu(args):
         return [a.elapsed_time(b) for a, b in per]
 
     # eager: one API call per operation
-    launches0 = ctx.launch_count() + (fctx.launch_count() if two else 0)
+    launches0 = ctx.launch_count() + sum(f.launch_count() for f in forks)
     ctx.profile(True)
     with ClockSampler(local) as clk_eager:
         torch.cuda.synchronize()
         times_eager = timed_steps(lambda: step(dXT, dX, dr, dw))
     loop_ms, loop_launches = ctx.profile_read()
     ctx.profile(False)
-    launches_eager = ctx.launch_count() + (fctx.launch_count() if two else 0) - launches0
+    launches_eager = ctx.launch_count() + sum(f.launch_count() for f in forks) - launches0
     step_loop_ms = loop_ms / max(loop_launches, 1)
 
     # graph: the same calls captured once (he.Graph) and replayed with one launch per step
-    graph = he.Graph(ctx, lambda: step(dXT, dX, dr, dw), forks=[fctx] if two else [])
+    graph = he.Graph(ctx, lambda: step(dXT, dX, dr, dw), forks=forks)
     for i in range(args.warmup):
         graph.replay()
     res_g.zero_()
@@ -719,8 +730,8 @@ def main():
     ap.add_argument("--no-vfl-nn", action="store_true")
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time the eager step (one API call per operation) as the headline")
-    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
-                    help="2: the forward product on a forked context and its own stream, overlapping the gradient product")
+    ap.add_argument("--streams", type=int, default=4, choices=[1, 2, 4],
+                    help="2: the forward product on a forked context and its own stream, overlapping the gradient product; 4: also each matrix encoding on a stream of its own")
     ap.add_argument("--loop-variant", type=int, default=-1,
                     help="pin the MatMult loop-kernel variant of the plain products (default: autotune)")
     ap.add_argument("--serve-requests", type=int, default=2000)

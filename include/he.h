@@ -88,9 +88,12 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *cuda_stream, he_ctx *
 void he_ctx_destroy(he_ctx *ctx);
 /* A context on another stream that shares parent's tables, secret and Galois keys (keys made on
  * any context of the family are seen by all), with its own scratch, so calls on the two streams
- * can run concurrently.  The family's tables and keys are freed with its last context; forks and
- * parent may be destroyed in any order.  he_keygen on one context may run while the others work
- * (the key table is guarded).  Waits for the parent's stream once. */
+ * can run concurrently.  Plaintext matrices and weight matrices made on one context of the
+ * family may be encoded into and used on any other; the caller orders the streams (a matrix
+ * encoded on one stream and used on another needs an event between them) and frees a matrix
+ * before the context that made it.  The family's tables and keys are freed with its last
+ * context; forks and parent may be destroyed in any order.  he_keygen on one context may run
+ * while the others work (the key table is guarded).  Waits for the parent's stream once. */
 int he_ctx_fork(he_ctx *parent, void *cuda_stream, he_ctx **out);
 /* Wait for every call issued on the context's stream. */
 int he_synchronize(he_ctx *ctx);

@@ -752,7 +752,7 @@ static int ptmat_alloc(he_ctx *ctx, const he_plan *plan, int level, double scale
 }
 
 int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X) {
-    if (!ctx || !pm || !X || pm->ctx != ctx) return HE_EINVAL;
+    if (!ctx || !pm || !X || !same_family(pm->ctx, ctx)) return HE_EINVAL;
     const he_plan &p = pm->plan;
     const size_t N = ctx->n, count = (size_t)p.row_blocks * p.col_blocks * p.m_prime;
     uint64_t *s = ctx_scratch(ctx, count * (N / 2) + count * N);
@@ -779,7 +779,7 @@ int he_encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int leve
 }
 
 int he_ptmat_export(he_ctx *ctx, const he_ptmat *pm, uint64_t *coeffs_out) {
-    if (!ctx || !pm || !coeffs_out || pm->ctx != ctx) return HE_EINVAL;
+    if (!ctx || !pm || !coeffs_out || !same_family(pm->ctx, ctx)) return HE_EINVAL;
     const he_plan &p = pm->plan;
     const int count = (int)(p.row_blocks * p.col_blocks * p.m_prime);
     const LimbMap m = qpmap(ctx, pm->level);
@@ -855,7 +855,7 @@ int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm) {
 }
 
 int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm_c, const he_ct *ins, int n_in, he_ct *outs, int n_out) {
-    if (!ctx || !plan || !pm_c || !ins || !outs || pm_c->ctx != ctx) return HE_EINVAL;
+    if (!ctx || !plan || !pm_c || !ins || !outs || !same_family(pm_c->ctx, ctx)) return HE_EINVAL;
     he_ptmat *pm = const_cast<he_ptmat *>(pm_c);
     const he_plan &p = pm->plan;
     if (p.m != plan->m || p.n != plan->n || p.slots != plan->slots) return HE_EINVAL;
@@ -891,11 +891,15 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
         for (size_t c = 0; c < C; ++c)
             launch_matmult_loop(ctx, pm, r, (int)c, ins[c].data, rot ? D + c * mu.ndig * ext * N : nullptr, acc, cacc, c > 0);
         const uint64_t *pre = cacc;
-        if (rot) {
-            launch_moddown(ctx, acc, level, 2, cacc, cacc + nl * N, sum, tmp);
-            pre = sum;
+        if (rot && moddown_rescale_fused(ctx, level)) {
+            launch_moddown_rescale(ctx, acc, level, cacc, cacc + nl * N, outs[r].data);
+        } else {
+            if (rot) {
+                launch_moddown(ctx, acc, level, 2, cacc, cacc + nl * N, sum, tmp);
+                pre = sum;
+            }
+            launch_rescale(ctx, pre, level, outs[r].data, tmp);
         }
-        launch_rescale(ctx, pre, level, outs[r].data, tmp);
         outs[r].level = level - 1;
         outs[r].scale = ins[0].scale * pm->scale / (double)ctx->primes[level];
     }
@@ -1031,7 +1035,7 @@ int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const h
     *out = nullptr;
     const int level = pms[0] ? pms[0]->level : -1;
     for (int j = 0; j < count; ++j) {
-        if (!plans[j] || !pms[j] || pms[j]->ctx != ctx) return HE_EINVAL;
+        if (!plans[j] || !pms[j] || !same_family(pms[j]->ctx, ctx)) return HE_EINVAL;
         const he_plan &p = pms[j]->plan;
         if (p.m != plans[j]->m || p.n != plans[j]->n || p.row_blocks != 1 || p.col_blocks != 1) return HE_EINVAL;
         if (pms[j]->level != level) return HE_ELEVEL;

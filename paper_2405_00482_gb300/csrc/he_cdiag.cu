@@ -263,7 +263,7 @@ int he_cdiag_encode_matrix(he_ctx *ctx, const double *A, int64_t m, int64_t n, d
 }
 
 int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct, he_ct *outs) {
-    if (!ctx || !W || !cts || !outs || W->ctx != ctx || n_ct < 1 || n_ct > CD_MAX_IN || n_ct > W->n) return HE_EINVAL;
+    if (!ctx || !W || !cts || !outs || !same_family(W->ctx, ctx) || n_ct < 1 || n_ct > CD_MAX_IN || n_ct > W->n) return HE_EINVAL;
     const int level = W->level, nl = level + 1;
     for (int i = 0; i < n_ct; ++i) {
         if (!cts[i].data) return HE_EINVAL;

@@ -162,6 +162,10 @@ struct he_ctx {
     size_t prof_used;
 };
 
+// contexts of one family (a context and its forks) share tables and keys, so plaintext
+// matrices made on one serve all
+inline bool same_family(const he_ctx *a, const he_ctx *b) { return a == b || (a && b && a->sh && a->sh == b->sh); }
+
 // one MatMult of a batch (device table entry)
 struct MMJob {
     const uint64_t *ct;            // input ciphertext [2][level+1][N]
@@ -332,6 +336,10 @@ void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const 
                     uint64_t *tmp);
 void launch_automorph(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, const LimbMap &map, uint32_t g);
 void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, uint64_t *tmp);
+// ModDown of [2][level+1+K][N] plus add0/add1 (NTT, [level+1][N] each, may be null), then
+// rescale, into out [2][level][N]: one cluster launch when moddown_rescale_fused says so
+bool moddown_rescale_fused(const he_ctx *ctx, int level);
+void launch_moddown_rescale(he_ctx *ctx, const uint64_t *x, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out);
 void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D,
                          uint64_t *acc /*[2][ext][N]*/, uint64_t *cacc /*[2][level+1][N]*/, int accumulate);
 

@@ -67,7 +67,7 @@ uint32_t galois_elem(const he_ctx *ctx, int64_t step) {
 
 extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in, he_ct *outs,
                                                int n_out) {
-    if (!ctx || !plan || !pm || !ins || !outs || pm->ctx != ctx) return HE_EINVAL;
+    if (!ctx || !plan || !pm || !ins || !outs || !same_family(pm->ctx, ctx)) return HE_EINVAL;
     const he_plan &p = pm->plan;
     if (p.m != plan->m || p.n != plan->n || p.slots != plan->slots) return HE_EINVAL;
     if (n_in != p.col_blocks || n_out != p.row_blocks) return HE_EINVAL;
@@ -118,11 +118,15 @@ extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan,
             launch_matmult_loop_with_tables(ctx, pm, r, (int)c, ins[c].data, rot ? D + c * mu.ndig * ext * N : nullptr, keys, galois, acc,
                                             cacc, c > 0);
         const uint64_t *pre = cacc;
-        if (rot) {
-            launch_moddown(ctx, acc, level, 2, cacc, cacc + nl * N, sum, tmp);
-            pre = sum;
+        if (rot && moddown_rescale_fused(ctx, level)) {
+            launch_moddown_rescale(ctx, acc, level, cacc, cacc + nl * N, outs[r].data);
+        } else {
+            if (rot) {
+                launch_moddown(ctx, acc, level, 2, cacc, cacc + nl * N, sum, tmp);
+                pre = sum;
+            }
+            launch_rescale(ctx, pre, level, outs[r].data, tmp);
         }
-        launch_rescale(ctx, pre, level, outs[r].data, tmp);
         outs[r].level = level - 1;
         outs[r].scale = ins[0].scale * pm->scale / (double)ctx->primes[level];
     }

@@ -55,12 +55,15 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, in
         for (int j = 0; j < NB; ++j) {
             const int h = E >> (j + 1);
             const int m = 1 << (s0 + j);
-            const int lg_2t = lg_t0 - j + 1;
+            // element x = base + (k << lg_tl) meets twiddle m + (x >> (lg_t0 - j + 1)), which is
+            // m + (g << j) + (k >> (NB - j)): 2^j consecutive entries, loaded once per stage
+            ulonglong2 wj[E / 2];
+#pragma unroll
+            for (int i = 0; i < (1 << j); ++i) wj[i] = tw(m, m + (g << j) + i);
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 if ((k & (2 * h - 1)) < h) {
-                    const int x = base + (k << lg_tl);
-                    const ulonglong2 w = tw(m, m + (x >> lg_2t));
+                    const ulonglong2 w = wj[k >> (NB - j)];
                     uint64_t X = r[k];
                     X = X >= two_q ? X - two_q : X;
                     const uint64_t T = mul_shoup_lazy(r[k + h], w.x, w.y, q);
@@ -101,12 +104,15 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
         for (int j = 0; j < NB; ++j) {
             const int h = 1 << j;
             const int m = N >> (s0 + j + 1);
-            const int lg_2t = lg_t0 + j + 1;
+            // element x = base + (k << lg_t0) meets twiddle m + (x >> (lg_t0 + j + 1)), which is
+            // m + (g << (NB - j - 1)) + (k >> (j + 1)): 2^(NB-j-1) consecutive entries
+            ulonglong2 wj[E / 2];
+#pragma unroll
+            for (int i = 0; i < (E >> (j + 1)); ++i) wj[i] = itw(m, m + (g << (NB - j - 1)) + i);
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 if ((k & (2 * h - 1)) < h) {
-                    const int x = base + (k << lg_t0);
-                    const ulonglong2 w = itw(m, m + (x >> lg_2t));
+                    const ulonglong2 w = wj[k >> (j + 1)];
                     const uint64_t U = r[k], V = r[k + h];
                     uint64_t X = U + V;
                     r[k] = X >= two_q ? X - two_q : X;

@@ -87,7 +87,8 @@ def test_fork_outlives_parent(he):
     assert e.value.status == he.HE_EKEY
 
 
-def test_fork_rejects_foreign_ptmat(he):
+def test_ptmat_shared_in_family_foreign_rejected(he):
+    """A plaintext matrix encoded on the fork serves the parent; another family's is refused."""
     import torch
 
     P = inputs.PARAMS_N8192
@@ -95,8 +96,16 @@ def test_fork_rejects_foreign_ptmat(he):
     plan = he.Plan(64, 64, P.slots)
     ctx.keygen(list(range(1, plan.m_prime)))
     fork = ctx.fork(torch.cuda.current_stream())
-    pm = ctx.encode_matrix(plan, torch.ones((64, 64), dtype=torch.float64, device="cuda"), P.top)
-    ct = ctx.encrypt(ctx.encode_vector(plan, torch.ones(64, dtype=torch.float64, device="cuda"), P.scale, P.top)[0], 1)
+    M = torch.from_numpy(np.random.default_rng(1).normal(size=(64, 64))).cuda()
+    y = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, 64)).cuda()
+    pm_fork = fork.encode_matrix(plan, M, P.top)
+    pm_ctx = ctx.encode_matrix(plan, M, P.top)
+    ct = ctx.encrypt(ctx.encode_vector(plan, y, P.scale, P.top)[0], 1)
+    a = he.as_u64(ctx.ct_export(ctx.matmult(plan, pm_fork, [ct])[0]))
+    b = he.as_u64(ctx.ct_export(fork.matmult(plan, pm_ctx, [ct])[0]))
+    assert np.array_equal(a, b)
+    other = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=2)
+    other.keygen(list(range(1, plan.m_prime)))
     with pytest.raises(he.HEError) as e:
-        fork.matmult(plan, pm, [ct])
+        other.matmult(plan, pm_ctx, [ct])
     assert e.value.status == he.HE_EINVAL
