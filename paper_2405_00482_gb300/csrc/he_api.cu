@@ -263,7 +263,8 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     }
 
     // per-prime constants and NTT twiddles
-    std::vector<uint64_t> tw((size_t)LK * 4 * N);
+    const size_t t4 = ctx->log_n >= 4 ? (size_t)15 * (N / 16) : 0, prime_words = (size_t)4 * N + 4 * t4;
+    std::vector<uint64_t> tw((size_t)LK * prime_words);
     for (int i = 0; i < LK; ++i) {
         const uint64_t q = ctx->primes[i];
         ctx->mc.push_back(make_modconst(q, ctx->log_n));
@@ -275,13 +276,35 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
             ipw[k] = hmul(ipw[k - 1], ipsi, q);
         }
         // [forward pairs (psi^brv(k), Shoup quotient)][inverse pairs (psi^-brv(k), quotient)]
-        uint64_t *t = tw.data() + (size_t)i * 4 * N;
+        uint64_t *t = tw.data() + (size_t)i * prime_words;
         for (int k = 0; k < N; ++k) {
             const uint64_t e = brv(k, ctx->log_n);
             t[2 * k] = pw[e];
             t[2 * k + 1] = shoup(pw[e], q);
             t[2 * N + 2 * k] = ipw[e];
             t[2 * N + 2 * k + 1] = shoup(ipw[e], q);
+        }
+        // stage-ordered copies for the radix-16 pass whose sets are its groups (G = N/16 sets):
+        // forward last pass, stage j (m = N/2^(4-j)): entry i < 2^j of set g at ((2^j - 1 + i) G + g)
+        // is table entry m + g 2^j + i; inverse first pass, stage j (m = N/2^(j+1)): entry
+        // i < 2^(3-j) at ((16 - 2^(4-j) + i) G + g) is entry m + g 2^(3-j) + i
+        if (t4) {
+            const int G = N / 16;
+            uint64_t *f4 = t + 4 * (size_t)N, *i4 = f4 + 2 * t4;
+            for (int j = 0; j < 4; ++j)
+                for (int g = 0; g < G; ++g) {
+                    for (int e = 0; e < (1 << j); ++e) {
+                        const size_t dst = 2 * ((size_t)((1 << j) - 1 + e) * G + g), src = 2 * ((size_t)(N >> (4 - j)) + ((size_t)g << j) + e);
+                        f4[dst] = t[src];
+                        f4[dst + 1] = t[src + 1];
+                    }
+                    for (int e = 0; e < (8 >> j); ++e) {
+                        const size_t dst = 2 * ((size_t)(16 - (16 >> j) + e) * G + g),
+                                     src = 2 * N + 2 * ((size_t)(N >> (j + 1)) + ((size_t)g << (3 - j)) + e);
+                        i4[dst] = t[src];
+                        i4[dst + 1] = t[src + 1];
+                    }
+                }
         }
     }
     // FFT tables as double-float (hi, lo) pairs: [N/4] exp(-2 pi i k/(N/2)), [N/2] exp(-i pi k / N),

@@ -143,7 +143,8 @@ struct he_ctx {
     std::vector<uint64_t> primes;     // Q then P
     std::vector<ModConst> mc;         // host copy
     ModConst *d_mc;                   // device copy
-    uint64_t *d_tw;                   // [L+K][2][N] pairs (w, Shoup(w)): forward psi^brv(k), inverse psi^-brv(k)
+    uint64_t *d_tw;                   // per prime: [2][N] pairs (w, Shoup(w)), forward psi^brv(k) and inverse psi^-brv(k),
+                                      // then [2][15 N/16] stage-ordered copies (he_ntt.cuh, tw_prime_words)
     void *d_fft;                      // encode/decode tables (double-float twiddles, twist, slot positions)
     uint64_t *d_sk_mont;              // [L+K][N] secret in NTT + Montgomery form
     uint64_t *d_sk;                   // [L+K][N] secret in NTT form

@@ -23,7 +23,7 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const uint64_t q = mc[p].q;
     tw_prefetch<CL, true>(s, twiddles(d_tw, p, 0, logn), logn);
     const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
+    stage_in(s, src, len, [](uint64_t v) { return v; });
     __syncthreads();
     fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
@@ -48,7 +48,7 @@ __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const uint64_t q = mc[p].q;
     tw_prefetch<CL, false>(s, twiddles(d_tw, p, 1, logn), logn);
     const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
+    stage_in(s, src, len, [](uint64_t v) { return v; });
     __syncthreads();
     inv_any<CL>(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
@@ -70,7 +70,8 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     const uint64_t q = mc[p].q;
     tw_prefetch<CL, true>(s, twiddles(d_tw, p, 0, logn), logn);
     const int64_t *src = in + (int64_t)g * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = reduce_signed(src[k], q, mc[p].mu);
+    const uint64_t mu = mc[p].mu;
+    stage_in(s, src, len, [q, mu](int64_t v) { return reduce_signed(v, q, mu); });
     __syncthreads();
     fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + ((int64_t)g * map.n + l) * N + off;

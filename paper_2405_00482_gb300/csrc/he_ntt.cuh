@@ -25,12 +25,51 @@ namespace cg = cooperative_groups;
 // strided passes (a CTA needs ntt_smem_words(N) = N + N/32 words).
 #define SIDX(k) ((k) + ((k) >> 5))
 
+// s[SIDX(k)] = f(src[k]) for k < len, thread t taking k = t + u blockDim.x: eight global loads in
+// flight per thread before the first is used, instead of one load and its wait per element
+template <class T, class F>
+__device__ __forceinline__ void stage_in(uint64_t *s, const T *__restrict__ src, int len, F f) {
+    constexpr int U = 8;
+    const int stride = blockDim.x;
+    for (int k0 = threadIdx.x; k0 < len; k0 += U * stride) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * stride;
+            v[u] = k < len ? src[k] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * stride;
+            if (k < len) s[SIDX(k)] = f(v[u]);
+        }
+    }
+}
+
 // Twiddle access: entry idx of the bit-reversed table (idx = m + j for a stage with m groups).
 // TwGlobal reads the table in global memory; the cluster forms read a per-slice copy in shared
 // memory (see tw_prefetch).
 struct TwGlobal {
     const ulonglong2 *tw;
     __device__ __forceinline__ ulonglong2 operator()(int, int idx) const { return tw[idx]; }
+    // entry i of the 2^j (forward) or 2^(NB-j-1) (inverse) consecutive ones that stage j of a
+    // pass gives set group g, entry idx of the bit-reversed table
+    __device__ __forceinline__ ulonglong2 at(int, int, int, int m, int idx) const { return tw[idx]; }
+};
+
+// The radix-16 pass whose sets are its groups (g = set: the forward transform's last pass, the
+// inverse's first) reads, at stage j, entries that lie 2^j (or 2^(3-j)) apart for neighbouring
+// threads, so a warp's load touches up to 32 lines.  These accessors read a copy of those
+// entries ordered [stage j][entry i][set g] (G = N/16 sets), one coalesced line run per load.
+struct TwLastFwd {
+    const ulonglong2 *t4;
+    int G;
+    __device__ __forceinline__ ulonglong2 at(int j, int g, int i, int, int) const { return t4[((1 << j) - 1 + i) * G + g]; }
+};
+struct TwFirstInv {
+    const ulonglong2 *t4;
+    int G;
+    __device__ __forceinline__ ulonglong2 at(int j, int g, int i, int, int) const { return t4[(16 - (16 >> j) + i) * G + g]; }
 };
 
 // A pass over sets [set0, set1) of stages s0..s0+NB-1; element x lives at s[SIDX(x - off)].
@@ -59,7 +98,7 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, in
             // m + (g << j) + (k >> (NB - j)): 2^j consecutive entries, loaded once per stage
             ulonglong2 wj[E / 2];
 #pragma unroll
-            for (int i = 0; i < (1 << j); ++i) wj[i] = tw(m, m + (g << j) + i);
+            for (int i = 0; i < (1 << j); ++i) wj[i] = tw.at(j, g, i, m, m + (g << j) + i);
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 if ((k & (2 * h - 1)) < h) {
@@ -108,7 +147,7 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
             // m + (g << (NB - j - 1)) + (k >> (j + 1)): 2^(NB-j-1) consecutive entries
             ulonglong2 wj[E / 2];
 #pragma unroll
-            for (int i = 0; i < (E >> (j + 1)); ++i) wj[i] = itw(m, m + (g << (NB - j - 1)) + i);
+            for (int i = 0; i < (E >> (j + 1)); ++i) wj[i] = itw.at(j, g, i, m, m + (g << (NB - j - 1)) + i);
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 if ((k & (2 * h - 1)) < h) {
@@ -126,6 +165,15 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
     __syncthreads();
 }
 
+// Per prime the twiddle block holds, in 16-byte pairs (w, Shoup quotient): the forward table
+// [N], the inverse table [N], then the stage-ordered copies [15 N/16] of the forward transform's
+// last pass and [15 N/16] of the inverse transform's first pass (none below N = 16).
+__host__ __device__ __forceinline__ size_t tw_t4_pairs(int logn) { return logn >= 4 ? (size_t)15 << (logn - 4) : 0; }
+__host__ __device__ __forceinline__ size_t tw_prime_words(int logn) { return ((size_t)4 << logn) + 4 * tw_t4_pairs(logn); }
+// from the forward (inverse) table of a prime to its copy for the last (first) pass
+__device__ __forceinline__ const ulonglong2 *tw_last_fwd(const ulonglong2 *tw, int logn) { return tw + (2 << logn); }
+__device__ __forceinline__ const ulonglong2 *tw_first_inv(const ulonglong2 *itw, int logn) { return itw + (1 << logn) + tw_t4_pairs(logn); }
+
 // in-place forward transform of canonical residues in s[SIDX(0..N)); output canonical
 // The stage count left over by the radix-16 passes (log N mod 4) runs first: the early stages use
 // few distinct twiddles (stage t has 2^t), so a short pass there costs little, while the last
@@ -137,7 +185,10 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t *s, const ulonglong2 *__re
         const int nb = (s0 == 0 && first) ? first : HE_NTT_RADIX_LOG;
         const bool last = s0 + nb == logn;
         switch (nb) {
-            case 4: ntt_fwd_pass<4>(s, TwGlobal{tw}, q, logn, s0, last); break;
+            case 4:
+                if (last) ntt_fwd_pass<4>(s, TwLastFwd{tw_last_fwd(tw, logn), 1 << (logn - 4)}, q, logn, s0, last);
+                else ntt_fwd_pass<4>(s, TwGlobal{tw}, q, logn, s0, last);
+                break;
             case 3: ntt_fwd_pass<3>(s, TwGlobal{tw}, q, logn, s0, last); break;
             case 2: ntt_fwd_pass<2>(s, TwGlobal{tw}, q, logn, s0, last); break;
             default: ntt_fwd_pass<1>(s, TwGlobal{tw}, q, logn, s0, last); break;
@@ -152,7 +203,10 @@ __device__ __forceinline__ void ntt_inv_smem(uint64_t *s, const ulonglong2 *__re
     while (s0 < logn) {
         const int nb = logn - s0 < HE_NTT_RADIX_LOG ? logn - s0 : HE_NTT_RADIX_LOG;
         switch (nb) {
-            case 4: ntt_inv_pass<4>(s, TwGlobal{itw}, q, logn, s0); break;
+            case 4:
+                if (s0 == 0) ntt_inv_pass<4>(s, TwFirstInv{tw_first_inv(itw, logn), 1 << (logn - 4)}, q, logn, s0);
+                else ntt_inv_pass<4>(s, TwGlobal{itw}, q, logn, s0);
+                break;
             case 3: ntt_inv_pass<3>(s, TwGlobal{itw}, q, logn, s0); break;
             case 2: ntt_inv_pass<2>(s, TwGlobal{itw}, q, logn, s0); break;
             default: ntt_inv_pass<1>(s, TwGlobal{itw}, q, logn, s0); break;
@@ -213,11 +267,13 @@ struct TwSliceFwd {
     const ulonglong2 *stw;
     int rank;
     __device__ __forceinline__ ulonglong2 operator()(int m, int idx) const { return stw[idx - m + (1 - rank) * (m >> 3) - 1]; }
+    __device__ __forceinline__ ulonglong2 at(int, int, int, int m, int idx) const { return (*this)(m, idx); }
 };
 struct TwSliceInv {
     const ulonglong2 *stw;
     int rank, half_n;
     __device__ __forceinline__ ulonglong2 operator()(int m, int idx) const { return stw[((half_n - m) >> 2) + idx - m - rank * (m >> 3)]; }
+    __device__ __forceinline__ ulonglong2 at(int, int, int, int m, int idx) const { return (*this)(m, idx); }
 };
 
 template <bool FWD>
@@ -358,5 +414,5 @@ __device__ __forceinline__ void inv_any(uint64_t *s, const ulonglong2 *tw, uint6
 
 // twiddle table of prime index p: which = 0 forward (psi^brv(k), Shoup), 1 inverse (psi^-brv(k), Shoup)
 __device__ __forceinline__ const ulonglong2 *twiddles(const uint64_t *d_tw, int p, int which, int logn) {
-    return reinterpret_cast<const ulonglong2 *>(d_tw + (((size_t)p * 2 + which) << (logn + 1)));
+    return reinterpret_cast<const ulonglong2 *>(d_tw + (size_t)p * tw_prime_words(logn) + ((size_t)which << (logn + 1)));
 }
