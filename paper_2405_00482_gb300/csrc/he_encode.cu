@@ -174,8 +174,10 @@ __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, c
 // local passes of the cluster form: radix 2, one butterfly per thread per stage (MS/2 threads, at
 // most 512), since a cluster transform is latency-bound and on GB300 the most warps with the
 // shortest chains finished it soonest (radix 8 > radix 4 > radix 2 in time)
-#define FFT_CL_RADIX_LOG 1
-template <int CLG>
+// RL: local passes of radix 2^RL (MS >> RL threads).  RL = 1 throughout: on GB300 radix 4 and 8
+// (and 2 CTAs per transform with radix 8, or one CTA) were slower even for the 64 transforms of
+// an encoded matrix, where the launch is throughput- rather than latency-bound
+template <int CLG, int RL>
 __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
     constexpr int CL = 1 << CLG;
     cg::cluster_group cl = cg::this_cluster();
@@ -183,9 +185,10 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
     const int lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
     int s0 = 0;
     while (s0 < lg_ms) {
-        const int nb = lg_ms - s0 < FFT_CL_RADIX_LOG ? lg_ms - s0 : FFT_CL_RADIX_LOG;
+        const int nb = lg_ms - s0 < RL ? lg_ms - s0 : RL;
         const int E = 1 << nb;
         switch (nb) {
+            case 3: fft_pass<3>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
             case 2: fft_pass<2>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
             default: fft_pass<1>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
         }
@@ -227,7 +230,7 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
 
 // cluster per plaintext: the slot values go straight to their bit-reversed positions in the
 // owning CTAs; each CTA then twists and rounds the coefficients of its slice
-template <int CLG>
+template <int CLG, int RL>
 __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
                                  const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
                                  int64_t *out, int logn) {
@@ -245,7 +248,7 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
         cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(v.hi, v.lo, 0.f, 0.f);
     }
     cl.sync();
-    fft_cluster<CLG>(a, tw, logm, -1);
+    fft_cluster<CLG, RL>(a, tw, logm, -1);
     const df f = df_from(2.0 / (double)N * scale);
     int64_t *o = out + (int64_t)item * N;
     for (int i = threadIdx.x; i < MS; i += blockDim.x) {
@@ -259,7 +262,7 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
 
 // cluster per polynomial: each CTA loads the coefficients whose bit-reversed positions it holds;
 // the slot values are read from the owning CTAs
-template <int CLG>
+template <int CLG, int RL>
 __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
                                  const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
     HE_GRID_DEP();
@@ -277,7 +280,7 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
         a[i] = c;
     }
     __syncthreads();
-    fft_cluster<CLG>(a, tw, logm, +1);
+    fft_cluster<CLG, RL>(a, tw, logm, +1);
     double *o = out + (int64_t)item * M;
     const double inv = 1.0 / scale;
     const int per = M >> CLG;
@@ -439,10 +442,10 @@ static int fft_cluster_log(int logn, int count) {
     return 0;
 }
 
-template <int CLG, typename... KArgs, typename... Args>
+template <int CLG, int RL, typename... KArgs, typename... Args>
 static void launch_fft_cl(void (*kernel)(KArgs...), he_ctx *ctx, int count, Args... args) {
     const int MS = ctx->n / 2 >> CLG;
-    int threads = MS >> FFT_CL_RADIX_LOG;
+    int threads = MS >> RL;
     threads = threads < 32 ? 32 : (threads > 512 ? 512 : threads);
     launch_cluster_n(kernel, count << CLG, threads, (size_t)MS * sizeof(float4), ctx->stream, 1 << CLG, args...);
 }
@@ -454,9 +457,9 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
     switch (fft_cluster_log(ctx->log_n, count)) {
-        case 3: launch_fft_cl<3>(encode_cl_kernel<3>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
-        case 2: launch_fft_cl<2>(encode_cl_kernel<2>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
-        case 1: launch_fft_cl<1>(encode_cl_kernel<1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 3: launch_fft_cl<3, 1>(encode_cl_kernel<3, 1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 2: launch_fft_cl<2, 1>(encode_cl_kernel<2, 1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 1: launch_fft_cl<1, 1>(encode_cl_kernel<1, 1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
         default: break;
     }
     launch_k(encode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
@@ -469,9 +472,9 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
     switch (fft_cluster_log(ctx->log_n, count)) {
-        case 3: launch_fft_cl<3>(decode_cl_kernel<3>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
-        case 2: launch_fft_cl<2>(decode_cl_kernel<2>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
-        case 1: launch_fft_cl<1>(decode_cl_kernel<1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 3: launch_fft_cl<3, 1>(decode_cl_kernel<3, 1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 2: launch_fft_cl<2, 1>(decode_cl_kernel<2, 1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 1: launch_fft_cl<1, 1>(decode_cl_kernel<1, 1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
         default: break;
     }
     launch_k(decode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, coeffs, scale, tw, twist, pos, slots, ctx->log_n);
@@ -532,6 +535,6 @@ void encode_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decrypt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decrypt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(encode_cl_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(decode_cl_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(encode_cl_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(decode_cl_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
 }
