@@ -1058,27 +1058,33 @@ int mm_batch_ctas_per_sm(int v, int ndig) {
 namespace {
 
 // ---- cleartext layout (Eq. 2 after Eq. 3) and lazy rotate-and-sum (Sec. 4.3) ----
+// Every size of a plan but m and n is a power of two (slots, padded and block sizes, m', block
+// counts), so the index arithmetic below is shifts and masks: log2 of such a size.
+__device__ __forceinline__ int lg2p(int64_t v) { return __ffsll(v) - 1; }
+
 __global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, double *out, int64_t total) {
     HE_GRID_DEP();
+    const int ls = lg2p(p.slots), lm = lg2p(p.m_prime), lc = lg2p(p.col_blocks), lnb = lg2p(p.nb), lmb = lg2p(p.mb);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = idx % p.slots;
-        int64_t rest = idx / p.slots;
-        const int64_t i = rest % p.m_prime;
-        rest /= p.m_prime;
-        const int64_t c = rest % p.col_blocks, r = rest / p.col_blocks;
-        const int64_t b = s / p.nb, jj = s % p.nb;
-        const int64_t row = r * p.mb + b * p.m_prime + (jj % p.m_prime);
-        const int64_t col = c * p.nb + (i + jj) % p.nb;
+        const int64_t s = idx & (p.slots - 1);
+        int64_t rest = idx >> ls;
+        const int64_t i = rest & (p.m_prime - 1);
+        rest >>= lm;
+        const int64_t c = rest & (p.col_blocks - 1), r = rest >> lc;
+        const int64_t b = s >> lnb, jj = s & (p.nb - 1);
+        const int64_t row = (r << lmb) + (b << lm) + (jj & (p.m_prime - 1));
+        const int64_t col = (c << lnb) + ((i + jj) & (p.nb - 1));
         out[idx] = (row < p.m && col < p.n) ? X[row * p.n + col] : 0.0;
     }
 }
 
 __global__ void layout_vector_kernel(he_plan p, const double *__restrict__ y, double *out) {
     HE_GRID_DEP();
+    const int ls = lg2p(p.slots), lnb = lg2p(p.nb);
     const int64_t total = p.col_blocks * p.slots;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = idx / p.slots, s = idx % p.slots;
-        const int64_t col = c * p.nb + s % p.nb;
+        const int64_t c = idx >> ls, s = idx & (p.slots - 1);
+        const int64_t col = (c << lnb) + (s & (p.nb - 1));
         out[idx] = col < p.n ? y[col] : 0.0;
     }
 }
@@ -1086,12 +1092,15 @@ __global__ void layout_vector_kernel(he_plan p, const double *__restrict__ y, do
 // y[r mb + b m' + t] = sum_{s < nb/m'} (slots - mask)[r][b nb + t + s m'] (mask may be null)
 __global__ void lazy_ras_kernel(he_plan p, const double *__restrict__ slots, const double *__restrict__ mask, double *y) {
     HE_GRID_DEP();
+    const int lmb = lg2p(p.mb), lm = lg2p(p.m_prime), lnb = lg2p(p.nb), ls = lg2p(p.slots);
+    const int64_t terms = p.nb >> lm;
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < p.m; row += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = row / p.mb, rem = row % p.mb;
-        const int64_t b = rem / p.m_prime, t = rem % p.m_prime;
-        const int64_t off = r * p.slots + b * p.nb + t;
-        double acc = 0.0;
-        for (int64_t s = 0; s < p.nb / p.m_prime; ++s) acc += mask ? slots[off + s * p.m_prime] - mask[off + s * p.m_prime] : slots[off + s * p.m_prime];
+        const int64_t r = row >> lmb, rem = row & (p.mb - 1);
+        const int64_t b = rem >> lm, t = rem & (p.m_prime - 1);
+        const int64_t off = (r << ls) + (b << lnb) + t;
+        double acc = 0.0;  // summed in order s = 0, 1, ...; the unrolling only issues the loads early
+#pragma unroll 8
+        for (int64_t s = 0; s < terms; ++s) acc += mask ? slots[off + (s << lm)] - mask[off + (s << lm)] : slots[off + (s << lm)];
         y[row] = acc;
     }
 }
@@ -1099,10 +1108,11 @@ __global__ void lazy_ras_kernel(he_plan p, const double *__restrict__ slots, con
 // after the ciphertext rotate-and-sum: y[r mb + b m' + t] = slots[r][b nb + t]
 __global__ void ras_gather_kernel(he_plan p, const double *__restrict__ slots, double *y) {
     HE_GRID_DEP();
+    const int lmb = lg2p(p.mb), lm = lg2p(p.m_prime), lnb = lg2p(p.nb), ls = lg2p(p.slots);
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < p.m; row += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = row / p.mb, rem = row % p.mb;
-        const int64_t b = rem / p.m_prime, t = rem % p.m_prime;
-        y[row] = slots[r * p.slots + b * p.nb + t];
+        const int64_t r = row >> lmb, rem = row & (p.mb - 1);
+        const int64_t b = rem >> lm, t = rem & (p.m_prime - 1);
+        y[row] = slots[(r << ls) + (b << lnb) + t];
     }
 }
 
