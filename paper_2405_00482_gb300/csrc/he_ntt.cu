@@ -56,11 +56,14 @@ __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], ni, nis, q);
 }
 
-// signed int64 coefficients of group g, reduced mod each limb's prime, then forward NTT
-template <bool CL>
+// signed int64 coefficients of group g, reduced mod each limb's prime, then forward NTT.
+// LOGN > 0 (one-CTA form only): the ring size at compile time, logn == LOGN.
+template <bool CL, int LOGN = 0>
 __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *out, LimbMap map, const uint64_t *__restrict__ d_tw,
-                                      const ModConst *__restrict__ mc, int logn, int to_mont) {
+                                      const ModConst *__restrict__ mc, int logn_rt, int to_mont) {
+    static_assert(!CL || LOGN == 0, "cluster form has a runtime ring size");
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int poly, off, len;
@@ -73,7 +76,8 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     const uint64_t mu = mc[p].mu;
     stage_in(s, src, len, [q, mu](int64_t v) { return reduce_signed(v, q, mu); });
     __syncthreads();
-    fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
+    if constexpr (LOGN > 0) ntt_fwd_smem_c<LOGN>(s, twiddles(d_tw, p, 0, logn), q);
+    else fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + ((int64_t)g * map.n + l) * N + off;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
@@ -174,9 +178,17 @@ void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int gr
     if (use_cluster(ctx->log_n, polys))
         launch_cluster(ntt_from_int64_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, out, map,
                        ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
-    else
-        launch_k(ntt_from_int64_kernel<false>, polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, in, out, map, ctx->d_tw,
-                                                                                                               ctx->d_mc, ctx->log_n, to_mont);
+    else {
+        // the ring sizes of the parameter sets in use get a transform with constant strides
+        auto k = ctx->log_n == 13 ? ntt_from_int64_kernel<false, 13>
+               : ctx->log_n == 14 ? ntt_from_int64_kernel<false, 14>
+               : ctx->log_n == 12 ? ntt_from_int64_kernel<false, 12>
+                                  : ntt_from_int64_kernel<false>;
+        // 72 registers: three CTAs fit on an SM, so in a multi-stream step the other streams'
+        // kernels find room beside it (capping it at two per SM made the encoded matrix alone
+        // faster, 80 against 95 us, and the benchmark step 3% slower)
+        launch_k(k, polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, in, out, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
+    }
 }
 
 void launch_to_mont(he_ctx *ctx, uint64_t *data, int groups, const LimbMap &map) {
@@ -190,6 +202,9 @@ void ntt_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(ntt_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(ntt_inv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(ntt_from_int64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_from_int64_kernel<false, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_from_int64_kernel<false, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    cudaFuncSetAttribute(ntt_from_int64_kernel<false, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     // cluster forms: slice plus its twiddles (above 48 KB from N = 2^14)
     cudaFuncSetAttribute(ntt_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(ntt_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);

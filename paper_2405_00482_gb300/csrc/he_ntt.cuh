@@ -87,9 +87,13 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, in
     for (int set = set0 + threadIdx.x; set < set1; set += blockDim.x) {
         const int g = set >> lg_tl, low = set & ((1 << lg_tl) - 1);
         const int base = (g << (lg_t0 + 1)) + low;
+        // element base + (k << lg_tl) sits at sb + SIDX(k << lg_tl): the low five bits of base
+        // plus those of k << lg_tl stay below 32 for every pass shape (and off is a multiple of
+        // 32), so the padding splits over the sum
+        const int sb = SIDX(base) - SIDX(off);
         uint64_t r[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_tl) - off)];
+        for (int k = 0; k < E; ++k) r[k] = s[sb + SIDX(k << lg_tl)];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const int h = E >> (j + 1);
@@ -120,7 +124,7 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, in
             }
         }
 #pragma unroll
-        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_tl) - off)] = r[k];
+        for (int k = 0; k < E; ++k) s[sb + SIDX(k << lg_tl)] = r[k];
     }
     __syncthreads();
 }
@@ -136,9 +140,10 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
     for (int set = set0 + threadIdx.x; set < set1; set += blockDim.x) {
         const int g = set >> lg_t0, low = set & ((1 << lg_t0) - 1);
         const int base = (g << (lg_t0 + NB)) + low;
+        const int sb = SIDX(base) - SIDX(off);  // as in the forward pass
         uint64_t r[E];
 #pragma unroll
-        for (int k = 0; k < E; ++k) r[k] = s[SIDX(base + (k << lg_t0) - off)];
+        for (int k = 0; k < E; ++k) r[k] = s[sb + SIDX(k << lg_t0)];
 #pragma unroll
         for (int j = 0; j < NB; ++j) {
             const int h = 1 << j;
@@ -160,7 +165,7 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
             }
         }
 #pragma unroll
-        for (int k = 0; k < E; ++k) s[SIDX(base + (k << lg_t0) - off)] = r[k];
+        for (int k = 0; k < E; ++k) s[sb + SIDX(k << lg_t0)] = r[k];
     }
     __syncthreads();
 }
@@ -194,6 +199,29 @@ __device__ __forceinline__ void ntt_fwd_smem(uint64_t *s, const ulonglong2 *__re
             default: ntt_fwd_pass<1>(s, TwGlobal{tw}, q, logn, s0, last); break;
         }
         s0 += nb;
+    }
+}
+
+// ntt_fwd_smem for a ring size known at compile time (LOGN >= 4): the pass schedule, strides,
+// twiddle offsets and shared-memory offsets fold to constants
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd_smem_c(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q) {
+    static_assert(LOGN >= 4 && LOGN <= 16, "compile-time ring size");
+    constexpr int R = HE_NTT_RADIX_LOG, FIRST = LOGN % R, NPASS = (LOGN + R - 1) / R;
+#pragma unroll
+    for (int pi = 0; pi < NPASS; ++pi) {
+        const int nb = (pi == 0 && FIRST) ? FIRST : R;
+        const int s0 = pi == 0 ? 0 : (FIRST ? FIRST : R) + (pi - 1) * R;
+        const bool last = pi == NPASS - 1;
+        switch (nb) {
+            case 4:
+                if (last) ntt_fwd_pass<4>(s, TwLastFwd{tw_last_fwd(tw, LOGN), 1 << (LOGN - 4)}, q, LOGN, s0, last);
+                else ntt_fwd_pass<4>(s, TwGlobal{tw}, q, LOGN, s0, last);
+                break;
+            case 3: ntt_fwd_pass<3>(s, TwGlobal{tw}, q, LOGN, s0, last); break;
+            case 2: ntt_fwd_pass<2>(s, TwGlobal{tw}, q, LOGN, s0, last); break;
+            default: ntt_fwd_pass<1>(s, TwGlobal{tw}, q, LOGN, s0, last); break;
+        }
     }
 }
 
