@@ -177,14 +177,16 @@ __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, c
 // RL: local passes of radix 2^RL (MS >> RL threads).  RL = 1 throughout: on GB300 radix 4 and 8
 // (and 2 CTAs per transform with radix 8, or one CTA) were slower even for the 64 transforms of
 // an encoded matrix, where the launch is throughput- rather than latency-bound
-template <int CLG, int RL>
+// LOGM > 0: log M at compile time (logm == LOGM), so the pass loop unrolls and indices fold
+template <int CLG, int RL, int LOGM = 0>
 __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
     constexpr int CL = 1 << CLG;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
-    int s0 = 0;
-    while (s0 < lg_ms) {
+#pragma unroll(LOGM > 0 ? 16 : 1)
+    for (int s0 = 0; s0 < (LOGM > 0 ? LOGM - CLG : 16); s0 += RL) {
+        if (s0 >= lg_ms) break;
         const int nb = lg_ms - s0 < RL ? lg_ms - s0 : RL;
         const int E = 1 << nb;
         switch (nb) {
@@ -192,7 +194,6 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
             case 2: fft_pass<2>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
             default: fft_pass<1>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
         }
-        s0 += nb;
     }
     cl.sync();
     float4 *rem[CL];
@@ -230,11 +231,12 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
 
 // cluster per plaintext: the slot values go straight to their bit-reversed positions in the
 // owning CTAs; each CTA then twists and rounds the coefficients of its slice
-template <int CLG, int RL>
+template <int CLG, int RL, int LOGN = 0>
 __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
                                  const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
-                                 int64_t *out, int logn) {
+                                 int64_t *out, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
@@ -248,7 +250,7 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
         cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(v.hi, v.lo, 0.f, 0.f);
     }
     cl.sync();
-    fft_cluster<CLG, RL>(a, tw, logm, -1);
+    fft_cluster<CLG, RL, LOGN ? LOGN - 1 : 0>(a, tw, logm, -1);
     const df f = df_from(2.0 / (double)N * scale);
     int64_t *o = out + (int64_t)item * N;
     for (int i = threadIdx.x; i < MS; i += blockDim.x) {
@@ -262,10 +264,11 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
 
 // cluster per polynomial: each CTA loads the coefficients whose bit-reversed positions it holds;
 // the slot values are read from the owning CTAs
-template <int CLG, int RL>
+template <int CLG, int RL, int LOGN = 0>
 __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
-                                 const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn) {
+                                 const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
@@ -280,7 +283,7 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
         a[i] = c;
     }
     __syncthreads();
-    fft_cluster<CLG, RL>(a, tw, logm, +1);
+    fft_cluster<CLG, RL, LOGN ? LOGN - 1 : 0>(a, tw, logm, +1);
     double *o = out + (int64_t)item * M;
     const double inv = 1.0 / scale;
     const int per = M >> CLG;
@@ -294,10 +297,11 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
 
 // decrypt limb 0: m = c0 + c1 s (NTT), inverse NTT, centred, as doubles.  One CTA per
 // ciphertext, or (CL) one cluster per ciphertext with each CTA on a slice.
-template <bool CL>
+template <bool CL, int LOGN = 0>
 __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words, int nl, const uint64_t *__restrict__ sk_mont,
-                               double *coeffs, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+                               double *coeffs, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int item, off, len;
@@ -307,7 +311,7 @@ __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words
     const uint64_t *c0 = ct + item * ct_words + off, *c1 = ct + item * ct_words + (int64_t)nl * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = add_mod(c0[k], mont_mul(c1[k], sk_mont[off + k], q, qinv), q);
     __syncthreads();
-    inv_any<CL>(s, twiddles(d_tw, 0, 1, logn), q, logn);
+    inv_any<CL, LOGN>(s, twiddles(d_tw, 0, 1, logn), q, logn);
     double *o = coeffs + (int64_t)item * N + off;
     const uint64_t half = q >> 1;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
@@ -457,9 +461,9 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
     switch (fft_cluster_log(ctx->log_n, count)) {
-        case 3: launch_fft_cl<3, 1>(encode_cl_kernel<3, 1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
-        case 2: launch_fft_cl<2, 1>(encode_cl_kernel<2, 1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
-        case 1: launch_fft_cl<1, 1>(encode_cl_kernel<1, 1>, ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 3: launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<3, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 2: launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<2, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 1: launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<1, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
         default: break;
     }
     launch_k(encode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
@@ -472,9 +476,9 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
     switch (fft_cluster_log(ctx->log_n, count)) {
-        case 3: launch_fft_cl<3, 1>(decode_cl_kernel<3, 1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
-        case 2: launch_fft_cl<2, 1>(decode_cl_kernel<2, 1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
-        case 1: launch_fft_cl<1, 1>(decode_cl_kernel<1, 1>, ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 3: launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<3, 1, L.value>; }), ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 2: launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<2, 1, L.value>; }), ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 1: launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<1, 1, L.value>; }), ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
         default: break;
     }
     launch_k(decode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, coeffs, scale, tw, twist, pos, slots, ctx->log_n);
@@ -484,11 +488,11 @@ void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count
     const int64_t words = 2 * (int64_t)(level + 1) * ctx->n;
     ctx->launches++;
     if (use_cluster(ctx->log_n, count)) {
-        launch_cluster(decrypt_kernel<true>, count * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, ct, words,
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return decrypt_kernel<true, L.value>; }), count * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, ct, words,
                        level + 1, (const uint64_t *)ctx->d_sk_mont, coeffs, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
         return;
     }
-    launch_k(decrypt_kernel<false>, count, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
+    launch_k(by_logn(ctx->log_n, [](auto L) { return decrypt_kernel<false, L.value>; }), count, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, ct, words, level + 1, ctx->d_sk_mont, coeffs, ctx->d_tw, ctx->d_mc,
                                                                     ctx->log_n);
 }
 
@@ -533,8 +537,10 @@ void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, ui
 void encode_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(decrypt_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(decrypt_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(encode_cl_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(decode_cl_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    each_logn([max_bytes](auto L) {
+        cudaFuncSetAttribute(decrypt_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decrypt_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    });
 }

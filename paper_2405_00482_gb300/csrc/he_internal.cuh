@@ -14,6 +14,7 @@
 
 #include <map>
 #include <memory>
+#include <type_traits>
 #include <mutex>
 #include <vector>
 
@@ -162,6 +163,26 @@ struct he_ctx {
     std::vector<cudaEvent_t> prof_events;  // start/end pairs, recorded on `stream`
     size_t prof_used;
 };
+
+// Kernels templated on the ring size: LOGN in {12, 13, 14} (the parameter sets in use) has it at
+// compile time, 0 reads it at run time.  by_logn(logn, f) calls f with the matching
+// std::integral_constant (f returns the kernel instance); each_logn(f) calls f with every one.
+template <class F>
+inline auto by_logn(int logn, F f) {
+    switch (logn) {
+        case 12: return f(std::integral_constant<int, 12>{});
+        case 13: return f(std::integral_constant<int, 13>{});
+        case 14: return f(std::integral_constant<int, 14>{});
+        default: return f(std::integral_constant<int, 0>{});
+    }
+}
+template <class F>
+inline void each_logn(F f) {
+    f(std::integral_constant<int, 0>{});
+    f(std::integral_constant<int, 12>{});
+    f(std::integral_constant<int, 13>{});
+    f(std::integral_constant<int, 14>{});
+}
 
 // contexts of one family (a context and its forks) share tables and keys, so plaintext
 // matrices made on one serve all

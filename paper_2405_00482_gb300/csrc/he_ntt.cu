@@ -10,10 +10,12 @@
 
 namespace {
 
-template <bool CL>
+// LOGN > 0: the ring size at compile time (logn_rt == LOGN); 0: at run time
+template <bool CL, int LOGN = 0>
 __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
-                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int to_mont) {
+                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt, int to_mont) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int poly, off, len;
@@ -25,7 +27,7 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
     stage_in(s, src, len, [](uint64_t v) { return v; });
     __syncthreads();
-    fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
+    fwd_any<CL, LOGN>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
@@ -35,10 +37,11 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     }
 }
 
-template <bool CL>
+template <bool CL, int LOGN = 0>
 __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
-                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+                               const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int poly, off, len;
@@ -50,18 +53,16 @@ __global__ void ntt_inv_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     const uint64_t *src = in + g * in_gs + (int64_t)l * N + off;
     stage_in(s, src, len, [](uint64_t v) { return v; });
     __syncthreads();
-    inv_any<CL>(s, twiddles(d_tw, p, 1, logn), q, logn);
+    inv_any<CL, LOGN>(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
     const uint64_t ni = mc[p].ninv, nis = mc[p].ninv_shoup;
     for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], ni, nis, q);
 }
 
 // signed int64 coefficients of group g, reduced mod each limb's prime, then forward NTT.
-// LOGN > 0 (one-CTA form only): the ring size at compile time, logn == LOGN.
 template <bool CL, int LOGN = 0>
 __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *out, LimbMap map, const uint64_t *__restrict__ d_tw,
                                       const ModConst *__restrict__ mc, int logn_rt, int to_mont) {
-    static_assert(!CL || LOGN == 0, "cluster form has a runtime ring size");
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
@@ -76,8 +77,7 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     const uint64_t mu = mc[p].mu;
     stage_in(s, src, len, [q, mu](int64_t v) { return reduce_signed(v, q, mu); });
     __syncthreads();
-    if constexpr (LOGN > 0) ntt_fwd_smem_c<LOGN>(s, twiddles(d_tw, p, 0, logn), q);
-    else fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), q, logn);
+    fwd_any<CL, LOGN>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + ((int64_t)g * map.n + l) * N + off;
     if (to_mont) {
         const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
@@ -135,11 +135,11 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
     ctx->launches++;
     const int polys = groups * map.n;
     if (use_cluster(ctx->log_n, polys))
-        launch_cluster(ntt_fwd_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out,
-                       out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return ntt_fwd_kernel<true, L.value>; }), polys * HE_NTT_CL, cl_threads(ctx->log_n),
+                       cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
     else
-        launch_k(ntt_fwd_kernel<false>, polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw,
-                                                                                                        ctx->d_mc, ctx->log_n, to_mont);
+        launch_k(by_logn(ctx->log_n, [](auto L) { return ntt_fwd_kernel<false, L.value>; }), polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n),
+                 ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
 }
 
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map) {
@@ -147,11 +147,11 @@ void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
     ctx->launches++;
     const int polys = groups * map.n;
     if (use_cluster(ctx->log_n, polys))
-        launch_cluster(ntt_inv_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out,
-                       out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n);
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return ntt_inv_kernel<true, L.value>; }), polys * HE_NTT_CL, cl_threads(ctx->log_n),
+                       cl_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n);
     else
-        launch_k(ntt_inv_kernel<false>, polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n), ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw,
-                                                                                                        ctx->d_mc, ctx->log_n);
+        launch_k(by_logn(ctx->log_n, [](auto L) { return ntt_inv_kernel<false, L.value>; }), polys, ntt_threads(ctx->log_n), ntt_smem_bytes(ctx->log_n),
+                 ctx->stream, in, in_gs, out, out_gs, map, ctx->d_tw, ctx->d_mc, ctx->log_n);
 }
 
 void launch_from_mont(he_ctx *ctx, const uint64_t *data, uint64_t *out, int groups, const LimbMap &map) {
@@ -176,14 +176,10 @@ void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int gr
     ctx->launches++;
     const int polys = groups * map.n;
     if (use_cluster(ctx->log_n, polys))
-        launch_cluster(ntt_from_int64_kernel<true>, polys * HE_NTT_CL, cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, in, out, map,
-                       ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return ntt_from_int64_kernel<true, L.value>; }), polys * HE_NTT_CL, cl_threads(ctx->log_n),
+                       cl_smem_bytes(ctx->log_n), ctx->stream, in, out, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
     else {
-        // the ring sizes of the parameter sets in use get a transform with constant strides
-        auto k = ctx->log_n == 13 ? ntt_from_int64_kernel<false, 13>
-               : ctx->log_n == 14 ? ntt_from_int64_kernel<false, 14>
-               : ctx->log_n == 12 ? ntt_from_int64_kernel<false, 12>
-                                  : ntt_from_int64_kernel<false>;
+        auto k = by_logn(ctx->log_n, [](auto L) { return ntt_from_int64_kernel<false, L.value>; });
         // 72 registers: three CTAs fit on an SM, so in a multi-stream step the other streams'
         // kernels find room beside it (capping it at two per SM made the encoded matrix alone
         // faster, 80 against 95 us, and the benchmark step 3% slower)
@@ -199,14 +195,13 @@ void launch_to_mont(he_ctx *ctx, uint64_t *data, int groups, const LimbMap &map)
 }
 
 void ntt_set_smem_limits(int max_bytes) {
-    cudaFuncSetAttribute(ntt_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_inv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_from_int64_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_from_int64_kernel<false, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_from_int64_kernel<false, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_from_int64_kernel<false, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    // cluster forms: slice plus its twiddles (above 48 KB from N = 2^14)
-    cudaFuncSetAttribute(ntt_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(ntt_from_int64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    // one-CTA forms, and the cluster forms (slice plus its twiddles: above 48 KB from N = 2^14)
+    each_logn([max_bytes](auto L) {
+        cudaFuncSetAttribute(ntt_fwd_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(ntt_inv_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(ntt_from_int64_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(ntt_fwd_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(ntt_inv_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(ntt_from_int64_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    });
 }

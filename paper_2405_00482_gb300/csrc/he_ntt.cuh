@@ -225,6 +225,26 @@ __device__ __forceinline__ void ntt_fwd_smem_c(uint64_t *s, const ulonglong2 *__
     }
 }
 
+// ntt_inv_smem for a ring size known at compile time (LOGN >= 4)
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv_smem_c(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q) {
+    static_assert(LOGN >= 4 && LOGN <= 16, "compile-time ring size");
+    constexpr int R = HE_NTT_RADIX_LOG, NPASS = (LOGN + R - 1) / R;
+#pragma unroll
+    for (int pi = 0; pi < NPASS; ++pi) {
+        const int s0 = pi * R, nb = LOGN - s0 < R ? LOGN - s0 : R;
+        switch (nb) {
+            case 4:
+                if (s0 == 0) ntt_inv_pass<4>(s, TwFirstInv{tw_first_inv(itw, LOGN), 1 << (LOGN - 4)}, q, LOGN, s0);
+                else ntt_inv_pass<4>(s, TwGlobal{itw}, q, LOGN, s0);
+                break;
+            case 3: ntt_inv_pass<3>(s, TwGlobal{itw}, q, LOGN, s0); break;
+            case 2: ntt_inv_pass<2>(s, TwGlobal{itw}, q, LOGN, s0); break;
+            default: ntt_inv_pass<1>(s, TwGlobal{itw}, q, LOGN, s0); break;
+        }
+    }
+}
+
 // in-place inverse transform without the N^-1 factor; input canonical, output in [0, 2q)
 __device__ __forceinline__ void ntt_inv_smem(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn) {
     int s0 = 0;
@@ -360,6 +380,9 @@ __device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 *__
 // forward transform of a slice held by each CTA of the cluster; output canonical, bit-reversed
 // positions [rank N/8, (rank+1) N/8) in this CTA.  s must have cl_tw_offset_words(logn) words of
 // data followed by room for N/8 twiddle pairs, whose copy tw_prefetch<true, true> started.
+// LOGN > 0: the ring size at compile time (logn == LOGN), so the pass loop unrolls and every
+// index folds to a constant; 0: runtime
+template <int LOGN = 0>
 __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -370,8 +393,9 @@ __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *_
     ntt_cross_step<true>(s, tw, q, logn);
     cl.sync();
     const TwSliceFwd tws{stw, rank};
-    int s0 = 3;
-    while (s0 < logn) {
+#pragma unroll(LOGN > 0 ? 16 : 1)
+    for (int s0 = 3; s0 < (LOGN > 0 ? LOGN : 16); s0 += HE_NTT_CL_RADIX_LOG) {
+        if (s0 >= logn) break;
         const int nb = logn - s0 < HE_NTT_CL_RADIX_LOG ? logn - s0 : HE_NTT_CL_RADIX_LOG;
         const bool last = s0 + nb == logn;
         const int E = 1 << nb;
@@ -379,12 +403,12 @@ __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *_
             case 2: ntt_fwd_pass<2>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
             default: ntt_fwd_pass<1>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
         }
-        s0 += nb;
     }
 }
 
 // inverse transform (without N^-1) of the slices; output in [0, 2q), natural order (twiddle copy
 // started by tw_prefetch<true, false>)
+template <int LOGN = 0>
 __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -393,15 +417,15 @@ __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *_
     tw_slice_wait();
     __syncthreads();
     const TwSliceInv tws{stw, rank, 1 << (logn - 1)};
-    int s0 = 0;
-    while (s0 < logn - 3) {
+#pragma unroll(LOGN > 0 ? 16 : 1)
+    for (int s0 = 0; s0 < (LOGN > 0 ? LOGN - 3 : 16); s0 += HE_NTT_CL_RADIX_LOG) {
+        if (s0 >= logn - 3) break;
         const int nb = logn - 3 - s0 < HE_NTT_CL_RADIX_LOG ? logn - 3 - s0 : HE_NTT_CL_RADIX_LOG;
         const int E = 1 << nb;
         switch (nb) {
             case 2: ntt_inv_pass<2>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
             default: ntt_inv_pass<1>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
         }
-        s0 += nb;
     }
     cl.sync();
     ntt_cross_step<false>(s, itw, q, logn);
@@ -429,14 +453,16 @@ __device__ __forceinline__ void slice_of(int logn, int &poly, int &off, int &len
     }
 }
 
-template <bool CL>
+template <bool CL, int LOGN = 0>
 __device__ __forceinline__ void fwd_any(uint64_t *s, const ulonglong2 *tw, uint64_t q, int logn) {
-    if (CL) ntt_fwd_cluster(s, tw, q, logn);
+    if constexpr (CL) ntt_fwd_cluster<LOGN>(s, tw, q, logn);
+    else if constexpr (LOGN > 0) ntt_fwd_smem_c<LOGN>(s, tw, q);
     else ntt_fwd_smem(s, tw, q, logn);
 }
-template <bool CL>
+template <bool CL, int LOGN = 0>
 __device__ __forceinline__ void inv_any(uint64_t *s, const ulonglong2 *tw, uint64_t q, int logn) {
-    if (CL) ntt_inv_cluster(s, tw, q, logn);
+    if constexpr (CL) ntt_inv_cluster<LOGN>(s, tw, q, logn);
+    else if constexpr (LOGN > 0) ntt_inv_smem_c<LOGN>(s, tw, q);
     else ntt_inv_smem(s, tw, q, logn);
 }
 

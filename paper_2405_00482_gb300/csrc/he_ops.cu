@@ -205,19 +205,23 @@ __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const
 
 // cluster inverse NTT of the slice [off, off + len) of limb-poly src (NTT form, prime index pr);
 // canonical coefficients are then s[SIDX(k)] * N^-1 (applied by the caller with mul_shoup)
+template <int LOGN = 0>
 __device__ __forceinline__ void cl_intt_slice(uint64_t *s, const uint64_t *__restrict__ src, int pr, const uint64_t *__restrict__ d_tw,
                                               const ModConst *__restrict__ mc, int logn, int len) {
     const ulonglong2 *itw = twiddles(d_tw, pr, 1, logn);
     tw_prefetch<true, false>(s, itw, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
-    ntt_inv_cluster(s, itw, mc[pr].q, logn);
+    ntt_inv_cluster<LOGN>(s, itw, mc[pr].q, logn);
 }
 __device__ __forceinline__ uint64_t *cl_acc_slice(uint64_t *s, int logn) { return s + cl_tw_offset_words(logn) + 2 * (1 << (logn - 3)); }
 
+// LOGN > 0: the ring size at compile time (logn_rt == LOGN)
+template <int LOGN = 0>
 __global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint64_t *D, ModUpConst mu, const uint64_t *__restrict__ d_tw,
-                                      const ModConst *__restrict__ mc, int logn) {
+                                      const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int item, off, len;
@@ -235,7 +239,7 @@ __global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint6
     uint64_t *acc = cl_acc_slice(s, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) acc[k] = 0;
     for (int i = lo; i < hi; ++i) {
-        cl_intt_slice(s, c1_ntt + (int64_t)i * N + off, i, d_tw, mc, logn, len);
+        cl_intt_slice<LOGN>(s, c1_ntt + (int64_t)i * N + off, i, d_tw, mc, logn, len);
         const uint64_t qi = mc[i].q;
         for (int k = threadIdx.x; k < len; k += blockDim.x) {
             uint64_t v = mul_shoup(s[SIDX(k)], mc[i].ninv, mc[i].ninv_shoup, qi);
@@ -248,16 +252,19 @@ __global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint6
     tw_prefetch<true, true>(s, tw, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = acc[k];
     __syncthreads();
-    ntt_fwd_cluster(s, tw, t, logn);
+    ntt_fwd_cluster<LOGN>(s, tw, t, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
 }
 
 // ModDown of component c, output limb j: conversion of the K special-prime limbs (each brought
 // to coefficient form here), NTT, out = add_c + (x_j - conv) P^-1
+// LOGN > 0: the ring size at compile time (logn_rt == LOGN)
+template <int LOGN = 0>
 __global__ void moddown_cl_fused_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, const uint64_t *__restrict__ add0,
                                         const uint64_t *__restrict__ add1, uint64_t *out, const uint64_t *__restrict__ d_tw,
-                                        const ModConst *__restrict__ mc, int logn) {
+                                        const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int item, off, len;
@@ -269,7 +276,7 @@ __global__ void moddown_cl_fused_kernel(const uint64_t *__restrict__ x, int ext,
     for (int k = threadIdx.x; k < len; k += blockDim.x) acc[k] = 0;
     for (int i = 0; i < md.K; ++i) {
         const int pr = md.p_prime[i];
-        cl_intt_slice(s, x + ((int64_t)c * ext + md.nq + i) * N + off, pr, d_tw, mc, logn, len);
+        cl_intt_slice<LOGN>(s, x + ((int64_t)c * ext + md.nq + i) * N + off, pr, d_tw, mc, logn, len);
         const uint64_t pi = mc[pr].q;
         for (int k = threadIdx.x; k < len; k += blockDim.x) {
             uint64_t v = mul_shoup(s[SIDX(k)], mc[pr].ninv, mc[pr].ninv_shoup, pi);
@@ -282,7 +289,7 @@ __global__ void moddown_cl_fused_kernel(const uint64_t *__restrict__ x, int ext,
     tw_prefetch<true, true>(s, tw, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = acc[k];
     __syncthreads();
-    ntt_fwd_cluster(s, tw, q, logn);
+    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
     const uint64_t *xj = x + ((int64_t)c * ext + j) * N + off;
     uint64_t *o = out + ((int64_t)c * md.nq + j) * N + off;
     const uint64_t *ad = c == 0 ? add0 : add1;
@@ -296,9 +303,12 @@ __global__ void moddown_cl_fused_kernel(const uint64_t *__restrict__ x, int ext,
 
 // rescale of component c, output limb j < level: the last limb in coefficient form (here),
 // centred, reduced mod q_j, NTT, out = (c_j - v) q_l^-1
+// LOGN > 0: the ring size at compile time (logn_rt == LOGN)
+template <int LOGN = 0>
 __global__ void rescale_cl_fused_kernel(const uint64_t *__restrict__ ct, int level, RescaleConst rc, uint64_t *out,
-                                        const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+                                        const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int item, off, len;
@@ -306,7 +316,7 @@ __global__ void rescale_cl_fused_kernel(const uint64_t *__restrict__ ct, int lev
     const int c = item / level, j = item % level;
     const uint64_t q = mc[j].q, ql = mc[level].q;
     uint64_t *lc = cl_acc_slice(s, logn);
-    cl_intt_slice(s, ct + ((int64_t)c * (level + 1) + level) * N + off, level, d_tw, mc, logn, len);
+    cl_intt_slice<LOGN>(s, ct + ((int64_t)c * (level + 1) + level) * N + off, level, d_tw, mc, logn, len);
     for (int k = threadIdx.x; k < len; k += blockDim.x) lc[k] = mul_shoup(s[SIDX(k)], mc[level].ninv, mc[level].ninv_shoup, ql);
     __syncthreads();
     const ulonglong2 *tw = twiddles(d_tw, j, 0, logn);
@@ -318,7 +328,7 @@ __global__ void rescale_cl_fused_kernel(const uint64_t *__restrict__ ct, int lev
         s[SIDX(k)] = reduce_signed(centred, q, mc[j].mu);
     }
     __syncthreads();
-    ntt_fwd_cluster(s, tw, q, logn);
+    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
     const uint64_t *cj = ct + ((int64_t)c * (level + 1) + j) * N + off;
     uint64_t *o = out + ((int64_t)c * level + j) * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
@@ -333,10 +343,13 @@ __global__ void rescale_cl_fused_kernel(const uint64_t *__restrict__ ct, int lev
 // Each step is exact arithmetic mod a prime, so the output is the canonical residue the two
 // separate stages give, bit for bit, after K + 2 cluster transforms per item in one launch
 // instead of K + 1 and 2 in two.
+// LOGN > 0: the ring size at compile time (logn_rt == LOGN)
+template <int LOGN = 0>
 __global__ void moddown_rescale_cl_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, RescaleConst rc,
                                           const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *out,
-                                          const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn) {
+                                          const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     int item, off, len;
@@ -349,7 +362,7 @@ __global__ void moddown_rescale_cl_kernel(const uint64_t *__restrict__ x, int ex
     for (int k = threadIdx.x; k < len; k += blockDim.x) acc_j[k] = acc_l[k] = 0;
     for (int i = 0; i < md.K; ++i) {  // conv_j and conv_L from the P limbs
         const int pr = md.p_prime[i];
-        cl_intt_slice(s, x + ((int64_t)c * ext + md.nq + i) * N + off, pr, d_tw, mc, logn, len);
+        cl_intt_slice<LOGN>(s, x + ((int64_t)c * ext + md.nq + i) * N + off, pr, d_tw, mc, logn, len);
         const uint64_t pi = mc[pr].q;
         for (int k = threadIdx.x; k < len; k += blockDim.x) {
             uint64_t v = mul_shoup(s[SIDX(k)], mc[pr].ninv, mc[pr].ninv_shoup, pi);
@@ -371,7 +384,7 @@ __global__ void moddown_rescale_cl_kernel(const uint64_t *__restrict__ x, int ex
             s[SIDX(k)] = v;
         }
         __syncthreads();
-        ntt_inv_cluster(s, itw, ql, logn);
+        ntt_inv_cluster<LOGN>(s, itw, ql, logn);
         for (int k = threadIdx.x; k < len; k += blockDim.x) {
             const uint64_t v = mul_shoup(s[SIDX(k)], mc[pl].ninv, mc[pl].ninv_shoup, ql);
             acc_l[k] = sub_mod(v, mul_shoup(acc_l[k], md.pinv[L], md.pinv_shoup[L], ql), ql);
@@ -387,7 +400,7 @@ __global__ void moddown_rescale_cl_kernel(const uint64_t *__restrict__ x, int ex
         s[SIDX(k)] = add_mod(mul_shoup(acc_j[k], md.pinv[j], md.pinv_shoup[j], q), reduce_signed(centred, q, mc[pj].mu), q);
     }
     __syncthreads();
-    ntt_fwd_cluster(s, tw, q, logn);
+    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
     const uint64_t *xj = x + ((int64_t)c * ext + j) * N + off;
     const uint64_t *aj = ad ? ad + (int64_t)j * N + off : nullptr;
     uint64_t *o = out + ((int64_t)c * L + j) * N + off;
@@ -1160,7 +1173,7 @@ void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, u
     const int items = mu.ndig * mu.ext;
     ctx->launches++;
     if (use_cluster(ctx->log_n, items)) {  // the inverse NTT of c1 happens inside
-        launch_cluster(modup_cl_fused_kernel, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream, c1_ntt,
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return modup_cl_fused_kernel<L.value>; }), items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream, c1_ntt,
                        D, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
         return;
     }
@@ -1189,7 +1202,7 @@ void launch_moddown(he_ctx *ctx, const uint64_t *x, int level, int ncomp, const 
     const int items = ncomp * md.nq;
     ctx->launches++;
     if (use_cluster(ctx->log_n, items)) {  // the inverse NTT of the P limbs happens inside
-        launch_cluster(moddown_cl_fused_kernel, items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream, x,
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return moddown_cl_fused_kernel<L.value>; }), items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream, x,
                        ext, md, add0, add1, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
         return;
     }
@@ -1225,7 +1238,7 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
     const RescaleConst rc = make_rescale_const(ctx, level);
     ctx->launches++;
     if (use_cluster(ctx->log_n, 2 * level)) {  // the inverse NTT of the last limb happens inside
-        launch_cluster(rescale_cl_fused_kernel, 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream,
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return rescale_cl_fused_kernel<L.value>; }), 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream,
                        ct, level, rc, out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
         return;
     }
@@ -1244,7 +1257,7 @@ void launch_moddown_rescale(he_ctx *ctx, const uint64_t *x, int level, const uin
     const ModDownConst &md = ctx->moddown[level];
     const RescaleConst rc = make_rescale_const(ctx, level);
     ctx->launches++;
-    launch_cluster(moddown_rescale_cl_kernel, 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
+    launch_cluster(by_logn(ctx->log_n, [](auto L) { return moddown_rescale_cl_kernel<L.value>; }), 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
                    cl_fused_smem_bytes(ctx->log_n) + ((size_t)8 << (ctx->log_n - 3)), ctx->stream, x, level + 1 + ctx->K, md, rc, add0, add1,
                    out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
 }
@@ -1422,10 +1435,10 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(modup_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(moddown_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(modup_cl_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(moddown_cl_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(rescale_cl_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    cudaFuncSetAttribute(moddown_rescale_cl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(modup_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
+    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
+    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(rescale_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
+    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     for (int v = 0; v < kMMVariants; ++v)
         for (int nd = 0; nd <= 3; ++nd)
             mm_dispatch(v, nd, []<int NDIG, int VEC, int G, int S, bool GA>() {
