@@ -5,9 +5,11 @@ r 1024 ~ U[-1,1], w 256 ~ N(0, 0.1).  One step is the whole hot path for the two
 products of a VFL linear-model iteration, both as single plain MatMult calls:
   gradient X^T [[r]] (m=256, n=1024, m'=64: 63 hoisted rotations) and
   forward  X [[w]]   (m=1024, n=256, m'=64),
-each = encode the diagonal plaintexts of the matrix, encode + encrypt the replicated
-vector, MatMult (ModUp, 63 key-switch / multiply-accumulate steps, ModDown, rescale),
-decrypt + decode, lazy rotate-and-sum.  Galois keys are made once, before timing.
+each = encode the diagonal plaintexts of the matrix (X^T read from X itself), encode +
+encrypt the replicated vector, MatMult (ModUp, 63 key-switch / multiply-accumulate steps,
+ModDown, rescale), decrypt + decode, lazy rotate-and-sum.  Galois keys are made once, before
+timing.  The two products and their matrix encodings run on four streams (a context and three
+forks) and the step is replayed as one captured CUDA graph (--no-graph: eager calls).
 value = MatMults per second over all ranks (2 per step per rank).
 
 --impl reference times the CPU oracle (the only reference implementation: the paper
@@ -122,7 +124,7 @@ def run_gpu(args):
     plan_f = he.Plan(1024, 256, P.slots)
     steps = sorted(set(range(1, plan_g.m_prime)) | set(range(1, plan_f.m_prime)))
     ctx.keygen(steps)
-    dXT, dX = torch.from_numpy(XT).to(dev), torch.from_numpy(X).to(dev)
+    dX = torch.from_numpy(X).to(dev)  # the gradient product encodes X^T from X (transposed=True)
     dr, dw = torch.from_numpy(r).to(dev), torch.from_numpy(w).to(dev)
     out_g = [ctx.new_ct(level - 1)]
     out_f = [ctx.new_ct(level - 1)]
@@ -133,7 +135,7 @@ def run_gpu(args):
     flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     # device buffers reused by every step: encoded matrices, vector plaintexts, ciphertexts
-    pm_g = ctx.encode_matrix(plan_g, dXT, level)
+    pm_g = ctx.encode_matrix(plan_g, dX, level, transposed=True)
     pm_f = ctx.encode_matrix(plan_f, dX, level)
     if args.loop_variant >= 0:
         pm_g.set_variant(args.loop_variant)
@@ -157,13 +159,13 @@ def run_gpu(args):
             pm_f.set_variant(args.loop_variant)
     main = torch.cuda.current_stream()
 
-    def product(c, cm, plan, pm, Md, vd, pt, ct, nonce, out, slots, res):
+    def product(c, cm, plan, pm, Md, trans, vd, pt, ct, nonce, out, slots, res):
         if cm is not c:
             cm.stream.wait_stream(c.stream)
             with torch.cuda.stream(cm.stream):
-                cm.encode_matrix(plan, Md, level, out=pm)
+                cm.encode_matrix(plan, Md, level, out=pm, transposed=trans)
         else:
-            c.encode_matrix(plan, Md, level, out=pm)
+            c.encode_matrix(plan, Md, level, out=pm, transposed=trans)
         c.encode_vector(plan, vd, P.scale, level, outs=[pt])
         c.encrypt(pt, nonce, out=ct)
         if cm is not c:
@@ -176,12 +178,12 @@ def run_gpu(args):
     # graph never encrypts twice under one nonce
     nonce = torch.tensor([0, 1], dtype=torch.int64, device=dev)
 
-    def step(XTd, Xd, rd, wd):
+    def step(Xd, rd, wd):
         if two:
             fctx.stream.wait_stream(main)  # inputs copied / produced on the main stream
-        product(ctx, menc[0], plan_g, pm_g, XTd, rd, pt_r, ct_r, nonce[0:1], out_g, slots_g, res_g)
+        product(ctx, menc[0], plan_g, pm_g, Xd, True, rd, pt_r, ct_r, nonce[0:1], out_g, slots_g, res_g)
         with torch.cuda.stream(fctx.stream):
-            product(fctx, menc[1], plan_f, pm_f, Xd, wd, pt_w, ct_w, nonce[1:2], out_f, slots_f, res_f)
+            product(fctx, menc[1], plan_f, pm_f, Xd, False, wd, pt_w, ct_w, nonce[1:2], out_f, slots_f, res_f)
         if two:
             main.wait_stream(fctx.stream)
         nonce.add_(2)
@@ -194,10 +196,10 @@ def run_gpu(args):
         return e
 
     # correctness of the timed configuration against the FP64 product
-    step(dXT, dX, dr, dw)
+    step(dX, dr, dw)
     err = check("eager step")
     for i in range(args.warmup):
-        step(dXT, dX, dr, dw)
+        step(dX, dr, dw)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -220,14 +222,14 @@ def run_gpu(args):
     ctx.profile(True)
     with ClockSampler(local) as clk_eager:
         torch.cuda.synchronize()
-        times_eager = timed_steps(lambda: step(dXT, dX, dr, dw))
+        times_eager = timed_steps(lambda: step(dX, dr, dw))
     loop_ms, loop_launches = ctx.profile_read()
     ctx.profile(False)
     launches_eager = ctx.launch_count() + sum(f.launch_count() for f in forks) - launches0
     step_loop_ms = loop_ms / max(loop_launches, 1)
 
     # graph: the same calls captured once (he.Graph) and replayed with one launch per step
-    graph = he.Graph(ctx, lambda: step(dXT, dX, dr, dw), forks=forks)
+    graph = he.Graph(ctx, lambda: step(dX, dr, dw), forks=forks)
     for i in range(args.warmup):
         graph.replay()
     res_g.zero_()
@@ -266,19 +268,18 @@ def run_gpu(args):
 
     # end to end through the API from pinned host buffers, result read back every step: the
     # inputs are copied into the buffers the graph reads, the graph replayed, the results read
-    hXT, hX = torch.from_numpy(XT).pin_memory(), torch.from_numpy(X).pin_memory()
+    hX = torch.from_numpy(X).pin_memory()
     hr, hw = torch.from_numpy(r).pin_memory(), torch.from_numpy(w).pin_memory()
     hres_g = torch.empty(256, dtype=torch.float64).pin_memory()
     hres_f = torch.empty(1024, dtype=torch.float64).pin_memory()
 
     def e2e_step():
         if use_graph:
-            for d, h in ((dXT, hXT), (dX, hX), (dr, hr), (dw, hw)):
+            for d, h in ((dX, hX), (dr, hr), (dw, hw)):
                 d.copy_(h, non_blocking=True)
             graph.replay()
         else:
-            step(hXT.to(dev, non_blocking=True), hX.to(dev, non_blocking=True), hr.to(dev, non_blocking=True),
-                 hw.to(dev, non_blocking=True))
+            step(hX.to(dev, non_blocking=True), hr.to(dev, non_blocking=True), hw.to(dev, non_blocking=True))
         hres_g.copy_(res_g, non_blocking=True)
         hres_f.copy_(res_f, non_blocking=True)
 
@@ -293,7 +294,7 @@ def run_gpu(args):
     if np.abs(hres_g.numpy() - XT @ r).max() > 1e-4 or np.abs(hres_f.numpy() - X @ w).max() > 1e-4:
         raise RuntimeError("end-to-end result above tolerance")
     e2e_s = max_over_ranks(sum(e2e), world, dev)
-    h2d = (XT.nbytes + X.nbytes + r.nbytes + w.nbytes)
+    h2d = (X.nbytes + r.nbytes + w.nbytes)
     d2h = 256 * 8 + 1024 * 8
 
     # dominant kernel roofline: key-switch / multiply-accumulate loop

@@ -174,6 +174,11 @@ int he_encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int leve
 /* Re-encode a new matrix X (same shape, device) into an existing encoded matrix, in place:
  * no allocation, asynchronous on the stream (a VFL iteration's next batch). */
 int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X);
+/* he_encode_matrix / he_ptmat_encode of the matrix X = Xt^T given its transpose Xt (device,
+ * row-major n x m): the same plaintexts, bit for bit, without a transposed copy (a VFL party
+ * holding its features X_A multiplies by X_A^T for the gradient and by X_A for the forward pass). */
+int he_encode_matrix_transposed(he_ctx *ctx, const he_plan *plan, const double *Xt, int level, he_ptmat **out);
+int he_ptmat_encode_transposed(he_ctx *ctx, he_ptmat *pm, const double *Xt);
 /* Same object from integer plaintexts already encoded elsewhere: coeffs (device) holds
  * [R][C][m'][level+1+n_p][N] canonical residues in coefficient form over q_0..q_level, p_*. */
 int he_ptmat_import(he_ctx *ctx, const he_plan *plan, const uint64_t *coeffs, int level, double scale, he_ptmat **out);

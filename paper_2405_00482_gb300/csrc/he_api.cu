@@ -774,7 +774,7 @@ static int ptmat_alloc(he_ctx *ctx, const he_plan *plan, int level, double scale
     return HE_OK;
 }
 
-int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X) {
+static int ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X, int trans) {
     if (!ctx || !pm || !X || !same_family(pm->ctx, ctx)) return HE_EINVAL;
     const he_plan &p = pm->plan;
     const size_t N = ctx->n, count = (size_t)p.row_blocks * p.col_blocks * p.m_prime;
@@ -782,23 +782,33 @@ int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X) {
     if (!s) return HE_ENOMEM;
     double *slots = reinterpret_cast<double *>(s);
     int64_t *coef = reinterpret_cast<int64_t *>(s + count * (N / 2));
-    launch_layout_matrix(ctx, p, X, slots);
+    launch_layout_matrix(ctx, p, X, slots, trans);
     launch_encode(ctx, slots, N / 2, N / 2, (int)count, pm->scale, coef);
     launch_ntt_from_int64(ctx, coef, pm->data, (int)count, qpmap(ctx, pm->level), 1);
     return last_launch();
 }
 
-int he_encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int level, he_ptmat **out) {
+int he_ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X) { return ptmat_encode(ctx, pm, X, 0); }
+int he_ptmat_encode_transposed(he_ctx *ctx, he_ptmat *pm, const double *Xt) { return ptmat_encode(ctx, pm, Xt, 1); }
+
+static int encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int level, int trans, he_ptmat **out) {
     if (!ctx || !X) return HE_EINVAL;
     if (level < 1 || level >= ctx->L) return HE_ELEVEL;
     int rc = ptmat_alloc(ctx, plan, level, (double)ctx->primes[level], out);
     if (rc != HE_OK) return rc;
-    rc = he_ptmat_encode(ctx, *out, X);
+    rc = ptmat_encode(ctx, *out, X, trans);
     if (rc != HE_OK) {
         he_ptmat_free(*out);
         *out = nullptr;
     }
     return rc;
+}
+
+int he_encode_matrix(he_ctx *ctx, const he_plan *plan, const double *X, int level, he_ptmat **out) {
+    return encode_matrix(ctx, plan, X, level, 0, out);
+}
+int he_encode_matrix_transposed(he_ctx *ctx, const he_plan *plan, const double *Xt, int level, he_ptmat **out) {
+    return encode_matrix(ctx, plan, Xt, level, 1, out);
 }
 
 int he_ptmat_export(he_ctx *ctx, const he_ptmat *pm, uint64_t *coeffs_out) {

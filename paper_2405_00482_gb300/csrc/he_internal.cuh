@@ -378,7 +378,7 @@ void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out
 void launch_sample_ternary(he_ctx *ctx, int64_t *out);
 void launch_encrypt_combine(he_ctx *ctx, const uint64_t *pt, const uint64_t *a, const uint64_t *e, int level, uint64_t *ct);
 void launch_keygen_combine(he_ctx *ctx, const uint64_t *a, const uint64_t *e, uint32_t g, int digit, uint64_t *key_d);
-void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots);
+void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots, int trans = 0);
 void launch_layout_vector(he_ctx *ctx, const he_plan &p, const double *y, double *slots);
 void launch_lazy_ras(he_ctx *ctx, const he_plan &p, const double *slots, const double *mask, double *y);
 void launch_ras_gather(he_ctx *ctx, const he_plan &p, const double *slots, double *y);

@@ -1075,7 +1075,8 @@ namespace {
 // counts), so the index arithmetic below is shifts and masks: log2 of such a size.
 __device__ __forceinline__ int lg2p(int64_t v) { return __ffsll(v) - 1; }
 
-__global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, double *out, int64_t total) {
+// trans: X holds the n x m transpose of the matrix (entry (row, col) at X[col m + row])
+__global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, double *out, int64_t total, int trans) {
     HE_GRID_DEP();
     const int ls = lg2p(p.slots), lm = lg2p(p.m_prime), lc = lg2p(p.col_blocks), lnb = lg2p(p.nb), lmb = lg2p(p.mb);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
@@ -1087,7 +1088,7 @@ __global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, do
         const int64_t b = s >> lnb, jj = s & (p.nb - 1);
         const int64_t row = (r << lmb) + (b << lm) + (jj & (p.m_prime - 1));
         const int64_t col = (c << lnb) + ((i + jj) & (p.nb - 1));
-        out[idx] = (row < p.m && col < p.n) ? X[row * p.n + col] : 0.0;
+        out[idx] = (row < p.m && col < p.n) ? X[trans ? col * p.m + row : row * p.n + col] : 0.0;
     }
 }
 
@@ -1324,12 +1325,12 @@ void launch_matmult_loop_with_tables(he_ctx *ctx, const he_ptmat *pm, int r, int
                       accumulate);
 }
 
-void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots) {
+void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots, int trans) {
     int64_t total = p.row_blocks * p.col_blocks * p.m_prime * p.slots;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 65535 * 8) blocks = 65535 * 8;
     ctx->launches++;
-    launch_k(layout_matrix_kernel, blocks, 256, 0, ctx->stream, p, X, slots, total);
+    launch_k(layout_matrix_kernel, blocks, 256, 0, ctx->stream, p, X, slots, total, trans);
 }
 
 void launch_layout_vector(he_ctx *ctx, const he_plan &p, const double *y, double *slots) {

@@ -70,6 +70,8 @@ _SIGS = {
     "he_plan_free": (None, [_vp]),
     "he_encode_matrix": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_ptmat_encode": (ctypes.c_int, [_vp, _vp, _vp]),
+    "he_encode_matrix_transposed": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "he_ptmat_encode_transposed": (ctypes.c_int, [_vp, _vp, _vp]),
     "he_ct_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int]),
     "he_pt_bytes": (ctypes.c_size_t, [_vp, ctypes.c_int]),
     "he_ptmat_export": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -547,13 +549,21 @@ class Context:
         return outs
 
     # ---- MatMult ----
-    def encode_matrix(self, plan: Plan, X: torch.Tensor, level: int, out: PtMatrix | None = None) -> PtMatrix:
+    def encode_matrix(self, plan: Plan, X: torch.Tensor, level: int, out: PtMatrix | None = None,
+                      transposed: bool = False) -> PtMatrix:
+        """Diagonal plaintexts of X (plan.m x plan.n); transposed=True: X given as its n x m
+        transpose (no transposed copy made)."""
         X = _dev(X, torch.float64)
+        want = (plan.n, plan.m) if transposed else (plan.m, plan.n)
+        if X.numel() != plan.m * plan.n or (X.dim() == 2 and tuple(X.shape) != want):
+            raise ValueError(f"matrix of shape {want} expected, got {tuple(X.shape)}")
         if out is not None:
-            _check(_lib().he_ptmat_encode(self.handle, out.handle, X.data_ptr()), "he_ptmat_encode")
+            fn = "he_ptmat_encode_transposed" if transposed else "he_ptmat_encode"
+            _check(getattr(_lib(), fn)(self.handle, out.handle, X.data_ptr()), fn)
             return out
         h = _vp()
-        _check(_lib().he_encode_matrix(self.handle, plan.handle, X.data_ptr(), level, ctypes.byref(h)), "he_encode_matrix")
+        fn = "he_encode_matrix_transposed" if transposed else "he_encode_matrix"
+        _check(getattr(_lib(), fn)(self.handle, plan.handle, X.data_ptr(), level, ctypes.byref(h)), fn)
         return PtMatrix(self, h, plan, level)
 
     def ptmat_import(self, plan: Plan, coeffs: torch.Tensor, level: int, scale: float) -> PtMatrix:

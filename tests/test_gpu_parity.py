@@ -317,3 +317,26 @@ def test_buffer_sizes(he):
         assert ctx.ct_bytes(level) == ctx.new_ct(level).data.numel() * 8 == 2 * (level + 1) * o.n * 8
         assert ctx.pt_bytes(level) == ctx.new_pt(level).data.numel() * 8
     assert ctx.ct_bytes(o.L) == 0 and ctx.pt_bytes(-1) == 0
+
+
+@pytest.mark.parametrize("name,m,n", [("n32", 4, 4), ("n32", 3, 5), ("n32", 1, 8), ("n8192", 256, 1024), ("n8192", 1024, 256),
+                                      ("n8192", 300, 5000), ("n8192", 5000, 300)])
+def test_encode_matrix_transposed_bit_exact(he, name, m, n):
+    """The matrix given as its transpose (he_encode_matrix_transposed, he_ptmat_encode_transposed)
+    encodes to the same plaintexts, bit for bit, as the matrix itself."""
+    import torch
+
+    ctx, o = pair(he, name)
+    rng = np.random.default_rng(7 * m + n)
+    X = rng.normal(size=(m, n))
+    level = o.L - 1
+    plan = he.Plan(m, n, o.slots)
+    want = he.as_u64(ctx.encode_matrix(plan, torch.from_numpy(X).cuda(), level).export())
+    Xt = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+    pm = ctx.encode_matrix(plan, Xt, level, transposed=True)
+    assert np.array_equal(he.as_u64(pm.export()), want)
+    ctx.encode_matrix(plan, torch.zeros_like(Xt), level, out=pm, transposed=True)
+    ctx.encode_matrix(plan, Xt, level, out=pm, transposed=True)  # in place
+    assert np.array_equal(he.as_u64(pm.export()), want)
+    with pytest.raises(ValueError):
+        ctx.encode_matrix(plan, Xt, level) if m != n else ctx.encode_matrix(plan, Xt[:, :1], level)
