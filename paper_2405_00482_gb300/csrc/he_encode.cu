@@ -63,9 +63,22 @@ __device__ __forceinline__ void cmul(float4 v, float4 w, float4 &out) {
 // there (the same operations on the same values as one stage at a time, so the result does not
 // depend on the grouping) and writes them back, so a 4096-point transform makes 4 trips through
 // shared memory and block barriers instead of 12, with 4 independent butterflies per stage.
-template <int NB>
-__device__ __forceinline__ void fft_pass(float4 *a, const float4 *__restrict__ tw, int logm, int s0, int sign, int set0 = 0, int set1 = -1,
-                                         int off = 0) {
+// Twiddle of a butterfly at stage lg whose element sits at pos = x mod 2^(lg-1): tw[pos 2^(log M - lg)].
+// TwFftGlobal reads the table; TwFftLocal a shared-memory copy of the entries the slice-local
+// stages of the cluster form read, stw[j] = tw[j 2^(log M - lg_ms)] for j < 2^(lg_ms - 1).
+struct TwFftGlobal {
+    const float4 *tw;
+    int logm;
+    __device__ __forceinline__ float4 at(int pos, int lg) const { return tw[pos << (logm - lg)]; }
+};
+struct TwFftLocal {
+    const float4 *stw;
+    int lg_ms;
+    __device__ __forceinline__ float4 at(int pos, int lg) const { return stw[pos << (lg_ms - lg)]; }
+};
+
+template <int NB, class TWA = TwFftGlobal>
+__device__ __forceinline__ void fft_pass(float4 *a, TWA tw, int logm, int s0, int sign, int set0 = 0, int set1 = -1, int off = 0) {
     constexpr int E = 1 << NB;
     if (set1 < 0) set1 = 1 << (logm - NB);
     a -= off;  // element x at a[x] (a slice holds [off, off + its length))
@@ -82,7 +95,7 @@ __device__ __forceinline__ void fft_pass(float4 *a, const float4 *__restrict__ t
             for (int k = 0; k < E; ++k) {
                 if ((k & (2 * h - 1)) < h) {
                     const int pos = (base + (k << s0)) & ((1 << (lg - 1)) - 1);
-                    float4 w = tw[pos << (logm - lg)];
+                    float4 w = tw.at(pos, lg);
                     if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
                     float4 v;
                     cmul(r[k + h], w, v);
@@ -105,9 +118,9 @@ __device__ void fft_smem(float4 *a, const float4 *__restrict__ tw, int logm, int
     while (s0 < logm) {
         const int nb = logm - s0 < 3 ? logm - s0 : 3;
         switch (nb) {
-            case 3: fft_pass<3>(a, tw, logm, s0, sign); break;
-            case 2: fft_pass<2>(a, tw, logm, s0, sign); break;
-            default: fft_pass<1>(a, tw, logm, s0, sign); break;
+            case 3: fft_pass<3>(a, TwFftGlobal{tw, logm}, logm, s0, sign); break;
+            case 2: fft_pass<2>(a, TwFftGlobal{tw, logm}, logm, s0, sign); break;
+            default: fft_pass<1>(a, TwFftGlobal{tw, logm}, logm, s0, sign); break;
         }
         s0 += nb;
     }
@@ -177,6 +190,20 @@ __global__ void decode_kernel(const double *__restrict__ coeffs, double scale, c
 // RL: local passes of radix 2^RL (MS >> RL threads).  RL = 1 throughout: on GB300 radix 4 and 8
 // (and 2 CTAs per transform with radix 8, or one CTA) were slower even for the 64 transforms of
 // an encoded matrix, where the launch is throughput- rather than latency-bound
+// The slice-local stages read their twiddles from a shared-memory copy placed right after the
+// slice (a + MS), which the kernel starts with fft_tw_issue before it loads its data; the copy is
+// the same for every CTA (those stages' twiddles do not depend on the slice).
+template <int CLG>
+__device__ __forceinline__ void fft_tw_issue(float4 *a, const float4 *__restrict__ tw, int logm) {
+    const int MS = 1 << (logm - CLG);
+    float4 *stw = a + MS;
+    for (int j = threadIdx.x; j < MS / 2; j += blockDim.x) {
+        const unsigned sa = (unsigned)__cvta_generic_to_shared(stw + j);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(tw + (j << CLG)) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 // LOGM > 0: log M at compile time (logm == LOGM), so the pass loop unrolls and indices fold
 template <int CLG, int RL, int LOGM = 0>
 __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict__ tw, int logm, int sign) {
@@ -184,15 +211,18 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the twiddle copy of fft_tw_issue
+    __syncthreads();
+    const TwFftLocal tloc{a + MS, lg_ms};
 #pragma unroll(LOGM > 0 ? 16 : 1)
     for (int s0 = 0; s0 < (LOGM > 0 ? LOGM - CLG : 16); s0 += RL) {
         if (s0 >= lg_ms) break;
         const int nb = lg_ms - s0 < RL ? lg_ms - s0 : RL;
         const int E = 1 << nb;
         switch (nb) {
-            case 3: fft_pass<3>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
-            case 2: fft_pass<2>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
-            default: fft_pass<1>(a, tw, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+            case 3: fft_pass<3>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+            case 2: fft_pass<2>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+            default: fft_pass<1>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
         }
     }
     cl.sync();
@@ -243,6 +273,7 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
     const double *z = slots + (int64_t)item * stride;
     const int per = M >> CLG;
+    fft_tw_issue<CLG>(a, tw, logm);
     cl.sync();  // every CTA of the cluster has started before its shared memory is written
     for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
         const int bt = __brev(slot_pos[j]) >> (32 - logm);
@@ -274,6 +305,7 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
     const double *m = coeffs + (int64_t)item * N;
+    fft_tw_issue<CLG>(a, tw, logm);
     for (int i = threadIdx.x; i < MS; i += blockDim.x) {
         const int k = __brev(off + i) >> (32 - logm);
         const float4 w = twist[k];
@@ -451,7 +483,7 @@ static void launch_fft_cl(void (*kernel)(KArgs...), he_ctx *ctx, int count, Args
     const int MS = ctx->n / 2 >> CLG;
     int threads = MS >> RL;
     threads = threads < 32 ? 32 : (threads > 512 ? 512 : threads);
-    launch_cluster_n(kernel, count << CLG, threads, (size_t)MS * sizeof(float4), ctx->stream, 1 << CLG, args...);
+    launch_cluster_n(kernel, count << CLG, threads, (size_t)MS * sizeof(float4) * 3 / 2, ctx->stream, 1 << CLG, args...);  // slice + twiddles
 }
 
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs) {
@@ -540,7 +572,12 @@ void encode_set_smem_limits(int max_bytes) {
     each_logn([max_bytes](auto L) {
         cudaFuncSetAttribute(decrypt_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decrypt_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        // cluster FFTs: the slice and the local stages' twiddles (1.5 MS float4)
         cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     });
 }
