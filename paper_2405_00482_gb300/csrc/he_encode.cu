@@ -293,6 +293,58 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
     }
 }
 
+// Two real inputs per transform: the slot vectors x (item 2p) and y (item 2p+1) go in as the real
+// and imaginary parts of one sequence, so a cluster runs one length-M FFT for two plaintexts.
+// The DFT is linear and maps a real sequence to a Hermitian one, so with Z = DFT(x + i y):
+// DFT(x)[k] = (Z[k] + conj Z[-k]) / 2 and DFT(y)[k] = -i (Z[k] - conj Z[-k]) / 2 (indices mod M);
+// each CTA reads Z[-k] of its slice from the CTA holding it.  Then the twist and rounding of
+// encode_cl_kernel for each (the 1/2 folded into the power-of-two factor).  An odd last item
+// pairs with zeros and writes one plaintext.
+template <int CLG, int RL, int LOGN = 0>
+__global__ void encode_pair_cl_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, int count, double scale,
+                                      const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
+                                      int64_t *out, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    extern __shared__ float4 a[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), pair = blockIdx.x >> CLG;
+    const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
+    const int ix = 2 * pair, iy = 2 * pair + 1;
+    const bool has_y = iy < count;
+    const double *zx = slots + (int64_t)ix * stride, *zy = slots + (int64_t)iy * stride;
+    const int per = M >> CLG;
+    fft_tw_issue<CLG>(a, tw, logm);
+    cl.sync();  // every CTA of the cluster has started before its shared memory is written
+    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
+        const int bt = __brev(slot_pos[j]) >> (32 - logm);
+        const df vx = df_from(j < n_slots ? zx[j] : 0.0), vy = df_from(has_y && j < n_slots ? zy[j] : 0.0);
+        cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(vx.hi, vx.lo, vy.hi, vy.lo);
+    }
+    cl.sync();
+    fft_cluster<CLG, RL, LOGN ? LOGN - 1 : 0>(a, tw, logm, -1);  // ends with a cluster barrier
+    const df f = df_from(1.0 / (double)N * scale);  // 2/N times the 1/2 of the separation
+    int64_t *ox = out + (int64_t)ix * N, *oy = out + (int64_t)iy * N;
+    for (int i = threadIdx.x; i < MS; i += blockDim.x) {
+        const int k = off + i, km = (M - k) & (M - 1);
+        const float4 zk = a[i], zm = cl.map_shared_rank(a, km >> lg_ms)[km & (MS - 1)];
+        const df zr{zk.x, zk.y}, zi{zk.z, zk.w}, mr{zm.x, zm.y}, mi{zm.z, zm.w};
+        // 2 DFT(x)[k] = (zr + mr) + i (zi - mi);  2 DFT(y)[k] = (zi + mi) - i (zr - mr)
+        const df xr = df_add(zr, mr), xi = df_add(zi, df_neg(mi));
+        const df yr = df_add(zi, mi), yi = df_add(mr, df_neg(zr));
+        float4 c;
+        cmul(make_float4(xr.hi, xr.lo, xi.hi, xi.lo), twist[k], c);
+        ox[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
+        ox[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
+        if (has_y) {
+            cmul(make_float4(yr.hi, yr.lo, yi.hi, yi.lo), twist[k], c);
+            oy[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
+            oy[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
+        }
+    }
+    cl.sync();  // the other CTAs read this one's shared memory until here
+}
+
 // cluster per polynomial: each CTA loads the coefficients whose bit-reversed positions it holds;
 // the slot values are read from the owning CTAs
 template <int CLG, int RL, int LOGN = 0>
@@ -492,6 +544,24 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
     const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
+    if (count >= 2 && ctx->log_n >= 10) {  // two real inputs per complex transform
+        const int pairs = (count + 1) / 2;
+        switch (fft_cluster_log(ctx->log_n, pairs)) {
+            case 3:
+                launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<3, 1, L.value>; }), ctx, pairs, slots, n_slots,
+                                    stride, count, scale, tw, twist, pos, coeffs, ctx->log_n);
+                return;
+            case 2:
+                launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<2, 1, L.value>; }), ctx, pairs, slots, n_slots,
+                                    stride, count, scale, tw, twist, pos, coeffs, ctx->log_n);
+                return;
+            case 1:
+                launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<1, 1, L.value>; }), ctx, pairs, slots, n_slots,
+                                    stride, count, scale, tw, twist, pos, coeffs, ctx->log_n);
+                return;
+            default: break;
+        }
+    }
     switch (fft_cluster_log(ctx->log_n, count)) {
         case 3: launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<3, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
         case 2: launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<2, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
@@ -578,6 +648,9 @@ void encode_set_smem_limits(int max_bytes) {
         cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     });
 }
