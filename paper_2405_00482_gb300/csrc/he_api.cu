@@ -116,6 +116,8 @@ ModConst make_modconst(uint64_t q, int log_n) {
     m.ninv = hinv((1ull << log_n) % q, q);
     m.ninv_shoup = shoup(m.ninv, q);
     m.mu = (uint64_t)((((u128)1) << 64) / q);
+    m.r1 = r1;
+    m.r1_shoup = shoup(r1, q);
     return m;
 }
 

@@ -92,6 +92,7 @@ struct ModConst {
     uint64_t r2;      // 2^128 mod q (to Montgomery form: redc(x * r2))
     uint64_t ninv, ninv_shoup;  // N^-1 mod q
     uint64_t mu;      // floor(2^64 / q), for reduce_barrett
+    uint64_t r1, r1_shoup;  // 2^64 mod q with its Shoup quotient: x -> x 2^64 mod q (Montgomery form)
 };
 
 // index map from a batch's limb position to the context's prime index

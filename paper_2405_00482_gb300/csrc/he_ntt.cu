@@ -29,9 +29,9 @@ __global__ void ntt_fwd_kernel(const uint64_t *__restrict__ in, int64_t in_gs, u
     __syncthreads();
     fwd_any<CL, LOGN>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
-    if (to_mont) {
-        const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
-        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
+    if (to_mont) {  // x 2^64 mod q: one Shoup product by the constant 2^64 mod q
+        const uint64_t r1 = mc[p].r1, r1s = mc[p].r1_shoup;
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], r1, r1s, q);
     } else {
         for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
     }
@@ -79,9 +79,9 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     __syncthreads();
     fwd_any<CL, LOGN>(s, twiddles(d_tw, p, 0, logn), q, logn);
     uint64_t *dst = out + ((int64_t)g * map.n + l) * N + off;
-    if (to_mont) {
-        const uint64_t r2 = mc[p].r2, qinv = mc[p].qinv;
-        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mont_mul(s[SIDX(k)], r2, q, qinv);
+    if (to_mont) {  // x 2^64 mod q: one Shoup product by the constant 2^64 mod q
+        const uint64_t r1 = mc[p].r1, r1s = mc[p].r1_shoup;
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], r1, r1s, q);
     } else {
         for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
     }
