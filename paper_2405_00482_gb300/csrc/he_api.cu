@@ -784,8 +784,10 @@ static int ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X, int trans) {
     if (!s) return HE_ENOMEM;
     double *slots = reinterpret_cast<double *>(s);
     int64_t *coef = reinterpret_cast<int64_t *>(s + count * (N / 2));
-    launch_layout_matrix(ctx, p, X, slots, trans);
-    launch_encode(ctx, slots, N / 2, N / 2, (int)count, pm->scale, coef);
+    if (!launch_encode_matrix(ctx, p, X, trans, (int)count, pm->scale, coef)) {
+        launch_layout_matrix(ctx, p, X, slots, trans);
+        launch_encode(ctx, slots, N / 2, N / 2, (int)count, pm->scale, coef);
+    }
     launch_ntt_from_int64(ctx, coef, pm->data, (int)count, qpmap(ctx, pm->level), 1);
     return last_launch();
 }

@@ -300,10 +300,31 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
 // each CTA reads Z[-k] of its slice from the CTA holding it.  Then the twist and rounding of
 // encode_cl_kernel for each (the 1/2 folded into the power-of-two factor).  An odd last item
 // pairs with zeros and writes one plaintext.
-template <int CLG, int RL, int LOGN = 0>
-__global__ void encode_pair_cl_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, int count, double scale,
-                                      const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
-                                      int64_t *out, int logn_rt) {
+// Slot value j of plaintext `item`: from a slot array ([count][stride], first n_slots used) or
+// straight from a cleartext matrix in the diagonal layout of Eq. 2 after Eq. 3 (item = (r C + c) m'
+// + i, the order of an encoded matrix; the same values layout_matrix_kernel writes).
+struct SlotsSrc {
+    const double *z;
+    int64_t n_slots, stride;
+    __device__ __forceinline__ double operator()(int item, int j) const { return j < n_slots ? z[(int64_t)item * stride + j] : 0.0; }
+};
+struct MatrixSrc {
+    he_plan p;
+    const double *X;  // m x n row-major, or its n x m transpose when trans
+    int trans, lm, lc, lnb, lmb;  // log2 of m', column blocks, nb, mb
+    __device__ __forceinline__ double operator()(int item, int j) const {
+        const int64_t i = item & (p.m_prime - 1), rest = item >> lm;
+        const int64_t c = rest & (p.col_blocks - 1), r = rest >> lc;
+        const int64_t b = j >> lnb, jj = j & (p.nb - 1);
+        const int64_t row = (r << lmb) + (b << lm) + (jj & (p.m_prime - 1));
+        const int64_t col = (c << lnb) + ((i + jj) & (p.nb - 1));
+        return (row < p.m && col < p.n) ? X[trans ? col * p.m + row : row * p.n + col] : 0.0;
+    }
+};
+
+template <int CLG, int RL, int LOGN, class SRC>
+__global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const float4 *__restrict__ tw, const float4 *__restrict__ twist,
+                                      const int32_t *__restrict__ slot_pos, int64_t *out, int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
@@ -312,13 +333,12 @@ __global__ void encode_pair_cl_kernel(const double *__restrict__ slots, int64_t 
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
     const int ix = 2 * pair, iy = 2 * pair + 1;
     const bool has_y = iy < count;
-    const double *zx = slots + (int64_t)ix * stride, *zy = slots + (int64_t)iy * stride;
     const int per = M >> CLG;
     fft_tw_issue<CLG>(a, tw, logm);
     cl.sync();  // every CTA of the cluster has started before its shared memory is written
     for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
         const int bt = __brev(slot_pos[j]) >> (32 - logm);
-        const df vx = df_from(j < n_slots ? zx[j] : 0.0), vy = df_from(has_y && j < n_slots ? zy[j] : 0.0);
+        const df vx = df_from(src(ix, j)), vy = df_from(has_y ? src(iy, j) : 0.0);
         cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(vx.hi, vx.lo, vy.hi, vy.lo);
     }
     cl.sync();
@@ -538,30 +558,47 @@ static void launch_fft_cl(void (*kernel)(KArgs...), he_ctx *ctx, int count, Args
     launch_cluster_n(kernel, count << CLG, threads, (size_t)MS * sizeof(float4) * 3 / 2, ctx->stream, 1 << CLG, args...);  // slice + twiddles
 }
 
+// the pair kernel for `count` plaintexts from src; false (nothing launched) below rings of 2^10
+template <class SRC>
+static bool launch_encode_pairs(he_ctx *ctx, SRC src, int count, double scale, int64_t *coeffs) {
+    if (ctx->log_n < 10) return false;
+    const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
+    const float4 *twist = tw + ctx->n / 4;
+    const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
+    const int pairs = (count + 1) / 2;
+    switch (fft_cluster_log(ctx->log_n, pairs)) {
+        case 3:
+            launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<3, 1, L.value, SRC>; }), ctx, pairs, src, count, scale, tw,
+                                twist, pos, coeffs, ctx->log_n);
+            return true;
+        case 2:
+            launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<2, 1, L.value, SRC>; }), ctx, pairs, src, count, scale, tw,
+                                twist, pos, coeffs, ctx->log_n);
+            return true;
+        case 1:
+            launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<1, 1, L.value, SRC>; }), ctx, pairs, src, count, scale, tw,
+                                twist, pos, coeffs, ctx->log_n);
+            return true;
+        default: return false;
+    }
+}
+
+bool launch_encode_matrix(he_ctx *ctx, const he_plan &p, const double *X, int trans, int count, double scale, int64_t *coeffs) {
+    if (count < 2) return false;
+    auto lg = [](int64_t v) { return __builtin_ctzll((unsigned long long)v); };
+    const MatrixSrc src{p, X, trans, lg(p.m_prime), lg(p.col_blocks), lg(p.nb), lg(p.mb)};
+    if (!launch_encode_pairs(ctx, src, count, scale, coeffs)) return false;
+    ctx->launches++;
+    return true;
+}
+
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs) {
     if (count == 0) return;
     const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
     const float4 *twist = tw + ctx->n / 4;
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
-    if (count >= 2 && ctx->log_n >= 10) {  // two real inputs per complex transform
-        const int pairs = (count + 1) / 2;
-        switch (fft_cluster_log(ctx->log_n, pairs)) {
-            case 3:
-                launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<3, 1, L.value>; }), ctx, pairs, slots, n_slots,
-                                    stride, count, scale, tw, twist, pos, coeffs, ctx->log_n);
-                return;
-            case 2:
-                launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<2, 1, L.value>; }), ctx, pairs, slots, n_slots,
-                                    stride, count, scale, tw, twist, pos, coeffs, ctx->log_n);
-                return;
-            case 1:
-                launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return encode_pair_cl_kernel<1, 1, L.value>; }), ctx, pairs, slots, n_slots,
-                                    stride, count, scale, tw, twist, pos, coeffs, ctx->log_n);
-                return;
-            default: break;
-        }
-    }
+    if (count >= 2 && launch_encode_pairs(ctx, SlotsSrc{slots, n_slots, stride}, count, scale, coeffs)) return;
     switch (fft_cluster_log(ctx->log_n, count)) {
         case 3: launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<3, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
         case 2: launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<2, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
@@ -648,9 +685,12 @@ void encode_set_smem_limits(int max_bytes) {
         cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value, MatrixSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value, MatrixSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value, MatrixSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     });
 }

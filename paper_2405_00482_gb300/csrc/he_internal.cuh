@@ -371,6 +371,9 @@ void launch_matmult_loop_with_tables(he_ctx *ctx, const he_ptmat *pm, int r, int
 
 // encoding, sampling, encryption
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs);
+// the diagonal layout of X (Eq. 2 after Eq. 3; X given transposed when trans) and its encoding
+// in one launch; false (nothing launched) where that form does not apply
+bool launch_encode_matrix(he_ctx *ctx, const he_plan &p, const double *X, int trans, int count, double scale, int64_t *coeffs);
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots);
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *tmp);
 void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int limb_offset, uint64_t *out,
