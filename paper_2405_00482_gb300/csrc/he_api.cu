@@ -566,6 +566,11 @@ static int encrypt_impl(he_ctx *ctx, const he_pt *pt, uint64_t nonce, const uint
     const int level = pt->level;
     if (level < 0 || level >= ctx->L) return HE_ELEVEL;
     const size_t N = ctx->n, nl = level + 1;
+    if (launch_encrypt_fused(ctx, pt->data, level, nonce, nonce_dev, out->data)) {
+        out->level = level;
+        out->scale = pt->scale;
+        return last_launch();
+    }
     uint64_t *tmp = ctx_scratch(ctx, 2 * nl * N + N);
     if (!tmp) return HE_ENOMEM;
     uint64_t *a = tmp, *e = tmp + nl * N;
@@ -862,8 +867,10 @@ int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double s
     if (!s) return HE_ENOMEM;
     double *slots = reinterpret_cast<double *>(s);
     int64_t *coef = reinterpret_cast<int64_t *>(s + C * (N / 2));
-    launch_layout_vector(ctx, *plan, y, slots);
-    launch_encode(ctx, slots, N / 2, N / 2, (int)C, scale, coef);
+    if (!launch_encode_vector(ctx, *plan, y, (int)C, scale, coef)) {
+        launch_layout_vector(ctx, *plan, y, slots);
+        launch_encode(ctx, slots, N / 2, N / 2, (int)C, scale, coef);
+    }
     for (size_t c = 0; c < C; ++c) {
         launch_ntt_from_int64(ctx, coef + c * N, outs[c].data, 1, qmap(level), 0);
         outs[c].level = level;

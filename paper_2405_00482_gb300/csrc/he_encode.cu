@@ -259,25 +259,55 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
     cl.sync();
 }
 
+// Slot value j of plaintext `item`: from a slot array ([count][stride], first n_slots used), or
+// straight from a cleartext matrix in the diagonal layout of Eq. 2 after Eq. 3 (item = (r C + c) m'
+// + i, the order of an encoded matrix; the values layout_matrix_kernel writes), or from a vector
+// replicated per Eq. 3 (item = column block c; the values layout_vector_kernel writes).
+struct SlotsSrc {
+    const double *z;
+    int64_t n_slots, stride;
+    __device__ __forceinline__ double operator()(int item, int j) const { return j < n_slots ? z[(int64_t)item * stride + j] : 0.0; }
+};
+struct MatrixSrc {
+    he_plan p;
+    const double *X;  // m x n row-major, or its n x m transpose when trans
+    int trans, lm, lc, lnb, lmb;  // log2 of m', column blocks, nb, mb
+    __device__ __forceinline__ double operator()(int item, int j) const {
+        const int64_t i = item & (p.m_prime - 1), rest = item >> lm;
+        const int64_t c = rest & (p.col_blocks - 1), r = rest >> lc;
+        const int64_t b = j >> lnb, jj = j & (p.nb - 1);
+        const int64_t row = (r << lmb) + (b << lm) + (jj & (p.m_prime - 1));
+        const int64_t col = (c << lnb) + ((i + jj) & (p.nb - 1));
+        return (row < p.m && col < p.n) ? X[trans ? col * p.m + row : row * p.n + col] : 0.0;
+    }
+};
+struct VectorSrc {
+    const double *y;
+    int64_t n, nb;
+    int lnb;  // log2 nb
+    __device__ __forceinline__ double operator()(int item, int j) const {
+        const int64_t col = ((int64_t)item << lnb) + (j & (nb - 1));
+        return col < n ? y[col] : 0.0;
+    }
+};
+
 // cluster per plaintext: the slot values go straight to their bit-reversed positions in the
 // owning CTAs; each CTA then twists and rounds the coefficients of its slice
-template <int CLG, int RL, int LOGN = 0>
-__global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slots, int64_t stride, double scale,
-                                 const float4 *__restrict__ tw, const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos,
-                                 int64_t *out, int logn_rt) {
+template <int CLG, int RL, int LOGN, class SRC>
+__global__ void encode_cl_kernel(SRC src, double scale, const float4 *__restrict__ tw, const float4 *__restrict__ twist,
+                                 const int32_t *__restrict__ slot_pos, int64_t *out, int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
-    const double *z = slots + (int64_t)item * stride;
     const int per = M >> CLG;
     fft_tw_issue<CLG>(a, tw, logm);
     cl.sync();  // every CTA of the cluster has started before its shared memory is written
     for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
         const int bt = __brev(slot_pos[j]) >> (32 - logm);
-        const df v = df_from(j < n_slots ? z[j] : 0.0);
+        const df v = df_from(src(item, j));
         cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(v.hi, v.lo, 0.f, 0.f);
     }
     cl.sync();
@@ -300,28 +330,6 @@ __global__ void encode_cl_kernel(const double *__restrict__ slots, int64_t n_slo
 // each CTA reads Z[-k] of its slice from the CTA holding it.  Then the twist and rounding of
 // encode_cl_kernel for each (the 1/2 folded into the power-of-two factor).  An odd last item
 // pairs with zeros and writes one plaintext.
-// Slot value j of plaintext `item`: from a slot array ([count][stride], first n_slots used) or
-// straight from a cleartext matrix in the diagonal layout of Eq. 2 after Eq. 3 (item = (r C + c) m'
-// + i, the order of an encoded matrix; the same values layout_matrix_kernel writes).
-struct SlotsSrc {
-    const double *z;
-    int64_t n_slots, stride;
-    __device__ __forceinline__ double operator()(int item, int j) const { return j < n_slots ? z[(int64_t)item * stride + j] : 0.0; }
-};
-struct MatrixSrc {
-    he_plan p;
-    const double *X;  // m x n row-major, or its n x m transpose when trans
-    int trans, lm, lc, lnb, lmb;  // log2 of m', column blocks, nb, mb
-    __device__ __forceinline__ double operator()(int item, int j) const {
-        const int64_t i = item & (p.m_prime - 1), rest = item >> lm;
-        const int64_t c = rest & (p.col_blocks - 1), r = rest >> lc;
-        const int64_t b = j >> lnb, jj = j & (p.nb - 1);
-        const int64_t row = (r << lmb) + (b << lm) + (jj & (p.m_prime - 1));
-        const int64_t col = (c << lnb) + ((i + jj) & (p.nb - 1));
-        return (row < p.m && col < p.n) ? X[trans ? col * p.m + row : row * p.n + col] : 0.0;
-    }
-};
-
 template <int CLG, int RL, int LOGN, class SRC>
 __global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const float4 *__restrict__ tw, const float4 *__restrict__ twist,
                                       const int32_t *__restrict__ slot_pos, int64_t *out, int logn_rt) {
@@ -496,6 +504,56 @@ __global__ void sample_ternary_kernel(uint64_t seed, int64_t *out, int logn) {
 }
 
 // c0 = m - a s + e, c1 = a (NTT domain, limbs 0..level)
+// Encryption of one plaintext limb on one 8-CTA cluster: the steps of sample_uniform_kernel
+// (tag 2), the forward NTT, sample_gauss_kernel (tag 3), ntt_from_int64_kernel and
+// encrypt_combine_kernel for the slice each CTA holds, in one launch: a uniform, c1 = NTT(a)
+// (written out, then read back by the same CTA for the combine), e reduced and transformed, and
+// c0 = pt - c1 s + e.  The same values in the same order, so the same ciphertext.
+template <int LOGN = 0>
+__global__ void encrypt_cl_kernel(const uint64_t *__restrict__ pt, const uint64_t *__restrict__ sk_mont, int nl, uint64_t seed, uint64_t nonce,
+                                  const uint64_t *nonce_dev, Cdt cdt, uint64_t *ct, const uint64_t *__restrict__ d_tw,
+                                  const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    extern __shared__ uint64_t s[];
+    if (nonce_dev) nonce = *nonce_dev;
+    const int N = 1 << logn;
+    int l, off, len;
+    slice_of<true>(logn, l, off, len);
+    const uint64_t q = mc[l].q, qinv = mc[l].qinv, mu = mc[l].mu;
+    const ulonglong2 *tw = twiddles(d_tw, l, 0, logn);
+    tw_prefetch<true, true>(s, tw, logn);
+    for (int b = (off >> 1) + threadIdx.x; b < ((off + len) >> 1); b += blockDim.x) {
+        uint64_t c[4] = {(uint64_t)b, (uint64_t)l, nonce, 0};
+        philox4x64(c, seed, 2);
+        s[SIDX(2 * b - off)] = (uint64_t)((((u128)c[1]) << 64 | c[0]) % q);
+        s[SIDX(2 * b + 1 - off)] = (uint64_t)((((u128)c[3]) << 64 | c[2]) % q);
+    }
+    __syncthreads();
+    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
+    uint64_t *c1 = ct + ((int64_t)nl + l) * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) c1[k] = s[SIDX(k)];
+    __syncthreads();  // the slice is read out before the error overwrites it (twiddles stay)
+    for (int b = (off >> 2) + threadIdx.x; b < ((off + len) >> 2); b += blockDim.x) {
+        uint64_t c[4] = {(uint64_t)b, 0, nonce, 0};
+        philox4x64(c, seed, 3);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint64_t r = c[w] >> 24;
+            int64_t x = -19;
+            for (int k = 0; k < 38; ++k) x += (r >= cdt.t[k]);
+            s[SIDX(4 * b + w - off)] = reduce_signed(x, q, mu);
+        }
+    }
+    __syncthreads();
+    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
+    const int64_t base = (int64_t)l * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        const uint64_t as = mont_mul(c1[k], sk_mont[base + k], q, qinv);
+        ct[base + k] = add_mod(sub_mod(pt[base + k], as, q), s[SIDX(k)], q);
+    }
+}
+
 __global__ void encrypt_combine_kernel(const uint64_t *__restrict__ pt, const uint64_t *__restrict__ a, const uint64_t *__restrict__ e,
                                        const uint64_t *__restrict__ sk_mont, int nl, uint64_t *ct, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
@@ -592,6 +650,35 @@ bool launch_encode_matrix(he_ctx *ctx, const he_plan &p, const double *X, int tr
     return true;
 }
 
+bool launch_encode_vector(he_ctx *ctx, const he_plan &p, const double *y, int count, double scale, int64_t *coeffs) {
+    const VectorSrc src{y, p.n, p.nb, __builtin_ctzll((unsigned long long)p.nb)};
+    if (count >= 2) {
+        if (!launch_encode_pairs(ctx, src, count, scale, coeffs)) return false;
+        ctx->launches++;
+        return true;
+    }
+    const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
+    const float4 *twist = tw + ctx->n / 4;
+    const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
+    switch (fft_cluster_log(ctx->log_n, count)) {
+        case 3:
+            launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<3, 1, L.value, VectorSrc>; }), ctx, count, src, scale, tw, twist,
+                                pos, coeffs, ctx->log_n);
+            break;
+        case 2:
+            launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<2, 1, L.value, VectorSrc>; }), ctx, count, src, scale, tw, twist,
+                                pos, coeffs, ctx->log_n);
+            break;
+        case 1:
+            launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<1, 1, L.value, VectorSrc>; }), ctx, count, src, scale, tw, twist,
+                                pos, coeffs, ctx->log_n);
+            break;
+        default: return false;
+    }
+    ctx->launches++;
+    return true;
+}
+
 void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t stride, int count, double scale, int64_t *coeffs) {
     if (count == 0) return;
     const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
@@ -600,9 +687,18 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
     ctx->launches++;
     if (count >= 2 && launch_encode_pairs(ctx, SlotsSrc{slots, n_slots, stride}, count, scale, coeffs)) return;
     switch (fft_cluster_log(ctx->log_n, count)) {
-        case 3: launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<3, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
-        case 2: launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<2, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
-        case 1: launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<1, 1, L.value>; }), ctx, count, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n); return;
+        case 3:
+            launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<3, 1, L.value, SlotsSrc>; }), ctx, count,
+                                SlotsSrc{slots, n_slots, stride}, scale, tw, twist, pos, coeffs, ctx->log_n);
+            return;
+        case 2:
+            launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<2, 1, L.value, SlotsSrc>; }), ctx, count,
+                                SlotsSrc{slots, n_slots, stride}, scale, tw, twist, pos, coeffs, ctx->log_n);
+            return;
+        case 1:
+            launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return encode_cl_kernel<1, 1, L.value, SlotsSrc>; }), ctx, count,
+                                SlotsSrc{slots, n_slots, stride}, scale, tw, twist, pos, coeffs, ctx->log_n);
+            return;
         default: break;
     }
     launch_k(encode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, slots, n_slots, stride, scale, tw, twist, pos, coeffs, ctx->log_n);
@@ -653,6 +749,17 @@ void launch_sample_ternary(he_ctx *ctx, int64_t *out) {
     launch_k(sample_ternary_kernel, (ctx->n / 4 + 255) / 256, 256, 0, ctx->stream, ctx->seed, out, ctx->log_n);
 }
 
+bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, int level, uint64_t nonce, const uint64_t *nonce_dev, uint64_t *ct) {
+    if (!use_cluster(ctx->log_n, level + 1)) return false;
+    Cdt c;
+    for (int k = 0; k < 38; ++k) c.t[k] = ctx->cdt[k];
+    ctx->launches++;
+    launch_cluster(by_logn(ctx->log_n, [](auto L) { return encrypt_cl_kernel<L.value>; }), (level + 1) * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
+                   cl_smem_bytes(ctx->log_n), ctx->stream, pt, (const uint64_t *)ctx->d_sk_mont, level + 1, ctx->seed, nonce, nonce_dev, c, ct,
+                   (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+    return true;
+}
+
 void launch_encrypt_combine(he_ctx *ctx, const uint64_t *pt, const uint64_t *a, const uint64_t *e, int level, uint64_t *ct) {
     dim3 grid((ctx->n + 255) / 256, level + 1);
     ctx->launches++;
@@ -679,18 +786,25 @@ void encode_set_smem_limits(int max_bytes) {
     each_logn([max_bytes](auto L) {
         cudaFuncSetAttribute(decrypt_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decrypt_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encrypt_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         // cluster FFTs: the slice and the local stages' twiddles (1.5 MS float4)
-        cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value, MatrixSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value, MatrixSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value, MatrixSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     });
 }

@@ -374,8 +374,13 @@ void launch_encode(he_ctx *ctx, const double *slots, int64_t n_slots, int64_t st
 // the diagonal layout of X (Eq. 2 after Eq. 3; X given transposed when trans) and its encoding
 // in one launch; false (nothing launched) where that form does not apply
 bool launch_encode_matrix(he_ctx *ctx, const he_plan &p, const double *X, int trans, int count, double scale, int64_t *coeffs);
+// the replicated layout of y (Eq. 3) and its encoding in one launch, count = column blocks; false
+// (nothing launched) where that form does not apply
+bool launch_encode_vector(he_ctx *ctx, const he_plan &p, const double *y, int count, double scale, int64_t *coeffs);
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots);
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *tmp);
+// he_encrypt's five steps as one cluster launch per limb (false: that form does not apply)
+bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, int level, uint64_t nonce, const uint64_t *nonce_dev, uint64_t *ct);
 void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int limb_offset, uint64_t *out,
                            const uint64_t *nonce_dev = nullptr);
 void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out, const uint64_t *nonce_dev = nullptr);
