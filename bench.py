@@ -166,8 +166,7 @@ def run_gpu(args):
                 cm.encode_matrix(plan, Md, level, out=pm, transposed=trans)
         else:
             c.encode_matrix(plan, Md, level, out=pm, transposed=trans)
-        c.encode_vector(plan, vd, P.scale, level, outs=[pt])
-        c.encrypt(pt, nonce, out=ct)
+        c.encrypt_vector(plan, vd, P.scale, level, nonce, outs=[ct])  # encode + encrypt in one call
         if cm is not c:
             c.stream.wait_stream(cm.stream)
         c.matmult(plan, pm, [ct], out)

@@ -191,6 +191,13 @@ void he_ptmat_free(he_ptmat *pm);
 /* P_B's side: replicate piece c of y (device, n doubles) N'/nb times and encode it into
  * outs[c] for c < col_blocks (Sec. 4.2.1, "[[d]] is expanded by replicating its pattern"). */
 int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double scale, int level, he_pt *outs);
+/* he_encode_vector then he_encrypt of each column block c, under nonce + c, or under the device
+ * nonce nonce_dev[c] (read when the kernels run, as he_encrypt_dnonce) when nonce_dev is not
+ * NULL: outs[0..col_blocks) ciphertexts at `level`.  The encoded coefficients join the error
+ * before its NTT (NTT(m) + NTT(e) = NTT(m + e) mod q), so the ciphertexts equal those of the
+ * separate calls bit for bit, in two launches for a single block. */
+int he_encrypt_vector(he_ctx *ctx, const he_plan *plan, const double *y, double scale, int level, uint64_t nonce, const uint64_t *nonce_dev,
+                      he_ct *outs);
 
 /* The hot path: outs[r] = Rescale( sum_c sum_{i<m'} e_{r,c,i} (x) HstRotL(ins[c], i) ) for
  * r < row_blocks, with ins[c] for c < col_blocks at the ptmat's level (Tab. 2 PackVFL row,

@@ -561,18 +561,9 @@ int he_encode(he_ctx *ctx, const double *slots, int64_t n_slots, double scale, i
     return last_launch();
 }
 
-static int encrypt_impl(he_ctx *ctx, const he_pt *pt, uint64_t nonce, const uint64_t *nonce_dev, he_ct *out) {
-    if (!ctx || !pt || !out || !pt->data || !out->data) return HE_EINVAL;
-    const int level = pt->level;
-    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+// the encryption as separate launches (sampling, NTTs, combine); tmp: 2 (level+1) N + N words
+static void encrypt_steps(he_ctx *ctx, const uint64_t *pt, int level, uint64_t nonce, const uint64_t *nonce_dev, uint64_t *ct, uint64_t *tmp) {
     const size_t N = ctx->n, nl = level + 1;
-    if (launch_encrypt_fused(ctx, pt->data, level, nonce, nonce_dev, out->data)) {
-        out->level = level;
-        out->scale = pt->scale;
-        return last_launch();
-    }
-    uint64_t *tmp = ctx_scratch(ctx, 2 * nl * N + N);
-    if (!tmp) return HE_ENOMEM;
     uint64_t *a = tmp, *e = tmp + nl * N;
     int64_t *e_int = reinterpret_cast<int64_t *>(tmp + 2 * nl * N);
     const LimbMap m = qmap(level);
@@ -580,7 +571,22 @@ static int encrypt_impl(he_ctx *ctx, const he_pt *pt, uint64_t nonce, const uint
     launch_ntt_fwd(ctx, a, a, 1, m);
     launch_sample_gauss(ctx, 3, nonce, e_int, nonce_dev);
     launch_ntt_from_int64(ctx, e_int, e, 1, m, 0);
-    launch_encrypt_combine(ctx, pt->data, a, e, level, out->data);
+    launch_encrypt_combine(ctx, pt, a, e, level, ct);
+}
+
+static int encrypt_impl(he_ctx *ctx, const he_pt *pt, uint64_t nonce, const uint64_t *nonce_dev, he_ct *out) {
+    if (!ctx || !pt || !out || !pt->data || !out->data) return HE_EINVAL;
+    const int level = pt->level;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    const size_t N = ctx->n, nl = level + 1;
+    if (launch_encrypt_fused(ctx, pt->data, nullptr, level, nonce, nonce_dev, out->data)) {
+        out->level = level;
+        out->scale = pt->scale;
+        return last_launch();
+    }
+    uint64_t *tmp = ctx_scratch(ctx, 2 * nl * N + N);
+    if (!tmp) return HE_ENOMEM;
+    encrypt_steps(ctx, pt->data, level, nonce, nonce_dev, out->data, tmp);
     out->level = level;
     out->scale = pt->scale;
     return last_launch();
@@ -873,6 +879,39 @@ int he_encode_vector(he_ctx *ctx, const he_plan *plan, const double *y, double s
     }
     for (size_t c = 0; c < C; ++c) {
         launch_ntt_from_int64(ctx, coef + c * N, outs[c].data, 1, qmap(level), 0);
+        outs[c].level = level;
+        outs[c].scale = scale;
+    }
+    return last_launch();
+}
+
+int he_encrypt_vector(he_ctx *ctx, const he_plan *plan, const double *y, double scale, int level, uint64_t nonce, const uint64_t *nonce_dev,
+                      he_ct *outs) {
+    if (!ctx || !plan || !y || !outs || plan->slots != ctx->n / 2) return HE_EINVAL;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    const size_t N = ctx->n, C = plan->col_blocks, nl = level + 1;
+    for (size_t c = 0; c < C; ++c)
+        if (!outs[c].data) return HE_EINVAL;
+    const bool fused = use_cluster(ctx->log_n, (int)nl);
+    // slots, integer coefficients, and (separate launches only) one plaintext and the encryption's temporaries
+    const size_t w_slots = C * (N / 2), w_coef = C * N, w_pt = fused ? 0 : nl * N, w_tmp = fused ? 0 : 2 * nl * N + N;
+    uint64_t *s = ctx_scratch(ctx, w_slots + w_coef + w_pt + w_tmp);
+    if (!s) return HE_ENOMEM;
+    double *slots = reinterpret_cast<double *>(s);
+    int64_t *coef = reinterpret_cast<int64_t *>(s + w_slots);
+    if (!launch_encode_vector(ctx, *plan, y, (int)C, scale, coef)) {
+        launch_layout_vector(ctx, *plan, y, slots);
+        launch_encode(ctx, slots, N / 2, N / 2, (int)C, scale, coef);
+    }
+    for (size_t c = 0; c < C; ++c) {
+        const uint64_t *nd = nonce_dev ? nonce_dev + c : nullptr;
+        if (fused) {
+            launch_encrypt_fused(ctx, nullptr, coef + c * N, level, nonce + c, nd, outs[c].data);
+        } else {
+            uint64_t *pt = s + w_slots + w_coef, *tmp = pt + w_pt;
+            launch_ntt_from_int64(ctx, coef + c * N, pt, 1, qmap(level), 0);
+            encrypt_steps(ctx, pt, level, nonce + c, nd, outs[c].data, tmp);
+        }
         outs[c].level = level;
         outs[c].scale = scale;
     }

@@ -508,9 +508,13 @@ __global__ void sample_ternary_kernel(uint64_t seed, int64_t *out, int logn) {
 // (tag 2), the forward NTT, sample_gauss_kernel (tag 3), ntt_from_int64_kernel and
 // encrypt_combine_kernel for the slice each CTA holds, in one launch: a uniform, c1 = NTT(a)
 // (written out, then read back by the same CTA for the combine), e reduced and transformed, and
-// c0 = pt - c1 s + e.  The same values in the same order, so the same ciphertext.
+// c0 = pt - c1 s + e.  The same values in the same order, so the same ciphertext.  With m_int
+// (the plaintext's integer coefficients, pt null) the error becomes m + e before its NTT and
+// c0 = NTT(m + e) - c1 s: NTT(m) + NTT(e) = NTT(m + e) mod q, so the ciphertext equals that of
+// encoding m to a plaintext and encrypting it.
 template <int LOGN = 0>
-__global__ void encrypt_cl_kernel(const uint64_t *__restrict__ pt, const uint64_t *__restrict__ sk_mont, int nl, uint64_t seed, uint64_t nonce,
+__global__ void __launch_bounds__(512) encrypt_cl_kernel(const uint64_t *__restrict__ pt, const int64_t *__restrict__ m_int, const uint64_t *__restrict__ sk_mont, int nl,
+                                  uint64_t seed, uint64_t nonce,
                                   const uint64_t *nonce_dev, Cdt cdt, uint64_t *ct, const uint64_t *__restrict__ d_tw,
                                   const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
@@ -542,6 +546,7 @@ __global__ void encrypt_cl_kernel(const uint64_t *__restrict__ pt, const uint64_
             const uint64_t r = c[w] >> 24;
             int64_t x = -19;
             for (int k = 0; k < 38; ++k) x += (r >= cdt.t[k]);
+            if (m_int) x += m_int[4 * b + w];
             s[SIDX(4 * b + w - off)] = reduce_signed(x, q, mu);
         }
     }
@@ -550,7 +555,7 @@ __global__ void encrypt_cl_kernel(const uint64_t *__restrict__ pt, const uint64_
     const int64_t base = (int64_t)l * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
         const uint64_t as = mont_mul(c1[k], sk_mont[base + k], q, qinv);
-        ct[base + k] = add_mod(sub_mod(pt[base + k], as, q), s[SIDX(k)], q);
+        ct[base + k] = m_int ? sub_mod(s[SIDX(k)], as, q) : add_mod(sub_mod(pt[base + k], as, q), s[SIDX(k)], q);
     }
 }
 
@@ -749,13 +754,14 @@ void launch_sample_ternary(he_ctx *ctx, int64_t *out) {
     launch_k(sample_ternary_kernel, (ctx->n / 4 + 255) / 256, 256, 0, ctx->stream, ctx->seed, out, ctx->log_n);
 }
 
-bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, int level, uint64_t nonce, const uint64_t *nonce_dev, uint64_t *ct) {
+bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, const int64_t *m_int, int level, uint64_t nonce, const uint64_t *nonce_dev,
+                          uint64_t *ct) {
     if (!use_cluster(ctx->log_n, level + 1)) return false;
     Cdt c;
     for (int k = 0; k < 38; ++k) c.t[k] = ctx->cdt[k];
     ctx->launches++;
     launch_cluster(by_logn(ctx->log_n, [](auto L) { return encrypt_cl_kernel<L.value>; }), (level + 1) * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
-                   cl_smem_bytes(ctx->log_n), ctx->stream, pt, (const uint64_t *)ctx->d_sk_mont, level + 1, ctx->seed, nonce, nonce_dev, c, ct,
+                   cl_smem_bytes(ctx->log_n), ctx->stream, pt, m_int, (const uint64_t *)ctx->d_sk_mont, level + 1, ctx->seed, nonce, nonce_dev, c, ct,
                    (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
     return true;
 }

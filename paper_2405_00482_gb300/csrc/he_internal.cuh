@@ -379,8 +379,10 @@ bool launch_encode_matrix(he_ctx *ctx, const he_plan &p, const double *X, int tr
 bool launch_encode_vector(he_ctx *ctx, const he_plan &p, const double *y, int count, double scale, int64_t *coeffs);
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots);
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *tmp);
-// he_encrypt's five steps as one cluster launch per limb (false: that form does not apply)
-bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, int level, uint64_t nonce, const uint64_t *nonce_dev, uint64_t *ct);
+// he_encrypt's five steps as one cluster launch per limb (false: that form does not apply); with
+// m_int (integer coefficients, pt null) the plaintext is encoded into the same launch
+bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, const int64_t *m_int, int level, uint64_t nonce, const uint64_t *nonce_dev,
+                          uint64_t *ct);
 void launch_sample_uniform(he_ctx *ctx, uint64_t tag, uint64_t nonce, const LimbMap &map, int limb_offset, uint64_t *out,
                            const uint64_t *nonce_dev = nullptr);
 void launch_sample_gauss(he_ctx *ctx, uint64_t tag, uint64_t nonce, int64_t *out, const uint64_t *nonce_dev = nullptr);

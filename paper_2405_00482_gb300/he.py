@@ -53,6 +53,7 @@ _SIGS = {
     "he_encode": (ctypes.c_int, [_vp, _vp, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
     "he_encrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _u64, ctypes.POINTER(HeCt)]),
     "he_encrypt_dnonce": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp, ctypes.POINTER(HeCt)]),
+    "he_encrypt_vector": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _u64, _vp, _vp]),
     "he_decrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_add": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
     "he_add_plain": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HePt), ctypes.POINTER(HeCt)]),
@@ -580,6 +581,25 @@ class Context:
         for p, a in zip(pts, arr):
             p.level, p.scale = a.level, a.scale
         return pts
+
+    def encrypt_vector(self, plan: Plan, y: torch.Tensor, scale: float, level: int, nonce,
+                       outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
+        """encode_vector then encrypt of each column block c in one call (he_encrypt_vector): nonce
+        an int (block c under nonce + c) or an int64 device tensor of col_blocks nonces read when
+        the kernels run."""
+        y = _dev(y, torch.float64)
+        cts = outs or [self.new_ct(level) for _ in range(plan.col_blocks)]
+        arr = (HeCt * len(cts))(*[c.c() for c in cts])
+        if isinstance(nonce, torch.Tensor):
+            if nonce.numel() != plan.col_blocks or nonce.dtype != torch.int64 or not nonce.is_cuda:
+                raise ValueError("device nonces: col_blocks int64 elements on the GPU")
+            n_host, n_dev = 0, _vp(nonce.data_ptr())
+        else:
+            n_host, n_dev = nonce, None
+        _check(_lib().he_encrypt_vector(self.handle, plan.handle, y.data_ptr(), scale, level, n_host, n_dev, arr), "he_encrypt_vector")
+        for c, a in zip(cts, arr):
+            c.level, c.scale = a.level, a.scale
+        return cts
 
     def matmult(self, plan: Plan, pm: PtMatrix, cts: list[Ciphertext], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
         outs = outs or [self.new_ct(pm.level - 1) for _ in range(plan.row_blocks)]

@@ -100,3 +100,28 @@ def test_graph_needs_non_default_stream(he):
     ctx = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=1, stream=torch.cuda.default_stream())
     with pytest.raises(ValueError):
         he.Graph(ctx, lambda: None)
+
+
+@pytest.mark.parametrize("log_n,m,n", [(5, 4, 40), (5, 8, 8), (13, 256, 1024), (13, 1024, 256), (13, 64, 9000)])
+def test_encrypt_vector_equals_encode_then_encrypt(he, log_n, m, n):
+    """he_encrypt_vector (encoded coefficients joined to the error before its NTT at N >= 2^10)
+    gives the ciphertexts of encode_vector then encrypt under nonce + c, bit for bit; likewise
+    with the nonces in device memory."""
+    import torch
+
+    qb, pb, d = [60, 40, 40], [60], 3
+    ctx = he.Context(log_n, qb, pb, d, seed=8)
+    plan = he.Plan(m, n, ctx.slots)
+    y = torch.from_numpy(np.random.default_rng(n).uniform(-1, 1, n)).cuda()
+    level, scale = 2, 2.0**40
+    pts = ctx.encode_vector(plan, y, scale, level)
+    want = [he.as_u64(ctx.ct_export(ctx.encrypt(p, 40 + c))) for c, p in enumerate(pts)]
+    got = ctx.encrypt_vector(plan, y, scale, level, 40)
+    assert len(got) == plan.col_blocks
+    for g, w in zip(got, want):
+        assert g.level == level and g.scale == scale
+        assert np.array_equal(he.as_u64(ctx.ct_export(g)), w)
+    nonces = torch.arange(40, 40 + plan.col_blocks, dtype=torch.int64, device="cuda")
+    got = ctx.encrypt_vector(plan, y, scale, level, nonces)
+    for g, w in zip(got, want):
+        assert np.array_equal(he.as_u64(ctx.ct_export(g)), w)
