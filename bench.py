@@ -8,8 +8,9 @@ products of a VFL linear-model iteration, both as single plain MatMult calls:
 each = encode the diagonal plaintexts of the matrix (X^T read from X itself), encode +
 encrypt the replicated vector, MatMult (ModUp, 63 key-switch / multiply-accumulate steps,
 ModDown, rescale), decrypt + decode, lazy rotate-and-sum.  Galois keys are made once, before
-timing.  The two products and their matrix encodings run on four streams (a context and three
-forks) and the step is replayed as one captured CUDA graph (--no-graph: eager calls).
+timing.  The two products run on two streams (a context and a fork; --streams 4 gives each
+matrix encoding a stream of its own too) and the step is replayed as one captured CUDA graph
+(--no-graph: eager calls).
 value = MatMults per second over all ranks (2 per step per rank).
 
 --impl reference times the CPU oracle (the only reference implementation: the paper
@@ -730,7 +731,7 @@ def main():
     ap.add_argument("--no-vfl-nn", action="store_true")
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time the eager step (one API call per operation) as the headline")
-    ap.add_argument("--streams", type=int, default=4, choices=[1, 2, 4],
+    ap.add_argument("--streams", type=int, default=2, choices=[1, 2, 4],
                     help="2: the forward product on a forked context and its own stream, overlapping the gradient product; 4: also each matrix encoding on a stream of its own")
     ap.add_argument("--loop-variant", type=int, default=-1,
                     help="pin the MatMult loop-kernel variant of the plain products (default: autotune)")
