@@ -975,7 +975,7 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
             launch_matmult_loop(ctx, pm, r, (int)c, ins[c].data, rot ? D + c * mu.ndig * ext * N : nullptr, acc, cacc, c > 0);
         const uint64_t *pre = cacc;
         if (rot && moddown_rescale_fused(ctx, level)) {
-            launch_moddown_rescale(ctx, acc, level, cacc, cacc + nl * N, outs[r].data);
+            launch_moddown_rescale(ctx, acc, level, cacc, cacc + nl * N, outs[r].data, tmp);
         } else {
             if (rot) {
                 launch_moddown(ctx, acc, level, 2, cacc, cacc + nl * N, sum, tmp);

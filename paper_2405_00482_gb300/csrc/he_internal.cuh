@@ -362,7 +362,8 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
 // ModDown of [2][level+1+K][N] plus add0/add1 (NTT, [level+1][N] each, may be null), then
 // rescale, into out [2][level][N]: one cluster launch when moddown_rescale_fused says so
 bool moddown_rescale_fused(const he_ctx *ctx, int level);
-void launch_moddown_rescale(he_ctx *ctx, const uint64_t *x, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out);
+void launch_moddown_rescale(he_ctx *ctx, const uint64_t *x, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out,
+                            uint64_t *tmp);  // tmp: 2 (K+1) N words
 void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D,
                          uint64_t *acc /*[2][ext][N]*/, uint64_t *cacc /*[2][level+1][N]*/, int accumulate);
 

@@ -334,20 +334,63 @@ __global__ void rescale_cl_fused_kernel(const uint64_t *__restrict__ ct, int lev
     for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = mul_shoup(sub_mod(cj[k], s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
 }
 
-// ModDown then rescale (the MatMult epilogue) as one cluster launch.  Component c, output limb
-// j < L (L = md.nq - 1, the limb the rescale drops); a_i the P limbs in coefficient form and conv_t
-// their conversion to q_t.  ModDown gives sum_t = add_c[t] + (x_t - NTT(conv_t)) P^-1 and the
-// rescale out_j = (sum_j - NTT([INTT(sum_L)]_j)) q_L^-1, [.]_j the centred lift reduced mod q_j.
-// The NTT being linear mod q_j, out_j = (add_c[j] + x_j P^-1 - NTT(w_j)) q_L^-1 with
+// ModDown then rescale (the MatMult epilogue).  Component c, output limb j < L (L = md.nq - 1,
+// the limb the rescale drops); a_i the P limbs in coefficient form and conv_t their conversion to
+// q_t.  ModDown gives sum_t = add_c[t] + (x_t - NTT(conv_t)) P^-1 and the rescale
+// out_j = (sum_j - NTT([INTT(sum_L)]_j)) q_L^-1, [.]_j the centred lift reduced mod q_j.  The NTT
+// being linear mod q_j, out_j = (add_c[j] + x_j P^-1 - NTT(w_j)) q_L^-1 with
 // w_j = conv_j P^-1 + [INTT(sum_L)]_j, and INTT(sum_L) = INTT(add_c[L] + x_L P^-1) - conv_L P^-1.
 // Each step is exact arithmetic mod a prime, so the output is the canonical residue the two
-// separate stages give, bit for bit, after K + 2 cluster transforms per item in one launch
-// instead of K + 1 and 2 in two.
-// LOGN > 0: the ring size at compile time (logn_rt == LOGN)
+// separate stages give, bit for bit.  Two launches, each one cluster transform deep:
+// moddown_rescale_intt_kernel brings every input limb the combination needs to coefficient form
+// at once (per component the K limbs of P, already scaled by [(P/p_i)^-1]_{p_i}, and
+// add_c[L] + x_L P^-1), into tmp [2][K+1][N]; moddown_rescale_ntt_kernel forms w_j per coefficient
+// and transforms it.  (One launch doing the K + 2 transforms in a row took longer.)
 template <int LOGN = 0>
-__global__ void moddown_rescale_cl_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, RescaleConst rc,
-                                          const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *out,
-                                          const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
+__global__ void moddown_rescale_intt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, const uint64_t *__restrict__ add0,
+                                            const uint64_t *__restrict__ add1, uint64_t *tmp, const uint64_t *__restrict__ d_tw,
+                                            const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int c = item / (md.K + 1), r = item % (md.K + 1);
+    const int L = md.nq - 1;
+    uint64_t *o = tmp + ((int64_t)c * (md.K + 1) + r) * N + off;
+    if (r < md.K) {  // P limb r: INTT, N^-1, [(P/p_r)^-1]
+        const int pr = md.p_prime[r];
+        const uint64_t pi = mc[pr].q;
+        cl_intt_slice<LOGN>(s, x + ((int64_t)c * ext + md.nq + r) * N + off, pr, d_tw, mc, logn, len);
+        for (int k = threadIdx.x; k < len; k += blockDim.x) {
+            const uint64_t v = mul_shoup(s[SIDX(k)], mc[pr].ninv, mc[pr].ninv_shoup, pi);
+            o[k] = mul_shoup(v, md.inv[r], md.inv_shoup[r], pi);
+        }
+        return;
+    }
+    // add_c[L] + x_L P^-1, INTT, N^-1
+    const int pl = md.q_prime[L];
+    const uint64_t ql = mc[pl].q;
+    const ulonglong2 *itw = twiddles(d_tw, pl, 1, logn);
+    tw_prefetch<true, false>(s, itw, logn);
+    const uint64_t *xl = x + ((int64_t)c * ext + L) * N + off;
+    const uint64_t *ad = c == 0 ? add0 : add1;
+    const uint64_t *al = ad ? ad + (int64_t)L * N + off : nullptr;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        uint64_t v = mul_shoup(xl[k], md.pinv[L], md.pinv_shoup[L], ql);
+        if (al) v = add_mod(v, al[k], ql);
+        s[SIDX(k)] = v;
+    }
+    __syncthreads();
+    ntt_inv_cluster<LOGN>(s, itw, ql, logn);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = mul_shoup(s[SIDX(k)], mc[pl].ninv, mc[pl].ninv_shoup, ql);
+}
+
+template <int LOGN = 0>
+__global__ void moddown_rescale_ntt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, RescaleConst rc,
+                                           const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, const uint64_t *__restrict__ tmp,
+                                           uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
@@ -358,50 +401,28 @@ __global__ void moddown_rescale_cl_kernel(const uint64_t *__restrict__ x, int ex
     const int c = item / L, j = item % L;
     const int pj = md.q_prime[j], pl = md.q_prime[L];
     const uint64_t q = mc[pj].q, ql = mc[pl].q;
-    uint64_t *acc_j = cl_acc_slice(s, logn), *acc_l = acc_j + (N >> 3);
-    for (int k = threadIdx.x; k < len; k += blockDim.x) acc_j[k] = acc_l[k] = 0;
-    for (int i = 0; i < md.K; ++i) {  // conv_j and conv_L from the P limbs
-        const int pr = md.p_prime[i];
-        cl_intt_slice<LOGN>(s, x + ((int64_t)c * ext + md.nq + i) * N + off, pr, d_tw, mc, logn, len);
-        const uint64_t pi = mc[pr].q;
-        for (int k = threadIdx.x; k < len; k += blockDim.x) {
-            uint64_t v = mul_shoup(s[SIDX(k)], mc[pr].ninv, mc[pr].ninv_shoup, pi);
-            v = mul_shoup(v, md.inv[i], md.inv_shoup[i], pi);
-            acc_j[k] = add_mod(acc_j[k], mul_shoup(v, md.hat[i][j], md.hat_shoup[i][j], q), q);
-            acc_l[k] = add_mod(acc_l[k], mul_shoup(v, md.hat[i][L], md.hat_shoup[i][L], ql), ql);
-        }
-        __syncthreads();
-    }
-    const uint64_t *ad = c == 0 ? add0 : add1;
-    {  // INTT(add_c[L] + x_L P^-1), then minus conv_L P^-1: sum_L in coefficient form (in acc_l)
-        const ulonglong2 *itw = twiddles(d_tw, pl, 1, logn);
-        tw_prefetch<true, false>(s, itw, logn);
-        const uint64_t *xl = x + ((int64_t)c * ext + L) * N + off;
-        const uint64_t *al = ad ? ad + (int64_t)L * N + off : nullptr;
-        for (int k = threadIdx.x; k < len; k += blockDim.x) {
-            uint64_t v = mul_shoup(xl[k], md.pinv[L], md.pinv_shoup[L], ql);
-            if (al) v = add_mod(v, al[k], ql);
-            s[SIDX(k)] = v;
-        }
-        __syncthreads();
-        ntt_inv_cluster<LOGN>(s, itw, ql, logn);
-        for (int k = threadIdx.x; k < len; k += blockDim.x) {
-            const uint64_t v = mul_shoup(s[SIDX(k)], mc[pl].ninv, mc[pl].ninv_shoup, ql);
-            acc_l[k] = sub_mod(v, mul_shoup(acc_l[k], md.pinv[L], md.pinv_shoup[L], ql), ql);
-        }
-        __syncthreads();
-    }
     const ulonglong2 *tw = twiddles(d_tw, pj, 0, logn);
     tw_prefetch<true, true>(s, tw, logn);
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {  // w_j = conv_j P^-1 + [sum_L]_j
-        uint64_t r = acc_l[k] + rc.half;
-        if (r >= rc.ql) r -= rc.ql;
-        const int64_t centred = (int64_t)r - (int64_t)rc.half;
-        s[SIDX(k)] = add_mod(mul_shoup(acc_j[k], md.pinv[j], md.pinv_shoup[j], q), reduce_signed(centred, q, mc[pj].mu), q);
+    const uint64_t *tc = tmp + (int64_t)c * (md.K + 1) * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        // conv_j and conv_L of the scaled P limbs, in limb order
+        uint64_t acc_j = 0, acc_l = 0;
+        for (int i = 0; i < md.K; ++i) {
+            const uint64_t v = tc[(int64_t)i * N + k];
+            acc_j = add_mod(acc_j, mul_shoup(v, md.hat[i][j], md.hat_shoup[i][j], q), q);
+            acc_l = add_mod(acc_l, mul_shoup(v, md.hat[i][L], md.hat_shoup[i][L], ql), ql);
+        }
+        // sum_L in coefficient form, centred, reduced mod q_j; w_j = conv_j P^-1 + [sum_L]_j
+        const uint64_t sl = sub_mod(tc[(int64_t)md.K * N + k], mul_shoup(acc_l, md.pinv[L], md.pinv_shoup[L], ql), ql);
+        uint64_t rr = sl + rc.half;
+        if (rr >= rc.ql) rr -= rc.ql;
+        const int64_t centred = (int64_t)rr - (int64_t)rc.half;
+        s[SIDX(k)] = add_mod(mul_shoup(acc_j, md.pinv[j], md.pinv_shoup[j], q), reduce_signed(centred, q, mc[pj].mu), q);
     }
     __syncthreads();
     ntt_fwd_cluster<LOGN>(s, tw, q, logn);
     const uint64_t *xj = x + ((int64_t)c * ext + j) * N + off;
+    const uint64_t *ad = c == 0 ? add0 : add1;
     const uint64_t *aj = ad ? ad + (int64_t)j * N + off : nullptr;
     uint64_t *o = out + ((int64_t)c * L + j) * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
@@ -1254,13 +1275,18 @@ void launch_rescale(he_ctx *ctx, const uint64_t *ct, int level, uint64_t *out, u
 
 bool moddown_rescale_fused(const he_ctx *ctx, int level) { return level >= 1 && use_cluster(ctx->log_n, 2 * level); }
 
-void launch_moddown_rescale(he_ctx *ctx, const uint64_t *x, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out) {
+void launch_moddown_rescale(he_ctx *ctx, const uint64_t *x, int level, const uint64_t *add0, const uint64_t *add1, uint64_t *out,
+                            uint64_t *tmp) {
     const ModDownConst &md = ctx->moddown[level];
     const RescaleConst rc = make_rescale_const(ctx, level);
-    ctx->launches++;
-    launch_cluster(by_logn(ctx->log_n, [](auto L) { return moddown_rescale_cl_kernel<L.value>; }), 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
-                   cl_fused_smem_bytes(ctx->log_n) + ((size_t)8 << (ctx->log_n - 3)), ctx->stream, x, level + 1 + ctx->K, md, rc, add0, add1,
-                   out, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+    const int ext = level + 1 + ctx->K;
+    ctx->launches += 2;
+    launch_cluster(by_logn(ctx->log_n, [](auto L) { return moddown_rescale_intt_kernel<L.value>; }), 2 * (ctx->K + 1) * HE_NTT_CL_SIZE,
+                   cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, x, ext, md, add0, add1, tmp, (const uint64_t *)ctx->d_tw,
+                   (const ModConst *)ctx->d_mc, ctx->log_n);
+    launch_cluster(by_logn(ctx->log_n, [](auto L) { return moddown_rescale_ntt_kernel<L.value>; }), 2 * level * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
+                   cl_smem_bytes(ctx->log_n), ctx->stream, x, ext, md, rc, add0, add1, (const uint64_t *)tmp, out, (const uint64_t *)ctx->d_tw,
+                   (const ModConst *)ctx->d_mc, ctx->log_n);
 }
 
 void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const uint64_t *ct, const uint64_t *D, uint64_t *acc,
@@ -1439,7 +1465,8 @@ void ops_set_smem_limits(int max_bytes) {
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(modup_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(rescale_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
-    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
+    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_intt_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
+    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_ntt_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     for (int v = 0; v < kMMVariants; ++v)
         for (int nd = 0; nd <= 3; ++nd)
             mm_dispatch(v, nd, []<int NDIG, int VEC, int G, int S, bool GA>() {
