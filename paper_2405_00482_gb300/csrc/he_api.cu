@@ -892,7 +892,7 @@ int he_encrypt_vector(he_ctx *ctx, const he_plan *plan, const double *y, double 
     const size_t N = ctx->n, C = plan->col_blocks, nl = level + 1;
     for (size_t c = 0; c < C; ++c)
         if (!outs[c].data) return HE_EINVAL;
-    const bool fused = use_cluster(ctx->log_n, (int)nl);
+    const bool fused = use_cluster(ctx->log_n, 2 * (int)nl);  // the condition of launch_encrypt_fused
     // slots, integer coefficients, and (separate launches only) one plaintext and the encryption's temporaries
     const size_t w_slots = C * (N / 2), w_coef = C * N, w_pt = fused ? 0 : nl * N, w_tmp = fused ? 0 : 2 * nl * N + N;
     uint64_t *s = ctx_scratch(ctx, w_slots + w_coef + w_pt + w_tmp);

@@ -504,58 +504,67 @@ __global__ void sample_ternary_kernel(uint64_t seed, int64_t *out, int logn) {
 }
 
 // c0 = m - a s + e, c1 = a (NTT domain, limbs 0..level)
-// Encryption of one plaintext limb on one 8-CTA cluster: the steps of sample_uniform_kernel
-// (tag 2), the forward NTT, sample_gauss_kernel (tag 3), ntt_from_int64_kernel and
-// encrypt_combine_kernel for the slice each CTA holds, in one launch: a uniform, c1 = NTT(a)
-// (written out, then read back by the same CTA for the combine), e reduced and transformed, and
-// c0 = pt - c1 s + e.  The same values in the same order, so the same ciphertext.  With m_int
+// Encryption as two launches: the steps of sample_uniform_kernel (tag 2) and the forward NTT,
+// and of sample_gauss_kernel (tag 3) and ntt_from_int64_kernel, for every limb at once (item
+// (limb l, which): which 0 gives c1 = NTT(a) in place, which 1 NTT(e) in the c0 slot), then
+// encrypt_finish_kernel's c0 = pt - c1 s + e elementwise.  The same values, so the same
+// ciphertext as the five separate kernels, one cluster transform deep instead of two.  With m_int
 // (the plaintext's integer coefficients, pt null) the error becomes m + e before its NTT and
 // c0 = NTT(m + e) - c1 s: NTT(m) + NTT(e) = NTT(m + e) mod q, so the ciphertext equals that of
 // encoding m to a plaintext and encrypting it.
 template <int LOGN = 0>
-__global__ void __launch_bounds__(512) encrypt_cl_kernel(const uint64_t *__restrict__ pt, const int64_t *__restrict__ m_int, const uint64_t *__restrict__ sk_mont, int nl,
-                                  uint64_t seed, uint64_t nonce,
-                                  const uint64_t *nonce_dev, Cdt cdt, uint64_t *ct, const uint64_t *__restrict__ d_tw,
-                                  const ModConst *__restrict__ mc, int logn_rt) {
+__global__ void __launch_bounds__(512) encrypt_ntt_cl_kernel(const int64_t *__restrict__ m_int, int nl, uint64_t seed, uint64_t nonce,
+                                                             const uint64_t *nonce_dev, Cdt cdt, uint64_t *ct, const uint64_t *__restrict__ d_tw,
+                                                             const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
     if (nonce_dev) nonce = *nonce_dev;
     const int N = 1 << logn;
-    int l, off, len;
-    slice_of<true>(logn, l, off, len);
-    const uint64_t q = mc[l].q, qinv = mc[l].qinv, mu = mc[l].mu;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int l = item >> 1, which = item & 1;
+    const uint64_t q = mc[l].q, mu = mc[l].mu;
     const ulonglong2 *tw = twiddles(d_tw, l, 0, logn);
     tw_prefetch<true, true>(s, tw, logn);
-    for (int b = (off >> 1) + threadIdx.x; b < ((off + len) >> 1); b += blockDim.x) {
-        uint64_t c[4] = {(uint64_t)b, (uint64_t)l, nonce, 0};
-        philox4x64(c, seed, 2);
-        s[SIDX(2 * b - off)] = (uint64_t)((((u128)c[1]) << 64 | c[0]) % q);
-        s[SIDX(2 * b + 1 - off)] = (uint64_t)((((u128)c[3]) << 64 | c[2]) % q);
-    }
-    __syncthreads();
-    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
-    uint64_t *c1 = ct + ((int64_t)nl + l) * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) c1[k] = s[SIDX(k)];
-    __syncthreads();  // the slice is read out before the error overwrites it (twiddles stay)
-    for (int b = (off >> 2) + threadIdx.x; b < ((off + len) >> 2); b += blockDim.x) {
-        uint64_t c[4] = {(uint64_t)b, 0, nonce, 0};
-        philox4x64(c, seed, 3);
+    if (which == 0) {  // uniform residues of limb l, two per Philox block
+        for (int b = (off >> 1) + threadIdx.x; b < ((off + len) >> 1); b += blockDim.x) {
+            uint64_t c[4] = {(uint64_t)b, (uint64_t)l, nonce, 0};
+            philox4x64(c, seed, 2);
+            s[SIDX(2 * b - off)] = (uint64_t)((((u128)c[1]) << 64 | c[0]) % q);
+            s[SIDX(2 * b + 1 - off)] = (uint64_t)((((u128)c[3]) << 64 | c[2]) % q);
+        }
+    } else {  // the error (plus m), four per Philox block
+        for (int b = (off >> 2) + threadIdx.x; b < ((off + len) >> 2); b += blockDim.x) {
+            uint64_t c[4] = {(uint64_t)b, 0, nonce, 0};
+            philox4x64(c, seed, 3);
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const uint64_t r = c[w] >> 24;
-            int64_t x = -19;
-            for (int k = 0; k < 38; ++k) x += (r >= cdt.t[k]);
-            if (m_int) x += m_int[4 * b + w];
-            s[SIDX(4 * b + w - off)] = reduce_signed(x, q, mu);
+            for (int w = 0; w < 4; ++w) {
+                const uint64_t r = c[w] >> 24;
+                int64_t x = -19;
+                for (int k = 0; k < 38; ++k) x += (r >= cdt.t[k]);
+                if (m_int) x += m_int[4 * b + w];
+                s[SIDX(4 * b + w - off)] = reduce_signed(x, q, mu);
+            }
         }
     }
     __syncthreads();
     ntt_fwd_cluster<LOGN>(s, tw, q, logn);
-    const int64_t base = (int64_t)l * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        const uint64_t as = mont_mul(c1[k], sk_mont[base + k], q, qinv);
-        ct[base + k] = m_int ? sub_mod(s[SIDX(k)], as, q) : add_mod(sub_mod(pt[base + k], as, q), s[SIDX(k)], q);
+    uint64_t *o = ct + ((int64_t)(which == 0 ? nl : 0) + l) * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = s[SIDX(k)];
+}
+
+// c0 = pt - c1 s + e (pt null: c0 = (m + e) - c1 s), e (or m + e) read from the c0 slot
+__global__ void encrypt_finish_kernel(const uint64_t *__restrict__ pt, const uint64_t *__restrict__ sk_mont, int nl, uint64_t *ct,
+                                      const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
+    const int N = 1 << logn;
+    const int l = blockIdx.y;
+    const uint64_t q = mc[l].q, qinv = mc[l].qinv;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+        const int64_t i = (int64_t)l * N + k;
+        const uint64_t as = mont_mul(ct[(int64_t)nl * N + i], sk_mont[i], q, qinv);
+        ct[i] = pt ? add_mod(sub_mod(pt[i], as, q), ct[i], q) : sub_mod(ct[i], as, q);
     }
 }
 
@@ -756,13 +765,15 @@ void launch_sample_ternary(he_ctx *ctx, int64_t *out) {
 
 bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, const int64_t *m_int, int level, uint64_t nonce, const uint64_t *nonce_dev,
                           uint64_t *ct) {
-    if (!use_cluster(ctx->log_n, level + 1)) return false;
+    if (!use_cluster(ctx->log_n, 2 * (level + 1))) return false;
     Cdt c;
     for (int k = 0; k < 38; ++k) c.t[k] = ctx->cdt[k];
-    ctx->launches++;
-    launch_cluster(by_logn(ctx->log_n, [](auto L) { return encrypt_cl_kernel<L.value>; }), (level + 1) * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
-                   cl_smem_bytes(ctx->log_n), ctx->stream, pt, m_int, (const uint64_t *)ctx->d_sk_mont, level + 1, ctx->seed, nonce, nonce_dev, c, ct,
+    ctx->launches += 2;
+    launch_cluster(by_logn(ctx->log_n, [](auto L) { return encrypt_ntt_cl_kernel<L.value>; }), 2 * (level + 1) * HE_NTT_CL_SIZE,
+                   cl_threads(ctx->log_n), cl_smem_bytes(ctx->log_n), ctx->stream, m_int, level + 1, ctx->seed, nonce, nonce_dev, c, ct,
                    (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+    launch_k(encrypt_finish_kernel, dim3((ctx->n + 255) / 256, level + 1), 256, 0, ctx->stream, pt, (const uint64_t *)ctx->d_sk_mont, level + 1, ct,
+             (const ModConst *)ctx->d_mc, ctx->log_n);
     return true;
 }
 
@@ -792,7 +803,7 @@ void encode_set_smem_limits(int max_bytes) {
     each_logn([max_bytes](auto L) {
         cudaFuncSetAttribute(decrypt_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(decrypt_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(encrypt_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(encrypt_ntt_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         // cluster FFTs: the slice and the local stages' twiddles (1.5 MS float4)
         cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
