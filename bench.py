@@ -174,8 +174,7 @@ def run_gpu(args):
         if cm is not c:
             c.stream.wait_stream(cm.stream)
         c.matmult(plan, pm, [ct], out)
-        c.decrypt(out[0], slots[0])
-        c.matmult_decode(plan, slots, res)
+        c.matmult_decrypt(plan, out, res)  # decrypt, decode and lazy rotate-and-sum
 
     # encryption nonces live in device memory and advance by 2 on every step, so a replayed
     # graph never encrypts twice under one nonce

@@ -305,6 +305,11 @@ int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_c
 
 /* P_B's side after decryption: lazy rotate-and-sum (Sec. 4.3).  slots: device
  * [row_blocks][N/2] doubles (he_decrypt of each output), y_out: device m doubles. */
+/* Decryption, decoding and the lazy rotate-and-sum of a MatMult's outputs in one call:
+ * cts[0..row_blocks) (one scale), mask as he_matmult_decode_masked (device [row_blocks][N/2],
+ * may be NULL), y_out (device, m doubles).  The same doubles as he_decrypt of each ciphertext
+ * then he_matmult_decode(_masked), without the slot array (the sums run in the decoding launch). */
+int he_matmult_decrypt(he_ctx *ctx, const he_plan *plan, const he_ct *cts, int n_ct, const double *mask, double *y_out);
 int he_matmult_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out);
 /* Alg. 1's last step: remove a slot mask (device [row_blocks][N/2] doubles, the values that
  * were encoded and added with he_add_plain before decryption; NULL = none) and apply the lazy

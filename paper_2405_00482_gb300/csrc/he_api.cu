@@ -1232,6 +1232,25 @@ int he_matmult_decode_masked(he_ctx *ctx, const he_plan *plan, const double *slo
     return last_launch();
 }
 
+int he_matmult_decrypt(he_ctx *ctx, const he_plan *plan, const he_ct *cts, int n_ct, const double *mask, double *y_out) {
+    if (!ctx || !plan || !cts || !y_out || plan->slots != ctx->n / 2 || n_ct != plan->row_blocks) return HE_EINVAL;
+    for (int r = 0; r < n_ct; ++r) {
+        if (!cts[r].data) return HE_EINVAL;
+        if (cts[r].level < 0 || cts[r].level >= ctx->L) return HE_ELEVEL;
+        if (cts[r].scale != cts[0].scale) return HE_ESCALE;
+    }
+    const size_t N = ctx->n;
+    uint64_t *s = ctx_scratch(ctx, (size_t)n_ct * N + (size_t)n_ct * (N / 2));
+    if (!s) return HE_ENOMEM;
+    double *coef = reinterpret_cast<double *>(s), *slots = coef + (size_t)n_ct * N;
+    for (int r = 0; r < n_ct; ++r) launch_decrypt_coeffs(ctx, cts[r].data, cts[r].level, 1, coef + (size_t)r * N, nullptr);
+    if (!launch_decode_ras(ctx, *plan, coef, n_ct, cts[0].scale, mask, y_out)) {
+        launch_decode(ctx, coef, n_ct, cts[0].scale, slots);
+        launch_lazy_ras(ctx, *plan, slots, mask, y_out);
+    }
+    return last_launch();
+}
+
 int he_plan_ras_steps(const he_plan *p, int32_t *steps, int *n_steps) {
     if (!p || !n_steps) return HE_EINVAL;
     int n = 0;

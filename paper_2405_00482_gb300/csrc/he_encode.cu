@@ -375,9 +375,53 @@ __global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const fl
 
 // cluster per polynomial: each CTA loads the coefficients whose bit-reversed positions it holds;
 // the slot values are read from the owning CTAs
-template <int CLG, int RL, int LOGN = 0>
+// What the decode writes once the slot values are in the cluster's shared memory.  DecodeSlots:
+// slot j of plaintext `item` to out[item][j].  DecodeRas: the lazy rotate-and-sum of the rows of
+// row block `item` (Sec. 4.3), y[row] = sum over s < nb/m' of slot[b nb + t + s m'] (minus the
+// mask), each row by one thread in the order s = 0, 1, ... of lazy_ras_kernel, over the same
+// slot values, so the same doubles without the slot array.
+struct DecodeSlots {
+    double *out;
+    __device__ __forceinline__ void operator()(cg::cluster_group &cl, const float4 *a, int item, int rank, int clg, int M, int lg_ms,
+                                               const int32_t *__restrict__ slot_pos, double inv) const {
+        double *o = out + (int64_t)item * M;
+        const int per = M >> clg, MS = 1 << lg_ms;
+        for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
+            const int pos = slot_pos[j];
+            const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
+            o[j] = df_to(df{v.x, v.y}) * inv;
+        }
+    }
+};
+struct DecodeRas {
+    he_plan p;
+    const double *mask;  // [row blocks][slots] or null
+    double *y;
+    int lm, lnb, ls, lmb;  // log2 of m', nb, slots, mb
+    __device__ __forceinline__ void operator()(cg::cluster_group &cl, const float4 *a, int item, int rank, int clg, int, int lg_ms,
+                                               const int32_t *__restrict__ slot_pos, double inv) const {
+        const int MS = 1 << lg_ms;
+        const int64_t terms = p.nb >> lm;
+        for (int64_t rem = (int64_t)rank * blockDim.x + threadIdx.x; rem < p.mb; rem += (int64_t)blockDim.x << clg) {
+            const int64_t row = ((int64_t)item << lmb) + rem;
+            if (row >= p.m) break;
+            const int64_t base = ((rem >> lm) << lnb) + (rem & (p.m_prime - 1));
+            double acc = 0.0;
+            for (int64_t s = 0; s < terms; ++s) {
+                const int64_t j = base + (s << lm);
+                const int pos = slot_pos[j];
+                const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
+                const double val = df_to(df{v.x, v.y}) * inv;
+                acc += mask ? val - mask[((int64_t)item << ls) + j] : val;
+            }
+            y[row] = acc;
+        }
+    }
+};
+
+template <int CLG, int RL, int LOGN, class EPI>
 __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
-                                 const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, double *out, int logn_rt) {
+                                 const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, EPI epi, int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
@@ -396,14 +440,7 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
     }
     __syncthreads();
     fft_cluster<CLG, RL, LOGN ? LOGN - 1 : 0>(a, tw, logm, +1);
-    double *o = out + (int64_t)item * M;
-    const double inv = 1.0 / scale;
-    const int per = M >> CLG;
-    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
-        const int pos = slot_pos[j];
-        const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
-        o[j] = df_to(df{v.x, v.y}) * inv;
-    }
+    epi(cl, a, item, rank, CLG, M, lg_ms, slot_pos, 1.0 / scale);
     cl.sync();  // the other CTAs read this one's shared memory until here
 }
 
@@ -725,12 +762,46 @@ void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, d
     const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
     ctx->launches++;
     switch (fft_cluster_log(ctx->log_n, count)) {
-        case 3: launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<3, 1, L.value>; }), ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
-        case 2: launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<2, 1, L.value>; }), ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
-        case 1: launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<1, 1, L.value>; }), ctx, count, coeffs, scale, tw, twist, pos, slots, ctx->log_n); return;
+        case 3:
+            launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<3, 1, L.value, DecodeSlots>; }), ctx, count, coeffs, scale, tw,
+                                twist, pos, DecodeSlots{slots}, ctx->log_n);
+            return;
+        case 2:
+            launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<2, 1, L.value, DecodeSlots>; }), ctx, count, coeffs, scale, tw,
+                                twist, pos, DecodeSlots{slots}, ctx->log_n);
+            return;
+        case 1:
+            launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<1, 1, L.value, DecodeSlots>; }), ctx, count, coeffs, scale, tw,
+                                twist, pos, DecodeSlots{slots}, ctx->log_n);
+            return;
         default: break;
     }
     launch_k(decode_kernel, count, FFT_THREADS, fft_smem_bytes(ctx->log_n), ctx->stream, coeffs, scale, tw, twist, pos, slots, ctx->log_n);
+}
+
+bool launch_decode_ras(he_ctx *ctx, const he_plan &p, const double *coeffs, int count, double scale, const double *mask, double *y) {
+    const float4 *tw = reinterpret_cast<const float4 *>(ctx->d_fft);
+    const float4 *twist = tw + ctx->n / 4;
+    const int32_t *pos = reinterpret_cast<const int32_t *>(twist + ctx->n / 2);
+    auto lg = [](int64_t v) { return __builtin_ctzll((unsigned long long)v); };
+    const DecodeRas epi{p, mask, y, lg(p.m_prime), lg(p.nb), lg(p.slots), lg(p.mb)};
+    switch (fft_cluster_log(ctx->log_n, count)) {
+        case 3:
+            launch_fft_cl<3, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<3, 1, L.value, DecodeRas>; }), ctx, count, coeffs, scale, tw, twist,
+                                pos, epi, ctx->log_n);
+            break;
+        case 2:
+            launch_fft_cl<2, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<2, 1, L.value, DecodeRas>; }), ctx, count, coeffs, scale, tw, twist,
+                                pos, epi, ctx->log_n);
+            break;
+        case 1:
+            launch_fft_cl<1, 1>(by_logn(ctx->log_n, [](auto L) { return decode_cl_kernel<1, 1, L.value, DecodeRas>; }), ctx, count, coeffs, scale, tw, twist,
+                                pos, epi, ctx->log_n);
+            break;
+        default: return false;
+    }
+    ctx->launches++;
+    return true;
 }
 
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *) {
@@ -807,10 +878,12 @@ void encode_set_smem_limits(int max_bytes) {
         // cluster FFTs: the slice and the local stages' twiddles (1.5 MS float4)
         cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<1, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(decode_cl_kernel<1, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<1, 1, L.value, DecodeSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<1, 1, L.value, DecodeRas>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<2, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(decode_cl_kernel<2, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<2, 1, L.value, DecodeSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<2, 1, L.value, DecodeRas>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_cl_kernel<3, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value, SlotsSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
@@ -822,6 +895,7 @@ void encode_set_smem_limits(int max_bytes) {
         cudaFuncSetAttribute(encode_pair_cl_kernel<1, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<2, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(encode_pair_cl_kernel<3, 1, L.value, VectorSrc>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(decode_cl_kernel<3, 1, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<3, 1, L.value, DecodeSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(decode_cl_kernel<3, 1, L.value, DecodeRas>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     });
 }

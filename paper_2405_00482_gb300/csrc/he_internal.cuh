@@ -380,6 +380,9 @@ bool launch_encode_matrix(he_ctx *ctx, const he_plan &p, const double *X, int tr
 bool launch_encode_vector(he_ctx *ctx, const he_plan &p, const double *y, int count, double scale, int64_t *coeffs);
 void launch_decode(he_ctx *ctx, const double *coeffs, int count, double scale, double *slots);
 void launch_decrypt_coeffs(he_ctx *ctx, const uint64_t *ct, int level, int count, double *coeffs, uint64_t *tmp);
+// decode of `count` decrypted coefficient vectors (the row blocks' output ciphertexts) with the lazy
+// rotate-and-sum of the plan in the same launch, into y [m]; false where that form does not apply
+bool launch_decode_ras(he_ctx *ctx, const he_plan &p, const double *coeffs, int count, double scale, const double *mask, double *y);
 // he_encrypt's five steps as one cluster launch per limb (false: that form does not apply); with
 // m_int (integer coefficients, pt null) the plaintext is encoded into the same launch
 bool launch_encrypt_fused(he_ctx *ctx, const uint64_t *pt, const int64_t *m_int, int level, uint64_t nonce, const uint64_t *nonce_dev,

@@ -54,6 +54,7 @@ _SIGS = {
     "he_encrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _u64, ctypes.POINTER(HeCt)]),
     "he_encrypt_dnonce": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp, ctypes.POINTER(HeCt)]),
     "he_encrypt_vector": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _u64, _vp, _vp]),
+    "he_matmult_decrypt": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "he_decrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_add": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(HeCt)]),
     "he_add_plain": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), ctypes.POINTER(HePt), ctypes.POINTER(HeCt)]),
@@ -631,6 +632,18 @@ class Context:
             mask = _dev(mask, torch.float64)
             _check(_lib().he_matmult_decode_masked(self.handle, plan.handle, slots.data_ptr(), mask.data_ptr(), out.data_ptr()),
                    "he_matmult_decode_masked")
+        return out
+
+    def matmult_decrypt(self, plan: Plan, cts: list[Ciphertext], out: torch.Tensor | None = None,
+                        mask: torch.Tensor | None = None) -> torch.Tensor:
+        """decrypt of each output ciphertext then matmult_decode in one call (he_matmult_decrypt)."""
+        out = out if out is not None else torch.empty(plan.m, dtype=torch.float64, device=self.device)
+        arr = (HeCt * len(cts))(*[c.c() for c in cts])
+        mp = None
+        if mask is not None:
+            mask = _dev(mask, torch.float64)
+            mp = _vp(mask.data_ptr())
+        _check(_lib().he_matmult_decrypt(self.handle, plan.handle, arr, len(cts), mp, _vp(out.data_ptr())), "he_matmult_decrypt")
         return out
 
     # ---- VFL-NN forward pass with the encrypted matrix diagonally encoded (Alg. 3) ----

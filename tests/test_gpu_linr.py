@@ -145,3 +145,29 @@ def test_vfl_linr_gradient_step_n8192(he):
     want = XA.T @ (uA + uB - y)
     assert np.abs(grad - want).max() < TOL
     assert np.abs(ctx.matmult_decode(pg, slots).cpu().numpy() - want).max() > 1.0
+
+
+@pytest.mark.parametrize("log_n,m,n", [(5, 4, 4), (5, 40, 8), (13, 256, 1024), (13, 1024, 256), (13, 9000, 64), (13, 300, 5000)])
+def test_matmult_decrypt_equals_decrypt_then_decode(he, log_n, m, n):
+    """he_matmult_decrypt (decoding and lazy RaS in one launch at N >= 2^10) gives the doubles of
+    decrypt on every output then matmult_decode(_masked), bit for bit."""
+    import torch
+
+    ctx, o = _ctx_pair(he, log_n, 31)
+    rng = np.random.default_rng(m + 7 * n)
+    X, y = rng.normal(size=(m, n)), rng.uniform(-1, 1, n)
+    D, level = 2.0**40, 2
+    plan = he.Plan(m, n, o.slots)
+    ctx.keygen(list(range(1, plan.m_prime)))
+    pm = ctx.encode_matrix(plan, torch.from_numpy(X).cuda(), level)
+    cts = ctx.encrypt_vector(plan, torch.from_numpy(y).cuda(), D, level, 5)
+    outs = ctx.matmult(plan, pm, cts)
+    slots = torch.stack([ctx.decrypt(c) for c in outs])
+    mask = torch.from_numpy(rng.uniform(-10, 10, size=(plan.row_blocks, o.slots))).cuda()
+    for mk in (None, mask):
+        want = ctx.matmult_decode(plan, slots, mask=mk).cpu().numpy()
+        got = ctx.matmult_decrypt(plan, outs, mask=mk).cpu().numpy()
+        assert np.array_equal(got, want)
+    assert np.abs(ctx.matmult_decrypt(plan, outs).cpu().numpy() - X @ y).max() < TOL
+    with pytest.raises(he.HEError):
+        ctx.matmult_decrypt(plan, outs[:-1] if len(outs) > 1 else outs + outs)
