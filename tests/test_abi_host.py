@@ -93,3 +93,17 @@ def test_loop_variant_table_and_argument_checks(he):
 @pytest.mark.parametrize("m,n,slots", [(4, 4, 8), (16, 64, 2048), (256, 1024, 4096), (3, 5, 8), (1, 8, 16), (5000, 300, 4096)])
 def test_ras_steps_agree_with_oracle(he, m, n, slots):
     assert he.Plan(m, n, slots).ras_steps == layout.ras_steps(layout.make_plan(m, n, slots))
+
+
+def test_new_entry_points_reject_null_arguments(he):
+    """Context forks, device-nonce encryption, vector encryption, transposed matrix encoding and
+    the fused decryption check their arguments before any device work (no GPU needed)."""
+    lib = he.lib()
+    out = ctypes.c_void_p()
+    assert lib.he_ctx_fork(None, None, ctypes.byref(out)) == he.HE_EINVAL
+    assert lib.he_ctx_fork(None, None, None) == he.HE_EINVAL
+    assert lib.he_encrypt_dnonce(None, None, None, None) == he.HE_EINVAL
+    assert lib.he_encrypt_vector(None, None, None, 1.0, 0, 0, None, None) == he.HE_EINVAL
+    assert lib.he_encode_matrix_transposed(None, None, None, 1, ctypes.byref(out)) == he.HE_EINVAL
+    assert lib.he_ptmat_encode_transposed(None, None, None) == he.HE_EINVAL
+    assert lib.he_matmult_decrypt(None, None, None, 0, None, None) == he.HE_EINVAL
