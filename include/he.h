@@ -273,7 +273,9 @@ int he_server_create(he_ctx *ctx, int slots, int level, size_t hbm_budget_bytes,
  * data when the request completes. */
 int he_server_submit(he_server *s, const he_plan *plan, const he_ptmat *pm, const he_ct *in, he_ct *out, int64_t *request_id);
 /* Block until the request completes (its output is then ready for any stream) or timeout_us
- * passes (HE_ETIMEOUT); latency_s (optional) = completion - submission, host clock. */
+ * passes (HE_ETIMEOUT); latency_s (optional) = completion - submission, host clock.  Once it
+ * has returned the request's status, the server forgets the request: a second wait on the same
+ * id returns HE_EINVAL.  After HE_ETIMEOUT the request is still known and can be waited for again. */
 int he_server_wait(he_server *s, int64_t request_id, int64_t timeout_us, double *latency_s);
 int he_server_stats(he_server *s, int64_t *completed, int64_t *launches, size_t *bytes_in_use);
 /* Finishes every queued request, stops the scheduler and releases the lanes. */
@@ -302,6 +304,10 @@ int he_cdiag_decode(he_ctx *ctx, int64_t m, int64_t n, int64_t K, const double *
  * when m >= n, r = (-k) mod n when m < n (the printed RotR form does not give A^T's diagonals).
  * Needs the Galois keys of those steps (HE_EKEY otherwise); outs must not alias cts. */
 int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_ct *outs);
+/* Host only: the distinct nonzero rotation steps he_cdiag_transpose uses for an m x n matrix
+ * (the Galois keys to make first), ascending; steps may be NULL to count them (at most
+ * min(m, n) - 1). */
+int he_cdiag_transpose_steps(int64_t m, int64_t n, int32_t *steps, int *n_steps);
 
 /* P_B's side after decryption: lazy rotate-and-sum (Sec. 4.3).  slots: device
  * [row_blocks][N/2] doubles (he_decrypt of each output), y_out: device m doubles. */
@@ -325,6 +331,47 @@ int he_matmult_decode_masked(he_ctx *ctx, const he_plan *plan, const double *slo
 int he_plan_ras_steps(const he_plan *plan, int32_t *steps, int *n_steps);
 int he_ras(he_ctx *ctx, const he_plan *plan, const he_ct *in, he_ct *out);
 int he_ras_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out);
+
+/* Host-memory forms of the party-facing calls (the problem statement of Sec. 3 and Alg. 1: P_A
+ * holds the cleartext X, P_B encrypts y and decrypts the product, ciphertexts travel between the
+ * parties as bytes).  Each takes its bulk inputs from and writes its results to HOST memory and
+ * otherwise equals its device-memory counterpart above, bit for bit.  Inputs are copied on the
+ * context's stream with one copy per buffer: from page-locked memory (cudaMallocHost,
+ * cudaHostRegister) the copy is asynchronous, so the buffer must stay unchanged until the stream
+ * has passed it; from pageable memory the library first copies into its own page-locked staging
+ * (a stream capture of such a call returns HE_EINVAL).  Results: into page-locked memory the copy
+ * is queued and the values are valid once the stream reaches it (he_synchronize); into pageable
+ * memory the call waits and the values are valid on return.  The staging buffers belong to the
+ * context (a fork has its own) and grow on demand.
+ *
+ * he_encode_matrix_host / he_ptmat_encode_host: X host row-major m x n doubles (its transpose,
+ * n x m, when transposed != 0), as he_encode_matrix(_transposed) / he_ptmat_encode(_transposed).
+ * he_encrypt_vector_host: y host, n doubles, as he_encrypt_vector.
+ * he_decrypt_host: N/2 slot values into host memory, as he_decrypt.
+ * he_matmult_decrypt_host: mask host [row_blocks][N/2] doubles or NULL, y host m doubles, as
+ * he_matmult_decrypt. */
+int he_encode_matrix_host(he_ctx *ctx, const he_plan *plan, const double *X, int level, int transposed, he_ptmat **out);
+int he_ptmat_encode_host(he_ctx *ctx, he_ptmat *pm, const double *X, int transposed);
+int he_encrypt_vector_host(he_ctx *ctx, const he_plan *plan, const double *y, double scale, int level, uint64_t nonce,
+                           const uint64_t *nonce_dev, he_ct *outs);
+int he_decrypt_host(he_ctx *ctx, const he_ct *ct, double *slots);
+int he_matmult_decrypt_host(he_ctx *ctx, const he_plan *plan, const he_ct *cts, int n_ct, const double *mask, double *y);
+
+/* A ciphertext as bytes in host memory, for transport between parties (Alg. 1: [[d]] and the
+ * masked gradients cross the network).  Layout, little-endian: a 32-byte header (uint32 magic
+ * "HECT", uint32 version 1, int32 log_n, int32 level, double scale, 8 reserved bytes), the
+ * level+1 primes q_0..q_level (uint64), then [2][level+1][N] uint64 canonical coefficients
+ * (coefficient form, so the bytes do not depend on the NTT ordering).
+ * he_ct_export_host: with buf == NULL writes the byte count to *len; else *len is buf's capacity
+ * (HE_EINVAL, with the needed count in *len, if too small) and on return holds the bytes written.
+ * Synchronises: the bytes are complete on return.
+ * he_ct_host_level: the level stored in a buffer (to size the import's device buffer).
+ * he_ct_import_host: checks the header, that log_n and the primes are this context's and that
+ * every coefficient is canonical (HE_EINVAL otherwise, HE_ELEVEL for a level the context lacks);
+ * out->data (device) must hold he_ct_bytes(level) bytes; sets out's level and scale. */
+int he_ct_export_host(he_ctx *ctx, const he_ct *ct, void *buf, size_t *len);
+int he_ct_host_level(const void *buf, size_t len, int32_t *level);
+int he_ct_import_host(he_ctx *ctx, const void *buf, size_t len, he_ct *out);
 
 /* Canonical coefficient form (device, [2][level+1][N]) of a ciphertext, and back. */
 int he_ct_export(he_ctx *ctx, const he_ct *ct, uint64_t *coeffs_out);

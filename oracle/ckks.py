@@ -69,6 +69,8 @@ def lib():
             "or_rotate_hoisted": (None, [P, i32, _u64p, i32, _u64p, _u64p, _u64p]),
             "or_matmult_double": (None, [P, i32, _u64p, i32, _u64p, _u64p, _u64p, _u64p]),
             "or_rescale": (None, [P, i32, _u64p, _u64p]),
+            "or_max_threads": (i32, []),
+            "or_set_threads": (None, [i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

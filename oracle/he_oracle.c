@@ -21,6 +21,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef unsigned __int128 u128;
 
@@ -40,6 +43,25 @@ uint64_t or_powmod(uint64_t a, uint64_t e, uint64_t q) {
         e >>= 1;
     }
     return r;
+}
+
+/* Threads of the OpenMP loops below (1 when built without OpenMP).  Only loops whose
+ * iterations are independent, or whose partial results are combined by exact modular sums,
+ * are parallel, so results do not depend on the thread count. */
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 /* inverse modulo a prime q (Fermat) */
@@ -500,9 +522,8 @@ void or_matmult_double(const or_params *p, int level, const uint64_t *ct, int n_
     int n = p->n, nl = level + 1, ext = nl + p->K, nd = ndigits_at(p, level);
     size_t key_words = (size_t)p->dnum * 2 * (p->L + p->K) * n;
     uint64_t *D = malloc(sizeof(uint64_t) * (size_t)nd * ext * n);
-    uint64_t *u0 = malloc(sizeof(uint64_t) * (size_t)ext * n), *u1 = malloc(sizeof(uint64_t) * (size_t)ext * n);
     uint64_t *acc0 = calloc((size_t)ext * n, sizeof(uint64_t)), *acc1 = calloc((size_t)ext * n, sizeof(uint64_t));
-    uint64_t *v = malloc(sizeof(uint64_t) * (size_t)nl * n), *tmp = malloc(sizeof(uint64_t) * n), *rc = malloc(sizeof(uint64_t) * n);
+    uint64_t *v = malloc(sizeof(uint64_t) * (size_t)nl * n), *tmp = malloc(sizeof(uint64_t) * n);
     const uint64_t *c0 = ct, *c1 = ct + (size_t)nl * n;
     uint64_t *o0 = out, *o1 = out + (size_t)nl * n;
     memset(out, 0, sizeof(uint64_t) * 2 * (size_t)nl * n);
@@ -513,20 +534,40 @@ void or_matmult_double(const or_params *p, int level, const uint64_t *ct, int n_
         mul_into(n, q, c1 + (size_t)l * n, pts_qp + (size_t)l * n, o1 + (size_t)l * n, tmp);
     }
     if (n_pt > 1) or_modup(p, level, c1, D);
-    for (int i = 1; i < n_pt; ++i) {
-        uint64_t g = galois[i - 1];
-        const uint64_t *pt = pts_qp + (size_t)i * ext * n;
-        ks_inner(p, level, D, g, evks + (size_t)(i - 1) * key_words, u0, u1);
-        for (int u = 0; u < ext; ++u) {
-            uint64_t t = qp_prime(p, level, u);
-            mul_into(n, t, u0 + (size_t)u * n, pt + (size_t)u * n, acc0 + (size_t)u * n, tmp);
-            mul_into(n, t, u1 + (size_t)u * n, pt + (size_t)u * n, acc1 + (size_t)u * n, tmp);
+    /* i >= 1: each thread sums its diagonals into its own accumulators, which are then added
+     * (modular sums: the result does not depend on the split) */
+#pragma omp parallel
+    {
+        uint64_t *u0 = malloc(sizeof(uint64_t) * (size_t)ext * n), *u1 = malloc(sizeof(uint64_t) * (size_t)ext * n);
+        uint64_t *a0 = calloc((size_t)ext * n, sizeof(uint64_t)), *a1 = calloc((size_t)ext * n, sizeof(uint64_t));
+        uint64_t *b0 = calloc((size_t)nl * n, sizeof(uint64_t));
+        uint64_t *t = malloc(sizeof(uint64_t) * n), *rc = malloc(sizeof(uint64_t) * n);
+#pragma omp for schedule(dynamic, 1)
+        for (int i = 1; i < n_pt; ++i) {
+            uint64_t g = galois[i - 1];
+            const uint64_t *pt = pts_qp + (size_t)i * ext * n;
+            ks_inner(p, level, D, g, evks + (size_t)(i - 1) * key_words, u0, u1);
+            for (int u = 0; u < ext; ++u) {
+                uint64_t tq = qp_prime(p, level, u);
+                mul_into(n, tq, u0 + (size_t)u * n, pt + (size_t)u * n, a0 + (size_t)u * n, t);
+                mul_into(n, tq, u1 + (size_t)u * n, pt + (size_t)u * n, a1 + (size_t)u * n, t);
+            }
+            for (int l = 0; l < nl; ++l) {
+                uint64_t q = p->primes[l];
+                or_automorph(n, q, g, c0 + (size_t)l * n, rc);
+                mul_into(n, q, rc, pt + (size_t)l * n, b0 + (size_t)l * n, t);
+            }
         }
-        for (int l = 0; l < nl; ++l) {
-            uint64_t q = p->primes[l];
-            or_automorph(n, q, g, c0 + (size_t)l * n, rc);
-            mul_into(n, q, rc, pt + (size_t)l * n, o0 + (size_t)l * n, tmp);
+#pragma omp critical
+        {
+            for (size_t w = 0; w < (size_t)ext * n; ++w) {
+                uint64_t tq = qp_prime(p, level, (int)(w / n));
+                acc0[w] = addmod(acc0[w], a0[w], tq);
+                acc1[w] = addmod(acc1[w], a1[w], tq);
+            }
+            for (size_t w = 0; w < (size_t)nl * n; ++w) o0[w] = addmod(o0[w], b0[w], p->primes[w / n]);
         }
+        free(u0); free(u1); free(a0); free(a1); free(b0); free(t); free(rc);
     }
     if (n_pt > 1) {
         or_moddown(p, level, acc0, v);
@@ -534,7 +575,7 @@ void or_matmult_double(const or_params *p, int level, const uint64_t *ct, int n_
         or_moddown(p, level, acc1, v);
         for (size_t w = 0; w < (size_t)nl * n; ++w) o1[w] = addmod(o1[w], v[w], p->primes[w / n]);
     }
-    free(D); free(u0); free(u1); free(acc0); free(acc1); free(v); free(tmp); free(rc);
+    free(D); free(acc0); free(acc1); free(v); free(tmp);
 }
 
 /*

@@ -177,7 +177,7 @@ static int set_smem_limits_once() {
     return HE_OK;
 }
 
-static uint32_t galois_of(const he_ctx *ctx, int64_t step) {
+uint32_t galois_of(const he_ctx *ctx, int64_t step) {
     const int64_t slots = ctx->n / 2;
     int64_t r = ((step % slots) + slots) % slots;
     return (uint32_t)hpow(5, (uint64_t)r, 2ull * ctx->n);
@@ -231,6 +231,9 @@ void he_ctx_destroy(he_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->scratch);  // the tables and keys go with the family's last context (he_shared)
+    cudaFree(ctx->stage_dev);
+    cudaFreeHost(ctx->stage_host);
+    if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
     delete ctx;
 }
@@ -251,6 +254,10 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     ctx->alpha = (p->n_q + p->dnum - 1) / p->dnum;
     ctx->seed = seed;
     ctx->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return HE_ECUDA;
+    }
     rc = prime_chain(p->log_n, all_bits(p), ctx->primes);
     if (rc != HE_OK) {
         delete ctx;
@@ -446,6 +453,7 @@ int he_ctx_fork(he_ctx *parent, void *stream, he_ctx **out) {
     ctx->K = parent->K;
     ctx->dnum = parent->dnum;
     ctx->alpha = parent->alpha;
+    ctx->device = parent->device;
     ctx->seed = parent->seed;
     ctx->stream = (cudaStream_t)stream;
     ctx->primes = parent->primes;
@@ -660,25 +668,42 @@ int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, int k,
     if (!ctx || !in || !in->data || k < 0 || (k > 0 && (!steps || !outs))) return HE_EINVAL;
     const int level = in->level;
     if (level < 0 || level >= ctx->L) return HE_ELEVEL;
-    std::vector<const uint64_t *> keys(k);
+    const size_t N = ctx->n, nl = level + 1, ct_words = 2 * nl * N;
+    std::vector<RotJob> jobs;
+    jobs.reserve(k);
+    std::vector<int> copies;
     for (int i = 0; i < k; ++i) {
-        if (!outs[i].data || outs[i].data == in->data) return HE_EINVAL;
-        keys[i] = ctx->sh->key(galois_of(ctx, steps[i]));
-        if (!keys[i]) return HE_EKEY;
-    }
-    if (k == 0) return HE_OK;
-    const ModUpConst &mu = ctx->modup[level];
-    const size_t N = ctx->n, nl = level + 1, ext = mu.ext;
-    const size_t wD = mu.ndig * ext * N, wc = nl * N, wu = 2 * ext * N, wr = nl * N, wt = 2 * ctx->K * N;
-    uint64_t *s = ctx_scratch(ctx, wD + wc + wu + wr + wt);
-    if (!s) return HE_ENOMEM;
-    uint64_t *D = s, *coef = D + wD, *u = coef + wc, *rc0 = u + wu, *tmp = rc0 + wr;
-    launch_modup(ctx, in->data + nl * N, level, D, coef);
-    for (int i = 0; i < k; ++i) {
+        // an output must not overlap the input, whose c0 every rotation still reads
+        if (!outs[i].data || (outs[i].data < in->data + ct_words && in->data < outs[i].data + ct_words)) return HE_EINVAL;
+        const int64_t half = ctx->n / 2;
+        if (((int64_t)steps[i] % half + half) % half == 0) {  // RotL by a multiple of N/2 is the identity
+            copies.push_back(i);
+            continue;
+        }
         const uint32_t g = galois_of(ctx, steps[i]);
-        launch_ks_inner(ctx, D, level, g, keys[i], u);
-        launch_automorph(ctx, in->data, rc0, 1, qmap(level), g);
-        launch_moddown(ctx, u, level, 2, rc0, nullptr, outs[i].data, tmp);
+        const uint64_t *key = ctx->sh->key(g);
+        if (!key) return HE_EKEY;
+        jobs.push_back(RotJob{in->data, outs[i].data, key, g, 0});
+    }
+    for (int i : copies)
+        if (cudaMemcpyAsync(outs[i].data, in->data, ct_words * sizeof(uint64_t), cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            return HE_ECUDA;
+    const int n_jobs = (int)jobs.size();
+    if (n_jobs > 0) {
+        // one ModUp of c1 (O4), then every rotation's key switch in two launches
+        const ModUpConst &mu = ctx->modup[level];
+        const size_t wD = (size_t)mu.ndig * mu.ext * N, wc = nl * N, wp = keyswitch_many_pc_words(ctx, n_jobs);
+        const size_t job_words = (sizeof(RotJob) * (size_t)n_jobs + 7) / 8;
+        uint64_t *s = ctx_scratch(ctx, wD + wc + wp + job_words);
+        if (!s) return HE_ENOMEM;
+        uint64_t *D = s, *coef = D + wD, *pc = coef + wc;
+        RotJob *d_jobs = reinterpret_cast<RotJob *>(pc + wp);
+        // from pageable memory the copy stages the table before returning, so `jobs` may go
+        if (cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(RotJob) * n_jobs, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) return HE_ECUDA;
+        launch_modup(ctx, in->data + nl * N, level, D, coef);
+        launch_keyswitch_many(ctx, d_jobs, n_jobs, level, D, 0, pc);
+    }
+    for (int i = 0; i < k; ++i) {
         outs[i].level = level;
         outs[i].scale = in->scale;
     }

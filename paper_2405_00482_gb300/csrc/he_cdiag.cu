@@ -317,14 +317,42 @@ int he_cdiag_matmult(he_ctx *ctx, const he_cdmat *W, const he_ct *cts, int n_ct,
     return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
 }
 
+}  // extern "C"
+
+// Eq. 5 as read: A^T's diagonal i is RotL(e_k, r) with k = (-i) mod min(m, n) and r = i when
+// m >= n, r = (-k) mod n when m < n
+static void transpose_source(int64_t m, int64_t n, int64_t i, int64_t *k, int64_t *r) {
+    const int64_t lo = std::min(m, n);
+    *k = (lo - i) % lo;
+    *r = m >= n ? i : (n - *k) % n;
+}
+
+extern "C" {
+
+int he_cdiag_transpose_steps(int64_t m, int64_t n, int32_t *steps, int *n_steps) {
+    if (!n_steps || !pow2(m) || !pow2(n) || std::max(m, n) > ((int64_t)1 << 30)) return HE_EINVAL;
+    const int64_t lo = std::min(m, n);
+    std::vector<int32_t> out;
+    for (int64_t i = 0; i < lo; ++i) {
+        int64_t k, r;
+        transpose_source(m, n, i, &k, &r);
+        if (r) out.push_back((int32_t)r);
+    }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    if (steps)
+        for (size_t t = 0; t < out.size(); ++t) steps[t] = out[t];
+    *n_steps = (int)out.size();
+    return HE_OK;
+}
+
 int he_cdiag_transpose(he_ctx *ctx, const he_ct *cts, int64_t m, int64_t n, he_ct *outs) {
     if (!ctx || !cts || !outs || !pow2(m) || !pow2(n) || std::max(m, n) > ctx->n / 2) return HE_EINVAL;
     const int64_t lo = std::min(m, n);
-    // e'_i = RotL(e_k, r): k = (-i) mod lo; r = i (m >= n) or (-k) mod n (m < n)
     std::vector<std::pair<int64_t, int32_t>> kr((size_t)lo);
     for (int64_t i = 0; i < lo; ++i) {
-        const int64_t k = (lo - i) % lo;
-        const int64_t r = m >= n ? i : (n - k) % n;
+        int64_t k, r;
+        transpose_source(m, n, i, &k, &r);
         kr[(size_t)i] = {k, (int32_t)r};
         if (!cts[k].data || !outs[i].data || outs[i].data == cts[k].data) return HE_EINVAL;
         if (cts[k].level != cts[0].level) return HE_ELEVEL;

@@ -140,6 +140,7 @@ struct he_shared {
 
 struct he_ctx {
     int log_n, n, L, K, dnum, alpha;
+    int device;                       // CUDA device the context was created on (current at he_ctx_create)
     uint64_t seed;
     cudaStream_t stream;
     std::vector<uint64_t> primes;     // Q then P
@@ -158,6 +159,14 @@ struct he_ctx {
     uint64_t *scratch;
     size_t scratch_words;
     int batch_variant = 0;            // last variant a batch tuned to (used by serving lanes)
+    // staging of the host-memory entry points (he_host.cu), grown on demand: a device buffer for
+    // inputs and results, a page-locked host buffer for copies from or to pageable memory, and
+    // an event recorded after the last copy out of the host buffer
+    void *stage_dev = nullptr;
+    size_t stage_dev_bytes = 0;
+    void *stage_host = nullptr;
+    size_t stage_host_bytes = 0;
+    cudaEvent_t stage_ev = nullptr;
     // kernels launched so far, and CUDA-event timing of the MatMult loop kernel when enabled
     int64_t launches;
     bool prof_on;
@@ -258,6 +267,11 @@ int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
 // words of scratch per rotation job at `level`, and the launches of `count` jobs (device table)
 size_t rotate_many_words(const he_ctx *ctx, int level);
 void launch_rotate_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, uint64_t *scratch);
+// key switch (inner product, ModDown, automorphism of c0) of `count` rotations whose ModUp digits
+// are at D + j d_stride (d_stride 0: one shared decomposition), two launches; pc: scratch of
+// keyswitch_many_pc_words(ctx, count) words
+size_t keyswitch_many_pc_words(const he_ctx *ctx, int count);
+void launch_keyswitch_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc);
 int mm_variant_count();
 int mm_variant_tile(int v);  // coefficients per tile of loop-kernel variant v
 void mm_variant_shape(int v, int *vec, int *grp, int *stages, int *ga);
@@ -326,6 +340,8 @@ inline cudaError_t launch_cluster(void (*kernel)(KArgs...), int grid, int block,
 // launchers (all asynchronous on ctx->stream)
 // ------------------------------------------------------------------------------------------
 int he_check(cudaError_t e);
+// Galois element 5^r mod 2N of a left rotation by `step` slots, r = step mod N/2 in [0, N/2)
+uint32_t galois_of(const he_ctx *ctx, int64_t step);
 uint64_t *ctx_scratch(he_ctx *ctx, size_t words);  // nullptr on allocation failure
 
 // NTT of `groups` x map.n limb-polys; in and out may alias.

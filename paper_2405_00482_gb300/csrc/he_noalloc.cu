@@ -42,25 +42,24 @@ __global__ void fill_key_table_kernel(KeyChunk kc, int64_t n_steps) {
     }
 }
 
-int scratch_address(uint64_t **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HE_ECUDA;
+// The device address is looked up with the context's device current (the calling thread's
+// current device is restored afterwards), so a context on another GPU gets its own copy.
+int scratch_address(const he_ctx *ctx, uint64_t **out) {
+    const int dev = ctx->device;
+    if (dev < 0 || dev >= 64) return HE_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_addr[dev]) {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) return HE_ECUDA;
+        if (cur != dev && cudaSetDevice(dev) != cudaSuccess) return HE_ECUDA;
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HE_ECUDA;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (cur != dev) cudaSetDevice(cur);
+        if (e != cudaSuccess || !p) return HE_ECUDA;
         g_addr[dev] = static_cast<uint64_t *>(p);
     }
     *out = g_addr[dev];
     return HE_OK;
-}
-
-uint32_t galois_elem(const he_ctx *ctx, int64_t step) {
-    const uint64_t two_n = 2ull * ctx->n;
-    uint64_t r = 1, b = 5, e = (uint64_t)(step % (ctx->n / 2));
-    for (; e; e >>= 1, b = b * b % two_n)
-        if (e & 1) r = r * b % two_n;
-    return (uint32_t)r;
 }
 
 }  // namespace
@@ -90,9 +89,9 @@ extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan,
     const size_t need = w_tab_al + wD + wc + wa + wcc + wsum + wt;
     if (need > HE_NOALLOC_WORDS) return HE_EBUDGET;  // larger than the fixed 16 MiB array
     for (size_t i = 0; i < steps; ++i)
-        if (!ctx->sh->key(galois_elem(ctx, (int64_t)i + 1))) return HE_EKEY;
+        if (!ctx->sh->key(galois_of(ctx, (int64_t)i + 1))) return HE_EKEY;
     uint64_t *base = nullptr;
-    int rc = scratch_address(&base);
+    int rc = scratch_address(ctx, &base);
     if (rc != HE_OK) return rc;
     // the key table: kernel parameters carry the pointers, so nothing is staged through host memory
     for (size_t first = 0; first < steps; first += 128) {
@@ -100,7 +99,7 @@ extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan,
         kc.first = (int32_t)first;
         kc.count = (int32_t)(steps - first < 128 ? steps - first : 128);
         for (int t = 0; t < kc.count; ++t) {
-            const uint32_t g = galois_elem(ctx, (int64_t)(first + t) + 1);
+            const uint32_t g = galois_of(ctx, (int64_t)(first + t) + 1);
             kc.galois[t] = g;
             kc.key[t] = ctx->sh->key(g);
         }

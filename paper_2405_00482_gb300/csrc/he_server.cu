@@ -85,8 +85,9 @@ void finish(he_server *s, int64_t id, int status) {
     }
 }
 
-// one scheduling pass; returns true when something changed.  Called with s->mu held.
-bool schedule(he_server *s) {
+// one scheduling pass; returns true when something changed.  Called with s->mu held by `lock`
+// (released around a plain-mode product).
+bool schedule(he_server *s, std::unique_lock<std::mutex> &lock) {
     bool changed = false;
     if (s->plain) {
         // plain: one request per call on the context's stream, strictly in order
@@ -111,7 +112,15 @@ bool schedule(he_server *s) {
             Req &r = s->reqs[id];
             r.state = 2;
             r.t_start = now_s();
-            int rc = he_matmult_plain_cipher(s->ctx, r.plan, r.pm, &r.in, 1, &r.out, 1);
+            // the call (whose first use of a matrix also tunes its loop kernel, synchronising the
+            // stream) runs without the lock, so submit and wait are never held up by it; only this
+            // thread touches r's inputs meanwhile, and map references stay valid across inserts
+            const he_plan *plan = r.plan;
+            const he_ptmat *pm = r.pm;
+            he_ct in = r.in, out = r.out;
+            lock.unlock();
+            int rc = he_matmult_plain_cipher(s->ctx, plan, pm, &in, 1, &out, 1);
+            lock.lock();
             if (rc != HE_OK) {
                 finish(s, id, rc);
             } else {
@@ -176,9 +185,12 @@ bool schedule(he_server *s) {
 }
 
 void worker_main(he_server *s) {
+    // the scheduler's launches, events and graph replays belong to the context's device, whatever
+    // device the thread that made the server had current
+    cudaSetDevice(s->ctx->device);
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
-        const bool changed = schedule(s);
+        const bool changed = schedule(s, lock);
         if (changed) s->cv.notify_all();
         const bool idle = s->queue.empty() && s->admitted.empty() && !s->lanes[0].busy && !s->lanes[1].busy;
         if (s->stop && idle) break;
@@ -261,12 +273,18 @@ int he_server_wait(he_server *s, int64_t id, int64_t timeout_us, double *latency
     std::unique_lock<std::mutex> lock(s->mu);
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return HE_EINVAL;
+    // a reference, not the iterator: submit may insert (and rehash) while the wait releases the lock
+    Req &r = it->second;
     const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us < 0 ? 0 : timeout_us);
-    while (it->second.state < 3) {
-        if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout && it->second.state < 3) return HE_ETIMEOUT;
+    while (r.state < 3) {
+        if (s->cv.wait_until(lock, deadline) == std::cv_status::timeout && r.state < 3) return HE_ETIMEOUT;
     }
-    if (latency_s) *latency_s = it->second.t_done - it->second.t_submit;
-    return it->second.status;
+    if (latency_s) *latency_s = r.t_done - r.t_submit;
+    const int status = r.status;
+    // a finished request's entry (its event is already back in the pool) is dropped, so a
+    // long-running server's table holds only requests not yet waited for
+    s->reqs.erase(id);
+    return status;
 }
 
 int he_server_stats(he_server *s, int64_t *completed, int64_t *launches, size_t *bytes_in_use) {

@@ -105,6 +105,15 @@ _SIGS = {
     "he_server_wait": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(_dbl)]),
     "he_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_size_t)]),
     "he_server_free": (None, [_vp]),
+    "he_cdiag_transpose_steps": (ctypes.c_int, [_i64, _i64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]),
+    "he_encode_matrix_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "he_ptmat_encode_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    "he_encrypt_vector_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _u64, _vp, _vp]),
+    "he_decrypt_host": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
+    "he_matmult_decrypt_host": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
+    "he_ct_export_host": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "he_ct_host_level": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(_i32)]),
+    "he_ct_import_host": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(HeCt)]),
     "he_ct_export": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_ct_import": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(HeCt)]),
     "he_pt_export": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp]),
@@ -342,6 +351,21 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def _host(t, dtype) -> torch.Tensor:
+    """A contiguous host tensor of `dtype` from a host tensor or numpy array (a view when possible,
+    so a pinned tensor stays pinned)."""
+    if not isinstance(t, torch.Tensor):
+        t = torch.from_numpy(t)
+    if t.is_cuda:
+        raise ValueError("host tensor expected")
+    return t.to(dtype).contiguous()
+
+
+def _host_out(t: torch.Tensor, numel: int) -> None:
+    if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"contiguous host float64 tensor of {numel} elements expected")
 
 
 def _dev(t: torch.Tensor, dtype) -> torch.Tensor:
@@ -668,10 +692,12 @@ class Context:
 
     @staticmethod
     def cdiag_transpose_steps(m: int, n: int) -> list[int]:
-        """Rotation steps he_cdiag_transpose needs keys for."""
-        lo = min(m, n)
-        steps = [i if m >= n else (-((-i) % lo)) % n for i in range(lo)]
-        return sorted(set(s for s in steps if s))
+        """Rotation steps he_cdiag_transpose needs keys for (he_cdiag_transpose_steps)."""
+        cnt = ctypes.c_int()
+        _check(_lib().he_cdiag_transpose_steps(m, n, None, ctypes.byref(cnt)), "he_cdiag_transpose_steps")
+        arr = (ctypes.c_int32 * max(cnt.value, 1))()
+        _check(_lib().he_cdiag_transpose_steps(m, n, arr, ctypes.byref(cnt)), "he_cdiag_transpose_steps")
+        return [int(v) for v in arr[: cnt.value]]
 
     def cdiag_transpose(self, cts: list[Ciphertext], m: int, n: int) -> list[Ciphertext]:
         outs = [self.new_ct(cts[0].level) for _ in range(min(m, n))]
@@ -688,6 +714,84 @@ class Context:
         Z = torch.empty((m, K), dtype=torch.float64, device=self.device)
         _check(_lib().he_cdiag_decode(self.handle, m, n, K, slots.data_ptr(), Z.data_ptr()), "he_cdiag_decode")
         return Z
+
+    # ---- host-memory forms (the party-facing calls; inputs and results in host memory) ----
+    def encode_matrix_host(self, plan: Plan, X, level: int, out: PtMatrix | None = None, transposed: bool = False) -> PtMatrix:
+        """he_encode_matrix_host / he_ptmat_encode_host: X a host tensor or array (m x n, or its
+        n x m transpose with transposed=True)."""
+        X = _host(X, torch.float64)
+        if X.numel() != plan.m * plan.n:
+            raise ValueError(f"matrix of {plan.m * plan.n} elements expected, got {X.numel()}")
+        if out is not None:
+            _check(_lib().he_ptmat_encode_host(self.handle, out.handle, X.data_ptr(), int(transposed)), "he_ptmat_encode_host")
+            return out
+        h = _vp()
+        _check(_lib().he_encode_matrix_host(self.handle, plan.handle, X.data_ptr(), level, int(transposed), ctypes.byref(h)),
+               "he_encode_matrix_host")
+        return PtMatrix(self, h, plan, level)
+
+    def encrypt_vector_host(self, plan: Plan, y, scale: float, level: int, nonce,
+                            outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
+        """he_encrypt_vector_host: y a host tensor or array of n doubles; nonce as in encrypt_vector."""
+        y = _host(y, torch.float64)
+        if y.numel() != plan.n:
+            raise ValueError(f"vector of {plan.n} elements expected, got {y.numel()}")
+        cts = outs or [self.new_ct(level) for _ in range(plan.col_blocks)]
+        arr = (HeCt * len(cts))(*[c.c() for c in cts])
+        if isinstance(nonce, torch.Tensor):
+            if nonce.numel() != plan.col_blocks or nonce.dtype != torch.int64 or not nonce.is_cuda:
+                raise ValueError("device nonces: col_blocks int64 elements on the GPU")
+            n_host, n_dev = 0, _vp(nonce.data_ptr())
+        else:
+            n_host, n_dev = nonce, None
+        _check(_lib().he_encrypt_vector_host(self.handle, plan.handle, y.data_ptr(), scale, level, n_host, n_dev, arr),
+               "he_encrypt_vector_host")
+        for c, a in zip(cts, arr):
+            c.level, c.scale = a.level, a.scale
+        return cts
+
+    def decrypt_host(self, ct: Ciphertext, out: torch.Tensor | None = None) -> torch.Tensor:
+        """he_decrypt_host: N/2 slot values into a host tensor (valid on return unless `out` is
+        pinned, in which case after synchronize())."""
+        out = out if out is not None else torch.empty(self.slots, dtype=torch.float64)
+        _host_out(out, self.slots)
+        c = ct.c()
+        _check(_lib().he_decrypt_host(self.handle, ctypes.byref(c), out.data_ptr()), "he_decrypt_host")
+        return out
+
+    def matmult_decrypt_host(self, plan: Plan, cts: list[Ciphertext], out: torch.Tensor | None = None, mask=None) -> torch.Tensor:
+        """he_matmult_decrypt_host: the m results into a host tensor (valid on return unless `out`
+        is pinned, in which case after synchronize()); mask a host [row_blocks][N/2] array or None."""
+        out = out if out is not None else torch.empty(plan.m, dtype=torch.float64)
+        _host_out(out, plan.m)
+        arr = (HeCt * len(cts))(*[c.c() for c in cts])
+        mp = None
+        if mask is not None:
+            mask = _host(mask, torch.float64)
+            mp = _vp(mask.data_ptr())
+        _check(_lib().he_matmult_decrypt_host(self.handle, plan.handle, arr, len(cts), mp, _vp(out.data_ptr())),
+               "he_matmult_decrypt_host")
+        return out
+
+    def ct_export_host(self, ct: Ciphertext) -> bytes:
+        """he_ct_export_host: the ciphertext serialized into bytes (header, primes, coefficients)."""
+        c = ct.c()
+        n = ctypes.c_size_t()
+        _check(_lib().he_ct_export_host(self.handle, ctypes.byref(c), None, ctypes.byref(n)), "he_ct_export_host")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(_lib().he_ct_export_host(self.handle, ctypes.byref(c), buf, ctypes.byref(n)), "he_ct_export_host")
+        return buf.raw[: n.value]
+
+    def ct_import_host(self, data: bytes) -> Ciphertext:
+        """he_ct_import_host: a ciphertext from bytes made by ct_export_host under the same parameters."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        lvl = _i32()
+        _check(_lib().he_ct_host_level(buf, len(data), ctypes.byref(lvl)), "he_ct_host_level")
+        ct = self.new_ct(int(lvl.value))
+        c = ct.c()
+        _check(_lib().he_ct_import_host(self.handle, buf, len(data), ctypes.byref(c)), "he_ct_import_host")
+        ct.level, ct.scale = c.level, c.scale
+        return ct
 
     # ---- canonical coefficient form ----
     def ct_export(self, ct: Ciphertext) -> torch.Tensor:

@@ -107,3 +107,25 @@ def test_new_entry_points_reject_null_arguments(he):
     assert lib.he_encode_matrix_transposed(None, None, None, 1, ctypes.byref(out)) == he.HE_EINVAL
     assert lib.he_ptmat_encode_transposed(None, None, None) == he.HE_EINVAL
     assert lib.he_matmult_decrypt(None, None, None, 0, None, None) == he.HE_EINVAL
+
+
+@pytest.mark.parametrize("m,n", [(4096, 256), (256, 4096), (16, 4), (4, 16), (8, 8), (1, 64)])
+def test_transpose_steps_agree_with_oracle(he, m, n):
+    """he_cdiag_transpose_steps lists the nonzero steps of the oracle's Eq. 5 reading."""
+    want = sorted({r for _, r in layout.transpose_rotations(m, n) if r})
+    assert he.Context.cdiag_transpose_steps(m, n) == want
+
+
+def test_ct_host_level_reads_header(he):
+    """The serialized-ciphertext header (magic, version, level) is parsed on the host; bad
+    headers are refused."""
+    import struct
+
+    lib = he.lib()
+    hdr = struct.pack("<IIiidQ", 0x54434548, 1, 13, 2, 2.0**40, 0)
+    buf = ctypes.create_string_buffer(hdr, len(hdr))
+    lvl = ctypes.c_int32()
+    assert lib.he_ct_host_level(buf, len(hdr), ctypes.byref(lvl)) == 0 and lvl.value == 2
+    bad = ctypes.create_string_buffer(b"XECT" + hdr[4:], len(hdr))
+    assert lib.he_ct_host_level(bad, len(hdr), ctypes.byref(lvl)) == he.HE_EINVAL
+    assert lib.he_ct_host_level(buf, 16, ctypes.byref(lvl)) == he.HE_EINVAL

@@ -307,3 +307,27 @@ def test_vfl_linr_gradient_step():
     want = XA.T @ (uA + uB - y)
     assert np.abs(layout.lazy_ras(slots, plan) - want).max() > 1.0
     assert np.abs(layout.lazy_ras(slots - mask, plan) - want).max() < TOL_2_40
+
+
+def test_matmult_same_on_any_thread_count():
+    """The oracle's parallel MatMult loop combines per-thread partial sums with exact modular
+    additions, so one thread and every host core give the same ciphertext."""
+    o = ckks.Oracle(6, [60, 40, 40], [60], 3, seed=5)
+    rng = np.random.default_rng(5)
+    X = rng.normal(size=(32, 32))
+    y = rng.uniform(-1, 1, 32)
+    plan = layout.make_plan(32, 32, o.slots)
+    cts = o.encrypt_vector(y, plan, 2.0**40)
+    pts = o.encode_matrix(X, plan, o.L - 1, ext=True)
+    lib = ckks.lib()
+    cores = lib.or_max_threads()
+    try:
+        lib.or_set_threads(1)
+        one = o.matmult(pts, cts, plan)
+        lib.or_set_threads(max(cores, 4))
+        many = o.matmult(pts, cts, plan)
+    finally:
+        lib.or_set_threads(cores)
+    assert plan.m_prime > 8
+    for a, b in zip(one, many):
+        assert np.array_equal(a.data, b.data)
