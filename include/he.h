@@ -222,6 +222,28 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
 int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in, he_ct *outs,
                                     int n_out);
 
+/* Basis extension engine of ModUp (the fast base conversion inside hybrid key switching, O3/O4
+ * of Sec. 2.2) for this context's later calls: HE_BCONV_INT64 (default) sums the products
+ * v_i (Q_d/q_i mod t) with exact 64-bit modular arithmetic; HE_BCONV_INT8_TC cuts v_i and the
+ * constants into bytes, forms the byte products' 32-bit sums on the tensor cores (mma.sync
+ * m16n8k32 u8 x u8 -> s32) and recombines them exactly mod t.  Both give the same residues bit
+ * for bit (results never depend on the engine).  Used by he_rotate, he_rotate_hoisted,
+ * he_rotate_many (he_cdiag_transpose) and he_matmult_plain_cipher; the batch and serving kernels
+ * keep the INT64 form.  A fork starts with its parent's engine. */
+#define HE_BCONV_INT64 0
+#define HE_BCONV_INT8_TC 1
+int he_set_basis_extension(he_ctx *ctx, int engine);
+int he_get_basis_extension(const he_ctx *ctx, int *engine);
+/* Host only: sum_i v[i] h[i] mod t for i < alpha (1..4, any 64-bit v[i], h[i], 3 <= t < 2^62)
+ * computed as HE_BCONV_INT8_TC computes it (byte products, 32-bit partial sums, recombination),
+ * for checking that arithmetic on the CPU. */
+int he_bconv_i8_host(int alpha, const uint64_t *v, const uint64_t *h, uint64_t t, uint64_t *out);
+/* ModUp (Sec. 2.2) of ct's c1 with the context's engine, exported in canonical coefficient form:
+ * digits_out (device) [ndig][level+1+n_p][N] words, ndig = ceil((level+1) / alpha), alpha =
+ * ceil(n_q / dnum): digit d's primes copied, every other limb of Q_level U P the fast base
+ * conversion of the digit (for parity checks). */
+int he_modup_export(he_ctx *ctx, const he_ct *ct, uint64_t *digits_out);
+
 /* Batched form of the hot path for many independent MatMults of uneven shapes (one input
  * and one output ciphertext each, i.e. m, n <= N/2) at one level.  he_batch_create binds the
  * plans, encoded matrices and Galois keys and allocates the batch's scratch; he_batch_run

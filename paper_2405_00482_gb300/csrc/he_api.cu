@@ -14,6 +14,8 @@ void ntt_set_smem_limits(int max_bytes);
 void ops_set_smem_limits(int max_bytes);
 void encode_set_smem_limits(int max_bytes);
 void cdiag_set_smem_limits(int max_bytes);
+void bconv_set_smem_limits(int max_bytes);
+void keyswitch_set_smem_limits(int max_bytes);
 
 namespace {
 
@@ -118,6 +120,10 @@ ModConst make_modconst(uint64_t q, int log_n) {
     m.mu = (uint64_t)((((u128)1) << 64) / q);
     m.r1 = r1;
     m.r1_shoup = shoup(r1, q);
+    m.p40 = hpow(2, 40, q);
+    m.p40_shoup = shoup(m.p40, q);
+    m.p80 = hpow(2, 80, q);
+    m.p80_shoup = shoup(m.p80, q);
     return m;
 }
 
@@ -172,6 +178,8 @@ static int set_smem_limits_once() {
     ops_set_smem_limits(smem);
     encode_set_smem_limits(smem);
     cdiag_set_smem_limits(smem);
+    bconv_set_smem_limits(smem);
+    keyswitch_set_smem_limits(smem);
     if (cudaGetLastError() != cudaSuccess) return HE_ECUDA;
     done[dev] = true;
     return HE_OK;
@@ -427,6 +435,11 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
         he_ctx_destroy(ctx);
         return HE_ECUDA;
     }
+    rc = bconv_i8_tables(ctx);
+    if (rc != HE_OK) {
+        he_ctx_destroy(ctx);
+        return rc;
+    }
     *out = ctx;
     return HE_OK;
 }
@@ -468,6 +481,9 @@ int he_ctx_fork(he_ctx *parent, void *stream, he_ctx **out) {
     ctx->moddown = parent->moddown;
     memcpy(ctx->cdt, parent->cdt, sizeof(ctx->cdt));
     ctx->batch_variant = parent->batch_variant;
+    ctx->bconv = parent->bconv;
+    ctx->d_bconv_a = parent->d_bconv_a;
+    ctx->bconv_a_off = parent->bconv_a_off;
     // the parent's pending work (keys, tables) must be complete before the fork's stream uses it
     if (cudaStreamSynchronize(parent->stream) != cudaSuccess) {
         delete ctx;
@@ -690,18 +706,14 @@ int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *steps, int k,
             return HE_ECUDA;
     const int n_jobs = (int)jobs.size();
     if (n_jobs > 0) {
-        // one ModUp of c1 (O4), then every rotation's key switch in two launches
+        // one ModUp of c1 (O4), then the key switch of every rotation, two launches per 64
         const ModUpConst &mu = ctx->modup[level];
         const size_t wD = (size_t)mu.ndig * mu.ext * N, wc = nl * N, wp = keyswitch_many_pc_words(ctx, n_jobs);
-        const size_t job_words = (sizeof(RotJob) * (size_t)n_jobs + 7) / 8;
-        uint64_t *s = ctx_scratch(ctx, wD + wc + wp + job_words);
+        uint64_t *s = ctx_scratch(ctx, wD + wc + wp);
         if (!s) return HE_ENOMEM;
         uint64_t *D = s, *coef = D + wD, *pc = coef + wc;
-        RotJob *d_jobs = reinterpret_cast<RotJob *>(pc + wp);
-        // from pageable memory the copy stages the table before returning, so `jobs` may go
-        if (cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(RotJob) * n_jobs, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) return HE_ECUDA;
         launch_modup(ctx, in->data + nl * N, level, D, coef);
-        launch_keyswitch_many(ctx, d_jobs, n_jobs, level, D, 0, pc);
+        launch_keyswitch_many(ctx, jobs.data(), n_jobs, level, D, 0, pc);
     }
     for (int i = 0; i < k; ++i) {
         outs[i].level = level;
@@ -740,14 +752,12 @@ int he_rotate_many(he_ctx *ctx, const he_ct *ins, const int32_t *steps, int coun
     }
     const int n_jobs = (int)jobs.size();
     if (n_jobs > 0) {
-        const int chunk = n_jobs < 64 ? n_jobs : 64;
-        const size_t job_words = (sizeof(RotJob) * (size_t)n_jobs + 7) / 8;
-        uint64_t *s = ctx_scratch(ctx, (size_t)chunk * rotate_many_words(ctx, level) + job_words);
+        // chunks of HE_ROT_CHUNK rotations, their job tables passed as kernel parameters; the
+        // chunks reuse one scratch region in stream order
+        const int chunk = n_jobs < HE_ROT_CHUNK ? n_jobs : HE_ROT_CHUNK;
+        uint64_t *s = ctx_scratch(ctx, (size_t)chunk * rotate_many_words(ctx, level));
         if (!s) return HE_ENOMEM;
-        RotJob *d_jobs = reinterpret_cast<RotJob *>(s + (size_t)chunk * rotate_many_words(ctx, level));
-        // from pageable memory the copy stages the table before returning, so `jobs` may go
-        if (cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(RotJob) * n_jobs, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) return HE_ECUDA;
-        for (int c0 = 0; c0 < n_jobs; c0 += chunk) launch_rotate_many(ctx, d_jobs + c0, std::min(chunk, n_jobs - c0), level, s);
+        for (int c0 = 0; c0 < n_jobs; c0 += chunk) launch_rotate_many(ctx, jobs.data() + c0, std::min(chunk, n_jobs - c0), level, s);
     }
     for (int i = 0; i < count; ++i) {
         outs[i].level = level;
@@ -1325,6 +1335,23 @@ int he_ras(he_ctx *ctx, const he_plan *plan, const he_ct *in, he_ct *out) {
 int he_ras_decode(he_ctx *ctx, const he_plan *plan, const double *slots, double *y_out) {
     if (!ctx || !plan || !slots || !y_out || plan->slots != ctx->n / 2) return HE_EINVAL;
     launch_ras_gather(ctx, *plan, slots, y_out);
+    return last_launch();
+}
+
+int he_modup_export(he_ctx *ctx, const he_ct *ct, uint64_t *digits_out) {
+    if (!ctx || !ct || !ct->data || !digits_out) return HE_EINVAL;
+    const int level = ct->level;
+    if (level < 0 || level >= ctx->L) return HE_ELEVEL;
+    const ModUpConst &mu = ctx->modup[level];
+    const size_t N = ctx->n, nl = level + 1;
+    uint64_t *coef = ctx_scratch(ctx, nl * N);
+    if (!coef) return HE_ENOMEM;
+    launch_modup(ctx, ct->data + nl * N, level, digits_out, coef);
+    LimbMap emap{};
+    emap.n = mu.ext;
+    for (int u = 0; u < mu.ext; ++u) emap.prime[u] = mu.ext_prime[u];
+    const int64_t gs = (int64_t)mu.ext * ctx->n;
+    launch_ntt_inv_strided(ctx, digits_out, gs, digits_out, gs, mu.ndig, emap);
     return last_launch();
 }
 

@@ -93,6 +93,7 @@ struct ModConst {
     uint64_t ninv, ninv_shoup;  // N^-1 mod q
     uint64_t mu;      // floor(2^64 / q), for reduce_barrett
     uint64_t r1, r1_shoup;  // 2^64 mod q with its Shoup quotient: x -> x 2^64 mod q (Montgomery form)
+    uint64_t p40, p40_shoup, p80, p80_shoup;  // 2^40 and 2^80 mod q: recombination of byte-split products (he_bconv.cu)
 };
 
 // index map from a batch's limb position to the context's prime index
@@ -126,7 +127,7 @@ struct ModDownConst {
 struct he_shared {
     std::mutex mu;                            // guards keys (keygen on one context, lookups on others)
     std::map<uint32_t, uint64_t *> keys;      // Galois element -> [dnum][2][L+K][N]
-    void *owned[5] = {};                      // device tables: d_mc, d_tw, d_fft, d_sk, d_sk_mont
+    void *owned[6] = {};                      // device tables: d_mc, d_tw, d_fft, d_sk, d_sk_mont, d_bconv_a
     ~he_shared() {
         for (auto &kv : keys) cudaFree(kv.second);
         for (void *p : owned) cudaFree(p);
@@ -159,6 +160,9 @@ struct he_ctx {
     uint64_t *scratch;
     size_t scratch_words;
     int batch_variant = 0;            // last variant a batch tuned to (used by serving lanes)
+    int bconv = 0;                    // basis extension of ModUp: 0 exact INT64 products, 1 INT8 tensor-core limb split
+    uint32_t *d_bconv_a = nullptr;    // INT8 engine: tensor-core A fragments of every (level, digit), shared with forks
+    std::vector<size_t> bconv_a_off;  // their offsets (uint4 units), [level * dnum + digit]
     // staging of the host-memory entry points (he_host.cu), grown on demand: a device buffer for
     // inputs and results, a page-locked host buffer for copies from or to pageable memory, and
     // an event recorded after the last copy out of the host buffer
@@ -216,6 +220,12 @@ struct RotJob {
     uint32_t g;           // Galois element
     int32_t pad;
 };
+// up to HE_ROT_CHUNK rotations, passed to the kernels by value (kernel parameters), so a launch
+// needs no copy of a job table to the device
+#define HE_ROT_CHUNK 64
+struct RotTable {
+    RotJob j[HE_ROT_CHUNK];
+};
 
 // shared geometry and per-job scratch strides of a batch
 struct BatchGeom {
@@ -266,12 +276,20 @@ struct he_batch {
 int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream);
 // words of scratch per rotation job at `level`, and the launches of `count` jobs (device table)
 size_t rotate_many_words(const he_ctx *ctx, int level);
-void launch_rotate_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, uint64_t *scratch);
-// key switch (inner product, ModDown, automorphism of c0) of `count` rotations whose ModUp digits
-// are at D + j d_stride (d_stride 0: one shared decomposition), two launches; pc: scratch of
-// keyswitch_many_pc_words(ctx, count) words
+// count <= HE_ROT_CHUNK jobs (host table), scratch of count rotate_many_words
+void launch_rotate_many(he_ctx *ctx, const RotJob *jobs, int count, int level, uint64_t *scratch);
+// ModUp with the INT8 tensor-core basis extension (he_bconv.cu): for jobs j < count, c1 of job j
+// in NTT form (jobs[j].ct + (level+1) N when jobs is given, else c1_ntt) and in coefficient form
+// at coef + j coef_w, digits into D + j d_w ([ndig][ext][N], NTT form).  Two launches.
+void launch_modup_i8(he_ctx *ctx, const RotTable *jobs, int count, int level, const uint64_t *c1_ntt, const uint64_t *coef, int64_t coef_w,
+                     uint64_t *D, int64_t d_w);
+// the INT8 engine's A-fragment tables of every level and digit (at context creation)
+int bconv_i8_tables(he_ctx *ctx);
+// key switch (inner product, ModDown, automorphism of c0) of `count` rotations (host table) whose
+// ModUp digits are at D + j d_stride (d_stride 0: one shared decomposition), two launches per
+// HE_ROT_CHUNK rotations; pc: scratch of keyswitch_many_pc_words(ctx, count) words
 size_t keyswitch_many_pc_words(const he_ctx *ctx, int count);
-void launch_keyswitch_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc);
+void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc);
 int mm_variant_count();
 int mm_variant_tile(int v);  // coefficients per tile of loop-kernel variant v
 void mm_variant_shape(int v, int *vec, int *grp, int *stages, int *ga);

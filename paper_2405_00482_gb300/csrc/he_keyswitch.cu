@@ -1,0 +1,242 @@
+// he_keyswitch.cu -- key switching of many rotations after their decomposition (O3/O4, Sec. 2.2).
+//
+// Rotation j of a launch has Galois element g_j, key_j, input ciphertext ct_j and ModUp digits
+// D_j = D + j d_stride (d_stride 0: one decomposition shared by every rotation, O4's hoisting).
+// With u_c = sum_d phi_g(D_d) key_{d,c} over Q_level U P (c = 0, 1):
+//   ks_p_kernel, per (j, c, P limb i): u_c on p_i, inverse NTT, times N^-1 [(P/p_i)^-1] -> pc_j[c][i]
+//   ks_q_kernel, per (j, c, Q limb l): conv_l = sum_i pc_j[c][i] (P/p_i mod q_l), NTT, then
+//     out_j[c][l] = (u_c on q_l - conv_l) P^-1, plus phi_g(c0)[l] for c = 0,
+// with u_c on q_l formed in the same kernel, so the Q part of u_c is never stored.  This is
+// ModDown (x_Q - Conv_{P->Q}(x_P)) P^-1 of hybrid key switching; every step is exact modular
+// arithmetic, so the outputs are the canonical residues that a separate inner product,
+// automorphism and ModDown give, bit for bit.
+//
+// The inner products gather D at the automorphism's source index (L2: the digits are shared or
+// small) and stream the keys from HBM.  Each thread forms KS_U coefficients at once with every
+// load of those coefficients (all digits when their count is known at compile time) issued
+// before the first product, so a thread's loads overlap instead of queueing one after another.
+#include "he_internal.cuh"
+#include "he_ntt.cuh"
+
+namespace {
+
+struct KsGeom {
+    const uint64_t *D;   // digits [ndig][ext][N] of rotation j at D + j d_stride
+    int64_t d_stride;
+    uint64_t *pc;        // [count][2][K][N]: converted P limbs in coefficient form
+    int32_t ndig, ext, nl, L, LK, K;
+};
+
+constexpr int KS_U = 4;  // coefficients per thread per round: k, k + B, .., k + (KS_U - 1) B
+
+// r[v] = sum_d D_d[ue][src[v]] key[d][c][kl][kk[v]] mod q for the coefficients v with kk[v] < len
+// (key in Montgomery form: one REDC per 8 digits).  ND > 0: the digit count at compile time.
+template <int ND>
+__device__ __forceinline__ void ks_dot_u(uint64_t (&r)[KS_U], const uint64_t *__restrict__ D, int ndig_rt, int ext, int ue,
+                                         const uint64_t *__restrict__ key, int c, int kl, int LK, int64_t N, const uint32_t (&src)[KS_U],
+                                         const int (&kk)[KS_U], int len, int off, uint64_t q, uint64_t qinv) {
+#pragma unroll
+    for (int v = 0; v < KS_U; ++v) r[v] = 0;
+    if constexpr (ND > 0) {
+        static_assert(ND <= 8, "one REDC per 8 products");
+        uint64_t dv[ND][KS_U], kv[ND][KS_U];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const uint64_t *Dd = D + ((int64_t)d * ext + ue) * N, *Kd = key + ((int64_t)(d * 2 + c) * LK + kl) * N + off;
+#pragma unroll
+            for (int v = 0; v < KS_U; ++v) {
+                const bool ok = kk[v] < len;
+                dv[d][v] = ok ? Dd[src[v]] : 0;
+                kv[d][v] = ok ? Kd[kk[v]] : 0;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < KS_U; ++v) {
+            u128 t = 0;
+#pragma unroll
+            for (int d = 0; d < ND; ++d) t += (u128)dv[d][v] * kv[d][v];
+            r[v] = redc128(t, q, qinv);
+        }
+    } else {
+        for (int d0 = 0; d0 < ndig_rt; d0 += 8) {
+            u128 t[KS_U];
+#pragma unroll
+            for (int v = 0; v < KS_U; ++v) t[v] = 0;
+            for (int d = d0; d < ndig_rt && d < d0 + 8; ++d) {
+                const uint64_t *Dd = D + ((int64_t)d * ext + ue) * N, *Kd = key + ((int64_t)(d * 2 + c) * LK + kl) * N + off;
+                uint64_t dv[KS_U], kv[KS_U];
+#pragma unroll
+                for (int v = 0; v < KS_U; ++v) {
+                    const bool ok = kk[v] < len;
+                    dv[v] = ok ? Dd[src[v]] : 0;
+                    kv[v] = ok ? Kd[kk[v]] : 0;
+                }
+#pragma unroll
+                for (int v = 0; v < KS_U; ++v) t[v] += (u128)dv[v] * kv[v];
+            }
+#pragma unroll
+            for (int v = 0; v < KS_U; ++v) r[v] = add_mod(r[v], redc128(t[v], q, qinv), q);
+        }
+    }
+}
+
+template <bool CL, int LOGN, int ND>
+__global__ void ks_p_kernel(const RotTable jobs, KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+                            int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    extern __shared__ uint64_t s[];
+    const int64_t N = (int64_t)1 << logn;
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
+    const int j = item / (2 * kg.K), c = (item / kg.K) % 2, i = item % kg.K;
+    const int pr = md.p_prime[i];
+    const uint64_t q = mc[pr].q, qinv = mc[pr].qinv;
+    const ulonglong2 *itw = twiddles(d_tw, pr, 1, logn);
+    tw_prefetch<CL, false>(s, itw, logn);
+    const RotJob jb = jobs.j[j];
+    const uint64_t *D = kg.D + j * kg.d_stride;
+    const int B = blockDim.x;
+    for (int k0 = threadIdx.x; k0 < len; k0 += KS_U * B) {
+        uint32_t src[KS_U];
+        int kk[KS_U];
+#pragma unroll
+        for (int v = 0; v < KS_U; ++v) {
+            kk[v] = k0 + v * B;
+            src[v] = automorph_src((uint32_t)(off + kk[v]), jb.g, logn);
+        }
+        uint64_t r[KS_U];
+        ks_dot_u<ND>(r, D, kg.ndig, kg.ext, kg.nl + i, jb.key, c, kg.L + i, kg.LK, N, src, kk, len, off, q, qinv);
+#pragma unroll
+        for (int v = 0; v < KS_U; ++v)
+            if (kk[v] < len) s[SIDX(kk[v])] = r[v];
+    }
+    __syncthreads();
+    inv_any<CL, LOGN>(s, itw, q, logn);
+    uint64_t *dst = kg.pc + (((int64_t)j * 2 + c) * kg.K + i) * N + off;
+    const uint64_t ni = mc[pr].ninv, nis = mc[pr].ninv_shoup;
+    for (int k = threadIdx.x; k < len; k += B) dst[k] = mul_shoup(mul_shoup(s[SIDX(k)], ni, nis, q), md.inv[i], md.inv_shoup[i], q);
+}
+
+template <bool CL, int LOGN, int ND>
+__global__ void ks_q_kernel(const RotTable jobs, KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+                            int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    extern __shared__ uint64_t s[];
+    const int64_t N = (int64_t)1 << logn;
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
+    const int j = item / (2 * kg.nl), c = (item / kg.nl) % 2, l = item % kg.nl;
+    const int pl = md.q_prime[l];
+    const uint64_t q = mc[pl].q, qinv = mc[pl].qinv;
+    const ulonglong2 *tw = twiddles(d_tw, pl, 0, logn);
+    tw_prefetch<CL, true>(s, tw, logn);
+    const uint64_t *pc = kg.pc + ((int64_t)j * 2 + c) * kg.K * N + off;
+    const int B = blockDim.x;
+    for (int k0 = threadIdx.x; k0 < len; k0 += KS_U * B) {
+        uint64_t acc[KS_U];
+#pragma unroll
+        for (int v = 0; v < KS_U; ++v) acc[v] = 0;
+        for (int i = 0; i < kg.K; ++i) {
+            uint64_t x[KS_U];
+#pragma unroll
+            for (int v = 0; v < KS_U; ++v) x[v] = k0 + v * B < len ? pc[(int64_t)i * N + k0 + v * B] : 0;
+#pragma unroll
+            for (int v = 0; v < KS_U; ++v) acc[v] = add_mod(acc[v], mul_shoup(x[v], md.hat[i][l], md.hat_shoup[i][l], q), q);
+        }
+#pragma unroll
+        for (int v = 0; v < KS_U; ++v)
+            if (k0 + v * B < len) s[SIDX(k0 + v * B)] = acc[v];
+    }
+    __syncthreads();
+    fwd_any<CL, LOGN>(s, tw, q, logn);
+    const RotJob jb = jobs.j[j];
+    const uint64_t *D = kg.D + j * kg.d_stride;
+    uint64_t *o = jb.out + ((int64_t)c * kg.nl + l) * N + off;
+    const uint64_t *c0 = jb.ct + (int64_t)l * N;
+    const uint64_t pinv = md.pinv[l], pinvs = md.pinv_shoup[l];
+    for (int k0 = threadIdx.x; k0 < len; k0 += KS_U * B) {
+        uint32_t src[KS_U];
+        int kk[KS_U];
+        uint64_t a0[KS_U];
+#pragma unroll
+        for (int v = 0; v < KS_U; ++v) {
+            kk[v] = k0 + v * B;
+            src[v] = automorph_src((uint32_t)(off + kk[v]), jb.g, logn);
+            a0[v] = (c == 0 && kk[v] < len) ? c0[src[v]] : 0;
+        }
+        uint64_t x[KS_U];
+        ks_dot_u<ND>(x, D, kg.ndig, kg.ext, l, jb.key, c, l, kg.LK, N, src, kk, len, off, q, qinv);
+#pragma unroll
+        for (int v = 0; v < KS_U; ++v) {
+            if (kk[v] >= len) continue;
+            uint64_t y = mul_shoup(sub_mod(x[v], s[SIDX(kk[v])], q), pinv, pinvs, q);
+            if (c == 0) y = add_mod(y, a0[v], q);
+            o[kk[v]] = y;
+        }
+    }
+}
+
+// instance for (cluster form, ring size, digit count): 3 digits (the parameter sets' top
+// levels) at compile time, every other count at run time
+template <bool CL, class F>
+auto ks_pick(int logn, int ndig, F f) {
+    return by_logn(logn, [&](auto L) { return ndig == 3 ? f.template operator()<CL, L.value, 3>() : f.template operator()<CL, L.value, 0>(); });
+}
+
+}  // namespace
+
+size_t keyswitch_many_pc_words(const he_ctx *ctx, int count) {
+    const int c = count < HE_ROT_CHUNK ? count : HE_ROT_CHUNK;
+    return (size_t)c * 2 * ctx->K * ctx->n;
+}
+
+void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc) {
+    const ModUpConst &mu = ctx->modup[level];
+    const ModDownConst &md = ctx->moddown[level];
+    const int logn = ctx->log_n;
+    cudaStream_t st = ctx->stream;
+    const uint64_t *tw = ctx->d_tw;
+    const ModConst *mc = ctx->d_mc;
+    for (int c0 = 0; c0 < count; c0 += HE_ROT_CHUNK) {
+        const int n = count - c0 < HE_ROT_CHUNK ? count - c0 : HE_ROT_CHUNK;
+        RotTable tab{};
+        for (int j = 0; j < n; ++j) tab.j[j] = jobs[c0 + j];
+        KsGeom kg{};
+        kg.D = D + c0 * d_stride;
+        kg.d_stride = d_stride;
+        kg.pc = pc;  // reused by each chunk: the chunks run in stream order
+        kg.ndig = mu.ndig;
+        kg.ext = mu.ext;
+        kg.nl = level + 1;
+        kg.L = ctx->L;
+        kg.LK = ctx->L + ctx->K;
+        kg.K = ctx->K;
+        const int np = n * 2 * ctx->K, nq = n * 2 * (level + 1);
+        ctx->launches += 2;
+        const auto kp_cl = ks_pick<true>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_p_kernel<CL, LOGN, ND>; });
+        const auto kp_one = ks_pick<false>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_p_kernel<CL, LOGN, ND>; });
+        const auto kq_cl = ks_pick<true>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; });
+        const auto kq_one = ks_pick<false>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; });
+        if (use_cluster(logn, np))
+            launch_cluster(kp_cl, np * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+        else
+            launch_k(kp_one, np, ntt_threads(logn), ntt_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+        if (use_cluster(logn, nq))
+            launch_cluster(kq_cl, nq * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+        else
+            launch_k(kq_one, nq, ntt_threads(logn), ntt_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+    }
+}
+
+void keyswitch_set_smem_limits(int max_bytes) {
+    auto set = [max_bytes](auto k) { cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); };
+    for (int logn : {0, 12, 13, 14})
+        for (int nd : {0, 3}) {
+            set(ks_pick<true>(logn, nd, []<bool CL, int LOGN, int ND>() { return ks_p_kernel<CL, LOGN, ND>; }));
+            set(ks_pick<false>(logn, nd, []<bool CL, int LOGN, int ND>() { return ks_p_kernel<CL, LOGN, ND>; }));
+            set(ks_pick<true>(logn, nd, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; }));
+            set(ks_pick<false>(logn, nd, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; }));
+        }
+}

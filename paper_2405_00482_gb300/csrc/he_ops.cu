@@ -441,14 +441,14 @@ struct RotGeom {
     int64_t coef_w, d_w, p_w;    // their strides
 };
 
-__global__ void rot_intt_c1_kernel(const RotJob *__restrict__ jobs, RotGeom rg, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+__global__ void rot_intt_c1_kernel(const RotTable jobs, RotGeom rg, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
                                    int logn) {
     HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int j = blockIdx.x / rg.nl, l = blockIdx.x % rg.nl;
     const uint64_t q = mc[l].q;
-    const uint64_t *src = jobs[j].ct + ((int64_t)rg.nl + l) * N;
+    const uint64_t *src = jobs.j[j].ct + ((int64_t)rg.nl + l) * N;
     for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, l, 1, logn), q, logn);
@@ -456,107 +456,14 @@ __global__ void rot_intt_c1_kernel(const RotJob *__restrict__ jobs, RotGeom rg, 
     for (int k = threadIdx.x; k < N; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], mc[l].ninv, mc[l].ninv_shoup, q);
 }
 
-__global__ void rot_modup_kernel(const RotJob *__restrict__ jobs, RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+__global__ void rot_modup_kernel(const RotTable jobs, RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
                                  const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
     extern __shared__ uint64_t s[];
     const int per = mu.ndig * mu.ext;
     const int j = blockIdx.x / per, rest = blockIdx.x % per;
-    modup_body<false>(jobs[j].ct + (int64_t)rg.nl * (1 << logn), rg.coef + j * rg.coef_w, rg.D + j * rg.d_w, mu, rest / mu.ext, rest % mu.ext, s,
+    modup_body<false>(jobs.j[j].ct + (int64_t)rg.nl * (1 << logn), rg.coef + j * rg.coef_w, rg.D + j * rg.d_w, mu, rest / mu.ext, rest % mu.ext, s,
                       d_tw, mc, logn, 0, 1 << logn);
-}
-
-// ---- key switching of many rotations, two launches after the decomposition ----
-// Rotation j of a launch has Galois element g_j, key_j, input ciphertext ct_j and ModUp digits
-// D_j = D + j d_stride (d_stride 0: one decomposition shared by every rotation, O4).  With
-// u_c = sum_d phi_g(D_d) key_{d,c} over Q_level U P (c = 0, 1):
-//   ks_p_kernel, per (j, c, P limb i): u_c on p_i, inverse NTT, times N^-1 [(P/p_i)^-1] -> pc_j[c][i]
-//   ks_q_kernel, per (j, c, Q limb l): conv_l = sum_i pc_j[c][i] (P/p_i mod q_l), NTT, then
-//     out_j[c][l] = (u_c on q_l - conv_l) P^-1, plus phi_g(c0)[l] for c = 0,
-// with u_c on q_l formed in the same kernel, so the Q part of u_c is never stored.  This is
-// ModDown (x_Q - Conv_{P->Q}(x_P)) P^-1 of Sec. 2.2's hybrid key switching; every step is
-// exact modular arithmetic, so the outputs are the canonical residues that the separate
-// inner-product, automorphism and ModDown kernels give, bit for bit.
-struct KsGeom {
-    const uint64_t *D;   // digits [ndig][ext][N] of rotation j at D + j d_stride
-    int64_t d_stride;
-    uint64_t *pc;        // [count][2][K][N]: converted P limbs in coefficient form
-    int32_t ndig, ext, nl, L, LK, K;
-};
-
-// sum_d D_d[u][src] key[d][c][kl][k] mod q (key in Montgomery form: one REDC per 8 terms)
-__device__ __forceinline__ uint64_t ks_dot(const uint64_t *__restrict__ D, int ndig, int ext, int u, const uint64_t *__restrict__ key, int c,
-                                           int kl, int LK, int logn, uint32_t src, int k, uint64_t q, uint64_t qinv) {
-    const int64_t N = (int64_t)1 << logn;
-    uint64_t r = 0;
-    for (int d0 = 0; d0 < ndig; d0 += 8) {
-        u128 t = 0;
-        for (int d = d0; d < ndig && d < d0 + 8; ++d) t += (u128)D[((int64_t)d * ext + u) * N + src] * key[((int64_t)(d * 2 + c) * LK + kl) * N + k];
-        r = add_mod(r, redc128(t, q, qinv), q);
-    }
-    return r;
-}
-
-template <bool CL, int LOGN = 0>
-__global__ void ks_p_kernel(const RotJob *__restrict__ jobs, KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw,
-                            const ModConst *__restrict__ mc, int logn_rt) {
-    HE_GRID_DEP();
-    const int logn = LOGN ? LOGN : logn_rt;
-    extern __shared__ uint64_t s[];
-    const int N = 1 << logn;
-    int item, off, len;
-    slice_of<CL>(logn, item, off, len);
-    const int j = item / (2 * kg.K), c = (item / kg.K) % 2, i = item % kg.K;
-    const int pr = md.p_prime[i];
-    const uint64_t q = mc[pr].q, qinv = mc[pr].qinv;
-    const ulonglong2 *itw = twiddles(d_tw, pr, 1, logn);
-    tw_prefetch<CL, false>(s, itw, logn);
-    const RotJob jb = jobs[j];
-    const uint64_t *D = kg.D + j * kg.d_stride;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        const uint32_t src = automorph_src((uint32_t)(off + k), jb.g, logn);
-        s[SIDX(k)] = ks_dot(D, kg.ndig, kg.ext, kg.nl + i, jb.key, c, kg.L + i, kg.LK, logn, src, off + k, q, qinv);
-    }
-    __syncthreads();
-    inv_any<CL, LOGN>(s, itw, q, logn);
-    uint64_t *dst = kg.pc + (((int64_t)j * 2 + c) * kg.K + i) * N + off;
-    const uint64_t ni = mc[pr].ninv, nis = mc[pr].ninv_shoup;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = mul_shoup(mul_shoup(s[SIDX(k)], ni, nis, q), md.inv[i], md.inv_shoup[i], q);
-}
-
-template <bool CL, int LOGN = 0>
-__global__ void ks_q_kernel(const RotJob *__restrict__ jobs, KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw,
-                            const ModConst *__restrict__ mc, int logn_rt) {
-    HE_GRID_DEP();
-    const int logn = LOGN ? LOGN : logn_rt;
-    extern __shared__ uint64_t s[];
-    const int N = 1 << logn;
-    int item, off, len;
-    slice_of<CL>(logn, item, off, len);
-    const int j = item / (2 * kg.nl), c = (item / kg.nl) % 2, l = item % kg.nl;
-    const int pl = md.q_prime[l];
-    const uint64_t q = mc[pl].q, qinv = mc[pl].qinv;
-    const ulonglong2 *tw = twiddles(d_tw, pl, 0, logn);
-    tw_prefetch<CL, true>(s, tw, logn);
-    const uint64_t *pc = kg.pc + ((int64_t)j * 2 + c) * kg.K * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        uint64_t acc = 0;
-        for (int i = 0; i < kg.K; ++i) acc = add_mod(acc, mul_shoup(pc[(int64_t)i * N + k], md.hat[i][l], md.hat_shoup[i][l], q), q);
-        s[SIDX(k)] = acc;
-    }
-    __syncthreads();
-    fwd_any<CL, LOGN>(s, tw, q, logn);
-    const RotJob jb = jobs[j];
-    const uint64_t *D = kg.D + j * kg.d_stride;
-    uint64_t *o = jb.out + ((int64_t)c * kg.nl + l) * N + off;
-    const uint64_t *c0 = jb.ct + (int64_t)l * N;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        const uint32_t src = automorph_src((uint32_t)(off + k), jb.g, logn);
-        const uint64_t x = ks_dot(D, kg.ndig, kg.ext, l, jb.key, c, l, kg.LK, logn, src, off + k, q, qinv);
-        uint64_t v = mul_shoup(sub_mod(x, s[SIDX(k)], q), md.pinv[l], md.pinv_shoup[l], q);
-        if (c == 0) v = add_mod(v, c0[src], q);
-        o[k] = v;
-    }
 }
 
 // ---- batch forms: the same bodies over a job table (one job = one MatMult, R = C = 1) ----
@@ -1229,6 +1136,14 @@ static size_t cl_fused_smem_bytes(int logn) { return cl_smem_bytes(logn) + ((siz
 void launch_modup(he_ctx *ctx, const uint64_t *c1_ntt, int level, uint64_t *D, uint64_t *tmp_coeff) {
     const ModUpConst &mu = ctx->modup[level];
     const int items = mu.ndig * mu.ext;
+    if (ctx->bconv == HE_BCONV_INT8_TC) {  // c1 to coefficient form, then the tensor-core conversion and the NTTs
+        LimbMap qm{};
+        qm.n = level + 1;
+        for (int l = 0; l <= level; ++l) qm.prime[l] = l;
+        launch_ntt_inv_strided(ctx, c1_ntt, 0, tmp_coeff, 0, 1, qm);
+        launch_modup_i8(ctx, nullptr, 1, level, c1_ntt, tmp_coeff, 0, D, 0);
+        return;
+    }
     ctx->launches++;
     if (use_cluster(ctx->log_n, items)) {  // the inverse NTT of c1 happens inside
         launch_cluster(by_logn(ctx->log_n, [](auto L) { return modup_cl_fused_kernel<L.value>; }), items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n), cl_fused_smem_bytes(ctx->log_n), ctx->stream, c1_ntt,
@@ -1463,57 +1378,27 @@ size_t rotate_many_words(const he_ctx *ctx, int level) {
     return nl * N + (size_t)mu.ndig * mu.ext * N + 2 * (size_t)ctx->K * N;
 }
 
-void launch_keyswitch_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc);
-
-// O3 of `count` different ciphertexts: inverse NTT of every c1, ModUp of every digit, then the
-// key switch of all rotations in two launches (launch_keyswitch_many, one decomposition each)
-void launch_rotate_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, uint64_t *scratch) {
+// O3 of `count` (<= HE_ROT_CHUNK) different ciphertexts: inverse NTT of every c1, ModUp of every
+// digit, then the key switch of all rotations in two launches (launch_keyswitch_many, one
+// decomposition each)
+void launch_rotate_many(he_ctx *ctx, const RotJob *jobs, int count, int level, uint64_t *scratch) {
     if (count == 0) return;
     const ModUpConst &mu = ctx->modup[level];
     const RotGeom rg = rot_geom(ctx, level, scratch, count);
     const int thr = ntt_threads(ctx->log_n);
     const size_t smem = ntt_smem_bytes(ctx->log_n);
     cudaStream_t st = ctx->stream;
-    launch_k(rot_intt_c1_kernel, count * rg.nl, thr, smem, st, d_jobs, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    launch_k(rot_modup_kernel, count * mu.ndig * mu.ext, thr, smem, st, d_jobs, rg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    ctx->launches += 2;
-    launch_keyswitch_many(ctx, d_jobs, count, level, rg.D, rg.d_w, rg.pcoef);
-}
-
-size_t keyswitch_many_pc_words(const he_ctx *ctx, int count) { return (size_t)count * 2 * ctx->K * ctx->n; }
-
-void launch_keyswitch_many(he_ctx *ctx, const RotJob *d_jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc) {
-    if (count == 0) return;
-    const ModUpConst &mu = ctx->modup[level];
-    const ModDownConst &md = ctx->moddown[level];
-    KsGeom kg{};
-    kg.D = D;
-    kg.d_stride = d_stride;
-    kg.pc = pc;
-    kg.ndig = mu.ndig;
-    kg.ext = mu.ext;
-    kg.nl = level + 1;
-    kg.L = ctx->L;
-    kg.LK = ctx->L + ctx->K;
-    kg.K = ctx->K;
-    const int np = count * 2 * ctx->K, nq = count * 2 * (level + 1);
-    const int logn = ctx->log_n;
-    cudaStream_t st = ctx->stream;
-    const uint64_t *tw = ctx->d_tw;
-    const ModConst *mc = ctx->d_mc;
-    ctx->launches += 2;
-    if (use_cluster(logn, np))
-        launch_cluster(by_logn(logn, [](auto L) { return ks_p_kernel<true, L.value>; }), np * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st,
-                       d_jobs, kg, md, tw, mc, logn);
-    else
-        launch_k(by_logn(logn, [](auto L) { return ks_p_kernel<false, L.value>; }), np, ntt_threads(logn), ntt_smem_bytes(logn), st, d_jobs, kg, md,
-                 tw, mc, logn);
-    if (use_cluster(logn, nq))
-        launch_cluster(by_logn(logn, [](auto L) { return ks_q_kernel<true, L.value>; }), nq * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st,
-                       d_jobs, kg, md, tw, mc, logn);
-    else
-        launch_k(by_logn(logn, [](auto L) { return ks_q_kernel<false, L.value>; }), nq, ntt_threads(logn), ntt_smem_bytes(logn), st, d_jobs, kg, md,
-                 tw, mc, logn);
+    RotTable tab{};
+    for (int j = 0; j < count; ++j) tab.j[j] = jobs[j];
+    launch_k(rot_intt_c1_kernel, count * rg.nl, thr, smem, st, tab, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    ctx->launches++;
+    if (ctx->bconv == HE_BCONV_INT8_TC) {
+        launch_modup_i8(ctx, &tab, count, level, nullptr, rg.coef, rg.coef_w, rg.D, rg.d_w);
+    } else {
+        launch_k(rot_modup_kernel, count * mu.ndig * mu.ext, thr, smem, st, tab, rg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
+        ctx->launches++;
+    }
+    launch_keyswitch_many(ctx, jobs, count, level, rg.D, rg.d_w, rg.pcoef);
 }
 
 void ops_set_smem_limits(int max_bytes) {
@@ -1533,12 +1418,7 @@ void ops_set_smem_limits(int max_bytes) {
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(rescale_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_intt_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_ntt_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
-    each_logn([max_bytes](auto L) {
-        cudaFuncSetAttribute(ks_p_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(ks_p_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(ks_q_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-        cudaFuncSetAttribute(ks_q_kernel<false, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
-    });
+
     for (int v = 0; v < kMMVariants; ++v)
         for (int nd = 0; nd <= 3; ++nd)
             mm_dispatch(v, nd, []<int NDIG, int VEC, int G, int S, bool GA>() {

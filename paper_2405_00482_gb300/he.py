@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhe.so")
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_EKEY, HE_ELEVEL, HE_ESCALE, HE_ETIMEOUT, HE_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7, -8
+HE_BCONV_INT64, HE_BCONV_INT8_TC = 0, 1  # basis extension engines of ModUp
 
 
 class HEError(RuntimeError):
@@ -114,6 +115,10 @@ _SIGS = {
     "he_ct_export_host": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "he_ct_host_level": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(_i32)]),
     "he_ct_import_host": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(HeCt)]),
+    "he_set_basis_extension": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "he_get_basis_extension": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "he_bconv_i8_host": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _u64, ctypes.POINTER(_u64)]),
+    "he_modup_export": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_ct_export": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp]),
     "he_ct_import": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _dbl, ctypes.POINTER(HeCt)]),
     "he_pt_export": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp]),
@@ -792,6 +797,23 @@ class Context:
         _check(_lib().he_ct_import_host(self.handle, buf, len(data), ctypes.byref(c)), "he_ct_import_host")
         ct.level, ct.scale = c.level, c.scale
         return ct
+
+    # ---- basis extension engine of ModUp ----
+    def set_basis_extension(self, engine: int) -> None:
+        """HE_BCONV_INT64 (exact 64-bit products) or HE_BCONV_INT8_TC (byte-split products on the
+        tensor cores, recombined exactly): same results, for this context's later calls."""
+        _check(_lib().he_set_basis_extension(self.handle, engine), "he_set_basis_extension")
+
+    def basis_extension(self) -> int:
+        v = ctypes.c_int()
+        _check(_lib().he_get_basis_extension(self.handle, ctypes.byref(v)), "he_get_basis_extension")
+        return int(v.value)
+
+    def modup_export(self, ct: Ciphertext, out: torch.Tensor) -> torch.Tensor:
+        """ModUp digits of ct's c1, [ndig][level+1+K][N] canonical coefficient form (he_modup_export)."""
+        c = ct.c()
+        _check(_lib().he_modup_export(self.handle, ctypes.byref(c), out.data_ptr()), "he_modup_export")
+        return out
 
     # ---- canonical coefficient form ----
     def ct_export(self, ct: Ciphertext) -> torch.Tensor:

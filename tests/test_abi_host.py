@@ -129,3 +129,40 @@ def test_ct_host_level_reads_header(he):
     bad = ctypes.create_string_buffer(b"XECT" + hdr[4:], len(hdr))
     assert lib.he_ct_host_level(bad, len(hdr), ctypes.byref(lvl)) == he.HE_EINVAL
     assert lib.he_ct_host_level(buf, 16, ctypes.byref(lvl)) == he.HE_EINVAL
+
+
+def _bconv_i8(he, v, h, t):
+    lib = he.lib()
+    a = len(v)
+    va, ha, out = (ctypes.c_uint64 * a)(*v), (ctypes.c_uint64 * a)(*h), ctypes.c_uint64()
+    assert lib.he_bconv_i8_host(a, va, ha, t, ctypes.byref(out)) == 0
+    return out.value
+
+
+@pytest.mark.parametrize("t", [3, 17, 257])
+def test_int8_basis_extension_exhaustive_small_moduli(he, t):
+    """The INT8 engine's arithmetic (bytes of v and h, 32-bit sums of byte products, recombination
+    in three groups and reduction mod t) equals sum v_i h_i mod t on every pair of residues of a
+    small modulus, one and two source primes."""
+    r = range(t) if t <= 17 else range(0, t, 7)
+    for v0 in r:
+        for h0 in r:
+            assert _bconv_i8(he, [v0], [h0], t) == (v0 * h0) % t
+    if t <= 17:
+        for v0 in range(t):
+            for v1 in range(t):
+                for h0 in range(t):
+                    h1 = (v0 + 3 * v1 + h0) % t
+                    assert _bconv_i8(he, [v0, v1], [h0, h1], t) == (v0 * h0 + v1 * h1) % t
+
+
+def test_int8_basis_extension_wide_operands(he):
+    """Full-width operands (every byte 255 included) and 60-bit primes, one to four sources."""
+    rng = np.random.default_rng(7)
+    ts = [ckks.gen_primes(13, [60])[0], ckks.gen_primes(14, [40])[0], (1 << 61) - 1, 3]
+    for t in ts:
+        for a in (1, 2, 3, 4):
+            cases = [[(1 << 64) - 1] * a, [0] * a] + [[int(x) for x in rng.integers(0, 2**63, size=a, dtype=np.uint64)] for _ in range(50)]
+            for v in cases:
+                for h in cases[:3] + [[int(x) % t for x in v[::-1]]]:
+                    assert _bconv_i8(he, v, h, t) == sum(x * y for x, y in zip(v, h)) % t
