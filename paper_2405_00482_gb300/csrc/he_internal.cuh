@@ -286,8 +286,9 @@ void launch_modup_i8(he_ctx *ctx, const RotTable *jobs, int count, int level, co
 // the INT8 engine's A-fragment tables of every level and digit (at context creation)
 int bconv_i8_tables(he_ctx *ctx);
 // key switch (inner product, ModDown, automorphism of c0) of `count` rotations (host table) whose
-// ModUp digits are at D + j d_stride (d_stride 0: one shared decomposition), two launches per
-// HE_ROT_CHUNK rotations; pc: scratch of keyswitch_many_pc_words(ctx, count) words
+// ModUp digits are at D + j d_stride (d_stride 0: one shared decomposition), two (few rotations)
+// or four launches per HE_ROT_CHUNK rotations; pc: scratch of keyswitch_many_pc_words(ctx, count)
+// words, laid out [min(count, HE_ROT_CHUNK)][2][K][N] then [..][2][level+1][N]
 size_t keyswitch_many_pc_words(const he_ctx *ctx, int count);
 void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc);
 int mm_variant_count();

@@ -178,6 +178,131 @@ __global__ void ks_q_kernel(const RotTable jobs, KsGeom kg, ModDownConst md, con
     }
 }
 
+// ---- the same key switch for many rotations, in four launches ----
+// With many rotations the inner products' automorphism gathers and key streams run in
+// elementwise kernels (no shared memory, many warps per SM to hide their latency), and the
+// transforms in kernels that do nothing else:
+//   ks_up_kernel    u_c on the P limbs, NTT form -> pc_j[c][i]                       (elementwise)
+//   ks_pintt_kernel pc_j[c][i] -> inverse NTT, times N^-1 [(P/p_i)^-1]                (transform)
+//   ks_conv_kernel  conv_l = sum_i pc_j[c][i] (P/p_i mod q_l), NTT -> cv_j[c][l]      (transform)
+//   ks_out_kernel   out_j[c][l] = (u_c on q_l - cv_j[c][l]) P^-1 (+ phi_g(c0)[l])    (elementwise)
+// The values are those of ks_p_kernel / ks_q_kernel, bit for bit.
+
+// grid (N / 256, count * 2 * K): thread per coefficient of one (j, c, P limb i)
+template <int ND>
+__global__ void __launch_bounds__(256) ks_up_kernel(const RotTable jobs, KsGeom kg, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
+    const int64_t N = (int64_t)1 << logn;
+    const int item = blockIdx.y;
+    const int j = item / (2 * kg.K), c = (item / kg.K) % 2, i = item % kg.K;
+    const int pr = kg.L + i;
+    const uint64_t q = mc[pr].q, qinv = mc[pr].qinv;
+    const RotJob jb = jobs.j[j];
+    const uint64_t *D = kg.D + j * kg.d_stride;
+    uint32_t src[KS_U];
+    int kk[KS_U];
+    const int k0 = blockIdx.x * (256 * KS_U) + threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < KS_U; ++v) {
+        kk[v] = k0 + v * 256;
+        src[v] = automorph_src((uint32_t)kk[v], jb.g, logn);
+    }
+    uint64_t r[KS_U];
+    ks_dot_u<ND>(r, D, kg.ndig, kg.ext, kg.nl + i, jb.key, c, kg.L + i, kg.LK, N, src, kk, (int)N, 0, q, qinv);
+    uint64_t *dst = kg.pc + (int64_t)item * N;
+#pragma unroll
+    for (int v = 0; v < KS_U; ++v)
+        if (kk[v] < N) dst[kk[v]] = r[v];
+}
+
+// in place on pc: item (j, c, i)
+template <bool CL, int LOGN>
+__global__ void ks_pintt_kernel(KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    extern __shared__ uint64_t s[];
+    const int64_t N = (int64_t)1 << logn;
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
+    const int i = item % kg.K;
+    const int pr = md.p_prime[i];
+    const uint64_t q = mc[pr].q;
+    const ulonglong2 *itw = twiddles(d_tw, pr, 1, logn);
+    tw_prefetch<CL, false>(s, itw, logn);
+    uint64_t *x = kg.pc + (int64_t)item * N + off;
+    stage_in(s, x, len, [](uint64_t v) { return v; });
+    __syncthreads();
+    inv_any<CL, LOGN>(s, itw, q, logn);
+    const uint64_t ni = mc[pr].ninv, nis = mc[pr].ninv_shoup;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) x[k] = mul_shoup(mul_shoup(s[SIDX(k)], ni, nis, q), md.inv[i], md.inv_shoup[i], q);
+}
+
+// item (j, c, l): cv_j[c][l] = NTT(sum_i pc_j[c][i] (P/p_i mod q_l))
+template <bool CL, int LOGN>
+__global__ void ks_conv_kernel(KsGeom kg, uint64_t *cv, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+                               int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    extern __shared__ uint64_t s[];
+    const int64_t N = (int64_t)1 << logn;
+    int item, off, len;
+    slice_of<CL>(logn, item, off, len);
+    const int jc = item / kg.nl, l = item % kg.nl;
+    const int pl = md.q_prime[l];
+    const uint64_t q = mc[pl].q;
+    const ulonglong2 *tw = twiddles(d_tw, pl, 0, logn);
+    tw_prefetch<CL, true>(s, tw, logn);
+    const uint64_t *pc = kg.pc + (int64_t)jc * kg.K * N + off;
+    const uint64_t h0 = md.hat[0][l], h0s = md.hat_shoup[0][l];
+    stage_in(s, pc, len, [=](uint64_t v) { return mul_shoup(v, h0, h0s, q); });
+    __syncthreads();
+    for (int i = 1; i < kg.K; ++i) {
+        for (int k = threadIdx.x; k < len; k += blockDim.x)
+            s[SIDX(k)] = add_mod(s[SIDX(k)], mul_shoup(pc[(int64_t)i * N + k], md.hat[i][l], md.hat_shoup[i][l], q), q);
+        __syncthreads();
+    }
+    fwd_any<CL, LOGN>(s, tw, q, logn);
+    uint64_t *o = cv + (int64_t)item * N + off;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = s[SIDX(k)];
+}
+
+// grid (N / (256 KS_U), count * 2 * nl): thread per KS_U coefficients of one (j, c, Q limb l)
+template <int ND>
+__global__ void __launch_bounds__(256) ks_out_kernel(const RotTable jobs, KsGeom kg, const uint64_t *__restrict__ cv, ModDownConst md,
+                                                     const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
+    const int64_t N = (int64_t)1 << logn;
+    const int item = blockIdx.y;
+    const int j = item / (2 * kg.nl), c = (item / kg.nl) % 2, l = item % kg.nl;
+    const int pl = md.q_prime[l];
+    const uint64_t q = mc[pl].q, qinv = mc[pl].qinv;
+    const RotJob jb = jobs.j[j];
+    const uint64_t *D = kg.D + j * kg.d_stride;
+    const uint64_t *c0 = jb.ct + (int64_t)l * N, *cvl = cv + (int64_t)item * N;
+    uint32_t src[KS_U];
+    int kk[KS_U];
+    uint64_t a0[KS_U], w[KS_U];
+    const int k0 = blockIdx.x * (256 * KS_U) + threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < KS_U; ++v) {
+        kk[v] = k0 + v * 256;
+        src[v] = automorph_src((uint32_t)kk[v], jb.g, logn);
+        const bool ok = kk[v] < N;
+        a0[v] = (c == 0 && ok) ? c0[src[v]] : 0;
+        w[v] = ok ? cvl[kk[v]] : 0;
+    }
+    uint64_t x[KS_U];
+    ks_dot_u<ND>(x, D, kg.ndig, kg.ext, l, jb.key, c, l, kg.LK, N, src, kk, (int)N, 0, q, qinv);
+    uint64_t *o = jb.out + ((int64_t)c * kg.nl + l) * N;
+#pragma unroll
+    for (int v = 0; v < KS_U; ++v) {
+        if (kk[v] >= N) continue;
+        uint64_t y = mul_shoup(sub_mod(x[v], w[v], q), md.pinv[l], md.pinv_shoup[l], q);
+        if (c == 0) y = add_mod(y, a0[v], q);
+        o[kk[v]] = y;
+    }
+}
+
 // instance for (cluster form, ring size, digit count): 3 digits (the parameter sets' top
 // levels) at compile time, every other count at run time
 template <bool CL, class F>
@@ -189,7 +314,7 @@ auto ks_pick(int logn, int ndig, F f) {
 
 size_t keyswitch_many_pc_words(const he_ctx *ctx, int count) {
     const int c = count < HE_ROT_CHUNK ? count : HE_ROT_CHUNK;
-    return (size_t)c * 2 * ctx->K * ctx->n;
+    return (size_t)c * 2 * (ctx->K + ctx->L) * ctx->n;  // pc [c][2][K][N], then cv [c][2][nl][N] (nl <= L)
 }
 
 void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level, const uint64_t *D, int64_t d_stride, uint64_t *pc) {
@@ -199,6 +324,8 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
     cudaStream_t st = ctx->stream;
     const uint64_t *tw = ctx->d_tw;
     const ModConst *mc = ctx->d_mc;
+    const int cmax = count < HE_ROT_CHUNK ? count : HE_ROT_CHUNK;
+    uint64_t *cv = pc + (size_t)cmax * 2 * ctx->K * ctx->n;  // [cmax][2][level+1][N] after pc [cmax][2][K][N]
     for (int c0 = 0; c0 < count; c0 += HE_ROT_CHUNK) {
         const int n = count - c0 < HE_ROT_CHUNK ? count - c0 : HE_ROT_CHUNK;
         RotTable tab{};
@@ -206,7 +333,7 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
         KsGeom kg{};
         kg.D = D + c0 * d_stride;
         kg.d_stride = d_stride;
-        kg.pc = pc;  // reused by each chunk: the chunks run in stream order
+        kg.pc = pc;  // pc and cv are reused by each chunk: the chunks run in stream order
         kg.ndig = mu.ndig;
         kg.ext = mu.ext;
         kg.nl = level + 1;
@@ -214,19 +341,35 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
         kg.LK = ctx->L + ctx->K;
         kg.K = ctx->K;
         const int np = n * 2 * ctx->K, nq = n * 2 * (level + 1);
-        ctx->launches += 2;
-        const auto kp_cl = ks_pick<true>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_p_kernel<CL, LOGN, ND>; });
-        const auto kp_one = ks_pick<false>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_p_kernel<CL, LOGN, ND>; });
-        const auto kq_cl = ks_pick<true>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; });
-        const auto kq_one = ks_pick<false>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; });
-        if (use_cluster(logn, np))
-            launch_cluster(kp_cl, np * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+        if (use_cluster(logn, nq)) {
+            // few rotations: two cluster launches, the inner products inside the transforms
+            ctx->launches += 2;
+            const auto kp = ks_pick<true>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_p_kernel<CL, LOGN, ND>; });
+            const auto kq = ks_pick<true>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; });
+            launch_cluster(kp, np * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+            launch_cluster(kq, nq * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+            continue;
+        }
+        const unsigned eblocks = (unsigned)((ctx->n + 256 * KS_U - 1) / (256 * KS_U));
+        ctx->launches += 4;
+        if (mu.ndig == 3)
+            launch_k(ks_up_kernel<3>, dim3(eblocks, (unsigned)np), 256, 0, st, tab, kg, mc, logn);
         else
-            launch_k(kp_one, np, ntt_threads(logn), ntt_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
-        if (use_cluster(logn, nq))
-            launch_cluster(kq_cl, nq * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+            launch_k(ks_up_kernel<0>, dim3(eblocks, (unsigned)np), 256, 0, st, tab, kg, mc, logn);
+        auto transform = [&](auto kcl, auto kone, int items, auto... args) {
+            if (use_cluster(logn, items))
+                launch_cluster(kcl, items * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, args...);
+            else
+                launch_k(kone, items, ntt_threads(logn), ntt_smem_bytes(logn), st, args...);
+        };
+        transform(by_logn(logn, [](auto L) { return ks_pintt_kernel<true, L.value>; }), by_logn(logn, [](auto L) { return ks_pintt_kernel<false, L.value>; }),
+                  np, kg, md, tw, mc, logn);
+        transform(by_logn(logn, [](auto L) { return ks_conv_kernel<true, L.value>; }), by_logn(logn, [](auto L) { return ks_conv_kernel<false, L.value>; }),
+                  nq, kg, cv, md, tw, mc, logn);
+        if (mu.ndig == 3)
+            launch_k(ks_out_kernel<3>, dim3(eblocks, (unsigned)nq), 256, 0, st, tab, kg, (const uint64_t *)cv, md, mc, logn);
         else
-            launch_k(kq_one, nq, ntt_threads(logn), ntt_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
+            launch_k(ks_out_kernel<0>, dim3(eblocks, (unsigned)nq), 256, 0, st, tab, kg, (const uint64_t *)cv, md, mc, logn);
     }
 }
 
@@ -239,4 +382,10 @@ void keyswitch_set_smem_limits(int max_bytes) {
             set(ks_pick<true>(logn, nd, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; }));
             set(ks_pick<false>(logn, nd, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; }));
         }
+    each_logn([&](auto L) {
+        set(ks_pintt_kernel<true, L.value>);
+        set(ks_pintt_kernel<false, L.value>);
+        set(ks_conv_kernel<true, L.value>);
+        set(ks_conv_kernel<false, L.value>);
+    });
 }

@@ -1375,7 +1375,7 @@ static RotGeom rot_geom(const he_ctx *ctx, int level, uint64_t *scratch, int cou
 size_t rotate_many_words(const he_ctx *ctx, int level) {
     const ModUpConst &mu = ctx->modup[level];
     const size_t N = ctx->n, nl = level + 1;
-    return nl * N + (size_t)mu.ndig * mu.ext * N + 2 * (size_t)ctx->K * N;
+    return nl * N + (size_t)mu.ndig * mu.ext * N + 2 * (size_t)ctx->K * N + 2 * nl * N;  // the key switch's pc and cv too
 }
 
 // O3 of `count` (<= HE_ROT_CHUNK) different ciphertexts: inverse NTT of every c1, ModUp of every
