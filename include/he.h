@@ -222,6 +222,13 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
 int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in, he_ct *outs,
                                     int n_out);
 
+/* The key switch of many rotations (he_rotate_hoisted, he_rotate_many with at least 32 of them)
+ * runs its transforms as one CTA per limb-poly with the usual thread count (variant 0) or with
+ * 512 threads and at most 64 registers (variant 1).  The first such call on a context times both
+ * on its first chunk (synchronising the stream; not under stream capture) and keeps the faster:
+ * variant (-1 before) and ms[0..1] (may be NULL) report the choice and the timings. */
+int he_keyswitch_tuning(const he_ctx *ctx, int *variant, float *ms);
+
 /* Basis extension engine of ModUp (the fast base conversion inside hybrid key switching, O3/O4
  * of Sec. 2.2) for this context's later calls: HE_BCONV_INT64 (default) sums the products
  * v_i (Q_d/q_i mod t) with exact 64-bit modular arithmetic; HE_BCONV_INT8_TC cuts v_i and the

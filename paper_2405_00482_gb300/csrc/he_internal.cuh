@@ -161,6 +161,8 @@ struct he_ctx {
     size_t scratch_words;
     int batch_variant = 0;            // last variant a batch tuned to (used by serving lanes)
     int bconv = 0;                    // basis extension of ModUp: 0 exact INT64 products, 1 INT8 tensor-core limb split
+    int ks_variant = -1;              // transform variant of the many-rotation key switch, chosen by timing (-1: not yet)
+    float ks_tune_ms[2] = {};         // the timed milliseconds of each variant (one full chunk of rotations)
     uint32_t *d_bconv_a = nullptr;    // INT8 engine: tensor-core A fragments of every (level, digit), shared with forks
     std::vector<size_t> bconv_a_off;  // their offsets (uint4 units), [level * dnum + digit]
     // staging of the host-memory entry points (he_host.cu), grown on demand: a device buffer for

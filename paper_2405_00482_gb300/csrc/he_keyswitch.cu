@@ -215,9 +215,10 @@ __global__ void __launch_bounds__(256) ks_up_kernel(const RotTable jobs, KsGeom 
         if (kk[v] < N) dst[kk[v]] = r[v];
 }
 
-// in place on pc: item (j, c, i)
-template <bool CL, int LOGN>
-__global__ void ks_pintt_kernel(KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
+// in place on pc: item (j, c, i).  TPB 512: the one-CTA form with 512 threads and at most 64
+// registers (two CTAs per SM); 256: the usual thread count; 0: the cluster form
+template <bool CL, int LOGN, int TPB>
+__global__ void __launch_bounds__(512, TPB == 512 ? 2 : 1) ks_pintt_kernel(KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ uint64_t s[];
@@ -238,8 +239,8 @@ __global__ void ks_pintt_kernel(KsGeom kg, ModDownConst md, const uint64_t *__re
 }
 
 // item (j, c, l): cv_j[c][l] = NTT(sum_i pc_j[c][i] (P/p_i mod q_l))
-template <bool CL, int LOGN>
-__global__ void ks_conv_kernel(KsGeom kg, uint64_t *cv, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+template <bool CL, int LOGN, int TPB>
+__global__ void __launch_bounds__(512, TPB == 512 ? 2 : 1) ks_conv_kernel(KsGeom kg, uint64_t *cv, ModDownConst md, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
                                int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
@@ -326,7 +327,8 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
     const ModConst *mc = ctx->d_mc;
     const int cmax = count < HE_ROT_CHUNK ? count : HE_ROT_CHUNK;
     uint64_t *cv = pc + (size_t)cmax * 2 * ctx->K * ctx->n;  // [cmax][2][level+1][N] after pc [cmax][2][K][N]
-    for (int c0 = 0; c0 < count; c0 += HE_ROT_CHUNK) {
+    // one chunk's launches with transform variant v (0: ntt_threads per CTA, 1: 512 threads)
+    auto issue = [&](int c0, int v) {
         const int n = count - c0 < HE_ROT_CHUNK ? count - c0 : HE_ROT_CHUNK;
         RotTable tab{};
         for (int j = 0; j < n; ++j) tab.j[j] = jobs[c0 + j];
@@ -348,7 +350,7 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
             const auto kq = ks_pick<true>(logn, mu.ndig, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; });
             launch_cluster(kp, np * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
             launch_cluster(kq, nq * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, tab, kg, md, tw, mc, logn);
-            continue;
+            return;
         }
         const unsigned eblocks = (unsigned)((ctx->n + 256 * KS_U - 1) / (256 * KS_U));
         ctx->launches += 4;
@@ -356,21 +358,55 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
             launch_k(ks_up_kernel<3>, dim3(eblocks, (unsigned)np), 256, 0, st, tab, kg, mc, logn);
         else
             launch_k(ks_up_kernel<0>, dim3(eblocks, (unsigned)np), 256, 0, st, tab, kg, mc, logn);
-        auto transform = [&](auto kcl, auto kone, int items, auto... args) {
-            if (use_cluster(logn, items))
-                launch_cluster(kcl, items * HE_NTT_CL_SIZE, cl_threads(logn), cl_smem_bytes(logn), st, args...);
-            else
-                launch_k(kone, items, ntt_threads(logn), ntt_smem_bytes(logn), st, args...);
-        };
-        transform(by_logn(logn, [](auto L) { return ks_pintt_kernel<true, L.value>; }), by_logn(logn, [](auto L) { return ks_pintt_kernel<false, L.value>; }),
-                  np, kg, md, tw, mc, logn);
-        transform(by_logn(logn, [](auto L) { return ks_conv_kernel<true, L.value>; }), by_logn(logn, [](auto L) { return ks_conv_kernel<false, L.value>; }),
-                  nq, kg, cv, md, tw, mc, logn);
+        // the transforms: cluster form for few limb-polys, else one CTA each
+        const bool wide = v == 1 && logn >= 12;
+        if (use_cluster(logn, np))
+            launch_cluster(by_logn(logn, [](auto L) { return ks_pintt_kernel<true, L.value, 0>; }), np * HE_NTT_CL_SIZE, cl_threads(logn),
+                           cl_smem_bytes(logn), st, kg, md, tw, mc, logn);
+        else if (wide)
+            launch_k(by_logn(logn, [](auto L) { return ks_pintt_kernel<false, L.value, 512>; }), np, 512, ntt_smem_bytes(logn), st, kg, md, tw, mc, logn);
+        else
+            launch_k(by_logn(logn, [](auto L) { return ks_pintt_kernel<false, L.value, 256>; }), np, ntt_threads(logn), ntt_smem_bytes(logn), st, kg, md, tw,
+                     mc, logn);
+        if (wide)
+            launch_k(by_logn(logn, [](auto L) { return ks_conv_kernel<false, L.value, 512>; }), nq, 512, ntt_smem_bytes(logn), st, kg, cv, md, tw, mc, logn);
+        else
+            launch_k(by_logn(logn, [](auto L) { return ks_conv_kernel<false, L.value, 256>; }), nq, ntt_threads(logn), ntt_smem_bytes(logn), st, kg, cv, md,
+                     tw, mc, logn);
         if (mu.ndig == 3)
             launch_k(ks_out_kernel<3>, dim3(eblocks, (unsigned)nq), 256, 0, st, tab, kg, (const uint64_t *)cv, md, mc, logn);
         else
             launch_k(ks_out_kernel<0>, dim3(eblocks, (unsigned)nq), 256, 0, st, tab, kg, (const uint64_t *)cv, md, mc, logn);
+    };
+    // the first launch of at least 32 rotations on a context chooses the transform variant by timing
+    // both on its first chunk (the launches overwrite their outputs with the same values, so
+    // repeating them changes nothing); not under stream capture, where the usual thread count is taken
+    if (ctx->ks_variant < 0 && cmax >= 32 && !use_cluster(logn, cmax * 2 * (level + 1))) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cs == cudaStreamCaptureStatusNone && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+            int best = 0;
+            for (int v = 0; v < 2; ++v) {
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaEventRecord(e0, st);
+                    issue(0, v);
+                    cudaEventRecord(e1, st);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                    float t = 0.0f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0 && t < ms) ms = t;
+                }
+                ctx->ks_tune_ms[v] = ms;
+                if (ms < ctx->ks_tune_ms[best]) best = v;
+            }
+            ctx->ks_variant = best;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
     }
+    for (int c0 = 0; c0 < count; c0 += HE_ROT_CHUNK) issue(c0, ctx->ks_variant < 0 ? 0 : ctx->ks_variant);
 }
 
 void keyswitch_set_smem_limits(int max_bytes) {
@@ -383,9 +419,21 @@ void keyswitch_set_smem_limits(int max_bytes) {
             set(ks_pick<false>(logn, nd, []<bool CL, int LOGN, int ND>() { return ks_q_kernel<CL, LOGN, ND>; }));
         }
     each_logn([&](auto L) {
-        set(ks_pintt_kernel<true, L.value>);
-        set(ks_pintt_kernel<false, L.value>);
-        set(ks_conv_kernel<true, L.value>);
-        set(ks_conv_kernel<false, L.value>);
+        set(ks_pintt_kernel<true, L.value, 0>);
+        set(ks_pintt_kernel<false, L.value, 256>);
+        set(ks_pintt_kernel<false, L.value, 512>);
+        set(ks_conv_kernel<true, L.value, 0>);
+        set(ks_conv_kernel<false, L.value, 256>);
+        set(ks_conv_kernel<false, L.value, 512>);
     });
+}
+
+extern "C" int he_keyswitch_tuning(const he_ctx *ctx, int *variant, float *ms) {
+    if (!ctx || !variant) return HE_EINVAL;
+    *variant = ctx->ks_variant;
+    if (ms) {
+        ms[0] = ctx->ks_tune_ms[0];
+        ms[1] = ctx->ks_tune_ms[1];
+    }
+    return HE_OK;
 }

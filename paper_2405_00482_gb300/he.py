@@ -115,6 +115,7 @@ _SIGS = {
     "he_ct_export_host": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "he_ct_host_level": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(_i32)]),
     "he_ct_import_host": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(HeCt)]),
+    "he_keyswitch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "he_set_basis_extension": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_get_basis_extension": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "he_bconv_i8_host": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _u64, ctypes.POINTER(_u64)]),
@@ -562,21 +563,21 @@ class Context:
         out.level, out.scale = o.level, o.scale
         return out
 
-    def rotate(self, ct: Ciphertext, step: int) -> Ciphertext:
-        out = self.new_ct(ct.level)
+    def rotate(self, ct: Ciphertext, step: int, out: Ciphertext | None = None) -> Ciphertext:
+        out = out if out is not None else self.new_ct(ct.level)
         c, o = ct.c(), out.c()
         _check(_lib().he_rotate(self.handle, ctypes.byref(c), step, ctypes.byref(o)), "he_rotate")
-        out.scale = o.scale
+        out.level, out.scale = o.level, o.scale
         return out
 
-    def rotate_hoisted(self, ct: Ciphertext, steps) -> list[Ciphertext]:
-        outs = [self.new_ct(ct.level) for _ in steps]
+    def rotate_hoisted(self, ct: Ciphertext, steps, outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
+        outs = outs or [self.new_ct(ct.level) for _ in steps]
         arr = (HeCt * len(steps))(*[o.c() for o in outs])
         st = (_i32 * len(steps))(*steps)
         c = ct.c()
         _check(_lib().he_rotate_hoisted(self.handle, ctypes.byref(c), st, len(steps), arr), "he_rotate_hoisted")
         for o, a in zip(outs, arr):
-            o.scale = a.scale
+            o.level, o.scale = a.level, a.scale
         return outs
 
     # ---- MatMult ----
@@ -797,6 +798,14 @@ class Context:
         _check(_lib().he_ct_import_host(self.handle, buf, len(data), ctypes.byref(c)), "he_ct_import_host")
         ct.level, ct.scale = c.level, c.scale
         return ct
+
+    def keyswitch_tuning(self) -> dict:
+        """Transform variant of the many-rotation key switch (he_keyswitch_tuning): -1 before tuning."""
+        v = ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        _check(_lib().he_keyswitch_tuning(self.handle, ctypes.byref(v), ms), "he_keyswitch_tuning")
+        return {"variant": int(v.value), "variant_ms": [round(float(x), 4) for x in ms],
+                "variants": ["one CTA per limb-poly, usual threads", "one CTA per limb-poly, 512 threads, <= 64 registers"]}
 
     # ---- basis extension engine of ModUp ----
     def set_basis_extension(self, engine: int) -> None:
