@@ -37,6 +37,11 @@ __device__ __forceinline__ void ks_dot_u(uint64_t (&r)[KS_U], const uint64_t *__
                                          const int (&kk)[KS_U], int len, int off, uint64_t q, uint64_t qinv) {
 #pragma unroll
     for (int v = 0; v < KS_U; ++v) r[v] = 0;
+    // a coefficient past len reads coefficient 0 (in bounds; its result is not stored), so every
+    // load is unconditional and all of them are issued before the first product
+    int ki[KS_U];
+#pragma unroll
+    for (int v = 0; v < KS_U; ++v) ki[v] = kk[v] < len ? kk[v] : 0;
     if constexpr (ND > 0) {
         static_assert(ND <= 8, "one REDC per 8 products");
         uint64_t dv[ND][KS_U], kv[ND][KS_U];
@@ -45,9 +50,8 @@ __device__ __forceinline__ void ks_dot_u(uint64_t (&r)[KS_U], const uint64_t *__
             const uint64_t *Dd = D + ((int64_t)d * ext + ue) * N, *Kd = key + ((int64_t)(d * 2 + c) * LK + kl) * N + off;
 #pragma unroll
             for (int v = 0; v < KS_U; ++v) {
-                const bool ok = kk[v] < len;
-                dv[d][v] = ok ? Dd[src[v]] : 0;
-                kv[d][v] = ok ? Kd[kk[v]] : 0;
+                dv[d][v] = __ldg(Dd + src[v]);
+                kv[d][v] = __ldg(Kd + ki[v]);
             }
         }
 #pragma unroll
@@ -67,9 +71,8 @@ __device__ __forceinline__ void ks_dot_u(uint64_t (&r)[KS_U], const uint64_t *__
                 uint64_t dv[KS_U], kv[KS_U];
 #pragma unroll
                 for (int v = 0; v < KS_U; ++v) {
-                    const bool ok = kk[v] < len;
-                    dv[v] = ok ? Dd[src[v]] : 0;
-                    kv[v] = ok ? Kd[kk[v]] : 0;
+                    dv[v] = __ldg(Dd + src[v]);
+                    kv[v] = __ldg(Kd + ki[v]);
                 }
 #pragma unroll
                 for (int v = 0; v < KS_U; ++v) t[v] += (u128)dv[v] * kv[v];
@@ -287,10 +290,9 @@ __global__ void __launch_bounds__(256) ks_out_kernel(const RotTable jobs, KsGeom
 #pragma unroll
     for (int v = 0; v < KS_U; ++v) {
         kk[v] = k0 + v * 256;
-        src[v] = automorph_src((uint32_t)kk[v], jb.g, logn);
-        const bool ok = kk[v] < N;
-        a0[v] = (c == 0 && ok) ? c0[src[v]] : 0;
-        w[v] = ok ? cvl[kk[v]] : 0;
+        src[v] = automorph_src((uint32_t)kk[v], jb.g, logn);  // in range for any kk (its low log N bits)
+        w[v] = __ldg(cvl + (kk[v] < N ? kk[v] : 0));
+        a0[v] = c == 0 ? __ldg(c0 + src[v]) : 0;
     }
     uint64_t x[KS_U];
     ks_dot_u<ND>(x, D, kg.ndig, kg.ext, l, jb.key, c, l, kg.LK, N, src, kk, (int)N, 0, q, qinv);

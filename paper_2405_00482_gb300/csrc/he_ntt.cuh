@@ -46,6 +46,26 @@ __device__ __forceinline__ void stage_in(uint64_t *s, const T *__restrict__ src,
     }
 }
 
+// s[SIDX(k)] = f(s[SIDX(k)], src[k]) for k < len, with the same eight loads in flight per thread
+template <class T, class F>
+__device__ __forceinline__ void stage_acc(uint64_t *s, const T *__restrict__ src, int len, F f) {
+    constexpr int U = 8;
+    const int stride = blockDim.x;
+    for (int k0 = threadIdx.x; k0 < len; k0 += U * stride) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * stride;
+            v[u] = k < len ? src[k] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * stride;
+            if (k < len) s[SIDX(k)] = f(s[SIDX(k)], v[u]);
+        }
+    }
+}
+
 // Twiddle access: entry idx of the bit-reversed table (idx = m + j for a stage with m groups).
 // TwGlobal reads the table in global memory; the cluster forms read a per-slice copy in shared
 // memory (see tw_prefetch).

@@ -61,14 +61,16 @@ __device__ __forceinline__ void modup_body(const uint64_t *__restrict__ c1_ntt, 
     }
     tw_prefetch<CL, true>(s, twiddles(d_tw, p, 0, logn), logn);
     const int na = hi - lo;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        uint64_t acc = 0;
-        for (int i = 0; i < na; ++i) {
-            const uint64_t qi = mc[lo + i].q;
-            uint64_t v = mul_shoup(c1_coef[(int64_t)(lo + i) * N + off + k], mu.inv[d][i], mu.inv_shoup[d][i], qi);
-            acc = add_mod(acc, mul_shoup(v, mu.hat[d][i][u], mu.hat_shoup[d][i][u], t), t);
-        }
-        s[SIDX(k)] = acc;
+    // sum over the digit's primes of [x_i (Qd/q_i)^-1]_{q_i} (Qd/q_i mod t), one source limb at a
+    // time with its loads staged (eight in flight per thread)
+    for (int i = 0; i < na; ++i) {
+        const uint64_t qi = mc[lo + i].q, iv = mu.inv[d][i], ivs = mu.inv_shoup[d][i], h = mu.hat[d][i][u], hs = mu.hat_shoup[d][i][u];
+        const uint64_t *src = c1_coef + (int64_t)(lo + i) * N + off;
+        auto term = [=](uint64_t x) { return mul_shoup(mul_shoup(x, iv, ivs, qi), h, hs, t); };
+        if (i == 0)
+            stage_in(s, src, len, term);
+        else
+            stage_acc(s, src, len, [=](uint64_t a, uint64_t x) { return add_mod(a, term(x), t); });
     }
     __syncthreads();
     fwd_any<CL>(s, twiddles(d_tw, p, 0, logn), t, logn);
@@ -124,14 +126,13 @@ __device__ __forceinline__ void moddown_body(const uint64_t *__restrict__ x, int
     const uint64_t q = mc[pj].q;
     tw_prefetch<CL, true>(s, twiddles(d_tw, pj, 0, logn), logn);
     const uint64_t *xp = xp_coef + (int64_t)c * md.K * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        uint64_t acc = 0;
-        for (int i = 0; i < md.K; ++i) {
-            const uint64_t pi = mc[md.p_prime[i]].q;
-            uint64_t v = mul_shoup(xp[(int64_t)i * N + k], md.inv[i], md.inv_shoup[i], pi);
-            acc = add_mod(acc, mul_shoup(v, md.hat[i][j], md.hat_shoup[i][j], q), q);
-        }
-        s[SIDX(k)] = acc;
+    for (int i = 0; i < md.K; ++i) {  // conversion of the P limbs, loads staged as in modup_body
+        const uint64_t pi = mc[md.p_prime[i]].q, iv = md.inv[i], ivs = md.inv_shoup[i], h = md.hat[i][j], hs = md.hat_shoup[i][j];
+        auto term = [=](uint64_t x) { return mul_shoup(mul_shoup(x, iv, ivs, pi), h, hs, q); };
+        if (i == 0)
+            stage_in(s, xp, len, term);
+        else
+            stage_acc(s, xp + (int64_t)i * N, len, [=](uint64_t a, uint64_t x) { return add_mod(a, term(x), q); });
     }
     __syncthreads();
     fwd_any<CL>(s, twiddles(d_tw, pj, 0, logn), q, logn);
@@ -172,12 +173,12 @@ __device__ __forceinline__ void rescale_body(const uint64_t *__restrict__ ct, in
     const uint64_t q = mc[j].q;
     tw_prefetch<CL, true>(s, twiddles(d_tw, j, 0, logn), logn);
     const uint64_t *lc = last_coef + (int64_t)c * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        uint64_t r = lc[k] + rc.half;
-        if (r >= rc.ql) r -= rc.ql;
-        int64_t centred = (int64_t)r - (int64_t)rc.half;
-        s[SIDX(k)] = reduce_signed(centred, q, mc[j].mu);
-    }
+    const uint64_t ql = rc.ql, half = rc.half, mu = mc[j].mu;
+    stage_in(s, lc, len, [=](uint64_t x) {
+        uint64_t r = x + half;
+        if (r >= ql) r -= ql;
+        return reduce_signed((int64_t)r - (int64_t)half, q, mu);
+    });
     __syncthreads();
     fwd_any<CL>(s, twiddles(d_tw, j, 0, logn), q, logn);
     const uint64_t *cj = ct + ((int64_t)c * (level + 1) + j) * N + off;
@@ -449,7 +450,7 @@ __global__ void rot_intt_c1_kernel(const RotTable jobs, RotGeom rg, const uint64
     const int j = blockIdx.x / rg.nl, l = blockIdx.x % rg.nl;
     const uint64_t q = mc[l].q;
     const uint64_t *src = jobs.j[j].ct + ((int64_t)rg.nl + l) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    stage_in(s, src, N, [](uint64_t v) { return v; });
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, l, 1, logn), q, logn);
     uint64_t *dst = rg.coef + j * rg.coef_w + (int64_t)l * N;
@@ -478,7 +479,7 @@ __global__ void batch_intt_c1_kernel(const MMJob *__restrict__ jobs, BatchGeom b
     if (jobs[j].m_prime <= 1) return;
     const uint64_t q = mc[l].q;
     const uint64_t *src = jobs[j].ct + ((int64_t)bg.nq + l) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    stage_in(s, src, N, [](uint64_t v) { return v; });
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, l, 1, logn), q, logn);
     uint64_t *dst = bg.coef + (int64_t)j * bg.coef_words + (int64_t)l * N;
@@ -508,7 +509,7 @@ __global__ void batch_intt_p_kernel(const MMJob *__restrict__ jobs, BatchGeom bg
     const int p = bg.L + i;
     const uint64_t q = mc[p].q;
     const uint64_t *src = bg.acc + (int64_t)j * bg.acc_words + ((int64_t)c * bg.ext + bg.nq + i) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    stage_in(s, src, N, [](uint64_t v) { return v; });
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)c * bg.K + i) * N;
@@ -538,7 +539,7 @@ __global__ void batch_intt_last_kernel(const MMJob *__restrict__ jobs, BatchGeom
     const int p = bg.level;
     const uint64_t q = mc[p].q;
     const uint64_t *src = bg.sum + (int64_t)j * bg.sum_words + ((int64_t)c * bg.nq + bg.level) * N;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) s[SIDX(k)] = src[k];
+    stage_in(s, src, N, [](uint64_t v) { return v; });
     __syncthreads();
     ntt_inv_smem(s, twiddles(d_tw, p, 1, logn), q, logn);
     uint64_t *dst = bg.tmp + (int64_t)j * bg.tmp_words + ((int64_t)2 * bg.K + c) * N;
