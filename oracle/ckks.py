@@ -317,6 +317,45 @@ class Oracle:
         self.counts.hstrot += plan.col_blocks * len(steps)
         return outs
 
+    def encode_matrix_bsgs(self, X: np.ndarray, plan: layout.Plan, level: int, baby: int, ext: bool = False) -> np.ndarray:
+        """Plaintexts of the baby-step giant-step schedule, [R][C][m'][limbs][N] at scale q_level:
+        entry i = g B + b encodes RotR(e_i, g B) (layout.bsgs_diagonal_slots)."""
+        E = layout.bsgs_diagonal_slots(X, plan, baby)
+        R, C, M = E.shape[:3]
+        nl = level + 1 + (self.K if ext else 0)
+        out = np.zeros((R, C, M, nl, self.n), dtype=np.uint64)
+        for r in range(R):
+            for c in range(C):
+                for i in range(M):
+                    out[r, c, i] = self.encode(E[r, c, i], float(self.q[level]), level, ext)
+        return out
+
+    def matmult_bsgs(self, pts: np.ndarray, cts: list[Ciphertext], plan: layout.Plan, baby: int) -> list[Ciphertext]:
+        """X [[y]] by the baby-step giant-step schedule (layout.bsgs_cleartext_model), composed from
+        O1-O4: the baby rotations x_{c,b} = HstRotL(ct_c, b) share one decomposition; per row
+        block and giant step g the partial sum s_g = sum_c sum_b pt_{gB+b} (x) x_{c,b} (O2, O1), then
+        RotL(s_g, gB) (O3) for g >= 1, the sum over g, and one rescale.  Only the Q limbs of pts
+        are used."""
+        B, G = layout.bsgs_split(plan, baby)
+        level = cts[0].level
+        qp = float(self.q[level])
+        baby_steps, _ = layout.bsgs_steps(plan, baby)
+        xs = [[c] + self.rotate_hoisted(c, baby_steps) for c in cts]
+        outs = []
+        for r in range(plan.row_blocks):
+            acc = None
+            for g in range(G):
+                inner = None
+                for c in range(plan.col_blocks):
+                    for b in range(B):
+                        t = self.mul_plain(xs[c][b], pts[r, c, g * B + b][: level + 1], qp)
+                        inner = t if inner is None else self.add(inner, t)
+                if g > 0:
+                    inner = self.rotate(inner, g * B)
+                acc = inner if acc is None else self.add(acc, inner)
+            outs.append(self.rescale(acc))
+        return outs
+
     def matmult_decode(self, outs: list[Ciphertext], plan: layout.Plan) -> np.ndarray:
         """P_B's side: decrypt every output and apply the lazy rotate-and-sum (Sec. 4.3)."""
         slots = np.stack([self.decrypt_slots(o) for o in outs])

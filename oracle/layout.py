@@ -249,3 +249,53 @@ def transpose_rotations(m: int, n: int) -> list[tuple[int, int]]:
         r = i if m >= n else (-k) % n
         out.append((k, r))
     return out
+
+
+# ---- baby-step giant-step schedule of the diagonal method (an extension of Tab. 2's row) -----
+#
+# With m' = B G diagonals, i = g B + b (b < B baby steps, g < G giant steps), and RotL of a
+# slot-wise product being the product of the RotLs,
+#   sum_i e_i (x) RotL(y, i) = sum_g RotL( sum_b RotR(e_{gB+b}, gB) (x) RotL(y, b), gB ),
+# so only the B - 1 baby rotations of y (hoisted, one decomposition) and G - 1 giant rotations of
+# the partial sums are needed: about 2 sqrt(m') Galois keys instead of m' - 1.
+
+def bsgs_split(plan: Plan, baby: int) -> tuple[int, int]:
+    """(B, G): baby steps B (a power of two dividing m') and giant steps G = m' / B."""
+    if baby < 1 or baby & (baby - 1) or plan.m_prime % baby:
+        raise ValueError("baby steps: a power of two dividing m'")
+    return baby, plan.m_prime // baby
+
+
+def bsgs_steps(plan: Plan, baby: int) -> tuple[list[int], list[int]]:
+    """Left-rotation steps: baby 1..B-1 (of every input ciphertext) and giant g B, g = 1..G-1
+    (of the partial sums)."""
+    B, G = bsgs_split(plan, baby)
+    return list(range(1, B)), [g * B for g in range(1, G)]
+
+
+def bsgs_diagonal_slots(X: np.ndarray, plan: Plan, baby: int) -> np.ndarray:
+    """The plaintext slots of the schedule, shape [R][C][m'][N']: entry i = g B + b holds
+    RotR(e_i, g B), RotR(v, r)[s] = v[(s - r) mod N']."""
+    B, _ = bsgs_split(plan, baby)
+    E = diagonal_slots(X, plan)
+    out = np.empty_like(E)
+    for i in range(plan.m_prime):
+        out[:, :, i] = np.roll(E[:, :, i], (i // B) * B, axis=-1)
+    return out
+
+
+def bsgs_cleartext_model(X: np.ndarray, y: np.ndarray, plan: Plan, baby: int) -> tuple[np.ndarray, np.ndarray]:
+    """Slot-exact cleartext model of the schedule: sum_g RotL(sum_c sum_b e'_{gB+b} (x) RotL(y_c, b), gB).
+    Returns (slots [R][N'], lazy-RaS result [m])."""
+    B, G = bsgs_split(plan, baby)
+    E = bsgs_diagonal_slots(X, plan, baby)
+    Y = vector_slots(y, plan)
+    acc = np.zeros((plan.row_blocks, plan.slots))
+    for r in range(plan.row_blocks):
+        for g in range(G):
+            inner = np.zeros(plan.slots)
+            for c in range(plan.col_blocks):
+                for b in range(B):
+                    inner += E[r, c, g * B + b] * rotl(Y[c], b)
+            acc[r] += rotl(inner, g * B)
+    return acc, lazy_ras(acc, plan)

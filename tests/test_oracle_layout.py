@@ -172,3 +172,43 @@ def test_ciphertext_ras_model_equals_lazy_ras(m, n, slots):
     for r in steps:
         T = T + np.stack([layout.rotl(row, r) for row in T])
     assert np.array_equal(layout.ras_decode(T, plan), layout.lazy_ras(S, plan))
+
+
+@pytest.mark.parametrize("m,n,slots", [(16, 16, 16), (256, 1024, 4096), (1024, 256, 4096), (64, 64, 64), (130, 130, 64),
+                                       (100, 37, 64), (20, 130, 64), (8, 8, 8)])
+def test_bsgs_schedule_equals_diagonal_method(m, n, slots):
+    """The baby-step giant-step schedule (sum_g RotL(sum_b RotR(e_{gB+b}, gB) (x) RotL(y, b), gB))
+    gives the slots of the diagonal method exactly, for every power-of-two split of m'; with the
+    pre-rotation left out (or its direction reversed) it does not."""
+    rng = np.random.default_rng(m * 31 + n)
+    X = rng.integers(-9, 10, size=(m, n)).astype(np.float64)
+    y = rng.integers(-9, 10, size=n).astype(np.float64)
+    plan = layout.make_plan(m, n, slots)
+    want, _ = layout.cleartext_model(X, y, plan)
+    B = 1
+    while B <= plan.m_prime:
+        got, out = layout.bsgs_cleartext_model(X, y, plan, B)
+        assert np.array_equal(got, want)
+        assert np.array_equal(out, X @ y)
+        baby, giant = layout.bsgs_steps(plan, B)
+        assert len(baby) + len(giant) == B - 1 + plan.m_prime // B - 1
+        B *= 2
+    if plan.m_prime >= 4:
+        B = plan.m_prime // 4  # G = 4 giant steps: RotR and RotL by g B differ for g = 1
+        E = layout.diagonal_slots(X, plan)
+        Y = layout.vector_slots(y, plan)
+        for sign in (0, -1):  # no pre-rotation; RotL instead of RotR
+            acc = np.zeros((plan.row_blocks, plan.slots))
+            for r in range(plan.row_blocks):
+                for g in range(plan.m_prime // B):
+                    inner = sum(np.roll(E[r, c, g * B + b], sign * g * B) * layout.rotl(Y[c], b)
+                                for c in range(plan.col_blocks) for b in range(B))
+                    acc[r] += layout.rotl(inner, g * B)
+            assert not np.array_equal(acc, want)
+
+
+def test_bsgs_split_rejects_bad_baby():
+    plan = layout.make_plan(256, 1024, 4096)
+    for bad in (0, 3, 128):
+        with pytest.raises(ValueError):
+            layout.bsgs_split(plan, bad)

@@ -331,3 +331,24 @@ def test_matmult_same_on_any_thread_count():
     assert plan.m_prime > 8
     for a, b in zip(one, many):
         assert np.array_equal(a.data, b.data)
+
+
+@pytest.mark.parametrize("m,n,baby", [(256, 256, 4), (256, 16, 2), (16, 256, 8), (128, 512, 16), (256, 256, 64)])
+def test_matmult_bsgs_matches_fp64_product(m, n, baby):
+    """The baby-step giant-step MatMult (O1-O4 composition) decrypts to X y within the scale-2^40
+    tolerance, and agrees with the diagonal method's result within it."""
+    o = ckks.Oracle(log_n=7, q_bits=[60, 40, 40], p_bits=[60], dnum=3, seed=9)
+    rng = np.random.default_rng(m + 3 * n + baby)
+    X = rng.normal(size=(m, n))
+    y = rng.uniform(-1, 1, n)
+    plan = layout.make_plan(m, n, o.slots)
+    if plan.m_prime % baby:
+        pytest.skip("baby steps must divide m'")
+    cts = o.encrypt_vector(y, plan, 2.0**40)
+    pts = o.encode_matrix_bsgs(X, plan, 2, baby)
+    outs = o.matmult_bsgs(pts, cts, plan, baby)
+    assert outs[0].level == 1 and abs(outs[0].scale - 2.0**40) < 1e-3
+    got = o.matmult_decode(outs, plan)
+    assert np.abs(got - X @ y).max() < TOL_2_40
+    ref = o.matmult_decode(o.matmult(o.encode_matrix(X, plan, 2, ext=True), cts, plan), plan)
+    assert np.abs(got - ref).max() < TOL_2_40
