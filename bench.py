@@ -381,6 +381,8 @@ def run_gpu(args):
         "clocks": clocks,
     }
     line["rotations"] = run_rotations(ctx, he, P, args, flush, world, dev)
+    if not args.no_bsgs:
+        line["bsgs"] = run_bsgs(ctx, he, inputs, P, args, flush, world, dev)
     if not args.no_batched:
         line["batched"] = run_batched(ctx, he, inputs, P, args, flush, world, dev)
     if not args.no_serving and rank == 0:
@@ -462,6 +464,63 @@ def _event_times(fn, reps, flush, warm=3):
 def _pct(times, q):
     t = sorted(times)
     return round(t[min(len(t) - 1, int(q * len(t)))], 4)
+
+
+def bsgs_baby(m_prime: int) -> int:
+    """Baby steps of the BSGS schedule for m' diagonals: the power of two nearest sqrt(m') from
+    above (so baby and giant counts differ by at most a factor 2)."""
+    b = 1
+    while b * b < m_prime:
+        b *= 2
+    return b
+
+
+def run_bsgs(ctx, he, inputs, P, args, flush, world, dev):
+    """The baby-step giant-step schedule (he_plan_set_baby_steps) against the diagonal method on the
+    same inputs: one plain MatMult call at the gradient shape (256 x 1024, m' = 64, B = 8), the 64
+    uneven batched jobs as plain calls, and Galois-key bytes resident for each."""
+    import numpy as np
+    import torch
+
+    level = P.top
+    key_bytes = P.dnum * 2 * (len(P.q_bits) + len(P.p_bits)) * P.n * 8
+    X, r, _ = inputs.gradient_and_forward_n8192(seed=0)
+    XT = torch.from_numpy(np.ascontiguousarray(X.T)).to(dev)
+    out = {}
+    for name, baby in (("diagonal", 0), ("bsgs", 8)):
+        plan = he.Plan(256, 1024, P.slots, baby=baby)
+        ctx.keygen(plan.rotation_steps)
+        pm = ctx.encode_matrix(plan, XT, level)
+        ct = ctx.encrypt_vector(plan, torch.from_numpy(r).to(dev), P.scale, level, 777)
+        res = [ctx.new_ct(level - 1)]
+        t = _event_times(lambda: ctx.matmult(plan, pm, ct, res), max(args.steps, 10), flush)
+        err = float(np.abs(ctx.matmult_decrypt(plan, res).cpu().numpy() - X.T @ r).max())
+        out[name] = {"matmult_ms": {"p50": _pct(t, 0.5), "p99": _pct(t, 0.99)}, "matmult_per_sec": round(1e3 / statistics.median(t), 1),
+                     "galois_keys": len(plan.rotation_steps), "key_bytes": len(plan.rotation_steps) * key_bytes, "max_abs_err": err,
+                     "baby_steps": baby}
+    # the batched workload's 64 uneven jobs, each as one plain call
+    jobs = inputs.batched_instances(64, seed=0)
+    for name, use in (("diagonal", False), ("bsgs", True)):
+        plans, pms, cts, steps = [], [], [], set()
+        for i, (Xj, rj) in enumerate(jobs):
+            b_, f_ = Xj.shape
+            base = he.Plan(f_, b_, P.slots)
+            plan = he.Plan(f_, b_, P.slots, baby=bsgs_baby(base.m_prime) if use else 0)
+            steps |= set(plan.rotation_steps)
+            plans.append(plan)
+        ctx.keygen(sorted(steps))
+        for i, ((Xj, rj), plan) in enumerate(zip(jobs, plans)):
+            pms.append(ctx.encode_matrix(plan, torch.from_numpy(Xj.T.copy()).to(dev), level))
+            cts.append(ctx.encrypt_vector(plan, torch.from_numpy(rj).to(dev), P.scale, level, 91000 + i))
+        outs = [[ctx.new_ct(level - 1)] for _ in jobs]
+        t = _event_times(lambda: [ctx.matmult(p, m, c, o) for p, m, c, o in zip(plans, pms, cts, outs)], max(3, min(args.steps, 10)), flush, warm=1)
+        out[name]["batched_jobs_as_plain_calls_per_sec"] = round(64e3 / statistics.median(t), 1)
+        out[name]["batched_jobs_galois_keys"] = len(steps)
+        out[name]["batched_jobs_key_bytes"] = len(steps) * key_bytes
+    out["workload"] = ("gradient X^T[[r]] 256x1024 (m'=64, B=8 baby x 8 giant steps) as one plain MatMult call; the 64 uneven batched "
+                       "jobs as plain calls (B = the power of two >= sqrt(m')); N=8192; the persistent batch kernel and the batched "
+                       "server lanes run the diagonal method only")
+    return out
 
 
 def run_small(he, inputs, args, flush, world, dev, rank):
@@ -840,6 +899,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-vfl-nn", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-bsgs", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time the eager step (one API call per operation) as the headline")
     ap.add_argument("--streams", type=int, default=2, choices=[1, 2, 4],
                     help="2: the forward product on a forked context and its own stream, overlapping the gradient product; 4: also each matrix encoding on a stream of its own")

@@ -166,6 +166,20 @@ int he_plan_create(int64_t m, int64_t n, int64_t slots, he_plan **out);
  * col_blocks (input cts), m_prime (diagonals per block), packed groups per ct. */
 int he_plan_query(const he_plan *plan, int64_t *info);
 void he_plan_free(he_plan *plan);
+/* Baby-step giant-step schedule of the diagonal method (an extension of Tab. 2's PackVFL row,
+ * not in the paper): with baby = B > 0 (a power of two dividing m') the plan's MatMult computes
+ * sum_g RotL( sum_b RotR(e_{gB+b}, gB) (x) RotL(y, b), gB ) over g < m'/B, b < B, which equals
+ * sum_i e_i (x) RotL(y, i).  Matrices encoded under the plan hold the pre-rotated plaintexts;
+ * he_matmult_plain_cipher then runs B - 1 hoisted baby rotations per input, one
+ * multiply-accumulate launch per output and m'/B - 1 giant rotations, with B - 1 + m'/B - 1
+ * Galois keys instead of m' - 1 (fewer key bytes, more key-switching launches).  baby = 0 (the
+ * default) restores the diagonal method.  Set it before encoding a matrix with the plan; batches,
+ * the batched server lanes and he_matmult_plain_cipher_noalloc take only baby = 0 plans
+ * (HE_EINVAL).  HE_EINVAL if baby is not 0 or a power of two dividing m'. */
+int he_plan_set_baby_steps(he_plan *plan, int64_t baby);
+/* The left-rotation steps whose Galois keys the plan's MatMult needs (1..m'-1, or the baby
+ * steps 1..B-1 then the giant steps g B), into steps (may be NULL to count them). */
+int he_plan_rotation_steps(const he_plan *plan, int32_t *steps, int *n_steps);
 
 /* Encode X (device, row-major m x n doubles) into its diagonal plaintexts (Eq. 2 after Eq. 3):
  * e_{r,c,i}[b nb + j] = X[r mb + b m' + (j mod m'), c nb + (i + j) mod nb], at scale

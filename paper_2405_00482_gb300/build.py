@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhe.so")
-SOURCES = ["he_api.cu", "he_ntt.cu", "he_ops.cu", "he_encode.cu", "he_noalloc.cu", "he_server.cu", "he_cdiag.cu", "he_host.cu", "he_bconv.cu", "he_keyswitch.cu"]
+SOURCES = ["he_api.cu", "he_ntt.cu", "he_ops.cu", "he_encode.cu", "he_noalloc.cu", "he_server.cu", "he_cdiag.cu", "he_host.cu", "he_bconv.cu", "he_keyswitch.cu", "he_bsgs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++20", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "--fmad=false"]
 

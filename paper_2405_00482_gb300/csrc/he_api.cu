@@ -788,7 +788,28 @@ int he_plan_create(int64_t m, int64_t n, int64_t slots, he_plan **out) {
     p->col_blocks = p->np / p->nb;
     p->m_prime = std::max<int64_t>(1, p->mb * p->nb / slots);
     p->blocks = slots / p->nb;
+    p->baby = 0;
     *out = p;
+    return HE_OK;
+}
+
+int he_plan_set_baby_steps(he_plan *p, int64_t baby) {
+    if (!p || baby < 0 || (baby & (baby - 1)) || (baby && p->m_prime % baby)) return HE_EINVAL;
+    p->baby = baby;
+    return HE_OK;
+}
+
+int he_plan_rotation_steps(const he_plan *p, int32_t *steps, int *n_steps) {
+    if (!p || !n_steps) return HE_EINVAL;
+    std::vector<int32_t> v;
+    if (p->baby == 0) {
+        for (int64_t i = 1; i < p->m_prime; ++i) v.push_back((int32_t)i);
+    } else {
+        for (int64_t b = 1; b < p->baby; ++b) v.push_back((int32_t)b);
+        for (int64_t g = 1; g < p->m_prime / p->baby; ++g) v.push_back((int32_t)(g * p->baby));
+    }
+    if (steps) std::copy(v.begin(), v.end(), steps);
+    *n_steps = (int)v.size();
     return HE_OK;
 }
 
@@ -985,6 +1006,7 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
     }
     for (int r = 0; r < n_out; ++r)
         if (!outs[r].data) return HE_EINVAL;
+    if (p.baby) return matmult_bsgs(ctx, pm, ins, outs);
     int rc = ptmat_bind_keys(ctx, pm);
     if (rc != HE_OK) return rc;
     const ModUpConst &mu = ctx->modup[level];
@@ -1155,7 +1177,7 @@ int he_batch_create(he_ctx *ctx, int count, const he_plan *const *plans, const h
     for (int j = 0; j < count; ++j) {
         if (!plans[j] || !pms[j] || !same_family(pms[j]->ctx, ctx)) return HE_EINVAL;
         const he_plan &p = pms[j]->plan;
-        if (p.m != plans[j]->m || p.n != plans[j]->n || p.row_blocks != 1 || p.col_blocks != 1) return HE_EINVAL;
+        if (p.m != plans[j]->m || p.n != plans[j]->n || p.row_blocks != 1 || p.col_blocks != 1 || p.baby) return HE_EINVAL;
         if (pms[j]->level != level) return HE_ELEVEL;
         int rc = ptmat_bind_keys(ctx, const_cast<he_ptmat *>(pms[j]));
         if (rc != HE_OK) return rc;

@@ -272,9 +272,11 @@ struct MatrixSrc {
     he_plan p;
     const double *X;  // m x n row-major, or its n x m transpose when trans
     int trans, lm, lc, lnb, lmb;  // log2 of m', column blocks, nb, mb
-    __device__ __forceinline__ double operator()(int item, int j) const {
+    __device__ __forceinline__ double operator()(int item, int j0) const {
         const int64_t i = item & (p.m_prime - 1), rest = item >> lm;
         const int64_t c = rest & (p.col_blocks - 1), r = rest >> lc;
+        // BSGS schedule: diagonal i = g B + b pre-rotated right by g B slots
+        const int64_t j = p.baby ? (j0 - (i - (i & (p.baby - 1)))) & (p.slots - 1) : j0;
         const int64_t b = j >> lnb, jj = j & (p.nb - 1);
         const int64_t row = (r << lmb) + (b << lm) + (jj & (p.m_prime - 1));
         const int64_t col = (c << lnb) + ((i + jj) & (p.nb - 1));

@@ -238,7 +238,10 @@ struct BatchGeom {
 
 struct he_plan {
     int64_t m, n, slots, mp, np, mb, nb, row_blocks, col_blocks, m_prime, blocks;
+    int64_t baby;  // 0: the diagonal method's m' - 1 hoisted rotations; else baby steps B of the BSGS schedule
 };
+// the BSGS MatMult (he_bsgs.cu) of an encoded matrix whose plan has baby steps
+int matmult_bsgs(he_ctx *ctx, he_ptmat *pm, const he_ct *ins, he_ct *outs);
 
 struct he_ptmat {
     he_ctx *ctx;

@@ -69,7 +69,7 @@ extern "C" int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan,
     if (!ctx || !plan || !pm || !ins || !outs || !same_family(pm->ctx, ctx)) return HE_EINVAL;
     const he_plan &p = pm->plan;
     if (p.m != plan->m || p.n != plan->n || p.slots != plan->slots) return HE_EINVAL;
-    if (n_in != p.col_blocks || n_out != p.row_blocks) return HE_EINVAL;
+    if (n_in != p.col_blocks || n_out != p.row_blocks || p.baby) return HE_EINVAL;
     const int level = pm->level;
     for (int c = 0; c < n_in; ++c) {
         if (!ins[c].data) return HE_EINVAL;

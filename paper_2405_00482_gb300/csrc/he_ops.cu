@@ -1045,9 +1045,10 @@ __global__ void layout_matrix_kernel(he_plan p, const double *__restrict__ X, do
     HE_GRID_DEP();
     const int ls = lg2p(p.slots), lm = lg2p(p.m_prime), lc = lg2p(p.col_blocks), lnb = lg2p(p.nb), lmb = lg2p(p.mb);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = idx & (p.slots - 1);
+        int64_t s = idx & (p.slots - 1);
         int64_t rest = idx >> ls;
         const int64_t i = rest & (p.m_prime - 1);
+        if (p.baby) s = (s - (i - (i & (p.baby - 1)))) & (p.slots - 1);  // BSGS: RotR(e_i, g B), i = g B + b
         rest >>= lm;
         const int64_t c = rest & (p.col_blocks - 1), r = rest >> lc;
         const int64_t b = s >> lnb, jj = s & (p.nb - 1);

@@ -236,6 +236,7 @@ int he_server_create(he_ctx *ctx, int slots, int level, size_t hbm_budget_bytes,
 int he_server_submit(he_server *s, const he_plan *plan, const he_ptmat *pm, const he_ct *in, he_ct *out, int64_t *request_id) {
     if (!s || !plan || !pm || !in || !out || !request_id || !in->data || !out->data || !same_family(pm->ctx, s->ctx)) return HE_EINVAL;
     if (pm->plan.row_blocks != 1 || pm->plan.col_blocks != 1 || pm->plan.m != plan->m || pm->plan.n != plan->n) return HE_EINVAL;
+    if (pm->plan.baby && !s->plain) return HE_EINVAL;  // the batch lanes run the diagonal method's loop kernel
     if (pm->level != s->level || in->level != s->level) return HE_ELEVEL;
     he_ctx *ctx = s->ctx;
     const size_t N = ctx->n;

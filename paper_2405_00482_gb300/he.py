@@ -71,6 +71,8 @@ _SIGS = {
     "he_plan_create": (ctypes.c_int, [_i64, _i64, _i64, ctypes.POINTER(_vp)]),
     "he_plan_query": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "he_plan_free": (None, [_vp]),
+    "he_plan_set_baby_steps": (ctypes.c_int, [_vp, _i64]),
+    "he_plan_rotation_steps": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]),
     "he_encode_matrix": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_ptmat_encode": (ctypes.c_int, [_vp, _vp, _vp]),
     "he_encode_matrix_transposed": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(_vp)]),
@@ -181,10 +183,15 @@ class Plan:
 
     FIELDS = ("m", "n", "slots", "mp", "np", "mb", "nb", "row_blocks", "col_blocks", "m_prime", "blocks")
 
-    def __init__(self, m: int, n: int, slots: int):
+    def __init__(self, m: int, n: int, slots: int, baby: int = 0):
+        """baby > 0: the baby-step giant-step schedule with that many baby steps
+        (he_plan_set_baby_steps); 0: the diagonal method."""
         h = _vp()
         _check(_lib().he_plan_create(m, n, slots, ctypes.byref(h)), "he_plan_create")
         self.handle = h
+        self.baby = baby
+        if baby:
+            _check(_lib().he_plan_set_baby_steps(h, baby), "he_plan_set_baby_steps")
         info = (_i64 * 11)()
         _check(_lib().he_plan_query(h, info), "he_plan_query")
         for k, v in zip(self.FIELDS, info):
@@ -194,6 +201,10 @@ class Plan:
         steps = (ctypes.c_int32 * max(n.value, 1))()
         _check(_lib().he_plan_ras_steps(h, steps, ctypes.byref(n)), "he_plan_ras_steps")
         self.ras_steps = [int(v) for v in steps[: n.value]]
+        _check(_lib().he_plan_rotation_steps(h, None, ctypes.byref(n)), "he_plan_rotation_steps")
+        steps = (ctypes.c_int32 * max(n.value, 1))()
+        _check(_lib().he_plan_rotation_steps(h, steps, ctypes.byref(n)), "he_plan_rotation_steps")
+        self.rotation_steps = [int(v) for v in steps[: n.value]]
 
     def __del__(self):
         if getattr(self, "handle", None):

@@ -166,3 +166,22 @@ def test_int8_basis_extension_wide_operands(he):
             for v in cases:
                 for h in cases[:3] + [[int(x) % t for x in v[::-1]]]:
                     assert _bconv_i8(he, v, h, t) == sum(x * y for x, y in zip(v, h)) % t
+
+
+@pytest.mark.parametrize("m,n,slots,baby", [(256, 1024, 4096, 8), (256, 1024, 4096, 1), (256, 1024, 4096, 64), (16, 16, 16, 4),
+                                            (600, 300, 512, 2), (1, 1, 8, 1)])
+def test_plan_baby_steps_agree_with_oracle(he, m, n, slots, baby):
+    """he_plan_rotation_steps lists the oracle's baby then giant steps; 0 gives 1..m'-1."""
+    plan = he.Plan(m, n, slots, baby=baby)
+    op = layout.make_plan(m, n, slots)
+    bs, gs = layout.bsgs_steps(op, baby)
+    assert plan.rotation_steps == bs + gs
+    assert he.Plan(m, n, slots).rotation_steps == op.rotation_steps
+
+
+def test_plan_baby_steps_rejected(he):
+    lib = he.lib()
+    plan = he.Plan(256, 1024, 4096)
+    for bad in (-1, 3, 128, 48):
+        assert lib.he_plan_set_baby_steps(plan.handle, bad) == he.HE_EINVAL
+    assert lib.he_plan_set_baby_steps(plan.handle, 0) == 0
