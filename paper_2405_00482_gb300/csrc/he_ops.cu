@@ -218,15 +218,13 @@ __device__ __forceinline__ void cl_intt_slice(uint64_t *s, const uint64_t *__res
 __device__ __forceinline__ uint64_t *cl_acc_slice(uint64_t *s, int logn) { return s + cl_tw_offset_words(logn) + 2 * (1 << (logn - 3)); }
 
 // LOGN > 0: the ring size at compile time (logn_rt == LOGN)
+// ModUp item (d, u) of one ciphertext (c1 in NTT form) as a cluster, the inverse NTT inside
 template <int LOGN = 0>
-__global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint64_t *D, ModUpConst mu, const uint64_t *__restrict__ d_tw,
-                                      const ModConst *__restrict__ mc, int logn_rt) {
-    HE_GRID_DEP();
-    const int logn = LOGN ? LOGN : logn_rt;
+__device__ __forceinline__ void modup_cl_fused_body(const uint64_t *__restrict__ c1_ntt, uint64_t *D, const ModUpConst &mu, int item,
+                                                    const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int off,
+                                                    int len) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
-    int item, off, len;
-    slice_of<true>(logn, item, off, len);
     const int d = item / mu.ext, u = item % mu.ext;
     const int lo = d * mu.alpha;
     const int hi = lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq;
@@ -255,6 +253,16 @@ __global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint6
     __syncthreads();
     ntt_fwd_cluster<LOGN>(s, tw, t, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
+}
+
+template <int LOGN = 0>
+__global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint64_t *D, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                      const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    modup_cl_fused_body<LOGN>(c1_ntt, D, mu, item, d_tw, mc, logn, off, len);
 }
 
 // ModDown of component c, output limb j: conversion of the K special-prime limbs (each brought
@@ -465,6 +473,22 @@ __global__ void rot_modup_kernel(const RotTable jobs, RotGeom rg, ModUpConst mu,
     const int j = blockIdx.x / per, rest = blockIdx.x % per;
     modup_body<false>(jobs.j[j].ct + (int64_t)rg.nl * (1 << logn), rg.coef + j * rg.coef_w, rg.D + j * rg.d_w, mu, rest / mu.ext, rest % mu.ext, s,
                       d_tw, mc, logn, 0, 1 << logn);
+}
+
+// ModUp of the jobs' c1 (NTT form) as clusters, item (j, d, u), the inverse NTT inside: for
+// launches of few rotations (at most HE_ROT_CL_MAX_ITEMS items, 8 CTAs each), where one CTA per
+// limb-poly would leave most SMs idle
+#define HE_ROT_CL_MAX_ITEMS 128
+template <int LOGN = 0>
+__global__ void rot_modup_cl_kernel(const RotTable jobs, RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                    const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int per = mu.ndig * mu.ext;
+    const int j = item / per;
+    modup_cl_fused_body<LOGN>(jobs.j[j].ct + (int64_t)rg.nl * (1 << logn), rg.D + j * rg.d_w, mu, item % per, d_tw, mc, logn, off, len);
 }
 
 // ---- batch forms: the same bodies over a job table (one job = one MatMult, R = C = 1) ----
@@ -1392,6 +1416,15 @@ void launch_rotate_many(he_ctx *ctx, const RotJob *jobs, int count, int level, u
     cudaStream_t st = ctx->stream;
     RotTable tab{};
     for (int j = 0; j < count; ++j) tab.j[j] = jobs[j];
+    const int items = count * mu.ndig * mu.ext;
+    if (ctx->bconv != HE_BCONV_INT8_TC && ctx->log_n >= HE_NTT_CL_MIN_LOGN && items <= HE_ROT_CL_MAX_ITEMS) {
+        // few rotations: one cluster launch does the inverse NTTs and the conversions
+        launch_cluster(by_logn(ctx->log_n, [](auto L) { return rot_modup_cl_kernel<L.value>; }), items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
+                       cl_fused_smem_bytes(ctx->log_n), st, tab, rg, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
+        ctx->launches++;
+        launch_keyswitch_many(ctx, jobs, count, level, rg.D, rg.d_w, rg.pcoef);
+        return;
+    }
     launch_k(rot_intt_c1_kernel, count * rg.nl, thr, smem, st, tab, rg, ctx->d_tw, ctx->d_mc, ctx->log_n);
     ctx->launches++;
     if (ctx->bconv == HE_BCONV_INT8_TC) {
@@ -1416,6 +1449,7 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(moddown_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(modup_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
+    each_logn([max_bytes](auto L) { cudaFuncSetAttribute(rot_modup_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(rescale_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_intt_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
