@@ -661,39 +661,50 @@ def run_batched(ctx, he, inputs, P, args, flush, world, dev):
             "plain_same_jobs": round(whole_job_rate(64 * args.steps, world, sp), 1), "speedup_vs_plain": round(sp / sb, 3),
             "rotations_per_sec": round(rot * args.steps * world / sb, 1), "batch_ms": {"p50": round(tb[len(tb) // 2], 4),
             "p99": round(tb[min(len(tb) - 1, int(0.99 * len(tb)))], 4)}, "hoisted_rotations_per_batch": rot,
-            "bit_identical_to_plain": bool(same), "autotune": batch.tuning(),
+            "bit_identical_to_plain": bool(same), "autotune": batch.tuning(), "stage_form": batch.stage_tuning(),
             "workload": "64 gradient MatMults X^T[[r]], X b x f ~ N(0,1), b ~ U{128..4096}, f ~ U{16..512} (seed 0), N=8192"}
 
 
 def run_serving(ctx, he, inputs, P, args, dev):
-    """Poisson arrivals (mean 500 requests/s, seed 0) of MatMult requests whose shapes are drawn
-    uniformly from the N = 8192 workloads (gradient 256x1024, forward 1024x256, the 16x64
-    gradient shape, and the 64 uneven batched shapes), matrices and keys resident, admission by
-    a 120 GB budget.  The continuous-batching server and the one-request-per-call server see
-    the same arrival times; a second pass offers requests as fast as they can be submitted."""
+    """Poisson arrivals (mean 500 requests/s for --serve-seconds, seed 0) of MatMult requests whose
+    shapes are drawn uniformly from the configurations: the 16x64 gradient on its own N = 4096 ring
+    (chain [40, 20 | 40], scale 2^20), the N = 8192 gradient 256x1024 and forward 1024x256, and the
+    64 uneven batched shapes (N = 8192).  One server holds both rings under one 120 GB budget,
+    matrices and keys resident; every matrix has made one product (its loop-kernel tuning) before
+    timing.  The continuous-batching server and the one-request-per-call server see the same
+    arrival times; a second pass offers the requests as fast as they can be submitted."""
     import numpy as np
     import torch
 
     level = P.top
+    PS = inputs.PARAMS_SMALL
+    small = he.Context(PS.log_n, list(PS.q_bits), list(PS.p_bits), PS.dnum, seed=300)
     rng = np.random.default_rng(0)
-    shapes = [(256, 1024), (1024, 256), (16, 64)] + [(X.shape[1], X.shape[0]) for X, _ in inputs.batched_instances(64, seed=0)]
+    # (config, ring context, level, scale, shape)
+    kinds = [("cfg1 16x64 N=4096", small, PS.top, PS.scale, (16, 64)), ("cfg2 256x1024", ctx, level, P.scale, (256, 1024)),
+             ("cfg2 1024x256", ctx, level, P.scale, (1024, 256))]
+    kinds += [("cfg3 batched shapes", ctx, level, P.scale, (X.shape[1], X.shape[0])) for X, _ in inputs.batched_instances(64, seed=0)]
     pool = []
-    for i, (m, n) in enumerate(shapes):
-        plan = he.Plan(m, n, P.slots)
-        ctx.keygen(list(range(1, plan.m_prime)))
+    for i, (name, c, lvl, scale, (m, n)) in enumerate(kinds):
+        plan = he.Plan(m, n, c.slots)
+        c.keygen(list(range(1, plan.m_prime)))
         X = torch.from_numpy(rng.normal(size=(m, n))).to(dev)
         y = torch.from_numpy(rng.uniform(-1, 1, n)).to(dev)
-        pm = ctx.encode_matrix(plan, X, level)
-        ct = ctx.encrypt(ctx.encode_vector(plan, y, P.scale, level)[0], 70000 + i)
-        pool.append((plan, pm, ct))
-    ring = [ctx.new_ct(level - 1) for _ in range(1024)]
+        pm = c.encode_matrix(plan, X, lvl)
+        ct = c.encrypt_vector(plan, y, scale, lvl, 70000 + i)[0]
+        c.matmult(plan, pm, [ct])  # tunes the matrix's loop kernel before any timing
+        pool.append((name, c, lvl, plan, pm, ct))
     ctx.synchronize()
-    n_req = args.serve_requests
-    kinds = rng.integers(0, len(pool), size=n_req)
+    small.synchronize()
+    n_req = int(500 * args.serve_seconds)
+    pick = rng.integers(0, 3, size=n_req)  # config 1, 2 or 3 uniformly
+    which = np.where(pick == 0, 0, np.where(pick == 1, 1 + rng.integers(0, 2, size=n_req), 3 + rng.integers(0, 64, size=n_req)))
     gaps = rng.exponential(1.0 / 500.0, size=n_req)
+    ring_out = {id(ctx): [ctx.new_ct(level - 1) for _ in range(1024)], id(small): [small.new_ct(PS.top - 1) for _ in range(1024)]}
 
     def serve(plain: bool, paced: bool):
         server = he.Server(ctx, slots=32, level=level, hbm_budget_bytes=120 << 30, plain=plain)
+        server.add_ring(small, PS.top)
         rids, lat_of = [], {}
         t0 = time.perf_counter()
         t_next = t0
@@ -702,23 +713,30 @@ def run_serving(ctx, he, inputs, P, args, dev):
                 t_next += gaps[i]
                 while time.perf_counter() < t_next:
                     pass
-            plan, pm, ct = pool[kinds[i]]
-            rids.append(server.submit(plan, pm, ct, ring[i % len(ring)]))
-            if i >= len(ring) - 1:  # the output ring slot is reused: wait for its previous owner
-                r = rids[i - len(ring) + 1]
+            name, c, lvl, plan, pm, ct = pool[which[i]]
+            rids.append(server.submit(plan, pm, ct, ring_out[id(c)][i % 1024]))
+            if i >= 1023:  # the output ring slot is reused: wait for its previous owner
+                r = rids[i - 1023]
                 lat_of[r] = server.wait(r)
-        lats = [lat_of[r] if r in lat_of else server.wait(r) for r in rids]
+        lats = np.array([lat_of[r] if r in lat_of else server.wait(r) for r in rids])
         wall = time.perf_counter() - t0
         _, launches, _ = server.stats()
         server.close()
-        lat = sorted(lats)
-        return {"throughput": round(n_req / wall, 1), "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
-                "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3), "launches": launches}
 
-    out = {"offered_req_s": 500, "requests": n_req, "budget_gb": 120, "slots": 32,
+        def pcts(v):
+            v = np.sort(v)
+            return {"p50_ms": round(1e3 * v[len(v) // 2], 3), "p99_ms": round(1e3 * v[min(len(v) - 1, int(0.99 * len(v)))], 3), "n": int(len(v))}
+
+        cfg = np.array([pool[k][0].split()[0] for k in which])
+        out = {"throughput": round(n_req / wall, 1), **pcts(lats), "launches": launches,
+               "per_config": {c_: pcts(lats[cfg == c_]) for c_ in ("cfg1", "cfg2", "cfg3")}}
+        return out
+
+    out = {"offered_req_s": 500, "seconds": args.serve_seconds, "requests": n_req, "budget_gb": 120, "slots": 32,
            "batched": serve(False, True), "plain": serve(True, True),
            "saturated_batched": serve(False, False), "saturated_plain": serve(True, False),
-           "workload": "Poisson 500 req/s, shapes uniform over {256x1024, 1024x256, 16x64, 64 uneven batched shapes}, N=8192"}
+           "workload": "Poisson 500 req/s; configs 1-3 uniformly: cfg1 16x64 on an N=4096 ring, cfg2 256x1024 / 1024x256 and cfg3's "
+                       "64 uneven shapes on the N=8192 ring; one server, both rings, one 120 GB budget; matrices tuned before timing"}
     return out
 
 
@@ -905,7 +923,7 @@ def main():
                     help="2: the forward product on a forked context and its own stream, overlapping the gradient product; 4: also each matrix encoding on a stream of its own")
     ap.add_argument("--loop-variant", type=int, default=-1,
                     help="pin the MatMult loop-kernel variant of the plain products (default: autotune)")
-    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the paced Poisson stream (500 requests/s)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -299,6 +299,13 @@ int he_batch_tuning(const he_batch *batch, int *variant, float *ms);
  * graph on its next run (this call waits for the batch's previous run to finish). */
 int he_ptmat_set_variant(he_ptmat *pm, int v);
 int he_batch_set_variant(he_batch *batch, int v);
+/* A batch's ModUp, ModDown and rescale run as one CTA per limb-poly (form 0) or as 8-CTA clusters
+ * per limb-poly (form 1: fewer, shorter launches, for batches of few jobs); the results are the
+ * same.  The first he_batch_run times both forms with the chosen loop variant and keeps the faster;
+ * he_batch_stage_form reports it (form, and ms[0..1] when ms is not NULL), he_batch_set_stage_form
+ * pins one (0 or 1; re-captures the graph on the next run).  A server's batch lanes use form 1. */
+int he_batch_stage_form(const he_batch *batch, int *form, float *ms);
+int he_batch_set_stage_form(he_batch *batch, int form);
 
 /* Serving loop with continuous batching (requests of differing shapes, m, n <= N/2, at one
  * level).  A scheduler thread admits requests in arrival order while the device bytes they pin
@@ -311,9 +318,16 @@ int he_batch_set_variant(he_batch *batch, int v);
  * with CUDA events; no kernel waits on another. */
 typedef struct he_server he_server;
 int he_server_create(he_ctx *ctx, int slots, int level, size_t hbm_budget_bytes, int plain, he_server **out);
-/* Queue outs = MatMult(pm, in); in must be ready on the context's stream when this is called.
- * HE_EBUDGET if the request alone exceeds the budget.  *out's level and scale are set now, its
- * data when the request completes. */
+/* Serve a further ring: requests whose encoded matrix belongs to ctx's family at `level` (another
+ * ring size or parameter set, e.g. an N = 4096 context beside an N = 8192 one) get lanes of their
+ * own on ctx's stream, under the same budget and in the same arrival order.  Only before the first
+ * submit (HE_EINVAL after, for a ring already served, or beyond 8 rings).  The server owns every
+ * ring's context while it runs, as it owns the first. */
+int he_server_add_ring(he_server *s, he_ctx *ctx, int level);
+/* Queue outs = MatMult(pm, in); in must be ready on its ring context's stream when this is called.
+ * HE_EBUDGET if the request alone exceeds the budget; HE_EINVAL for a matrix of no served ring
+ * (HE_ELEVEL for a served family at another level), or a baby-step plan on batch lanes.  *out's
+ * level and scale are set now, its data when the request completes. */
 int he_server_submit(he_server *s, const he_plan *plan, const he_ptmat *pm, const he_ct *in, he_ct *out, int64_t *request_id);
 /* Block until the request completes (its output is then ready for any stream) or timeout_us
  * passes (HE_ETIMEOUT); latency_s (optional) = completion - submission, host clock.  Once it

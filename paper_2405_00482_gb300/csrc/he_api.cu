@@ -1223,9 +1223,27 @@ int he_batch_run(he_ctx *ctx, he_batch *b, const he_ct *ins, he_ct *outs) {
                 best = v;
             }
         }
+        // then the stage form (one-CTA or cluster ModUp / ModDown / rescale) with that variant
+        b->variant = best;
+        int best_form = 0;
+        for (int f = 0; f < 2; ++f) {
+            b->stage_form = f;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, b->stream);
+                if (launch_matmult_batch(ctx, b, b->stream) != HE_OK) break;
+                cudaEventRecord(e1, b->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0 && t < ms) ms = t;
+            }
+            b->stage_ms[f] = ms;
+            if (ms < b->stage_ms[best_form]) best_form = f;
+        }
+        b->stage_form = best_form;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        b->variant = best;
         ctx->batch_variant = best;
     }
     int rc = batch_launch(ctx, b);
@@ -1276,6 +1294,27 @@ int he_batch_tuning(const he_batch *b, int *variant, float *ms) {
     *variant = b->variant;
     if (ms)
         for (int v = 0; v < mm_variant_count(); ++v) ms[v] = b->tune_ms[v];
+    return HE_OK;
+}
+
+int he_batch_stage_form(const he_batch *b, int *form, float *ms) {
+    if (!b || !form) return HE_EINVAL;
+    *form = b->stage_form;
+    if (ms) {
+        ms[0] = b->stage_ms[0];
+        ms[1] = b->stage_ms[1];
+    }
+    return HE_OK;
+}
+
+int he_batch_set_stage_form(he_batch *b, int form) {
+    if (!b || form < 0 || form > 1) return HE_EINVAL;
+    if (b->have_graph) {
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HE_ECUDA;
+        cudaGraphExecDestroy(b->exec);
+        b->have_graph = false;
+    }
+    b->stage_form = form;
     return HE_OK;
 }
 

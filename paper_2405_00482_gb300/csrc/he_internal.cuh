@@ -269,6 +269,8 @@ struct he_batch {
     int ctas_v[HE_MM_MAX_VARIANTS] = {};           // persistent grid per variant (resident CTAs per SM x SMs)
     int variant = -1;            // chosen by timing on the first run (-1: not yet)
     float tune_ms[HE_MM_MAX_VARIANTS] = {};
+    int stage_form = 0;          // ModUp / ModDown / rescale stages: 0 one CTA per limb-poly, 1 8-CTA clusters (timed with the variant)
+    float stage_ms[2] = {};
     unsigned int *d_counter;     // work-queue head
     BatchGeom bg;
     uint64_t *mem;               // per-job scratch

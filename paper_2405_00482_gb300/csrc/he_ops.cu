@@ -356,15 +356,12 @@ __global__ void rescale_cl_fused_kernel(const uint64_t *__restrict__ ct, int lev
 // add_c[L] + x_L P^-1), into tmp [2][K+1][N]; moddown_rescale_ntt_kernel forms w_j per coefficient
 // and transforms it.  (One launch doing the K + 2 transforms in a row took longer.)
 template <int LOGN = 0>
-__global__ void moddown_rescale_intt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, const uint64_t *__restrict__ add0,
-                                            const uint64_t *__restrict__ add1, uint64_t *tmp, const uint64_t *__restrict__ d_tw,
-                                            const ModConst *__restrict__ mc, int logn_rt) {
-    HE_GRID_DEP();
-    const int logn = LOGN ? LOGN : logn_rt;
+__device__ __forceinline__ void moddown_rescale_intt_body(const uint64_t *__restrict__ x, int ext, const ModDownConst &md,
+                                                          const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *tmp,
+                                                          int item, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn,
+                                                          int off, int len) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
-    int item, off, len;
-    slice_of<true>(logn, item, off, len);
     const int c = item / (md.K + 1), r = item % (md.K + 1);
     const int L = md.nq - 1;
     uint64_t *o = tmp + ((int64_t)c * (md.K + 1) + r) * N + off;
@@ -397,15 +394,23 @@ __global__ void moddown_rescale_intt_kernel(const uint64_t *__restrict__ x, int 
 }
 
 template <int LOGN = 0>
-__global__ void moddown_rescale_ntt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, RescaleConst rc,
-                                           const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, const uint64_t *__restrict__ tmp,
-                                           uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
+__global__ void moddown_rescale_intt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, const uint64_t *__restrict__ add0,
+                                            const uint64_t *__restrict__ add1, uint64_t *tmp, const uint64_t *__restrict__ d_tw,
+                                            const ModConst *__restrict__ mc, int logn_rt) {
     HE_GRID_DEP();
     const int logn = LOGN ? LOGN : logn_rt;
-    extern __shared__ uint64_t s[];
-    const int N = 1 << logn;
     int item, off, len;
     slice_of<true>(logn, item, off, len);
+    moddown_rescale_intt_body<LOGN>(x, ext, md, add0, add1, tmp, item, d_tw, mc, logn, off, len);
+}
+
+template <int LOGN = 0>
+__device__ __forceinline__ void moddown_rescale_ntt_body(const uint64_t *__restrict__ x, int ext, const ModDownConst &md, const RescaleConst &rc,
+                                                         const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1,
+                                                         const uint64_t *__restrict__ tmp, uint64_t *out, int item, const uint64_t *__restrict__ d_tw,
+                                                         const ModConst *__restrict__ mc, int logn, int off, int len) {
+    extern __shared__ uint64_t s[];
+    const int N = 1 << logn;
     const int L = md.nq - 1;
     const int c = item / L, j = item % L;
     const int pj = md.q_prime[j], pl = md.q_prime[L];
@@ -439,6 +444,17 @@ __global__ void moddown_rescale_ntt_kernel(const uint64_t *__restrict__ x, int e
         if (aj) v = add_mod(v, aj[k], q);
         o[k] = mul_shoup(sub_mod(v, s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
     }
+}
+
+template <int LOGN = 0>
+__global__ void moddown_rescale_ntt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, RescaleConst rc,
+                                           const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, const uint64_t *__restrict__ tmp,
+                                           uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    moddown_rescale_ntt_body<LOGN>(x, ext, md, rc, add0, add1, tmp, out, item, d_tw, mc, logn, off, len);
 }
 
 // ---- many rotations: O3 of different ciphertexts, each by its own step, one launch per stage ----
@@ -579,6 +595,52 @@ __global__ void batch_rescale_kernel(const MMJob *__restrict__ jobs, BatchGeom b
     if (jobs[j].m_prime == 0) return;  // empty slot
     rescale_body<false>(bg.sum + (int64_t)j * bg.sum_words, bg.level, bg.tmp + (int64_t)j * bg.tmp_words + (int64_t)2 * bg.K * (1 << logn),
                         rc, jobs[j].out, c, l, s, d_tw, mc, logn, 0, 1 << logn);
+}
+
+// ---- batch stages as clusters (stage form 1): for batches with few jobs (a serving lane's),
+// where one CTA per limb-poly leaves most SMs idle and each stage waits a whole one-CTA
+// transform.  ModUp of every job in one launch (inverse NTT inside), then ModDown and rescale in
+// two launches, each item one 8-CTA cluster; empty slots (m' = 0, or m' = 1 for ModUp) return at
+// once, uniformly over their cluster.  The same bodies as the single MatMult's cluster kernels,
+// so the results are bit-identical to the one-CTA stages.
+template <int LOGN = 0>
+__global__ void batch_modup_cl_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                      const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int per = mu.ndig * mu.ext, j = item / per;
+    if (jobs[j].m_prime <= 1) return;
+    modup_cl_fused_body<LOGN>(jobs[j].ct + (int64_t)bg.nq * (1 << logn), bg.D + (int64_t)j * bg.d_words, mu, item % per, d_tw, mc, logn, off, len);
+}
+
+template <int LOGN = 0>
+__global__ void batch_mdr_intt_cl_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                         const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int per = 2 * (md.K + 1), j = item / per;
+    if (jobs[j].m_prime == 0) return;
+    const uint64_t *cacc = bg.cacc + (int64_t)j * bg.cacc_words;
+    moddown_rescale_intt_body<LOGN>(bg.acc + (int64_t)j * bg.acc_words, bg.ext, md, cacc, cacc + (int64_t)bg.nq * (1 << logn),
+                                    bg.tmp + (int64_t)j * bg.tmp_words, item % per, d_tw, mc, logn, off, len);
+}
+
+template <int LOGN = 0>
+__global__ void batch_mdr_ntt_cl_kernel(const MMJob *__restrict__ jobs, BatchGeom bg, ModDownConst md, RescaleConst rc, const uint64_t *__restrict__ d_tw,
+                                        const ModConst *__restrict__ mc, int logn_rt) {
+    HE_GRID_DEP();
+    const int logn = LOGN ? LOGN : logn_rt;
+    int item, off, len;
+    slice_of<true>(logn, item, off, len);
+    const int per = 2 * bg.level, j = item / per;
+    if (jobs[j].m_prime == 0) return;
+    const uint64_t *cacc = bg.cacc + (int64_t)j * bg.cacc_words;
+    moddown_rescale_ntt_body<LOGN>(bg.acc + (int64_t)j * bg.acc_words, bg.ext, md, rc, cacc, cacc + (int64_t)bg.nq * (1 << logn),
+                                   bg.tmp + (int64_t)j * bg.tmp_words, jobs[j].out, item % per, d_tw, mc, logn, off, len);
 }
 
 // The double-hoisted MatMult loop.  For every coefficient k of extended limb u:
@@ -1366,10 +1428,24 @@ int launch_matmult_batch(he_ctx *ctx, he_batch *b, cudaStream_t stream) {
     const RescaleConst rc = make_rescale_const(ctx, level);
     if (cudaMemcpyAsync(b->d_jobs, b->h_jobs, sizeof(MMJob) * count, cudaMemcpyHostToDevice, stream) != cudaSuccess) return HE_ECUDA;
     if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), stream) != cudaSuccess) return HE_ECUDA;
-    launch_k(batch_intt_c1_kernel, count * bg.nq, thr, smem, stream, b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
-    launch_k(batch_modup_kernel, count * mu.ndig * mu.ext, thr, smem, stream, b->d_jobs, bg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
     const int v = b->variant < 0 ? 0 : b->variant;
     const dim3 pgrid((unsigned)b->ctas_v[v]);
+    const int logn = ctx->log_n;
+    if (b->stage_form == 1 && logn >= HE_NTT_CL_MIN_LOGN && level >= 1) {
+        // stages as clusters: ModUp, loop, ModDown + rescale (four launches)
+        const int cl = cl_threads(logn);
+        launch_cluster(by_logn(logn, [](auto L) { return batch_modup_cl_kernel<L.value>; }), count * mu.ndig * mu.ext * HE_NTT_CL_SIZE, cl,
+                       cl_fused_smem_bytes(logn), stream, (const MMJob *)b->d_jobs, bg, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, logn);
+        mm_launch_batch_variant(v, pgrid, stream, b->d_jobs, b->d_order_v[v], b->n_items_v[v], b->d_counter, bg, ctx->d_mc, logn);
+        launch_cluster(by_logn(logn, [](auto L) { return batch_mdr_intt_cl_kernel<L.value>; }), count * 2 * (ctx->K + 1) * HE_NTT_CL_SIZE, cl,
+                       cl_smem_bytes(logn), stream, (const MMJob *)b->d_jobs, bg, md, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, logn);
+        launch_cluster(by_logn(logn, [](auto L) { return batch_mdr_ntt_cl_kernel<L.value>; }), count * 2 * level * HE_NTT_CL_SIZE, cl,
+                       cl_smem_bytes(logn), stream, (const MMJob *)b->d_jobs, bg, md, rc, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, logn);
+        ctx->launches += 4;
+        return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
+    }
+    launch_k(batch_intt_c1_kernel, count * bg.nq, thr, smem, stream, b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
+    launch_k(batch_modup_kernel, count * mu.ndig * mu.ext, thr, smem, stream, b->d_jobs, bg, mu, ctx->d_tw, ctx->d_mc, ctx->log_n);
     mm_launch_batch_variant(v, pgrid, stream, b->d_jobs, b->d_order_v[v], b->n_items_v[v], b->d_counter, bg, ctx->d_mc, ctx->log_n);
     launch_k(batch_intt_p_kernel, count * 2 * bg.K, thr, smem, stream, b->d_jobs, bg, ctx->d_tw, ctx->d_mc, ctx->log_n);
     launch_k(batch_moddown_kernel, count * 2 * md.nq, thr, smem, stream, b->d_jobs, bg, md, ctx->d_tw, ctx->d_mc, ctx->log_n);
@@ -1450,6 +1526,11 @@ void ops_set_smem_limits(int max_bytes) {
     cudaFuncSetAttribute(rescale_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(modup_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(rot_modup_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
+    each_logn([max_bytes](auto L) {
+        cudaFuncSetAttribute(batch_modup_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(batch_mdr_intt_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(batch_mdr_ntt_cl_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+    });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(rescale_cl_fused_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });
     each_logn([max_bytes](auto L) { cudaFuncSetAttribute(moddown_rescale_intt_kernel<L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes); });

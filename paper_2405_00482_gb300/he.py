@@ -93,6 +93,8 @@ _SIGS = {
     "he_ptmat_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "he_batch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "he_loop_variant_count": (ctypes.c_int, []),
+    "he_batch_stage_form": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "he_batch_set_stage_form": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_ptmat_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_loop_variant_shape": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -105,6 +107,7 @@ _SIGS = {
     "he_cdiag_transpose": (ctypes.c_int, [_vp, ctypes.POINTER(HeCt), _i64, _i64, ctypes.POINTER(HeCt)]),
     "he_server_create": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)]),
     "he_server_submit": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(HeCt), ctypes.POINTER(HeCt), ctypes.POINTER(_i64)]),
+    "he_server_add_ring": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "he_server_wait": (ctypes.c_int, [_vp, _i64, _i64, ctypes.POINTER(_dbl)]),
     "he_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_size_t)]),
     "he_server_free": (None, [_vp]),
@@ -299,6 +302,16 @@ class Batch:
         """Pin the loop-kernel variant (-1: tune again on the next run)."""
         _check(_lib().he_batch_set_variant(self.handle, v), "he_batch_set_variant")
 
+    def stage_tuning(self) -> dict:
+        """ModUp / ModDown / rescale stage form (0 one CTA per limb-poly, 1 clusters) and both timings."""
+        f = ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        _check(_lib().he_batch_stage_form(self.handle, ctypes.byref(f), ms), "he_batch_stage_form")
+        return {"form": int(f.value), "form_ms": [round(float(x), 4) for x in ms]}
+
+    def set_stage_form(self, form: int) -> None:
+        _check(_lib().he_batch_set_stage_form(self.handle, form), "he_batch_set_stage_form")
+
     def run(self, cts: list[Ciphertext], outs: list[Ciphertext] | None = None) -> list[Ciphertext]:
         outs = outs or [self.ctx.new_ct(self.level - 1) for _ in cts]
         ia = (HeCt * len(cts))(*[c.c() for c in cts])
@@ -340,6 +353,11 @@ class Server:
         _check(_lib().he_server_create(ctx.handle, slots, level, hbm_budget_bytes, int(plain), ctypes.byref(h)), "he_server_create")
         self.handle = h
         self._keep = {}
+
+    def add_ring(self, ctx: "Context", level: int) -> None:
+        """Also serve ctx's family at `level` (he_server_add_ring), before the first submit."""
+        _check(_lib().he_server_add_ring(self.handle, ctx.handle, level), "he_server_add_ring")
+        self._ctxs = getattr(self, "_ctxs", []) + [ctx]
 
     def submit(self, plan: Plan, pm: "PtMatrix", ct: Ciphertext, out: Ciphertext) -> int:
         ci, co = ct.c(), out.c()

@@ -95,3 +95,23 @@ def test_batch_rejects_partitioned_plans(he):
     with pytest.raises(he.HEError) as e:
         he.Batch(ctx, [plan], [pm])
     assert e.value.status == he.HE_EINVAL
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_batch_stage_forms_bit_identical(he, form):
+    """The batch's ModUp / ModDown / rescale as one CTA per limb-poly (form 0) or as clusters
+    (form 1) give the single calls' ciphertexts bit for bit, at N = 8192 with an m' = 1 job and
+    uneven shapes; the first run's tuning reports both forms' times."""
+    ctx = he.Context(13, [60, 40, 40], [60], 3, seed=8)
+    shapes = [(16, 64), (256, 1024), (100, 300), (4096, 2), (7, 4000)]
+    jobs = _jobs(he, ctx, shapes, 3, 2.0**40)
+    b = he.Batch(ctx, [j[2] for j in jobs], [j[3] for j in jobs])
+    b.run([j[4] for j in jobs])  # tunes the loop variant, then the stage form
+    t = b.stage_tuning()
+    assert t["form"] in (0, 1) and all(ms > 0 for ms in t["form_ms"])
+    b.set_stage_form(form)
+    for rep in range(2):
+        outs = b.run([j[4] for j in jobs])
+        for (X, y, plan, pm, ct), o in zip(jobs, outs):
+            single = ctx.matmult(plan, pm, [ct])[0]
+            assert np.array_equal(he.as_u64(ctx.ct_export(o)), he.as_u64(ctx.ct_export(single)))

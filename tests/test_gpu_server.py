@@ -107,3 +107,43 @@ def test_wait_times_out_on_unfinished_request(env):
     for r in rids:
         server.wait(r)
     server.close()
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_two_rings_in_one_stream(env, plain):
+    """Requests on an N = 4096 ring (chain [40, 20 | 40], the 16 x 64 gradient shape) and on the
+    N = 8192 ring, submitted interleaved to one server under one budget: each result equals the
+    single call's ciphertext on its own ring."""
+    import torch
+
+    he, ctx, pool = env
+    small = he.Context(12, [40, 20], [40], 2, seed=12)
+    rng = np.random.default_rng(9)
+    spool = []
+    for i, (m, n) in enumerate([(16, 64), (64, 16), (100, 700)]):
+        X = rng.normal(size=(m, n))
+        y = rng.uniform(-1, 1, n)
+        plan = he.Plan(m, n, small.slots)
+        small.keygen(list(range(1, plan.m_prime)))
+        pm = small.encode_matrix(plan, torch.from_numpy(X).cuda(), 1)
+        ct = small.encrypt(small.encode_vector(plan, torch.from_numpy(y).cuda(), 2.0**20, 1)[0], 800 + i)
+        spool.append((plan, pm, ct, he.as_u64(small.ct_export(small.matmult(plan, pm, [ct])[0]))))
+    small.synchronize()
+    server = he.Server(ctx, slots=4, level=2, hbm_budget_bytes=120 << 30, plain=plain)
+    server.add_ring(small, 1)
+    subs = []
+    for t in range(12):
+        if t % 2:
+            plan, pm, ct, want = spool[t % len(spool)]
+            out = small.new_ct(0)
+            subs.append((server.submit(plan, pm, ct, out), out, want, small))
+        else:
+            plan, pm, ct, want, _, _ = pool[t % len(pool)]
+            out = ctx.new_ct(1)
+            subs.append((server.submit(plan, pm, ct, out), out, want, ctx))
+    for rid, out, want, c in subs:
+        server.wait(rid)
+        assert np.array_equal(he.as_u64(c.ct_export(out)), want)
+    completed, _, in_use = server.stats()
+    server.close()
+    assert completed == len(subs) and in_use == 0
