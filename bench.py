@@ -268,6 +268,24 @@ def run_gpu(args):
     ctx.profile(False)
     mm_ms = sorted(a.elapsed_time(b) for a, b in mm)
 
+    # the encoded matrix's transform (256 limb-polys: 64 diagonals x 4 limbs of Q U P), timed alone
+    ctx.profile(True)
+    _event_times(lambda: ctx.encode_matrix(plan_g, dX, level, out=pm_g, transposed=True), max(args.steps, 10), flush)
+    ntt_ms, ntt_n = ctx.profile_read(he.HE_PROF_MATRIX_NTT)
+    ctx.profile(False)
+    ntt_s = ntt_ms / max(ntt_n, 1) / 1e3
+    n_pt, limbs = plan_g.m_prime, level + 1 + len(P.p_bits)
+    ntt_bytes = 8 * P.n * n_pt * (1 + limbs)  # int64 coefficients read once per plaintext, residues written per limb
+    ntt_bfly = n_pt * limbs * (P.n // 2) * (P.n.bit_length() - 1)
+    bf_peak = 152 * 128 * 2.07e9 / BUTTERFLY_INSTR
+    ntt_roof = {"kernel": "ntt_from_int64_kernel (encoded matrix: 64 plaintexts x 4 limbs, N=8192, one CTA per limb-poly)",
+                "launch_ms": round(1e3 * ntt_s, 5), "launches_timed": ntt_n,
+                "hbm": {"achieved": round(ntt_bytes / ntt_s / 1e9, 1), "peak": _peaks()["hbm_gbs"], "unit": "GB/s",
+                        "frac": round(ntt_bytes / ntt_s / 1e9 / _peaks()["hbm_gbs"], 4), "alg_bytes_per_launch": ntt_bytes},
+                "alu": {"achieved": round(ntt_bfly / ntt_s / 1e12, 4), "peak": round(bf_peak / 1e12, 4), "unit": "T butterflies/s",
+                        "frac": round(ntt_bfly / ntt_s / bf_peak, 4), "butterflies_per_launch": ntt_bfly},
+                "bound": "alu"}
+
     # end to end through the C ABI's host-memory entry points: X, r and w in page-locked host
     # memory, every step encodes X (he_ptmat_encode_host, once as X^T for the gradient, once as X
     # for the forward product), encrypts r and w (he_encrypt_vector_host), multiplies
@@ -371,6 +389,7 @@ def run_gpu(args):
                                   "ms_per_step": round(1e3 * e2e_graph_s / args.steps, 4),
                                   "how": "the same host-memory calls captured once into a CUDA graph, replayed per step"}
                                  if e2e_graph_s else {"error": graph_err})},
+        "ntt_roofline": ntt_roof,
         "gpu_launches": launches,
         "eager": {"value": round(whole_job_rate(2 * args.steps, world, eager_s), 2), "unit": "MatMult/s",
                   "ms_per_step": round(1e3 * eager_s / args.steps, 4), "gpu_launches": launches_eager,
@@ -432,12 +451,49 @@ def run_rotations(ctx, he, P, args, flush, world, dev):
     t_hoist = max_over_ranks(timed(lambda: ctx.rotate_hoisted(ct, steps, outs=outs), reps), world, dev)
     t_many = max_over_ranks(timed(lambda: ctx.rotate_many(cts, steps, outs), reps), world, dev)
     n = len(steps) * reps * world
+    # the hoisted key switch's kernels timed on their own (CUDA events around them, one call at a time)
+    ctx.profile(True)
+    timed(lambda: ctx.rotate_hoisted(ct, steps, outs=outs), reps)
+    ms_el, n_el = ctx.profile_read(he.HE_PROF_KS_ELEMENTWISE)
+    ms_tr, n_tr = ctx.profile_read(he.HE_PROF_KS_TRANSFORM)
+    ctx.profile(False)
+    calls = max(n_tr, 1)
+    N, nl, K, ndig = P.n, level + 1, len(P.p_bits), P.dnum
+    ext = nl + K
+    k = len(steps)
+    el_bytes = 8 * N * k * (2 * ndig * ext + 2 * nl)  # Galois keys read, rotated ciphertexts written
+    butterflies = k * 2 * (K + nl) * (N // 2) * (N.bit_length() - 1)  # inverse NTTs of the P limbs, NTTs of the Q limbs
+    peaks = _peaks()
+    el_s, tr_s = ms_el / calls / 1e3, ms_tr / calls / 1e3
+    bf_peak = 152 * 128 * 2.07e9 / BUTTERFLY_INSTR
+    roof = {"keyswitch_elementwise": {"kernels": "ks_up_kernel + ks_out_kernel (inner products, ModDown combination)", "bound": "hbm",
+                                      "achieved": round(el_bytes / el_s / 1e9, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                      "frac": round(el_bytes / el_s / 1e9 / peaks["hbm_gbs"], 4), "alg_bytes_per_call": el_bytes,
+                                      "ms_per_call": round(1e3 * el_s, 4), "launches_timed": n_el,
+                                      "counted": "8N k (2 ndig ext + 2 (l+1)): the k Galois keys read and the k rotated ciphertexts written"},
+            "keyswitch_transform": {"kernels": "ks_pintt_kernel + ks_conv_kernel (transform only)", "bound": "alu",
+                                    "achieved": round(butterflies / tr_s / 1e12, 4), "peak": round(bf_peak / 1e12, 4), "unit": "T butterflies/s",
+                                    "frac": round(butterflies / tr_s / bf_peak, 4), "butterflies_per_call": butterflies,
+                                    "ms_per_call": round(1e3 * tr_s, 4),
+                                    "peak_source": f"derived: 152 SMs x 128 lanes x 2070 MHz / {BUTTERFLY_INSTR} thread instructions per "
+                                                   "modular butterfly (Shoup product and lazy add/sub on 64-bit residues)"}}
     return {"single_per_sec": round(n / t_single, 1), "hoisted_per_sec": round(n / t_hoist, 1), "many_per_sec": round(n / t_many, 1),
-            "keyswitch_tuning": ctx.keyswitch_tuning(),
+            "keyswitch_tuning": ctx.keyswitch_tuning(), "roofline": roof,
             "unit": "rotations/s",
             "workload": "RotL by 1..63, N=8192, Q=[60,40,40], P=[60], dnum=3; O3 single = one call per rotation of one ciphertext, "
                         "O4 hoisted = one call for all 63 rotations of one ciphertext, many = one call rotating 63 different "
                         "ciphertexts by 1..63"}
+
+
+# thread instructions of one modular butterfly's arithmetic (64-bit Shoup product about 17 32-bit
+# operations, lazy add and subtract with their corrections about 11): the ALU floor of an NTT
+BUTTERFLY_INSTR = 28
+
+
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = json.load(open(p)) if os.path.exists(p) else {}
+    return {"hbm_gbs": float(d.get("hbm_gbs", 6800.0)), "source": "MEASURED_PEAKS.json (measured)" if d else "fallback 6800 GB/s"}
 
 
 def _event_times(fn, reps, flush, warm=3):

@@ -102,11 +102,22 @@ int he_ctx_info(const he_ctx *ctx, int64_t *n, int32_t *n_q, int32_t *n_p);
 
 /* Number of kernels this context has launched so far (all calls). */
 int he_launch_count(const he_ctx *ctx, int64_t *count);
-/* Per-launch CUDA-event timing, on the context's stream, of the MatMult's key-switch /
- * multiply-accumulate loop kernel.  Enabling (on != 0) or disabling clears the record. */
+/* Per-launch CUDA-event timing, on the context's stream, of some kernel classes: the MatMult's
+ * key-switch / multiply-accumulate loop kernel (HE_PROF_LOOP), the transform of an encoded
+ * matrix's limb-polys (HE_PROF_MATRIX_NTT), and the many-rotation key switch's transform-only
+ * kernels (HE_PROF_KS_TRANSFORM: inverse NTT of the P limbs, conversion and NTT of the Q limbs) and
+ * its elementwise kernels (HE_PROF_KS_ELEMENTWISE: inner products, ModDown's combination).
+ * Enabling (on != 0) or disabling clears every record. */
+#define HE_PROF_LOOP 0
+#define HE_PROF_MATRIX_NTT 1
+#define HE_PROF_KS_TRANSFORM 2
+#define HE_PROF_KS_ELEMENTWISE 3
+#define HE_PROF_KINDS 4
 int he_profile_enable(he_ctx *ctx, int on);
-/* Synchronises the stream; total milliseconds and number of timed launches since enabling. */
+/* Synchronises the stream; total milliseconds and number of timed launches of the loop kernel
+ * since enabling (he_profile_read_kind with HE_PROF_LOOP). */
 int he_profile_read(he_ctx *ctx, double *ms_total, int64_t *launches);
+int he_profile_read_kind(he_ctx *ctx, int kind, double *ms_total, int64_t *launches);
 
 /* Bytes of a caller-owned ciphertext ([2][level+1][N] uint64 residues) or plaintext
  * ([level+1][N]) buffer at `level`; 0 for a NULL context or a level outside 0 .. L-1. */
@@ -312,7 +323,8 @@ int he_batch_set_stage_form(he_batch *batch, int form);
  * (encoded matrix, input and output ciphertext) fit hbm_budget_bytes, packs admitted requests
  * into up to `slots` slots of one of two batch lanes and launches that lane's captured batch
  * graph; requests arriving while a lane runs join the other lane's next launch, so their work
- * overlaps.  plain != 0 serves one request per he_matmult_plain_cipher call instead (the
+ * overlaps.  A request that arrives alone while nothing of its ring runs is served by one
+ * he_matmult_plain_cipher call on the context's stream instead (no batch of one).  plain != 0 serves one request per he_matmult_plain_cipher call instead (the
  * one-request-per-launch baseline).  While a server runs it owns the context's stream and
  * scratch: make no other calls on the context until he_server_free.  Completion is observed
  * with CUDA events; no kernel waits on another. */

@@ -242,7 +242,8 @@ void he_ctx_destroy(he_ctx *ctx) {
     cudaFree(ctx->stage_dev);
     cudaFreeHost(ctx->stage_host);
     if (ctx->stage_ev) cudaEventDestroy(ctx->stage_ev);
-    for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+    for (auto &v : ctx->prof_events)
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -508,23 +509,25 @@ int he_profile_enable(he_ctx *ctx, int on) {
     if (!ctx) return HE_EINVAL;
     cudaStreamSynchronize(ctx->stream);
     ctx->prof_on = on != 0;
-    ctx->prof_used = 0;
+    for (size_t &u : ctx->prof_used) u = 0;
     return HE_OK;
 }
 
-int he_profile_read(he_ctx *ctx, double *ms_total, int64_t *launches) {
-    if (!ctx || !ms_total || !launches) return HE_EINVAL;
+int he_profile_read_kind(he_ctx *ctx, int kind, double *ms_total, int64_t *launches) {
+    if (!ctx || !ms_total || !launches || kind < 0 || kind >= HE_PROF_KINDS) return HE_EINVAL;
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return HE_ECUDA;
     double total = 0.0;
-    for (size_t i = 0; i + 1 < ctx->prof_used; i += 2) {
+    for (size_t i = 0; i + 1 < ctx->prof_used[kind]; i += 2) {
         float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, ctx->prof_events[i], ctx->prof_events[i + 1]) != cudaSuccess) return HE_ECUDA;
+        if (cudaEventElapsedTime(&ms, ctx->prof_events[kind][i], ctx->prof_events[kind][i + 1]) != cudaSuccess) return HE_ECUDA;
         total += ms;
     }
     *ms_total = total;
-    *launches = (int64_t)(ctx->prof_used / 2);
+    *launches = (int64_t)(ctx->prof_used[kind] / 2);
     return HE_OK;
 }
+
+int he_profile_read(he_ctx *ctx, double *ms_total, int64_t *launches) { return he_profile_read_kind(ctx, HE_PROF_LOOP, ms_total, launches); }
 
 int he_ctx_info(const he_ctx *ctx, int64_t *n, int32_t *n_q, int32_t *n_p) {
     if (!ctx) return HE_EINVAL;
@@ -855,7 +858,10 @@ static int ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X, int trans) {
         launch_layout_matrix(ctx, p, X, slots, trans);
         launch_encode(ctx, slots, N / 2, N / 2, (int)count, pm->scale, coef);
     }
+    cudaEvent_t *ev = prof_pair(ctx, HE_PROF_MATRIX_NTT);
+    if (ev) cudaEventRecord(ev[0], ctx->stream);
     launch_ntt_from_int64(ctx, coef, pm->data, (int)count, qpmap(ctx, pm->level), 1);
+    if (ev) cudaEventRecord(ev[1], ctx->stream);
     return last_launch();
 }
 

@@ -96,6 +96,9 @@ struct ModConst {
     uint64_t p40, p40_shoup, p80, p80_shoup;  // 2^40 and 2^80 mod q: recombination of byte-split products (he_bconv.cu)
 };
 
+// next start/end event pair of profiled kernel class `kind` (HE_PROF_*), or nullptr when profiling is off
+cudaEvent_t *prof_pair(he_ctx *ctx, int kind);
+
 // index map from a batch's limb position to the context's prime index
 struct LimbMap {
     int32_t n;                     // limbs per group
@@ -176,8 +179,8 @@ struct he_ctx {
     // kernels launched so far, and CUDA-event timing of the MatMult loop kernel when enabled
     int64_t launches;
     bool prof_on;
-    std::vector<cudaEvent_t> prof_events;  // start/end pairs, recorded on `stream`
-    size_t prof_used;
+    std::vector<cudaEvent_t> prof_events[HE_PROF_KINDS];  // per profiled kernel class: start/end pairs, recorded on `stream`
+    size_t prof_used[HE_PROF_KINDS];
 };
 
 // Kernels templated on the ring size: LOGN in {12, 13, 14} (the parameter sets in use) has it at

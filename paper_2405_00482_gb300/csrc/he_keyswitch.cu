@@ -356,10 +356,18 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
         }
         const unsigned eblocks = (unsigned)((ctx->n + 256 * KS_U - 1) / (256 * KS_U));
         ctx->launches += 4;
+        // CUDA-event timing of the transforms and of the elementwise kernels, when profiling
+        cudaEvent_t *pe = prof_pair(ctx, HE_PROF_KS_ELEMENTWISE), *pt = nullptr;
+        if (pe) cudaEventRecord(pe[0], st);
         if (mu.ndig == 3)
             launch_k(ks_up_kernel<3>, dim3(eblocks, (unsigned)np), 256, 0, st, tab, kg, mc, logn);
         else
             launch_k(ks_up_kernel<0>, dim3(eblocks, (unsigned)np), 256, 0, st, tab, kg, mc, logn);
+        if (pe) {
+            cudaEventRecord(pe[1], st);
+            pt = prof_pair(ctx, HE_PROF_KS_TRANSFORM);
+            if (pt) cudaEventRecord(pt[0], st);
+        }
         // the transforms: cluster form for few limb-polys, else one CTA each
         const bool wide = v == 1 && logn >= 12;
         if (use_cluster(logn, np))
@@ -375,10 +383,17 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
         else
             launch_k(by_logn(logn, [](auto L) { return ks_conv_kernel<false, L.value, 256>; }), nq, ntt_threads(logn), ntt_smem_bytes(logn), st, kg, cv, md,
                      tw, mc, logn);
+        cudaEvent_t *pe2 = nullptr;
+        if (pt) {
+            cudaEventRecord(pt[1], st);
+            pe2 = prof_pair(ctx, HE_PROF_KS_ELEMENTWISE);
+            if (pe2) cudaEventRecord(pe2[0], st);
+        }
         if (mu.ndig == 3)
             launch_k(ks_out_kernel<3>, dim3(eblocks, (unsigned)nq), 256, 0, st, tab, kg, (const uint64_t *)cv, md, mc, logn);
         else
             launch_k(ks_out_kernel<0>, dim3(eblocks, (unsigned)nq), 256, 0, st, tab, kg, (const uint64_t *)cv, md, mc, logn);
+        if (pe2) cudaEventRecord(pe2[1], st);
     };
     // the first launch of at least 32 rotations on a context chooses the transform variant by timing
     // both on its first chunk (the launches overwrite their outputs with the same values, so

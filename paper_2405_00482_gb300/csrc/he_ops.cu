@@ -1184,23 +1184,28 @@ __global__ void ras_gather_kernel(he_plan p, const double *__restrict__ slots, d
 
 inline dim3 elem_grid(int n, int y, int z = 1) { return dim3((n + 255) / 256, y, z); }
 
-// next start/end event pair of the profiled kernel, or nullptr when profiling is off
-cudaEvent_t *prof_pair(he_ctx *ctx) {
+}  // namespace
+
+// next start/end event pair of profiled kernel class `kind`, or nullptr when profiling is off
+cudaEvent_t *prof_pair(he_ctx *ctx, int kind) {
     if (!ctx->prof_on) return nullptr;
-    if (ctx->prof_used + 2 > ctx->prof_events.size()) {
+    std::vector<cudaEvent_t> &evs = ctx->prof_events[kind];
+    if (ctx->prof_used[kind] + 2 > evs.size()) {
         cudaEvent_t a, b;
         if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
         if (cudaEventCreate(&b) != cudaSuccess) {
             cudaEventDestroy(a);
             return nullptr;
         }
-        ctx->prof_events.push_back(a);
-        ctx->prof_events.push_back(b);
+        evs.push_back(a);
+        evs.push_back(b);
     }
-    cudaEvent_t *ev = ctx->prof_events.data() + ctx->prof_used;
-    ctx->prof_used += 2;
+    cudaEvent_t *ev = evs.data() + ctx->prof_used[kind];
+    ctx->prof_used[kind] += 2;
     return ev;
 }
+
+namespace {
 
 }  // namespace
 
@@ -1334,7 +1339,7 @@ void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const ui
     const ModUpConst &mu = ctx->modup[level];
     const he_plan &p = pm->plan;
     const uint64_t *pts = pm->data + (((int64_t)r * p.col_blocks + c) * p.m_prime) * pm->ext * ctx->n;
-    cudaEvent_t *ev = prof_pair(ctx);
+    cudaEvent_t *ev = prof_pair(ctx, HE_PROF_LOOP);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
     mm_launch_variant(ctx, pm->variant < 0 ? 0 : pm->variant, ct, D, pts, pm->d_keys, pm->d_galois, (int)p.m_prime, mu.ndig, mu.ext,
                       level + 1, acc, cacc, accumulate);

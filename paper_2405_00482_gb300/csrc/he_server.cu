@@ -7,7 +7,8 @@
 // requests into the slots of a free lane and launches the lane's captured batch graph (empty
 // slots are skipped by every kernel); while one lane runs, the next requests are packed into the
 // other, so arrivals during a launch join the next one and their work overlaps the launch in
-// flight, and the rings' lanes run side by side on their own streams.  Completion is observed with
+// flight, and the rings' lanes run side by side on their own streams.  A request that finds its
+// ring idle and alone runs as one plain call.  Completion is observed with
 // CUDA events; no kernel waits on anything.  Plain mode serves one request per
 // he_matmult_plain_cipher call instead (in order per ring), the baseline a serving measurement is
 // compared with.
@@ -48,7 +49,8 @@ struct Ring {
     he_ctx *ctx = nullptr;
     int level = 0;
     Lane lanes[2];
-    cudaEvent_t plain_done = nullptr;  // plain mode: the request in flight on ctx's stream
+    cudaEvent_t plain_done = nullptr;  // plain mode, or a lone request in batched mode: the call in flight on ctx's stream
+    Lane solo;                         // batched mode: a lone request run as one call (see schedule_batched)
     std::deque<int64_t> admitted;
 };
 
@@ -95,28 +97,16 @@ void finish(he_server *s, int64_t id, int status) {
     }
 }
 
-bool ring_busy(const he_server *s, const Ring &g) { return s->plain ? g.lanes[0].busy : (g.lanes[0].busy || g.lanes[1].busy); }
+bool ring_busy(const he_server *s, const Ring &g) { return s->plain ? g.lanes[0].busy : (g.lanes[0].busy || g.lanes[1].busy || g.solo.busy); }
 
-// one ring's plain-mode pass: one request per he_matmult_plain_cipher call, strictly in order
-bool schedule_plain(he_server *s, Ring &g, std::unique_lock<std::mutex> &lock) {
-    bool changed = false;
-    Lane &ln = g.lanes[0];
-    if (ln.busy) {
-        if (cudaEventQuery(g.plain_done) != cudaSuccess) return false;
-        for (int64_t id : ln.ids) finish(s, id, HE_OK);
-        ln.ids.clear();
-        ln.busy = false;
-        changed = true;
-    }
-    if (g.admitted.empty()) return changed;
-    const int64_t id = g.admitted.front();
-    g.admitted.pop_front();
+// run request id as one he_matmult_plain_cipher call on the ring context's stream (the lock released
+// around it: the call may tune a matrix's loop kernel, synchronising); its completion is recorded
+// in g.plain_done and tracked by `ln`
+bool run_single(he_server *s, Ring &g, Lane &ln, int64_t id, std::unique_lock<std::mutex> &lock) {
     Req &r = s->reqs[id];
     r.state = 2;
     r.t_start = now_s();
-    // the call (whose first use of a matrix also tunes its loop kernel, synchronising the stream)
-    // runs without the lock, so submit and wait are never held up by it; only this thread
-    // touches r's inputs meanwhile, and map references stay valid across inserts
+    // only this thread touches r's inputs meanwhile, and map references stay valid across inserts
     const he_plan *plan = r.plan;
     const he_ptmat *pm = r.pm;
     he_ct in = r.in, out = r.out;
@@ -134,8 +124,28 @@ bool schedule_plain(he_server *s, Ring &g, std::unique_lock<std::mutex> &lock) {
     return true;
 }
 
-// one ring's batched pass: completions, then every free lane takes up to `slots` admitted requests
-bool schedule_batched(he_server *s, Ring &g) {
+// one ring's plain-mode pass: one request per he_matmult_plain_cipher call, strictly in order
+bool schedule_plain(he_server *s, Ring &g, std::unique_lock<std::mutex> &lock) {
+    bool changed = false;
+    Lane &ln = g.lanes[0];
+    if (ln.busy) {
+        if (cudaEventQuery(g.plain_done) != cudaSuccess) return false;
+        for (int64_t id : ln.ids) finish(s, id, HE_OK);
+        ln.ids.clear();
+        ln.busy = false;
+        changed = true;
+    }
+    if (g.admitted.empty()) return changed;
+    const int64_t id = g.admitted.front();
+    g.admitted.pop_front();
+    return run_single(s, g, ln, id, lock);
+}
+
+// one ring's batched pass: completions, then every free lane takes up to `slots` admitted
+// requests.  A lone request with nothing of its ring on the GPU runs as one plain call instead
+// (a batch launch would carry one job and its empty slots; at low load this keeps its latency
+// that of the plain path), and requests arriving meanwhile go to the lanes.
+bool schedule_batched(he_server *s, Ring &g, std::unique_lock<std::mutex> &lock) {
     bool changed = false;
     for (Lane &ln : g.lanes) {
         if (ln.busy && cudaEventQuery(ln.b->ev_out) == cudaSuccess) {
@@ -144,6 +154,17 @@ bool schedule_batched(he_server *s, Ring &g) {
             ln.busy = false;
             changed = true;
         }
+    }
+    if (g.solo.busy && cudaEventQuery(g.plain_done) == cudaSuccess) {
+        for (int64_t id : g.solo.ids) finish(s, id, HE_OK);
+        g.solo.ids.clear();
+        g.solo.busy = false;
+        changed = true;
+    }
+    if (g.admitted.size() == 1 && !g.lanes[0].busy && !g.lanes[1].busy && !g.solo.busy) {
+        const int64_t id = g.admitted.front();
+        g.admitted.pop_front();
+        return run_single(s, g, g.solo, id, lock);
     }
     for (Lane &ln : g.lanes) {
         if (ln.busy || g.admitted.empty()) continue;
@@ -194,7 +215,7 @@ bool schedule(he_server *s, std::unique_lock<std::mutex> &lock) {
         s->rings[r.ring].admitted.push_back(id);
         changed = true;
     }
-    for (Ring &g : s->rings) changed |= s->plain ? schedule_plain(s, g, lock) : schedule_batched(s, g);
+    for (Ring &g : s->rings) changed |= s->plain ? schedule_plain(s, g, lock) : schedule_batched(s, g, lock);
     return changed;
 }
 
@@ -217,7 +238,8 @@ void worker_main(he_server *s) {
 int ring_init(he_server *s, Ring &g, he_ctx *ctx, int level) {
     g.ctx = ctx;
     g.level = level;
-    if (s->plain) return cudaEventCreateWithFlags(&g.plain_done, cudaEventDisableTiming) == cudaSuccess ? HE_OK : HE_ECUDA;
+    if (cudaEventCreateWithFlags(&g.plain_done, cudaEventDisableTiming) != cudaSuccess) return HE_ECUDA;
+    if (s->plain) return HE_OK;
     for (Lane &ln : g.lanes) {
         int rc = batch_create_impl(ctx, s->slots, level, nullptr, &ln.b);
         if (rc != HE_OK) return rc;

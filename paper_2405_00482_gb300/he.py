@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhe.so")
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_EKEY, HE_ELEVEL, HE_ESCALE, HE_ETIMEOUT, HE_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7, -8
 HE_BCONV_INT64, HE_BCONV_INT8_TC = 0, 1  # basis extension engines of ModUp
+HE_PROF_LOOP, HE_PROF_MATRIX_NTT, HE_PROF_KS_TRANSFORM, HE_PROF_KS_ELEMENTWISE = 0, 1, 2, 3  # profiled kernel classes
 
 
 class HEError(RuntimeError):
@@ -51,6 +52,7 @@ _SIGS = {
     "he_launch_count": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "he_profile_enable": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
+    "he_profile_read_kind": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
     "he_encode": (ctypes.c_int, [_vp, _vp, _i64, _dbl, ctypes.c_int, ctypes.POINTER(HePt)]),
     "he_encrypt": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _u64, ctypes.POINTER(HeCt)]),
     "he_encrypt_dnonce": (ctypes.c_int, [_vp, ctypes.POINTER(HePt), _vp, ctypes.POINTER(HeCt)]),
@@ -499,9 +501,10 @@ class Context:
     def profile(self, on: bool):
         _check(_lib().he_profile_enable(self.handle, int(on)), "he_profile_enable")
 
-    def profile_read(self) -> tuple[float, int]:
+    def profile_read(self, kind: int = HE_PROF_LOOP) -> tuple[float, int]:
+        """(total ms, timed launches) of a profiled kernel class since profile(True)."""
         ms, n = _dbl(), _i64()
-        _check(_lib().he_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(n)), "he_profile_read")
+        _check(_lib().he_profile_read_kind(self.handle, kind, ctypes.byref(ms), ctypes.byref(n)), "he_profile_read_kind")
         return float(ms.value), int(n.value)
 
     # ---- keys / encode / encrypt / decrypt ----
