@@ -744,6 +744,10 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
             // and 3 ND + 1 the c0 gather (aligned pairs when VEC = 2)
             constexpr int F = 2 * ND + 1 + (GA ? ND + 1 : 0);
             auto slot = [&](int st, int f) { return pipe + ((st * F + f) * MM_THREADS + (int)threadIdx.x) * VEC; };
+            // GA with VEC = 2: bit st is the parity of the gather source staged in stage st (set when
+            // the gathers are issued, read when they are consumed), so the source index is computed
+            // once per step
+            uint32_t odd_bits = 0;
             auto issue = [&](int t) {
                 const int i = 1 + grp + t * G;
                 if (i < m_prime) {
@@ -758,6 +762,7 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                     if constexpr (GA) {
                         const uint32_t src = automorph_src(k, galois[i - 1], logn);
                         const uint32_t sa = VEC == 2 ? (src & ~1u) : src;
+                        if constexpr (VEC == 2) odd_bits = (odd_bits & ~(1u << st)) | ((src & 1u) << st);
 #pragma unroll
                         for (int d = 0; d < ND; ++d) cp_async<8 * VEC>(slot(st, 2 * ND + 1 + d), D + ((int64_t)d * ext + u) * N + sa);
                         if (inq) cp_async<8 * VEC>(slot(st, 3 * ND + 1), ct + (int64_t)u * N + sa);
@@ -770,22 +775,24 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
             auto gather = [&](int t) {
                 const int i = 1 + grp + t * G;
                 if (i >= m_prime) return;
-                const uint32_t src = automorph_src(k, galois[i - 1], logn);
                 if constexpr (GA) {
                     const int st = t % SP;
-                    const bool odd = VEC == 2 && (src & 1);
+                    // the staged aligned pair holds (src, src ^ 1) in ascending order: coefficient j
+                    // reads word j ^ odd, as two 8-byte shared-memory loads at offsets odd, 1 - odd
+                    const int odd = VEC == 2 ? (int)((odd_bits >> st) & 1u) : 0;
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
                         const uint64_t *g = slot(st, 2 * ND + 1 + d);
 #pragma unroll
-                        for (int j = 0; j < VEC; ++j) dv[d][j] = g[odd ? VEC - 1 - j : j];
+                        for (int j = 0; j < VEC; ++j) dv[d][j] = g[j ^ odd];
                     }
                     if (inq) {
                         const uint64_t *g = slot(st, 3 * ND + 1);
 #pragma unroll
-                        for (int j = 0; j < VEC; ++j) cv[j] = g[odd ? VEC - 1 - j : j];
+                        for (int j = 0; j < VEC; ++j) cv[j] = g[j ^ odd];
                     }
                 } else {
+                    const uint32_t src = automorph_src(k, galois[i - 1], logn);
 #pragma unroll
                     for (int d = 0; d < ND; ++d) gatherv<VEC>(D + ((int64_t)d * ext + u) * N, src, dv[d]);
                     if (inq) gatherv<VEC>(ct + (int64_t)u * N, src, cv);
