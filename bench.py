@@ -284,7 +284,7 @@ def run_gpu(args):
                         "frac": round(ntt_bytes / ntt_s / 1e9 / _peaks()["hbm_gbs"], 4), "alg_bytes_per_launch": ntt_bytes},
                 "alu": {"achieved": round(ntt_bfly / ntt_s / 1e12, 4), "peak": round(bf_peak / 1e12, 4), "unit": "T butterflies/s",
                         "frac": round(ntt_bfly / ntt_s / bf_peak, 4), "butterflies_per_launch": ntt_bfly},
-                "bound": "alu"}
+                "bound": "alu", "form": ctx.ntt_form()}
 
     # end to end through the C ABI's host-memory entry points: X, r and w in page-locked host
     # memory, every step encodes X (he_ptmat_encode_host, once as X^T for the gradient, once as X

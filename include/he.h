@@ -254,6 +254,17 @@ int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_p
  * variant (-1 before) and ms[0..1] (may be NULL) report the choice and the timings. */
 int he_keyswitch_tuning(const he_ctx *ctx, int *variant, float *ms);
 
+/* NTT launches of many limb-polys (an encoded matrix's 4 x m' transforms, import and export of
+ * plaintext batches) run as one CTA per limb-poly (form 0) or as a 2-CTA cluster per limb-poly
+ * (form 1: each CTA holds half of the coefficients, the one stage that pairs the halves goes
+ * through distributed shared memory).  The first matrix a context encodes times both on its
+ * transform (synchronising the stream; not under stream capture) and keeps the faster for the
+ * context; he_ntt_form reports the choice (-1 before) and ms[0..1] (may be NULL), he_set_ntt_form
+ * pins one (0, 1, or -1 to time again).  Results are the same in either form.  A fork starts with
+ * its parent's choice. */
+int he_ntt_form(const he_ctx *ctx, int *form, float *ms);
+int he_set_ntt_form(he_ctx *ctx, int form);
+
 /* Basis extension engine of ModUp (the fast base conversion inside hybrid key switching, O3/O4
  * of Sec. 2.2) for this context's later calls: HE_BCONV_INT64 (default) sums the products
  * v_i (Q_d/q_i mod t) with exact 64-bit modular arithmetic; HE_BCONV_INT8_TC cuts v_i and the

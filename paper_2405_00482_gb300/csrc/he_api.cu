@@ -483,6 +483,9 @@ int he_ctx_fork(he_ctx *parent, void *stream, he_ctx **out) {
     memcpy(ctx->cdt, parent->cdt, sizeof(ctx->cdt));
     ctx->batch_variant = parent->batch_variant;
     ctx->bconv = parent->bconv;
+    ctx->ntt_form = parent->ntt_form;
+    ctx->ntt_form_ms[0] = parent->ntt_form_ms[0];
+    ctx->ntt_form_ms[1] = parent->ntt_form_ms[1];
     ctx->d_bconv_a = parent->d_bconv_a;
     ctx->bconv_a_off = parent->bconv_a_off;
     // the parent's pending work (keys, tables) must be complete before the fork's stream uses it
@@ -846,6 +849,42 @@ static int ptmat_alloc(he_ctx *ctx, const he_plan *plan, int level, double scale
     return HE_OK;
 }
 
+// The first matrix encoded on a context times its transform (one launch of many limb-polys) in
+// both NTT forms, one CTA or a 2-CTA pair per limb-poly (the same values: the launch is repeated
+// on the same input), and keeps the faster for every such launch of the context; not under
+// stream capture, nor for launches small enough for the cluster form.  Synchronises the stream.
+static void tune_ntt_form(he_ctx *ctx, const int64_t *coef, uint64_t *out, int groups, const LimbMap &map) {
+    const int polys = groups * map.n;
+    if (use_cluster(ctx->log_n, polys) || ctx->log_n < 12 || ctx->log_n > 14) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return;
+    }
+    int best = 0;
+    for (int f = 0; f < 2; ++f) {
+        ctx->ntt_form = f;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, ctx->stream);
+            launch_ntt_from_int64(ctx, coef, out, groups, map, 1);
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0 && t < ms) ms = t;
+        }
+        ctx->ntt_form_ms[f] = ms;
+        if (ms < ctx->ntt_form_ms[best]) best = f;
+    }
+    ctx->ntt_form = best;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
 static int ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X, int trans) {
     if (!ctx || !pm || !X || !same_family(pm->ctx, ctx)) return HE_EINVAL;
     const he_plan &p = pm->plan;
@@ -858,6 +897,7 @@ static int ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X, int trans) {
         launch_layout_matrix(ctx, p, X, slots, trans);
         launch_encode(ctx, slots, N / 2, N / 2, (int)count, pm->scale, coef);
     }
+    if (ctx->ntt_form < 0) tune_ntt_form(ctx, coef, pm->data, (int)count, qpmap(ctx, pm->level));
     cudaEvent_t *ev = prof_pair(ctx, HE_PROF_MATRIX_NTT);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
     launch_ntt_from_int64(ctx, coef, pm->data, (int)count, qpmap(ctx, pm->level), 1);
@@ -1452,6 +1492,22 @@ int he_pt_import(he_ctx *ctx, const uint64_t *coeffs, int level, double scale, h
     out->level = level;
     out->scale = scale;
     return last_launch();
+}
+
+int he_ntt_form(const he_ctx *ctx, int *form, float *ms) {
+    if (!ctx || !form) return HE_EINVAL;
+    *form = ctx->ntt_form;
+    if (ms) {
+        ms[0] = ctx->ntt_form_ms[0];
+        ms[1] = ctx->ntt_form_ms[1];
+    }
+    return HE_OK;
+}
+
+int he_set_ntt_form(he_ctx *ctx, int form) {
+    if (!ctx || form < -1 || form > 1) return HE_EINVAL;
+    ctx->ntt_form = form;
+    return HE_OK;
 }
 
 }  // extern "C"

@@ -164,6 +164,8 @@ struct he_ctx {
     size_t scratch_words;
     int batch_variant = 0;            // last variant a batch tuned to (used by serving lanes)
     int bconv = 0;                    // basis extension of ModUp: 0 exact INT64 products, 1 INT8 tensor-core limb split
+    int ntt_form = -1;                // NTT launches of many limb-polys: 0 one CTA each, 1 a 2-CTA cluster each (-1: not yet timed)
+    float ntt_form_ms[2] = {};        // the timed milliseconds of each form (an encoded matrix's transform)
     int ks_variant = -1;              // transform variant of the many-rotation key switch, chosen by timing (-1: not yet)
     float ks_tune_ms[2] = {};         // the timed milliseconds of each variant (one full chunk of rotations)
     uint32_t *d_bconv_a = nullptr;    // INT8 engine: tensor-core A fragments of every (level, digit), shared with forks
@@ -383,6 +385,7 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map);
 int ntt_threads(int logn);
 bool use_cluster(int logn, int polys);  // launch in the cluster form (few limb-polys)
+bool use_pair(const he_ctx *ctx, int polys);  // launch in the 2-CTA pair form (many limb-polys, when the context chose it)
 int cl_threads(int logn);
 size_t cl_smem_bytes(int logn);
 // dynamic shared memory of a CTA that holds one limb-poly for the NTT (padded layout)

@@ -4,6 +4,7 @@
 // Batch layout: limb l of group g sits at base + g * group_stride + l * N, with prime
 // index map.prime[l].  Grid = groups * map.n CTAs.
 #include <algorithm>
+#include <type_traits>
 
 #include "he_internal.cuh"
 #include "he_ntt.cuh"
@@ -87,6 +88,68 @@ __global__ void ntt_from_int64_kernel(const int64_t *__restrict__ in, uint64_t *
     }
 }
 
+// ---- pair forms (two CTAs per limb-poly, he_ntt.cuh): the same operations as the kernels above ----
+// Launch bounds: pair_threads(LOGN) threads, registers for three CTAs of 256 threads per SM at
+// N = 2^13 (at most 85; at 64 the passes spill)
+__device__ __forceinline__ int pair_rank() { return (int)cg::this_cluster().block_rank(); }
+#define PAIR_BOUNDS(LOGN) __launch_bounds__(pair_threads_c(LOGN), 768 / pair_threads_c(LOGN))
+
+template <int LOGN>
+__global__ void PAIR_BOUNDS(LOGN) ntt_fwd_pair_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
+                                                           const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int to_mont) {
+    HE_GRID_DEP();
+    extern __shared__ uint64_t s[];
+    constexpr int N = 1 << LOGN, NS = N / 2;
+    const int poly = blockIdx.x / 2, off = pair_rank() * NS;
+    const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    stage_in(s, in + g * in_gs + (int64_t)l * N + off, NS, [](uint64_t v) { return v; });
+    ntt_fwd_pair<LOGN>(s, twiddles(d_tw, p, 0, LOGN), q);
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
+    if (to_mont) {
+        const uint64_t r1 = mc[p].r1, r1s = mc[p].r1_shoup;
+        for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], r1, r1s, q);
+    } else {
+        for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = s[SIDX(k)];
+    }
+}
+
+template <int LOGN>
+__global__ void PAIR_BOUNDS(LOGN) ntt_inv_pair_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs, LimbMap map,
+                                                           const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    extern __shared__ uint64_t s[];
+    constexpr int N = 1 << LOGN, NS = N / 2;
+    const int poly = blockIdx.x / 2, off = pair_rank() * NS;
+    const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    stage_in(s, in + g * in_gs + (int64_t)l * N + off, NS, [](uint64_t v) { return v; });
+    ntt_inv_pair<LOGN>(s, twiddles(d_tw, p, 1, LOGN), q);
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N + off;
+    const uint64_t ni = mc[p].ninv, nis = mc[p].ninv_shoup;
+    for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], ni, nis, q);
+}
+
+template <int LOGN>
+__global__ void PAIR_BOUNDS(LOGN) ntt_from_int64_pair_kernel(const int64_t *__restrict__ in, uint64_t *out, LimbMap map,
+                                                                  const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int to_mont) {
+    HE_GRID_DEP();
+    extern __shared__ uint64_t s[];
+    constexpr int N = 1 << LOGN, NS = N / 2;
+    const int poly = blockIdx.x / 2, off = pair_rank() * NS;
+    const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
+    const uint64_t q = mc[p].q, mu = mc[p].mu;
+    stage_in(s, in + (int64_t)g * N + off, NS, [q, mu](int64_t v) { return reduce_signed(v, q, mu); });
+    ntt_fwd_pair<LOGN>(s, twiddles(d_tw, p, 0, LOGN), q);
+    uint64_t *dst = out + ((int64_t)g * map.n + l) * N + off;
+    if (to_mont) {
+        const uint64_t r1 = mc[p].r1, r1s = mc[p].r1_shoup;
+        for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = mul_shoup(s[SIDX(k)], r1, r1s, q);
+    } else {
+        for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = s[SIDX(k)];
+    }
+}
+
 // out = data 2^-64 mod q (Montgomery form back to canonical); grid (blocks, groups, limbs)
 __global__ void from_mont_kernel(const uint64_t *__restrict__ data, uint64_t *out, LimbMap map, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
@@ -129,10 +192,30 @@ int ntt_threads(int logn) {
     return sets < cap ? sets : cap;
 }
 
+// the pair form instance for a compile-time ring size (nullptr: none, use the one-CTA form)
+template <class F>
+static auto pair_instance(int logn, F f) {
+    using K = decltype(f(std::integral_constant<int, 13>{}));
+    switch (logn) {
+        case 12: return f(std::integral_constant<int, 12>{});
+        case 13: return f(std::integral_constant<int, 13>{});
+        case 14: return f(std::integral_constant<int, 14>{});
+        default: return (K) nullptr;
+    }
+}
+
+bool use_pair(const he_ctx *ctx, int polys) { return ctx->ntt_form == 1 && !use_cluster(ctx->log_n, polys) && ctx->log_n >= 12 && ctx->log_n <= 14; }
+
 void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
                             const LimbMap &map, int to_mont) {
     if (groups * map.n == 0) return;
     ctx->launches++;
+    if (use_pair(ctx, groups * map.n)) {
+        launch_cluster_n(pair_instance(ctx->log_n, [](auto L) { return ntt_fwd_pair_kernel<L.value>; }), groups * map.n * 2, pair_threads(ctx->log_n),
+                         pair_smem_bytes(ctx->log_n), ctx->stream, 2, in, in_gs, out, out_gs, map, (const uint64_t *)ctx->d_tw,
+                         (const ModConst *)ctx->d_mc, to_mont);
+        return;
+    }
     const int polys = groups * map.n;
     if (use_cluster(ctx->log_n, polys))
         launch_cluster(by_logn(ctx->log_n, [](auto L) { return ntt_fwd_kernel<true, L.value>; }), polys * HE_NTT_CL, cl_threads(ctx->log_n),
@@ -145,6 +228,12 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map) {
     if (groups * map.n == 0) return;
     ctx->launches++;
+    if (use_pair(ctx, groups * map.n)) {
+        launch_cluster_n(pair_instance(ctx->log_n, [](auto L) { return ntt_inv_pair_kernel<L.value>; }), groups * map.n * 2, pair_threads(ctx->log_n),
+                         pair_smem_bytes(ctx->log_n), ctx->stream, 2, in, in_gs, out, out_gs, map, (const uint64_t *)ctx->d_tw,
+                         (const ModConst *)ctx->d_mc);
+        return;
+    }
     const int polys = groups * map.n;
     if (use_cluster(ctx->log_n, polys))
         launch_cluster(by_logn(ctx->log_n, [](auto L) { return ntt_inv_kernel<true, L.value>; }), polys * HE_NTT_CL, cl_threads(ctx->log_n),
@@ -175,6 +264,11 @@ void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int gr
     if (groups * map.n == 0) return;
     ctx->launches++;
     const int polys = groups * map.n;
+    if (use_pair(ctx, polys)) {
+        launch_cluster_n(pair_instance(ctx->log_n, [](auto L) { return ntt_from_int64_pair_kernel<L.value>; }), polys * 2, pair_threads(ctx->log_n),
+                         pair_smem_bytes(ctx->log_n), ctx->stream, 2, in, out, map, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, to_mont);
+        return;
+    }
     if (use_cluster(ctx->log_n, polys))
         launch_cluster(by_logn(ctx->log_n, [](auto L) { return ntt_from_int64_kernel<true, L.value>; }), polys * HE_NTT_CL, cl_threads(ctx->log_n),
                        cl_smem_bytes(ctx->log_n), ctx->stream, in, out, map, ctx->d_tw, ctx->d_mc, ctx->log_n, to_mont);
@@ -204,4 +298,10 @@ void ntt_set_smem_limits(int max_bytes) {
         cudaFuncSetAttribute(ntt_inv_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
         cudaFuncSetAttribute(ntt_from_int64_kernel<true, L.value>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
     });
+    for (int logn : {12, 13, 14}) {
+        cudaFuncSetAttribute(pair_instance(logn, [](auto L) { return ntt_fwd_pair_kernel<L.value>; }), cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(pair_instance(logn, [](auto L) { return ntt_inv_pair_kernel<L.value>; }), cudaFuncAttributeMaxDynamicSharedMemorySize, max_bytes);
+        cudaFuncSetAttribute(pair_instance(logn, [](auto L) { return ntt_from_int64_pair_kernel<L.value>; }), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             max_bytes);
+    }
 }

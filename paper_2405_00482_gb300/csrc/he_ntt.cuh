@@ -486,6 +486,101 @@ __device__ __forceinline__ void inv_any(uint64_t *s, const ulonglong2 *tw, uint6
     else ntt_inv_smem(s, tw, q, logn);
 }
 
+// ---------------------------------------------------------------------------------------
+// Pair form: a 2-CTA cluster per limb-poly, CTA r holding the half [r N/2, (r+1) N/2) in its shared
+// memory (padded layout, local index x - r N/2).  A throughput form for launches of many
+// limb-polys: twice the CTAs, each with half the work, so 256 limb-polys on 152 SMs become 512
+// halves spread 3-4 per SM instead of 1-2 transforms per SM.  Only the forward transform's first
+// stage (the inverse's last) pairs elements of the two halves, x and x + N/2: one step through
+// distributed shared memory, each CTA taking half of those butterflies.  Every other stage runs in
+// the radix-16 passes of the one-CTA form, on the CTA's half of the sets (its groups lie wholly in
+// one half), with the same twiddle tables.  The butterflies are those of the one-CTA form, so the
+// output is the same canonical transform.
+template <int LOGN>
+__device__ __forceinline__ void pair_cross_step(uint64_t *s, ulonglong2 w, uint64_t q, bool fwd) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    constexpr int NS = 1 << (LOGN - 1);
+    uint64_t *a = cl.map_shared_rank(s, 0), *b = cl.map_shared_rank(s, 1);
+    const uint64_t two_q = 2 * q;
+    for (int j = rank * (NS / 2) + threadIdx.x; j < (rank + 1) * (NS / 2); j += blockDim.x) {
+        const uint64_t U = a[SIDX(j)], V = b[SIDX(j)];
+        if (fwd) {  // Cooley-Tukey stage 0, inputs canonical
+            const uint64_t T = mul_shoup_lazy(V, w.x, w.y, q);
+            a[SIDX(j)] = U + T;
+            b[SIDX(j)] = U - T + two_q;
+        } else {  // Gentleman-Sande last stage, inputs in [0, 2q)
+            const uint64_t X = U + V;
+            a[SIDX(j)] = X >= two_q ? X - two_q : X;
+            b[SIDX(j)] = mul_shoup_lazy(U - V + two_q, w.x, w.y, q);
+        }
+    }
+}
+
+// forward transform of the two halves (canonical in, canonical bit-reversed out); every thread of
+// both CTAs calls it after its half is in shared memory
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd_pair(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q) {
+    static_assert(LOGN >= 6, "pair form: halves of at least 32 elements");
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    constexpr int R = HE_NTT_RADIX_LOG, LOC = LOGN - 1, FIRST = LOC % R, NPASS = (LOC + R - 1) / R;
+    constexpr int NS = 1 << LOC;
+    cl.sync();
+    pair_cross_step<LOGN>(s, tw[1], q, true);
+    cl.sync();
+#pragma unroll
+    for (int pi = 0; pi < NPASS; ++pi) {
+        const int nb = (pi == 0 && FIRST) ? FIRST : R;
+        const int s0 = 1 + (pi == 0 ? 0 : (FIRST ? FIRST : R) + (pi - 1) * R);
+        const bool last = pi == NPASS - 1;
+        const int E = 1 << nb;
+        const int set0 = rank * (NS / E), set1 = (rank + 1) * (NS / E), off = rank * NS;
+        switch (nb) {
+            case 4:
+                if (last) ntt_fwd_pass<4>(s, TwLastFwd{tw_last_fwd(tw, LOGN), 1 << (LOGN - 4)}, q, LOGN, s0, last, set0, set1, off);
+                else ntt_fwd_pass<4>(s, TwGlobal{tw}, q, LOGN, s0, last, set0, set1, off);
+                break;
+            case 3: ntt_fwd_pass<3>(s, TwGlobal{tw}, q, LOGN, s0, last, set0, set1, off); break;
+            case 2: ntt_fwd_pass<2>(s, TwGlobal{tw}, q, LOGN, s0, last, set0, set1, off); break;
+            default: ntt_fwd_pass<1>(s, TwGlobal{tw}, q, LOGN, s0, last, set0, set1, off); break;
+        }
+    }
+}
+
+// inverse transform (without N^-1) of the two halves: input canonical, output in [0, 2q)
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv_pair(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q) {
+    static_assert(LOGN >= 6, "pair form: halves of at least 32 elements");
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    constexpr int R = HE_NTT_RADIX_LOG, LOC = LOGN - 1, NPASS = (LOC + R - 1) / R;
+    constexpr int NS = 1 << LOC;
+#pragma unroll
+    for (int pi = 0; pi < NPASS; ++pi) {
+        const int s0 = pi * R, nb = LOC - s0 < R ? LOC - s0 : R;
+        const int E = 1 << nb;
+        const int set0 = rank * (NS / E), set1 = (rank + 1) * (NS / E), off = rank * NS;
+        switch (nb) {
+            case 4:
+                if (s0 == 0) ntt_inv_pass<4>(s, TwFirstInv{tw_first_inv(itw, LOGN), 1 << (LOGN - 4)}, q, LOGN, s0, set0, set1, off);
+                else ntt_inv_pass<4>(s, TwGlobal{itw}, q, LOGN, s0, set0, set1, off);
+                break;
+            case 3: ntt_inv_pass<3>(s, TwGlobal{itw}, q, LOGN, s0, set0, set1, off); break;
+            case 2: ntt_inv_pass<2>(s, TwGlobal{itw}, q, LOGN, s0, set0, set1, off); break;
+            default: ntt_inv_pass<1>(s, TwGlobal{itw}, q, LOGN, s0, set0, set1, off); break;
+        }
+    }
+    cl.sync();
+    pair_cross_step<LOGN>(s, itw[1], q, false);
+    cl.sync();
+}
+
+// dynamic shared memory and threads of a pair-form CTA: a half (padded), one radix-16 set per thread
+__host__ __device__ __forceinline__ size_t pair_smem_bytes(int logn) { return ((size_t)1 << (logn - 1)) * 8 + ((size_t)1 << (logn - 1)) / 32 * 8; }
+constexpr int pair_threads_c(int logn) { return (1 << (logn - 1 - HE_NTT_RADIX_LOG)) > 512 ? 512 : (1 << (logn - 1 - HE_NTT_RADIX_LOG)); }
+__host__ __device__ __forceinline__ int pair_threads(int logn) { return pair_threads_c(logn); }
+
 // twiddle table of prime index p: which = 0 forward (psi^brv(k), Shoup), 1 inverse (psi^-brv(k), Shoup)
 __device__ __forceinline__ const ulonglong2 *twiddles(const uint64_t *d_tw, int p, int which, int logn) {
     return reinterpret_cast<const ulonglong2 *>(d_tw + (size_t)p * tw_prime_words(logn) + ((size_t)which << (logn + 1)));

@@ -123,6 +123,8 @@ _SIGS = {
     "he_ct_host_level": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.POINTER(_i32)]),
     "he_ct_import_host": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(HeCt)]),
     "he_keyswitch_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "he_ntt_form": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "he_set_ntt_form": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_set_basis_extension": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_get_basis_extension": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "he_bconv_i8_host": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _u64, ctypes.POINTER(_u64)]),
@@ -838,6 +840,17 @@ class Context:
         _check(_lib().he_keyswitch_tuning(self.handle, ctypes.byref(v), ms), "he_keyswitch_tuning")
         return {"variant": int(v.value), "variant_ms": [round(float(x), 4) for x in ms],
                 "variants": ["one CTA per limb-poly, usual threads", "one CTA per limb-poly, 512 threads, <= 64 registers"]}
+
+    def ntt_form(self) -> dict:
+        """NTT form of launches of many limb-polys (he_ntt_form): 0 one CTA, 1 a 2-CTA cluster per limb-poly."""
+        f = ctypes.c_int()
+        ms = (ctypes.c_float * 2)()
+        _check(_lib().he_ntt_form(self.handle, ctypes.byref(f), ms), "he_ntt_form")
+        return {"form": int(f.value), "form_ms": [round(float(x), 4) for x in ms],
+                "forms": ["one CTA per limb-poly", "2-CTA cluster per limb-poly"]}
+
+    def set_ntt_form(self, form: int) -> None:
+        _check(_lib().he_set_ntt_form(self.handle, form), "he_set_ntt_form")
 
     # ---- basis extension engine of ModUp ----
     def set_basis_extension(self, engine: int) -> None:
