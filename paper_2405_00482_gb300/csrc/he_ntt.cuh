@@ -548,7 +548,8 @@ __device__ __forceinline__ void ntt_fwd_pair(uint64_t *s, const ulonglong2 *__re
     }
 }
 
-// inverse transform (without N^-1) of the two halves: input canonical, output in [0, 2q)
+// inverse transform (without N^-1) of the two halves: input canonical, output in [0, 2q); every
+// thread of both CTAs calls it after writing its part of the half to shared memory
 template <int LOGN>
 __device__ __forceinline__ void ntt_inv_pair(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q) {
     static_assert(LOGN >= 6, "pair form: halves of at least 32 elements");
@@ -556,6 +557,7 @@ __device__ __forceinline__ void ntt_inv_pair(uint64_t *s, const ulonglong2 *__re
     const int rank = (int)cl.block_rank();
     constexpr int R = HE_NTT_RADIX_LOG, LOC = LOGN - 1, NPASS = (LOC + R - 1) / R;
     constexpr int NS = 1 << LOC;
+    __syncthreads();  // the half staged by this CTA's threads (the local passes come first)
 #pragma unroll
     for (int pi = 0; pi < NPASS; ++pi) {
         const int s0 = pi * R, nb = LOC - s0 < R ? LOC - s0 : R;
