@@ -573,6 +573,24 @@ def run_bsgs(ctx, he, inputs, P, args, flush, world, dev):
         out[name]["batched_jobs_as_plain_calls_per_sec"] = round(64e3 / statistics.median(t), 1)
         out[name]["batched_jobs_galois_keys"] = len(steps)
         out[name]["batched_jobs_key_bytes"] = len(steps) * key_bytes
+        # served one request per call (the batched lanes run the diagonal method only): 1000
+        # Poisson arrivals at 500 requests/s over the 64 jobs
+        rng = np.random.default_rng(1)
+        pick, gaps = rng.integers(0, 64, size=1000), rng.exponential(1.0 / 500.0, size=1000)
+        server = he.Server(ctx, slots=1, level=level, hbm_budget_bytes=120 << 30, plain=True)
+        rids, t_next = [], time.perf_counter()
+        t0 = t_next
+        for i in range(1000):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                pass
+            j = int(pick[i])
+            rids.append(server.submit(plans[j], pms[j], cts[j][0], outs[j][0]))
+        lats = np.sort(np.array([server.wait(r) for r in rids]))
+        wall = time.perf_counter() - t0
+        server.close()
+        out[name]["served_plain_500rps"] = {"requests": 1000, "throughput": round(1000 / wall, 1), "p50_ms": round(1e3 * lats[500], 3),
+                                            "p99_ms": round(1e3 * lats[990], 3)}
     out["workload"] = ("gradient X^T[[r]] 256x1024 (m'=64, B=8 baby x 8 giant steps) as one plain MatMult call; the 64 uneven batched "
                        "jobs as plain calls (B = the power of two >= sqrt(m')); N=8192; the persistent batch kernel and the batched "
                        "server lanes run the diagonal method only")
@@ -649,6 +667,12 @@ def run_vfl_nn(he, inputs, args, flush, world, dev, rank):
     reps = max(3, min(args.steps, 10))
     t_fwd = _event_times(lambda: ctx.cdiag_matmult(Wm, cts, fwd_out), reps, flush, warm=1)
     t_tr = _event_times(lambda: ctx.cdiag_transpose(cts, m, n), reps, flush, warm=1)
+    # the same 255 key switches with the basis extension of their ModUp on the INT8 tensor cores
+    # (byte-split products, exact recombination); the ciphertexts are the same bit for bit
+    ctx.set_basis_extension(he.HE_BCONV_INT8_TC)
+    t_tr8 = _event_times(lambda: ctx.cdiag_transpose(cts, m, n), reps, flush, warm=1)
+    same8 = all(torch.equal(ctx.ct_export(a), ctx.ct_export(b)) for a, b in zip(ctx.cdiag_transpose(cts, m, n)[:8], tcts[:8]))
+    ctx.set_basis_extension(he.HE_BCONV_INT64)
     t_bwd = _event_times(lambda: ctx.cdiag_matmult(Dm, tcts, bwd_out), reps, flush, warm=1)
     s_fwd = max_over_ranks(sum(t_fwd) / 1e3, world, dev)
     macs = K * (level + 1) * P.n * 2 * n  # 64-bit modular multiply-adds of one forward product
@@ -659,7 +683,10 @@ def run_vfl_nn(he, inputs, args, flush, world, dev, rank):
     return {"workload": "A 4096x256 ~ U[-1,1] as 256 diagonal ciphertexts, W 256x128 ~ N(0,1/256), D^T 4096x128 ~ N(0,1/4096); "
                         "N=16384, Q=[60,40x6], P=[60,60,60], dnum=3, scale 2^40",
             "forward_per_sec": round(whole_job_rate(reps, world, s_fwd), 2), "forward_ms": {"p50": _pct(t_fwd, 0.5), "p99": _pct(t_fwd, 0.99)},
-            "transpose_ms": {"p50": _pct(t_tr, 0.5), "p99": _pct(t_tr, 0.99), "key_switches": len(he.Context.cdiag_transpose_steps(m, n))},
+            "transpose_ms": {"p50": _pct(t_tr, 0.5), "p99": _pct(t_tr, 0.99), "key_switches": len(he.Context.cdiag_transpose_steps(m, n)),
+                             "basis_extension": "INT64"},
+            "transpose_int8_tc_ms": {"p50": _pct(t_tr8, 0.5), "p99": _pct(t_tr8, 0.99), "basis_extension": "INT8 tensor cores (mma.sync u8)",
+                                     "bit_identical_to_int64": bool(same8)},
             "backward_matmult_ms": {"p50": _pct(t_bwd, 0.5), "p99": _pct(t_bwd, 0.99)}, "max_abs_err": err,
             "roofline": {"kernel": "cdiag_mac_kernel (+ rescale, whole call)", "bound": "alu", "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "T modmul-add/s", "frac": round(achieved / peak, 4),
@@ -713,11 +740,24 @@ def run_batched(ctx, he, inputs, P, args, flush, world, dev):
     sp = max_over_ranks(sum(t_plain) / 1e3, world, dev)
     rot = sum(p.m_prime - 1 for p in plans)
     tb = sorted(t_batch)
+    # bytes the batch must move: every job's plaintexts (Q U P limbs) and ciphertexts, the keys once
+    ext = level + 1 + len(P.p_bits)
+    pt_bytes = sum(p.m_prime for p in plans) * ext * P.n * 8
+    key_bytes = len(steps) * P.dnum * 2 * (len(P.q_bits) + len(P.p_bits)) * P.n * 8
+    ct_bytes = len(plans) * (2 * (level + 1) + 2 * level) * P.n * 8
+    alg = pt_bytes + key_bytes + ct_bytes
+    b_s = statistics.median(t_batch) / 1e3
+    peak = _peaks()["hbm_gbs"]
+    batch_roof = {"bound": "alu (integer multiply issue)", "hbm_achieved": round(alg / b_s / 1e9, 1), "hbm_peak": peak, "unit": "GB/s",
+                  "hbm_frac": round(alg / b_s / 1e9 / peak, 4), "alg_bytes_per_batch": alg,
+                  "counted": "plaintexts of every job (m' x (l+1+K) limbs) + Galois keys once + input and output ciphertexts",
+                  "note": "the loop kernel is about 95% of the batch; ncu: ~220 thread instructions per (rotation, limb, coefficient), "
+                          "issue active ~50%"}
     return {"value": round(whole_job_rate(64 * args.steps, world, sb), 1), "unit": "MatMult/s",
             "plain_same_jobs": round(whole_job_rate(64 * args.steps, world, sp), 1), "speedup_vs_plain": round(sp / sb, 3),
             "rotations_per_sec": round(rot * args.steps * world / sb, 1), "batch_ms": {"p50": round(tb[len(tb) // 2], 4),
             "p99": round(tb[min(len(tb) - 1, int(0.99 * len(tb)))], 4)}, "hoisted_rotations_per_batch": rot,
-            "bit_identical_to_plain": bool(same), "autotune": batch.tuning(), "stage_form": batch.stage_tuning(),
+            "bit_identical_to_plain": bool(same), "autotune": batch.tuning(), "stage_form": batch.stage_tuning(), "roofline": batch_roof,
             "workload": "64 gradient MatMults X^T[[r]], X b x f ~ N(0,1), b ~ U{128..4096}, f ~ U{16..512} (seed 0), N=8192"}
 
 
