@@ -242,7 +242,12 @@ def run_gpu(args):
         torch.distributed.barrier()
     with ClockSampler(local) as clk_graph:
         torch.cuda.synchronize()
+        if args.profile_region:  # the timed graph replays alone between cudaProfilerStart and Stop
+            torch.cuda.profiler.start()
         times_graph = timed_steps(graph.replay)
+        if args.profile_region:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
     use_graph = not args.no_graph
     times = times_graph if use_graph else times_eager
     clk = clk_graph if use_graph else clk_eager
@@ -1002,6 +1007,66 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """One small workload for an ncu capture (--profile-from-start off): the inputs are made and the
+    kernels warmed up, then the profiled calls run between cudaProfilerStart and cudaProfilerStop.
+    Cases: hoisted_rotations (63 rotations of one N = 8192 ciphertext), rotate_many (63 different
+    ciphertexts), matrix_encode (the 256 x 1024 gradient matrix's diagonals), batch (the first
+    --case-jobs of the 64 uneven batched jobs, one batch run), bsgs (the gradient MatMult with 8 baby
+    steps), int8_modup (hoisted rotations with the INT8 tensor-core basis extension), matmult (the
+    gradient MatMult call)."""
+    import numpy as np
+    import torch
+
+    from paper_2405_00482_gb300 import he, inputs
+
+    P = inputs.PARAMS_N8192
+    lvl = P.top
+    ctx = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=0)
+    dev = torch.device("cuda", 0)
+    case = args.profile_case
+    X, r, _ = inputs.gradient_and_forward_n8192(seed=0)
+    ones = torch.ones(P.slots, dtype=torch.float64, device=dev)
+    steps = list(range(1, 64))
+    if case in ("hoisted_rotations", "rotate_many", "int8_modup"):
+        ctx.keygen(steps)
+        if case == "int8_modup":
+            ctx.set_basis_extension(he.HE_BCONV_INT8_TC)
+        ct = ctx.encrypt(ctx.encode(ones, P.scale, lvl), 4242)
+        cts = [ctx.encrypt(ctx.encode(ones, P.scale, lvl), 50 + i) for i in steps]
+        outs = [ctx.new_ct(lvl) for _ in steps]
+        run = (lambda: ctx.rotate_many(cts, steps, outs)) if case == "rotate_many" else (lambda: ctx.rotate_hoisted(ct, steps, outs=outs))
+    elif case in ("matrix_encode", "matmult", "bsgs"):
+        plan = he.Plan(256, 1024, P.slots, baby=8 if case == "bsgs" else 0)
+        ctx.keygen(plan.rotation_steps)
+        dX = torch.from_numpy(X).to(dev)
+        pm = ctx.encode_matrix(plan, dX, lvl, transposed=True)
+        cts = ctx.encrypt_vector(plan, torch.from_numpy(r).to(dev), P.scale, lvl, 7)
+        res = [ctx.new_ct(lvl - 1)]
+        run = (lambda: ctx.encode_matrix(plan, dX, lvl, out=pm, transposed=True)) if case == "matrix_encode" else (
+            lambda: ctx.matmult(plan, pm, cts, res))
+    elif case == "batch":
+        jobs = inputs.batched_instances(64, seed=0)[: args.case_jobs]
+        plans = [he.Plan(Xj.shape[1], Xj.shape[0], P.slots) for Xj, _ in jobs]
+        ctx.keygen(sorted({s_ for p_ in plans for s_ in p_.rotation_steps}))
+        pms = [ctx.encode_matrix(p_, torch.from_numpy(Xj.T.copy()).to(dev), lvl) for p_, (Xj, _) in zip(plans, jobs)]
+        cts = [ctx.encrypt_vector(p_, torch.from_numpy(rj).to(dev), P.scale, lvl, 9000 + i)[0] for i, (p_, (_, rj)) in enumerate(zip(plans, jobs))]
+        batch = he.Batch(ctx, plans, pms)
+        outs = [ctx.new_ct(lvl - 1) for _ in jobs]
+        run = lambda: batch.run(cts, outs)
+    else:
+        raise SystemExit(f"unknown case {case}")
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(args.case_calls):
+        run()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_case": case, "calls": args.case_calls}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1020,7 +1085,15 @@ def main():
     ap.add_argument("--loop-variant", type=int, default=-1,
                     help="pin the MatMult loop-kernel variant of the plain products (default: autotune)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="length of the paced Poisson stream (500 requests/s)")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed graph replays with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--profile-case", default=None, help="run one small workload between cudaProfilerStart/Stop for ncu (see run_profile_case)")
+    ap.add_argument("--case-calls", type=int, default=1)
+    ap.add_argument("--case-jobs", type=int, default=16)
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
