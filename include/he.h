@@ -243,7 +243,8 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
  * so make that first call before any stream capture.  Every call uses the same array: calls
  * that overlap on the GPU (other streams, other contexts, other threads) race and corrupt each
  * other's results, so serialise them.  Nothing in the array has to start at zero: each call
- * writes every word before reading it. */
+ * writes every word before reading it.  Plans with baby steps (he_plan_set_baby_steps) are
+ * refused with HE_EINVAL. */
 int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm, const he_ct *ins, int n_in, he_ct *outs,
                                     int n_out);
 
