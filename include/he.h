@@ -256,13 +256,17 @@ int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_p
 int he_keyswitch_tuning(const he_ctx *ctx, int *variant, float *ms);
 
 /* NTT launches of many limb-polys (an encoded matrix's 4 x m' transforms, import and export of
- * plaintext batches) run as one CTA per limb-poly (form 0) or as a 2-CTA cluster per limb-poly
+ * plaintext batches) run as one CTA per limb-poly (form 0), as a 2-CTA cluster per limb-poly
  * (form 1: each CTA holds half of the coefficients, the one stage that pairs the halves goes
- * through distributed shared memory).  The first matrix a context encodes times both on its
- * transform (synchronising the stream; not under stream capture) and keeps the faster for the
- * context; he_ntt_form reports the choice (-1 before) and ms[0..1] (may be NULL), he_set_ntt_form
- * pins one (0, 1, or -1 to time again).  Results are the same in either form.  A fork starts with
- * its parent's choice. */
+ * through distributed shared memory), or, for forward transforms, in two phases (form 2: with
+ * N = 64 C, stages 0-5 as 64-point transforms of the C columns x = l C + c, then the remaining
+ * stages as C-point transforms of the 64 rows, each phase one launch of many small CTAs, the
+ * intermediate values in global memory; inverse transforms then use form 0).  The first matrix a
+ * context encodes times the forms on its transform (synchronising the stream; not under stream
+ * capture) and keeps the fastest for the context; he_ntt_form reports the choice (-1 before) and
+ * ms[0..HE_NTT_FORMS-1] (may be NULL), he_set_ntt_form pins one (0 .. HE_NTT_FORMS-1, or -1 to
+ * time again).  Results are the same in every form.  A fork starts with its parent's choice. */
+#define HE_NTT_FORMS 3
 int he_ntt_form(const he_ctx *ctx, int *form, float *ms);
 int he_set_ntt_form(he_ctx *ctx, int form);
 
@@ -322,6 +326,30 @@ int he_batch_tuning(const he_batch *batch, int *variant, float *ms);
  * graph on its next run (this call waits for the batch's previous run to finish). */
 int he_ptmat_set_variant(he_ptmat *pm, int v);
 int he_batch_set_variant(he_batch *batch, int v);
+/* Fused key tables (Sec. 2.2 O4 with the plaintext product of Sec. 4.2 folded in): for an encoded
+ * matrix that is multiplied more than once, the MatMult can read, for every rotation step i,
+ * digit d and component c, the products F_i[d][c] = ksk_i[d][c] (x) pt_i (Montgomery form, built
+ * once on the GPU from the bound Galois keys) instead of the key and the plaintext, so that the
+ * loop accumulates sum_i sum_d D_d(src_i) F_i[d][c] with one product per operand pair and no
+ * per-step reduction.  The residues, and so the outputs, are the same as without the tables.
+ * Memory: (m' - 1) ndig 2 (l+1+K) N 8 bytes per plaintext block, owned by the encoded matrix.
+ * he_set_key_fusion sets the context family's policy: mode 0 never; 1 (default) when an encoding
+ * is multiplied a second time without being re-encoded; 2 at the first MatMult; tables above
+ * max_bytes (0: 8 GiB) are never built.  When built, both forms are timed on that call (which
+ * then synchronises the stream) and the tables kept only if faster.  Re-encoding a matrix that
+ * holds tables rebuilds them in stream order.  Only for 1 to 3 digits, not under stream
+ * capture (a captured MatMult uses the tables if they exist), not on the batched, BSGS and
+ * allocation-free paths.  he_ptmat_key_fusion reports state (0 not tried, 1 in use, -1 not
+ * used), the fused form's variant and, when ms is not NULL, its timed ms per variant
+ * (HE_MM_MAX_VARIANTS entries, 0 for variants without a fused form);
+ * he_ptmat_set_key_fusion(pm, 0, -1) frees the tables and keeps them off for pm;
+ * (pm, 1, -1) makes pm eligible again; (pm, 1, v) pins the fused form with loop-kernel variant v
+ * (one with cp.async stages, he_loop_variant_shape) for pm whatever the context's mode: the
+ * tables are built at pm's next MatMult (not under capture) and used without timing.  HE_EINVAL
+ * for NULL, a mode out of range or a variant without a fused form. */
+int he_set_key_fusion(he_ctx *ctx, int mode, size_t max_bytes);
+int he_ptmat_key_fusion(const he_ptmat *pm, int *state, int *variant, float *ms);
+int he_ptmat_set_key_fusion(he_ptmat *pm, int on, int variant);
 /* A batch's ModUp, ModDown and rescale run as one CTA per limb-poly (form 0) or as 8-CTA clusters
  * per limb-poly (form 1: fewer, shorter launches, for batches of few jobs); the results are the
  * same.  The first he_batch_run times both forms with the chosen loop variant and keeps the faster;

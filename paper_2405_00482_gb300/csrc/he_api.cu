@@ -263,7 +263,8 @@ int he_ctx_create(const he_params *p, uint64_t seed, void *stream, he_ctx **out)
     ctx->alpha = (p->n_q + p->dnum - 1) / p->dnum;
     ctx->seed = seed;
     ctx->stream = (cudaStream_t)stream;
-    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess) {
         delete ctx;
         return HE_ECUDA;
     }
@@ -468,6 +469,7 @@ int he_ctx_fork(he_ctx *parent, void *stream, he_ctx **out) {
     ctx->dnum = parent->dnum;
     ctx->alpha = parent->alpha;
     ctx->device = parent->device;
+    ctx->sms = parent->sms;
     ctx->seed = parent->seed;
     ctx->stream = (cudaStream_t)stream;
     ctx->primes = parent->primes;
@@ -484,8 +486,7 @@ int he_ctx_fork(he_ctx *parent, void *stream, he_ctx **out) {
     ctx->batch_variant = parent->batch_variant;
     ctx->bconv = parent->bconv;
     ctx->ntt_form = parent->ntt_form;
-    ctx->ntt_form_ms[0] = parent->ntt_form_ms[0];
-    ctx->ntt_form_ms[1] = parent->ntt_form_ms[1];
+    for (int f = 0; f < HE_NTT_FORMS; ++f) ctx->ntt_form_ms[f] = parent->ntt_form_ms[f];
     ctx->d_bconv_a = parent->d_bconv_a;
     ctx->bconv_a_off = parent->bconv_a_off;
     // the parent's pending work (keys, tables) must be complete before the fork's stream uses it
@@ -850,9 +851,10 @@ static int ptmat_alloc(he_ctx *ctx, const he_plan *plan, int level, double scale
 }
 
 // The first matrix encoded on a context times its transform (one launch of many limb-polys) in
-// both NTT forms, one CTA or a 2-CTA pair per limb-poly (the same values: the launch is repeated
-// on the same input), and keeps the faster for every such launch of the context; not under
-// stream capture, nor for launches small enough for the cluster form.  Synchronises the stream.
+// every NTT form, one CTA or a 2-CTA pair per limb-poly or two phases (the same values: the
+// launch is repeated on the same input), and keeps the fastest for every such launch of the
+// context; not under stream capture, nor for launches small enough for the cluster form.
+// Synchronises the stream.
 static void tune_ntt_form(he_ctx *ctx, const int64_t *coef, uint64_t *out, int groups, const LimbMap &map) {
     const int polys = groups * map.n;
     if (use_cluster(ctx->log_n, polys) || ctx->log_n < 12 || ctx->log_n > 14) return;
@@ -865,7 +867,7 @@ static void tune_ntt_form(he_ctx *ctx, const int64_t *coef, uint64_t *out, int g
         return;
     }
     int best = 0;
-    for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < HE_NTT_FORMS; ++f) {
         ctx->ntt_form = f;
         float ms = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
@@ -902,6 +904,11 @@ static int ptmat_encode(he_ctx *ctx, he_ptmat *pm, const double *X, int trans) {
     if (ev) cudaEventRecord(ev[0], ctx->stream);
     launch_ntt_from_int64(ctx, coef, pm->data, (int)count, qpmap(ctx, pm->level), 1);
     if (ev) cudaEventRecord(ev[1], ctx->stream);
+    pm->enc_gen++;
+    if (pm->fuse_state == 1 && pm->fused) {  // keep the fused key tables in step with the plaintexts
+        launch_fuse_keys(ctx, pm);
+        pm->fused_gen = pm->enc_gen;
+    }
     return last_launch();
 }
 
@@ -959,6 +966,7 @@ int he_ptmat_import(he_ctx *ctx, const he_plan *plan, const uint64_t *coeffs, in
 void he_ptmat_free(he_ptmat *pm) {
     if (!pm) return;
     cudaStreamSynchronize(pm->ctx->stream);
+    cudaFree(pm->fused);
     cudaFree(pm->data);
     cudaFree(pm->d_keys);
     cudaFree(pm->d_galois);
@@ -1020,6 +1028,73 @@ int he_encrypt_vector(he_ctx *ctx, const he_plan *plan, const double *y, double 
     return last_launch();
 }
 
+// Build pm's fused key tables, time the fused forms against the two-level form's tuned time and
+// keep the tables only if faster (he_set_key_fusion).  A table over the size limit or an
+// allocation failure leaves the matrix on the two-level form.  Synchronises the stream.
+static int fuse_try(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc) {
+    const he_plan &p = pm->plan;
+    const size_t bytes =
+        (size_t)p.row_blocks * p.col_blocks * (p.m_prime - 1) * 2 * ctx->modup[pm->level].ndig * pm->ext * ctx->n * sizeof(uint64_t);
+    pm->fuse_state = -1;
+    if (pm->fvariant_pin < 0 && (bytes > ctx->sh->fuse_max || pm->variant < 0)) return HE_OK;
+    if (cudaMalloc(&pm->fused, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        pm->fused = nullptr;
+        return HE_OK;
+    }
+    launch_fuse_keys(ctx, pm);
+    pm->fused_gen = pm->enc_gen;
+    if (pm->fvariant_pin >= 0) {
+        pm->fvariant = pm->fvariant_pin;
+        pm->fuse_state = 1;
+        return last_launch();
+    }
+    const int rc = tune_matmult_fused(ctx, pm, ct, D, acc, cacc);
+    if (rc != HE_OK) return rc;
+    if (pm->fvariant >= 0 && pm->fuse_ms[pm->fvariant] < pm->tune_ms[pm->variant]) {
+        pm->fuse_state = 1;
+        return HE_OK;
+    }
+    cudaFree(pm->fused);  // the tuning synchronised the stream
+    pm->fused = nullptr;
+    return HE_OK;
+}
+
+int he_set_key_fusion(he_ctx *ctx, int mode, size_t max_bytes) {
+    if (!ctx || mode < 0 || mode > 2) return HE_EINVAL;
+    ctx->sh->key_fusion = mode;
+    ctx->sh->fuse_max = max_bytes ? max_bytes : ((size_t)8 << 30);
+    return HE_OK;
+}
+
+int he_ptmat_key_fusion(const he_ptmat *pm, int *state, int *variant, float *ms) {
+    if (!pm || !state || !variant) return HE_EINVAL;
+    *state = pm->fuse_state;
+    *variant = pm->fvariant;
+    if (ms)
+        for (int v = 0; v < mm_variant_count(); ++v) ms[v] = pm->fuse_ms[v];
+    return HE_OK;
+}
+
+int he_ptmat_set_key_fusion(he_ptmat *pm, int on, int variant) {
+    if (!pm || on < 0 || on > 1 || variant < -1 || variant >= mm_variant_count()) return HE_EINVAL;
+    if (on && variant >= 0 && !mm_variant_fusable(variant, pm->ctx->modup[pm->level].ndig)) return HE_EINVAL;
+    pm->fvariant_pin = on ? variant : -1;
+    if (!on) {
+        if (pm->fused) {
+            cudaStreamSynchronize(pm->ctx->stream);
+            cudaFree(pm->fused);
+            pm->fused = nullptr;
+        }
+        pm->fuse_state = -1;
+    } else if (pm->fuse_state < 0) {
+        pm->fuse_state = 0;
+    } else if (pm->fuse_state == 1 && variant >= 0) {
+        pm->fvariant = variant;
+    }
+    return HE_OK;
+}
+
 // resolve the Galois keys of rotation steps 1..m'-1 into a device pointer table, once
 int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm) {
     const int64_t steps = pm->plan.m_prime - 1;
@@ -1071,6 +1146,16 @@ int he_matmult_plain_cipher(he_ctx *ctx, const he_plan *plan, const he_ptmat *pm
             if (rc != HE_OK) return rc;
         } else {
             pm->variant = 0;
+        }
+    }
+    if (rot) {
+        const bool reused = pm->mm_gen == pm->enc_gen;  // this encoding was multiplied before
+        pm->mm_gen = pm->enc_gen;
+        const int mode = ctx->sh->key_fusion;
+        const bool pinned = pm->fvariant_pin >= 0;
+        if (pm->fuse_state == 0 && (pinned || (mode > 0 && (reused || mode == 2))) && mu.ndig <= 3 && !capturing(ctx->stream)) {
+            rc = fuse_try(ctx, pm, ins[0].data, D, acc, cacc);
+            if (rc != HE_OK) return rc;
         }
     }
     for (int r = 0; r < n_out; ++r) {
@@ -1497,15 +1582,13 @@ int he_pt_import(he_ctx *ctx, const uint64_t *coeffs, int level, double scale, h
 int he_ntt_form(const he_ctx *ctx, int *form, float *ms) {
     if (!ctx || !form) return HE_EINVAL;
     *form = ctx->ntt_form;
-    if (ms) {
-        ms[0] = ctx->ntt_form_ms[0];
-        ms[1] = ctx->ntt_form_ms[1];
-    }
+    if (ms)
+        for (int f = 0; f < HE_NTT_FORMS; ++f) ms[f] = ctx->ntt_form_ms[f];
     return HE_OK;
 }
 
 int he_set_ntt_form(he_ctx *ctx, int form) {
-    if (!ctx || form < -1 || form > 1) return HE_EINVAL;
+    if (!ctx || form < -1 || form >= HE_NTT_FORMS) return HE_EINVAL;
     ctx->ntt_form = form;
     return HE_OK;
 }

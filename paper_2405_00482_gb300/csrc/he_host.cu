@@ -13,6 +13,11 @@
 
 int he_check(cudaError_t e);
 
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 namespace {
 
 // A host pointer the GPU can copy from asynchronously (cudaMallocHost / cudaHostRegister memory).
@@ -23,11 +28,6 @@ bool page_locked(const void *p) {
         return false;
     }
     return a.type == cudaMemoryTypeHost;
-}
-
-bool capturing(cudaStream_t st) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
 }
 
 // device staging of at least `bytes`; the previous contents are not kept.  Growing waits for

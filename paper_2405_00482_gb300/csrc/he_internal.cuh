@@ -130,6 +130,8 @@ struct ModDownConst {
 struct he_shared {
     std::mutex mu;                            // guards keys (keygen on one context, lookups on others)
     std::map<uint32_t, uint64_t *> keys;      // Galois element -> [dnum][2][L+K][N]
+    int key_fusion = 1;                       // fused key tables of encoded matrices: 0 never, 1 on reuse, 2 always
+    size_t fuse_max = (size_t)8 << 30;        // largest fused table built (bytes)
     void *owned[6] = {};                      // device tables: d_mc, d_tw, d_fft, d_sk, d_sk_mont, d_bconv_a
     ~he_shared() {
         for (auto &kv : keys) cudaFree(kv.second);
@@ -145,6 +147,7 @@ struct he_shared {
 struct he_ctx {
     int log_n, n, L, K, dnum, alpha;
     int device;                       // CUDA device the context was created on (current at he_ctx_create)
+    int sms = 1;                      // its multiprocessors
     uint64_t seed;
     cudaStream_t stream;
     std::vector<uint64_t> primes;     // Q then P
@@ -164,8 +167,9 @@ struct he_ctx {
     size_t scratch_words;
     int batch_variant = 0;            // last variant a batch tuned to (used by serving lanes)
     int bconv = 0;                    // basis extension of ModUp: 0 exact INT64 products, 1 INT8 tensor-core limb split
-    int ntt_form = -1;                // NTT launches of many limb-polys: 0 one CTA each, 1 a 2-CTA cluster each (-1: not yet timed)
-    float ntt_form_ms[2] = {};        // the timed milliseconds of each form (an encoded matrix's transform)
+    int ntt_form = -1;                // NTT launches of many limb-polys: 0 one CTA each, 1 a 2-CTA cluster each, 2 two phases
+                                      // (forward only; -1: not yet timed)
+    float ntt_form_ms[HE_NTT_FORMS] = {};  // the timed milliseconds of each form (an encoded matrix's transform)
     int ks_variant = -1;              // transform variant of the many-rotation key switch, chosen by timing (-1: not yet)
     float ks_tune_ms[2] = {};         // the timed milliseconds of each variant (one full chunk of rotations)
     uint32_t *d_bconv_a = nullptr;    // INT8 engine: tensor-core A fragments of every (level, digit), shared with forks
@@ -260,6 +264,15 @@ struct he_ptmat {
     uint32_t *d_galois;      // [m'-1]
     int variant = -1;        // loop-kernel variant chosen by timing (-1: not yet tuned)
     float tune_ms[HE_MM_MAX_VARIANTS] = {};
+    // fused key tables [R][C][m'-1][ndig][2][ext][N] (key_i pt_i products, he_set_key_fusion)
+    uint64_t *fused = nullptr;
+    int fuse_state = 0;      // 0 not tried, 1 built and faster (used), -1 not used for this matrix
+    int fvariant = -1;       // staged variant of the fused form chosen by timing
+    int fvariant_pin = -1;   // >= 0: fused form with this variant, built without timing
+    float fuse_ms[HE_MM_MAX_VARIANTS] = {};
+    uint64_t enc_gen = 0;    // bumped by every (re-)encoding of data
+    uint64_t fused_gen = 0;  // enc_gen the fused tables were built from
+    uint64_t mm_gen = ~0ull; // enc_gen at the last MatMult
 };
 
 // a prepared batch of R = C = 1 MatMults at one level (he_batch_create)
@@ -308,6 +321,10 @@ int mm_variant_tile(int v);  // coefficients per tile of loop-kernel variant v
 void mm_variant_shape(int v, int *vec, int *grp, int *stages, int *ga);
 int mm_batch_ctas_per_sm(int v, int ndig);
 int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc);
+int tune_matmult_fused(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc);
+bool capturing(cudaStream_t st);           // st is being captured into a graph
+bool mm_variant_fusable(int v, int ndig);  // variant v has a fused-key form for ndig digits
+void launch_fuse_keys(he_ctx *ctx, he_ptmat *pm);  // pm->fused from pm->data and the bound Galois keys
 // defined in he_api.cu (inside its extern "C" block)
 extern "C" {
 int batch_create_impl(he_ctx *ctx, int count, int level, const he_ptmat *const *pms, he_batch **out);

@@ -151,6 +151,109 @@ __global__ void PAIR_BOUNDS(LOGN) ntt_from_int64_pair_kernel(const int64_t *__re
 }
 
 // out = data 2^-64 mod q (Montgomery form back to canonical); grid (blocks, groups, limbs)
+// ---- two-phase form (he_set_ntt_form 2): the transform as column and row sub-transforms ----
+// With N = 64 C (C = 2^(log N - 6)), stages 0..5 of the forward transform only combine the 64
+// elements x = l C + c of one column c (their stage-s group x >> (log N - s) = l >> (6 - s) does
+// not depend on c), and stages 6..log N - 1 only the C elements of one row x = b C + m.  The
+// column phase takes NTT2_TC columns of one limb-poly per CTA (two radix-8 passes in registers,
+// one exchange through shared memory) and writes the stage-5 values (below 4q) to out; the row
+// phase takes NTT2_TR rows per CTA in place (a radix-2^NB1 and a radix-2^NB2 pass) and finishes
+// as the other forms do: canonical residues, times 2^64 mod q when to_mont.  The butterflies
+// and their stage order are those of the other forms, so the values are the same; the work
+// spreads over the SMs in blocks of 1/(C/NTT2_TC) (columns) or 1/4 (rows) of a limb-poly.
+#define NTT2_TC 16
+#define NTT2_TR 16
+#define NTT2_THREADS 128
+
+template <int LOGN, bool I64>
+__global__ void __launch_bounds__(NTT2_THREADS) ntt2_cols_kernel(const void *__restrict__ in_v, int64_t in_gs, uint64_t *out, int64_t out_gs,
+                                                               LimbMap map, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, C = N >> 6, TILES = C / NTT2_TC, PAD = NTT2_TC + 1;
+    static_assert(NTT2_THREADS == 8 * NTT2_TC, "one thread per (column, set of 8)");
+    __shared__ uint64_t sm[64 * PAD];
+    const int poly = blockIdx.x / TILES, c0 = (blockIdx.x % TILES) * NTT2_TC;
+    const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    const TwGlobal tw{twiddles(d_tw, p, 0, LOGN)};
+    const int c = threadIdx.x % NTT2_TC, r = threadIdx.x / NTT2_TC;
+    uint64_t v[8];
+    // stages 0-2 on the column's elements l = r + 8 i (one group at stage 0)
+    if constexpr (I64) {  // int64 coefficients, shared by the limbs of group g, reduced mod q
+        const int64_t *src = static_cast<const int64_t *>(in_v) + g * in_gs + c0 + c;
+        const uint64_t mu = mc[p].mu;
+        int64_t t[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t[i] = src[(int64_t)(r + 8 * i) * C];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = reduce_signed(t[i], q, mu);
+    } else {
+        const uint64_t *src = static_cast<const uint64_t *>(in_v) + g * in_gs + (int64_t)l * N + c0 + c;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = src[(int64_t)(r + 8 * i) * C];
+    }
+    ntt_fwd_radix<3>(v, tw, q, 0, 0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sm[(r + 8 * i) * PAD + c] = v[i];
+    __syncthreads();
+    // stages 3-5 on l = 8 r + i: group r at stage 3
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = sm[(8 * r + i) * PAD + c];
+    ntt_fwd_radix<3>(v, tw, q, 3, r);
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N + c0 + c;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[(int64_t)(8 * r + i) * C] = v[i];
+}
+
+// shared-memory row stride of the row phase: one pad word per 8 elements, and rows r, r + 1 on
+// opposite halves of the banks
+__host__ __device__ constexpr int ntt2_row_pitch(int lb) { return ((1 << lb) + (1 << lb) / 8) % 16 == 0 ? (1 << lb) + (1 << lb) / 8 + 8 : (1 << lb) + (1 << lb) / 8; }
+
+template <int LOGN, int NB1>
+__global__ void __launch_bounds__(NTT2_THREADS) ntt2_rows_kernel(uint64_t *data, int64_t gs, LimbMap map, const uint64_t *__restrict__ d_tw,
+                                                               const ModConst *__restrict__ mc, int to_mont) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, LB = LOGN - 6, R = 1 << LB, NB2 = LB - NB1, TILES = 64 / NTT2_TR, RP = ntt2_row_pitch(LB);
+    constexpr int S1 = R >> NB1, S2 = R >> NB2;  // sets per row of the two passes
+    __shared__ uint64_t sm[NTT2_TR * RP];
+    const int poly = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
+    const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
+    const uint64_t q = mc[p].q;
+    const TwGlobal tw{twiddles(d_tw, p, 0, LOGN)};
+    uint64_t *row0 = data + g * gs + (int64_t)l * N + (int64_t)b0 * R;
+    auto at = [](int m) { return m + (m >> 3); };
+    // stages 6 .. 5 + NB1 on the elements m = j + S1 i of row b (group b at stage 6)
+    for (int set = threadIdx.x; set < NTT2_TR * S1; set += NTT2_THREADS) {
+        const int rb = set / S1, j = set % S1;
+        uint64_t v[1 << NB1];
+#pragma unroll
+        for (int i = 0; i < (1 << NB1); ++i) v[i] = row0[(int64_t)rb * R + j + S1 * i];
+        ntt_fwd_radix<NB1>(v, tw, q, 6, b0 + rb);
+#pragma unroll
+        for (int i = 0; i < (1 << NB1); ++i) sm[rb * RP + at(j + S1 * i)] = v[i];
+    }
+    __syncthreads();
+    // the last NB2 stages on 2^NB2 consecutive elements m = 2^NB2 e + i: group b 2^NB1 + e
+    const uint64_t two_q = 2 * q, r1 = mc[p].r1, r1s = mc[p].r1_shoup;
+    for (int set = threadIdx.x; set < NTT2_TR * S2; set += NTT2_THREADS) {
+        const int rb = set / S2, e = set % S2;
+        uint64_t v[1 << NB2];
+#pragma unroll
+        for (int i = 0; i < (1 << NB2); ++i) v[i] = sm[rb * RP + at((e << NB2) + i)];
+        ntt_fwd_radix<NB2>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
+#pragma unroll
+        for (int i = 0; i < (1 << NB2); ++i) {
+            uint64_t x = v[i];
+            x = x >= two_q ? x - two_q : x;
+            x = x >= q ? x - q : x;
+            v[i] = to_mont ? mul_shoup(x, r1, r1s, q) : x;
+        }
+        ulonglong2 *d = reinterpret_cast<ulonglong2 *>(row0 + (int64_t)rb * R + (e << NB2));
+#pragma unroll
+        for (int i = 0; i < (1 << NB2) / 2; ++i) d[i] = make_ulonglong2(v[2 * i], v[2 * i + 1]);
+    }
+}
+
 __global__ void from_mont_kernel(const uint64_t *__restrict__ data, uint64_t *out, LimbMap map, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
     const int N = 1 << logn;
@@ -205,10 +308,34 @@ static auto pair_instance(int logn, F f) {
 }
 
 bool use_pair(const he_ctx *ctx, int polys) { return ctx->ntt_form == 1 && !use_cluster(ctx->log_n, polys) && ctx->log_n >= 12 && ctx->log_n <= 14; }
+static bool use_two_phase(const he_ctx *ctx, int polys) {
+    return ctx->ntt_form == 2 && !use_cluster(ctx->log_n, polys) && ctx->log_n >= 12 && ctx->log_n <= 14;
+}
+
+// the two launches of the two-phase forward transform (from int64 coefficients when I64)
+template <bool I64>
+static void launch_two_phase(he_ctx *ctx, const void *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int polys, const LimbMap &map, int to_mont) {
+    const int logn = ctx->log_n, C = ctx->n >> 6;
+    const unsigned cols = (unsigned)(polys * (C / NTT2_TC)), rows = (unsigned)(polys * (64 / NTT2_TR));
+    const uint64_t *tw = ctx->d_tw;
+    const ModConst *mc = ctx->d_mc;
+    ctx->launches += 2;
+    auto go = [&](auto L, auto NB1) {
+        launch_k(ntt2_cols_kernel<decltype(L)::value, I64>, cols, NTT2_THREADS, 0, ctx->stream, in, in_gs, out, out_gs, map, tw, mc);
+        launch_k(ntt2_rows_kernel<decltype(L)::value, decltype(NB1)::value>, rows, NTT2_THREADS, 0, ctx->stream, out, out_gs, map, tw, mc, to_mont);
+    };
+    if (logn == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
+    else if (logn == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 4>{});
+    else go(std::integral_constant<int, 14>{}, std::integral_constant<int, 4>{});
+}
 
 void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups,
                             const LimbMap &map, int to_mont) {
     if (groups * map.n == 0) return;
+    if (use_two_phase(ctx, groups * map.n)) {
+        launch_two_phase<false>(ctx, in, in_gs, out, out_gs, groups * map.n, map, to_mont);
+        return;
+    }
     ctx->launches++;
     if (use_pair(ctx, groups * map.n)) {
         launch_cluster_n(pair_instance(ctx->log_n, [](auto L) { return ntt_fwd_pair_kernel<L.value>; }), groups * map.n * 2, pair_threads(ctx->log_n),
@@ -262,8 +389,12 @@ void launch_ntt_inv(he_ctx *ctx, const uint64_t *in, uint64_t *out, int groups, 
 
 void launch_ntt_from_int64(he_ctx *ctx, const int64_t *in, uint64_t *out, int groups, const LimbMap &map, int to_mont) {
     if (groups * map.n == 0) return;
-    ctx->launches++;
     const int polys = groups * map.n;
+    if (use_two_phase(ctx, polys)) {
+        launch_two_phase<true>(ctx, in, ctx->n, out, (int64_t)map.n * ctx->n, polys, map, to_mont);
+        return;
+    }
+    ctx->launches++;
     if (use_pair(ctx, polys)) {
         launch_cluster_n(pair_instance(ctx->log_n, [](auto L) { return ntt_from_int64_pair_kernel<L.value>; }), polys * 2, pair_threads(ctx->log_n),
                          pair_smem_bytes(ctx->log_n), ctx->stream, 2, in, out, map, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, to_mont);

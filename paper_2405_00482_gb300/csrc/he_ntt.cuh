@@ -92,6 +92,36 @@ struct TwFirstInv {
     __device__ __forceinline__ ulonglong2 at(int j, int g, int i, int, int) const { return t4[(16 - (16 >> j) + i) * G + g]; }
 };
 
+// NB forward stages s0..s0+NB-1 on the 2^NB elements of one set held in registers, r[k] the
+// element base + (k << lg_tl) of a set whose stage-s0 group is g (g = base >> (log N - s0)):
+// at stage s0 + j element k meets twiddle entry m + (g << j) + (k >> (NB - j)), m = 2^(s0+j),
+// the 2^j consecutive entries loaded once per stage.  Harvey's lazy butterfly: inputs below 4q,
+// outputs below 4q.
+template <int NB, class TWA>
+__device__ __forceinline__ void ntt_fwd_radix(uint64_t (&r)[1 << NB], TWA tw, uint64_t q, int s0, int g) {
+    constexpr int E = 1 << NB;
+    const uint64_t two_q = 2 * q;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const int h = E >> (j + 1);
+        const int m = 1 << (s0 + j);
+        ulonglong2 wj[E / 2];
+#pragma unroll
+        for (int i = 0; i < (1 << j); ++i) wj[i] = tw.at(j, g, i, m, m + (g << j) + i);
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            if ((k & (2 * h - 1)) < h) {
+                const ulonglong2 w = wj[k >> (NB - j)];
+                uint64_t X = r[k];
+                X = X >= two_q ? X - two_q : X;
+                const uint64_t T = mul_shoup_lazy(r[k + h], w.x, w.y, q);
+                r[k] = X + T;
+                r[k + h] = X - T + two_q;
+            }
+        }
+    }
+}
+
 // A pass over sets [set0, set1) of stages s0..s0+NB-1; element x lives at s[SIDX(x - off)].
 // The whole transform in one CTA uses set0 = 0, set1 = N >> NB, off = 0; a cluster member
 // holding the slice [off, off + N/8) uses the sets whose elements fall in its slice.
@@ -114,27 +144,9 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, in
         uint64_t r[E];
 #pragma unroll
         for (int k = 0; k < E; ++k) r[k] = s[sb + SIDX(k << lg_tl)];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const int h = E >> (j + 1);
-            const int m = 1 << (s0 + j);
-            // element x = base + (k << lg_tl) meets twiddle m + (x >> (lg_t0 - j + 1)), which is
-            // m + (g << j) + (k >> (NB - j)): 2^j consecutive entries, loaded once per stage
-            ulonglong2 wj[E / 2];
-#pragma unroll
-            for (int i = 0; i < (1 << j); ++i) wj[i] = tw.at(j, g, i, m, m + (g << j) + i);
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                if ((k & (2 * h - 1)) < h) {
-                    const ulonglong2 w = wj[k >> (NB - j)];
-                    uint64_t X = r[k];
-                    X = X >= two_q ? X - two_q : X;
-                    const uint64_t T = mul_shoup_lazy(r[k + h], w.x, w.y, q);
-                    r[k] = X + T;
-                    r[k + h] = X - T + two_q;
-                }
-            }
-        }
+        // element x = base + (k << lg_tl) meets twiddle m + (x >> (lg_t0 - j + 1)) at stage
+        // s0 + j, which is m + (g << j) + (k >> (NB - j))
+        ntt_fwd_radix<NB>(r, tw, q, s0, g);
         if (last) {
 #pragma unroll
             for (int k = 0; k < E; ++k) {

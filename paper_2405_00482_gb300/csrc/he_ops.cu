@@ -658,6 +658,11 @@ __global__ void batch_mdr_ntt_cl_kernel(const MMJob *__restrict__ jobs, BatchGeo
 #define MM_THREADS 256
 
 __device__ __forceinline__ uint64_t fold(u128 t, uint64_t q, uint64_t qinv) { return redc128(t, q, qinv); }
+// t 2^-64 mod q for any t < 2^128: the high word is reduced mod q first (Barrett), so the
+// Montgomery step's input is below q 2^64
+__device__ __forceinline__ uint64_t fold_wide(u128 t, uint64_t q, uint64_t qinv, uint64_t mu) {
+    return redc(reduce_barrett((uint64_t)(t >> 64), q, mu), (uint64_t)t, q, qinv);
+}
 
 template <int VEC>
 __device__ __forceinline__ void ldv(const uint64_t *p, uint64_t (&o)[VEC]) {
@@ -706,27 +711,36 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
-// One tile: MM_THREADS / G lanes of VEC coefficients starting at coefficient k0 of extended
-// limb u.  Every thread of the block calls it (it synchronises once).  red: 3*VEC*MM_THREADS
-// words.  With S > 0 stages (fixed digit count only) each thread streams its key and plaintext
+// One block: `lanes` (<= MM_THREADS / G) lanes of VEC consecutive coefficients each, thread t
+// serving lane t % lanes in rotation group t / lanes; the calling thread's lane starts at
+// coefficient k of extended limb u (k >= N: no lane).  Every thread of the block calls it (it
+// synchronises once).  red: 3*VEC*MM_THREADS words.  With S > 0 stages (fixed digit count only) each thread streams its key and plaintext
 // operands through S private stages of pipe, so S rotation steps of HBM loads are in flight
 // without occupying registers.  With GA the digit and c0 gathers (L2 hits) go through the same
 // stages; without, they keep the one-step register prefetch.  keys / galois may point to shared
 // memory (the kernels stage the tables there), so no global round trip precedes a step's loads.
-template <int NDIG, int VEC, int G, int S, bool GA>
+//
+// With FK (fused keys, staged forms with a fixed digit count only) the key operands of step i are
+// the encoded matrix's fused tables F_i[d][c][u][k] = keyM_i[d][c][kl(u)][k] ptM_i[u][k] 2^-64
+// (fuse_keys_kernel) in place of the Galois key, so that
+//   acc_c[u][k] = redc(sum_i sum_d D[d][u][src_i(k)] F_i[d][c][u][k]),
+// the same residue as the two-level form: no per-step reduction and no second product.  The
+// 128-bit sums then take up to 64 products (< 64 q^2 < 2^128 for q < 2^61); their high word is
+// reduced mod q before the Montgomery step, whose input must stay below q 2^64.
+template <int NDIG, int VEC, int G, int S, bool GA, bool FK = false>
 __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
                                         const uint64_t *const *keys, const uint32_t *galois, int m_prime,
-                                        int ndig_rt, int ext, int nq, int L, int LK, int u, int p, int k0, uint64_t *acc, uint64_t *cacc,
-                                        int accumulate, const ModConst *__restrict__ mc, int logn, uint64_t *red, uint64_t *pipe) {
-    constexpr int LANES = MM_THREADS / G;
+                                        int ndig_rt, int ext, int nq, int L, int LK, int u, int k, int lanes, uint64_t *acc,
+                                        uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn, uint64_t *red,
+                                        uint64_t *pipe, const uint64_t *__restrict__ fused = nullptr) {
+    static_assert(!FK || (NDIG > 0 && S > 0), "fused key tables: staged forms with a fixed digit count");
     const int N = 1 << logn;
     const int ndig = NDIG > 0 ? NDIG : ndig_rt;
-    const int kl = u < nq ? u : L + (u - nq);
+    const int kl = u < nq ? u : L + (u - nq), p = kl;
     const uint64_t q = mc[p].q, qinv = mc[p].qinv;
     const bool inq = u < nq;
-    const int lane = threadIdx.x % LANES, grp = threadIdx.x / LANES;
-    const int k = k0 + VEC * lane;
-    auto R = [&](int g, int which, int j) -> uint64_t & { return red[((g * 3 + which) * VEC + j) * LANES + lane]; };
+    const int lane = threadIdx.x % lanes, grp = threadIdx.x / lanes;
+    auto R = [&](int g, int which, int j) -> uint64_t & { return red[((g * 3 + which) * VEC + j) * lanes + lane]; };
 
     uint64_t r0[VEC], r1[VEC], rc[VEC];
 #pragma unroll
@@ -751,14 +765,21 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
             auto issue = [&](int t) {
                 const int i = 1 + grp + t * G;
                 if (i < m_prime) {
-                    const uint64_t *key = keys[i - 1];
                     const int st = t % SP;
+                    if constexpr (FK) {
+                        const uint64_t *f = fused + ((int64_t)(i - 1) * 2 * ND * ext + u) * N + k;
 #pragma unroll
-                    for (int d = 0; d < ND; ++d) {
-                        cp_async<8 * VEC>(slot(st, 2 * d), key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k);
-                        cp_async<8 * VEC>(slot(st, 2 * d + 1), key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k);
+                        for (int d = 0; d < 2 * ND; ++d) cp_async<8 * VEC>(slot(st, d), f + (int64_t)d * ext * N);
+                        if (inq) cp_async<8 * VEC>(slot(st, 2 * ND), pts + ((int64_t)i * ext + u) * N + k);
+                    } else {
+                        const uint64_t *key = keys[i - 1];
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            cp_async<8 * VEC>(slot(st, 2 * d), key + ((int64_t)(d * 2 + 0) * LK + kl) * N + k);
+                            cp_async<8 * VEC>(slot(st, 2 * d + 1), key + ((int64_t)(d * 2 + 1) * LK + kl) * N + k);
+                        }
+                        cp_async<8 * VEC>(slot(st, 2 * ND), pts + ((int64_t)i * ext + u) * N + k);
                     }
-                    cp_async<8 * VEC>(slot(st, 2 * ND), pts + ((int64_t)i * ext + u) * N + k);
                     if constexpr (GA) {
                         const uint32_t src = automorph_src(k, galois[i - 1], logn);
                         const uint32_t sa = VEC == 2 ? (src & ~1u) : src;
@@ -805,6 +826,45 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                 cp_async_wait<SP - 1>();
                 const int st = t % SP;
                 if constexpr (GA) gather(t);
+                if constexpr (FK) {
+                    // t0, t1: sum over steps and digits of D F; tc: sum of c0 ptM
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        const uint64_t *a = slot(st, 2 * d), *b = slot(st, 2 * d + 1);
+#pragma unroll
+                        for (int j = 0; j < VEC; ++j) {
+                            t0[j] += (u128)dv[d][j] * a[j];
+                            t1[j] += (u128)dv[d][j] * b[j];
+                        }
+                    }
+                    uint64_t pmc[VEC], c0v[VEC];
+                    if (inq) {
+                        const uint64_t *pp = slot(st, 2 * ND);
+#pragma unroll
+                        for (int j = 0; j < VEC; ++j) {
+                            pmc[j] = pp[j];
+                            c0v[j] = cv[j];
+                        }
+                    }
+                    issue(t + SP);
+                    if constexpr (!GA) gather(t + 1);
+                    if (inq) {
+#pragma unroll
+                        for (int j = 0; j < VEC; ++j) tc[j] += (u128)c0v[j] * pmc[j];
+                    }
+                    if (++pending == 64 / ND) {
+                        const uint64_t mu = mc[p].mu;
+#pragma unroll
+                        for (int j = 0; j < VEC; ++j) {
+                            r0[j] = add_mod(r0[j], fold_wide(t0[j], q, qinv, mu), q);
+                            r1[j] = add_mod(r1[j], fold_wide(t1[j], q, qinv, mu), q);
+                            rc[j] = add_mod(rc[j], fold_wide(tc[j], q, qinv, mu), q);
+                            t0[j] = t1[j] = tc[j] = 0;
+                        }
+                        pending = 0;
+                    }
+                    continue;
+                }
                 u128 s0[VEC], s1[VEC];
 #pragma unroll
                 for (int j = 0; j < VEC; ++j) s0[j] = s1[j] = 0;
@@ -844,6 +904,16 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                 }
             }
             cp_async_wait<0>();
+            if constexpr (FK) {
+                const uint64_t mu = mc[p].mu;
+#pragma unroll
+                for (int j = 0; j < VEC; ++j) {
+                    r0[j] = add_mod(r0[j], fold_wide(t0[j], q, qinv, mu), q);
+                    r1[j] = add_mod(r1[j], fold_wide(t1[j], q, qinv, mu), q);
+                    rc[j] = add_mod(rc[j], fold_wide(tc[j], q, qinv, mu), q);
+                    t0[j] = t1[j] = tc[j] = 0;
+                }
+            }
         } else {
             uint64_t dv[ND][VEC], kv0[ND][VEC], kv1[ND][VEC], pm[VEC], cv[VEC];
             auto fetch = [&](int i) {
@@ -994,23 +1064,59 @@ __device__ __forceinline__ void stage_tables(MMTables &tb, const uint64_t *const
     }
 }
 
-// single MatMult: block (coefficient tile, extended limb)
-template <int NDIG, int VEC, int G, int S, bool GA>
+// single MatMult: the ext * N / VEC lanes of the extended limbs, in limb-major order, are cut
+// into runs of blockDim.x / G lanes, one per block, whose size the launcher picks so that the
+// blocks spread evenly over the multiprocessors (a run may cross a limb boundary); with FK,
+// fused = the plaintext block's fused key tables [m'-1][NDIG][2][ext][N]
+template <int NDIG, int VEC, int G, int S, bool GA, bool FK = false>
 __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_loop_kernel(
     const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
     const uint64_t *const *__restrict__ keys, const uint32_t *__restrict__ galois, int m_prime, int ndig_rt, int ext, int nq, int L,
-    int LK, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn) {
+    int LK, uint64_t *acc, uint64_t *cacc, int accumulate, const ModConst *__restrict__ mc, int logn, const uint64_t *__restrict__ fused) {
     HE_GRID_DEP();
     __shared__ uint64_t red[G * 3 * VEC * (MM_THREADS / G)];
     __shared__ MMTables tb;
     extern __shared__ uint4 mm_pipe[];
-    const int u = blockIdx.y;
     const uint64_t *const *k_use;
     const uint32_t *g_use;
     stage_tables(tb, keys, galois, m_prime, k_use, g_use);
-    mm_tile<NDIG, VEC, G, S, GA>(ct, D, pts, k_use, g_use, m_prime, ndig_rt, ext, nq, L, LK, u, u < nq ? u : L + (u - nq),
-                                 blockIdx.x * (MM_THREADS / G) * VEC, acc, cacc, accumulate, mc, logn, red,
-                                 reinterpret_cast<uint64_t *>(mm_pipe));
+    const int lanes = (int)blockDim.x / G, per_limb = (1 << logn) / VEC;
+    const int flat = (int)blockIdx.x * lanes + (int)threadIdx.x % lanes;
+    int u = flat / per_limb, k = (flat % per_limb) * VEC;
+    if (u >= ext) {  // past the last limb: no lane
+        u = 0;
+        k = 1 << logn;
+    }
+    mm_tile<NDIG, VEC, G, S, GA, FK>(ct, D, pts, k_use, g_use, m_prime, ndig_rt, ext, nq, L, LK, u, k, lanes, acc, cacc, accumulate, mc, logn,
+                                     red, reinterpret_cast<uint64_t *>(mm_pipe), fused);
+}
+
+// Fused key tables of an encoded matrix (see mm_tile): one thread per (plaintext block, step
+// i >= 1, extended limb u, coefficient pair),
+//   F[b][i-1][d][c][u][k] = keyM_i[d][c][kl(u)][k] ptM_{b,i}[u][k] 2^-64 mod q_u,
+// i.e. the Montgomery form of key_i pt_{b,i}.
+__global__ void __launch_bounds__(256) fuse_keys_kernel(const uint64_t *__restrict__ pts, const uint64_t *const *__restrict__ keys,
+                                                       uint64_t *__restrict__ fused, int64_t total, int m_prime, int ndig, int ext, int nq,
+                                                       int L, int LK, const ModConst *__restrict__ mc, int logn) {
+    HE_GRID_DEP();
+    const int64_t N = (int64_t)1 << logn, half = N / 2;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = 2 * (idx % half);
+        int64_t rest = idx / half;
+        const int u = (int)(rest % ext);
+        rest /= ext;
+        const int i = (int)(rest % (m_prime - 1)) + 1;
+        const int64_t b = rest / (m_prime - 1);
+        const int kl = u < nq ? u : L + (u - nq);
+        const uint64_t q = mc[kl].q, qinv = mc[kl].qinv;
+        const ulonglong2 pt = __ldg(reinterpret_cast<const ulonglong2 *>(pts + ((b * m_prime + i) * ext + u) * N + k));
+        const uint64_t *key = keys[i - 1] + (int64_t)kl * N + k;
+        uint64_t *f = fused + ((b * (m_prime - 1) + (i - 1)) * 2 * ndig * ext + u) * N + k;
+        for (int dc = 0; dc < 2 * ndig; ++dc) {
+            const ulonglong2 kv = __ldg(reinterpret_cast<const ulonglong2 *>(key + (int64_t)dc * LK * N));
+            *reinterpret_cast<ulonglong2 *>(f + (int64_t)dc * ext * N) = make_ulonglong2(mont_mul(kv.x, pt.x, q, qinv), mont_mul(kv.y, pt.y, q, qinv));
+        }
+    }
 }
 
 // batch: persistent CTAs pull (tile, limb, job) items from an ordered queue
@@ -1040,8 +1146,9 @@ __global__ void __launch_bounds__(MM_THREADS, VEC == 2 ? 2 : 3) matmult_batch_lo
         const uint64_t *const *k_use;
         const uint32_t *g_use;
         stage_tables(tb, jb.keys, jb.galois, jb.m_prime, k_use, g_use);
+        constexpr int LANES = MM_THREADS / G;
         mm_tile<NDIG, VEC, G, S, GA>(jb.ct, bg.D + (int64_t)j * bg.d_words, jb.pts, k_use, g_use, jb.m_prime, bg.ndig, bg.ext, bg.nq, bg.L,
-                                     bg.LK, u, u < bg.nq ? u : bg.L + (u - bg.nq), tile * TILE, bg.acc + (int64_t)j * bg.acc_words,
+                                     bg.LK, u, tile * TILE + VEC * ((int)threadIdx.x % LANES), LANES, bg.acc + (int64_t)j * bg.acc_words,
                                      bg.cacc + (int64_t)j * bg.cacc_words, 0, mc, logn, red, reinterpret_cast<uint64_t *>(mm_pipe));
         __syncthreads();
     }
@@ -1083,6 +1190,24 @@ void mm_dispatch_nd(int ndig, F &&f) {
         default: f.template operator()<0, VEC, G, 0, false>(); break;
     }
 }
+// the fused-key forms: staged variants (4-7) with 1-3 digits
+template <int VEC, int G, int S, bool GA, typename F>
+void mm_dispatch_fk_nd(int ndig, F &&f) {
+    switch (ndig) {
+        case 1: f.template operator()<1, VEC, G, S, GA>(); break;
+        case 2: f.template operator()<2, VEC, G, S, GA>(); break;
+        default: f.template operator()<3, VEC, G, S, GA>(); break;
+    }
+}
+template <typename F>
+void mm_dispatch_fk(int v, int ndig, F &&f) {
+    switch (v) {
+        case 5: mm_dispatch_fk_nd<2, 4, 2, true>(ndig, f); break;
+        case 6: mm_dispatch_fk_nd<1, 4, 2, true>(ndig, f); break;
+        case 7: mm_dispatch_fk_nd<1, 8, 2, true>(ndig, f); break;
+        default: mm_dispatch_fk_nd<2, 4, 3, false>(ndig, f); break;
+    }
+}
 template <typename F>
 void mm_dispatch(int v, int ndig, F &&f) {
     switch (v) {
@@ -1099,13 +1224,57 @@ void mm_dispatch(int v, int ndig, F &&f) {
 
 }  // namespace
 
+// Lanes per block of the single-MatMult loop kernel: the multiple of 32 / G (whole warps) up to
+// MM_THREADS / G that minimises lanes x ceil(blocks / SMs), the lanes the busiest
+// multiprocessor serves (ties: the larger run).  For ext = 4, N = 8192, VEC = 2 on 152 SMs this
+// is 56 (293 blocks, at most 2 per SM) instead of 64 (256 blocks: 104 SMs with 2, 48 with 1).
+int mm_block_lanes(int v, int64_t total_lanes, int sms) {
+    const int g = kMMShapes[v].grp, lmax = MM_THREADS / g, step = 32 / g;
+    int best = lmax;
+    int64_t best_cost = -1;
+    for (int l = lmax; l >= step; l -= step) {
+        const int64_t blocks = (total_lanes + l - 1) / l;
+        const int64_t cost = (int64_t)l * ((blocks + sms - 1) / sms);
+        if (best_cost < 0 || cost < best_cost) {
+            best = l;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 void mm_launch_variant(he_ctx *ctx, int v, const uint64_t *ct, const uint64_t *D, const uint64_t *pts, const uint64_t *const *keys,
-                       const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate) {
-    const dim3 grid((unsigned)((ctx->n + mm_variant_tile(v) - 1) / mm_variant_tile(v)), (unsigned)ext);
+                       const uint32_t *galois, int m_prime, int ndig, int ext, int nq, uint64_t *acc, uint64_t *cacc, int accumulate,
+                       const uint64_t *fused) {
+    const int64_t total = (int64_t)ext * (ctx->n / kMMShapes[v].vec);
+    const int lanes = mm_block_lanes(v, total, ctx->sms);
+    const unsigned grid = (unsigned)((total + lanes - 1) / lanes), threads = (unsigned)(lanes * kMMShapes[v].grp);
     ctx->launches++;
+    if (fused && mm_variant_fusable(v, ndig)) {
+        mm_dispatch_fk(v, ndig, [&]<int NDIG, int VEC, int G, int S, bool GA>() {
+            launch_k(matmult_loop_kernel<NDIG, VEC, G, S, GA, true>, grid, threads, mm_pipe_bytes(NDIG, VEC, S, GA), ctx->stream, ct, D, pts, keys,
+                     galois, m_prime, ndig, ext, nq, ctx->L, ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n, fused);
+        });
+        return;
+    }
     mm_dispatch(v, ndig, [&]<int NDIG, int VEC, int G, int S, bool GA>() {
-        launch_k(matmult_loop_kernel<NDIG, VEC, G, S, GA>, grid, MM_THREADS, mm_pipe_bytes(NDIG, VEC, S, GA), ctx->stream, ct, D, pts, keys, galois, m_prime, ndig, ext, nq, ctx->L, ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n);
+        launch_k(matmult_loop_kernel<NDIG, VEC, G, S, GA>, grid, threads, mm_pipe_bytes(NDIG, VEC, S, GA), ctx->stream, ct, D, pts, keys, galois,
+                 m_prime, ndig, ext, nq, ctx->L, ctx->L + ctx->K, acc, cacc, accumulate, ctx->d_mc, ctx->log_n, (const uint64_t *)nullptr);
     });
+}
+
+bool mm_variant_fusable(int v, int ndig) { return ndig >= 1 && ndig <= 3 && kMMShapes[v].stages > 0; }
+
+void launch_fuse_keys(he_ctx *ctx, he_ptmat *pm) {
+    const he_plan &p = pm->plan;
+    const int ndig = ctx->modup[pm->level].ndig, nq = pm->level + 1;
+    const int64_t total = (int64_t)p.row_blocks * p.col_blocks * (p.m_prime - 1) * pm->ext * (ctx->n / 2);
+    if (total <= 0) return;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    ctx->launches++;
+    launch_k(fuse_keys_kernel, (unsigned)blocks, 256, 0, ctx->stream, (const uint64_t *)pm->data, (const uint64_t *const *)pm->d_keys, pm->fused,
+             total, (int)p.m_prime, ndig, pm->ext, nq, ctx->L, ctx->L + ctx->K, (const ModConst *)ctx->d_mc, ctx->log_n);
 }
 
 void mm_launch_batch_variant(int v, dim3 grid, cudaStream_t st, const MMJob *jobs, const int32_t *order, int n_items, unsigned int *counter,
@@ -1346,17 +1515,59 @@ void launch_matmult_loop(he_ctx *ctx, const he_ptmat *pm, int r, int c, const ui
     const ModUpConst &mu = ctx->modup[level];
     const he_plan &p = pm->plan;
     const uint64_t *pts = pm->data + (((int64_t)r * p.col_blocks + c) * p.m_prime) * pm->ext * ctx->n;
+    const bool fk = pm->fuse_state == 1 && pm->fused && pm->fused_gen == pm->enc_gen && pm->fvariant >= 0;
+    const uint64_t *fused = fk ? pm->fused + ((int64_t)r * p.col_blocks + c) * (p.m_prime - 1) * 2 * mu.ndig * pm->ext * ctx->n : nullptr;
     cudaEvent_t *ev = prof_pair(ctx, HE_PROF_LOOP);
     if (ev) cudaEventRecord(ev[0], ctx->stream);
-    mm_launch_variant(ctx, pm->variant < 0 ? 0 : pm->variant, ct, D, pts, pm->d_keys, pm->d_galois, (int)p.m_prime, mu.ndig, mu.ext,
-                      level + 1, acc, cacc, accumulate);
+    mm_launch_variant(ctx, fk ? pm->fvariant : (pm->variant < 0 ? 0 : pm->variant), ct, D, pts, pm->d_keys, pm->d_galois, (int)p.m_prime,
+                      mu.ndig, mu.ext, level + 1, acc, cacc, accumulate, fused);
     if (ev) cudaEventRecord(ev[1], ctx->stream);
+}
+
+// best of three timed launches (after one untimed) of variant v on block (0, 0); 1e30 on error
+static float time_loop_variant(he_ctx *ctx, he_ptmat *pm, int v, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc,
+                               const uint64_t *fused, cudaEvent_t a, cudaEvent_t b) {
+    const ModUpConst &mu = ctx->modup[pm->level];
+    float ms = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a, ctx->stream);
+        mm_launch_variant(ctx, v, ct, D, pm->data, pm->d_keys, pm->d_galois, (int)pm->plan.m_prime, mu.ndig, mu.ext, pm->level + 1, acc, cacc, 0,
+                          fused);
+        cudaEventRecord(b, ctx->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) break;
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, a, b);
+        if (rep > 0 && t < ms) ms = t;
+    }
+    return ms;
+}
+
+// Time the fused-key forms of the staged variants on this matrix (its tables built) and keep the
+// fastest in pm->fvariant; the caller compares it with the two-level form.  Synchronises.
+int tune_matmult_fused(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc) {
+    const int ndig = ctx->modup[pm->level].ndig;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return HE_ECUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return HE_ECUDA;
+    }
+    int best = -1;
+    for (int v = 0; v < mm_variant_count(); ++v) {
+        pm->fuse_ms[v] = 0.0f;
+        if (!mm_variant_fusable(v, ndig)) continue;
+        pm->fuse_ms[v] = time_loop_variant(ctx, pm, v, ct, D, acc, cacc, pm->fused, a, b);
+        if (best < 0 || pm->fuse_ms[v] < pm->fuse_ms[best]) best = v;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    pm->fvariant = best;
+    return cudaGetLastError() == cudaSuccess ? HE_OK : HE_ECUDA;
 }
 
 // Time every loop-kernel variant once on this matrix's first product (the results are identical:
 // modular sums do not depend on the order) and keep the fastest.  Synchronises the stream.
 int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint64_t *D, uint64_t *acc, uint64_t *cacc) {
-    const ModUpConst &mu = ctx->modup[pm->level];
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return HE_ECUDA;
     if (cudaEventCreate(&b) != cudaSuccess) {
@@ -1367,17 +1578,7 @@ int tune_matmult_loop(he_ctx *ctx, he_ptmat *pm, const uint64_t *ct, const uint6
     float best_ms = 1e30f;
     for (int v = 0; v < mm_variant_count(); ++v) {
         // one untimed launch (it also loads the variant's code), then the best of three
-        float ms = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {
-            cudaEventRecord(a, ctx->stream);
-            mm_launch_variant(ctx, v, ct, D, pm->data, pm->d_keys, pm->d_galois, (int)pm->plan.m_prime, mu.ndig, mu.ext, pm->level + 1, acc, cacc,
-                              0);
-            cudaEventRecord(b, ctx->stream);
-            if (cudaEventSynchronize(b) != cudaSuccess) break;
-            float t = 0.0f;
-            cudaEventElapsedTime(&t, a, b);
-            if (rep > 0 && t < ms) ms = t;
-        }
+        const float ms = time_loop_variant(ctx, pm, v, ct, D, acc, cacc, nullptr, a, b);
         pm->tune_ms[v] = ms;
         if (ms < best_ms) {
             best_ms = ms;
@@ -1399,7 +1600,7 @@ void launch_matmult_loop_with_tables(he_ctx *ctx, const he_ptmat *pm, int r, int
     const he_plan &p = pm->plan;
     const uint64_t *pts = pm->data + (((int64_t)r * p.col_blocks + c) * p.m_prime) * pm->ext * ctx->n;
     mm_launch_variant(ctx, pm->variant < 0 ? 0 : pm->variant, ct, D, pts, keys, galois, (int)p.m_prime, mu.ndig, mu.ext, level + 1, acc, cacc,
-                      accumulate);
+                      accumulate, nullptr);
 }
 
 void launch_layout_matrix(he_ctx *ctx, const he_plan &p, const double *X, double *slots, int trans) {
@@ -1560,4 +1761,13 @@ void ops_set_smem_limits(int max_bytes) {
                 cudaFuncSetAttribute(matmult_batch_loop_kernel<NDIG, VEC, G, S, GA>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      (int)cudaSharedmemCarveoutMaxShared);
             });
+    for (int v = 0; v < kMMVariants; ++v)
+        for (int nd = 1; nd <= 3; ++nd)
+            if (mm_variant_fusable(v, nd))
+                mm_dispatch_fk(v, nd, []<int NDIG, int VEC, int G, int S, bool GA>() {
+                    const int bytes = (int)mm_pipe_bytes(NDIG, VEC, S, GA);
+                    cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S, GA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                    cudaFuncSetAttribute(matmult_loop_kernel<NDIG, VEC, G, S, GA, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared);
+                });
 }

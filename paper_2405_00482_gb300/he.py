@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhe.so")
 
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_EKEY, HE_ELEVEL, HE_ESCALE, HE_ETIMEOUT, HE_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7, -8
 HE_BCONV_INT64, HE_BCONV_INT8_TC = 0, 1  # basis extension engines of ModUp
+HE_NTT_FORMS = 3  # NTT forms of launches of many limb-polys
 HE_PROF_LOOP, HE_PROF_MATRIX_NTT, HE_PROF_KS_TRANSFORM, HE_PROF_KS_ELEMENTWISE = 0, 1, 2, 3  # profiled kernel classes
 
 
@@ -98,6 +99,9 @@ _SIGS = {
     "he_batch_stage_form": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "he_batch_set_stage_form": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_ptmat_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "he_set_key_fusion": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_size_t]),
+    "he_ptmat_key_fusion": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "he_ptmat_set_key_fusion": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "he_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_loop_variant_shape": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -272,6 +276,19 @@ class PtMatrix:
     def set_variant(self, v: int) -> None:
         """Pin the loop-kernel variant (-1: tune again on the next MatMult)."""
         _check(_lib().he_ptmat_set_variant(self.handle, v), "he_ptmat_set_variant")
+
+    def key_fusion(self) -> dict:
+        """Fused key tables (he_ptmat_key_fusion): state 0 not tried, 1 in use, -1 not used; the
+        fused form's variant and its timed ms per variant."""
+        st, v = ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * HE_MM_MAX_VARIANTS)()
+        _check(_lib().he_ptmat_key_fusion(self.handle, ctypes.byref(st), ctypes.byref(v), ms), "he_ptmat_key_fusion")
+        n = _lib().he_loop_variant_count()
+        return {"state": int(st.value), "variant": int(v.value), "variant_ms": [round(float(x), 4) for x in ms[:n]]}
+
+    def set_key_fusion(self, on: bool, variant: int = -1) -> None:
+        """he_ptmat_set_key_fusion: off (tables freed), eligible again, or pinned to a variant."""
+        _check(_lib().he_ptmat_set_key_fusion(self.handle, int(on), variant), "he_ptmat_set_key_fusion")
 
     def export(self) -> torch.Tensor:
         """Plaintexts [R][C][m'][level+1+K][N] in canonical coefficient form (int64 storage)."""
@@ -842,15 +859,21 @@ class Context:
                 "variants": ["one CTA per limb-poly, usual threads", "one CTA per limb-poly, 512 threads, <= 64 registers"]}
 
     def ntt_form(self) -> dict:
-        """NTT form of launches of many limb-polys (he_ntt_form): 0 one CTA, 1 a 2-CTA cluster per limb-poly."""
+        """NTT form of launches of many limb-polys (he_ntt_form): 0 one CTA, 1 a 2-CTA cluster per
+        limb-poly, 2 two phases (columns, then rows)."""
         f = ctypes.c_int()
-        ms = (ctypes.c_float * 2)()
+        ms = (ctypes.c_float * HE_NTT_FORMS)()
         _check(_lib().he_ntt_form(self.handle, ctypes.byref(f), ms), "he_ntt_form")
         return {"form": int(f.value), "form_ms": [round(float(x), 4) for x in ms],
-                "forms": ["one CTA per limb-poly", "2-CTA cluster per limb-poly"]}
+                "forms": ["one CTA per limb-poly", "2-CTA cluster per limb-poly", "two phases: 64-point columns, then rows"]}
 
     def set_ntt_form(self, form: int) -> None:
         _check(_lib().he_set_ntt_form(self.handle, form), "he_set_ntt_form")
+
+    def set_key_fusion(self, mode: int, max_bytes: int = 0) -> None:
+        """Fused key tables for the context family's encoded matrices (he_set_key_fusion):
+        0 never, 1 when an encoding is multiplied again (default), 2 at the first MatMult."""
+        _check(_lib().he_set_key_fusion(self.handle, mode, max_bytes), "he_set_key_fusion")
 
     # ---- basis extension engine of ModUp ----
     def set_basis_extension(self, engine: int) -> None:
