@@ -161,13 +161,25 @@ __global__ void PAIR_BOUNDS(LOGN) ntt_from_int64_pair_kernel(const int64_t *__re
 // as the other forms do: canonical residues, times 2^64 mod q when to_mont.  The butterflies
 // and their stage order are those of the other forms, so the values are the same; the work
 // spreads over the SMs in blocks of 1/(C/NTT2_TC) (columns) or 1/4 (rows) of a limb-poly.
+// Two changes of operation order that leave every output the same residue: the factor 2^64 mod q
+// of to_mont multiplies the inputs (one Shoup product, which for int64 inputs also does the
+// reduction mod q) instead of the outputs, the transform being linear; and for primes below 2^59
+// the butterflies skip the lazy correction (ntt_fwd_radix), the row phase reducing at the end.
 #define NTT2_TC 16
 #define NTT2_TR 16
 #define NTT2_THREADS 128
 
+// canonical residue of v 2^64 mod q for a signed v (Shoup product by 2^64 mod q of |v|)
+__device__ __forceinline__ uint64_t signed_to_mont(int64_t v, uint64_t r1, uint64_t r1s, uint64_t q) {
+    const uint64_t a = v >= 0 ? (uint64_t)v : 0ull - (uint64_t)v;
+    const uint64_t r = mul_shoup(a, r1, r1s, q);
+    return (v < 0 && r != 0) ? q - r : r;
+}
+
 template <int LOGN, bool I64>
-__global__ void __launch_bounds__(NTT2_THREADS) ntt2_cols_kernel(const void *__restrict__ in_v, int64_t in_gs, uint64_t *out, int64_t out_gs,
-                                                               LimbMap map, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc) {
+__global__ void __launch_bounds__(NTT2_THREADS, 8) ntt2_cols_kernel(const void *__restrict__ in_v, int64_t in_gs, uint64_t *out, int64_t out_gs,
+                                                               LimbMap map, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+                                                               int to_mont) {
     HE_GRID_DEP();
     constexpr int N = 1 << LOGN, C = N >> 6, TILES = C / NTT2_TC, PAD = NTT2_TC + 1;
     static_assert(NTT2_THREADS == 8 * NTT2_TC, "one thread per (column, set of 8)");
@@ -177,6 +189,8 @@ __global__ void __launch_bounds__(NTT2_THREADS) ntt2_cols_kernel(const void *__r
     const uint64_t q = mc[p].q;
     const TwGlobal tw{twiddles(d_tw, p, 0, LOGN)};
     const int c = threadIdx.x % NTT2_TC, r = threadIdx.x / NTT2_TC;
+    const uint64_t r1 = mc[p].r1, r1s = mc[p].r1_shoup;
+    const bool corr = q >= HE_NTT_NOCORR_Q;
     uint64_t v[8];
     // stages 0-2 on the column's elements l = r + 8 i (one group at stage 0)
     if constexpr (I64) {  // int64 coefficients, shared by the limbs of group g, reduced mod q
@@ -186,20 +200,26 @@ __global__ void __launch_bounds__(NTT2_THREADS) ntt2_cols_kernel(const void *__r
 #pragma unroll
         for (int i = 0; i < 8; ++i) t[i] = src[(int64_t)(r + 8 * i) * C];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = reduce_signed(t[i], q, mu);
+        for (int i = 0; i < 8; ++i) v[i] = to_mont ? signed_to_mont(t[i], r1, r1s, q) : reduce_signed(t[i], q, mu);
     } else {
         const uint64_t *src = static_cast<const uint64_t *>(in_v) + g * in_gs + (int64_t)l * N + c0 + c;
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = src[(int64_t)(r + 8 * i) * C];
+        if (to_mont) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = mul_shoup(v[i], r1, r1s, q);
+        }
     }
-    ntt_fwd_radix<3>(v, tw, q, 0, 0);
+    if (corr) ntt_fwd_radix<3, TwGlobal, true>(v, tw, q, 0, 0);
+    else ntt_fwd_radix<3, TwGlobal, false>(v, tw, q, 0, 0);
 #pragma unroll
     for (int i = 0; i < 8; ++i) sm[(r + 8 * i) * PAD + c] = v[i];
     __syncthreads();
     // stages 3-5 on l = 8 r + i: group r at stage 3
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = sm[(8 * r + i) * PAD + c];
-    ntt_fwd_radix<3>(v, tw, q, 3, r);
+    if (corr) ntt_fwd_radix<3, TwGlobal, true>(v, tw, q, 3, r);
+    else ntt_fwd_radix<3, TwGlobal, false>(v, tw, q, 3, r);
     uint64_t *dst = out + g * out_gs + (int64_t)l * N + c0 + c;
 #pragma unroll
     for (int i = 0; i < 8; ++i) dst[(int64_t)(8 * r + i) * C] = v[i];
@@ -211,7 +231,7 @@ __host__ __device__ constexpr int ntt2_row_pitch(int lb) { return ((1 << lb) + (
 
 template <int LOGN, int NB1>
 __global__ void __launch_bounds__(NTT2_THREADS) ntt2_rows_kernel(uint64_t *data, int64_t gs, LimbMap map, const uint64_t *__restrict__ d_tw,
-                                                               const ModConst *__restrict__ mc, int to_mont) {
+                                                               const ModConst *__restrict__ mc) {
     HE_GRID_DEP();
     constexpr int N = 1 << LOGN, LB = LOGN - 6, R = 1 << LB, NB2 = LB - NB1, TILES = 64 / NTT2_TR, RP = ntt2_row_pitch(LB);
     constexpr int S1 = R >> NB1, S2 = R >> NB2;  // sets per row of the two passes
@@ -222,31 +242,37 @@ __global__ void __launch_bounds__(NTT2_THREADS) ntt2_rows_kernel(uint64_t *data,
     const TwGlobal tw{twiddles(d_tw, p, 0, LOGN)};
     uint64_t *row0 = data + g * gs + (int64_t)l * N + (int64_t)b0 * R;
     auto at = [](int m) { return m + (m >> 3); };
+    const bool corr = q >= HE_NTT_NOCORR_Q;
     // stages 6 .. 5 + NB1 on the elements m = j + S1 i of row b (group b at stage 6)
     for (int set = threadIdx.x; set < NTT2_TR * S1; set += NTT2_THREADS) {
         const int rb = set / S1, j = set % S1;
         uint64_t v[1 << NB1];
 #pragma unroll
         for (int i = 0; i < (1 << NB1); ++i) v[i] = row0[(int64_t)rb * R + j + S1 * i];
-        ntt_fwd_radix<NB1>(v, tw, q, 6, b0 + rb);
+        if (corr) ntt_fwd_radix<NB1, TwGlobal, true>(v, tw, q, 6, b0 + rb);
+        else ntt_fwd_radix<NB1, TwGlobal, false>(v, tw, q, 6, b0 + rb);
 #pragma unroll
         for (int i = 0; i < (1 << NB1); ++i) sm[rb * RP + at(j + S1 * i)] = v[i];
     }
     __syncthreads();
     // the last NB2 stages on 2^NB2 consecutive elements m = 2^NB2 e + i: group b 2^NB1 + e
-    const uint64_t two_q = 2 * q, r1 = mc[p].r1, r1s = mc[p].r1_shoup;
+    const uint64_t two_q = 2 * q, mu = mc[p].mu;
     for (int set = threadIdx.x; set < NTT2_TR * S2; set += NTT2_THREADS) {
         const int rb = set / S2, e = set % S2;
         uint64_t v[1 << NB2];
 #pragma unroll
         for (int i = 0; i < (1 << NB2); ++i) v[i] = sm[rb * RP + at((e << NB2) + i)];
-        ntt_fwd_radix<NB2>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
+        if (corr) {  // values below 4q
+            ntt_fwd_radix<NB2, TwGlobal, true>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
 #pragma unroll
-        for (int i = 0; i < (1 << NB2); ++i) {
-            uint64_t x = v[i];
-            x = x >= two_q ? x - two_q : x;
-            x = x >= q ? x - q : x;
-            v[i] = to_mont ? mul_shoup(x, r1, r1s, q) : x;
+            for (int i = 0; i < (1 << NB2); ++i) {
+                const uint64_t x = v[i] >= two_q ? v[i] - two_q : v[i];
+                v[i] = x >= q ? x - q : x;
+            }
+        } else {  // values below (1 + 2 log N) q
+            ntt_fwd_radix<NB2, TwGlobal, false>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
+#pragma unroll
+            for (int i = 0; i < (1 << NB2); ++i) v[i] = reduce_barrett(v[i], q, mu);
         }
         ulonglong2 *d = reinterpret_cast<ulonglong2 *>(row0 + (int64_t)rb * R + (e << NB2));
 #pragma unroll
@@ -321,8 +347,8 @@ static void launch_two_phase(he_ctx *ctx, const void *in, int64_t in_gs, uint64_
     const ModConst *mc = ctx->d_mc;
     ctx->launches += 2;
     auto go = [&](auto L, auto NB1) {
-        launch_k(ntt2_cols_kernel<decltype(L)::value, I64>, cols, NTT2_THREADS, 0, ctx->stream, in, in_gs, out, out_gs, map, tw, mc);
-        launch_k(ntt2_rows_kernel<decltype(L)::value, decltype(NB1)::value>, rows, NTT2_THREADS, 0, ctx->stream, out, out_gs, map, tw, mc, to_mont);
+        launch_k(ntt2_cols_kernel<decltype(L)::value, I64>, cols, NTT2_THREADS, 0, ctx->stream, in, in_gs, out, out_gs, map, tw, mc, to_mont);
+        launch_k(ntt2_rows_kernel<decltype(L)::value, decltype(NB1)::value>, rows, NTT2_THREADS, 0, ctx->stream, out, out_gs, map, tw, mc);
     };
     if (logn == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
     else if (logn == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 4>{});

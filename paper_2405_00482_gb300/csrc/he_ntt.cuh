@@ -96,8 +96,10 @@ struct TwFirstInv {
 // element base + (k << lg_tl) of a set whose stage-s0 group is g (g = base >> (log N - s0)):
 // at stage s0 + j element k meets twiddle entry m + (g << j) + (k >> (NB - j)), m = 2^(s0+j),
 // the 2^j consecutive entries loaded once per stage.  Harvey's lazy butterfly: inputs below 4q,
-// outputs below 4q.
-template <int NB, class TWA>
+// outputs below 4q.  Without CORR the top input is not brought below 2q first: each stage then
+// adds less than 2q to the bound, so canonical inputs stay below (1 + 2 log N) q, which fits in
+// 64 bits for q < 2^59 and log N <= 14 (the caller reduces at the end).
+template <int NB, class TWA, bool CORR = true>
 __device__ __forceinline__ void ntt_fwd_radix(uint64_t (&r)[1 << NB], TWA tw, uint64_t q, int s0, int g) {
     constexpr int E = 1 << NB;
     const uint64_t two_q = 2 * q;
@@ -113,7 +115,7 @@ __device__ __forceinline__ void ntt_fwd_radix(uint64_t (&r)[1 << NB], TWA tw, ui
             if ((k & (2 * h - 1)) < h) {
                 const ulonglong2 w = wj[k >> (NB - j)];
                 uint64_t X = r[k];
-                X = X >= two_q ? X - two_q : X;
+                if constexpr (CORR) X = X >= two_q ? X - two_q : X;
                 const uint64_t T = mul_shoup_lazy(r[k + h], w.x, w.y, q);
                 r[k] = X + T;
                 r[k + h] = X - T + two_q;
@@ -121,6 +123,8 @@ __device__ __forceinline__ void ntt_fwd_radix(uint64_t (&r)[1 << NB], TWA tw, ui
         }
     }
 }
+// primes for which the forward transform may skip the lazy correction (see ntt_fwd_radix)
+#define HE_NTT_NOCORR_Q (1ull << 59)
 
 // A pass over sets [set0, set1) of stages s0..s0+NB-1; element x lives at s[SIDX(x - off)].
 // The whole transform in one CTA uses set0 = 0, set1 = N >> NB, off = 0; a cluster member
