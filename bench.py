@@ -297,7 +297,8 @@ def run_gpu(args):
     ntt_bytes = 8 * P.n * n_pt * (1 + limbs)  # int64 coefficients read once per plaintext, residues written per limb
     ntt_bfly = n_pt * limbs * (P.n // 2) * (P.n.bit_length() - 1)
     bf_peak = 152 * 128 * 2.07e9 / BUTTERFLY_INSTR
-    ntt_roof = {"kernel": "ntt_from_int64_kernel (encoded matrix: 64 plaintexts x 4 limbs, N=8192, one CTA per limb-poly)",
+    ntt_roof = {"kernel": "the encoded matrix's NTT (64 plaintexts x 4 limbs, N=8192) in the context's NTT form (see form): "
+                          "ntt_from_int64_kernel (form 0), its pair form (1), or ntt2_cols_kernel + ntt2_rows_kernel (2)",
                 "launch_ms": round(1e3 * ntt_s, 5), "launches_timed": ntt_n,
                 "hbm": {"achieved": round(ntt_bytes / ntt_s / 1e9, 1), "peak": _peaks()["hbm_gbs"], "unit": "GB/s",
                         "frac": round(ntt_bytes / ntt_s / 1e9 / _peaks()["hbm_gbs"], 4), "alg_bytes_per_launch": ntt_bytes},
@@ -503,7 +504,8 @@ def run_rotations(ctx, he, P, args, flush, world, dev):
                                       "frac": round(el_bytes / el_s / 1e9 / peaks["hbm_gbs"], 4), "alg_bytes_per_call": el_bytes,
                                       "ms_per_call": round(1e3 * el_s, 4), "launches_timed": n_el,
                                       "counted": "8N k (2 ndig ext + 2 (l+1)): the k Galois keys read and the k rotated ciphertexts written"},
-            "keyswitch_transform": {"kernels": "ks_pintt_kernel + ks_conv_kernel (transform only)", "bound": "alu",
+            "keyswitch_transform": {"kernels": "the key switch's transforms only, in the tuned variant (keyswitch_tuning): ks_pintt_kernel + "
+                                               "ks_conv_kernel (variants 0, 1) or ks2_pinv_rows/cols + ks2_conv_cols/rows (2)", "bound": "alu",
                                     "achieved": round(butterflies / tr_s / 1e12, 4), "peak": round(bf_peak / 1e12, 4), "unit": "T butterflies/s",
                                     "frac": round(butterflies / tr_s / bf_peak, 4), "butterflies_per_call": butterflies,
                                     "ms_per_call": round(1e3 * tr_s, 4),

@@ -249,11 +249,17 @@ int he_matmult_plain_cipher_noalloc(he_ctx *ctx, const he_plan *plan, const he_p
                                     int n_out);
 
 /* The key switch of many rotations (he_rotate_hoisted, he_rotate_many with at least 32 of them)
- * runs its transforms as one CTA per limb-poly with the usual thread count (variant 0) or with
- * 512 threads and at most 64 registers (variant 1).  The first such call on a context times both
- * on its first chunk (synchronising the stream; not under stream capture) and keeps the faster:
- * variant (-1 before) and ms[0..1] (may be NULL) report the choice and the timings. */
+ * runs its transforms as one CTA per limb-poly with the usual thread count (variant 0), with
+ * 512 threads and at most 64 registers (variant 1), or in two phases of small CTAs per transform
+ * (variant 2, log N = 12..14: the NTT form 2 split into rows and columns, see he_ntt_form).  The
+ * first such call on a context times them on its first chunk (synchronising the stream; not
+ * under stream capture) and keeps the fastest: variant (-1 before) and ms[0..HE_KS_VARIANTS-1]
+ * (may be NULL) report the choice and the timings.  Every variant gives the same residues. */
+#define HE_KS_VARIANTS 3
 int he_keyswitch_tuning(const he_ctx *ctx, int *variant, float *ms);
+/* Pin the key switch's transform variant for this context (0 .. HE_KS_VARIANTS-1; variant 2 only
+ * at log N = 12..14, HE_EINVAL otherwise), or -1 to time them again on the next call. */
+int he_set_keyswitch_variant(he_ctx *ctx, int variant);
 
 /* NTT launches of many limb-polys (an encoded matrix's 4 x m' transforms, import and export of
  * plaintext batches) run as one CTA per limb-poly (form 0), as a 2-CTA cluster per limb-poly

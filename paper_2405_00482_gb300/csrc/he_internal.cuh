@@ -171,7 +171,7 @@ struct he_ctx {
                                       // (forward only; -1: not yet timed)
     float ntt_form_ms[HE_NTT_FORMS] = {};  // the timed milliseconds of each form (an encoded matrix's transform)
     int ks_variant = -1;              // transform variant of the many-rotation key switch, chosen by timing (-1: not yet)
-    float ks_tune_ms[2] = {};         // the timed milliseconds of each variant (one full chunk of rotations)
+    float ks_tune_ms[HE_KS_VARIANTS] = {};  // the timed milliseconds of each variant (one full chunk of rotations)
     uint32_t *d_bconv_a = nullptr;    // INT8 engine: tensor-core A fragments of every (level, digit), shared with forks
     std::vector<size_t> bconv_a_off;  // their offsets (uint4 units), [level * dnum + digit]
     // staging of the host-memory entry points (he_host.cu), grown on demand: a device buffer for

@@ -270,6 +270,82 @@ __global__ void __launch_bounds__(512, TPB == 512 ? 2 : 1) ks_conv_kernel(KsGeom
     for (int k = threadIdx.x; k < len; k += blockDim.x) o[k] = s[SIDX(k)];
 }
 
+// ---- transform variant 2: the two transforms in two phases each (he_ntt.cuh, NTT form 2) ----
+// P limbs: the inverse row phase, then the inverse column phase scaled by N^-1 [(P/p_i)^-1] (the
+// values of ks_pintt_kernel); Q limbs: the forward column phase on the conversion
+// sum_i pc_j[c][i] (P/p_i mod q_l), then the forward row phase (the values of ks_conv_kernel).
+template <int LOGN, int NBA>
+__global__ void __launch_bounds__(NTT2_THREADS) ks2_pinv_rows_kernel(KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                                                   const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
+    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    const int item = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
+    const int pr = md.p_prime[item % kg.K];
+    ntt2_inv_rows<LOGN, NBA>(sm, kg.pc + (int64_t)item * N, b0, TwGlobal{twiddles(d_tw, pr, 1, LOGN)}, mc[pr].q);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) ks2_pinv_cols_kernel(KsGeom kg, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                                                      const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = (N >> 6) / NTT2_TC;
+    __shared__ uint64_t sm[ntt2_cols_smem_words()];
+    const int item = blockIdx.x / TILES, c0 = (blockIdx.x % TILES) * NTT2_TC;
+    const int i = item % kg.K, pr = md.p_prime[i];
+    const uint64_t q = mc[pr].q, ni = mc[pr].ninv, nis = mc[pr].ninv_shoup, f = md.inv[i], fs = md.inv_shoup[i];
+    uint64_t *x = kg.pc + (int64_t)item * N;
+    ntt2_inv_cols<LOGN>(sm, x, c0, TwGlobal{twiddles(d_tw, pr, 1, LOGN)}, q,
+                        [=](int64_t k, uint64_t v) { x[k] = mul_shoup(mul_shoup(v, ni, nis, q), f, fs, q); });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) ks2_conv_cols_kernel(KsGeom kg, uint64_t *cv, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                                                      const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = (N >> 6) / NTT2_TC;
+    __shared__ uint64_t sm[ntt2_cols_smem_words()];
+    const int item = blockIdx.x / TILES, c0 = (blockIdx.x % TILES) * NTT2_TC;
+    const int jc = item / kg.nl, l = item % kg.nl, pl = md.q_prime[l];
+    const uint64_t q = mc[pl].q, h0 = md.hat[0][l], h0s = md.hat_shoup[0][l];
+    const uint64_t *pc = kg.pc + (int64_t)jc * kg.K * N;
+    ntt2_fwd_cols<LOGN>(
+        sm,
+        [&](int64_t x) {
+            uint64_t v = mul_shoup(pc[x], h0, h0s, q);
+            for (int i = 1; i < kg.K; ++i) v = add_mod(v, mul_shoup(pc[(int64_t)i * N + x], md.hat[i][l], md.hat_shoup[i][l], q), q);
+            return v;
+        },
+        cv + (int64_t)item * N, c0, TwGlobal{twiddles(d_tw, pl, 0, LOGN)}, q);
+}
+
+template <int LOGN, int NB1>
+__global__ void __launch_bounds__(NTT2_THREADS) ks2_conv_rows_kernel(uint64_t *cv, int nl, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                                                   const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
+    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    const int item = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
+    const int pl = md.q_prime[item % nl];
+    ntt2_fwd_rows<LOGN, NB1>(sm, cv + (int64_t)item * N, b0, TwGlobal{twiddles(d_tw, pl, 0, LOGN)}, mc[pl].q, mc[pl].mu);
+}
+
+// the four launches of transform variant 2 (log N = 12, 13, 14)
+void ks2_transforms(int logn, const KsGeom &kg, uint64_t *cv, const ModDownConst &md, const uint64_t *tw, const ModConst *mc, int np, int nq,
+                    cudaStream_t st) {
+    const int tiles_c = (1 << (logn - 6)) / NTT2_TC, tiles_r = 64 / NTT2_TR;
+    auto go = [&](auto L, auto NB) {
+        constexpr int LG = decltype(L)::value, NB1 = decltype(NB)::value;
+        launch_k(ks2_pinv_rows_kernel<LG, LG - 6 - NB1>, (unsigned)(np * tiles_r), NTT2_THREADS, 0, st, kg, md, tw, mc);
+        launch_k(ks2_pinv_cols_kernel<LG>, (unsigned)(np * tiles_c), NTT2_THREADS, 0, st, kg, md, tw, mc);
+        launch_k(ks2_conv_cols_kernel<LG>, (unsigned)(nq * tiles_c), NTT2_THREADS, 0, st, kg, cv, md, tw, mc);
+        launch_k(ks2_conv_rows_kernel<LG, NB1>, (unsigned)(nq * tiles_r), NTT2_THREADS, 0, st, cv, kg.nl, md, tw, mc);
+    };
+    if (logn == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
+    else if (logn == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 4>{});
+    else go(std::integral_constant<int, 14>{}, std::integral_constant<int, 4>{});
+}
+
 // grid (N / (256 KS_U), count * 2 * nl): thread per KS_U coefficients of one (j, c, Q limb l)
 template <int ND>
 __global__ void __launch_bounds__(256) ks_out_kernel(const RotTable jobs, KsGeom kg, const uint64_t *__restrict__ cv, ModDownConst md,
@@ -329,7 +405,8 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
     const ModConst *mc = ctx->d_mc;
     const int cmax = count < HE_ROT_CHUNK ? count : HE_ROT_CHUNK;
     uint64_t *cv = pc + (size_t)cmax * 2 * ctx->K * ctx->n;  // [cmax][2][level+1][N] after pc [cmax][2][K][N]
-    // one chunk's launches with transform variant v (0: ntt_threads per CTA, 1: 512 threads)
+    // one chunk's launches with transform variant v (0: ntt_threads per CTA, 1: 512 threads,
+    // 2: two phases of small CTAs per transform)
     auto issue = [&](int c0, int v) {
         const int n = count - c0 < HE_ROT_CHUNK ? count - c0 : HE_ROT_CHUNK;
         RotTable tab{};
@@ -368,9 +445,12 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
             pt = prof_pair(ctx, HE_PROF_KS_TRANSFORM);
             if (pt) cudaEventRecord(pt[0], st);
         }
-        // the transforms: cluster form for few limb-polys, else one CTA each
+        // the transforms: cluster form for few limb-polys, else one CTA each, or two phases each
         const bool wide = v == 1 && logn >= 12;
-        if (use_cluster(logn, np))
+        if (v == 2 && logn >= 12 && logn <= 14) {
+            ctx->launches += 2;
+            ks2_transforms(logn, kg, cv, md, tw, mc, np, nq, st);
+        } else if (use_cluster(logn, np))
             launch_cluster(by_logn(logn, [](auto L) { return ks_pintt_kernel<true, L.value, 0>; }), np * HE_NTT_CL_SIZE, cl_threads(logn),
                            cl_smem_bytes(logn), st, kg, md, tw, mc, logn);
         else if (wide)
@@ -378,7 +458,9 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
         else
             launch_k(by_logn(logn, [](auto L) { return ks_pintt_kernel<false, L.value, 256>; }), np, ntt_threads(logn), ntt_smem_bytes(logn), st, kg, md, tw,
                      mc, logn);
-        if (wide)
+        if (v == 2 && logn >= 12 && logn <= 14)
+            ;  // both transforms launched above
+        else if (wide)
             launch_k(by_logn(logn, [](auto L) { return ks_conv_kernel<false, L.value, 512>; }), nq, 512, ntt_smem_bytes(logn), st, kg, cv, md, tw, mc, logn);
         else
             launch_k(by_logn(logn, [](auto L) { return ks_conv_kernel<false, L.value, 256>; }), nq, ntt_threads(logn), ntt_smem_bytes(logn), st, kg, cv, md,
@@ -404,7 +486,7 @@ void launch_keyswitch_many(he_ctx *ctx, const RotJob *jobs, int count, int level
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (cs == cudaStreamCaptureStatusNone && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
             int best = 0;
-            for (int v = 0; v < 2; ++v) {
+            for (int v = 0; v < (logn >= 12 && logn <= 14 ? HE_KS_VARIANTS : 2); ++v) {
                 float ms = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
                     cudaEventRecord(e0, st);
@@ -445,12 +527,17 @@ void keyswitch_set_smem_limits(int max_bytes) {
     });
 }
 
+extern "C" int he_set_keyswitch_variant(he_ctx *ctx, int variant) {
+    if (!ctx || variant < -1 || variant >= HE_KS_VARIANTS) return HE_EINVAL;
+    if (variant == 2 && (ctx->log_n < 12 || ctx->log_n > 14)) return HE_EINVAL;
+    ctx->ks_variant = variant;
+    return HE_OK;
+}
+
 extern "C" int he_keyswitch_tuning(const he_ctx *ctx, int *variant, float *ms) {
     if (!ctx || !variant) return HE_EINVAL;
     *variant = ctx->ks_variant;
-    if (ms) {
-        ms[0] = ctx->ks_tune_ms[0];
-        ms[1] = ctx->ks_tune_ms[1];
-    }
+    if (ms)
+        for (int v = 0; v < HE_KS_VARIANTS; ++v) ms[v] = ctx->ks_tune_ms[v];
     return HE_OK;
 }

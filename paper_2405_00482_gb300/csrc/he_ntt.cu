@@ -151,133 +151,38 @@ __global__ void PAIR_BOUNDS(LOGN) ntt_from_int64_pair_kernel(const int64_t *__re
 }
 
 // out = data 2^-64 mod q (Montgomery form back to canonical); grid (blocks, groups, limbs)
-// ---- two-phase form (he_set_ntt_form 2): the transform as column and row sub-transforms ----
-// With N = 64 C (C = 2^(log N - 6)), stages 0..5 of the forward transform only combine the 64
-// elements x = l C + c of one column c (their stage-s group x >> (log N - s) = l >> (6 - s) does
-// not depend on c), and stages 6..log N - 1 only the C elements of one row x = b C + m.  The
-// column phase takes NTT2_TC columns of one limb-poly per CTA (two radix-8 passes in registers,
-// one exchange through shared memory) and writes the stage-5 values (below 4q) to out; the row
-// phase takes NTT2_TR rows per CTA in place (a radix-2^NB1 and a radix-2^NB2 pass) and finishes
-// as the other forms do: canonical residues, times 2^64 mod q when to_mont.  The butterflies
-// and their stage order are those of the other forms, so the values are the same; the work
-// spreads over the SMs in blocks of 1/(C/NTT2_TC) (columns) or 1/4 (rows) of a limb-poly.
-// Two changes of operation order that leave every output the same residue: the factor 2^64 mod q
-// of to_mont multiplies the inputs (one Shoup product, which for int64 inputs also does the
-// reduction mod q) instead of the outputs, the transform being linear; and for primes below 2^59
-// the butterflies skip the lazy correction (ntt_fwd_radix), the row phase reducing at the end.
-#define NTT2_TC 16
-#define NTT2_TR 16
-#define NTT2_THREADS 128
-
-// canonical residue of v 2^64 mod q for a signed v (Shoup product by 2^64 mod q of |v|)
-__device__ __forceinline__ uint64_t signed_to_mont(int64_t v, uint64_t r1, uint64_t r1s, uint64_t q) {
-    const uint64_t a = v >= 0 ? (uint64_t)v : 0ull - (uint64_t)v;
-    const uint64_t r = mul_shoup(a, r1, r1s, q);
-    return (v < 0 && r != 0) ? q - r : r;
-}
-
+// ---- two-phase form (he_set_ntt_form 2): the bodies are in he_ntt.cuh ----
 template <int LOGN, bool I64>
 __global__ void __launch_bounds__(NTT2_THREADS, 8) ntt2_cols_kernel(const void *__restrict__ in_v, int64_t in_gs, uint64_t *out, int64_t out_gs,
-                                                               LimbMap map, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
-                                                               int to_mont) {
+                                                                  LimbMap map, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc,
+                                                                  int to_mont) {
     HE_GRID_DEP();
-    constexpr int N = 1 << LOGN, C = N >> 6, TILES = C / NTT2_TC, PAD = NTT2_TC + 1;
-    static_assert(NTT2_THREADS == 8 * NTT2_TC, "one thread per (column, set of 8)");
-    __shared__ uint64_t sm[64 * PAD];
+    constexpr int N = 1 << LOGN, TILES = (N >> 6) / NTT2_TC;
+    __shared__ uint64_t sm[ntt2_cols_smem_words()];
     const int poly = blockIdx.x / TILES, c0 = (blockIdx.x % TILES) * NTT2_TC;
     const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
-    const uint64_t q = mc[p].q;
-    const TwGlobal tw{twiddles(d_tw, p, 0, LOGN)};
-    const int c = threadIdx.x % NTT2_TC, r = threadIdx.x / NTT2_TC;
-    const uint64_t r1 = mc[p].r1, r1s = mc[p].r1_shoup;
-    const bool corr = q >= HE_NTT_NOCORR_Q;
-    uint64_t v[8];
-    // stages 0-2 on the column's elements l = r + 8 i (one group at stage 0)
+    const uint64_t q = mc[p].q, r1 = mc[p].r1, r1s = mc[p].r1_shoup, mu = mc[p].mu;
+    uint64_t *dst = out + g * out_gs + (int64_t)l * N;
     if constexpr (I64) {  // int64 coefficients, shared by the limbs of group g, reduced mod q
-        const int64_t *src = static_cast<const int64_t *>(in_v) + g * in_gs + c0 + c;
-        const uint64_t mu = mc[p].mu;
-        int64_t t[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) t[i] = src[(int64_t)(r + 8 * i) * C];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = to_mont ? signed_to_mont(t[i], r1, r1s, q) : reduce_signed(t[i], q, mu);
+        const int64_t *src = static_cast<const int64_t *>(in_v) + g * in_gs;
+        ntt2_fwd_cols<LOGN>(sm, [=](int64_t x) { return to_mont ? signed_to_mont(src[x], r1, r1s, q) : reduce_signed(src[x], q, mu); }, dst, c0,
+                            TwGlobal{twiddles(d_tw, p, 0, LOGN)}, q);
     } else {
-        const uint64_t *src = static_cast<const uint64_t *>(in_v) + g * in_gs + (int64_t)l * N + c0 + c;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = src[(int64_t)(r + 8 * i) * C];
-        if (to_mont) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = mul_shoup(v[i], r1, r1s, q);
-        }
+        const uint64_t *src = static_cast<const uint64_t *>(in_v) + g * in_gs + (int64_t)l * N;
+        ntt2_fwd_cols<LOGN>(sm, [=](int64_t x) { return to_mont ? mul_shoup(src[x], r1, r1s, q) : src[x]; }, dst, c0,
+                            TwGlobal{twiddles(d_tw, p, 0, LOGN)}, q);
     }
-    if (corr) ntt_fwd_radix<3, TwGlobal, true>(v, tw, q, 0, 0);
-    else ntt_fwd_radix<3, TwGlobal, false>(v, tw, q, 0, 0);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) sm[(r + 8 * i) * PAD + c] = v[i];
-    __syncthreads();
-    // stages 3-5 on l = 8 r + i: group r at stage 3
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = sm[(8 * r + i) * PAD + c];
-    if (corr) ntt_fwd_radix<3, TwGlobal, true>(v, tw, q, 3, r);
-    else ntt_fwd_radix<3, TwGlobal, false>(v, tw, q, 3, r);
-    uint64_t *dst = out + g * out_gs + (int64_t)l * N + c0 + c;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) dst[(int64_t)(8 * r + i) * C] = v[i];
 }
-
-// shared-memory row stride of the row phase: one pad word per 8 elements, and rows r, r + 1 on
-// opposite halves of the banks
-__host__ __device__ constexpr int ntt2_row_pitch(int lb) { return ((1 << lb) + (1 << lb) / 8) % 16 == 0 ? (1 << lb) + (1 << lb) / 8 + 8 : (1 << lb) + (1 << lb) / 8; }
 
 template <int LOGN, int NB1>
 __global__ void __launch_bounds__(NTT2_THREADS) ntt2_rows_kernel(uint64_t *data, int64_t gs, LimbMap map, const uint64_t *__restrict__ d_tw,
                                                                const ModConst *__restrict__ mc) {
     HE_GRID_DEP();
-    constexpr int N = 1 << LOGN, LB = LOGN - 6, R = 1 << LB, NB2 = LB - NB1, TILES = 64 / NTT2_TR, RP = ntt2_row_pitch(LB);
-    constexpr int S1 = R >> NB1, S2 = R >> NB2;  // sets per row of the two passes
-    __shared__ uint64_t sm[NTT2_TR * RP];
+    constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
+    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
     const int poly = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
     const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
-    const uint64_t q = mc[p].q;
-    const TwGlobal tw{twiddles(d_tw, p, 0, LOGN)};
-    uint64_t *row0 = data + g * gs + (int64_t)l * N + (int64_t)b0 * R;
-    auto at = [](int m) { return m + (m >> 3); };
-    const bool corr = q >= HE_NTT_NOCORR_Q;
-    // stages 6 .. 5 + NB1 on the elements m = j + S1 i of row b (group b at stage 6)
-    for (int set = threadIdx.x; set < NTT2_TR * S1; set += NTT2_THREADS) {
-        const int rb = set / S1, j = set % S1;
-        uint64_t v[1 << NB1];
-#pragma unroll
-        for (int i = 0; i < (1 << NB1); ++i) v[i] = row0[(int64_t)rb * R + j + S1 * i];
-        if (corr) ntt_fwd_radix<NB1, TwGlobal, true>(v, tw, q, 6, b0 + rb);
-        else ntt_fwd_radix<NB1, TwGlobal, false>(v, tw, q, 6, b0 + rb);
-#pragma unroll
-        for (int i = 0; i < (1 << NB1); ++i) sm[rb * RP + at(j + S1 * i)] = v[i];
-    }
-    __syncthreads();
-    // the last NB2 stages on 2^NB2 consecutive elements m = 2^NB2 e + i: group b 2^NB1 + e
-    const uint64_t two_q = 2 * q, mu = mc[p].mu;
-    for (int set = threadIdx.x; set < NTT2_TR * S2; set += NTT2_THREADS) {
-        const int rb = set / S2, e = set % S2;
-        uint64_t v[1 << NB2];
-#pragma unroll
-        for (int i = 0; i < (1 << NB2); ++i) v[i] = sm[rb * RP + at((e << NB2) + i)];
-        if (corr) {  // values below 4q
-            ntt_fwd_radix<NB2, TwGlobal, true>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
-#pragma unroll
-            for (int i = 0; i < (1 << NB2); ++i) {
-                const uint64_t x = v[i] >= two_q ? v[i] - two_q : v[i];
-                v[i] = x >= q ? x - q : x;
-            }
-        } else {  // values below (1 + 2 log N) q
-            ntt_fwd_radix<NB2, TwGlobal, false>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
-#pragma unroll
-            for (int i = 0; i < (1 << NB2); ++i) v[i] = reduce_barrett(v[i], q, mu);
-        }
-        ulonglong2 *d = reinterpret_cast<ulonglong2 *>(row0 + (int64_t)rb * R + (e << NB2));
-#pragma unroll
-        for (int i = 0; i < (1 << NB2) / 2; ++i) d[i] = make_ulonglong2(v[2 * i], v[2 * i + 1]);
-    }
+    ntt2_fwd_rows<LOGN, NB1>(sm, data + g * gs + (int64_t)l * N, b0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, mc[p].q, mc[p].mu);
 }
 
 __global__ void from_mont_kernel(const uint64_t *__restrict__ data, uint64_t *out, LimbMap map, const ModConst *__restrict__ mc, int logn) {

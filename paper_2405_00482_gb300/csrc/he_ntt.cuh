@@ -165,6 +165,35 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, in
     __syncthreads();
 }
 
+// NB inverse stages s0..s0+NB-1 on the 2^NB elements of one set held in registers, r[k] the
+// element base + (k << s0) of a set whose group at the pass's last stage is g
+// (g = base >> (s0 + NB)): at stage s0 + j element k meets twiddle entry
+// m + (g << (NB - j - 1)) + (k >> (j + 1)), m = N >> (s0 + j + 1).  Gentleman-Sande lazy
+// butterflies: inputs and outputs below 2q.
+template <int NB, class TWA>
+__device__ __forceinline__ void ntt_inv_radix(uint64_t (&r)[1 << NB], TWA itw, uint64_t q, int N, int s0, int g) {
+    constexpr int E = 1 << NB;
+    const uint64_t two_q = 2 * q;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const int h = 1 << j;
+        const int m = N >> (s0 + j + 1);
+        ulonglong2 wj[E / 2];
+#pragma unroll
+        for (int i = 0; i < (E >> (j + 1)); ++i) wj[i] = itw.at(j, g, i, m, m + (g << (NB - j - 1)) + i);
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            if ((k & (2 * h - 1)) < h) {
+                const ulonglong2 w = wj[k >> (j + 1)];
+                const uint64_t U = r[k], V = r[k + h];
+                uint64_t X = U + V;
+                r[k] = X >= two_q ? X - two_q : X;
+                r[k + h] = mul_shoup_lazy(U - V + two_q, w.x, w.y, q);
+            }
+        }
+    }
+}
+
 template <int NB, class TWA>
 __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, int logn, int s0, int set0 = 0, int set1 = -1,
                                              int off = 0) {
@@ -172,7 +201,6 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
     const int N = 1 << logn;
     if (set1 < 0) set1 = N >> NB;
     const int lg_t0 = s0;  // t of the pass's first stage
-    const uint64_t two_q = 2 * q;
     for (int set = set0 + threadIdx.x; set < set1; set += blockDim.x) {
         const int g = set >> lg_t0, low = set & ((1 << lg_t0) - 1);
         const int base = (g << (lg_t0 + NB)) + low;
@@ -180,30 +208,172 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
         uint64_t r[E];
 #pragma unroll
         for (int k = 0; k < E; ++k) r[k] = s[sb + SIDX(k << lg_t0)];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const int h = 1 << j;
-            const int m = N >> (s0 + j + 1);
-            // element x = base + (k << lg_t0) meets twiddle m + (x >> (lg_t0 + j + 1)), which is
-            // m + (g << (NB - j - 1)) + (k >> (j + 1)): 2^(NB-j-1) consecutive entries
-            ulonglong2 wj[E / 2];
-#pragma unroll
-            for (int i = 0; i < (E >> (j + 1)); ++i) wj[i] = itw.at(j, g, i, m, m + (g << (NB - j - 1)) + i);
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                if ((k & (2 * h - 1)) < h) {
-                    const ulonglong2 w = wj[k >> (j + 1)];
-                    const uint64_t U = r[k], V = r[k + h];
-                    uint64_t X = U + V;
-                    r[k] = X >= two_q ? X - two_q : X;
-                    r[k + h] = mul_shoup_lazy(U - V + two_q, w.x, w.y, q);
-                }
-            }
-        }
+        // element x = base + (k << lg_t0) meets twiddle m + (x >> (lg_t0 + j + 1)), which is
+        // m + (g << (NB - j - 1)) + (k >> (j + 1)): 2^(NB-j-1) consecutive entries
+        ntt_inv_radix<NB>(r, itw, q, N, s0, g);
 #pragma unroll
         for (int k = 0; k < E; ++k) s[sb + SIDX(k << lg_t0)] = r[k];
     }
     __syncthreads();
+}
+
+// ---- two-phase transforms of many limb-polys (NTT form 2) ----
+// With N = 64 C (C = 2^(log N - 6)), stages 0..5 of the forward transform only combine the 64
+// elements x = l C + c of one column c (their stage-s group x >> (log N - s) = l >> (6 - s) does
+// not depend on c), and stages 6..log N - 1 only the C elements of one row x = b C + m; the
+// inverse transform runs the same stages in the other order (rows first).  A column phase takes
+// NTT2_TC columns of one limb-poly per CTA (two radix-8 passes in registers, one exchange through
+// shared memory); a row phase NTT2_TR rows per CTA (a radix-2^NB1 and a radix-2^(log N - 6 - NB1)
+// pass).  The butterflies and their stage order are those of the one-CTA form, so the values are
+// the same.  Forward: for primes below HE_NTT_NOCORR_Q the butterflies skip the lazy correction
+// (ntt_fwd_radix) and the row phase reduces with one Barrett step at the end; the other primes
+// end with the usual two conditional subtractions.  Inverse: values stay below 2q; the column
+// phase hands each output to a store functor (the caller's scaling).
+#define NTT2_TC 16
+#define NTT2_TR 16
+#define NTT2_THREADS 128
+__host__ __device__ constexpr int ntt2_cols_smem_words() { return 64 * (NTT2_TC + 1); }
+// shared-memory row stride of a row phase: one pad word per 8 elements, rows r and r + 1 on
+// opposite halves of the banks
+__host__ __device__ constexpr int ntt2_row_pitch(int lb) {
+    return ((1 << lb) + (1 << lb) / 8) % 16 == 0 ? (1 << lb) + (1 << lb) / 8 + 8 : (1 << lb) + (1 << lb) / 8;
+}
+__host__ __device__ constexpr int ntt2_rows_smem_words(int lb) { return NTT2_TR * ntt2_row_pitch(lb); }
+__device__ __forceinline__ int ntt2_at(int m) { return m + (m >> 3); }
+
+// canonical residue of v 2^64 mod q for a signed v (Shoup product by 2^64 mod q of |v|)
+__device__ __forceinline__ uint64_t signed_to_mont(int64_t v, uint64_t r1, uint64_t r1s, uint64_t q) {
+    const uint64_t a = v >= 0 ? (uint64_t)v : 0ull - (uint64_t)v;
+    const uint64_t r = mul_shoup(a, r1, r1s, q);
+    return (v < 0 && r != 0) ? q - r : r;
+}
+
+// forward stages 0-5 of columns c0 .. c0 + NTT2_TC - 1 of one limb-poly: load(x) gives the
+// canonical input of element x; writes the stage-5 values to dst[x]
+template <int LOGN, class LOAD>
+__device__ __forceinline__ void ntt2_fwd_cols(uint64_t *sm, LOAD load, uint64_t *dst, int c0, TwGlobal tw, uint64_t q) {
+    constexpr int C = (1 << LOGN) >> 6, PAD = NTT2_TC + 1;
+    static_assert(NTT2_THREADS == 8 * NTT2_TC, "one thread per (column, set of 8)");
+    const int c = threadIdx.x % NTT2_TC, r = threadIdx.x / NTT2_TC;
+    const bool corr = q >= HE_NTT_NOCORR_Q;
+    uint64_t v[8];
+    // stages 0-2 on the column's elements l = r + 8 i (one group at stage 0)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = load((int64_t)(r + 8 * i) * C + c0 + c);
+    if (corr) ntt_fwd_radix<3, TwGlobal, true>(v, tw, q, 0, 0);
+    else ntt_fwd_radix<3, TwGlobal, false>(v, tw, q, 0, 0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sm[(r + 8 * i) * PAD + c] = v[i];
+    __syncthreads();
+    // stages 3-5 on l = 8 r + i: group r at stage 3
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = sm[(8 * r + i) * PAD + c];
+    if (corr) ntt_fwd_radix<3, TwGlobal, true>(v, tw, q, 3, r);
+    else ntt_fwd_radix<3, TwGlobal, false>(v, tw, q, 3, r);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[(int64_t)(8 * r + i) * C + c0 + c] = v[i];
+}
+
+// forward stages 6 .. log N - 1 of rows b0 .. b0 + NTT2_TR - 1 of one limb-poly, in place;
+// canonical outputs
+template <int LOGN, int NB1>
+__device__ __forceinline__ void ntt2_fwd_rows(uint64_t *sm, uint64_t *poly, int b0, TwGlobal tw, uint64_t q, uint64_t mu) {
+    constexpr int LB = LOGN - 6, R = 1 << LB, NB2 = LB - NB1, RP = ntt2_row_pitch(LB);
+    constexpr int S1 = R >> NB1, S2 = R >> NB2;  // sets per row of the two passes
+    uint64_t *row0 = poly + (int64_t)b0 * R;
+    const bool corr = q >= HE_NTT_NOCORR_Q;
+    // stages 6 .. 5 + NB1 on the elements m = j + S1 i of row b (group b at stage 6)
+    for (int set = threadIdx.x; set < NTT2_TR * S1; set += NTT2_THREADS) {
+        const int rb = set / S1, j = set % S1;
+        uint64_t v[1 << NB1];
+#pragma unroll
+        for (int i = 0; i < (1 << NB1); ++i) v[i] = row0[(int64_t)rb * R + j + S1 * i];
+        if (corr) ntt_fwd_radix<NB1, TwGlobal, true>(v, tw, q, 6, b0 + rb);
+        else ntt_fwd_radix<NB1, TwGlobal, false>(v, tw, q, 6, b0 + rb);
+#pragma unroll
+        for (int i = 0; i < (1 << NB1); ++i) sm[rb * RP + ntt2_at(j + S1 * i)] = v[i];
+    }
+    __syncthreads();
+    // the last NB2 stages on 2^NB2 consecutive elements m = 2^NB2 e + i: group b 2^NB1 + e
+    const uint64_t two_q = 2 * q;
+    for (int set = threadIdx.x; set < NTT2_TR * S2; set += NTT2_THREADS) {
+        const int rb = set / S2, e = set % S2;
+        uint64_t v[1 << NB2];
+#pragma unroll
+        for (int i = 0; i < (1 << NB2); ++i) v[i] = sm[rb * RP + ntt2_at((e << NB2) + i)];
+        if (corr) {  // values below 4q
+            ntt_fwd_radix<NB2, TwGlobal, true>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
+#pragma unroll
+            for (int i = 0; i < (1 << NB2); ++i) {
+                const uint64_t x = v[i] >= two_q ? v[i] - two_q : v[i];
+                v[i] = x >= q ? x - q : x;
+            }
+        } else {  // values below (1 + 2 log N) q
+            ntt_fwd_radix<NB2, TwGlobal, false>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
+#pragma unroll
+            for (int i = 0; i < (1 << NB2); ++i) v[i] = reduce_barrett(v[i], q, mu);
+        }
+        ulonglong2 *d = reinterpret_cast<ulonglong2 *>(row0 + (int64_t)rb * R + (e << NB2));
+#pragma unroll
+        for (int i = 0; i < (1 << NB2) / 2; ++i) d[i] = make_ulonglong2(v[2 * i], v[2 * i + 1]);
+    }
+}
+
+// inverse stages 0 .. log N - 7 of rows b0 .. b0 + NTT2_TR - 1 of one limb-poly (inputs below 2q),
+// in place: a radix-2^NBA pass on consecutive elements, then one of stride 2^NBA
+template <int LOGN, int NBA>
+__device__ __forceinline__ void ntt2_inv_rows(uint64_t *sm, uint64_t *poly, int b0, TwGlobal itw, uint64_t q) {
+    constexpr int N = 1 << LOGN, LB = LOGN - 6, R = 1 << LB, NBB = LB - NBA, RP = ntt2_row_pitch(LB);
+    constexpr int SA = R >> NBA, SB = R >> NBB;  // sets per row of the two passes
+    uint64_t *row0 = poly + (int64_t)b0 * R;
+    // stages 0 .. NBA - 1 on m = 2^NBA e + i: group at stage NBA - 1 is b 2^(LB - NBA) + e
+    for (int set = threadIdx.x; set < NTT2_TR * SA; set += NTT2_THREADS) {
+        const int rb = set / SA, e = set % SA;
+        uint64_t v[1 << NBA];
+        const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(row0 + (int64_t)rb * R + (e << NBA));
+#pragma unroll
+        for (int i = 0; i < (1 << NBA) / 2; ++i) {
+            const ulonglong2 t = s2[i];
+            v[2 * i] = t.x;
+            v[2 * i + 1] = t.y;
+        }
+        ntt_inv_radix<NBA>(v, itw, q, N, 0, ((b0 + rb) << (LB - NBA)) + e);
+#pragma unroll
+        for (int i = 0; i < (1 << NBA); ++i) sm[rb * RP + ntt2_at((e << NBA) + i)] = v[i];
+    }
+    __syncthreads();
+    // stages NBA .. LB - 1 on m = j + 2^NBA i: group b at stage LB - 1
+    for (int set = threadIdx.x; set < NTT2_TR * SB; set += NTT2_THREADS) {
+        const int rb = set / SB, j = set % SB;
+        uint64_t v[1 << NBB];
+#pragma unroll
+        for (int i = 0; i < (1 << NBB); ++i) v[i] = sm[rb * RP + ntt2_at(j + SB * i)];
+        ntt_inv_radix<NBB>(v, itw, q, N, NBA, b0 + rb);
+#pragma unroll
+        for (int i = 0; i < (1 << NBB); ++i) row0[(int64_t)rb * R + j + SB * i] = v[i];
+    }
+}
+
+// inverse stages log N - 6 .. log N - 1 of columns c0 .. c0 + NTT2_TC - 1 of one limb-poly:
+// reads poly[x] (below 2q), hands each result (below 2q) to store(x, v)
+template <int LOGN, class STORE>
+__device__ __forceinline__ void ntt2_inv_cols(uint64_t *sm, const uint64_t *poly, int c0, TwGlobal itw, uint64_t q, STORE store) {
+    constexpr int N = 1 << LOGN, LB = LOGN - 6, C = 1 << LB, PAD = NTT2_TC + 1;
+    const int c = threadIdx.x % NTT2_TC, r = threadIdx.x / NTT2_TC;
+    uint64_t v[8];
+    // stages LB .. LB + 2 on l = 8 r + i: group r at stage LB + 2
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = poly[(int64_t)(8 * r + i) * C + c0 + c];
+    ntt_inv_radix<3>(v, itw, q, N, LB, r);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sm[(8 * r + i) * PAD + c] = v[i];
+    __syncthreads();
+    // stages LB + 3 .. LB + 5 on l = r + 8 i: one group
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = sm[(r + 8 * i) * PAD + c];
+    ntt_inv_radix<3>(v, itw, q, N, LB + 3, 0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) store((int64_t)(r + 8 * i) * C + c0 + c, v[i]);
 }
 
 // Per prime the twiddle block holds, in 16-byte pairs (w, Shoup quotient): the forward table

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhe.so")
 HE_OK, HE_EINVAL, HE_ENOMEM, HE_ECUDA, HE_EKEY, HE_ELEVEL, HE_ESCALE, HE_ETIMEOUT, HE_EBUDGET = 0, -1, -2, -3, -4, -5, -6, -7, -8
 HE_BCONV_INT64, HE_BCONV_INT8_TC = 0, 1  # basis extension engines of ModUp
 HE_NTT_FORMS = 3  # NTT forms of launches of many limb-polys
+HE_KS_VARIANTS = 3  # transform variants of the many-rotation key switch
 HE_PROF_LOOP, HE_PROF_MATRIX_NTT, HE_PROF_KS_TRANSFORM, HE_PROF_KS_ELEMENTWISE = 0, 1, 2, 3  # profiled kernel classes
 
 
@@ -100,6 +101,7 @@ _SIGS = {
     "he_batch_set_stage_form": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_ptmat_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_set_key_fusion": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_size_t]),
+    "he_set_keyswitch_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
     "he_ptmat_key_fusion": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "he_ptmat_set_key_fusion": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "he_batch_set_variant": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -853,10 +855,15 @@ class Context:
     def keyswitch_tuning(self) -> dict:
         """Transform variant of the many-rotation key switch (he_keyswitch_tuning): -1 before tuning."""
         v = ctypes.c_int()
-        ms = (ctypes.c_float * 2)()
+        ms = (ctypes.c_float * HE_KS_VARIANTS)()
         _check(_lib().he_keyswitch_tuning(self.handle, ctypes.byref(v), ms), "he_keyswitch_tuning")
         return {"variant": int(v.value), "variant_ms": [round(float(x), 4) for x in ms],
-                "variants": ["one CTA per limb-poly, usual threads", "one CTA per limb-poly, 512 threads, <= 64 registers"]}
+                "variants": ["one CTA per limb-poly, usual threads", "one CTA per limb-poly, 512 threads, <= 64 registers",
+                             "two phases of small CTAs per transform"]}
+
+    def set_keyswitch_variant(self, v: int) -> None:
+        """Pin the many-rotation key switch's transform variant (-1: time again)."""
+        _check(_lib().he_set_keyswitch_variant(self.handle, v), "he_set_keyswitch_variant")
 
     def ntt_form(self) -> dict:
         """NTT form of launches of many limb-polys (he_ntt_form): 0 one CTA, 1 a 2-CTA cluster per

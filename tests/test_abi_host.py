@@ -94,6 +94,7 @@ def test_loop_variant_table_and_argument_checks(he):
     assert lib.he_set_key_fusion(None, 1, 0) == he.HE_EINVAL
     assert lib.he_ptmat_key_fusion(None, ctypes.byref(a), ctypes.byref(b), ms) == he.HE_EINVAL
     assert lib.he_ptmat_set_key_fusion(None, 1, -1) == he.HE_EINVAL
+    assert lib.he_set_keyswitch_variant(None, 0) == he.HE_EINVAL
 
 
 @pytest.mark.parametrize("m,n,slots", [(4, 4, 8), (16, 64, 2048), (256, 1024, 4096), (3, 5, 8), (1, 8, 16), (5000, 300, 4096)])

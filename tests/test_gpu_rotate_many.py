@@ -72,3 +72,32 @@ def test_rotate_many_argument_checks(he):
         ctx.rotate_many(cts, [1, 2, 1])  # no key for step 2
     assert e.value.status == he.HE_EKEY
     assert ctx.rotate_many([], []) == []
+
+
+@pytest.mark.parametrize("log_n,qb,pb,dnum", [(12, [40, 20], [40], 2), (13, [60, 40, 40], [60], 3), (14, [60] + [40] * 6, [60, 60, 60], 3)])
+def test_keyswitch_variants_agree(he, log_n, qb, pb, dnum):
+    """Every transform variant of the many-rotation key switch (one CTA per limb-poly at two
+    thread counts, two phases per transform), pinned in turn: hoisted and many-ciphertext
+    rotations bit-identical across variants and to single rotations (the cluster key switch)."""
+    import torch
+
+    ctx = he.Context(log_n, qb, pb, dnum, seed=33)
+    rng = np.random.default_rng(log_n)
+    level, scale = len(qb) - 1, 2.0**20 if log_n == 12 else 2.0**40
+    enc = lambda i: ctx.encrypt(ctx.encode(torch.from_numpy(rng.uniform(-1, 1, ctx.slots)).cuda(), scale, level), 200 + i)
+    steps = list(range(1, 41))  # at least 32 rotations: the many-rotation key switch
+    ctx.keygen(steps)
+    ct, cts = enc(0), [enc(1 + i) for i in range(len(steps))]
+    results = []
+    for v in range(he.HE_KS_VARIANTS):
+        ctx.set_keyswitch_variant(v)
+        hoisted = torch.stack([ctx.ct_export(o) for o in ctx.rotate_hoisted(ct, steps)])
+        many = torch.stack([ctx.ct_export(o) for o in ctx.rotate_many(cts, steps)])
+        results.append((hoisted, many))
+    ctx.set_keyswitch_variant(-1)
+    for v in range(1, he.HE_KS_VARIANTS):
+        assert torch.equal(results[v][0], results[0][0]), f"hoisted, variant {v}"
+        assert torch.equal(results[v][1], results[0][1]), f"many, variant {v}"
+    for s in (1, 7, 40):
+        assert torch.equal(results[0][0][s - 1], ctx.ct_export(ctx.rotate(ct, s)))
+        assert torch.equal(results[0][1][s - 1], ctx.ct_export(ctx.rotate(cts[s - 1], s)))
