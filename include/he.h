@@ -264,10 +264,11 @@ int he_set_keyswitch_variant(he_ctx *ctx, int variant);
 /* NTT launches of many limb-polys (an encoded matrix's 4 x m' transforms, import and export of
  * plaintext batches) run as one CTA per limb-poly (form 0), as a 2-CTA cluster per limb-poly
  * (form 1: each CTA holds half of the coefficients, the one stage that pairs the halves goes
- * through distributed shared memory), or, for forward transforms, in two phases (form 2: with
- * N = 64 C, stages 0-5 as 64-point transforms of the C columns x = l C + c, then the remaining
- * stages as C-point transforms of the 64 rows, each phase one launch of many small CTAs, the
- * intermediate values in global memory; inverse transforms then use form 0).  The first matrix a
+ * through distributed shared memory), or in two phases (form 2, log N = 12..14: with N = 64 C,
+ * the forward transform's stages 0-5 as 64-point transforms of the C columns x = l C + c, then
+ * the remaining stages as C-point transforms of the 64 rows, each phase one launch of many small
+ * CTAs, the intermediate values in global memory; the inverse transform rows first; the ModUp of
+ * he_rotate_many takes this form too).  The first matrix a
  * context encodes times the forms on its transform (synchronising the stream; not under stream
  * capture) and keeps the fastest for the context; he_ntt_form reports the choice (-1 before) and
  * ms[0..HE_NTT_FORMS-1] (may be NULL), he_set_ntt_form pins one (0 .. HE_NTT_FORMS-1, or -1 to

@@ -403,6 +403,7 @@ void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
 int ntt_threads(int logn);
 bool use_cluster(int logn, int polys);  // launch in the cluster form (few limb-polys)
 bool use_pair(const he_ctx *ctx, int polys);  // launch in the 2-CTA pair form (many limb-polys, when the context chose it)
+bool use_two_phase(const he_ctx *ctx, int polys);  // launch in two phases (many limb-polys, NTT form 2, log N = 12..14)
 int cl_threads(int logn);
 size_t cl_smem_bytes(int logn);
 // dynamic shared memory of a CTA that holds one limb-poly for the NTT (padded layout)

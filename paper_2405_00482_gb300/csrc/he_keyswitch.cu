@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(NTT2_THREADS) ks2_pinv_rows_kernel(KsGeom kg, 
     __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
     const int item = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
     const int pr = md.p_prime[item % kg.K];
-    ntt2_inv_rows<LOGN, NBA>(sm, kg.pc + (int64_t)item * N, b0, TwGlobal{twiddles(d_tw, pr, 1, LOGN)}, mc[pr].q);
+    uint64_t *x = kg.pc + (int64_t)item * N;
+    ntt2_inv_rows<LOGN, NBA>(sm, x, x, b0, TwGlobal{twiddles(d_tw, pr, 1, LOGN)}, mc[pr].q);
 }
 
 template <int LOGN>

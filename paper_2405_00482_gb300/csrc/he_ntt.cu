@@ -185,6 +185,32 @@ __global__ void __launch_bounds__(NTT2_THREADS) ntt2_rows_kernel(uint64_t *data,
     ntt2_fwd_rows<LOGN, NB1>(sm, data + g * gs + (int64_t)l * N, b0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, mc[p].q, mc[p].mu);
 }
 
+// inverse: rows (in to out), then columns in place with the factor N^-1
+template <int LOGN, int NBA>
+__global__ void __launch_bounds__(NTT2_THREADS) ntt2_inv_rows_kernel(const uint64_t *__restrict__ in, int64_t in_gs, uint64_t *out, int64_t out_gs,
+                                                                   LimbMap map, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
+    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    const int poly = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
+    const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
+    ntt2_inv_rows<LOGN, NBA>(sm, in + g * in_gs + (int64_t)l * N, out + g * out_gs + (int64_t)l * N, b0, TwGlobal{twiddles(d_tw, p, 1, LOGN)},
+                             mc[p].q);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) ntt2_inv_cols_kernel(uint64_t *data, int64_t gs, LimbMap map, const uint64_t *__restrict__ d_tw,
+                                                                      const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = (N >> 6) / NTT2_TC;
+    __shared__ uint64_t sm[ntt2_cols_smem_words()];
+    const int poly = blockIdx.x / TILES, c0 = (blockIdx.x % TILES) * NTT2_TC;
+    const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
+    const uint64_t q = mc[p].q, ni = mc[p].ninv, nis = mc[p].ninv_shoup;
+    uint64_t *x = data + g * gs + (int64_t)l * N;
+    ntt2_inv_cols<LOGN>(sm, x, c0, TwGlobal{twiddles(d_tw, p, 1, LOGN)}, q, [=](int64_t k, uint64_t v) { x[k] = mul_shoup(v, ni, nis, q); });
+}
+
 __global__ void from_mont_kernel(const uint64_t *__restrict__ data, uint64_t *out, LimbMap map, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
     const int N = 1 << logn;
@@ -239,7 +265,7 @@ static auto pair_instance(int logn, F f) {
 }
 
 bool use_pair(const he_ctx *ctx, int polys) { return ctx->ntt_form == 1 && !use_cluster(ctx->log_n, polys) && ctx->log_n >= 12 && ctx->log_n <= 14; }
-static bool use_two_phase(const he_ctx *ctx, int polys) {
+bool use_two_phase(const he_ctx *ctx, int polys) {
     return ctx->ntt_form == 2 && !use_cluster(ctx->log_n, polys) && ctx->log_n >= 12 && ctx->log_n <= 14;
 }
 
@@ -285,6 +311,22 @@ void launch_ntt_fwd_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint
 
 void launch_ntt_inv_strided(he_ctx *ctx, const uint64_t *in, int64_t in_gs, uint64_t *out, int64_t out_gs, int groups, const LimbMap &map) {
     if (groups * map.n == 0) return;
+    if (use_two_phase(ctx, groups * map.n)) {
+        const int polys = groups * map.n, C = ctx->n >> 6;
+        const unsigned cols = (unsigned)(polys * (C / NTT2_TC)), rows = (unsigned)(polys * (64 / NTT2_TR));
+        const uint64_t *tw = ctx->d_tw;
+        const ModConst *mc = ctx->d_mc;
+        ctx->launches += 2;
+        auto go = [&](auto L, auto NBA) {
+            launch_k(ntt2_inv_rows_kernel<decltype(L)::value, decltype(NBA)::value>, rows, NTT2_THREADS, 0, ctx->stream, in, in_gs, out, out_gs, map, tw,
+                     mc);
+            launch_k(ntt2_inv_cols_kernel<decltype(L)::value>, cols, NTT2_THREADS, 0, ctx->stream, out, out_gs, map, tw, mc);
+        };
+        if (ctx->log_n == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
+        else if (ctx->log_n == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 3>{});
+        else go(std::integral_constant<int, 14>{}, std::integral_constant<int, 4>{});
+        return;
+    }
     ctx->launches++;
     if (use_pair(ctx, groups * map.n)) {
         launch_cluster_n(pair_instance(ctx->log_n, [](auto L) { return ntt_inv_pair_kernel<L.value>; }), groups * map.n * 2, pair_threads(ctx->log_n),

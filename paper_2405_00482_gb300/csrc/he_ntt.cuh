@@ -320,17 +320,19 @@ __device__ __forceinline__ void ntt2_fwd_rows(uint64_t *sm, uint64_t *poly, int 
 }
 
 // inverse stages 0 .. log N - 7 of rows b0 .. b0 + NTT2_TR - 1 of one limb-poly (inputs below 2q),
-// in place: a radix-2^NBA pass on consecutive elements, then one of stride 2^NBA
+// from src to dst (which may be src): a radix-2^NBA pass on consecutive elements, then one of
+// stride 2^NBA
 template <int LOGN, int NBA>
-__device__ __forceinline__ void ntt2_inv_rows(uint64_t *sm, uint64_t *poly, int b0, TwGlobal itw, uint64_t q) {
+__device__ __forceinline__ void ntt2_inv_rows(uint64_t *sm, const uint64_t *src, uint64_t *dst, int b0, TwGlobal itw, uint64_t q) {
     constexpr int N = 1 << LOGN, LB = LOGN - 6, R = 1 << LB, NBB = LB - NBA, RP = ntt2_row_pitch(LB);
     constexpr int SA = R >> NBA, SB = R >> NBB;  // sets per row of the two passes
-    uint64_t *row0 = poly + (int64_t)b0 * R;
+    const uint64_t *in0 = src + (int64_t)b0 * R;
+    uint64_t *row0 = dst + (int64_t)b0 * R;
     // stages 0 .. NBA - 1 on m = 2^NBA e + i: group at stage NBA - 1 is b 2^(LB - NBA) + e
     for (int set = threadIdx.x; set < NTT2_TR * SA; set += NTT2_THREADS) {
         const int rb = set / SA, e = set % SA;
         uint64_t v[1 << NBA];
-        const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(row0 + (int64_t)rb * R + (e << NBA));
+        const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(in0 + (int64_t)rb * R + (e << NBA));
 #pragma unroll
         for (int i = 0; i < (1 << NBA) / 2; ++i) {
             const ulonglong2 t = s2[i];

@@ -491,6 +491,86 @@ __global__ void rot_modup_kernel(const RotTable jobs, RotGeom rg, ModUpConst mu,
                       d_tw, mc, logn, 0, 1 << logn);
 }
 
+// ---- the same ModUp in two phases per transform (NTT form 2, he_ntt.cuh): the inverse NTT of
+// every c1 limb as rows (from the job's ciphertext into coef) then columns scaled by N^-1, and
+// every (j, d, u) target as columns on the conversion then rows; the digit's own limbs are
+// copied from the NTT-form input by the column launch and skipped by the row launch.  The values
+// of rot_intt_c1_kernel and rot_modup_kernel. ----
+template <int LOGN, int NBA>
+__global__ void __launch_bounds__(NTT2_THREADS) rot2_intt_rows_kernel(const RotTable jobs, RotGeom rg, const uint64_t *__restrict__ d_tw,
+                                                                    const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
+    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    const int item = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
+    const int j = item / rg.nl, l = item % rg.nl;
+    ntt2_inv_rows<LOGN, NBA>(sm, jobs.j[j].ct + ((int64_t)rg.nl + l) * N, rg.coef + j * rg.coef_w + (int64_t)l * N, b0,
+                             TwGlobal{twiddles(d_tw, l, 1, LOGN)}, mc[l].q);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) rot2_intt_cols_kernel(RotGeom rg, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = (N >> 6) / NTT2_TC;
+    __shared__ uint64_t sm[ntt2_cols_smem_words()];
+    const int item = blockIdx.x / TILES, c0 = (blockIdx.x % TILES) * NTT2_TC;
+    const int j = item / rg.nl, l = item % rg.nl;
+    const uint64_t q = mc[l].q, ni = mc[l].ninv, nis = mc[l].ninv_shoup;
+    uint64_t *x = rg.coef + j * rg.coef_w + (int64_t)l * N;
+    ntt2_inv_cols<LOGN>(sm, x, c0, TwGlobal{twiddles(d_tw, l, 1, LOGN)}, q, [=](int64_t k, uint64_t v) { x[k] = mul_shoup(v, ni, nis, q); });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) rot2_modup_cols_kernel(const RotTable jobs, RotGeom rg, ModUpConst mu,
+                                                                        const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, C = N >> 6, TILES = C / NTT2_TC;
+    __shared__ uint64_t sm[ntt2_cols_smem_words()];
+    const int item = blockIdx.x / TILES, c0 = (blockIdx.x % TILES) * NTT2_TC;
+    const int per = mu.ndig * mu.ext, j = item / per, d = (item % per) / mu.ext, u = item % mu.ext;
+    const int lo = d * mu.alpha, hi = lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq;
+    const int p = mu.ext_prime[u];
+    const uint64_t t = mc[p].q;
+    uint64_t *dst = rg.D + j * rg.d_w + ((int64_t)d * mu.ext + u) * N;
+    if (u >= lo && u < hi) {  // the digit's own limb: its NTT form is the input's (uniform over the CTA)
+        const uint64_t *src = jobs.j[j].ct + ((int64_t)rg.nl + u) * N;
+        for (int e = threadIdx.x; e < 64 * NTT2_TC; e += NTT2_THREADS) {
+            const int64_t x = (int64_t)(e / NTT2_TC) * C + c0 + e % NTT2_TC;
+            dst[x] = src[x];
+        }
+        return;
+    }
+    const uint64_t *coef = rg.coef + j * rg.coef_w;
+    // sum over the digit's primes of [x_i (Qd/q_i)^-1]_{q_i} (Qd/q_i mod t), as in modup_body
+    ntt2_fwd_cols<LOGN>(
+        sm,
+        [&](int64_t x) {
+            uint64_t a = 0;
+            for (int i = 0; i < hi - lo; ++i) {
+                const uint64_t qi = mc[lo + i].q;
+                const uint64_t term = mul_shoup(mul_shoup(coef[(int64_t)(lo + i) * N + x], mu.inv[d][i], mu.inv_shoup[d][i], qi), mu.hat[d][i][u],
+                                                mu.hat_shoup[d][i][u], t);
+                a = i == 0 ? term : add_mod(a, term, t);
+            }
+            return a;
+        },
+        dst, c0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, t);
+}
+
+template <int LOGN, int NB1>
+__global__ void __launch_bounds__(NTT2_THREADS) rot2_modup_rows_kernel(RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                                                     const ModConst *__restrict__ mc) {
+    HE_GRID_DEP();
+    constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
+    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    const int item = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
+    const int per = mu.ndig * mu.ext, j = item / per, d = (item % per) / mu.ext, u = item % mu.ext;
+    const int lo = d * mu.alpha, hi = lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq;
+    if (u >= lo && u < hi) return;  // copied, already in NTT form
+    const int p = mu.ext_prime[u];
+    ntt2_fwd_rows<LOGN, NB1>(sm, rg.D + j * rg.d_w + ((int64_t)d * mu.ext + u) * N, b0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, mc[p].q, mc[p].mu);
+}
+
 // ModUp of the jobs' c1 (NTT form) as clusters, item (j, d, u), the inverse NTT inside: for
 // launches of few rotations (at most HE_ROT_CL_MAX_ITEMS items, 8 CTAs each), where one CTA per
 // limb-poly would leave most SMs idle
@@ -1711,6 +1791,24 @@ void launch_rotate_many(he_ctx *ctx, const RotJob *jobs, int count, int level, u
         launch_cluster(by_logn(ctx->log_n, [](auto L) { return rot_modup_cl_kernel<L.value>; }), items * HE_NTT_CL_SIZE, cl_threads(ctx->log_n),
                        cl_fused_smem_bytes(ctx->log_n), st, tab, rg, mu, (const uint64_t *)ctx->d_tw, (const ModConst *)ctx->d_mc, ctx->log_n);
         ctx->launches++;
+        launch_keyswitch_many(ctx, jobs, count, level, rg.D, rg.d_w, rg.pcoef);
+        return;
+    }
+    if (ctx->bconv != HE_BCONV_INT8_TC && use_two_phase(ctx, items)) {
+        const int tiles_c = (ctx->n >> 6) / NTT2_TC, tiles_r = 64 / NTT2_TR;
+        const uint64_t *tw = ctx->d_tw;
+        const ModConst *mc = ctx->d_mc;
+        auto go = [&](auto L, auto NB) {
+            constexpr int LG = decltype(L)::value, NB1 = decltype(NB)::value;
+            launch_k(rot2_intt_rows_kernel<LG, LG - 6 - NB1>, (unsigned)(count * rg.nl * tiles_r), NTT2_THREADS, 0, st, tab, rg, tw, mc);
+            launch_k(rot2_intt_cols_kernel<LG>, (unsigned)(count * rg.nl * tiles_c), NTT2_THREADS, 0, st, rg, tw, mc);
+            launch_k(rot2_modup_cols_kernel<LG>, (unsigned)(items * tiles_c), NTT2_THREADS, 0, st, tab, rg, mu, tw, mc);
+            launch_k(rot2_modup_rows_kernel<LG, NB1>, (unsigned)(items * tiles_r), NTT2_THREADS, 0, st, rg, mu, tw, mc);
+        };
+        if (ctx->log_n == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
+        else if (ctx->log_n == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 4>{});
+        else go(std::integral_constant<int, 14>{}, std::integral_constant<int, 4>{});
+        ctx->launches += 4;
         launch_keyswitch_many(ctx, jobs, count, level, rg.D, rg.d_w, rg.pcoef);
         return;
     }

@@ -101,3 +101,27 @@ def test_keyswitch_variants_agree(he, log_n, qb, pb, dnum):
     for s in (1, 7, 40):
         assert torch.equal(results[0][0][s - 1], ctx.ct_export(ctx.rotate(ct, s)))
         assert torch.equal(results[0][1][s - 1], ctx.ct_export(ctx.rotate(cts[s - 1], s)))
+
+
+@pytest.mark.parametrize("log_n,qb,pb,dnum", [(12, [40, 20], [40], 2), (13, [60, 40, 40], [60], 3), (14, [60] + [40] * 6, [60, 60, 60], 3)])
+def test_modup_forms_agree(he, log_n, qb, pb, dnum):
+    """The ModUp of many ciphertexts in each NTT form (one CTA per limb-poly, or the two-phase
+    inverse and forward transforms of form 2): rotations of 40 different ciphertexts bit-identical
+    across forms and to single rotations."""
+    import torch
+
+    ctx = he.Context(log_n, qb, pb, dnum, seed=34)
+    rng = np.random.default_rng(log_n + 1)
+    level, scale = len(qb) - 1, 2.0**20 if log_n == 12 else 2.0**40
+    steps = [int(s) for s in rng.integers(1, ctx.slots, size=40)]
+    ctx.keygen(sorted(set(steps)))
+    cts = [ctx.encrypt(ctx.encode(torch.from_numpy(rng.uniform(-1, 1, ctx.slots)).cuda(), scale, level), 300 + i) for i in range(len(steps))]
+    got = []
+    for form in range(he.HE_NTT_FORMS):
+        ctx.set_ntt_form(form)
+        got.append(torch.stack([ctx.ct_export(o) for o in ctx.rotate_many(cts, steps)]))
+    ctx.set_ntt_form(-1)
+    for f in range(1, he.HE_NTT_FORMS):
+        assert torch.equal(got[f], got[0]), f"form {f}"
+    for i in (0, 13, 39):
+        assert torch.equal(got[0][i], ctx.ct_export(ctx.rotate(cts[i], steps[i])))
