@@ -1057,6 +1057,8 @@ def run_profile_case(args):
     ctx = he.Context(P.log_n, list(P.q_bits), list(P.p_bits), P.dnum, seed=0)
     if args.ntt_form >= 0:
         ctx.set_ntt_form(args.ntt_form)
+    if args.ks_variant >= 0:
+        ctx.set_keyswitch_variant(args.ks_variant)
     dev = torch.device("cuda", 0)
     case = args.profile_case
     X, r, _ = inputs.gradient_and_forward_n8192(seed=0)
@@ -1133,6 +1135,7 @@ def main():
     ap.add_argument("--profile-region", action="store_true",
                     help="bracket the timed graph replays with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--ntt-form", type=int, default=-1, help="with --profile-case: pin the NTT form of launches of many limb-polys")
+    ap.add_argument("--ks-variant", type=int, default=-1, help="with --profile-case: pin the transform variant of the many-rotation key switch")
     ap.add_argument("--profile-case", default=None, help="run one small workload between cudaProfilerStart/Stop for ncu (see run_profile_case)")
     ap.add_argument("--case-calls", type=int, default=1)
     ap.add_argument("--case-jobs", type=int, default=16)

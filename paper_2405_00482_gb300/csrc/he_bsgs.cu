@@ -26,7 +26,8 @@ struct BsgsGeom {
 };
 
 // grid (N / 256, nl, G): inner_g[comp][l][k] = sum_c sum_b ptM[c][gB+b][l][k] x_{c,b}[comp][l][k],
-// products accumulated in 128 bits and reduced (REDC, plaintext in Montgomery form) every 8 terms
+// products accumulated in 128 bits and reduced (REDC, plaintext in Montgomery form) every
+// lazy_terms(q) terms
 __global__ void __launch_bounds__(256) bsgs_mac_kernel(BsgsGeom bg, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
     const int64_t N = (int64_t)1 << logn;
@@ -39,13 +40,14 @@ __global__ void __launch_bounds__(256) bsgs_mac_kernel(BsgsGeom bg, const ModCon
     uint64_t r0 = 0, r1 = 0;
     u128 t0 = 0, t1 = 0;
     int pending = 0;
+    const int period = lazy_terms(q);
     for (int c = 0; c < bg.C; ++c) {
         for (int b = 0; b < bg.B; ++b) {
             const uint64_t *x = bg.X + ((int64_t)c * bg.B + b) * ct_w + (int64_t)l * N + k;
             const uint64_t p = __ldg(bg.pts + (((int64_t)c * mp + g * bg.B + b) * bg.ext + l) * N + k);
             t0 += (u128)__ldg(x) * p;
             t1 += (u128)__ldg(x + (int64_t)bg.nl * N) * p;
-            if (++pending == 8) {
+            if (++pending == period) {
                 r0 = add_mod(r0, redc128(t0, q, qinv), q);
                 r1 = add_mod(r1, redc128(t1, q, qinv), q);
                 t0 = t1 = 0;

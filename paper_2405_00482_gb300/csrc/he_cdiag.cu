@@ -44,7 +44,7 @@ struct OutTable {
 // contiguous run of 128 words, and each diagonal's fixed work (automorphism index, ciphertext
 // loads, gather address) is shared by 16 multiply-adds per lane.  Ciphertext words are used once
 // and loaded with an evict-first hint, so the weight table (read once per diagonal) stays in L2.
-// Products of residues below q < 2^61 are summed 8 at a time in 128 bits.
+// Products of residues below q are summed lazy_terms(q) at a time in 128 bits (8 for 61-bit primes).
 __global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts, int n_ct, int nl, const uint64_t *__restrict__ pt, int K,
                                                                     int k_base, uint64_t *pre, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts
     };
     uint32_t g = 1;
     int pending = 0;
+    const int period = lazy_terms(q);  // diagonals per reduction
     for (int i = 0; i < n_ct; ++i) {
         fetch(i, g);
         g = (uint32_t)(((uint64_t)g * 5u) & two_n_mask);
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(CD_WARPS * 32, 2) cdiag_mac_kernel(CtTable cts
             a0[kk] += (u128)c0n * pvn[kk];
             a1[kk] += (u128)c1n * pvn[kk];
         }
-        if (++pending == 8) {
+        if (++pending == period) {
 #pragma unroll
             for (int kk = 0; kk < CD_COLS; ++kk) {
                 r0[kk] = add_mod(r0[kk], redc128(a0[kk], q, qinv), q);

@@ -57,6 +57,12 @@ __device__ __forceinline__ uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, u
 __device__ __forceinline__ uint64_t redc128(u128 t, uint64_t q, uint64_t qinv) {
     return redc((uint64_t)(t >> 64), (uint64_t)t, q, qinv);
 }
+// How many products of two residues below q a 128-bit sum may take before redc128, whose input
+// must stay below q 2^64: 2^(64 - bits(q)) (8 for 61-bit primes, 2^24 for 40-bit ones; capped)
+__device__ __forceinline__ int lazy_terms(uint64_t q) {
+    const int b = 64 - __clzll((long long)q);
+    return 1 << (64 - b < 24 ? 64 - b : 24);
+}
 // a * bM 2^-64 mod q  (bM in Montgomery form -> canonical product)
 __device__ __forceinline__ uint64_t mont_mul(uint64_t a, uint64_t bM, uint64_t q, uint64_t qinv) {
     return redc128((u128)a * bM, q, qinv);

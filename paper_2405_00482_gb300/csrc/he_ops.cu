@@ -733,8 +733,8 @@ __global__ void batch_mdr_ntt_cl_kernel(const MMJob *__restrict__ jobs, BatchGeo
 // shared memory.  With VEC = 2 a lane's pair (k, k+1), k even, gathers the aligned pair
 // (src, src ^ 1) of each digit, so every load is 16 bytes; VEC = 1 halves the registers and
 // doubles the warps.  Each lane loads the next rotation step's operands while it computes the
-// current one.  Products are accumulated in 128 bits and reduced once per 8 terms
-// (8 q^2 < q 2^64 for q < 2^61).
+// current one.  Products are accumulated in 128 bits and reduced once per lazy_terms(q) terms
+// (8 for q < 2^61: 8 q^2 < q 2^64; 2^24 for the 40-bit primes).
 #define MM_THREADS 256
 
 __device__ __forceinline__ uint64_t fold(u128 t, uint64_t q, uint64_t qinv) { return redc128(t, q, qinv); }
@@ -805,7 +805,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // (fuse_keys_kernel) in place of the Galois key, so that
 //   acc_c[u][k] = redc(sum_i sum_d D[d][u][src_i(k)] F_i[d][c][u][k]),
 // the same residue as the two-level form: no per-step reduction and no second product.  The
-// 128-bit sums then take up to 64 products (< 64 q^2 < 2^128 for q < 2^61); their high word is
+// 128-bit sums then take up to 2^(128 - 2 bits(q)) products (64 for q < 2^61); their high word is
 // reduced mod q before the Montgomery step, whose input must stay below q 2^64.
 template <int NDIG, int VEC, int G, int S, bool GA, bool FK = false>
 __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const uint64_t *__restrict__ D, const uint64_t *__restrict__ pts,
@@ -831,6 +831,12 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
         for (int j = 0; j < VEC; ++j) t0[j] = t1[j] = tc[j] = 0;
         int pending = 0;
         constexpr int ND = NDIG > 0 ? NDIG : 8;
+        // steps per reduction of the 128-bit sums: each step adds one product of two residues
+        // (lazy_terms); with FK, ND products of two residues, and the sums are reduced with
+        // fold_wide, which only needs them below 2^128: 2^(128 - 2 bits(q)) / ND steps
+        const int period = lazy_terms(q);
+        const int qb = 64 - __clzll((long long)q);
+        const int fk_period = FK ? ((128 - 2 * qb < 24 ? 1 << (128 - 2 * qb) : 1 << 24) / ND) : 0;
         constexpr int SP = NDIG > 0 ? S : 0;
         if constexpr (SP > 0) {
             // slot (stage, field f, thread) at pipe[((stage F + f) MM_THREADS + tid) VEC]: fields
@@ -932,7 +938,7 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
 #pragma unroll
                         for (int j = 0; j < VEC; ++j) tc[j] += (u128)c0v[j] * pmc[j];
                     }
-                    if (++pending == 64 / ND) {
+                    if (++pending == fk_period) {
                         const uint64_t mu = mc[p].mu;
 #pragma unroll
                         for (int j = 0; j < VEC; ++j) {
@@ -972,7 +978,7 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                     t1[j] += (u128)fold(s1[j], q, qinv) * pmc[j];
                     if (inq) tc[j] += (u128)c0v[j] * pmc[j];
                 }
-                if (++pending == 8) {
+                if (++pending == period) {
 #pragma unroll
                     for (int j = 0; j < VEC; ++j) {
                         r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
@@ -1038,7 +1044,7 @@ __device__ __forceinline__ void mm_tile(const uint64_t *__restrict__ ct, const u
                     t1[j] += (u128)fold(s1[j], q, qinv) * pmc[j];
                     if (inq) tc[j] += (u128)c0v[j] * pmc[j];
                 }
-                if (++pending == 8) {
+                if (++pending == period) {
     #pragma unroll
                     for (int j = 0; j < VEC; ++j) {
                         r0[j] = add_mod(r0[j], fold(t0[j], q, qinv), q);
