@@ -607,7 +607,9 @@ def run_bsgs(ctx, he, inputs, P, args, flush, world, dev):
             pms.append(ctx.encode_matrix(plan, torch.from_numpy(Xj.T.copy()).to(dev), level))
             cts.append(ctx.encrypt_vector(plan, torch.from_numpy(rj).to(dev), P.scale, level, 91000 + i))
         outs = [[ctx.new_ct(level - 1)] for _ in jobs]
-        t = _event_times(lambda: [ctx.matmult(p, m, c, o) for p, m, c, o in zip(plans, pms, cts, outs)], max(3, min(args.steps, 10)), flush, warm=1)
+        # two untimed passes: the first tunes each matrix's loop kernel, the second builds and
+        # times its fused key tables (plain calls reuse the encodings)
+        t = _event_times(lambda: [ctx.matmult(p, m, c, o) for p, m, c, o in zip(plans, pms, cts, outs)], max(3, min(args.steps, 10)), flush, warm=2)
         out[name]["batched_jobs_as_plain_calls_per_sec"] = round(64e3 / statistics.median(t), 1)
         out[name]["batched_jobs_galois_keys"] = len(steps)
         out[name]["batched_jobs_key_bytes"] = len(steps) * key_bytes
