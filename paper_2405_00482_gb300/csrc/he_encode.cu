@@ -55,6 +55,17 @@ __device__ __forceinline__ void cmul(float4 v, float4 w, float4 &out) {
     out = make_float4(re.hi, re.lo, im.hi, im.lo);
 }
 
+// one radix-2 butterfly (u, v) <- (u + v w, u - v w) in double-float
+__device__ __forceinline__ void fft_bfly(float4 &u4, float4 &v4, float4 w) {
+    float4 v;
+    cmul(v4, w, v);
+    const float4 u = u4;
+    const df ur{u.x, u.y}, ui{u.z, u.w}, vr{v.x, v.y}, vi{v.z, v.w};
+    const df s0r = df_add(ur, vr), s0i = df_add(ui, vi), d0r = df_add(ur, df_neg(vr)), d0i = df_add(ui, df_neg(vi));
+    u4 = make_float4(s0r.hi, s0r.lo, s0i.hi, s0i.lo);
+    v4 = make_float4(d0r.hi, d0r.lo, d0i.hi, d0i.lo);
+}
+
 // Radix-2 decimation-in-time FFT of M = N/2 complex values in shared memory, input in
 // bit-reversed order: stage lg (1..log M) combines a[i1], a[i2 = i1 + 2^(lg-1)] with
 // w = tw[(i1 mod 2^(lg-1)) * M / 2^lg], tw[k] = exp(-2 pi i k / M) (its conjugate for
@@ -97,13 +108,7 @@ __device__ __forceinline__ void fft_pass(float4 *a, TWA tw, int logm, int s0, in
                     const int pos = (base + (k << s0)) & ((1 << (lg - 1)) - 1);
                     float4 w = tw.at(pos, lg);
                     if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
-                    float4 v;
-                    cmul(r[k + h], w, v);
-                    const float4 u = r[k];
-                    const df ur{u.x, u.y}, ui{u.z, u.w}, vr{v.x, v.y}, vi{v.z, v.w};
-                    const df s0r = df_add(ur, vr), s0i = df_add(ui, vi), d0r = df_add(ur, df_neg(vr)), d0i = df_add(ui, df_neg(vi));
-                    r[k] = make_float4(s0r.hi, s0r.lo, s0i.hi, s0i.lo);
-                    r[k + h] = make_float4(d0r.hi, d0r.lo, d0i.hi, d0i.lo);
+                    fft_bfly(r[k], r[k + h], w);
                 }
             }
         }
@@ -243,13 +248,7 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
                     const int pos = (j + (c << lg_ms)) & ((1 << (lg - 1)) - 1);
                     float4 w = tw[pos << (logm - lg)];
                     if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
-                    float4 v;
-                    cmul(r[c + h], w, v);
-                    const float4 u = r[c];
-                    const df ur{u.x, u.y}, ui{u.z, u.w}, vr{v.x, v.y}, vi{v.z, v.w};
-                    const df s0r = df_add(ur, vr), s0i = df_add(ui, vi), d0r = df_add(ur, df_neg(vr)), d0i = df_add(ui, df_neg(vi));
-                    r[c] = make_float4(s0r.hi, s0r.lo, s0i.hi, s0i.lo);
-                    r[c + h] = make_float4(d0r.hi, d0r.lo, d0i.hi, d0i.lo);
+                    fft_bfly(r[c], r[c + h], w);
                 }
             }
         }
