@@ -90,8 +90,9 @@ void he_ctx_destroy(he_ctx *ctx);
  * any context of the family are seen by all), with its own scratch, so calls on the two streams
  * can run concurrently.  Plaintext matrices and weight matrices made on one context of the
  * family may be encoded into and used on any other; the caller orders the streams (a matrix
- * encoded on one stream and used on another needs an event between them) and frees a matrix
- * before the context that made it.  The family's tables and keys are freed with its last
+ * encoded on one stream and used on another needs an event between them), makes no two calls on
+ * one matrix from two host threads at once (a call may tune the matrix or build its fused key
+ * tables) and frees a matrix before the context that made it.  The family's tables and keys are freed with its last
  * context; forks and parent may be destroyed in any order.  he_keygen on one context may run
  * while the others work (the key table is guarded).  Waits for the parent's stream once. */
 int he_ctx_fork(he_ctx *parent, void *cuda_stream, he_ctx **out);
@@ -349,7 +350,8 @@ int he_batch_set_variant(he_batch *batch, int v);
  * allocation-free paths.  he_ptmat_key_fusion reports state (0 not tried, 1 in use, -1 not
  * used), the fused form's variant and, when ms is not NULL, its timed ms per variant
  * (HE_MM_MAX_VARIANTS entries, 0 for variants without a fused form);
- * he_ptmat_set_key_fusion(pm, 0, -1) frees the tables and keeps them off for pm;
+ * he_ptmat_set_key_fusion(pm, 0, -1) frees the tables (after pm's context's stream: no graph
+ * captured with them may be replayed afterwards) and keeps them off for pm;
  * (pm, 1, -1) makes pm eligible again; (pm, 1, v) pins the fused form with loop-kernel variant v
  * (one with cp.async stages, he_loop_variant_shape) for pm whatever the context's mode: the
  * tables are built at pm's next MatMult (not under capture) and used without timing.  HE_EINVAL
