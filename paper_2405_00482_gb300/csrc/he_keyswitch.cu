@@ -320,15 +320,15 @@ __global__ void __launch_bounds__(NTT2_THREADS, 8) ks2_conv_cols_kernel(KsGeom k
         cv + (int64_t)item * N, c0, TwGlobal{twiddles(d_tw, pl, 0, LOGN)}, q);
 }
 
-template <int LOGN, int NB1>
-__global__ void __launch_bounds__(NTT2_THREADS) ks2_conv_rows_kernel(uint64_t *cv, int nl, ModDownConst md, const uint64_t *__restrict__ d_tw,
-                                                                   const ModConst *__restrict__ mc) {
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) ks2_conv_rows_kernel(uint64_t *cv, int nl, ModDownConst md, const uint64_t *__restrict__ d_tw,
+                                                                      const ModConst *__restrict__ mc) {
     HE_GRID_DEP();
     constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
-    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    __shared__ uint64_t sm[ntt2_frows_smem_words(LOGN - 6)];
     const int item = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
     const int pl = md.q_prime[item % nl];
-    ntt2_fwd_rows<LOGN, NB1>(sm, cv + (int64_t)item * N, b0, TwGlobal{twiddles(d_tw, pl, 0, LOGN)}, mc[pl].q, mc[pl].mu);
+    ntt2_fwd_rows<LOGN>(sm, cv + (int64_t)item * N, b0, TwGlobal{twiddles(d_tw, pl, 0, LOGN)}, mc[pl].q, mc[pl].mu);
 }
 
 // the four launches of transform variant 2 (log N = 12, 13, 14)
@@ -340,7 +340,7 @@ void ks2_transforms(int logn, const KsGeom &kg, uint64_t *cv, const ModDownConst
         launch_k(ks2_pinv_rows_kernel<LG, LG - 6 - NB1>, (unsigned)(np * tiles_r), NTT2_THREADS, 0, st, kg, md, tw, mc);
         launch_k(ks2_pinv_cols_kernel<LG>, (unsigned)(np * tiles_c), NTT2_THREADS, 0, st, kg, md, tw, mc);
         launch_k(ks2_conv_cols_kernel<LG>, (unsigned)(nq * tiles_c), NTT2_THREADS, 0, st, kg, cv, md, tw, mc);
-        launch_k(ks2_conv_rows_kernel<LG, NB1>, (unsigned)(nq * tiles_r), NTT2_THREADS, 0, st, cv, kg.nl, md, tw, mc);
+        launch_k(ks2_conv_rows_kernel<LG>, (unsigned)(nq * tiles_r), NTT2_THREADS, 0, st, cv, kg.nl, md, tw, mc);
     };
     if (logn == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
     else if (logn == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 4>{});

@@ -174,15 +174,15 @@ __global__ void __launch_bounds__(NTT2_THREADS, 8) ntt2_cols_kernel(const void *
     }
 }
 
-template <int LOGN, int NB1>
-__global__ void __launch_bounds__(NTT2_THREADS) ntt2_rows_kernel(uint64_t *data, int64_t gs, LimbMap map, const uint64_t *__restrict__ d_tw,
-                                                               const ModConst *__restrict__ mc) {
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) ntt2_rows_kernel(uint64_t *data, int64_t gs, LimbMap map, const uint64_t *__restrict__ d_tw,
+                                                                  const ModConst *__restrict__ mc) {
     HE_GRID_DEP();
     constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
-    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    __shared__ uint64_t sm[ntt2_frows_smem_words(LOGN - 6)];
     const int poly = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
     const int g = poly / map.n, l = poly % map.n, p = map.prime[l];
-    ntt2_fwd_rows<LOGN, NB1>(sm, data + g * gs + (int64_t)l * N, b0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, mc[p].q, mc[p].mu);
+    ntt2_fwd_rows<LOGN>(sm, data + g * gs + (int64_t)l * N, b0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, mc[p].q, mc[p].mu);
 }
 
 // inverse: rows (in to out), then columns in place with the factor N^-1
@@ -279,7 +279,7 @@ static void launch_two_phase(he_ctx *ctx, const void *in, int64_t in_gs, uint64_
     ctx->launches += 2;
     auto go = [&](auto L, auto NB1) {
         launch_k(ntt2_cols_kernel<decltype(L)::value, I64>, cols, NTT2_THREADS, 0, ctx->stream, in, in_gs, out, out_gs, map, tw, mc, to_mont);
-        launch_k(ntt2_rows_kernel<decltype(L)::value, decltype(NB1)::value>, rows, NTT2_THREADS, 0, ctx->stream, out, out_gs, map, tw, mc);
+        launch_k(ntt2_rows_kernel<decltype(L)::value>, rows, NTT2_THREADS, 0, ctx->stream, out, out_gs, map, tw, mc);
     };
     if (logn == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
     else if (logn == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 4>{});

@@ -129,7 +129,7 @@ __device__ __forceinline__ void ntt_fwd_radix(uint64_t (&r)[1 << NB], TWA tw, ui
 // A pass over sets [set0, set1) of stages s0..s0+NB-1; element x lives at s[SIDX(x - off)].
 // The whole transform in one CTA uses set0 = 0, set1 = N >> NB, off = 0; a cluster member
 // holding the slice [off, off + N/8) uses the sets whose elements fall in its slice.
-template <int NB, class TWA>
+template <int NB, class TWA, bool CORR = true>
 __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, int logn, int s0, bool last, int set0 = 0, int set1 = -1,
                                              int off = 0) {
     constexpr int E = 1 << NB;
@@ -150,8 +150,8 @@ __device__ __forceinline__ void ntt_fwd_pass(uint64_t *s, TWA tw, uint64_t q, in
         for (int k = 0; k < E; ++k) r[k] = s[sb + SIDX(k << lg_tl)];
         // element x = base + (k << lg_tl) meets twiddle m + (x >> (lg_t0 - j + 1)) at stage
         // s0 + j, which is m + (g << j) + (k >> (NB - j))
-        ntt_fwd_radix<NB>(r, tw, q, s0, g);
-        if (last) {
+        ntt_fwd_radix<NB, TWA, CORR>(r, tw, q, s0, g);
+        if (CORR && last) {
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 uint64_t v = r[k];
@@ -239,6 +239,8 @@ __host__ __device__ constexpr int ntt2_row_pitch(int lb) {
     return ((1 << lb) + (1 << lb) / 8) % 16 == 0 ? (1 << lb) + (1 << lb) / 8 + 8 : (1 << lb) + (1 << lb) / 8;
 }
 __host__ __device__ constexpr int ntt2_rows_smem_words(int lb) { return NTT2_TR * ntt2_row_pitch(lb); }
+// the forward row phase's staged slice: NTT2_TR rows with one pad word per 32
+__host__ __device__ constexpr int ntt2_frows_smem_words(int lb) { return NTT2_TR * (1 << lb) + NTT2_TR * (1 << lb) / 32; }
 __device__ __forceinline__ int ntt2_at(int m) { return m + (m >> 3); }
 
 // canonical residue of v 2^64 mod q for a signed v (Shoup product by 2^64 mod q of |v|)
@@ -275,47 +277,35 @@ __device__ __forceinline__ void ntt2_fwd_cols(uint64_t *sm, LOAD load, uint64_t 
 }
 
 // forward stages 6 .. log N - 1 of rows b0 .. b0 + NTT2_TR - 1 of one limb-poly, in place;
-// canonical outputs
-template <int LOGN, int NB1>
+// canonical outputs.  The rows are staged into shared memory (sm: ntt2_rows_smem_words) as the
+// slice [b0 R, (b0 + NTT2_TR) R) of the transform and run through the one-CTA form's passes of up
+// to three stages (ntt_fwd_pass over the sets whose elements fall in the slice, as a cluster
+// member does), so a thread holds 8 values at a time.
+template <int LOGN>
 __device__ __forceinline__ void ntt2_fwd_rows(uint64_t *sm, uint64_t *poly, int b0, TwGlobal tw, uint64_t q, uint64_t mu) {
-    constexpr int LB = LOGN - 6, R = 1 << LB, NB2 = LB - NB1, RP = ntt2_row_pitch(LB);
-    constexpr int S1 = R >> NB1, S2 = R >> NB2;  // sets per row of the two passes
-    uint64_t *row0 = poly + (int64_t)b0 * R;
-    const bool corr = q >= HE_NTT_NOCORR_Q;
-    // stages 6 .. 5 + NB1 on the elements m = j + S1 i of row b (group b at stage 6)
-    for (int set = threadIdx.x; set < NTT2_TR * S1; set += NTT2_THREADS) {
-        const int rb = set / S1, j = set % S1;
-        uint64_t v[1 << NB1];
-#pragma unroll
-        for (int i = 0; i < (1 << NB1); ++i) v[i] = row0[(int64_t)rb * R + j + S1 * i];
-        if (corr) ntt_fwd_radix<NB1, TwGlobal, true>(v, tw, q, 6, b0 + rb);
-        else ntt_fwd_radix<NB1, TwGlobal, false>(v, tw, q, 6, b0 + rb);
-#pragma unroll
-        for (int i = 0; i < (1 << NB1); ++i) sm[rb * RP + ntt2_at(j + S1 * i)] = v[i];
-    }
+    constexpr int LB = LOGN - 6, R = 1 << LB, LEN = NTT2_TR * R;
+    const int off = b0 * R;  // a multiple of 32, so SIDX splits over the offset
+    stage_in(sm, poly + off, LEN, [](uint64_t v) { return v; });
     __syncthreads();
-    // the last NB2 stages on 2^NB2 consecutive elements m = 2^NB2 e + i: group b 2^NB1 + e
-    const uint64_t two_q = 2 * q;
-    for (int set = threadIdx.x; set < NTT2_TR * S2; set += NTT2_THREADS) {
-        const int rb = set / S2, e = set % S2;
-        uint64_t v[1 << NB2];
+    const bool corr = q >= HE_NTT_NOCORR_Q;
 #pragma unroll
-        for (int i = 0; i < (1 << NB2); ++i) v[i] = sm[rb * RP + ntt2_at((e << NB2) + i)];
-        if (corr) {  // values below 4q
-            ntt_fwd_radix<NB2, TwGlobal, true>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
-#pragma unroll
-            for (int i = 0; i < (1 << NB2); ++i) {
-                const uint64_t x = v[i] >= two_q ? v[i] - two_q : v[i];
-                v[i] = x >= q ? x - q : x;
-            }
-        } else {  // values below (1 + 2 log N) q
-            ntt_fwd_radix<NB2, TwGlobal, false>(v, tw, q, 6 + NB1, ((b0 + rb) << NB1) + e);
-#pragma unroll
-            for (int i = 0; i < (1 << NB2); ++i) v[i] = reduce_barrett(v[i], q, mu);
+    for (int s0 = 6; s0 < LOGN; s0 += 3) {
+        const bool last = s0 + 3 >= LOGN;
+        if (LOGN - s0 >= 3) {
+            if (corr) ntt_fwd_pass<3, TwGlobal, true>(sm, tw, q, LOGN, s0, last, off >> 3, (off + LEN) >> 3, off);
+            else ntt_fwd_pass<3, TwGlobal, false>(sm, tw, q, LOGN, s0, false, off >> 3, (off + LEN) >> 3, off);
+        } else if (LOGN - s0 == 2) {
+            if (corr) ntt_fwd_pass<2, TwGlobal, true>(sm, tw, q, LOGN, s0, last, off >> 2, (off + LEN) >> 2, off);
+            else ntt_fwd_pass<2, TwGlobal, false>(sm, tw, q, LOGN, s0, false, off >> 2, (off + LEN) >> 2, off);
+        } else {
+            if (corr) ntt_fwd_pass<1, TwGlobal, true>(sm, tw, q, LOGN, s0, last, off >> 1, (off + LEN) >> 1, off);
+            else ntt_fwd_pass<1, TwGlobal, false>(sm, tw, q, LOGN, s0, false, off >> 1, (off + LEN) >> 1, off);
         }
-        ulonglong2 *d = reinterpret_cast<ulonglong2 *>(row0 + (int64_t)rb * R + (e << NB2));
-#pragma unroll
-        for (int i = 0; i < (1 << NB2) / 2; ++i) d[i] = make_ulonglong2(v[2 * i], v[2 * i + 1]);
+    }
+    // without the lazy correction the values are below (1 + 2 log N) q: one Barrett step
+    for (int k = threadIdx.x; k < LEN; k += NTT2_THREADS) {
+        const uint64_t v = sm[SIDX(k)];
+        poly[off + k] = corr ? v : reduce_barrett(v, q, mu);
     }
 }
 

@@ -557,18 +557,18 @@ __global__ void __launch_bounds__(NTT2_THREADS, 8) rot2_modup_cols_kernel(const 
         dst, c0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, t);
 }
 
-template <int LOGN, int NB1>
-__global__ void __launch_bounds__(NTT2_THREADS) rot2_modup_rows_kernel(RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
-                                                                     const ModConst *__restrict__ mc) {
+template <int LOGN>
+__global__ void __launch_bounds__(NTT2_THREADS, 8) rot2_modup_rows_kernel(RotGeom rg, ModUpConst mu, const uint64_t *__restrict__ d_tw,
+                                                                        const ModConst *__restrict__ mc) {
     HE_GRID_DEP();
     constexpr int N = 1 << LOGN, TILES = 64 / NTT2_TR;
-    __shared__ uint64_t sm[ntt2_rows_smem_words(LOGN - 6)];
+    __shared__ uint64_t sm[ntt2_frows_smem_words(LOGN - 6)];
     const int item = blockIdx.x / TILES, b0 = (blockIdx.x % TILES) * NTT2_TR;
     const int per = mu.ndig * mu.ext, j = item / per, d = (item % per) / mu.ext, u = item % mu.ext;
     const int lo = d * mu.alpha, hi = lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq;
     if (u >= lo && u < hi) return;  // copied, already in NTT form
     const int p = mu.ext_prime[u];
-    ntt2_fwd_rows<LOGN, NB1>(sm, rg.D + j * rg.d_w + ((int64_t)d * mu.ext + u) * N, b0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, mc[p].q, mc[p].mu);
+    ntt2_fwd_rows<LOGN>(sm, rg.D + j * rg.d_w + ((int64_t)d * mu.ext + u) * N, b0, TwGlobal{twiddles(d_tw, p, 0, LOGN)}, mc[p].q, mc[p].mu);
 }
 
 // ModUp of the jobs' c1 (NTT form) as clusters, item (j, d, u), the inverse NTT inside: for
@@ -1809,7 +1809,7 @@ void launch_rotate_many(he_ctx *ctx, const RotJob *jobs, int count, int level, u
             launch_k(rot2_intt_rows_kernel<LG, LG - 6 - NB1>, (unsigned)(count * rg.nl * tiles_r), NTT2_THREADS, 0, st, tab, rg, tw, mc);
             launch_k(rot2_intt_cols_kernel<LG>, (unsigned)(count * rg.nl * tiles_c), NTT2_THREADS, 0, st, rg, tw, mc);
             launch_k(rot2_modup_cols_kernel<LG>, (unsigned)(items * tiles_c), NTT2_THREADS, 0, st, tab, rg, mu, tw, mc);
-            launch_k(rot2_modup_rows_kernel<LG, NB1>, (unsigned)(items * tiles_r), NTT2_THREADS, 0, st, rg, mu, tw, mc);
+            launch_k(rot2_modup_rows_kernel<LG>, (unsigned)(items * tiles_r), NTT2_THREADS, 0, st, rg, mu, tw, mc);
         };
         if (ctx->log_n == 12) go(std::integral_constant<int, 12>{}, std::integral_constant<int, 3>{});
         else if (ctx->log_n == 13) go(std::integral_constant<int, 13>{}, std::integral_constant<int, 4>{});
