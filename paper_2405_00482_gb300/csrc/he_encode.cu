@@ -5,6 +5,8 @@
 //   z at t  =  sum_{k<N/2} (c_k zeta^k) w^(t k),  w = exp(2 pi i / (N/2)),
 // so encoding is an inverse length-N/2 DFT followed by a twist by zeta^-k, and decoding the
 // forward one.  Slot j sits at t_j = (5^j mod 2N - 1) / 4.
+#include <climits>
+
 #include "he_internal.cuh"
 #include "he_ntt.cuh"
 
@@ -41,11 +43,83 @@ __device__ __forceinline__ df df_mul(df a, df b) {
     e = __fmaf_rn(a.lo, b.hi, e);
     return quick_two_sum(p, e);
 }
+// hi = x rounded to float, lo = the remainder x - hi rounded to float.  GB300's FP64 pipe is
+// about 1.7 lanes per clock per SM with a 64-cycle dependent latency, so for 2^-60 <= |x| < 2^101
+// both come from the significand with integer operations: hi is its top 24 bits rounded to
+// nearest (ties to even; a carry out raises the exponent), and the remainder, at most 2^28 units
+// of x's last place, is rounded by the int -> float conversion and scaled by that place's value
+// (a normal float in this range).  Bit-identical to the two FP64 conversions, which serve the rest.
 __device__ __forceinline__ df df_from(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E >= 1023 - 60 && E <= 1023 + 100) {
+        const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        unsigned long long Mh = M >> 29;
+        const unsigned long long r = M & ((1ull << 29) - 1);
+        Mh += (r > (1ull << 28)) || (r == (1ull << 28) && (Mh & 1));
+        const int rem = (int)((long long)M - (long long)(Mh << 29));
+        const unsigned sgn = (unsigned)(b >> 63) << 31;
+        const float hi = __uint_as_float(sgn | ((unsigned)(E - 896 + (int)(Mh >> 24)) << 23) | (unsigned)(Mh & 0x7FFFFF));
+        const float lo = __fmul_rn(__int2float_rn(sgn ? -rem : rem), __uint_as_float((unsigned)(E - 1075 + 127) << 23));
+        return {hi, lo};
+    }
     const float h = __double2float_rn(x);
     return {h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+// u as a double, rounded to nearest (ties to even), with integer operations only: the leading
+// bit's position is the exponent, the 53 bits from it the significand
+__device__ __forceinline__ double u64_to_double_rn(unsigned long long u, bool negative) {
+    if (!u) return 0.0;
+    int e = 63 - __clzll((long long)u);
+    unsigned long long mant;
+    if (e <= 52) {
+        mant = u << (52 - e);
+    } else {
+        const int sh = e - 52;
+        mant = u >> sh;
+        const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        mant += (rem > half) || (rem == half && (mant & 1));
+        if (mant >> 53) {
+            mant >>= 1;
+            ++e;
+        }
+    }
+    return __longlong_as_double((long long)(((unsigned long long)negative << 63) | ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull)));
+}
+// a float as a double, exactly: for normal floats the exponent re-biased and the significand
+// widened with integer operations (no FP64-pipe conversion); zero, subnormals, inf and NaN by the cast
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned b = __float_as_uint(f), e = (b >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)f;
+    return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+__device__ __forceinline__ double df_to(df a) { return f2d_exact(a.hi) + f2d_exact(a.lo); }
+
+// Rounding to an integer without the FP64 pipe (on GB300 a small fraction of the FP32 rate, and
+// the encoders round every coefficient).  rint_f: nearest integer, ties to even (below 2^23 by
+// adding and removing 2^23, which leaves units in the last place; above it x is an integer).
+__device__ __forceinline__ float rint_f(float x) {
+    const float m = copysignf(8388608.0f, x);
+    return fabsf(x) < 8388608.0f ? __fsub_rn(__fadd_rn(x, m), m) : x;
+}
+// an integral float as int64, from its exponent and significand (saturating beyond 2^63)
+__device__ __forceinline__ long long f2ll_integral(float f) {
+    const unsigned b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xFFu) - 150;  // |f| = significand * 2^e
+    if (e > 39) return (int)b < 0 ? LLONG_MIN : LLONG_MAX;
+    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const long long v = e >= 0 ? m << e : (e > -24 ? m >> -e : 0);  // e < 0: the low bits are zero
+    return (int)b < 0 ? -v : v;
+}
+// nearest integer to the double-float value hi + lo: rint(hi) plus the rounded remainder
+// (hi - rint(hi), exact, plus lo).  Above 2^24 hi is even and the remainder is lo itself, so ties go
+// to even as in exact rounding; below, the float remainder can pick the other neighbour within
+// 2^-24 of a half-integer, far inside the transform's own error (relative ~2^-44).
+__device__ __forceinline__ long long df_round_ll(df a) {
+    const float rh = rint_f(a.hi);
+    return f2ll_integral(rh) + f2ll_integral(rint_f(__fadd_rn(__fsub_rn(a.hi, rh), a.lo)));
+}
 
 // complex value in shared memory: (re.hi, re.lo, im.hi, im.lo)
 __device__ __forceinline__ void cmul(float4 v, float4 w, float4 &out) {
@@ -64,6 +138,11 @@ __device__ __forceinline__ void fft_bfly(float4 &u4, float4 &v4, float4 w) {
     const df s0r = df_add(ur, vr), s0i = df_add(ui, vi), d0r = df_add(ur, df_neg(vr)), d0i = df_add(ui, df_neg(vi));
     u4 = make_float4(s0r.hi, s0r.lo, s0i.hi, s0i.lo);
     v4 = make_float4(d0r.hi, d0r.lo, d0i.hi, d0i.lo);
+}
+
+__device__ __forceinline__ float4 shfl4(float4 v, int src) {
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src), __shfl_sync(0xffffffffu, v.z, src),
+                       __shfl_sync(0xffffffffu, v.w, src));
 }
 
 // Radix-2 decimation-in-time FFT of M = N/2 complex values in shared memory, input in
@@ -152,8 +231,8 @@ __global__ void encode_kernel(const double *__restrict__ slots, int64_t n_slots,
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
         float4 c;
         cmul(a[k], twist[k], c);  // times zeta^-k
-        o[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
-        o[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
+        o[k] = df_round_ll(df_mul(df{c.x, c.y}, f));
+        o[k + M] = df_round_ll(df_mul(df{c.z, c.w}, f));
     }
 }
 
@@ -230,30 +309,49 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
             default: fft_pass<1>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
         }
     }
+    // The cross-CTA stages: the CL elements j + c MS of an offset j go through CLG radix-2
+    // stages, stage st pairing c and c + 2^st.  2^(CLG-1) adjacent lanes share an offset, each
+    // holding the pair of one butterfly per stage: lane p holds c = ins(p, st) and c + 2^st (bit st
+    // inserted into p), and between stages the lanes swap elements by warp shuffles, so every
+    // thread of the CTA takes part (MS / 2 butterflies per stage).  The butterfly of c uses twiddle
+    // position j + g MS with g = c mod 2^st = p mod 2^st; the thread's twiddles of its first offset
+    // are loaded before the cluster barrier, their latency overlapping the wait.
+    constexpr int T = CL > 1 ? CL / 2 : 1;
+    const int per = MS >> CLG, p = threadIdx.x & (T - 1), lane_base = (threadIdx.x & 31) & ~(T - 1);
+    auto ins = [](int v, int st) { return (v & ((1 << st) - 1)) | ((v >> st) << (st + 1)); };
+    float4 wc[CLG > 0 ? CLG : 1];
+    auto cross_tw = [&](int j) {
+#pragma unroll
+        for (int st = 0; st < CLG; ++st) wc[st] = tw[(j + ((p & ((1 << st) - 1)) << lg_ms)) << (logm - lg_ms - st - 1)];
+    };
+    // MS / 2 is a multiple of 32 and of blockDim.x (MS >= 64 for the rings that use clusters), so
+    // whole warps run each iteration and the shuffles see every lane
+    if ((int)threadIdx.x < per * T) cross_tw(rank * per + (int)(threadIdx.x / T));
     cl.sync();
-    float4 *rem[CL];
-#pragma unroll
-    for (int c = 0; c < CL; ++c) rem[c] = cl.map_shared_rank(a, c);
-    const int per = MS >> CLG;
-    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
-        float4 r[CL];
-#pragma unroll
-        for (int c = 0; c < CL; ++c) r[c] = rem[c][j];
+    for (int t = threadIdx.x; t < per * T; t += blockDim.x) {
+        const int j = rank * per + t / T;
+        if (t != (int)threadIdx.x) cross_tw(j);
+        int c_lo = ins(p, 0);
+        float4 x0 = cl.map_shared_rank(a, c_lo)[j], x1 = cl.map_shared_rank(a, c_lo | 1)[j];
 #pragma unroll
         for (int st = 0; st < CLG; ++st) {
-            const int h = 1 << st, lg = lg_ms + st + 1;
-#pragma unroll
-            for (int c = 0; c < CL; ++c) {
-                if ((c & (2 * h - 1)) < h) {
-                    const int pos = (j + (c << lg_ms)) & ((1 << (lg - 1)) - 1);
-                    float4 w = tw[pos << (logm - lg)];
-                    if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
-                    fft_bfly(r[c], r[c + h], w);
-                }
+            if (st > 0) {
+                // this lane's new pair from the lanes holding them at stage st - 1 (element c sits
+                // at lane c with bit st - 1 removed, in slot bit st - 1 of c)
+                const int lo = ins(p, st), hi = lo | (1 << st);
+                const int src_lo = lane_base + ((lo & ((1 << (st - 1)) - 1)) | ((lo >> st) << (st - 1)));
+                const int src_hi = lane_base + ((hi & ((1 << (st - 1)) - 1)) | ((hi >> st) << (st - 1)));
+                const float4 a0 = shfl4(x0, src_lo), a1 = shfl4(x1, src_lo), b0 = shfl4(x0, src_hi), b1 = shfl4(x1, src_hi);
+                x0 = (lo >> (st - 1)) & 1 ? a1 : a0;
+                x1 = (hi >> (st - 1)) & 1 ? b1 : b0;
+                c_lo = lo;
             }
+            float4 w = wc[st];
+            if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
+            fft_bfly(x0, x1, w);
         }
-#pragma unroll
-        for (int c = 0; c < CL; ++c) rem[c][j] = r[c];
+        cl.map_shared_rank(a, c_lo)[j] = x0;
+        cl.map_shared_rank(a, c_lo | (1 << (CLG > 0 ? CLG - 1 : 0)))[j] = x1;
     }
     cl.sync();
 }
@@ -297,17 +395,24 @@ struct VectorSrc {
 template <int CLG, int RL, int LOGN, class SRC>
 __global__ void encode_cl_kernel(SRC src, double scale, const float4 *__restrict__ tw, const float4 *__restrict__ twist,
                                  const int32_t *__restrict__ slot_pos, int64_t *out, int logn_rt) {
-    HE_GRID_DEP();
+    HE_GRID_LAUNCH();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
     const int per = M >> CLG;
+    // the context's tables before the wait: the twiddle copy and the first two slot positions
     fft_tw_issue<CLG>(a, tw, logm);
+    int pos_pre[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        if ((int)threadIdx.x + r * (int)blockDim.x < per) pos_pre[r] = slot_pos[rank * per + threadIdx.x + r * blockDim.x];
+    HE_GRID_WAIT();
     cl.sync();  // every CTA of the cluster has started before its shared memory is written
-    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
-        const int bt = __brev(slot_pos[j]) >> (32 - logm);
+    int r = 0;
+    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x, ++r) {
+        const int bt = __brev(r == 0 ? pos_pre[0] : (r == 1 ? pos_pre[1] : slot_pos[j])) >> (32 - logm);
         const df v = df_from(src(item, j));
         cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(v.hi, v.lo, 0.f, 0.f);
     }
@@ -319,8 +424,8 @@ __global__ void encode_cl_kernel(SRC src, double scale, const float4 *__restrict
         const int k = off + i;
         float4 c;
         cmul(a[i], twist[k], c);
-        o[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
-        o[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
+        o[k] = df_round_ll(df_mul(df{c.x, c.y}, f));
+        o[k + M] = df_round_ll(df_mul(df{c.z, c.w}, f));
     }
 }
 
@@ -334,7 +439,7 @@ __global__ void encode_cl_kernel(SRC src, double scale, const float4 *__restrict
 template <int CLG, int RL, int LOGN, class SRC>
 __global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const float4 *__restrict__ tw, const float4 *__restrict__ twist,
                                       const int32_t *__restrict__ slot_pos, int64_t *out, int logn_rt) {
-    HE_GRID_DEP();
+    HE_GRID_LAUNCH();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
@@ -343,10 +448,16 @@ __global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const fl
     const int ix = 2 * pair, iy = 2 * pair + 1;
     const bool has_y = iy < count;
     const int per = M >> CLG;
-    fft_tw_issue<CLG>(a, tw, logm);
+    fft_tw_issue<CLG>(a, tw, logm);  // the context's tables before the wait, as in encode_cl_kernel
+    int pos_pre[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        if ((int)threadIdx.x + r * (int)blockDim.x < per) pos_pre[r] = slot_pos[rank * per + threadIdx.x + r * blockDim.x];
+    HE_GRID_WAIT();
     cl.sync();  // every CTA of the cluster has started before its shared memory is written
-    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
-        const int bt = __brev(slot_pos[j]) >> (32 - logm);
+    int r = 0;
+    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x, ++r) {
+        const int bt = __brev(r == 0 ? pos_pre[0] : (r == 1 ? pos_pre[1] : slot_pos[j])) >> (32 - logm);
         const df vx = df_from(src(ix, j)), vy = df_from(has_y ? src(iy, j) : 0.0);
         cl.map_shared_rank(a, bt >> lg_ms)[bt & (MS - 1)] = make_float4(vx.hi, vx.lo, vy.hi, vy.lo);
     }
@@ -363,12 +474,12 @@ __global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const fl
         const df yr = df_add(zi, mi), yi = df_add(mr, df_neg(zr));
         float4 c;
         cmul(make_float4(xr.hi, xr.lo, xi.hi, xi.lo), twist[k], c);
-        ox[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
-        ox[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
+        ox[k] = df_round_ll(df_mul(df{c.x, c.y}, f));
+        ox[k + M] = df_round_ll(df_mul(df{c.z, c.w}, f));
         if (has_y) {
             cmul(make_float4(yr.hi, yr.lo, yi.hi, yi.lo), twist[k], c);
-            oy[k] = __double2ll_rn(df_to(df_mul(df{c.x, c.y}, f)));
-            oy[k + M] = __double2ll_rn(df_to(df_mul(df{c.z, c.w}, f)));
+            oy[k] = df_round_ll(df_mul(df{c.x, c.y}, f));
+            oy[k + M] = df_round_ll(df_mul(df{c.z, c.w}, f));
         }
     }
     cl.sync();  // the other CTAs read this one's shared memory until here
@@ -381,14 +492,28 @@ __global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const fl
 // row block `item` (Sec. 4.3), y[row] = sum over s < nb/m' of slot[b nb + t + s m'] (minus the
 // mask), each row by one thread in the order s = 0, 1, ... of lazy_ras_kernel, over the same
 // slot values, so the same doubles without the slot array.
+// Each epilogue's slot positions of its first two iterations are read by prefetch() before the
+// kernel waits for its predecessor.
+struct EpiPre {
+    int pos[2];
+};
 struct DecodeSlots {
     double *out;
+    __device__ __forceinline__ EpiPre prefetch(int, int rank, int clg, int M, int, const int32_t *__restrict__ slot_pos) const {
+        EpiPre pre;
+        const int per = M >> clg;
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if ((int)threadIdx.x + r * (int)blockDim.x < per) pre.pos[r] = slot_pos[rank * per + threadIdx.x + r * blockDim.x];
+        return pre;
+    }
     __device__ __forceinline__ void operator()(cg::cluster_group &cl, const float4 *a, int item, int rank, int clg, int M, int lg_ms,
-                                               const int32_t *__restrict__ slot_pos, double inv) const {
+                                               const int32_t *__restrict__ slot_pos, double inv, double *, const EpiPre &pre) const {
         double *o = out + (int64_t)item * M;
         const int per = M >> clg, MS = 1 << lg_ms;
-        for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
-            const int pos = slot_pos[j];
+        int r = 0;
+        for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x, ++r) {
+            const int pos = r == 0 ? pre.pos[0] : (r == 1 ? pre.pos[1] : slot_pos[j]);
             const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
             o[j] = df_to(df{v.x, v.y}) * inv;
         }
@@ -399,23 +524,73 @@ struct DecodeRas {
     const double *mask;  // [row blocks][slots] or null
     double *y;
     int lm, lnb, ls, lmb;  // log2 of m', nb, slots, mb
-    __device__ __forceinline__ void operator()(cg::cluster_group &cl, const float4 *a, int item, int rank, int clg, int, int lg_ms,
-                                               const int32_t *__restrict__ slot_pos, double inv) const {
-        const int MS = 1 << lg_ms;
-        const int64_t terms = p.nb >> lm;
-        for (int64_t rem = (int64_t)rank * blockDim.x + threadIdx.x; rem < p.mb; rem += (int64_t)blockDim.x << clg) {
-            const int64_t row = ((int64_t)item << lmb) + rem;
-            if (row >= p.m) break;
-            const int64_t base = ((rem >> lm) << lnb) + (rem & (p.m_prime - 1));
-            double acc = 0.0;
-            for (int64_t s = 0; s < terms; ++s) {
-                const int64_t j = base + (s << lm);
-                const int pos = slot_pos[j];
-                const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
-                const double val = df_to(df{v.x, v.y}) * inv;
-                acc += mask ? val - mask[((int64_t)item << ls) + j] : val;
+    // Row rem of the block goes to CTA rem mod CL.  A CTA first forms every term of its rows, term
+    // s of its i-th row (slot value, minus the mask) into vals[i terms + s], all threads taking
+    // some so that the FP64 work (a pipe of about 1.7 lanes per clock per SM) is spread over the
+    // CTA's warps and its load latencies overlap; then each row's terms are summed in the order
+    // s = 0, 1, ... by one thread (rows spread over four warps, one per scheduler).  vals is the
+    // CTA's twiddle copy, free after the transform: MS doubles, which the terms fit whenever the
+    // block's rows hold each slot at most once; otherwise each thread forms and sums a row itself.
+    // slot of term q (row i = q / terms, term s = q mod terms) of this CTA's rows
+    __device__ __forceinline__ int64_t slot_of(int64_t q, int lt, int rank, int clg) const {
+        const int64_t rem = ((q >> lt) << clg) + rank;
+        return ((rem >> lm) << lnb) + (rem & (p.m_prime - 1)) + ((q & ((1ll << lt) - 1)) << lm);
+    }
+    __device__ __forceinline__ EpiPre prefetch(int, int rank, int clg, int, int lg_ms, const int32_t *__restrict__ slot_pos) const {
+        EpiPre pre;
+        const int64_t terms = p.nb >> lm, rows = rank < p.mb ? ((p.mb - 1 - rank) >> clg) + 1 : 0;
+        const int lt = terms ? lnb - lm : 0;
+        if (rows * terms <= (1 << lg_ms)) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int64_t q = threadIdx.x + (int64_t)r * blockDim.x;
+                if (q < rows * terms) pre.pos[r] = slot_pos[slot_of(q, lt, rank, clg)];
             }
-            y[row] = acc;
+        }
+        return pre;
+    }
+    __device__ __forceinline__ void operator()(cg::cluster_group &cl, const float4 *a, int item, int rank, int clg, int, int lg_ms,
+                                               const int32_t *__restrict__ slot_pos, double inv, double *vals, const EpiPre &pre) const {
+        const int MS = 1 << lg_ms;
+        const int64_t terms = p.nb >> lm, row0 = (int64_t)item << lmb;
+        const int lt = terms ? lnb - lm : 0;
+        const int64_t rows = rank < p.mb ? ((p.mb - 1 - rank) >> clg) + 1 : 0;
+        auto term_at = [&](int64_t j, int pos) {
+            const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
+            const double val = df_to(df{v.x, v.y}) * inv;
+            return mask ? val - mask[((int64_t)item << ls) + j] : val;
+        };
+        auto term = [&](int64_t rem, int64_t s) {
+            const int64_t j = ((rem >> lm) << lnb) + (rem & (p.m_prime - 1)) + (s << lm);
+            return term_at(j, slot_pos[j]);
+        };
+        if (rows * terms <= MS) {
+            int r = 0;
+#pragma unroll 2
+            for (int64_t q = threadIdx.x; q < rows * terms; q += blockDim.x, ++r) {
+                const int64_t rem = ((q >> lt) << clg) + rank, j = slot_of(q, lt, rank, clg);
+                if (row0 + rem < p.m) vals[q] = term_at(j, r == 0 ? pre.pos[0] : (r == 1 ? pre.pos[1] : slot_pos[j]));
+            }
+            __syncthreads();
+            const int nw = blockDim.x >= 128 ? 4 : (int)(blockDim.x >> 5);
+            if ((int)threadIdx.x < 32 * nw) {
+                for (int64_t i = ((threadIdx.x & 31) * nw) + (threadIdx.x >> 5); i < rows; i += 32 * nw) {
+                    const int64_t row = row0 + (i << clg) + rank;
+                    if (row >= p.m) break;
+                    double acc = 0.0;
+#pragma unroll 4
+                    for (int64_t s = 0; s < terms; ++s) acc += vals[(i << lt) + s];
+                    y[row] = acc;
+                }
+            }
+            return;
+        }
+        for (int64_t i = threadIdx.x; i < rows; i += blockDim.x) {
+            const int64_t rem = (i << clg) + rank;
+            if (row0 + rem >= p.m) break;
+            double acc = 0.0;
+            for (int64_t s = 0; s < terms; ++s) acc += term(rem, s);
+            y[row0 + rem] = acc;
         }
     }
 };
@@ -423,17 +598,26 @@ struct DecodeRas {
 template <int CLG, int RL, int LOGN, class EPI>
 __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale, const float4 *__restrict__ tw,
                                  const float4 *__restrict__ twist, const int32_t *__restrict__ slot_pos, EPI epi, int logn_rt) {
-    HE_GRID_DEP();
+    HE_GRID_LAUNCH();
     const int logn = LOGN ? LOGN : logn_rt;
     extern __shared__ float4 a[];
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), item = blockIdx.x >> CLG;
     const int logm = logn - 1, M = 1 << logm, N = 1 << logn, lg_ms = logm - CLG, MS = 1 << lg_ms, off = rank * MS;
-    const double *m = coeffs + (int64_t)item * N;
+    // the context's tables before the wait: the twiddle copy, the twist factors of the first two
+    // iterations and the epilogue's first slot positions
     fft_tw_issue<CLG>(a, tw, logm);
-    for (int i = threadIdx.x; i < MS; i += blockDim.x) {
+    float4 w_pre[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+        if ((int)threadIdx.x + r * (int)blockDim.x < MS) w_pre[r] = twist[__brev(off + threadIdx.x + r * blockDim.x) >> (32 - logm)];
+    const EpiPre pre = epi.prefetch(item, rank, CLG, M, lg_ms, slot_pos);
+    HE_GRID_WAIT();
+    const double *m = coeffs + (int64_t)item * N;
+    int r = 0;
+    for (int i = threadIdx.x; i < MS; i += blockDim.x, ++r) {
         const int k = __brev(off + i) >> (32 - logm);
-        const float4 w = twist[k];
+        const float4 w = r == 0 ? w_pre[0] : (r == 1 ? w_pre[1] : twist[k]);
         const df re = df_from(m[k]), im = df_from(m[k + M]);
         float4 c;
         cmul(make_float4(re.hi, re.lo, im.hi, im.lo), make_float4(w.x, w.y, -w.z, -w.w), c);
@@ -441,7 +625,7 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
     }
     __syncthreads();
     fft_cluster<CLG, RL, LOGN ? LOGN - 1 : 0>(a, tw, logm, +1);
-    epi(cl, a, item, rank, CLG, M, lg_ms, slot_pos, 1.0 / scale);
+    epi(cl, a, item, rank, CLG, M, lg_ms, slot_pos, 1.0 / scale, reinterpret_cast<double *>(a + MS), pre);  // the twiddle copy as scratch
     cl.sync();  // the other CTAs read this one's shared memory until here
 }
 
@@ -466,7 +650,7 @@ __global__ void decrypt_kernel(const uint64_t *__restrict__ ct, int64_t ct_words
     const uint64_t half = q >> 1;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
         const uint64_t v = mul_shoup(s[SIDX(k)], mc[0].ninv, mc[0].ninv_shoup, q);
-        o[k] = v > half ? -(double)(q - v) : (double)v;
+        o[k] = v > half ? u64_to_double_rn(q - v, true) : u64_to_double_rn(v, false);
     }
 }
 

@@ -349,6 +349,12 @@ int ptmat_bind_keys(he_ctx *ctx, he_ptmat *pm);
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   \
         asm volatile("griddepcontrol.wait;" ::: "memory");                \
     } while (0)
+// The two halves, for kernels that start loads before the wait.  Those loads may read only the
+// context's tables written at its creation (which synchronises), never data of an earlier launch:
+// with every kernel releasing its successor on entry, a kernel's pre-wait code can run while
+// kernels two or more launches back are still running.
+#define HE_GRID_LAUNCH() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+#define HE_GRID_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {

@@ -758,7 +758,7 @@ __device__ __forceinline__ void ntt_inv_pair(uint64_t *s, const ulonglong2 *__re
 
 // dynamic shared memory and threads of a pair-form CTA: a half (padded), one radix-16 set per thread
 __host__ __device__ __forceinline__ size_t pair_smem_bytes(int logn) { return ((size_t)1 << (logn - 1)) * 8 + ((size_t)1 << (logn - 1)) / 32 * 8; }
-constexpr int pair_threads_c(int logn) { return (1 << (logn - 1 - HE_NTT_RADIX_LOG)) > 512 ? 512 : (1 << (logn - 1 - HE_NTT_RADIX_LOG)); }
+__host__ __device__ constexpr int pair_threads_c(int logn) { return (1 << (logn - 1 - HE_NTT_RADIX_LOG)) > 512 ? 512 : (1 << (logn - 1 - HE_NTT_RADIX_LOG)); }
 __host__ __device__ __forceinline__ int pair_threads(int logn) { return pair_threads_c(logn); }
 
 // twiddle table of prime index p: which = 0 forward (psi^brv(k), Shoup), 1 inverse (psi^-brv(k), Shoup)
