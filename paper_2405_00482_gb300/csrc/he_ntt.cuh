@@ -522,56 +522,68 @@ struct TwSliceInv {
     __device__ __forceinline__ ulonglong2 at(int, int, int, int m, int idx) const { return (*this)(m, idx); }
 };
 
+// The cross-CTA stages of the cluster form: the 8 elements j + c NS of an offset j, one per CTA,
+// go through three radix-2 stages (forward: c paired with c + 4, then c + 2, then c + 1;
+// inverse: c + 1, c + 2, c + 4).  Four adjacent lanes share an offset, lane p holding the pair of
+// one butterfly per stage (the stage's bit inserted into p), and between stages they swap
+// elements by warp shuffles, so every thread of the CTA takes part.  A stage's twiddle does not
+// depend on j: forward tw[2^st + (c >> (3 - st))], inverse tw[(4 >> st) + (c >> (st + 1))] for
+// the pair's lower element c; cross_tw_load reads them before the cluster barrier.
+__device__ __forceinline__ int ins_bit(int v, int b) { return (v & ((1 << b) - 1)) | ((v >> b) << (b + 1)); }
+__device__ __forceinline__ int del_bit(int v, int b) { return (v & ((1 << b) - 1)) | ((v >> (b + 1)) << b); }
 template <bool FWD>
-__device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
+__device__ __forceinline__ int cross_bit(int st) { return FWD ? 2 - st : st; }
+template <bool FWD>
+__device__ __forceinline__ void cross_tw_load(ulonglong2 w[3], const ulonglong2 *__restrict__ tw) {
+    const int p = threadIdx.x & 3;
+#pragma unroll
+    for (int st = 0; st < 3; ++st) {
+        const int c = ins_bit(p, cross_bit<FWD>(st));
+        w[st] = FWD ? tw[(1 << st) + (c >> (3 - st))] : tw[(4 >> st) + (c >> (st + 1))];
+    }
+}
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    return ((uint64_t)__shfl_sync(0xffffffffu, (unsigned)(v >> 32), src) << 32) | __shfl_sync(0xffffffffu, (unsigned)v, src);
+}
+template <bool FWD>
+__device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 w[3], uint64_t q, int logn) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int lg_ns = logn - 3, NS = 1 << lg_ns;
+    const int NS = 1 << (logn - 3), per = NS >> 3;
     const uint64_t two_q = 2 * q;
-    uint64_t *rem[8];
+    const int p = threadIdx.x & 3, lane_base = (threadIdx.x & 31) & ~3;
+    // 4 lanes per offset: NS / 2 of them, a multiple of 32 (NS >= 128), and blockDim.x a multiple
+    // of 32, so whole warps run each iteration and the shuffles see every lane
+    for (int t = threadIdx.x; t < per * 4; t += blockDim.x) {
+        const int j = SIDX(rank * per + (t >> 2));
+        int lo = ins_bit(p, cross_bit<FWD>(0));
+        uint64_t x0 = cl.map_shared_rank(s, lo)[j], x1 = cl.map_shared_rank(s, lo | (1 << cross_bit<FWD>(0)))[j];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) rem[c] = cl.map_shared_rank(s, c);
-    const int per = NS >> 3;
-    for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x) {
-        uint64_t r[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) r[c] = rem[c][SIDX(j)];
-        if (FWD) {  // stages 0..2: t0 = N/2, elements j + c NS
-#pragma unroll
-            for (int st = 0; st < 3; ++st) {
-                const int h = 8 >> (st + 1), m = 1 << st, lg_2t = logn - st;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if ((c & (2 * h - 1)) < h) {
-                        const int x = j + (c << lg_ns);
-                        const ulonglong2 w = tw[m + (x >> lg_2t)];
-                        uint64_t X = r[c];
-                        X = X >= two_q ? X - two_q : X;
-                        const uint64_t T = mul_shoup_lazy(r[c + h], w.x, w.y, q);
-                        r[c] = X + T;
-                        r[c + h] = X - T + two_q;
-                    }
-                }
+        for (int st = 0; st < 3; ++st) {
+            if (st > 0) {
+                // this lane's pair from the lanes that held them at stage st - 1 (element c at lane
+                // c with that stage's bit removed, in the slot given by the bit)
+                const int b = cross_bit<FWD>(st), bp = cross_bit<FWD>(st - 1);
+                const int nlo = ins_bit(p, b), nhi = nlo | (1 << b);
+                const int sl = lane_base + del_bit(nlo, bp), sh = lane_base + del_bit(nhi, bp);
+                const uint64_t a0 = shfl64(x0, sl), a1 = shfl64(x1, sl), b0 = shfl64(x0, sh), b1 = shfl64(x1, sh);
+                x0 = (nlo >> bp) & 1 ? a1 : a0;
+                x1 = (nhi >> bp) & 1 ? b1 : b0;
+                lo = nlo;
             }
-        } else {  // stages logn-3..logn-1: t = NS, 2NS, 4NS
-#pragma unroll
-            for (int st = 0; st < 3; ++st) {
-                const int h = 1 << st, m = 4 >> st, lg_2t = lg_ns + st + 1;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    if ((c & (2 * h - 1)) < h) {
-                        const int x = j + (c << lg_ns);
-                        const ulonglong2 w = tw[m + (x >> lg_2t)];
-                        const uint64_t U = r[c], V = r[c + h];
-                        const uint64_t X = U + V;
-                        r[c] = X >= two_q ? X - two_q : X;
-                        r[c + h] = mul_shoup_lazy(U - V + two_q, w.x, w.y, q);
-                    }
-                }
+            if (FWD) {  // Cooley-Tukey, lazy: inputs in [0, 4q)
+                const uint64_t X = x0 >= two_q ? x0 - two_q : x0;
+                const uint64_t T = mul_shoup_lazy(x1, w[st].x, w[st].y, q);
+                x0 = X + T;
+                x1 = X - T + two_q;
+            } else {  // Gentleman-Sande, inputs in [0, 2q)
+                const uint64_t X = x0 + x1, D = x0 - x1 + two_q;
+                x0 = X >= two_q ? X - two_q : X;
+                x1 = mul_shoup_lazy(D, w[st].x, w[st].y, q);
             }
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) rem[c][SIDX(j)] = r[c];
+        cl.map_shared_rank(s, lo)[j] = x0;
+        cl.map_shared_rank(s, lo | (1 << cross_bit<FWD>(2)))[j] = x1;
     }
 }
 
@@ -586,9 +598,11 @@ __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *_
     const int rank = (int)cl.block_rank();
     const int NS = 1 << (logn - 3), off = rank * NS;
     ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(s + cl_tw_offset_words(logn));
+    ulonglong2 wx[3];
+    cross_tw_load<true>(wx, tw);
     tw_slice_wait();
     cl.sync();
-    ntt_cross_step<true>(s, tw, q, logn);
+    ntt_cross_step<true>(s, wx, q, logn);
     cl.sync();
     const TwSliceFwd tws{stw, rank};
 #pragma unroll(LOGN > 0 ? 16 : 1)
@@ -612,6 +626,8 @@ __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *_
     const int rank = (int)cl.block_rank();
     const int NS = 1 << (logn - 3), off = rank * NS;
     ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(s + cl_tw_offset_words(logn));
+    ulonglong2 wx[3];
+    cross_tw_load<false>(wx, itw);
     tw_slice_wait();
     __syncthreads();
     const TwSliceInv tws{stw, rank, 1 << (logn - 1)};
@@ -626,7 +642,7 @@ __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *_
         }
     }
     cl.sync();
-    ntt_cross_step<false>(s, itw, q, logn);
+    ntt_cross_step<false>(s, wx, q, logn);
     cl.sync();
 }
 
