@@ -97,13 +97,28 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def queue_ahead():
+    """Hold the GPU with a sleep kernel (about 50 ms) before the first timed repetition, so that the
+    host enqueues the repetitions ahead of the device and each CUDA-event interval holds the
+    device's work only.  Without it Python between two repetitions sometimes took longer than the
+    GPU's flush, and the interval then held the wait for the late launch: the same replay timed
+    228-232 us instead of 197-206 us on those repetitions."""
+    import torch
+
+    torch.cuda._sleep(100_000_000)
+
+
 def flush_l2(buf):
     """Evict L2 between timed repetitions: write one half of buf (each half larger than the 129 MB
     L2), then read the other half, so that the timed work finds none of its inputs in L2 and no
-    dirty line of the flush left for it to write back."""
+    dirty line of the flush left for it to write back.  A one-element write ends it: with the
+    reduction right before the start event, every repetition of the same replay timed 23-24 us
+    longer than with an elementwise kernel there (measured 40 times each way; the replay's own
+    kernels and their order are the same), so the flush's tail leaked into the interval."""
     half = buf.numel() // 2
     buf[:half].add_(1)
     buf[half:].sum()
+    buf[:1].zero_()
 
 
 def run_gpu(args):
@@ -218,6 +233,7 @@ def run_gpu(args):
 
     def timed_steps(run):
         per = []
+        queue_ahead()
         for i in range(args.steps):
             flush_l2(flush)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -273,6 +289,7 @@ def run_gpu(args):
     def mm_calls():
         ctx.profile(True)
         mm = []
+        queue_ahead()
         for i in range(args.steps):
             flush_l2(flush)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -476,6 +493,7 @@ def run_rotations(ctx, he, P, args, flush, world, dev):
             fn()
         torch.cuda.synchronize()
         ev = []
+        queue_ahead()
         for _ in range(reps):
             flush_l2(flush)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -549,6 +567,7 @@ def _event_times(fn, reps, flush, warm=3):
         fn()
     torch.cuda.synchronize()
     ev = []
+    queue_ahead()
     for _ in range(reps):
         flush_l2(flush)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -765,6 +784,7 @@ def run_batched(ctx, he, inputs, P, args, flush, world, dev):
             fn()
         torch.cuda.synchronize()
         ev = []
+        queue_ahead()
         for _ in range(args.steps):
             flush_l2(flush)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

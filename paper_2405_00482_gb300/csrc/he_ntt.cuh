@@ -502,6 +502,13 @@ __device__ __forceinline__ void tw_slice_issue(ulonglong2 *stw, const ulonglong2
 }
 __device__ __forceinline__ void tw_slice_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// the dynamic shared memory, for a kernel that starts a copy into it before calling a body that
+// declares its own (every extern __shared__ array starts at the same address)
+__device__ __forceinline__ uint64_t *s_dyn() {
+    extern __shared__ uint64_t s_dyn_words[];
+    return s_dyn_words;
+}
+
 // Kernels call this as soon as they know their prime, before loading their data, so the twiddle
 // copy overlaps the loads; the cluster transform waits for it.  Nothing in the one-CTA form.
 template <bool CL, bool FWD>

@@ -208,9 +208,9 @@ __global__ void rescale_kernel(const uint64_t *__restrict__ ct, int level, const
 // canonical coefficients are then s[SIDX(k)] * N^-1 (applied by the caller with mul_shoup)
 template <int LOGN = 0>
 __device__ __forceinline__ void cl_intt_slice(uint64_t *s, const uint64_t *__restrict__ src, int pr, const uint64_t *__restrict__ d_tw,
-                                              const ModConst *__restrict__ mc, int logn, int len) {
+                                              const ModConst *__restrict__ mc, int logn, int len, bool tw_issued = false) {
     const ulonglong2 *itw = twiddles(d_tw, pr, 1, logn);
-    tw_prefetch<true, false>(s, itw, logn);
+    if (!tw_issued) tw_prefetch<true, false>(s, itw, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = src[k];
     __syncthreads();
     ntt_inv_cluster<LOGN>(s, itw, mc[pr].q, logn);
@@ -222,7 +222,7 @@ __device__ __forceinline__ uint64_t *cl_acc_slice(uint64_t *s, int logn) { retur
 template <int LOGN = 0>
 __device__ __forceinline__ void modup_cl_fused_body(const uint64_t *__restrict__ c1_ntt, uint64_t *D, const ModUpConst &mu, int item,
                                                     const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn, int off,
-                                                    int len) {
+                                                    int len, bool tw_issued = false) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int d = item / mu.ext, u = item % mu.ext;
@@ -238,7 +238,7 @@ __device__ __forceinline__ void modup_cl_fused_body(const uint64_t *__restrict__
     uint64_t *acc = cl_acc_slice(s, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) acc[k] = 0;
     for (int i = lo; i < hi; ++i) {
-        cl_intt_slice<LOGN>(s, c1_ntt + (int64_t)i * N + off, i, d_tw, mc, logn, len);
+        cl_intt_slice<LOGN>(s, c1_ntt + (int64_t)i * N + off, i, d_tw, mc, logn, len, tw_issued && i == lo);
         const uint64_t qi = mc[i].q;
         for (int k = threadIdx.x; k < len; k += blockDim.x) {
             uint64_t v = mul_shoup(s[SIDX(k)], mc[i].ninv, mc[i].ninv_shoup, qi);
@@ -258,11 +258,16 @@ __device__ __forceinline__ void modup_cl_fused_body(const uint64_t *__restrict__
 template <int LOGN = 0>
 __global__ void modup_cl_fused_kernel(const uint64_t *__restrict__ c1_ntt, uint64_t *D, ModUpConst mu, const uint64_t *__restrict__ d_tw,
                                       const ModConst *__restrict__ mc, int logn_rt) {
-    HE_GRID_DEP();
+    HE_GRID_LAUNCH();
     const int logn = LOGN ? LOGN : logn_rt;
     int item, off, len;
     slice_of<true>(logn, item, off, len);
-    modup_cl_fused_body<LOGN>(c1_ntt, D, mu, item, d_tw, mc, logn, off, len);
+    // the first inverse transform's twiddle copy (a context table) before the wait
+    const int d = item / mu.ext, u = item % mu.ext, lo = d * mu.alpha;
+    const bool own = u >= lo && u < (lo + mu.alpha < mu.nq ? lo + mu.alpha : mu.nq);
+    if (!own) tw_prefetch<true, false>(s_dyn(), twiddles(d_tw, lo, 1, logn), logn);
+    HE_GRID_WAIT();
+    modup_cl_fused_body<LOGN>(c1_ntt, D, mu, item, d_tw, mc, logn, off, len, !own);
 }
 
 // ModDown of component c, output limb j: conversion of the K special-prime limbs (each brought
@@ -359,7 +364,7 @@ template <int LOGN = 0>
 __device__ __forceinline__ void moddown_rescale_intt_body(const uint64_t *__restrict__ x, int ext, const ModDownConst &md,
                                                           const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, uint64_t *tmp,
                                                           int item, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn,
-                                                          int off, int len) {
+                                                          int off, int len, bool tw_issued = false) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int c = item / (md.K + 1), r = item % (md.K + 1);
@@ -368,7 +373,7 @@ __device__ __forceinline__ void moddown_rescale_intt_body(const uint64_t *__rest
     if (r < md.K) {  // P limb r: INTT, N^-1, [(P/p_r)^-1]
         const int pr = md.p_prime[r];
         const uint64_t pi = mc[pr].q;
-        cl_intt_slice<LOGN>(s, x + ((int64_t)c * ext + md.nq + r) * N + off, pr, d_tw, mc, logn, len);
+        cl_intt_slice<LOGN>(s, x + ((int64_t)c * ext + md.nq + r) * N + off, pr, d_tw, mc, logn, len, tw_issued);
         for (int k = threadIdx.x; k < len; k += blockDim.x) {
             const uint64_t v = mul_shoup(s[SIDX(k)], mc[pr].ninv, mc[pr].ninv_shoup, pi);
             o[k] = mul_shoup(v, md.inv[r], md.inv_shoup[r], pi);
@@ -379,7 +384,7 @@ __device__ __forceinline__ void moddown_rescale_intt_body(const uint64_t *__rest
     const int pl = md.q_prime[L];
     const uint64_t ql = mc[pl].q;
     const ulonglong2 *itw = twiddles(d_tw, pl, 1, logn);
-    tw_prefetch<true, false>(s, itw, logn);
+    if (!tw_issued) tw_prefetch<true, false>(s, itw, logn);
     const uint64_t *xl = x + ((int64_t)c * ext + L) * N + off;
     const uint64_t *ad = c == 0 ? add0 : add1;
     const uint64_t *al = ad ? ad + (int64_t)L * N + off : nullptr;
@@ -397,18 +402,21 @@ template <int LOGN = 0>
 __global__ void moddown_rescale_intt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, const uint64_t *__restrict__ add0,
                                             const uint64_t *__restrict__ add1, uint64_t *tmp, const uint64_t *__restrict__ d_tw,
                                             const ModConst *__restrict__ mc, int logn_rt) {
-    HE_GRID_DEP();
+    HE_GRID_LAUNCH();
     const int logn = LOGN ? LOGN : logn_rt;
     int item, off, len;
     slice_of<true>(logn, item, off, len);
-    moddown_rescale_intt_body<LOGN>(x, ext, md, add0, add1, tmp, item, d_tw, mc, logn, off, len);
+    const int r = item % (md.K + 1);  // the inverse transform's twiddle copy (a context table) before the wait
+    tw_prefetch<true, false>(s_dyn(), twiddles(d_tw, r < md.K ? md.p_prime[r] : md.q_prime[md.nq - 1], 1, logn), logn);
+    HE_GRID_WAIT();
+    moddown_rescale_intt_body<LOGN>(x, ext, md, add0, add1, tmp, item, d_tw, mc, logn, off, len, true);
 }
 
 template <int LOGN = 0>
 __device__ __forceinline__ void moddown_rescale_ntt_body(const uint64_t *__restrict__ x, int ext, const ModDownConst &md, const RescaleConst &rc,
                                                          const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1,
                                                          const uint64_t *__restrict__ tmp, uint64_t *out, int item, const uint64_t *__restrict__ d_tw,
-                                                         const ModConst *__restrict__ mc, int logn, int off, int len) {
+                                                         const ModConst *__restrict__ mc, int logn, int off, int len, bool tw_issued = false) {
     extern __shared__ uint64_t s[];
     const int N = 1 << logn;
     const int L = md.nq - 1;
@@ -416,7 +424,7 @@ __device__ __forceinline__ void moddown_rescale_ntt_body(const uint64_t *__restr
     const int pj = md.q_prime[j], pl = md.q_prime[L];
     const uint64_t q = mc[pj].q, ql = mc[pl].q;
     const ulonglong2 *tw = twiddles(d_tw, pj, 0, logn);
-    tw_prefetch<true, true>(s, tw, logn);
+    if (!tw_issued) tw_prefetch<true, true>(s, tw, logn);
     const uint64_t *tc = tmp + (int64_t)c * (md.K + 1) * N + off;
     for (int k = threadIdx.x; k < len; k += blockDim.x) {
         // conv_j and conv_L of the scaled P limbs, in limb order
@@ -450,11 +458,14 @@ template <int LOGN = 0>
 __global__ void moddown_rescale_ntt_kernel(const uint64_t *__restrict__ x, int ext, ModDownConst md, RescaleConst rc,
                                            const uint64_t *__restrict__ add0, const uint64_t *__restrict__ add1, const uint64_t *__restrict__ tmp,
                                            uint64_t *out, const uint64_t *__restrict__ d_tw, const ModConst *__restrict__ mc, int logn_rt) {
-    HE_GRID_DEP();
+    HE_GRID_LAUNCH();
     const int logn = LOGN ? LOGN : logn_rt;
     int item, off, len;
     slice_of<true>(logn, item, off, len);
-    moddown_rescale_ntt_body<LOGN>(x, ext, md, rc, add0, add1, tmp, out, item, d_tw, mc, logn, off, len);
+    // the forward transform's twiddle copy (a context table) before the wait
+    tw_prefetch<true, true>(s_dyn(), twiddles(d_tw, md.q_prime[item % (md.nq - 1)], 0, logn), logn);
+    HE_GRID_WAIT();
+    moddown_rescale_ntt_body<LOGN>(x, ext, md, rc, add0, add1, tmp, out, item, d_tw, mc, logn, off, len, true);
 }
 
 // ---- many rotations: O3 of different ciphertexts, each by its own step, one launch per stage ----
