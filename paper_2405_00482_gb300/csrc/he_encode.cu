@@ -155,6 +155,10 @@ __device__ __forceinline__ void fft_bfly(float4 &u4, float4 &v4, float4 w) {
     v4 = make_float4(d0r.hi, d0r.lo, d0i.hi, d0i.lo);
 }
 
+__device__ __forceinline__ float4 shfl4_xor(float4 v) {
+    return make_float4(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1), __shfl_xor_sync(0xffffffffu, v.z, 1),
+                       __shfl_xor_sync(0xffffffffu, v.w, 1));
+}
 __device__ __forceinline__ float4 shfl4(float4 v, int src) {
     return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src), __shfl_sync(0xffffffffu, v.z, src),
                        __shfl_sync(0xffffffffu, v.w, src));
@@ -208,6 +212,34 @@ __device__ __forceinline__ void fft_pass(float4 *a, TWA tw, int logm, int s0, in
         }
 #pragma unroll
         for (int k = 0; k < E; ++k) a[base + (k << s0)] = r[k];
+    }
+    __syncthreads();
+}
+
+// Stages s0 and s0 + 1 over sets [set0, set1) of four elements base + k 2^s0 (k < 4), two lanes
+// per set: at stage s0 lane p holds k = 2p, 2p + 1 (one butterfly, twiddle position low); then
+// the lanes swap one element by shuffle (lane 0 gives k = 1 for k = 2) and lane p holds k = p,
+// p + 2 for stage s0 + 1 (twiddle position low + p 2^s0).  The same butterflies as two radix-2
+// passes, one trip through shared memory and one barrier instead of two.  2 (set1 - set0) is a
+// multiple of blockDim.x, so whole warps run each iteration.
+template <class TWA>
+__device__ __forceinline__ void fft_pass_pair(float4 *a, TWA tw, int s0, int sign, int set0, int set1, int off) {
+    a -= off;
+    const int p = threadIdx.x & 1, d = 1 << s0;
+    for (int t = 2 * set0 + (int)threadIdx.x; t < 2 * set1; t += blockDim.x) {
+        const int set = t >> 1, g = set >> s0, low = set & (d - 1);
+        const int base = (g << (s0 + 2)) + low;
+        float4 x0 = a[base + 2 * p * d], x1 = a[base + (2 * p + 1) * d];
+        float4 w = tw.at(low, s0 + 1);
+        if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
+        fft_bfly(x0, x1, w);
+        const float4 got = shfl4_xor(p ? x0 : x1);
+        float4 y0 = p ? got : x0, y1 = p ? x1 : got;
+        w = tw.at(low + p * d, s0 + 2);
+        if (sign > 0) w = make_float4(w.x, w.y, -w.z, -w.w);
+        fft_bfly(y0, y1, w);
+        a[base + p * d] = y0;
+        a[base + (p + 2) * d] = y1;
     }
     __syncthreads();
 }
@@ -313,15 +345,25 @@ __device__ __forceinline__ void fft_cluster(float4 *a, const float4 *__restrict_
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // the twiddle copy of fft_tw_issue
     __syncthreads();
     const TwFftLocal tloc{a + MS, lg_ms};
+    if constexpr (RL == 1) {
+        // radix-2 stages two at a time, lane pairs swapping one element by shuffle in between
 #pragma unroll(LOGM > 0 ? 16 : 1)
-    for (int s0 = 0; s0 < (LOGM > 0 ? LOGM - CLG : 16); s0 += RL) {
-        if (s0 >= lg_ms) break;
-        const int nb = lg_ms - s0 < RL ? lg_ms - s0 : RL;
-        const int E = 1 << nb;
-        switch (nb) {
-            case 3: fft_pass<3>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
-            case 2: fft_pass<2>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
-            default: fft_pass<1>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+        for (int s0 = 0; s0 + 1 < (LOGM > 0 ? LOGM - CLG : 16); s0 += 2) {
+            if (s0 + 1 >= lg_ms) break;
+            fft_pass_pair(a, tloc, s0, sign, rank * (MS / 4), (rank + 1) * (MS / 4), off);
+        }
+        if (lg_ms & 1) fft_pass<1>(a, tloc, logm, lg_ms - 1, sign, rank * (MS / 2), (rank + 1) * (MS / 2), off);
+    } else {
+#pragma unroll(LOGM > 0 ? 16 : 1)
+        for (int s0 = 0; s0 < (LOGM > 0 ? LOGM - CLG : 16); s0 += RL) {
+            if (s0 >= lg_ms) break;
+            const int nb = lg_ms - s0 < RL ? lg_ms - s0 : RL;
+            const int E = 1 << nb;
+            switch (nb) {
+                case 3: fft_pass<3>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+                case 2: fft_pass<2>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+                default: fft_pass<1>(a, tloc, logm, s0, sign, rank * (MS / E), (rank + 1) * (MS / E), off); break;
+            }
         }
     }
     // The cross-CTA stages: the CL elements j + c MS of an offset j go through CLG radix-2
