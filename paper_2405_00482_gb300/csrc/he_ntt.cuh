@@ -217,6 +217,80 @@ __device__ __forceinline__ void ntt_inv_pass(uint64_t *s, TWA itw, uint64_t q, i
     __syncthreads();
 }
 
+// Two radix-2 stages per pass with two lanes per set of four elements, which swap one element by
+// warp shuffle between the stages: the butterflies, twiddles and lazy bounds of ntt_fwd_pass<2> /
+// ntt_inv_pass<2>, with each thread holding one butterfly's pair per stage (the thread count of a
+// radix-2 pass) and one trip through shared memory and one barrier per two stages.
+// 2 (set1 - set0) must be a multiple of blockDim.x and of 32, so whole warps run each iteration.
+__device__ __forceinline__ uint64_t shfl64_xor1(uint64_t v) {
+    return ((uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), 1) << 32) | __shfl_xor_sync(0xffffffffu, (unsigned)v, 1);
+}
+// forward stages s0, s0 + 1: elements base + k 2^lg_tl; stage s0 pairs k, k + 2 (lane p: k = p),
+// stage s0 + 1 pairs k, k + 1 (lane p: k = 2p)
+template <class TWA>
+__device__ __forceinline__ void ntt_fwd_pass_pair(uint64_t *s, TWA tw, uint64_t q, int logn, int s0, bool last, int set0, int set1, int off) {
+    const int lg_t0 = logn - 1 - s0, lg_tl = lg_t0 - 1;
+    const uint64_t two_q = 2 * q;
+    const int p = threadIdx.x & 1;
+    for (int t = 2 * set0 + (int)threadIdx.x; t < 2 * set1; t += blockDim.x) {
+        const int set = t >> 1, g = set >> lg_tl, low = set & ((1 << lg_tl) - 1);
+        const int sb = SIDX((g << (lg_t0 + 1)) + low) - SIDX(off);
+        uint64_t x0 = s[sb + SIDX(p << lg_tl)], x1 = s[sb + SIDX((p + 2) << lg_tl)];
+        const int m0 = 1 << s0, m1 = 2 << s0;
+        ulonglong2 w = tw.at(0, g, 0, m0, m0 + g);
+        uint64_t X = x0 >= two_q ? x0 - two_q : x0;
+        uint64_t T = mul_shoup_lazy(x1, w.x, w.y, q);
+        x0 = X + T;
+        x1 = X - T + two_q;
+        const uint64_t got = shfl64_xor1(p ? x0 : x1);
+        if (p) x0 = got;
+        else x1 = got;
+        w = tw.at(1, g, p, m1, m1 + (g << 1) + p);
+        X = x0 >= two_q ? x0 - two_q : x0;
+        T = mul_shoup_lazy(x1, w.x, w.y, q);
+        x0 = X + T;
+        x1 = X - T + two_q;
+        if (last) {
+            x0 = x0 >= two_q ? x0 - two_q : x0;
+            x0 = x0 >= q ? x0 - q : x0;
+            x1 = x1 >= two_q ? x1 - two_q : x1;
+            x1 = x1 >= q ? x1 - q : x1;
+        }
+        s[sb + SIDX((2 * p) << lg_tl)] = x0;
+        s[sb + SIDX((2 * p + 1) << lg_tl)] = x1;
+    }
+    __syncthreads();
+}
+// inverse stages s0, s0 + 1: elements base + k 2^s0; stage s0 pairs k, k + 1 (lane p: k = 2p),
+// stage s0 + 1 pairs k, k + 2 (lane p: k = p)
+template <class TWA>
+__device__ __forceinline__ void ntt_inv_pass_pair(uint64_t *s, TWA itw, uint64_t q, int logn, int s0, int set0, int set1, int off) {
+    const int N = 1 << logn;
+    const uint64_t two_q = 2 * q;
+    const int p = threadIdx.x & 1;
+    for (int t = 2 * set0 + (int)threadIdx.x; t < 2 * set1; t += blockDim.x) {
+        const int set = t >> 1, g = set >> s0, low = set & ((1 << s0) - 1);
+        const int sb = SIDX((g << (s0 + 2)) + low) - SIDX(off);
+        uint64_t x0 = s[sb + SIDX((2 * p) << s0)], x1 = s[sb + SIDX((2 * p + 1) << s0)];
+        const int m0 = N >> (s0 + 1), m1 = N >> (s0 + 2);
+        ulonglong2 w = itw.at(0, g, p, m0, m0 + (g << 1) + p);
+        uint64_t X = x0 + x1, D = x0 - x1 + two_q;
+        x0 = X >= two_q ? X - two_q : X;
+        x1 = mul_shoup_lazy(D, w.x, w.y, q);
+        const uint64_t got = shfl64_xor1(p ? x0 : x1);
+        if (p) x0 = got;
+        else x1 = got;
+        w = itw.at(1, g, 0, m1, m1 + g);
+        X = x0 + x1;
+        D = x0 - x1 + two_q;
+        x0 = X >= two_q ? X - two_q : X;
+        x1 = mul_shoup_lazy(D, w.x, w.y, q);
+        s[sb + SIDX(p << s0)] = x0;
+        s[sb + SIDX((p + 2) << s0)] = x1;
+    }
+    __syncthreads();
+}
+
 // ---- two-phase transforms of many limb-polys (NTT form 2) ----
 // With N = 64 C (C = 2^(log N - 6)), stages 0..5 of the forward transform only combine the 64
 // elements x = l C + c of one column c (their stage-s group x >> (log N - s) = l >> (6 - s) does
@@ -613,16 +687,11 @@ __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *_
     cl.sync();
     const TwSliceFwd tws{stw, rank};
 #pragma unroll(LOGN > 0 ? 16 : 1)
-    for (int s0 = 3; s0 < (LOGN > 0 ? LOGN : 16); s0 += HE_NTT_CL_RADIX_LOG) {
-        if (s0 >= logn) break;
-        const int nb = logn - s0 < HE_NTT_CL_RADIX_LOG ? logn - s0 : HE_NTT_CL_RADIX_LOG;
-        const bool last = s0 + nb == logn;
-        const int E = 1 << nb;
-        switch (nb) {
-            case 2: ntt_fwd_pass<2>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-            default: ntt_fwd_pass<1>(s, tws, q, logn, s0, last, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-        }
+    for (int s0 = 3; s0 + 1 < (LOGN > 0 ? LOGN : 16); s0 += 2) {  // stages in pairs, the last alone if odd
+        if (s0 + 1 >= logn) break;
+        ntt_fwd_pass_pair(s, tws, q, logn, s0, s0 + 2 == logn, rank * (NS / 4), (rank + 1) * (NS / 4), off);
     }
+    if (((logn - 3) & 1) != 0) ntt_fwd_pass<1>(s, tws, q, logn, logn - 1, true, rank * (NS / 2), (rank + 1) * (NS / 2), off);
 }
 
 // inverse transform (without N^-1) of the slices; output in [0, 2q), natural order (twiddle copy
@@ -639,15 +708,11 @@ __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *_
     __syncthreads();
     const TwSliceInv tws{stw, rank, 1 << (logn - 1)};
 #pragma unroll(LOGN > 0 ? 16 : 1)
-    for (int s0 = 0; s0 < (LOGN > 0 ? LOGN - 3 : 16); s0 += HE_NTT_CL_RADIX_LOG) {
-        if (s0 >= logn - 3) break;
-        const int nb = logn - 3 - s0 < HE_NTT_CL_RADIX_LOG ? logn - 3 - s0 : HE_NTT_CL_RADIX_LOG;
-        const int E = 1 << nb;
-        switch (nb) {
-            case 2: ntt_inv_pass<2>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-            default: ntt_inv_pass<1>(s, tws, q, logn, s0, rank * (NS / E), (rank + 1) * (NS / E), off); break;
-        }
+    for (int s0 = 0; s0 + 1 < (LOGN > 0 ? LOGN - 3 : 16); s0 += 2) {  // stages in pairs, the last alone if odd
+        if (s0 + 1 >= logn - 3) break;
+        ntt_inv_pass_pair(s, tws, q, logn, s0, rank * (NS / 4), (rank + 1) * (NS / 4), off);
     }
+    if (((logn - 3) & 1) != 0) ntt_inv_pass<1>(s, tws, q, logn, logn - 4, rank * (NS / 2), (rank + 1) * (NS / 2), off);
     cl.sync();
     ntt_cross_step<false>(s, wx, q, logn);
     cl.sync();
