@@ -291,6 +291,66 @@ __device__ __forceinline__ void ntt_inv_pass_pair(uint64_t *s, TWA itw, uint64_t
     __syncthreads();
 }
 
+// Four forward stages s0..s0+3 (a radix-16 set) on two lanes of eight elements: lane p holds the
+// elements k = 2i + p (i < 8) of the set base + k 2^lg_tl, so stages s0..s0+2 (pairs k, k + 8,
+// + 4, + 2) stay within a lane; before stage s0 + 3 (pairs 2i, 2i + 1) the lanes swap four
+// elements by shuffle and lane p takes i = 4p .. 4p + 3.  The butterflies, twiddles and lazy
+// bounds of ntt_fwd_pass<4, TWA, CORR> with the registers of a radix-8 pass per thread.
+// 2 (set1 - set0) must be a multiple of blockDim.x and of 32.
+template <class TWA, bool CORR = true>
+__device__ __forceinline__ void ntt_fwd_pass16_lanes(uint64_t *s, TWA tw, uint64_t q, int logn, int s0, bool last, int set0, int set1, int off) {
+    const int lg_t0 = logn - 1 - s0, lg_tl = lg_t0 - 3;
+    const uint64_t two_q = 2 * q;
+    const int p = threadIdx.x & 1;
+    auto bfly = [&](uint64_t &a, uint64_t &b, ulonglong2 w) {
+        uint64_t X = a;
+        if constexpr (CORR) X = X >= two_q ? X - two_q : X;
+        const uint64_t T = mul_shoup_lazy(b, w.x, w.y, q);
+        a = X + T;
+        b = X - T + two_q;
+    };
+    for (int t = 2 * set0 + (int)threadIdx.x; t < 2 * set1; t += blockDim.x) {
+        const int set = t >> 1, g = set >> lg_tl, low = set & ((1 << lg_tl) - 1);
+        const int sb = SIDX((g << (lg_t0 + 1)) + low) - SIDX(off);
+        uint64_t r[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) r[i] = s[sb + SIDX((2 * i + p) << lg_tl)];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {  // element k = 2i + p meets entry m + (g << j) + (k >> (4 - j))
+            const int hi = 4 >> j, m = 1 << (s0 + j);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if ((i & (2 * hi - 1)) < hi) {
+                    const int e = (2 * i + p) >> (4 - j);
+                    bfly(r[i], r[i + hi], tw.at(j, g, e, m, m + (g << j) + e));
+                }
+            }
+        }
+        uint64_t got[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t v = p ? r[u] : r[4 + u];
+            got[u] = ((uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), 1) << 32) | __shfl_xor_sync(0xffffffffu, (unsigned)v, 1);
+        }
+        const int m3 = 8 << s0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = 4 * p + u;  // the pair (2i, 2i + 1), twiddle entry m3 + (g << 3) + i
+            uint64_t a = p ? got[u] : r[u], b = p ? r[4 + u] : got[u];
+            bfly(a, b, tw.at(3, g, i, m3, m3 + (g << 3) + i));
+            if (CORR && last) {
+                a = a >= two_q ? a - two_q : a;
+                a = a >= q ? a - q : a;
+                b = b >= two_q ? b - two_q : b;
+                b = b >= q ? b - q : b;
+            }
+            s[sb + SIDX((2 * i) << lg_tl)] = a;
+            s[sb + SIDX((2 * i + 1) << lg_tl)] = b;
+        }
+    }
+    __syncthreads();
+}
+
 // ---- two-phase transforms of many limb-polys (NTT form 2) ----
 // With N = 64 C (C = 2^(log N - 6)), stages 0..5 of the forward transform only combine the 64
 // elements x = l C + c of one column c (their stage-s group x >> (log N - s) = l >> (6 - s) does
@@ -362,6 +422,15 @@ __device__ __forceinline__ void ntt2_fwd_rows(uint64_t *sm, uint64_t *poly, int 
     stage_in(sm, poly + off, LEN, [](uint64_t v) { return v; });
     __syncthreads();
     const bool corr = q >= HE_NTT_NOCORR_Q;
+    if constexpr (LB == 7) {  // stages 6-8 as a radix-8 pass, 9-12 as a radix-16 one on lane pairs
+        if (corr) {
+            ntt_fwd_pass<3, TwGlobal, true>(sm, tw, q, LOGN, 6, false, off >> 3, (off + LEN) >> 3, off);
+            ntt_fwd_pass16_lanes<TwGlobal, true>(sm, tw, q, LOGN, 9, true, off >> 4, (off + LEN) >> 4, off);
+        } else {
+            ntt_fwd_pass<3, TwGlobal, false>(sm, tw, q, LOGN, 6, false, off >> 3, (off + LEN) >> 3, off);
+            ntt_fwd_pass16_lanes<TwGlobal, false>(sm, tw, q, LOGN, 9, false, off >> 4, (off + LEN) >> 4, off);
+        }
+    } else
 #pragma unroll
     for (int s0 = 6; s0 < LOGN; s0 += 3) {
         const bool last = s0 + 3 >= LOGN;
