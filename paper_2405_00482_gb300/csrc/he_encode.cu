@@ -1,4 +1,4 @@
-// he_encode.cu -- CKKS encoding/decoding (FP64 FFT), Philox-4x64-10 sampling, encryption.
+// he_encode.cu -- CKKS encoding/decoding (double-float FFT), Philox-4x64-10 sampling, encryption.
 //
 // Encoding (Sec. 2.2): the real polynomial m with m(zeta^(5^j)) = z_j, zeta = exp(i pi/N).
 // Since 5^j = 1 mod 4, the N/2 slot roots are zeta^(4t+1), and with c_k = m_k + i m_{k+N/2}
