@@ -442,14 +442,25 @@ __device__ __forceinline__ void moddown_rescale_ntt_body(const uint64_t *__restr
         s[SIDX(k)] = add_mod(mul_shoup(acc_j, md.pinv[j], md.pinv_shoup[j], q), reduce_signed(centred, q, mc[pj].mu), q);
     }
     __syncthreads();
-    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
+    // the combination's other inputs of the first two iterations, loaded before the transform
     const uint64_t *xj = x + ((int64_t)c * ext + j) * N + off;
     const uint64_t *ad = c == 0 ? add0 : add1;
     const uint64_t *aj = ad ? ad + (int64_t)j * N + off : nullptr;
+    uint64_t xv[2], av[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int k = threadIdx.x + r * blockDim.x;
+        if (k < len) {
+            xv[r] = xj[k];
+            av[r] = aj ? aj[k] : 0;
+        }
+    }
+    ntt_fwd_cluster<LOGN>(s, tw, q, logn);
     uint64_t *o = out + ((int64_t)c * L + j) * N + off;
-    for (int k = threadIdx.x; k < len; k += blockDim.x) {
-        uint64_t v = mul_shoup(xj[k], md.pinv[j], md.pinv_shoup[j], q);
-        if (aj) v = add_mod(v, aj[k], q);
+    int r = 0;
+    for (int k = threadIdx.x; k < len; k += blockDim.x, ++r) {
+        uint64_t v = mul_shoup(r == 0 ? xv[0] : (r == 1 ? xv[1] : xj[k]), md.pinv[j], md.pinv_shoup[j], q);
+        if (aj) v = add_mod(v, r == 0 ? av[0] : (r == 1 ? av[1] : aj[k]), q);
         o[k] = mul_shoup(sub_mod(v, s[SIDX(k)], q), rc.inv[j], rc.inv_shoup[j], q);
     }
 }
