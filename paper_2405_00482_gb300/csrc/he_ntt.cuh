@@ -695,19 +695,10 @@ __device__ __forceinline__ void cross_tw_load(ulonglong2 w[3], const ulonglong2 
 __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
     return ((uint64_t)__shfl_sync(0xffffffffu, (unsigned)(v >> 32), src) << 32) | __shfl_sync(0xffffffffu, (unsigned)v, src);
 }
+// the three stages on lane p's pair (x0, x1) = elements (lo, lo + 2^b) of stage 0's bit b
 template <bool FWD>
-__device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 w[3], uint64_t q, int logn) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int NS = 1 << (logn - 3), per = NS >> 3;
+__device__ __forceinline__ void cross_stages(uint64_t &x0, uint64_t &x1, int &lo, int p, int lane_base, const ulonglong2 w[3], uint64_t q) {
     const uint64_t two_q = 2 * q;
-    const int p = threadIdx.x & 3, lane_base = (threadIdx.x & 31) & ~3;
-    // 4 lanes per offset: NS / 2 of them, a multiple of 32 (NS >= 128), and blockDim.x a multiple
-    // of 32, so whole warps run each iteration and the shuffles see every lane
-    for (int t = threadIdx.x; t < per * 4; t += blockDim.x) {
-        const int j = SIDX(rank * per + (t >> 2));
-        int lo = ins_bit(p, cross_bit<FWD>(0));
-        uint64_t x0 = cl.map_shared_rank(s, lo)[j], x1 = cl.map_shared_rank(s, lo | (1 << cross_bit<FWD>(0)))[j];
 #pragma unroll
         for (int st = 0; st < 3; ++st) {
             if (st > 0) {
@@ -732,9 +723,61 @@ __device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 w[3
                 x1 = mul_shoup_lazy(D, w[st].x, w[st].y, q);
             }
         }
+}
+template <bool FWD>
+__device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 w[3], uint64_t q, int logn) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int NS = 1 << (logn - 3), per = NS >> 3;
+    const int p = threadIdx.x & 3, lane_base = (threadIdx.x & 31) & ~3;
+    // 4 lanes per offset: NS / 2 of them, a multiple of 32 (NS >= 128), and blockDim.x a multiple
+    // of 32, so whole warps run each iteration and the shuffles see every lane
+    for (int t = threadIdx.x; t < per * 4; t += blockDim.x) {
+        const int j = SIDX(rank * per + (t >> 2));
+        int lo = ins_bit(p, cross_bit<FWD>(0));
+        uint64_t x0 = cl.map_shared_rank(s, lo)[j], x1 = cl.map_shared_rank(s, lo | (1 << cross_bit<FWD>(0)))[j];
+        cross_stages<FWD>(x0, x1, lo, p, lane_base, w, q);
         cl.map_shared_rank(s, lo)[j] = x0;
         cl.map_shared_rank(s, lo | (1 << cross_bit<FWD>(2)))[j] = x1;
     }
+}
+// An inverse transform's three cross-CTA stages (prime qi, twiddles wi), an elementwise map f to
+// another prime t's residues, then a forward transform's three cross-CTA stages (prime t,
+// twiddles wf), in one pass through distributed shared memory: the inverse's last stage and the
+// forward's first both pair c and c + 4, so each lane already holds its forward pair.  The same
+// values as ntt_cross_step<false>, f on every element, then ntt_cross_step<true>.
+template <class F>
+__device__ __forceinline__ void ntt_cross_inv_fwd(uint64_t *s, const ulonglong2 wi[3], uint64_t qi, F f, const ulonglong2 wf[3], uint64_t t, int logn) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int NS = 1 << (logn - 3), per = NS >> 3;
+    const int p = threadIdx.x & 3, lane_base = (threadIdx.x & 31) & ~3;
+    for (int u = threadIdx.x; u < per * 4; u += blockDim.x) {
+        const int j = SIDX(rank * per + (u >> 2));
+        int lo = ins_bit(p, cross_bit<false>(0));
+        uint64_t x0 = cl.map_shared_rank(s, lo)[j], x1 = cl.map_shared_rank(s, lo | (1 << cross_bit<false>(0)))[j];
+        cross_stages<false>(x0, x1, lo, p, lane_base, wi, qi);  // lo = ins_bit(p, 2) = ins_bit(p, cross_bit<true>(0))
+        x0 = f(x0);
+        x1 = f(x1);
+        cross_stages<true>(x0, x1, lo, p, lane_base, wf, t);
+        cl.map_shared_rank(s, lo)[j] = x0;
+        cl.map_shared_rank(s, lo | (1 << cross_bit<true>(2)))[j] = x1;
+    }
+}
+
+// the local stages (3 .. log N - 1) of ntt_fwd_cluster, after its cross-CTA stages and a cluster
+// barrier that follows the slice's twiddle copy
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd_cluster_local(uint64_t *s, uint64_t q, int logn) {
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int NS = 1 << (logn - 3), off = rank * NS;
+    const TwSliceFwd tws{reinterpret_cast<const ulonglong2 *>(s + cl_tw_offset_words(logn)), rank};
+#pragma unroll(LOGN > 0 ? 16 : 1)
+    for (int s0 = 3; s0 + 1 < (LOGN > 0 ? LOGN : 16); s0 += 2) {  // stages in pairs, the last alone if odd
+        if (s0 + 1 >= logn) break;
+        ntt_fwd_pass_pair(s, tws, q, logn, s0, s0 + 2 == logn, rank * (NS / 4), (rank + 1) * (NS / 4), off);
+    }
+    if (((logn - 3) & 1) != 0) ntt_fwd_pass<1>(s, tws, q, logn, logn - 1, true, rank * (NS / 2), (rank + 1) * (NS / 2), off);
 }
 
 // forward transform of a slice held by each CTA of the cluster; output canonical, bit-reversed
@@ -745,22 +788,30 @@ __device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 w[3
 template <int LOGN = 0>
 __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *__restrict__ tw, uint64_t q, int logn) {
     cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int NS = 1 << (logn - 3), off = rank * NS;
-    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(s + cl_tw_offset_words(logn));
     ulonglong2 wx[3];
     cross_tw_load<true>(wx, tw);
     tw_slice_wait();
     cl.sync();
     ntt_cross_step<true>(s, wx, q, logn);
     cl.sync();
-    const TwSliceFwd tws{stw, rank};
+    ntt_fwd_cluster_local<LOGN>(s, q, logn);
+}
+
+// the local stages (0 .. log N - 4) of ntt_inv_cluster: waits for the slice's twiddle copy and
+// ends with a block barrier, before the cluster barrier of the cross-CTA stages
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv_cluster_local(uint64_t *s, uint64_t q, int logn) {
+    const int rank = (int)cg::this_cluster().block_rank();
+    const int NS = 1 << (logn - 3), off = rank * NS;
+    tw_slice_wait();
+    __syncthreads();
+    const TwSliceInv tws{reinterpret_cast<const ulonglong2 *>(s + cl_tw_offset_words(logn)), rank, 1 << (logn - 1)};
 #pragma unroll(LOGN > 0 ? 16 : 1)
-    for (int s0 = 3; s0 + 1 < (LOGN > 0 ? LOGN : 16); s0 += 2) {  // stages in pairs, the last alone if odd
-        if (s0 + 1 >= logn) break;
-        ntt_fwd_pass_pair(s, tws, q, logn, s0, s0 + 2 == logn, rank * (NS / 4), (rank + 1) * (NS / 4), off);
+    for (int s0 = 0; s0 + 1 < (LOGN > 0 ? LOGN - 3 : 16); s0 += 2) {  // stages in pairs, the last alone if odd
+        if (s0 + 1 >= logn - 3) break;
+        ntt_inv_pass_pair(s, tws, q, logn, s0, rank * (NS / 4), (rank + 1) * (NS / 4), off);
     }
-    if (((logn - 3) & 1) != 0) ntt_fwd_pass<1>(s, tws, q, logn, logn - 1, true, rank * (NS / 2), (rank + 1) * (NS / 2), off);
+    if (((logn - 3) & 1) != 0) ntt_inv_pass<1>(s, tws, q, logn, logn - 4, rank * (NS / 2), (rank + 1) * (NS / 2), off);
 }
 
 // inverse transform (without N^-1) of the slices; output in [0, 2q), natural order (twiddle copy
@@ -768,20 +819,9 @@ __device__ __forceinline__ void ntt_fwd_cluster(uint64_t *s, const ulonglong2 *_
 template <int LOGN = 0>
 __device__ __forceinline__ void ntt_inv_cluster(uint64_t *s, const ulonglong2 *__restrict__ itw, uint64_t q, int logn) {
     cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int NS = 1 << (logn - 3), off = rank * NS;
-    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(s + cl_tw_offset_words(logn));
     ulonglong2 wx[3];
     cross_tw_load<false>(wx, itw);
-    tw_slice_wait();
-    __syncthreads();
-    const TwSliceInv tws{stw, rank, 1 << (logn - 1)};
-#pragma unroll(LOGN > 0 ? 16 : 1)
-    for (int s0 = 0; s0 + 1 < (LOGN > 0 ? LOGN - 3 : 16); s0 += 2) {  // stages in pairs, the last alone if odd
-        if (s0 + 1 >= logn - 3) break;
-        ntt_inv_pass_pair(s, tws, q, logn, s0, rank * (NS / 4), (rank + 1) * (NS / 4), off);
-    }
-    if (((logn - 3) & 1) != 0) ntt_inv_pass<1>(s, tws, q, logn, logn - 4, rank * (NS / 2), (rank + 1) * (NS / 2), off);
+    ntt_inv_cluster_local<LOGN>(s, q, logn);
     cl.sync();
     ntt_cross_step<false>(s, wx, q, logn);
     cl.sync();

@@ -235,6 +235,34 @@ __device__ __forceinline__ void modup_cl_fused_body(const uint64_t *__restrict__
         for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = c1_ntt[(int64_t)u * N + off + k];
         return;
     }
+    if (hi - lo == 1) {
+        // one limb per digit: its inverse transform's cross-CTA stages, the conversion to t and
+        // the forward transform's cross-CTA stages in one pass (ntt_cross_inv_fwd); the same
+        // operations as the general path below
+        const int i = lo;
+        const uint64_t qi = mc[i].q;
+        const ulonglong2 *itw = twiddles(d_tw, i, 1, logn), *tw = twiddles(d_tw, p, 0, logn);
+        if (!tw_issued) tw_prefetch<true, false>(s, itw, logn);
+        for (int k = threadIdx.x; k < len; k += blockDim.x) s[SIDX(k)] = c1_ntt[(int64_t)i * N + off + k];
+        __syncthreads();
+        ulonglong2 wi[3], wf[3];
+        cross_tw_load<false>(wi, itw);
+        cross_tw_load<true>(wf, tw);
+        ntt_inv_cluster_local<LOGN>(s, qi, logn);
+        tw_prefetch<true, true>(s, tw, logn);  // the inverse copy is no longer read
+        cg::this_cluster().sync();
+        const ModConst mi = mc[i];
+        const uint64_t inv = mu.inv[d][0], inv_s = mu.inv_shoup[d][0], hat = mu.hat[d][0][u], hat_s = mu.hat_shoup[d][0][u];
+        ntt_cross_inv_fwd(
+            s, wi, qi,
+            [&](uint64_t x) { return mul_shoup(mul_shoup(mul_shoup(x, mi.ninv, mi.ninv_shoup, qi), inv, inv_s, qi), hat, hat_s, t); }, wf, t,
+            logn);
+        tw_slice_wait();
+        cg::this_cluster().sync();
+        ntt_fwd_cluster_local<LOGN>(s, t, logn);
+        for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = s[SIDX(k)];
+        return;
+    }
     uint64_t *acc = cl_acc_slice(s, logn);
     for (int k = threadIdx.x; k < len; k += blockDim.x) acc[k] = 0;
     for (int i = lo; i < hi; ++i) {
