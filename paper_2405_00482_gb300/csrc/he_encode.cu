@@ -732,6 +732,13 @@ __device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t 
 // integer (word 2(j&1)+1 : word 2(j&1)) of block (j/2, prime index, nonce, 0), key (seed, tag)
 // (nonce_dev, when given, holds the nonce in device memory: read when the kernel runs, so a
 // captured graph draws fresh randomness on every replay)
+// (hi 2^64 + lo) mod q without a 128-bit division: hi reduced by Barrett, then Montgomery
+// reduction gives the value times 2^-64 mod q and a Montgomery product by 2^128 mod q restores the
+// factor; exact and canonical, so the same residue as the division
+__device__ __forceinline__ uint64_t mod128(uint64_t hi, uint64_t lo, const ModConst &m) {
+    return mont_mul(redc(reduce_barrett(hi, m.q, m.mu), lo, m.q, m.qinv), m.r2, m.q, m.qinv);
+}
+
 __global__ void sample_uniform_kernel(uint64_t seed, uint64_t tag, uint64_t nonce, const uint64_t *nonce_dev, LimbMap map,
                                       uint64_t *out, const ModConst *__restrict__ mc, int logn) {
     HE_GRID_DEP();
@@ -739,12 +746,12 @@ __global__ void sample_uniform_kernel(uint64_t seed, uint64_t tag, uint64_t nonc
     const int N = 1 << logn;
     const int l = blockIdx.y;
     const int p = map.prime[l];
-    const uint64_t q = mc[p].q;
+    const ModConst m = mc[p];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < N / 2; b += gridDim.x * blockDim.x) {
         uint64_t c[4] = {(uint64_t)b, (uint64_t)p, nonce, 0};
         philox4x64(c, seed, tag);
-        out[(int64_t)l * N + 2 * b] = (uint64_t)((((u128)c[1]) << 64 | c[0]) % q);
-        out[(int64_t)l * N + 2 * b + 1] = (uint64_t)((((u128)c[3]) << 64 | c[2]) % q);
+        out[(int64_t)l * N + 2 * b] = mod128(c[1], c[0], m);
+        out[(int64_t)l * N + 2 * b + 1] = mod128(c[3], c[2], m);
     }
 }
 
@@ -812,8 +819,8 @@ __global__ void __launch_bounds__(512) encrypt_ntt_cl_kernel(const int64_t *__re
         for (int b = (off >> 1) + threadIdx.x; b < ((off + len) >> 1); b += blockDim.x) {
             uint64_t c[4] = {(uint64_t)b, (uint64_t)l, nonce, 0};
             philox4x64(c, seed, 2);
-            s[SIDX(2 * b - off)] = (uint64_t)((((u128)c[1]) << 64 | c[0]) % q);
-            s[SIDX(2 * b + 1 - off)] = (uint64_t)((((u128)c[3]) << 64 | c[2]) % q);
+            s[SIDX(2 * b - off)] = mod128(c[1], c[0], mc[l]);
+            s[SIDX(2 * b + 1 - off)] = mod128(c[3], c[2], mc[l]);
         }
     } else {  // the error (plus m), four per Philox block
         for (int b = (off >> 2) + threadIdx.x; b < ((off + len) >> 2); b += blockDim.x) {
