@@ -465,8 +465,8 @@ __global__ void encode_cl_kernel(SRC src, double scale, const float4 *__restrict
 #pragma unroll
     for (int r = 0; r < 2; ++r)
         if ((int)threadIdx.x + r * (int)blockDim.x < per) pos_pre[r] = slot_pos[rank * per + threadIdx.x + r * blockDim.x];
+    cl.sync();  // every CTA of the cluster has started before its shared memory is written (no data of an earlier launch)
     HE_GRID_WAIT();
-    cl.sync();  // every CTA of the cluster has started before its shared memory is written
     int r = 0;
     for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x, ++r) {
         const int bt = __brev(r == 0 ? pos_pre[0] : (r == 1 ? pos_pre[1] : slot_pos[j])) >> (32 - logm);
@@ -510,8 +510,8 @@ __global__ void encode_pair_cl_kernel(SRC src, int count, double scale, const fl
 #pragma unroll
     for (int r = 0; r < 2; ++r)
         if ((int)threadIdx.x + r * (int)blockDim.x < per) pos_pre[r] = slot_pos[rank * per + threadIdx.x + r * blockDim.x];
+    cl.sync();  // every CTA of the cluster has started before its shared memory is written (no data of an earlier launch)
     HE_GRID_WAIT();
-    cl.sync();  // every CTA of the cluster has started before its shared memory is written
     int r = 0;
     for (int j = rank * per + threadIdx.x; j < (rank + 1) * per; j += blockDim.x, ++r) {
         const int bt = __brev(r == 0 ? pos_pre[0] : (r == 1 ? pos_pre[1] : slot_pos[j])) >> (32 - logm);
