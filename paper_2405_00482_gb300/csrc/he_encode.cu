@@ -574,6 +574,7 @@ struct DecodeSlots {
             const float4 v = cl.map_shared_rank(a, pos >> lg_ms)[pos & (MS - 1)];
             o[j] = df_to(df{v.x, v.y}) * inv;
         }
+        cl.barrier_arrive();  // done with the other CTAs' shared memory (the kernel waits at its end)
     }
 };
 struct DecodeRas {
@@ -628,6 +629,7 @@ struct DecodeRas {
                 const int64_t rem = ((q >> lt) << clg) + rank, j = slot_of(q, lt, rank, clg);
                 if (row0 + rem < p.m) vals[q] = term_at(j, r == 0 ? pre.pos[0] : (r == 1 ? pre.pos[1] : slot_pos[j]));
             }
+            cl.barrier_arrive();  // done with the other CTAs' shared memory: the row sums overlap the barrier
             __syncthreads();
             const int nw = blockDim.x >= 128 ? 4 : (int)(blockDim.x >> 5);
             if ((int)threadIdx.x < 32 * nw) {
@@ -649,6 +651,7 @@ struct DecodeRas {
             for (int64_t s = 0; s < terms; ++s) acc += term(rem, s);
             y[row0 + rem] = acc;
         }
+        cl.barrier_arrive();
     }
 };
 
@@ -683,7 +686,7 @@ __global__ void decode_cl_kernel(const double *__restrict__ coeffs, double scale
     __syncthreads();
     fft_cluster<CLG, RL, LOGN ? LOGN - 1 : 0>(a, tw, logm, +1);
     epi(cl, a, item, rank, CLG, M, lg_ms, slot_pos, 1.0 / scale, reinterpret_cast<double *>(a + MS), pre);  // the twiddle copy as scratch
-    cl.sync();  // the other CTAs read this one's shared memory until here
+    cl.barrier_wait();  // the epilogue arrived once the other CTAs' shared memory was last read
 }
 
 // decrypt limb 0: m = c0 + c1 s (NTT), inverse NTT, centred, as doubles.  One CTA per
