@@ -462,9 +462,12 @@ __global__ void encode_cl_kernel(SRC src, double scale, const float4 *__restrict
     // the context's tables before the wait: the twiddle copy and the first two slot positions
     fft_tw_issue<CLG>(a, tw, logm);
     int pos_pre[2];
+    float4 tw_pre[2];  // the epilogue's twist factors
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < 2; ++r) {
         if ((int)threadIdx.x + r * (int)blockDim.x < per) pos_pre[r] = slot_pos[rank * per + threadIdx.x + r * blockDim.x];
+        if ((int)threadIdx.x + r * (int)blockDim.x < MS) tw_pre[r] = twist[off + threadIdx.x + r * blockDim.x];
+    }
     cl.sync();  // every CTA of the cluster has started before its shared memory is written (no data of an earlier launch)
     HE_GRID_WAIT();
     int r = 0;
@@ -477,10 +480,11 @@ __global__ void encode_cl_kernel(SRC src, double scale, const float4 *__restrict
     fft_cluster<CLG, RL, LOGN ? LOGN - 1 : 0>(a, tw, logm, -1);
     const df f = df_from(2.0 / (double)N * scale);
     int64_t *o = out + (int64_t)item * N;
-    for (int i = threadIdx.x; i < MS; i += blockDim.x) {
+    r = 0;
+    for (int i = threadIdx.x; i < MS; i += blockDim.x, ++r) {
         const int k = off + i;
         float4 c;
-        cmul(a[i], twist[k], c);
+        cmul(a[i], r == 0 ? tw_pre[0] : (r == 1 ? tw_pre[1] : twist[k]), c);
         o[k] = df_round_ll(df_mul(df{c.x, c.y}, f));
         o[k + M] = df_round_ll(df_mul(df{c.z, c.w}, f));
     }
