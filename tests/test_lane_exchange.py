@@ -191,3 +191,30 @@ def test_cluster_fft_schedules(logn, clg):
     assert [s for s0, nb in passes for s in range(s0, s0 + nb)] == list(range(lg_ms))
     threads = min(512, max(32, MS // 2))
     assert (MS // 2) % 32 == 0 and (MS // 2) % threads == 0
+
+
+@pytest.mark.parametrize("m,n,log_n", [(256, 1024, 13), (1024, 256, 13), (16, 64, 12), (64, 16, 12), (9000, 2, 13), (300, 5000, 13),
+                                       (700, 300, 13), (4096, 256, 14), (100, 20, 11), (20, 100, 10)])
+def test_decode_rotate_and_sum_terms(m, n, log_n):
+    """The decode's rotate-and-sum epilogue (DecodeRas): row rem of a block goes to CTA rem mod CL,
+    its terms s < nb/m' read slot ((rem >> lm) << lnb) + (rem mod m') + (s << lm).  Over a block's
+    rows every slot is read at most once, so each CTA's rows x terms fit the MS doubles of its
+    twiddle copy (the fast path's condition) for the cluster sizes the decoder picks."""
+    from oracle import layout
+
+    slots = 1 << (log_n - 1)
+    p = layout.make_plan(m, n, slots)
+    mb, nb, mp = p.mb, p.nb, p.m_prime
+    lm, lnb = mp.bit_length() - 1, nb.bit_length() - 1
+    terms = nb >> lm
+    seen = set()
+    for rem in range(mb):
+        for s in range(terms):
+            j = ((rem >> lm) << lnb) + (rem & (mp - 1)) + (s << lm)
+            assert 0 <= j < slots and j not in seen
+            seen.add(j)
+    for clg in (1, 2, 3):
+        MS = slots >> clg
+        for rank in range(1 << clg):
+            rows = ((mb - 1 - rank) >> clg) + 1 if rank < mb else 0
+            assert rows * terms <= MS
