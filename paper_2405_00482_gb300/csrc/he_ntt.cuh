@@ -700,29 +700,29 @@ template <bool FWD>
 __device__ __forceinline__ void cross_stages(uint64_t &x0, uint64_t &x1, int &lo, int p, int lane_base, const ulonglong2 w[3], uint64_t q) {
     const uint64_t two_q = 2 * q;
 #pragma unroll
-        for (int st = 0; st < 3; ++st) {
-            if (st > 0) {
-                // this lane's pair from the lanes that held them at stage st - 1 (element c at lane
-                // c with that stage's bit removed, in the slot given by the bit)
-                const int b = cross_bit<FWD>(st), bp = cross_bit<FWD>(st - 1);
-                const int nlo = ins_bit(p, b), nhi = nlo | (1 << b);
-                const int sl = lane_base + del_bit(nlo, bp), sh = lane_base + del_bit(nhi, bp);
-                const uint64_t a0 = shfl64(x0, sl), a1 = shfl64(x1, sl), b0 = shfl64(x0, sh), b1 = shfl64(x1, sh);
-                x0 = (nlo >> bp) & 1 ? a1 : a0;
-                x1 = (nhi >> bp) & 1 ? b1 : b0;
-                lo = nlo;
-            }
-            if (FWD) {  // Cooley-Tukey, lazy: inputs in [0, 4q)
-                const uint64_t X = x0 >= two_q ? x0 - two_q : x0;
-                const uint64_t T = mul_shoup_lazy(x1, w[st].x, w[st].y, q);
-                x0 = X + T;
-                x1 = X - T + two_q;
-            } else {  // Gentleman-Sande, inputs in [0, 2q)
-                const uint64_t X = x0 + x1, D = x0 - x1 + two_q;
-                x0 = X >= two_q ? X - two_q : X;
-                x1 = mul_shoup_lazy(D, w[st].x, w[st].y, q);
-            }
+    for (int st = 0; st < 3; ++st) {
+        if (st > 0) {
+            // this lane's pair from the lanes that held them at stage st - 1 (element c at lane
+            // c with that stage's bit removed, in the slot given by the bit)
+            const int b = cross_bit<FWD>(st), bp = cross_bit<FWD>(st - 1);
+            const int nlo = ins_bit(p, b), nhi = nlo | (1 << b);
+            const int sl = lane_base + del_bit(nlo, bp), sh = lane_base + del_bit(nhi, bp);
+            const uint64_t a0 = shfl64(x0, sl), a1 = shfl64(x1, sl), b0 = shfl64(x0, sh), b1 = shfl64(x1, sh);
+            x0 = (nlo >> bp) & 1 ? a1 : a0;
+            x1 = (nhi >> bp) & 1 ? b1 : b0;
+            lo = nlo;
         }
+        if (FWD) {  // Cooley-Tukey, lazy: inputs in [0, 4q)
+            const uint64_t X = x0 >= two_q ? x0 - two_q : x0;
+            const uint64_t T = mul_shoup_lazy(x1, w[st].x, w[st].y, q);
+            x0 = X + T;
+            x1 = X - T + two_q;
+        } else {  // Gentleman-Sande, inputs in [0, 2q)
+            const uint64_t X = x0 + x1, D = x0 - x1 + two_q;
+            x0 = X >= two_q ? X - two_q : X;
+            x1 = mul_shoup_lazy(D, w[st].x, w[st].y, q);
+        }
+    }
 }
 template <bool FWD>
 __device__ __forceinline__ void ntt_cross_step(uint64_t *s, const ulonglong2 w[3], uint64_t q, int logn) {
