@@ -420,7 +420,7 @@ def run_gpu(args):
         "dtype": "u64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "matmults_per_step": 2, "hoisted_rotations_per_step": rot_per_step,
-                   "l2": "flushed between timed steps (256 MB written, then another 256 MB read)", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MB written, then another 256 MB read, then a one-element write); the timed steps queued behind a 50 ms sleep kernel", "parallelism": f"replicas x{world}",
                    "streams": args.streams, "graph": use_graph},
         "rotations_per_sec": round(rot_per_step * args.steps * world / total_s, 1),
         "matmult_call_ms": {"p50": round(mm_ms[len(mm_ms) // 2], 4), "p99": round(mm_ms[min(len(mm_ms) - 1, int(0.99 * len(mm_ms)))], 4)},
